@@ -1,0 +1,150 @@
+"""Pins of the oracle's best-first batched BnB (Sec. III-E, Algorithm 2):
+exact agreement with exhaustive search where the bound is exact, planted-pose
+recovery, and the threshold rule."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_10023_gb300 import synth
+
+
+def _window_ranges(pose, half_yaw=0.12, rp=0.02):
+    # a 3-cell window of level-2 cells (2 m at r = 0.5) around the planted position
+    x0 = math.floor(pose[0] / 2.0) * 2.0 - 2.0
+    y0 = math.floor(pose[1] / 2.0) * 2.0 - 2.0
+    return oracle.make_ranges((x0, y0, 0.0), (x0 + 3.9, y0 + 3.9, 1.9),
+                              (-rp, -rp, pose[5] - half_yaw), (rp, rp, pose[5] + half_yaw))
+
+
+@pytest.mark.parametrize("scan_index", [0, 1])
+@pytest.mark.parametrize("batch", [1, 64, 100000])
+def test_translation_only_bnb_equals_brute_force(room, scan_index, batch):
+    """Translation-only branching makes the bound exact, so BnB must return the
+    exhaustive maximum over the same leaf set (Sec. III-B: BnB is equivalent to
+    the full search when the bound holds)."""
+    w, m, _, _ = room
+    s, pose = synth.make_scan(1, scan_index)
+    s = s[:200]
+    M = oracle.Maps(m, w.r, w.levels)
+    rg = _window_ranges(pose)
+    flags = oracle.TRANSLATION_ONLY
+    res = oracle.localize(M, s, rg, score_frac=0.5, batch=batch, flags=flags)
+    g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), rg, flags)
+    best, node = oracle.brute_force(M, g, s)
+    assert res.status == oracle.OK
+    assert res.best_score == best
+    assert M.score_nodes(g, s, [list(res.node)])[0] == best
+    assert res.node[6] == 0
+
+
+def test_brute_force_planted_is_k():
+    """Exhaustive search over a window around a planted voxel-centre scan finds
+    all K points at the planted leaf (single exact rotation: zero-width ranges)."""
+    from test_oracle_maps_score import _planted
+    M, g0, scan, leaf, _ = _planted(seed=11, k=60)
+    ang = [g0.angle(0, i, leaf[3 + i]) for i in range(3)]
+    rg = oracle.make_ranges((leaf[0] * 0.5 - 1.0, leaf[1] * 0.5 - 1.0, leaf[2] * 0.5 - 1.0),
+                            (leaf[0] * 0.5 + 0.9, leaf[1] * 0.5 + 0.9, leaf[2] * 0.5 + 0.9), ang, ang)
+    g = oracle.Grid(0.5, 3, 20.0, rg)
+    assert g.N(0) == (1, 1, 1)
+    best, node = oracle.brute_force(M, g, scan)
+    assert best == len(scan)
+    assert M.score_nodes(g, scan, [list(node)])[0] == len(scan)
+
+
+def test_roto_translational_bnb_bounded_by_brute(room):
+    w, m, _, _ = room
+    s, pose = synth.make_scan(1, 0)
+    s = s[:200]
+    M = oracle.Maps(m, w.r, w.levels)
+    rg = _window_ranges(pose)
+    res = oracle.localize(M, s, rg, score_frac=0.5, batch=1000)
+    g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), rg)
+    best, _ = oracle.brute_force(M, g, s)
+    assert res.status == oracle.OK
+    assert res.best_score <= best                 # BnB never beats the full search
+    assert M.score_nodes(g, s, [list(res.node)])[0] == res.best_score
+
+
+def test_room_planted_pose(room):
+    """Full room search recovers the planted pose: translation within one voxel of
+    the returned cell (dilated leaf), yaw within two angular steps, and the paper's
+    own 2.0 m / 0.05 rad success criterion (Sec. IV)."""
+    w, m, s, pose = room
+    M = oracle.Maps(m, w.r, w.levels)
+    rg = oracle.make_ranges(w.lo, w.hi, w.ang_lo, w.ang_hi)
+    res = oracle.localize(M, s, rg, score_frac=w.score_frac, batch=w.batch)
+    assert res.status == oracle.OK
+    g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), rg)
+    assert res.best_score >= math.ceil(0.95 * len(s))
+    for i in range(3):
+        assert abs(res.pose[i] - pose[i]) <= w.r + 0.1
+    dyaw = (res.pose[5] - pose[5] + math.pi) % (2 * math.pi) - math.pi
+    assert abs(dyaw) <= 2 * g.dprime(0)[2]
+    for i in (3, 4):
+        assert abs(res.pose[i] - pose[i]) < 0.05
+
+
+def test_threshold_rule():
+    """score == ceil(theta K) is accepted, one less is not."""
+    from test_oracle_maps_score import _planted
+    M, g, scan, leaf, _ = _planted(seed=3, k=950)
+    far = np.full((50, 3), 1000.0, np.float32)       # never inside the map
+    s = np.concatenate([scan, far])
+    rg = oracle.make_ranges((leaf[0] * 0.5, leaf[1] * 0.5, leaf[2] * 0.5),
+                            (leaf[0] * 0.5 + 0.4, leaf[1] * 0.5 + 0.4, leaf[2] * 0.5 + 0.4),
+                            (g.angle(0, 0, leaf[3]) - 1e-9, g.angle(0, 1, leaf[4]) - 1e-9, g.angle(0, 2, leaf[5]) - 1e-9),
+                            (g.angle(0, 0, leaf[3]) + 1e-9, g.angle(0, 1, leaf[4]) + 1e-9, g.angle(0, 2, leaf[5]) + 1e-9))
+    M0 = oracle.Maps(synth.make_map(1), 0.5, 3, oracle.LEAF_UNDILATED)
+    res = oracle.localize(M0, s, rg, score_frac=0.95, batch=100, d_max=20.0)
+    assert res.status == oracle.OK and res.best_score >= 950
+    res2 = oracle.localize(M0, s[1:], rg, score_frac=0.95, batch=100, d_max=20.0)
+    # 949 planted hits out of 999 points: ceil(0.95 * 999) = 950 is not reached
+    assert res2.status == oracle.NOT_FOUND
+
+
+def test_empty_scan_not_found(room):
+    w, m, _, _ = room
+    M = oracle.Maps(m, w.r, w.levels)
+    rg = oracle.make_ranges(w.lo, w.hi, w.ang_lo, w.ang_hi)
+    res = oracle.localize(M, np.zeros((0, 3), np.float32), rg)
+    assert res.status == oracle.NOT_FOUND
+
+
+def test_invalid_scan_rejected(room):
+    w, m, s, _ = room
+    M = oracle.Maps(m, w.r, w.levels)
+    rg = oracle.make_ranges(w.lo, w.hi, w.ang_lo, w.ang_hi)
+    bad = s.copy()
+    bad[3, 1] = np.inf
+    assert oracle.localize(M, bad, rg).status == oracle.EINVAL
+    assert oracle.localize(M, s, rg, score_frac=0.0).status == oracle.EINVAL
+    assert oracle.localize(M, s, rg, batch=0).status == oracle.EINVAL
+
+
+def test_tie_break_is_lexmin_leaf():
+    """With exact bounds (translation-only) and a batch large enough to expand
+    every top-scoring node each iteration, all leaves tied at the maximum share
+    one bucket when it is popped, so the match is the lexicographic minimum
+    over all tied leaves -- the exhaustive search's lexmin argmax."""
+    from test_oracle_maps_score import _planted
+    _, g0, scan, leaf, _ = _planted(seed=21, k=120)
+    M = oracle.Maps(synth.make_map(1), 0.5, 3)            # dilated leaf: a plateau of ties
+    ang = [g0.angle(0, i, leaf[3 + i]) for i in range(3)]
+    rg = oracle.make_ranges((leaf[0] * 0.5 - 2.0, leaf[1] * 0.5 - 2.0, leaf[2] * 0.5 - 1.0),
+                            (leaf[0] * 0.5 + 1.9, leaf[1] * 0.5 + 1.9, leaf[2] * 0.5 + 0.9), ang, ang)
+    flags = oracle.TRANSLATION_ONLY
+    res = oracle.localize(M, scan, rg, score_frac=0.9, batch=10 ** 9, d_max=20.0, flags=flags)
+    g = oracle.Grid(0.5, 3, 20.0, rg, flags)
+    best, node = oracle.brute_force(M, g, scan)
+    assert res.status == oracle.OK and res.best_score == best == len(scan)
+    tied = 0
+    (a0, a1, a2), (b0, b1, b2) = g.wrange()
+    assert tuple(res.node) == tuple(node)
+    # the plateau really has ties: the planted leaf and its -1 neighbours
+    s = M.score_nodes(g, scan, [[leaf[0] - jx, leaf[1] - jy, leaf[2] - jz, 0, 0, 0, 0]
+                                for jx in (0, 1) for jy in (0, 1) for jz in (0, 1)])
+    tied = int((s == len(scan)).sum())
+    assert tied == 8
