@@ -1,0 +1,209 @@
+/*
+ * bbs.h -- C ABI of libbbs: GPU (sm_103a) batched best-first branch-and-bound
+ * scan matching for global localization, after 3D-BBS (Aoki et al.,
+ * arxiv 2310.10023).
+ *
+ * Problem (Sec. III-A): given a map point cloud M = {m_n} and a LiDAR scan
+ * S = {s_k}, find the pose x = [x, y, z, roll, pitch, yaw] maximizing the
+ * number of transformed scan points that fall into occupied map voxels
+ * (Eq. (1), (11)).  The search is a tree over a pose grid (Sec. III-B/D),
+ * explored best-first in batches (Sec. III-E, Algorithm 2); each node's score
+ * is an exact integer count against a per-level dilated sparse hash voxel
+ * map (Sec. III-C, Eq. (10)).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Return value: BBS_OK (0), BBS_NOT_FOUND (1: no leaf reached the score
+ *   threshold; Algorithm 2 returns a match only "when set"), or a negative
+ *   error code.  Errors never abort the process; bbs_last_error() gives a
+ *   thread-local description of the last failure on the calling thread.
+ * - Point clouds are K x 3 float32, row-major (x, y, z), metres.
+ * - is_device != 0: every pointer argument of the call (clouds, nodes,
+ *   scores) is CUDA device memory on the current device; otherwise host
+ *   memory.  The library only reads inputs during the call and never keeps
+ *   a pointer to caller memory; results go to caller memory.
+ * - Nodes are int32 x 7: (c_x, c_y, c_z, c_alpha, c_beta, c_gamma, c_l) as in
+ *   Sec. III-C: translation index c at level l means a translation of
+ *   c * 2^l * r metres; angle indices are segment indices of the level's
+ *   roll / pitch / yaw grid (Eq. (12)); c_l is the level (0 = leaf).
+ * - Work runs on opts->cuda_stream (NULL: the legacy default stream).  Calls
+ *   return after their work completes on that stream.
+ * - Thread safety: distinct handles are independent; one bbs_maps may be
+ *   shared read-only by concurrent calls.
+ */
+#ifndef BBS_H
+#define BBS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define BBS_OK          0
+#define BBS_NOT_FOUND   1
+#define BBS_EINVAL     -1   /* bad argument: non-finite input, r <= 0, levels outside 1..16, ... */
+#define BBS_ENOMEM     -2   /* device memory or frontier capacity exhausted                       */
+#define BBS_ECUDA      -3   /* a CUDA runtime call failed                                         */
+#define BBS_ETIMEOUT   -4   /* a bounded device wait or the iteration limit ran out               */
+#define BBS_EKEYRANGE  -5   /* a voxel key or translation index beyond +-2^20 fine voxels         */
+#define BBS_ECORRUPT   -6   /* an internal consistency check failed                               */
+
+/* ---- flags (bbs_build_maps and bbs_opts.flags) ------------------------- */
+/* every level uses the level-0 angle grid and only translations branch
+ * (Table I configurations (d)-(f)); the bound is then exact */
+#define BBS_TRANSLATION_ONLY  0x1u
+/* level 0 stores the plain occupancy without the dilation of Sec. III-C
+ * (pass to bbs_build_maps) */
+#define BBS_LEAF_UNDILATED    0x2u
+/* reserved for Algorithm 2's '<' pruning; rejected with BBS_EINVAL */
+#define BBS_PRUNE_GE          0x4u
+/* angle of segment index c is W_min + c * delta' instead of the centre
+ * W_min + (c + 1/2) * delta' */
+#define BBS_ANGLE_LOWER_EDGE  0x8u
+/* rotational children a*c + j literally as printed in Eq. (13) instead of
+ * the finer segments whose centres lie inside the parent's segment */
+#define BBS_CHILD_LITERAL     0x10u
+
+#define BBS_MAX_LEVELS 16
+
+typedef struct bbs_maps bbs_maps;      /* opaque: device-resident hash pyramid */
+
+/* Search ranges (Sec. III-B, III-D): translation box [lo, hi] in metres and
+ * roll / pitch / yaw ranges [ang_lo, ang_hi] in radians (index 0, 1, 2).  The
+ * paper's defaults are the map's bounding box (bbs_maps_bbox), roll and pitch
+ * (-0.02, 0.02) and yaw (0, 2 pi). */
+typedef struct {
+    double lo[3], hi[3];
+    double ang_lo[3], ang_hi[3];
+} bbs_ranges;
+
+/* Search options; a zero field takes its default. */
+typedef struct {
+    double   score_frac;    /* threshold = ceil(score_frac * K); default 0.95 (Sec. IV)       */
+    int64_t  batch;         /* b: children popped per iteration; default 10000 (Sec. IV)     */
+    double   d_max;         /* maximum scan range for Eq. (2); default max_k |s_k|           */
+    uint32_t flags;         /* BBS_* flags                                                   */
+    void*    cuda_stream;   /* cudaStream_t to run on; NULL = legacy default stream          */
+    int64_t  max_frontier;  /* frontier capacity in nodes; default 2^24; BBS_ENOMEM beyond   */
+} bbs_opts;
+
+/* Result of a localization.  pose = x_c of the matched leaf (Sec. III-B):
+ * translation c * r metres, angles of the level-0 grid. */
+typedef struct {
+    int32_t status;         /* same as the return value                                       */
+    int32_t found;          /* 1 if a leaf reached the threshold                              */
+    int32_t best_score;     /* score of the match, or threshold - 1 when not found            */
+    int32_t num_points;     /* K                                                              */
+    int32_t node[7];        /* matched leaf node                                              */
+    double  pose[6];        /* x, y, z (m), roll, pitch, yaw (rad)                            */
+    int64_t nodes_scored;   /* children and initial nodes scored                              */
+    int64_t probes;         /* nodes_scored * K: point-probes                                 */
+    int64_t iterations;     /* batched BnB iterations (Algorithm 2 batches)                   */
+    int64_t peak_frontier;  /* largest frontier size seen                                     */
+    int64_t parents_branched;
+    double  ms_to_optimum;  /* call start to the end of the iteration that set the match      */
+    double  ms_total;       /* call start to return                                           */
+    /* phases after Table III: 0 set source point cloud (upload, d_max, grid,
+     * rotation tables), 1 initial nodes calculation, 2 find best score,
+     * 3 pop remaining queue, 4 result read-back */
+    double  phase_ms[5];
+} bbs_result;
+
+/* ---- maps: Sec. III-C ---------------------------------------------------
+ * bbs_build_maps -- build the per-level voxel maps H^l on the current device.
+ *   xyz, n    : map cloud (n x 3 float32), host or device per is_device.
+ *   r         : finest voxel size r (m), > 0.  Level l has voxel size 2^l r.
+ *   levels    : L in 1..16 (l_max = L - 1).
+ *   flags     : BBS_LEAF_UNDILATED or 0.
+ *   stream    : cudaStream_t or NULL.
+ *   out       : receives the handle; owned by the caller until bbs_free_maps.
+ * Level l holds every voxel floor(u / 2^l) - j, j in {0,1}^3, for each map
+ * point's fine key u = floor(fl32(m * fl32(1/r))) (the dilation of the last
+ * paragraph of Sec. III-C; level 0 undilated with BBS_LEAF_UNDILATED).
+ * Errors: BBS_EINVAL (non-finite point, r <= 0, bad levels, n < 0),
+ * BBS_EKEYRANGE (a fine key with |u| > 2^20 - 4), BBS_ENOMEM, BBS_ECUDA. */
+int  bbs_build_maps(const float* xyz, int64_t n, int is_device, float r, int levels,
+                    uint32_t flags, void* cuda_stream, bbs_maps** out);
+void bbs_free_maps(bbs_maps* maps);
+
+/* Map bounding box of the input cloud (the paper's default translation range). */
+int  bbs_maps_bbox(const bbs_maps* maps, double lo[3], double hi[3]);
+
+/* Statistics of level `level`: stored voxels |H^l|, hash buckets in use,
+ * buckets in the table (T_l), longest probe sequence, and the fraction of
+ * buckets not in their home slot (the collision rate of Sec. III-C). */
+int  bbs_maps_info(const bbs_maps* maps, int level, int64_t* n_voxels, int64_t* n_buckets,
+                   int64_t* table_size, int32_t* max_probe, double* collision_rate);
+
+/* Target load (buckets in use / buckets) of the tables built by later
+ * bbs_build_maps calls in this process; default 0.5.  Sec. III-C sizes T_l
+ * "until the hash collision rate becomes small"; the load trades that rate
+ * against the table's footprint in L2.  BBS_EINVAL outside (0.01, 0.9]. */
+int  bbs_set_load_factor(double load);
+
+/* All voxel keys of level `level` (n_voxels x 3 int32) into the host buffer
+ * out (capacity cap keys); *n receives the count.  BBS_EINVAL if cap is short. */
+int  bbs_maps_keys(const bbs_maps* maps, int level, int32_t* out, int64_t cap, int64_t* n);
+
+/* ---- pose grid: Sec. III-B Eq. (2)-(5), Sec. III-D Eq. (12)-(14) --------
+ * Fills, for one (map, scan, ranges, opts) tuple and one level:
+ *   dims[0..2]  : angle segments N_l for roll, pitch, yaw,
+ *   dims[3..5]  : divisions a_l (Eq. (14); 1 at level 0),
+ *   dims[6..11] : initial translation indices w_min[3], w_max[3] (Eq. (3)-(5)),
+ * and, if A_out is not NULL, the N_alpha N_beta N_gamma scaled rotation
+ * matrices A = fl32(R(alpha, beta, gamma) / r), R = Rz(gamma) Ry(beta) Rx(alpha),
+ * row-major 9 floats each, rotation index (i_a N_b + i_b) N_g + i_g, into the
+ * host buffer A_out (capacity cap matrices).  *n_rot receives N_a N_b N_g. */
+int  bbs_pose_grid(const bbs_maps* maps, const float* scan_xyz, int64_t k, int is_device,
+                   const bbs_ranges* ranges, const bbs_opts* opts, int level, int64_t* dims,
+                   float* A_out, int64_t cap, int64_t* n_rot);
+
+/* ---- scores: Sec. III-C Eq. (11) ------------------------------------------
+ * bbs_score_batch -- score(c) = #{k : key_{c_l}(T_{x_c} s_k) in H^{c_l}} for n
+ * caller nodes.  nodes: n x 7 int32; scores: n int32 (both host or both
+ * device, per is_device).  The fine key of s under node c is
+ * u = floor(fl32(A s)) with FP32 products and sums in the order
+ * ((A_i0 s_x + A_i1 s_y) + A_i2 s_z), no FMA; the level key is
+ * floor((u + c 2^l) / 2^l).  Errors: BBS_EINVAL for a node outside the grid
+ * (level, angle index) or with |c 2^l| > 2^20, or bad scan points. */
+int  bbs_score_batch(const bbs_maps* maps, const float* scan_xyz, int64_t k, int is_device,
+                     const bbs_ranges* ranges, const bbs_opts* opts, const int32_t* nodes,
+                     int64_t n, int32_t* scores);
+
+/* bbs_score_children -- branch (Eq. (13)) and score every child of n parent
+ * nodes with the fused branch-and-score kernel of the search.  Writes, per
+ * parent in order, its children in the order (alpha, beta, gamma, x, y, z)
+ * into child_nodes (cap x 7 int32) and child_scores (cap int32); *n_children
+ * receives the total.  Leaves (level 0) have no children.  Pointers follow
+ * is_device.  BBS_EINVAL if cap is short or a parent is outside the grid. */
+int  bbs_score_children(const bbs_maps* maps, const float* scan_xyz, int64_t k, int is_device,
+                        const bbs_ranges* ranges, const bbs_opts* opts, const int32_t* parents,
+                        int64_t n, int32_t* child_nodes, int32_t* child_scores, int64_t cap,
+                        int64_t* n_children);
+
+/* ---- search: Sec. III-E, Algorithm 2 ---------------------------------------
+ * bbs_localize -- global localization of one scan.  Canonical batched
+ * best-first iteration: best = ceil(theta K) - 1; the frontier F holds scored
+ * nodes bucketed by score; each iteration pops whole top buckets until the
+ * popped parents have at least b children, a bucket at or below best clears
+ * F, a bucket holding a leaf sets best and the match (lexicographic minimum
+ * leaf of that bucket) and clears F; the popped parents are branched
+ * (Eq. (13)) and children scoring above best join F.  ranges NULL: map
+ * bounding box, roll/pitch (-0.02, 0.02), yaw (0, 2 pi).  opts may be NULL.
+ * Returns BBS_OK, BBS_NOT_FOUND, or an error (also in out->status). */
+int  bbs_localize(const bbs_maps* maps, const float* scan_xyz, int64_t k, int is_device,
+                  const bbs_ranges* ranges, const bbs_opts* opts, bbs_result* out);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char* bbs_last_error(void);
+
+/* Library version string. */
+const char* bbs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BBS_H */

@@ -1,0 +1,272 @@
+// bbs_internal.cuh -- shared internals of libbbs (GPU 3D-BBS, arxiv 2310.10023).
+//
+// Layout of a level map H^l (Sec. III-C) in HBM: an open-addressing hash
+// table (linear probing, Eq. (10)) whose buckets are 32-byte "bricks".  A
+// brick covers the 4 x 4 x 4 voxels 4b + [0,4)^3 and stores the occupancy
+// of the overlapping 5 x 5 x 5 block 4b + [0,5)^3 as five 25-bit planes, so
+// the 2 x 2 x 2 voxel block v + {0,1}^3 of ANY voxel v lies inside the single
+// brick floor(v / 4).  One probe -- one 32-byte L2 sector -- therefore
+// answers membership for all eight translational siblings of a branched node
+// (children 2c + j, Eq. (13)) at once.  Membership is exact; the hash
+// function and table size change speed only, never a score.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bbs.h"
+
+namespace bbs {
+
+constexpr int32_t KEY_LIMIT = 1 << 20;         // voxel keys live in [-2^20, 2^20)
+constexpr int32_t MAP_KEY_MAX = (1 << 20) - 4; // |fine map key| bound (BBS_EKEYRANGE beyond)
+constexpr int32_t BRICK_BIAS = 1 << 19;        // brick coordinates in [-2^19, 2^19)
+constexpr unsigned long long EMPTY_KEY = ~0ull;
+constexpr int MAX_LEVELS = BBS_MAX_LEVELS;
+
+struct __align__(32) Brick {
+    unsigned long long key;  // packed brick coordinates, EMPTY_KEY when free
+    uint32_t plane[5];       // plane z: bit (x + 5 y) = voxel 4b + (x, y, z) occupied
+    uint32_t pad;
+};
+static_assert(sizeof(Brick) == 32, "brick must be one 32-byte sector");
+
+// Read-only view of one level's table passed to kernels by value.
+struct LevelView {
+    const Brick* slots;
+    uint32_t shift;   // home slot = hash >> shift   (table size 2^(32 - shift))
+    uint32_t mask;    // table size - 1
+    int32_t maxp;     // longest probe distance of any stored brick
+    int32_t pad;
+};
+
+// Search grid passed to kernels by value.
+struct DevGrid {
+    int32_t levels;
+    uint32_t flags;
+    int32_t N[MAX_LEVELS][3];    // angle segments per level and axis
+    int32_t a[MAX_LEVELS][3];    // Eq. (14) divisions (index l: from l to l-1)
+    int64_t rot_off[MAX_LEVELS]; // first rotation of level l in the rotation table
+};
+
+// Node / task record in HBM: translation indices and (rotation index << 5 | level).
+struct __align__(16) NodeRec {
+    int32_t cx, cy, cz;
+    uint32_t rl;
+};
+
+__host__ __device__ __forceinline__ uint32_t rl_pack(uint32_t rot, int level) { return (rot << 5) | (uint32_t)level; }
+__host__ __device__ __forceinline__ int rl_level(uint32_t rl) { return (int)(rl & 31u); }
+__host__ __device__ __forceinline__ uint32_t rl_rot(uint32_t rl) { return rl >> 5; }
+
+__host__ __device__ __forceinline__ unsigned long long brick_pack(int32_t bx, int32_t by, int32_t bz)
+{
+    return ((unsigned long long)(uint32_t)(bx + BRICK_BIAS) << 40) |
+           ((unsigned long long)(uint32_t)(by + BRICK_BIAS) << 20) |
+           (unsigned long long)(uint32_t)(bz + BRICK_BIAS);
+}
+
+// 32-bit mix of the three brick coordinates; the table uses the top bits.
+__host__ __device__ __forceinline__ uint32_t brick_hash(int32_t bx, int32_t by, int32_t bz)
+{
+    uint32_t h = (uint32_t)bx * 0x9E3779B1u ^ (uint32_t)by * 0x85EBCA77u ^ (uint32_t)bz * 0xC2B2AE3Du;
+    h ^= h >> 16;
+    h *= 0x7FEB352Du;
+    h ^= h >> 15;
+    return h;
+}
+
+__device__ __forceinline__ bool key_in_range(int32_t k)
+{
+    return (uint32_t)(k + KEY_LIMIT) < (uint32_t)(2 * KEY_LIMIT);
+}
+
+// Find brick (bx, by, bz).  On success lo = {key, plane0, plane1},
+// hi = {plane2, plane3, plane4, pad}.  Bounded by the table's longest probe.
+__device__ __forceinline__ bool probe_brick(const LevelView& L, int32_t bx, int32_t by, int32_t bz,
+                                            uint4& lo, uint4& hi)
+{
+    const unsigned long long key = brick_pack(bx, by, bz);
+    uint32_t s = brick_hash(bx, by, bz) >> L.shift;
+    for (int p = 0; p <= L.maxp; ++p) {
+        const uint4* q = reinterpret_cast<const uint4*>(L.slots + ((s + (uint32_t)p) & L.mask));
+        lo = __ldg(q);
+        hi = __ldg(q + 1);
+        const unsigned long long k = ((unsigned long long)lo.y << 32) | lo.x;
+        if (k == key) return true;
+        if (k == EMPTY_KEY) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ uint32_t brick_plane(const uint4& lo, const uint4& hi, int z)
+{
+    uint32_t p = lo.z;
+    p = (z == 1) ? lo.w : p;
+    p = (z == 2) ? hi.x : p;
+    p = (z == 3) ? hi.y : p;
+    p = (z == 4) ? hi.z : p;
+    return p;
+}
+
+// Occupancy of voxel key k at one level (bbs_score_batch).
+__device__ __forceinline__ uint32_t voxel_bit(const LevelView& L, int32_t kx, int32_t ky, int32_t kz)
+{
+    if (!(key_in_range(kx) && key_in_range(ky) && key_in_range(kz))) return 0u;
+    uint4 lo, hi;
+    if (!probe_brick(L, kx >> 2, ky >> 2, kz >> 2, lo, hi)) return 0u;
+    return (brick_plane(lo, hi, kz & 3) >> ((kx & 3) + 5 * (ky & 3))) & 1u;
+}
+
+// Fine voxel key: u_i = floor(((A_i0 s_x + A_i1 s_y) + A_i2 s_z)), every
+// product and sum rounded to FP32 on its own (no FMA), then an exact floor.
+__device__ __forceinline__ int32_t fine_key(float4 row, float4 s)
+{
+    const float q = __fadd_rn(__fadd_rn(__fmul_rn(row.x, s.x), __fmul_rn(row.y, s.y)), __fmul_rn(row.z, s.z));
+    return __float2int_rd(q);
+}
+
+// Rotational children of angle index c at level l: [lo, hi) at level l - 1.
+// Default: the finer segments whose centres fall inside segment c, i.e. the
+// smallest c' with (2c' + 1) N_l >= 2 c N_{l-1} starts the range; with
+// BBS_CHILD_LITERAL the printed a*c + j, j < a, clipped to N_{l-1}.
+__host__ __device__ __forceinline__ int64_t child_first(int64_t np, int64_t nc, int64_t c)
+{
+    const int64_t num = 2 * c * nc - np;
+    return num <= 0 ? 0 : (num + 2 * np - 1) / (2 * np);
+}
+
+__host__ __device__ __forceinline__ void child_range(const DevGrid& g, int l, int ax, int32_t c, int32_t& lo,
+                                                     int32_t& hi)
+{
+    const int64_t np = g.N[l][ax], nc = g.N[l - 1][ax];
+    if (g.flags & BBS_CHILD_LITERAL) {
+        const int64_t a = g.a[l][ax];
+        int64_t x = a * c, y = a * c + a;
+        lo = (int32_t)(x < nc ? x : nc);
+        hi = (int32_t)(y < nc ? y : nc);
+        return;
+    }
+    const int64_t x = child_first(np, nc, c);
+    int64_t y = child_first(np, nc, (int64_t)c + 1);
+    lo = (int32_t)(x < nc ? x : nc);
+    hi = (int32_t)(y < nc ? y : nc);
+}
+
+// number of children of a node at level l (0 for leaves): 8 translations
+// times the rotational children of each axis
+__host__ __device__ __forceinline__ int64_t node_children(const DevGrid& g, int l, uint32_t rot)
+{
+    if (l <= 0) return 0;
+    const int32_t ng = g.N[l][2], nb = g.N[l][1];
+    const int32_t cg = (int32_t)(rot % (uint32_t)ng);
+    const int32_t cb = (int32_t)((rot / (uint32_t)ng) % (uint32_t)nb);
+    const int32_t ca = (int32_t)(rot / ((uint32_t)ng * (uint32_t)nb));
+    int32_t lo, hi;
+    int64_t n = 8;
+    child_range(g, l, 0, ca, lo, hi);
+    n *= (hi - lo);
+    child_range(g, l, 1, cb, lo, hi);
+    n *= (hi - lo);
+    child_range(g, l, 2, cg, lo, hi);
+    n *= (hi - lo);
+    return n;
+}
+
+// ---- host side ------------------------------------------------------------
+
+int set_error(int code, const char* fmt, ...);
+void clear_error();
+
+#define BBS_CUDA_TRY(call)                                                                              \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess)                                                                          \
+            return ::bbs::set_error(BBS_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                                    __LINE__);                                                          \
+    } while (0)
+
+#define BBS_TRY(expr)           \
+    do {                        \
+        int rc_ = (expr);       \
+        if (rc_ < 0) return rc_; \
+    } while (0)
+
+// Per-level host record of a built map.
+struct LevelTable {
+    Brick* slots;
+    int log2T;
+    int32_t maxp;
+    int64_t n_bricks;
+    int64_t n_voxels;
+    int64_t displaced;   // bricks not in their home slot
+};
+
+}  // namespace bbs
+
+struct bbs_maps {
+    int device;
+    int levels;
+    float r;
+    uint32_t flags;
+    double lo[3], hi[3];
+    bbs::LevelTable lv[BBS_MAX_LEVELS];
+    void* arena;          // one device allocation holding every level table
+    size_t arena_bytes;
+};
+
+namespace bbs {
+
+inline LevelView level_view(const bbs_maps* m, int l)
+{
+    LevelView v;
+    v.slots = m->lv[l].slots;
+    v.shift = (uint32_t)(32 - m->lv[l].log2T);
+    v.mask = (uint32_t)((1ull << m->lv[l].log2T) - 1ull);
+    v.maxp = m->lv[l].maxp;
+    v.pad = 0;
+    return v;
+}
+
+// Host pose grid (Sec. III-B Eq. (2)-(5), Sec. III-D Eq. (12)-(14)).
+struct HostGrid {
+    int levels;
+    double r;
+    double d_max;
+    uint32_t flags;
+    double ang_lo[3], ang_range[3];
+    double delta[MAX_LEVELS];
+    double dprime[MAX_LEVELS][3];
+    int64_t N[MAX_LEVELS][3];
+    int64_t a[MAX_LEVELS][3];
+    int64_t wmin[3], wmax[3];
+    int64_t nrot[MAX_LEVELS];
+    int64_t rot_off[MAX_LEVELS];
+    int64_t total_rot;
+};
+
+int grid_build(double r, int levels, double d_max, const bbs_ranges* rg, uint32_t flags, HostGrid* g);
+double grid_angle(const HostGrid& g, int level, int axis, int64_t c);
+DevGrid dev_grid(const HostGrid& g);
+void default_ranges(const bbs_maps* m, bbs_ranges* rg);
+
+// Per-call scan + grid state on the device.
+struct ScanState {
+    float4* scan;      // K points, w = 0
+    int64_t k;
+    double d_max;
+    HostGrid grid;
+    float4* rot;       // 3 float4 rows per rotation, all levels
+};
+
+int scan_prepare(const bbs_maps* m, const float* xyz, int64_t k, int is_device, const bbs_ranges* rg,
+                 const bbs_opts* opts, cudaStream_t st, ScanState* out);
+void scan_release(ScanState* s, cudaStream_t st);
+
+// kernels launched from more than one translation unit
+int launch_score_nodes(const bbs_maps* m, const ScanState& s, const int32_t* d_nodes, int64_t n, int32_t* d_scores,
+                       int* d_err, cudaStream_t st);
+int launch_branch_dense(const bbs_maps* m, const ScanState& s, const NodeRec* d_parents, int64_t n_parents,
+                        int rmax, int32_t* d_scores, cudaStream_t st);
+
+}  // namespace bbs

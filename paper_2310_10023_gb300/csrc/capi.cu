@@ -1,0 +1,335 @@
+// capi.cu -- the extern "C" entry points of libbbs (declared in include/bbs.h).
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "branch.cuh"
+
+namespace bbs {
+
+static thread_local char g_err[512];
+
+int set_error(int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+void clear_error() { g_err[0] = 0; }
+
+int maps_build(const float* xyz, int64_t n, int is_device, float r, int levels, uint32_t flags, cudaStream_t st,
+               bbs_maps** out);
+int maps_keys(const bbs_maps* m, int level, int32_t* out, int64_t cap, int64_t* n);
+int maps_set_load(double load);
+int search_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device, const bbs_ranges* rg,
+               const bbs_opts* opts, cudaStream_t st, bbs_result* res);
+
+// make the maps' device current for the duration of a call
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+static cudaStream_t stream_of(const bbs_opts* o) { return o ? (cudaStream_t)o->cuda_stream : (cudaStream_t)0; }
+
+static int copy_in(const void* src, size_t bytes, int is_device, void** dst, cudaStream_t st, bool* owned)
+{
+    *owned = false;
+    if (is_device) {
+        *dst = const_cast<void*>(src);
+        return BBS_OK;
+    }
+    BBS_CUDA_TRY(cudaMallocAsync(dst, bytes > 0 ? bytes : 1, st));
+    *owned = true;
+    if (bytes) BBS_CUDA_TRY(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, st));
+    return BBS_OK;
+}
+
+}  // namespace bbs
+
+using namespace bbs;
+
+extern "C" {
+
+int bbs_build_maps(const float* xyz, int64_t n, int is_device, float r, int levels, uint32_t flags, void* cuda_stream,
+                   bbs_maps** out)
+{
+    clear_error();
+    if (!out) return set_error(BBS_EINVAL, "build_maps: out is NULL");
+    return maps_build(xyz, n, is_device, r, levels, flags, (cudaStream_t)cuda_stream, out);
+}
+
+void bbs_free_maps(bbs_maps* m)
+{
+    if (!m) return;
+    DeviceGuard g(m->device);
+    for (int l = 0; l < BBS_MAX_LEVELS; ++l)
+        if (m->lv[l].slots) cudaFree(m->lv[l].slots);
+    delete m;
+}
+
+int bbs_maps_bbox(const bbs_maps* m, double lo[3], double hi[3])
+{
+    clear_error();
+    if (!m || !lo || !hi) return set_error(BBS_EINVAL, "maps_bbox: NULL argument");
+    for (int i = 0; i < 3; ++i) {
+        lo[i] = m->lo[i];
+        hi[i] = m->hi[i];
+    }
+    return BBS_OK;
+}
+
+int bbs_maps_info(const bbs_maps* m, int level, int64_t* n_voxels, int64_t* n_buckets, int64_t* table_size,
+                  int32_t* max_probe, double* collision_rate)
+{
+    clear_error();
+    if (!m || level < 0 || level >= m->levels) return set_error(BBS_EINVAL, "maps_info: bad handle or level");
+    const LevelTable& t = m->lv[level];
+    if (n_voxels) *n_voxels = t.n_voxels;
+    if (n_buckets) *n_buckets = t.n_bricks;
+    if (table_size) *table_size = (int64_t)1 << t.log2T;
+    if (max_probe) *max_probe = t.maxp;
+    if (collision_rate) *collision_rate = t.n_bricks ? (double)t.displaced / (double)t.n_bricks : 0.0;
+    return BBS_OK;
+}
+
+int bbs_maps_keys(const bbs_maps* m, int level, int32_t* out, int64_t cap, int64_t* n)
+{
+    clear_error();
+    if (!m || !n) return set_error(BBS_EINVAL, "maps_keys: NULL argument");
+    DeviceGuard g(m->device);
+    return maps_keys(m, level, out, cap, n);
+}
+
+int bbs_pose_grid(const bbs_maps* m, const float* scan_xyz, int64_t k, int is_device, const bbs_ranges* ranges,
+                  const bbs_opts* opts, int level, int64_t* dims, float* A_out, int64_t cap, int64_t* n_rot)
+{
+    clear_error();
+    if (!m || !dims || !n_rot) return set_error(BBS_EINVAL, "pose_grid: NULL argument");
+    DeviceGuard dg(m->device);
+    cudaStream_t st = stream_of(opts);
+    ScanState S;
+    BBS_TRY(scan_prepare(m, scan_xyz, k, is_device, ranges, opts, st, &S));
+    const HostGrid& g = S.grid;
+    int rc = BBS_OK;
+    if (level < 0 || level >= g.levels) rc = set_error(BBS_EINVAL, "pose_grid: level %d", level);
+    if (rc == BBS_OK) {
+        for (int i = 0; i < 3; ++i) {
+            dims[i] = g.N[level][i];
+            dims[3 + i] = g.a[level][i];
+            dims[6 + i] = g.wmin[i];
+            dims[9 + i] = g.wmax[i];
+        }
+        *n_rot = g.nrot[level];
+        if (A_out) {
+            if (cap < g.nrot[level]) {
+                rc = set_error(BBS_EINVAL, "pose_grid: capacity %lld < %lld", (long long)cap, (long long)g.nrot[level]);
+            } else {
+                std::vector<float4> h((size_t)(3 * g.nrot[level]));
+                cudaError_t e = cudaMemcpyAsync(h.data(), S.rot + 3 * g.rot_off[level], sizeof(float4) * h.size(),
+                                                cudaMemcpyDeviceToHost, st);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+                if (e != cudaSuccess) rc = set_error(BBS_ECUDA, "pose_grid: %s", cudaGetErrorString(e));
+                for (int64_t t = 0; rc == BBS_OK && t < g.nrot[level]; ++t)
+                    for (int row = 0; row < 3; ++row) {
+                        const float4 v = h[(size_t)(3 * t + row)];
+                        A_out[9 * t + 3 * row + 0] = v.x;
+                        A_out[9 * t + 3 * row + 1] = v.y;
+                        A_out[9 * t + 3 * row + 2] = v.z;
+                    }
+            }
+        }
+    }
+    scan_release(&S, st);
+    cudaStreamSynchronize(st);
+    return rc;
+}
+
+int bbs_score_batch(const bbs_maps* m, const float* scan_xyz, int64_t k, int is_device, const bbs_ranges* ranges,
+                    const bbs_opts* opts, const int32_t* nodes, int64_t n, int32_t* scores)
+{
+    clear_error();
+    if (!m || n < 0 || (n > 0 && (!nodes || !scores))) return set_error(BBS_EINVAL, "score_batch: bad arguments");
+    if (n == 0) return BBS_OK;
+    DeviceGuard dg(m->device);
+    cudaStream_t st = stream_of(opts);
+    ScanState S;
+    BBS_TRY(scan_prepare(m, scan_xyz, k, is_device, ranges, opts, st, &S));
+    int rc = BBS_OK;
+    void* d_nodes = nullptr;
+    bool own_nodes = false;
+    int32_t* d_scores = scores;
+    int* d_err = nullptr;
+    rc = copy_in(nodes, sizeof(int32_t) * 7 * (size_t)n, is_device, &d_nodes, st, &own_nodes);
+    if (rc == BBS_OK && !is_device && cudaMallocAsync((void**)&d_scores, sizeof(int32_t) * (size_t)n, st) != cudaSuccess)
+        rc = set_error(BBS_ENOMEM, "score_batch: scores buffer");
+    if (rc == BBS_OK && cudaMallocAsync((void**)&d_err, sizeof(int), st) != cudaSuccess)
+        rc = set_error(BBS_ENOMEM, "score_batch: status word");
+    if (rc == BBS_OK && cudaMemsetAsync(d_err, 0, sizeof(int), st) != cudaSuccess) rc = set_error(BBS_ECUDA, "memset");
+    if (rc == BBS_OK) rc = launch_score_nodes(m, S, (const int32_t*)d_nodes, n, d_scores, d_err, st);
+    int herr = 0;
+    if (rc == BBS_OK) {
+        cudaError_t e = cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && !is_device)
+            e = cudaMemcpyAsync(scores, d_scores, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = set_error(BBS_ECUDA, "score_batch: %s", cudaGetErrorString(e));
+        else if (herr) rc = set_error(BBS_EINVAL, "score_batch: a node lies outside the pose grid");
+    }
+    if (own_nodes) cudaFreeAsync(d_nodes, st);
+    if (!is_device && d_scores && d_scores != scores) cudaFreeAsync(d_scores, st);
+    if (d_err) cudaFreeAsync(d_err, st);
+    scan_release(&S, st);
+    cudaStreamSynchronize(st);
+    return rc;
+}
+
+int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int is_device, const bbs_ranges* ranges,
+                       const bbs_opts* opts, const int32_t* parents, int64_t n, int32_t* child_nodes,
+                       int32_t* child_scores, int64_t cap, int64_t* n_children)
+{
+    clear_error();
+    if (!m || n < 0 || !n_children || (n > 0 && !parents)) return set_error(BBS_EINVAL, "score_children: bad arguments");
+    DeviceGuard dg(m->device);
+    cudaStream_t st = stream_of(opts);
+    std::vector<int32_t> hp((size_t)(7 * n));
+    if (n > 0) {
+        if (is_device) {
+            BBS_CUDA_TRY(cudaMemcpyAsync(hp.data(), parents, sizeof(int32_t) * hp.size(), cudaMemcpyDeviceToHost, st));
+            BBS_CUDA_TRY(cudaStreamSynchronize(st));
+        } else {
+            std::memcpy(hp.data(), parents, sizeof(int32_t) * hp.size());
+        }
+    }
+    ScanState S;
+    BBS_TRY(scan_prepare(m, scan_xyz, k, is_device, ranges, opts, st, &S));
+    struct Rel {
+        ScanState* s;
+        cudaStream_t st;
+        ~Rel()
+        {
+            scan_release(s, st);
+            cudaStreamSynchronize(st);
+        }
+    } rel{&S, st};
+    const HostGrid& g = S.grid;
+    const DevGrid dgr = dev_grid(g);
+    std::vector<NodeRec> recs((size_t)n);
+    std::vector<int32_t> cnt((size_t)n), lo((size_t)(3 * n)), ext((size_t)(3 * n));
+    int64_t total = 0;
+    int rmax = 1;
+    for (int64_t p = 0; p < n; ++p) {
+        const int32_t* c = &hp[(size_t)(7 * p)];
+        const int l = c[6];
+        bool ok = l >= 0 && l < g.levels;
+        for (int i = 0; ok && i < 3; ++i) {
+            ok = c[3 + i] >= 0 && c[3 + i] < g.N[l][i];
+            const int64_t t = (int64_t)c[i] * ((int64_t)1 << l);
+            ok = ok && t >= -(int64_t)KEY_LIMIT && t <= (int64_t)KEY_LIMIT;
+        }
+        if (!ok) return set_error(BBS_EINVAL, "score_children: parent %lld lies outside the pose grid", (long long)p);
+        const uint32_t rot = (uint32_t)(((int64_t)c[3] * g.N[l][1] + c[4]) * g.N[l][2] + c[5]);
+        recs[(size_t)p] = NodeRec{c[0], c[1], c[2], rl_pack(rot, l)};
+        int32_t count = 0;
+        if (l > 0) {
+            count = 1;
+            for (int i = 0; i < 3; ++i) {
+                int32_t a0, a1;
+                child_range(dgr, l, i, c[3 + i], a0, a1);
+                lo[(size_t)(3 * p + i)] = a0;
+                ext[(size_t)(3 * p + i)] = a1 - a0;
+                count *= (a1 - a0);
+            }
+        }
+        cnt[(size_t)p] = count;
+        total += 8 * (int64_t)count;
+        rmax = std::max(rmax, count);
+    }
+    *n_children = total;
+    if (total > cap) return set_error(BBS_EINVAL, "score_children: capacity %lld < %lld children", (long long)cap, (long long)total);
+    if (total == 0) return BBS_OK;
+    NodeRec* d_par = nullptr;
+    int32_t* d_dense = nullptr;
+    const int64_t items = n * rmax;
+    BBS_CUDA_TRY(cudaMallocAsync((void**)&d_par, sizeof(NodeRec) * (size_t)n, st));
+    BBS_CUDA_TRY(cudaMallocAsync((void**)&d_dense, sizeof(int32_t) * 8 * (size_t)items, st));
+    BBS_CUDA_TRY(cudaMemcpyAsync(d_par, recs.data(), sizeof(NodeRec) * (size_t)n, cudaMemcpyHostToDevice, st));
+    int rc = launch_branch_dense(m, S, d_par, n, rmax, d_dense, st);
+    std::vector<int32_t> dense((size_t)(8 * items));
+    if (rc == BBS_OK) {
+        cudaError_t e = cudaMemcpyAsync(dense.data(), d_dense, sizeof(int32_t) * dense.size(), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = set_error(BBS_ECUDA, "score_children: %s", cudaGetErrorString(e));
+    }
+    cudaFreeAsync(d_par, st);
+    cudaFreeAsync(d_dense, st);
+    if (rc != BBS_OK) return rc;
+    std::vector<int32_t> on((size_t)(7 * total)), os((size_t)total);
+    int64_t o = 0;
+    for (int64_t p = 0; p < n; ++p) {
+        const int32_t* c = &hp[(size_t)(7 * p)];
+        const int32_t nb = ext[(size_t)(3 * p + 1)], ng = ext[(size_t)(3 * p + 2)];
+        for (int32_t j = 0; j < cnt[(size_t)p]; ++j) {
+            const int32_t ja = j / (nb * ng), jb = (j / ng) % nb, jg = j % ng;
+            for (int t = 0; t < 8; ++t) {
+                int32_t* d = &on[(size_t)(7 * o)];
+                d[0] = 2 * c[0] + (t >> 2);
+                d[1] = 2 * c[1] + ((t >> 1) & 1);
+                d[2] = 2 * c[2] + (t & 1);
+                d[3] = lo[(size_t)(3 * p)] + ja;
+                d[4] = lo[(size_t)(3 * p + 1)] + jb;
+                d[5] = lo[(size_t)(3 * p + 2)] + jg;
+                d[6] = c[6] - 1;
+                os[(size_t)o] = dense[(size_t)(8 * (p * rmax + j) + t)];
+                ++o;
+            }
+        }
+    }
+    if (is_device) {
+        BBS_CUDA_TRY(cudaMemcpyAsync(child_nodes, on.data(), sizeof(int32_t) * on.size(), cudaMemcpyHostToDevice, st));
+        BBS_CUDA_TRY(cudaMemcpyAsync(child_scores, os.data(), sizeof(int32_t) * os.size(), cudaMemcpyHostToDevice, st));
+        BBS_CUDA_TRY(cudaStreamSynchronize(st));
+    } else {
+        std::memcpy(child_nodes, on.data(), sizeof(int32_t) * on.size());
+        std::memcpy(child_scores, os.data(), sizeof(int32_t) * os.size());
+    }
+    return BBS_OK;
+}
+
+int bbs_localize(const bbs_maps* m, const float* scan_xyz, int64_t k, int is_device, const bbs_ranges* ranges,
+                 const bbs_opts* opts, bbs_result* out)
+{
+    clear_error();
+    if (!m || !out) return set_error(BBS_EINVAL, "localize: NULL argument");
+    DeviceGuard dg(m->device);
+    cudaStream_t st = stream_of(opts);
+    int rc = search_run(m, scan_xyz, k, is_device, ranges, opts, st, out);
+    out->status = rc;
+    cudaStreamSynchronize(st);
+    return rc;
+}
+
+const char* bbs_last_error(void) { return g_err; }
+
+const char* bbs_version(void) { return "bbs-gb300 0.1 sm_103a"; }
+
+int bbs_set_load_factor(double load)
+{
+    clear_error();
+    return maps_set_load(load);
+}
+
+}  // extern "C"

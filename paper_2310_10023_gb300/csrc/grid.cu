@@ -1,0 +1,291 @@
+// grid.cu -- pose grid (Sec. III-B Eq. (2)-(5), Sec. III-D Eq. (12)-(14)),
+// scan upload and the per-level rotation tables.
+//
+// The grid is host FP64 arithmetic (a few hundred values).  The rotation
+// tables are built on the GPU from host cos/sin values with IEEE FP64
+// products, sums and a correctly rounded division (__dmul_rn, __dadd_rn,
+// __ddiv_rn), then rounded once to FP32: A = fl32(R / r).  Host code is
+// compiled with -ffp-contract=off and device code with -fmad=false, so every
+// FP64 operation rounds on its own.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "bbs_internal.cuh"
+
+namespace bbs {
+
+// Eq. (2): delta(r) = arccos(1 - r^2 / (2 d_max^2)), argument clamped to
+// [-1, 1]; d_max <= 0 gives pi.
+static double angular_step(double r, double d_max)
+{
+    if (!(d_max > 0.0)) return std::acos(-1.0);
+    double x = 1.0 - (r * r) / (2.0 * d_max * d_max);
+    if (x < -1.0) x = -1.0;
+    if (x > 1.0) x = 1.0;
+    return std::acos(x);
+}
+
+int grid_build(double r, int levels, double d_max, const bbs_ranges* rg, uint32_t flags, HostGrid* g)
+{
+    if (!(r > 0.0) || levels < 1 || levels > MAX_LEVELS)
+        return set_error(BBS_EINVAL, "grid: bad r (%g) or levels (%d)", r, levels);
+    std::memset(g, 0, sizeof(*g));
+    g->levels = levels;
+    g->r = r;
+    g->d_max = d_max;
+    g->flags = flags;
+    for (int i = 0; i < 3; ++i) {
+        if (!(rg->ang_hi[i] >= rg->ang_lo[i]) || !std::isfinite(rg->ang_lo[i]) || !std::isfinite(rg->ang_hi[i]))
+            return set_error(BBS_EINVAL, "grid: angle range %d is empty or not finite", i);
+        if (!(rg->hi[i] >= rg->lo[i]) || !std::isfinite(rg->lo[i]) || !std::isfinite(rg->hi[i]))
+            return set_error(BBS_EINVAL, "grid: translation range %d is empty or not finite", i);
+        g->ang_lo[i] = rg->ang_lo[i];
+        g->ang_range[i] = rg->ang_hi[i] - rg->ang_lo[i];
+    }
+    for (int l = 0; l < levels; ++l) {
+        // translation-only branching keeps the level-0 rotation grid everywhere
+        const int src = (flags & BBS_TRANSLATION_ONLY) ? 0 : l;
+        g->delta[l] = angular_step(std::ldexp(r, src), d_max);
+        for (int i = 0; i < 3; ++i) {
+            const double W = g->ang_range[i];
+            int64_t n = 1;  // a zero-width range is one segment of width 0
+            if (W > 0.0) {
+                const double q = std::ceil(W / g->delta[l]);   // Eq. (12)
+                if (!(q < 1e9)) return set_error(BBS_EINVAL, "grid: %g angle segments", q);
+                n = (int64_t)q;
+                if (n < 1) n = 1;
+            }
+            g->N[l][i] = n;
+            g->dprime[l][i] = W / (double)n;
+        }
+    }
+    // Eq. (14): a = ceil(delta'_l / delta'_{l-1}) = ceil(N_{l-1} / N_l) in
+    // integers; 1 when the finer level has a single segment.
+    for (int l = 1; l < levels; ++l)
+        for (int i = 0; i < 3; ++i) {
+            const int64_t np = g->N[l][i], nc = g->N[l - 1][i];
+            g->a[l][i] = ((flags & BBS_TRANSLATION_ONLY) || nc <= 1) ? 1 : (nc + np - 1) / np;
+        }
+    for (int i = 0; i < 3; ++i) g->a[0][i] = 1;
+    // Eq. (3)-(5): initial translation indices at l_max
+    const double rmax = std::ldexp(r, levels - 1);
+    for (int i = 0; i < 3; ++i) {
+        const double lo = std::floor(rg->lo[i] / rmax), hi = std::ceil(rg->hi[i] / rmax);
+        if (!(std::fabs(lo) < 1e15) || !(std::fabs(hi) < 1e15))
+            return set_error(BBS_EKEYRANGE, "grid: translation range beyond the key range");
+        g->wmin[i] = (int64_t)lo;
+        g->wmax[i] = (int64_t)hi;
+        const int64_t tlo = g->wmin[i] * ((int64_t)1 << (levels - 1));
+        const int64_t thi = (g->wmax[i] + 1) * ((int64_t)1 << (levels - 1));
+        if (tlo < -((int64_t)1 << 20) || thi > ((int64_t)1 << 20))
+            return set_error(BBS_EKEYRANGE, "grid: leaf translations beyond +-2^20 voxels on axis %d", i);
+    }
+    int64_t off = 0;
+    for (int l = 0; l < levels; ++l) {
+        const int64_t n = g->N[l][0] * g->N[l][1] * g->N[l][2];
+        if (n > ((int64_t)1 << 25))
+            return set_error(BBS_EINVAL, "grid: %lld rotations at level %d exceed 2^25", (long long)n, l);
+        g->nrot[l] = n;
+        g->rot_off[l] = off;
+        off += n;
+    }
+    if (off > ((int64_t)1 << 26)) return set_error(BBS_EINVAL, "grid: %lld rotations in total", (long long)off);
+    g->total_rot = off;
+    return BBS_OK;
+}
+
+// Angle of segment c: the segment centre W_min + (c + 1/2) delta' (the
+// paper gives no offset), or W_min + c delta' with BBS_ANGLE_LOWER_EDGE.
+double grid_angle(const HostGrid& g, int level, int axis, int64_t c)
+{
+    const double dp = g.dprime[level][axis];
+    if (g.flags & BBS_ANGLE_LOWER_EDGE) return g.ang_lo[axis] + (double)c * dp;
+    return g.ang_lo[axis] + ((double)c + 0.5) * dp;
+}
+
+DevGrid dev_grid(const HostGrid& g)
+{
+    DevGrid d;
+    std::memset(&d, 0, sizeof(d));
+    d.levels = g.levels;
+    d.flags = g.flags;
+    for (int l = 0; l < g.levels; ++l) {
+        for (int i = 0; i < 3; ++i) {
+            d.N[l][i] = (int32_t)g.N[l][i];
+            d.a[l][i] = (int32_t)g.a[l][i];
+        }
+        d.rot_off[l] = g.rot_off[l];
+    }
+    return d;
+}
+
+void default_ranges(const bbs_maps* m, bbs_ranges* rg)
+{
+    for (int i = 0; i < 3; ++i) {
+        rg->lo[i] = m->lo[i];
+        rg->hi[i] = m->hi[i];
+    }
+    rg->ang_lo[0] = rg->ang_lo[1] = -0.02;   // Sec. IV: roll, pitch (-0.02, 0.02)
+    rg->ang_hi[0] = rg->ang_hi[1] = 0.02;
+    rg->ang_lo[2] = 0.0;                      // Sec. III-D: yaw (0, 2 pi)
+    rg->ang_hi[2] = 2.0 * std::acos(-1.0);
+}
+
+// ---------------------------------------------------------------------------
+// scan upload: K x 3 float -> K float4; d_max and validation in FP64
+// ---------------------------------------------------------------------------
+
+__global__ void scan_pack_kernel(const float* __restrict__ xyz, int64_t k, float4* __restrict__ out, double bound,
+                                 unsigned long long* __restrict__ dmax_bits, int* __restrict__ bad)
+{
+    double m = 0.0;
+    int b = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
+        const float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+        out[i] = make_float4(x, y, z, 0.0f);
+        const double dx = x, dy = y, dz = z;
+        if (!(fabs(dx) <= bound && fabs(dy) <= bound && fabs(dz) <= bound)) b = 1;   // also catches NaN
+        // sqrt((x^2 + y^2) + z^2) with each operation rounded on its own
+        const double d = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+        if (d > m) m = d;
+    }
+    // non-negative doubles order like their bit patterns
+    for (int o = 16; o > 0; o >>= 1) {
+        const double t = __shfl_down_sync(0xffffffffu, m, o);
+        m = t > m ? t : m;
+        b |= __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (b) atomicOr(bad, 1);
+        atomicMax(dmax_bits, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+// A = fl32(R / r), R = Rz(gamma) Ry(beta) Rx(alpha) (Sec. III-A angles);
+// cs holds (cos, sin) of every segment angle, per level and axis.
+__global__ void rotation_table_kernel(const double2* __restrict__ cs, DevGrid g, const int64_t* __restrict__ cs_off,
+                                      int64_t total, double r, float4* __restrict__ out)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        int l = 0;
+        while (l + 1 < g.levels && t >= g.rot_off[l + 1]) ++l;
+        const int64_t rot = t - g.rot_off[l];
+        const int64_t ng = g.N[l][2], nb = g.N[l][1];
+        const int64_t ig = rot % ng, ib = (rot / ng) % nb, ia = rot / (ng * nb);
+        const double2 A_ = cs[cs_off[3 * l + 0] + ia];
+        const double2 B_ = cs[cs_off[3 * l + 1] + ib];
+        const double2 G_ = cs[cs_off[3 * l + 2] + ig];
+        const double ca = A_.x, sa = A_.y, cb = B_.x, sb = B_.y, cg = G_.x, sg = G_.y;
+        double R[9];
+        R[0] = __dmul_rn(cg, cb);
+        R[1] = __dsub_rn(__dmul_rn(__dmul_rn(cg, sb), sa), __dmul_rn(sg, ca));
+        R[2] = __dadd_rn(__dmul_rn(__dmul_rn(cg, sb), ca), __dmul_rn(sg, sa));
+        R[3] = __dmul_rn(sg, cb);
+        R[4] = __dadd_rn(__dmul_rn(__dmul_rn(sg, sb), sa), __dmul_rn(cg, ca));
+        R[5] = __dsub_rn(__dmul_rn(__dmul_rn(sg, sb), ca), __dmul_rn(cg, sa));
+        R[6] = -sb;
+        R[7] = __dmul_rn(cb, sa);
+        R[8] = __dmul_rn(cb, ca);
+        float A[9];
+        for (int i = 0; i < 9; ++i) A[i] = __double2float_rn(__ddiv_rn(R[i], r));
+        out[3 * t + 0] = make_float4(A[0], A[1], A[2], 0.0f);
+        out[3 * t + 1] = make_float4(A[3], A[4], A[5], 0.0f);
+        out[3 * t + 2] = make_float4(A[6], A[7], A[8], 0.0f);
+    }
+}
+
+static int grid_blocks(int64_t n, int threads)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 4096) b = 4096;
+    return (int)b;
+}
+
+int scan_prepare(const bbs_maps* m, const float* xyz, int64_t k, int is_device, const bbs_ranges* rg_in,
+                 const bbs_opts* opts, cudaStream_t st, ScanState* out)
+{
+    std::memset(out, 0, sizeof(*out));
+    if (k < 0) return set_error(BBS_EINVAL, "scan: k < 0");
+    if (k > 0 && !xyz) return set_error(BBS_EINVAL, "scan: NULL points");
+    bbs_ranges rg;
+    if (rg_in) rg = *rg_in;
+    else default_ranges(m, &rg);
+    out->k = k;
+    const int64_t kk = k > 0 ? k : 1;
+    BBS_CUDA_TRY(cudaMallocAsync((void**)&out->scan, sizeof(float4) * (size_t)kk, st));
+    struct Aux { unsigned long long dmax; int bad; int pad; };
+    Aux* d_aux = nullptr;
+    float* d_xyz = nullptr;
+    BBS_CUDA_TRY(cudaMallocAsync((void**)&d_aux, sizeof(Aux), st));
+    BBS_CUDA_TRY(cudaMemsetAsync(d_aux, 0, sizeof(Aux), st));
+    const float* src = xyz;
+    if (k > 0 && !is_device) {
+        BBS_CUDA_TRY(cudaMallocAsync((void**)&d_xyz, sizeof(float) * 3 * (size_t)k, st));
+        BBS_CUDA_TRY(cudaMemcpyAsync(d_xyz, xyz, sizeof(float) * 3 * (size_t)k, cudaMemcpyHostToDevice, st));
+        src = d_xyz;
+    }
+    const double bound = std::ldexp((double)m->r, 18);
+    if (k > 0) {
+        scan_pack_kernel<<<grid_blocks(k, 256), 256, 0, st>>>(src, k, out->scan, bound, &d_aux->dmax, &d_aux->bad);
+        BBS_CUDA_TRY(cudaGetLastError());
+    }
+    Aux aux;
+    BBS_CUDA_TRY(cudaMemcpyAsync(&aux, d_aux, sizeof(Aux), cudaMemcpyDeviceToHost, st));
+    BBS_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFreeAsync(d_aux, st);
+    if (d_xyz) cudaFreeAsync(d_xyz, st);
+    if (aux.bad) {
+        scan_release(out, st);
+        return set_error(BBS_EINVAL, "scan: a coordinate is not finite or exceeds 2^18 r");
+    }
+    double dm;
+    std::memcpy(&dm, &aux.dmax, sizeof(dm));
+    out->d_max = (opts && opts->d_max > 0.0) ? opts->d_max : dm;
+    const uint32_t flags = opts ? opts->flags : 0u;
+    int rc = grid_build((double)m->r, m->levels, out->d_max, &rg, flags, &out->grid);
+    if (rc < 0) {
+        scan_release(out, st);
+        return rc;
+    }
+    // cos / sin of every segment angle (host libm, FP64)
+    const HostGrid& g = out->grid;
+    std::vector<double2> cs;
+    std::vector<int64_t> cs_off(3 * MAX_LEVELS, 0);
+    for (int l = 0; l < g.levels; ++l)
+        for (int i = 0; i < 3; ++i) {
+            cs_off[3 * l + i] = (int64_t)cs.size();
+            for (int64_t c = 0; c < g.N[l][i]; ++c) {
+                const double ang = grid_angle(g, l, i, c);
+                cs.push_back(make_double2(std::cos(ang), std::sin(ang)));
+            }
+        }
+    double2* d_cs = nullptr;
+    int64_t* d_off = nullptr;
+    BBS_CUDA_TRY(cudaMallocAsync((void**)&d_cs, sizeof(double2) * cs.size(), st));
+    BBS_CUDA_TRY(cudaMallocAsync((void**)&d_off, sizeof(int64_t) * cs_off.size(), st));
+    BBS_CUDA_TRY(cudaMemcpyAsync(d_cs, cs.data(), sizeof(double2) * cs.size(), cudaMemcpyHostToDevice, st));
+    BBS_CUDA_TRY(cudaMemcpyAsync(d_off, cs_off.data(), sizeof(int64_t) * cs_off.size(), cudaMemcpyHostToDevice, st));
+    BBS_CUDA_TRY(cudaMallocAsync((void**)&out->rot, sizeof(float4) * 3 * (size_t)g.total_rot, st));
+    rotation_table_kernel<<<grid_blocks(g.total_rot, 256), 256, 0, st>>>(d_cs, dev_grid(g), d_off, g.total_rot,
+                                                                          (double)m->r, out->rot);
+    BBS_CUDA_TRY(cudaGetLastError());
+    // host vectors must outlive the asynchronous copies
+    BBS_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFreeAsync(d_cs, st);
+    cudaFreeAsync(d_off, st);
+    return BBS_OK;
+}
+
+void scan_release(ScanState* s, cudaStream_t st)
+{
+    if (s->scan) cudaFreeAsync(s->scan, st);
+    if (s->rot) cudaFreeAsync(s->rot, st);
+    s->scan = nullptr;
+    s->rot = nullptr;
+}
+
+}  // namespace bbs

@@ -1,0 +1,306 @@
+"""ctypes binding of libbbs (include/bbs.h): same names, argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts numpy arrays
+and torch tensors to pointers, picks host or device residency from the
+arguments, and turns status codes into exceptions.  Loading fails loudly when
+libbbs.so has not been built -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libbbs.so")
+
+OK, NOT_FOUND, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EKEYRANGE, ECORRUPT = 0, 1, -1, -2, -3, -4, -5, -6
+TRANSLATION_ONLY, LEAF_UNDILATED, PRUNE_GE, ANGLE_LOWER_EDGE, CHILD_LITERAL = 0x1, 0x2, 0x4, 0x8, 0x10
+MAX_LEVELS = 16
+
+_lock = threading.Lock()
+_lib = None
+
+
+class BBSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libbbs error {code}: {msg}")
+        self.code = code
+
+
+class Ranges(C.Structure):
+    _fields_ = [("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("ang_lo", C.c_double * 3), ("ang_hi", C.c_double * 3)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("score_frac", C.c_double), ("batch", C.c_int64), ("d_max", C.c_double),
+                ("flags", C.c_uint32), ("cuda_stream", C.c_void_p), ("max_frontier", C.c_int64)]
+
+
+class Result(C.Structure):
+    _fields_ = [
+        ("status", C.c_int32), ("found", C.c_int32), ("best_score", C.c_int32), ("num_points", C.c_int32),
+        ("node", C.c_int32 * 7), ("pose", C.c_double * 6),
+        ("nodes_scored", C.c_int64), ("probes", C.c_int64), ("iterations", C.c_int64),
+        ("peak_frontier", C.c_int64), ("parents_branched", C.c_int64),
+        ("ms_to_optimum", C.c_double), ("ms_total", C.c_double), ("phase_ms", C.c_double * 5),
+    ]
+
+    def as_dict(self) -> dict:
+        return {
+            "status": self.status, "found": self.found, "best_score": self.best_score,
+            "num_points": self.num_points, "node": list(self.node), "pose": list(self.pose),
+            "nodes_scored": self.nodes_scored, "probes": self.probes, "iterations": self.iterations,
+            "peak_frontier": self.peak_frontier, "parents_branched": self.parents_branched,
+            "ms_to_optimum": self.ms_to_optimum, "ms_total": self.ms_total, "phase_ms": list(self.phase_ms),
+        }
+
+
+EXPORTS = ("bbs_build_maps", "bbs_free_maps", "bbs_maps_bbox", "bbs_maps_info", "bbs_maps_keys",
+           "bbs_pose_grid", "bbs_score_batch", "bbs_score_children", "bbs_localize", "bbs_last_error",
+           "bbs_version")
+
+
+def load():
+    """Load libbbs.so; raise if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2310_10023_gb300.build.build() "
+                              "(the CUDA library is required; there is no fallback)")
+        L = C.CDLL(LIB_PATH)
+        P = C.POINTER
+        vp, i64, i32p, f32p, i64p, dp = C.c_void_p, C.c_int64, P(C.c_int32), C.c_void_p, P(C.c_int64), P(C.c_double)
+        L.bbs_build_maps.argtypes = [vp, i64, C.c_int, C.c_float, C.c_int, C.c_uint32, vp, P(C.c_void_p)]
+        L.bbs_free_maps.argtypes = [vp]
+        L.bbs_free_maps.restype = None
+        L.bbs_maps_bbox.argtypes = [vp, dp, dp]
+        L.bbs_maps_info.argtypes = [vp, C.c_int, i64p, i64p, i64p, i32p, dp]
+        L.bbs_maps_keys.argtypes = [vp, C.c_int, vp, i64, i64p]
+        L.bbs_pose_grid.argtypes = [vp, vp, i64, C.c_int, P(Ranges), P(Opts), C.c_int, i64p, vp, i64, i64p]
+        L.bbs_score_batch.argtypes = [vp, vp, i64, C.c_int, P(Ranges), P(Opts), vp, i64, vp]
+        L.bbs_score_children.argtypes = [vp, vp, i64, C.c_int, P(Ranges), P(Opts), vp, i64, vp, vp, i64, i64p]
+        L.bbs_localize.argtypes = [vp, vp, i64, C.c_int, P(Ranges), P(Opts), P(Result)]
+        L.bbs_last_error.restype = C.c_char_p
+        L.bbs_version.restype = C.c_char_p
+        L.bbs_set_load_factor.argtypes = [C.c_double]
+        _lib = L
+        return L
+
+
+def bbs_last_error() -> str:
+    return load().bbs_last_error().decode()
+
+
+def bbs_version() -> str:
+    return load().bbs_version().decode()
+
+
+def _check(rc: int, allow_not_found=False) -> int:
+    if rc == OK or (allow_not_found and rc == NOT_FOUND):
+        return rc
+    raise BBSError(rc, bbs_last_error())
+
+
+# ---- argument marshalling --------------------------------------------------
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _arr(x, dtype, cols=None):
+    """-> (pointer, is_device, n_rows, keepalive)."""
+    if _is_torch(x):
+        import torch
+        tdt = {np.float32: torch.float32, np.int32: torch.int32}[dtype]
+        t = x.detach()
+        if t.dtype != tdt:
+            raise TypeError(f"expected {tdt}, got {t.dtype}")
+        t = t.contiguous()
+        n = t.shape[0] if t.dim() > 0 else 0
+        if cols is not None and (t.dim() != 2 or t.shape[1] != cols):
+            raise ValueError(f"expected shape (n, {cols}), got {tuple(t.shape)}")
+        return C.c_void_p(t.data_ptr()), 1 if t.is_cuda else 0, n, t
+    a = np.ascontiguousarray(x, dtype=dtype)
+    if cols is not None:
+        a = a.reshape(-1, cols)
+    return C.c_void_p(a.ctypes.data), 0, a.shape[0], a
+
+
+def make_ranges(lo, hi, ang_lo, ang_hi) -> Ranges:
+    r = Ranges()
+    for i in range(3):
+        r.lo[i], r.hi[i] = float(lo[i]), float(hi[i])
+        r.ang_lo[i], r.ang_hi[i] = float(ang_lo[i]), float(ang_hi[i])
+    return r
+
+
+def make_opts(score_frac=0.0, batch=0, d_max=0.0, flags=0, stream=None, max_frontier=0) -> Opts:
+    o = Opts()
+    o.score_frac = float(score_frac)
+    o.batch = int(batch)
+    o.d_max = float(d_max)
+    o.flags = int(flags)
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                stream = torch.cuda.current_stream().cuda_stream
+        except Exception:  # noqa: BLE001 - torch is optional here
+            stream = None
+    o.cuda_stream = C.c_void_p(int(stream) if stream else 0)
+    o.max_frontier = int(max_frontier)
+    return o
+
+
+class Maps:
+    """Owning handle of a device-resident voxel-map pyramid."""
+
+    def __init__(self, handle: C.c_void_p, r: float, levels: int, flags: int):
+        self.h = handle
+        self.r = r
+        self.levels = levels
+        self.flags = flags
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().bbs_free_maps(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+
+# ---- the C-ABI, one function each -------------------------------------------
+
+def bbs_build_maps(xyz, r: float, levels: int, flags: int = 0, stream=None) -> Maps:
+    p, dev, n, keep = _arr(xyz, np.float32, 3)
+    h = C.c_void_p()
+    st = make_opts(stream=stream).cuda_stream
+    _check(load().bbs_build_maps(p, n, dev, C.c_float(r), int(levels), int(flags), st, C.byref(h)))
+    del keep
+    return Maps(h, float(np.float32(r)), int(levels), int(flags))
+
+
+def bbs_free_maps(maps: Maps) -> None:
+    maps.close()
+
+
+def bbs_maps_bbox(maps: Maps):
+    lo, hi = (C.c_double * 3)(), (C.c_double * 3)()
+    _check(load().bbs_maps_bbox(maps.h, lo, hi))
+    return tuple(lo), tuple(hi)
+
+
+def bbs_maps_info(maps: Maps, level: int) -> dict:
+    nv, nb, ts = C.c_int64(), C.c_int64(), C.c_int64()
+    mp, cr = C.c_int32(), C.c_double()
+    _check(load().bbs_maps_info(maps.h, int(level), C.byref(nv), C.byref(nb), C.byref(ts), C.byref(mp), C.byref(cr)))
+    return {"voxels": nv.value, "buckets": nb.value, "table_size": ts.value, "max_probe": mp.value,
+            "collision_rate": cr.value}
+
+
+def bbs_maps_keys(maps: Maps, level: int) -> np.ndarray:
+    n = bbs_maps_info(maps, level)["voxels"]
+    out = np.zeros((max(n, 1), 3), np.int32)
+    got = C.c_int64()
+    _check(load().bbs_maps_keys(maps.h, int(level), C.c_void_p(out.ctypes.data), n, C.byref(got)))
+    return out[:got.value]
+
+
+def bbs_pose_grid(maps: Maps, scan, ranges: Ranges | None = None, opts: Opts | None = None, level: int = 0,
+                  tables: bool = True):
+    """-> (dims dict, (n_rot, 9) float32 rotation table or None)."""
+    p, dev, k, keep = _arr(scan, np.float32, 3)
+    opts = opts or make_opts()
+    dims = (C.c_int64 * 12)()
+    nrot = C.c_int64()
+    _check(load().bbs_pose_grid(maps.h, p, k, dev, C.byref(ranges) if ranges else None, C.byref(opts), int(level),
+                                dims, None, 0, C.byref(nrot)))
+    A = None
+    if tables:
+        A = np.zeros((nrot.value, 9), np.float32)
+        _check(load().bbs_pose_grid(maps.h, p, k, dev, C.byref(ranges) if ranges else None, C.byref(opts),
+                                    int(level), dims, C.c_void_p(A.ctypes.data), nrot.value, C.byref(nrot)))
+    del keep
+    d = list(dims)
+    return {"N": tuple(d[0:3]), "a": tuple(d[3:6]), "wmin": tuple(d[6:9]), "wmax": tuple(d[9:12]),
+            "n_rot": nrot.value}, A
+
+
+def bbs_score_batch(maps: Maps, scan, nodes, ranges: Ranges | None = None, opts: Opts | None = None, out=None):
+    """Eq. (11) scores of caller nodes (n x 7 int32).  Device tensors in, device tensor out."""
+    sp, sdev, k, keep1 = _arr(scan, np.float32, 3)
+    npt, ndev, n, keep2 = _arr(nodes, np.int32, 7)
+    if sdev != ndev:
+        raise ValueError("scan and nodes must both be host or both be device memory")
+    if out is None:
+        if ndev:
+            import torch
+            out = torch.empty(n, dtype=torch.int32, device=keep2.device)
+        else:
+            out = np.zeros(n, np.int32)
+    op, odev, _, keep3 = _arr(out, np.int32)
+    if odev != ndev:
+        raise ValueError("scores must have the residency of nodes")
+    opts = opts or make_opts()
+    _check(load().bbs_score_batch(maps.h, sp, k, sdev, C.byref(ranges) if ranges else None, C.byref(opts),
+                                  npt, n, op))
+    del keep1, keep2
+    return keep3 if keep3 is not out and not _is_torch(out) else out
+
+
+def bbs_score_children(maps: Maps, scan, parents, ranges: Ranges | None = None, opts: Opts | None = None):
+    """Children (Eq. (13)) of each parent with their scores, canonical order."""
+    sp, sdev, k, keep1 = _arr(scan, np.float32, 3)
+    pp, pdev, n, keep2 = _arr(parents, np.int32, 7)
+    if sdev or pdev:
+        raise ValueError("bbs_score_children binding takes host arrays")
+    opts = opts or make_opts()
+    cnt = C.c_int64()
+    rg = C.byref(ranges) if ranges else None
+    rc = load().bbs_score_children(maps.h, sp, k, 0, rg, C.byref(opts), pp, n, None, None, 0, C.byref(cnt))
+    if rc not in (OK, EINVAL) or (rc == EINVAL and cnt.value == 0 and n > 0):
+        _check(rc)
+    nodes = np.zeros((max(cnt.value, 1), 7), np.int32)
+    scores = np.zeros(max(cnt.value, 1), np.int32)
+    _check(load().bbs_score_children(maps.h, sp, k, 0, rg, C.byref(opts), pp, n, C.c_void_p(nodes.ctypes.data),
+                                     C.c_void_p(scores.ctypes.data), cnt.value, C.byref(cnt)))
+    del keep1, keep2
+    return nodes[:cnt.value], scores[:cnt.value]
+
+
+def bbs_localize(maps: Maps, scan, ranges: Ranges | None = None, opts: Opts | None = None) -> Result:
+    p, dev, k, keep = _arr(scan, np.float32, 3)
+    opts = opts or make_opts()
+    res = Result()
+    _check(load().bbs_localize(maps.h, p, k, dev, C.byref(ranges) if ranges else None, C.byref(opts),
+                               C.byref(res)), allow_not_found=True)
+    del keep
+    return res
+
+
+def bbs_set_load_factor(load_factor: float) -> None:
+    _check(load().bbs_set_load_factor(float(load_factor)))
+
+
+@dataclass
+class Workload:
+    """Convenience bundle of ranges/opts for a synthetic workload."""
+    ranges: Ranges
+    opts: Opts
+
+
+def workload_args(w, stream=None, **kw) -> Workload:
+    return Workload(make_ranges(w.lo, w.hi, w.ang_lo, w.ang_hi),
+                    make_opts(score_frac=kw.pop("score_frac", w.score_frac), batch=kw.pop("batch", w.batch),
+                              stream=stream, **kw))

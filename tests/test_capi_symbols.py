@@ -1,0 +1,34 @@
+"""The C-ABI library loads and exports every function include/bbs.h declares
+(no compute call: this runs without a GPU)."""
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "bbs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b(bbs_[a-z_]+)\s*\(", src))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2310_10023_gb300 import build, native
+    build.build()
+    lib = native.load()
+    declared = _declared()
+    assert {"bbs_build_maps", "bbs_localize", "bbs_score_batch"} <= declared
+    missing = [n for n in sorted(declared) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_wraps_every_declared_function():
+    from paper_2310_10023_gb300 import native
+    for n in _declared():
+        assert hasattr(native, n), n
+
+
+def test_version_string():
+    from paper_2310_10023_gb300 import native
+    assert "sm_103a" in native.bbs_version()

@@ -1,0 +1,271 @@
+"""GPU (C-ABI) against the CPU oracle on the same seeded inputs.
+
+Integer results are compared exactly: voxel-key sets per level, pose-grid
+dimensions and rotation-table bits, Eq. (11) scores of arbitrary nodes and of
+every child of branched parents, and the search's best score, match,
+iteration count and number of nodes scored.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_10023_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def nv():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_10023_gb300 import build, native
+    build.build()
+    native.load()
+    return native
+
+
+def _keyset(a):
+    return set(map(tuple, np.asarray(a).reshape(-1, 3).tolist()))
+
+
+@pytest.fixture(scope="module")
+def room_pair(nv):
+    w = synth.WORKLOADS["room"]
+    m = synth.make_map(w.scene)
+    return w, m, nv.bbs_build_maps(m, w.r, w.levels), oracle.Maps(m, w.r, w.levels)
+
+
+def _ranges(nv, w, lo=None, hi=None, alo=None, ahi=None):
+    lo, hi = lo or w.lo, hi or w.hi
+    alo, ahi = alo or w.ang_lo, ahi or w.ang_hi
+    return nv.make_ranges(lo, hi, alo, ahi), oracle.make_ranges(lo, hi, alo, ahi)
+
+
+# ---- maps ------------------------------------------------------------------
+
+def test_room_map_levels_equal_oracle(nv, room_pair):
+    w, m, dm, om = room_pair
+    for l in range(w.levels):
+        assert _keyset(nv.bbs_maps_keys(dm, l)) == _keyset(om.keys(l)), l
+        info = nv.bbs_maps_info(dm, l)
+        assert info["voxels"] == om.count(l)
+        assert info["buckets"] * 2 <= info["table_size"] * 1.0 + 1024
+
+
+def test_undilated_leaf_and_device_input(nv):
+    w = synth.WORKLOADS["room"]
+    m = synth.make_map(w.scene)
+    dm = nv.bbs_build_maps(torch.from_numpy(np.array(m)).cuda(), w.r, w.levels, nv.LEAF_UNDILATED)
+    om = oracle.Maps(m, w.r, w.levels, oracle.LEAF_UNDILATED)
+    for l in range(w.levels):
+        assert _keyset(nv.bbs_maps_keys(dm, l)) == _keyset(om.keys(l)), l
+    assert nv.bbs_maps_bbox(dm) == om.bbox()
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_random_cloud_maps_with_negative_keys(nv, seed):
+    rng = np.random.default_rng(seed)
+    pts = rng.normal(0, 30, size=(20000, 3)).astype(np.float32)
+    pts[:50] = rng.uniform(-1e-3, 1e-3, size=(50, 3))          # around the zero boundary
+    for r, L in ((0.37, 5), (2.0, 4)):
+        dm = nv.bbs_build_maps(pts, r, L)
+        om = oracle.Maps(pts, r, L)
+        for l in range(L):
+            assert _keyset(nv.bbs_maps_keys(dm, l)) == _keyset(om.keys(l)), (r, l)
+
+
+def test_map_errors(nv):
+    with pytest.raises(nv.BBSError) as e:
+        nv.bbs_build_maps(np.array([[np.nan, 0, 0]], np.float32), 0.5, 2)
+    assert e.value.code == nv.EINVAL
+    with pytest.raises(nv.BBSError) as e:
+        nv.bbs_build_maps(np.array([[3e6, 0, 0]], np.float32), 1.0, 2)
+    assert e.value.code == nv.EKEYRANGE
+    with pytest.raises(nv.BBSError):
+        nv.bbs_build_maps(np.zeros((4, 3), np.float32), 0.5, 17)
+    dm = nv.bbs_build_maps(np.zeros((0, 3), np.float32), 0.5, 2)
+    assert nv.bbs_maps_info(dm, 0)["voxels"] == 0
+
+
+# ---- pose grid -------------------------------------------------------------
+
+@pytest.mark.parametrize("flags", [0, oracle.ANGLE_LOWER_EDGE, oracle.TRANSLATION_ONLY])
+def test_pose_grid_bits_equal_oracle(nv, room_pair, flags):
+    w, m, dm, om = room_pair
+    s, _ = synth.make_scan(1, 0)
+    nr, orr = _ranges(nv, w)
+    g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), orr, flags)
+    for l in range(w.levels):
+        dims, A = nv.bbs_pose_grid(dm, s, nr, nv.make_opts(flags=flags), l)
+        assert dims["N"] == g.N(l)
+        assert dims["a"] == (g.a(l) if l > 0 else (1, 1, 1))
+        assert (dims["wmin"], dims["wmax"]) == g.wrange()
+        idx = np.arange(len(A)) if len(A) <= 4000 else np.random.default_rng(l).choice(len(A), 4000, replace=False)
+        na, nb, ng = g.N(l)
+        for t in idx:
+            ia, ib, ig = t // (nb * ng), (t // ng) % nb, t % ng
+            assert np.array_equal(A[t].view(np.uint32), g.rotation(l, ia, ib, ig).view(np.uint32)), (l, t)
+
+
+# ---- scores ----------------------------------------------------------------
+
+def _random_nodes(g, rng, n, levels, tmin=-3, tmax=45):
+    out = []
+    for _ in range(n):
+        l = int(rng.integers(0, levels))
+        out.append([int(rng.integers(tmin >> l, (tmax >> l) + 1)), int(rng.integers(tmin >> l, (tmax >> l) + 1)),
+                    int(rng.integers(-2, (12 >> l) + 1)), *(int(rng.integers(0, g.N(l)[i])) for i in range(3)), l])
+    return np.array(out, np.int32)
+
+
+@pytest.mark.parametrize("scan_index", [0, 3])
+def test_score_batch_bit_exact_room(nv, room_pair, scan_index):
+    w, m, dm, om = room_pair
+    s, _ = synth.make_scan(1, scan_index)
+    nr, orr = _ranges(nv, w)
+    g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), orr)
+    nodes = _random_nodes(g, np.random.default_rng(scan_index), 3000, w.levels)
+    got = nv.bbs_score_batch(dm, s, nodes, nr)
+    want = om.score_nodes(g, s, nodes)
+    assert np.array_equal(got, want)
+    # device-resident scan / nodes / scores
+    gd = nv.bbs_score_batch(dm, torch.from_numpy(s).cuda(), torch.from_numpy(nodes).cuda(), nr)
+    assert gd.is_cuda and np.array_equal(gd.cpu().numpy(), want)
+
+
+def test_score_batch_ragged_and_edges(nv, room_pair):
+    w, m, dm, om = room_pair
+    s, _ = synth.make_scan(1, 1)
+    nr, orr = _ranges(nv, w)
+    for k in (1, 31, 33, 257, 999):
+        sk = s[:k]
+        g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(sk), orr)
+        nodes = _random_nodes(g, np.random.default_rng(k), 200, w.levels, tmin=-(1 << 10), tmax=1 << 10)
+        assert np.array_equal(nv.bbs_score_batch(dm, sk, nodes, nr), om.score_nodes(g, sk, nodes)), k
+    # the extreme translations the grid allows: keys far outside the map miss
+    g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), orr)
+    edge = np.array([[(1 << 20) >> l, -((1 << 20) >> l), 0, 0, 0, 0, l] for l in range(w.levels)], np.int32)
+    assert np.array_equal(nv.bbs_score_batch(dm, s, edge, nr), om.score_nodes(g, s, edge))
+    # empty node list
+    assert len(nv.bbs_score_batch(dm, s, np.zeros((0, 7), np.int32), nr)) == 0
+
+
+def test_score_batch_rejects_bad_nodes(nv, room_pair):
+    w, m, dm, om = room_pair
+    s, _ = synth.make_scan(1, 0)
+    nr, _ = _ranges(nv, w)
+    for bad in ([0, 0, 0, 0, 0, 0, 3], [0, 0, 0, -1, 0, 0, 0], [1 << 21, 0, 0, 0, 0, 0, 0]):
+        with pytest.raises(nv.BBSError) as e:
+            nv.bbs_score_batch(dm, s, np.array([bad], np.int32), nr)
+        assert e.value.code == nv.EINVAL
+    bad_scan = s.copy()
+    bad_scan[5, 2] = np.nan
+    with pytest.raises(nv.BBSError):
+        nv.bbs_score_batch(dm, bad_scan, np.zeros((1, 7), np.int32), nr)
+
+
+@pytest.mark.parametrize("flags", [0, oracle.CHILD_LITERAL, oracle.TRANSLATION_ONLY])
+def test_branch_kernel_children_bit_exact(nv, room_pair, flags):
+    """The fused branch-and-score kernel: every child of every parent, in
+    canonical order, with its Eq. (11) score."""
+    w, m, dm, om = room_pair
+    s, _ = synth.make_scan(1, 2)
+    ang = ((-0.05, -0.05, 0.0), (0.05, 0.05, 2 * math.pi)) if flags & oracle.TRANSLATION_ONLY else (w.ang_lo, w.ang_hi)
+    nr, orr = _ranges(nv, w, alo=ang[0], ahi=ang[1])
+    opts = nv.make_opts(flags=flags)
+    g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), orr, flags)
+    rng = np.random.default_rng(flags)
+    parents = _random_nodes(g, rng, 400, w.levels)
+    parents[:, 6] = np.maximum(parents[:, 6], 1)
+    for i, p in enumerate(parents):
+        for a in range(3):
+            parents[i, 3 + a] = min(p[3 + a], g.N(p[6])[a] - 1)
+    nodes, scores = nv.bbs_score_children(dm, s, parents, nr, opts)
+    want_nodes = np.concatenate([g.children(p) for p in parents])
+    assert np.array_equal(nodes, want_nodes)
+    assert np.array_equal(scores, om.score_nodes(g, s, want_nodes))
+
+
+# ---- search ----------------------------------------------------------------
+
+def _same_search(res, ores):
+    assert res.status == ores.status
+    assert res.best_score == ores.best_score
+    if ores.status == oracle.OK:
+        assert list(res.node) == list(ores.node)
+        assert np.allclose(list(res.pose), list(ores.pose), rtol=0, atol=1e-12)
+    assert res.iterations == ores.iterations
+    assert res.nodes_scored == ores.nodes_scored
+
+
+@pytest.mark.parametrize("batch", [1, 500, 10000, 100000])
+def test_room_localize_equals_oracle(nv, room_pair, batch):
+    w, m, dm, om = room_pair
+    s, pose = synth.make_scan(1, 0)
+    nr, orr = _ranges(nv, w)
+    if batch == 1:
+        # sequential best-first on a window (the full room is slow for the oracle at b = 1)
+        x0, y0 = math.floor(pose[0] / 2) * 2 - 2.0, math.floor(pose[1] / 2) * 2 - 2.0
+        nr, orr = _ranges(nv, w, (x0, y0, 0.0), (x0 + 5.9, y0 + 5.9, 3.9),
+                          (-0.05, -0.05, pose[5] - 0.2), (0.05, 0.05, pose[5] + 0.2))
+    res = nv.bbs_localize(dm, s, nr, nv.make_opts(score_frac=w.score_frac, batch=batch))
+    ores = oracle.localize(om, s, orr, score_frac=w.score_frac, batch=batch)
+    _same_search(res, ores)
+    assert res.status == nv.OK
+
+
+@pytest.mark.parametrize("scan_index", [1, 2, 5])
+def test_room_other_scans(nv, room_pair, scan_index):
+    w, m, dm, om = room_pair
+    s, pose = synth.make_scan(1, scan_index)
+    nr, orr = _ranges(nv, w)
+    res = nv.bbs_localize(dm, torch.from_numpy(s).cuda(), nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch))
+    ores = oracle.localize(om, s, orr, score_frac=w.score_frac, batch=w.batch)
+    _same_search(res, ores)
+
+
+def test_translation_only_equals_brute_force(nv, room_pair):
+    w, m, dm, om = room_pair
+    s, pose = synth.make_scan(1, 1)
+    s = s[:200]
+    x0, y0 = math.floor(pose[0] / 2) * 2 - 2.0, math.floor(pose[1] / 2) * 2 - 2.0
+    lo, hi = (x0, y0, 0.0), (x0 + 3.9, y0 + 3.9, 1.9)
+    alo, ahi = (-0.02, -0.02, pose[5] - 0.12), (0.02, 0.02, pose[5] + 0.12)
+    nr, orr = _ranges(nv, w, lo, hi, alo, ahi)
+    flags = oracle.TRANSLATION_ONLY
+    res = nv.bbs_localize(dm, s, nr, nv.make_opts(score_frac=0.5, batch=64, flags=flags))
+    g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), orr, flags)
+    best, _ = oracle.brute_force(om, g, s)
+    assert res.status == nv.OK and res.best_score == best
+    ores = oracle.localize(om, s, orr, score_frac=0.5, batch=64, flags=flags)
+    _same_search(res, ores)
+
+
+def test_not_found_and_empty(nv, room_pair):
+    w, m, dm, om = room_pair
+    s, _ = synth.make_scan(1, 0)
+    nr, orr = _ranges(nv, w)
+    far = s.copy()
+    far[:, 2] = np.float32(30.0)         # a plane 30 m above the room: no point can hit
+    res = nv.bbs_localize(dm, far, nr, nv.make_opts(score_frac=0.5))
+    assert res.status == nv.NOT_FOUND and res.found == 0
+    res = nv.bbs_localize(dm, np.zeros((0, 3), np.float32), nr)
+    assert res.status == nv.NOT_FOUND
+    with pytest.raises(nv.BBSError):
+        nv.bbs_localize(dm, s, nr, nv.make_opts(flags=nv.PRUNE_GE))
+
+
+def test_frontier_capacity_error(nv, room_pair):
+    w, m, dm, om = room_pair
+    s, _ = synth.make_scan(1, 0)
+    nr, _ = _ranges(nv, w)
+    with pytest.raises(nv.BBSError) as e:
+        nv.bbs_localize(dm, s, nr, nv.make_opts(score_frac=0.3, batch=10 ** 7, max_frontier=1000))
+    assert e.value.code == nv.ENOMEM
+    # the handle stays usable after the error
+    res = nv.bbs_localize(dm, s, nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch))
+    assert res.status == nv.OK
