@@ -66,6 +66,9 @@ extern "C" {
 /* rotational children a*c + j literally as printed in Eq. (13) instead of
  * the finer segments whose centres lie inside the parent's segment */
 #define BBS_CHILD_LITERAL     0x10u
+/* time every launch of the scoring kernel with CUDA events on the call's
+ * stream (bbs_result.score_ms); off by default */
+#define BBS_TIME_KERNELS      0x100u
 
 #define BBS_MAX_LEVELS 16
 
@@ -110,6 +113,12 @@ typedef struct {
      * rotation tables), 1 initial nodes calculation, 2 find best score,
      * 3 pop remaining queue, 4 result read-back */
     double  phase_ms[5];
+    int64_t gathers;        /* brick probes issued by the scoring kernel: items x K           */
+    int64_t launches;       /* kernels this call launched                                     */
+    int64_t score_launches; /* launches of the scoring kernel                                 */
+    double  score_ms;       /* their summed device time (BBS_TIME_KERNELS), else 0            */
+    int64_t h2d_bytes;      /* host-to-device bytes the call copied                           */
+    int64_t d2h_bytes;      /* device-to-host bytes the call copied                           */
 } bbs_result;
 
 /* ---- maps: Sec. III-C ---------------------------------------------------
@@ -196,6 +205,15 @@ int  bbs_score_children(const bbs_maps* maps, const float* scan_xyz, int64_t k, 
  * Returns BBS_OK, BBS_NOT_FOUND, or an error (also in out->status). */
 int  bbs_localize(const bbs_maps* maps, const float* scan_xyz, int64_t k, int is_device,
                   const bbs_ranges* ranges, const bbs_opts* opts, bbs_result* out);
+
+/* ---- measurement ----------------------------------------------------------
+ * bbs_bench_gather -- device time (ms, CUDA events on cuda_stream) of
+ * `gathers` random 32-byte bucket reads, issued as the scoring kernel's probes
+ * issue them, over a table of table_bytes (rounded down to a power of two
+ * buckets, at least 1 KiB).  Small tables stay in L2 and give the L2 gather
+ * roofline; tables well above L2 give the HBM one.  The call allocates and
+ * frees its own table. */
+int  bbs_bench_gather(int64_t table_bytes, int64_t gathers, void* cuda_stream, double* ms_out);
 
 /* Thread-local description of the last error on this thread ("" if none). */
 const char* bbs_last_error(void);

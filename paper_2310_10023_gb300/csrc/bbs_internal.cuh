@@ -257,6 +257,7 @@ struct ScanState {
     double d_max;
     HostGrid grid;
     float4* rot;       // 3 float4 rows per rotation, all levels
+    int64_t h2d, d2h;  // bytes copied while preparing
 };
 
 int scan_prepare(const bbs_maps* m, const float* xyz, int64_t k, int is_device, const bbs_ranges* rg,

@@ -226,6 +226,7 @@ int scan_prepare(const bbs_maps* m, const float* xyz, int64_t k, int is_device, 
     if (k > 0 && !is_device) {
         BBS_CUDA_TRY(cudaMallocAsync((void**)&d_xyz, sizeof(float) * 3 * (size_t)k, st));
         BBS_CUDA_TRY(cudaMemcpyAsync(d_xyz, xyz, sizeof(float) * 3 * (size_t)k, cudaMemcpyHostToDevice, st));
+        out->h2d += (int64_t)(sizeof(float) * 3 * (size_t)k);
         src = d_xyz;
     }
     const double bound = std::ldexp((double)m->r, 18);
@@ -235,6 +236,7 @@ int scan_prepare(const bbs_maps* m, const float* xyz, int64_t k, int is_device, 
     }
     Aux aux;
     BBS_CUDA_TRY(cudaMemcpyAsync(&aux, d_aux, sizeof(Aux), cudaMemcpyDeviceToHost, st));
+    out->d2h += (int64_t)sizeof(Aux);
     BBS_CUDA_TRY(cudaStreamSynchronize(st));
     cudaFreeAsync(d_aux, st);
     if (d_xyz) cudaFreeAsync(d_xyz, st);
@@ -269,6 +271,7 @@ int scan_prepare(const bbs_maps* m, const float* xyz, int64_t k, int is_device, 
     BBS_CUDA_TRY(cudaMallocAsync((void**)&d_off, sizeof(int64_t) * cs_off.size(), st));
     BBS_CUDA_TRY(cudaMemcpyAsync(d_cs, cs.data(), sizeof(double2) * cs.size(), cudaMemcpyHostToDevice, st));
     BBS_CUDA_TRY(cudaMemcpyAsync(d_off, cs_off.data(), sizeof(int64_t) * cs_off.size(), cudaMemcpyHostToDevice, st));
+    out->h2d += (int64_t)(sizeof(double2) * cs.size() + sizeof(int64_t) * cs_off.size());
     BBS_CUDA_TRY(cudaMallocAsync((void**)&out->rot, sizeof(float4) * 3 * (size_t)g.total_rot, st));
     rotation_table_kernel<<<grid_blocks(g.total_rot, 256), 256, 0, st>>>(d_cs, dev_grid(g), d_off, g.total_rot,
                                                                           (double)m->r, out->rot);

@@ -546,6 +546,8 @@ int search_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device, co
     hc.top = -1;
     hc.free_top = (unsigned long long)f.nchunks;
     BBS_CUDA_TRY(cudaMemcpyAsync(f.ctl, &hc, sizeof(hc), cudaMemcpyHostToDevice, st));
+    res->h2d_bytes = S.h2d + (int64_t)sizeof(hc);
+    res->d2h_bytes = S.d2h;
 
     BranchArgs ba;
     fill_branch_common(m, S, &ba);
@@ -559,7 +561,34 @@ int search_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device, co
     ba.h_leaf = f.h_leaf;
     ba.err = d_err;
 
+    const bool timed = (flags & BBS_TIME_KERNELS) != 0;
+    std::vector<cudaEvent_t> evs;
+    struct EvRel {
+        std::vector<cudaEvent_t>* v;
+        ~EvRel()
+        {
+            for (cudaEvent_t e : *v) cudaEventDestroy(e);
+        }
+    } evrel{&evs};
+    // scoring launch with optional CUDA-event timing on the call's stream
+    auto score = [&](int mode, const BranchArgs& a2, int64_t items) -> int {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (timed) {
+            BBS_CUDA_TRY(cudaEventCreate(&e0));
+            evs.push_back(e0);
+            BBS_CUDA_TRY(cudaEventCreate(&e1));
+            evs.push_back(e1);
+            BBS_CUDA_TRY(cudaEventRecord(e0, st));
+        }
+        BBS_CUDA_TRY(launch_branch(mode, a2, st));
+        if (timed) BBS_CUDA_TRY(cudaEventRecord(e1, st));
+        res->score_launches++;
+        res->launches++;
+        res->gathers += items * k;
+        return BBS_OK;
+    };
     auto insert = [&]() -> int {
+        res->launches += 2;
         alloc_kernel<<<1, 1024, 0, st>>>(f);
         scatter_kernel<<<1024, 256, 0, st>>>(f);
         BBS_CUDA_TRY(cudaMemsetAsync(&f.ctl->surv, 0, sizeof(unsigned long long), st));
@@ -587,7 +616,7 @@ int search_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device, co
         BranchArgs a2 = ba;
         a2.item0 = i0;
         a2.n_items = std::min(islice, init_items - i0);
-        BBS_CUDA_TRY(launch_branch(MODE_INITIAL, a2, st));
+        BBS_TRY(score(MODE_INITIAL, a2, a2.n_items));
         BBS_TRY(insert());
     }
     res->phase_ms[1] = ms_since(t0) - res->phase_ms[0];
@@ -599,9 +628,11 @@ int search_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device, co
     int64_t iters = 0;
     for (;;) {
         select_kernel<<<1, 1024, 0, st>>>(f);
+        res->launches++;
         BBS_CUDA_TRY(cudaGetLastError());
         BBS_CUDA_TRY(cudaMemcpyAsync(&hc, f.ctl, sizeof(hc), cudaMemcpyDeviceToHost, st));
         BBS_CUDA_TRY(cudaStreamSynchronize(st));
+        res->d2h_bytes += (int64_t)sizeof(hc);
         if (hc.err & 1) return set_error(BBS_ENOMEM, "localize: frontier exceeds %lld nodes", (long long)max_frontier);
         if (hc.err) return set_error(BBS_ECORRUPT, "localize: device error flags 0x%x", hc.err);
         if (hc.match_changed) t_match = ms_since(t0);
@@ -610,27 +641,36 @@ int search_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device, co
         if (iters > (int64_t)1 << 24) return set_error(BBS_ETIMEOUT, "localize: iteration limit");
         res->parents_branched += hc.n_parents;
         res->nodes_scored += hc.popped_kids;
+        res->gathers += (hc.popped_kids / 8) * k;   // one brick probe per point per rotational child
         gather_kernel<<<(int)std::min<int64_t>(std::max<int64_t>(hc.n_pop, 1), 8192), CH, 0, st>>>(f);
+        res->launches++;
         BBS_CUDA_TRY(cudaGetLastError());
         for (int64_t p0 = 0; p0 < hc.n_parents; p0 += pslice) {
             BranchArgs a2 = ba;
             a2.parents = f.parents + p0;
             a2.items_per = rmax;
             a2.n_items = std::min(pslice, hc.n_parents - p0) * rmax;
-            BBS_CUDA_TRY(launch_branch(MODE_SEARCH, a2, st));
+            BBS_TRY(score(MODE_SEARCH, a2, 0));
             BBS_TRY(insert());
         }
         // frontier size after this iteration's insertions
         int64_t sz = 0;
         BBS_CUDA_TRY(cudaMemcpyAsync(&sz, &f.ctl->size, sizeof(sz), cudaMemcpyDeviceToHost, st));
+        res->d2h_bytes += (int64_t)sizeof(sz);
         BBS_CUDA_TRY(cudaStreamSynchronize(st));
         res->peak_frontier = std::max(res->peak_frontier, sz);
     }
     int herr = 0;
     BBS_CUDA_TRY(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    res->d2h_bytes += (int64_t)sizeof(int);
     BBS_CUDA_TRY(cudaStreamSynchronize(st));
     if (herr) return set_error(BBS_ECORRUPT, "localize: survivor staging overflow (0x%x)", herr);
     const double t_end = ms_since(t0);
+    for (size_t i = 0; i + 1 < evs.size(); i += 2) {
+        float ms = 0.0f;
+        BBS_CUDA_TRY(cudaEventElapsedTime(&ms, evs[i], evs[i + 1]));
+        res->score_ms += ms;
+    }
     res->iterations = iters;
     res->probes = res->nodes_scored * k;
     res->best_score = hc.best;

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libbbs.so")
 
 OK, NOT_FOUND, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EKEYRANGE, ECORRUPT = 0, 1, -1, -2, -3, -4, -5, -6
 TRANSLATION_ONLY, LEAF_UNDILATED, PRUNE_GE, ANGLE_LOWER_EDGE, CHILD_LITERAL = 0x1, 0x2, 0x4, 0x8, 0x10
+TIME_KERNELS = 0x100
 MAX_LEVELS = 16
 
 _lock = threading.Lock()
@@ -48,6 +49,8 @@ class Result(C.Structure):
         ("nodes_scored", C.c_int64), ("probes", C.c_int64), ("iterations", C.c_int64),
         ("peak_frontier", C.c_int64), ("parents_branched", C.c_int64),
         ("ms_to_optimum", C.c_double), ("ms_total", C.c_double), ("phase_ms", C.c_double * 5),
+        ("gathers", C.c_int64), ("launches", C.c_int64), ("score_launches", C.c_int64), ("score_ms", C.c_double),
+        ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -57,6 +60,8 @@ class Result(C.Structure):
             "nodes_scored": self.nodes_scored, "probes": self.probes, "iterations": self.iterations,
             "peak_frontier": self.peak_frontier, "parents_branched": self.parents_branched,
             "ms_to_optimum": self.ms_to_optimum, "ms_total": self.ms_total, "phase_ms": list(self.phase_ms),
+            "gathers": self.gathers, "launches": self.launches, "score_launches": self.score_launches,
+            "score_ms": self.score_ms, "h2d_bytes": self.h2d_bytes, "d2h_bytes": self.d2h_bytes,
         }
 
 
@@ -90,6 +95,7 @@ def load():
         L.bbs_last_error.restype = C.c_char_p
         L.bbs_version.restype = C.c_char_p
         L.bbs_set_load_factor.argtypes = [C.c_double]
+        L.bbs_bench_gather.argtypes = [C.c_int64, C.c_int64, vp, P(C.c_double)]
         _lib = L
         return L
 
@@ -291,6 +297,14 @@ def bbs_localize(maps: Maps, scan, ranges: Ranges | None = None, opts: Opts | No
 
 def bbs_set_load_factor(load_factor: float) -> None:
     _check(load().bbs_set_load_factor(float(load_factor)))
+
+
+def bbs_bench_gather(table_bytes: int, gathers: int, stream=None) -> float:
+    """Device milliseconds of `gathers` random 32-byte bucket reads."""
+    ms = C.c_double()
+    _check(load().bbs_bench_gather(int(table_bytes), int(gathers), make_opts(stream=stream).cuda_stream,
+                                   C.byref(ms)))
+    return ms.value
 
 
 @dataclass
