@@ -193,6 +193,32 @@ int  bbs_score_children(const bbs_maps* maps, const float* scan_xyz, int64_t k, 
                         int64_t n, int32_t* child_nodes, int32_t* child_scores, int64_t cap,
                         int64_t* n_children);
 
+/* ---- scores without allocation ---------------------------------------------
+ * bbs_score_batch_noalloc -- the scores of bbs_score_batch for callers that
+ * cannot allocate memory while they run: real-time control loops that must
+ * not touch an allocator after start-up (unbounded latency, fragmentation),
+ * frameworks that own all device memory through their own pool, and servers
+ * that budget every byte up front.  The paper has no counterpart; this is a
+ * deployment variant of the Eq. (11) scoring above.
+ *   scan_xyz, nodes, scores : DEVICE memory on the maps' device (k x 3 float32,
+ *                             n x 7 int32, n int32), as in bbs_score_batch.
+ * It calls no cudaMalloc/cudaFree and no allocating routine; its scratch
+ * (the packed scan and the angle cosines/sines) is one file-scope device
+ * array of 3 MiB + 4 KiB that every GPU loading the library keeps until the
+ * process exits.  Limits: k <= BBS_NOALLOC_MAX_POINTS and at most
+ * BBS_NOALLOC_MAX_ANGLES angle segments summed over levels and axes;
+ * beyond them the call returns BBS_EINVAL and does no GPU work.  All calls
+ * share the array and it keeps the last call's contents (the status words are
+ * cleared at the start of each call), so calls that overlap on the GPU race:
+ * serialize them.  The first call on a device looks up the array's device
+ * address with that device current; make it before any stream capture.
+ * Same errors as bbs_score_batch. */
+#define BBS_NOALLOC_MAX_POINTS 131072
+#define BBS_NOALLOC_MAX_ANGLES 65536
+int  bbs_score_batch_noalloc(const bbs_maps* maps, const float* scan_xyz, int64_t k,
+                             const bbs_ranges* ranges, const bbs_opts* opts, const int32_t* nodes,
+                             int64_t n, int32_t* scores);
+
 /* ---- search: Sec. III-E, Algorithm 2 ---------------------------------------
  * bbs_localize -- global localization of one scan.  Canonical batched
  * best-first iteration: best = ceil(theta K) - 1; the frontier F holds scored

@@ -96,6 +96,7 @@ def load():
         L.bbs_version.restype = C.c_char_p
         L.bbs_set_load_factor.argtypes = [C.c_double]
         L.bbs_bench_gather.argtypes = [C.c_int64, C.c_int64, vp, P(C.c_double)]
+        L.bbs_score_batch_noalloc.argtypes = [vp, vp, i64, P(Ranges), P(Opts), vp, i64, vp]
         _lib = L
         return L
 
@@ -263,6 +264,30 @@ def bbs_score_batch(maps: Maps, scan, nodes, ranges: Ranges | None = None, opts:
                                   npt, n, op))
     del keep1, keep2
     return keep3 if keep3 is not out and not _is_torch(out) else out
+
+
+NOALLOC_MAX_POINTS = 131072
+NOALLOC_MAX_ANGLES = 65536
+
+
+def bbs_score_batch_noalloc(maps: Maps, scan, nodes, scores, ranges: Ranges | None = None,
+                            opts: Opts | None = None):
+    """Scores of caller nodes into the caller's `scores`, with no allocation
+    inside the library: scan, nodes and scores must be device tensors.  For
+    callers that cannot allocate while they run (real-time loops, external
+    memory pools).  Overlapping calls race on the library's shared scratch."""
+    sp, sdev, k, keep1 = _arr(scan, np.float32, 3)
+    npt, ndev, n, keep2 = _arr(nodes, np.int32, 7)
+    op, odev, no, keep3 = _arr(scores, np.int32)
+    if not (sdev and ndev and odev):
+        raise ValueError("bbs_score_batch_noalloc takes device tensors only")
+    if no < n:
+        raise ValueError("scores is shorter than nodes")
+    opts = opts or make_opts()
+    _check(load().bbs_score_batch_noalloc(maps.h, sp, k, C.byref(ranges) if ranges else None, C.byref(opts),
+                                          npt, n, op))
+    del keep1, keep2, keep3
+    return scores
 
 
 def bbs_score_children(maps: Maps, scan, parents, ranges: Ranges | None = None, opts: Opts | None = None):
