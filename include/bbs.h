@@ -153,6 +153,13 @@ int  bbs_maps_info(const bbs_maps* maps, int level, int64_t* n_voxels, int64_t* 
  * against the table's footprint in L2.  BBS_EINVAL outside (0.01, 0.9]. */
 int  bbs_set_load_factor(double load);
 
+/* Bucket layout of the tables built by later bbs_build_maps calls in this
+ * process: 0 (default) uses the compact layout -- a 32-bit key relative to the
+ * level's key box and one 16-byte load per probe -- for every level whose box
+ * fits 8192 x 8192 x 4092 voxels, the wide layout (64-bit key, 32-byte probe)
+ * otherwise; 1 always uses the wide layout.  Scores do not depend on it. */
+int  bbs_set_probe_layout(int layout);
+
 /* All voxel keys of level `level` (n_voxels x 3 int32) into the host buffer
  * out (capacity cap keys); *n receives the count.  BBS_EINVAL if cap is short. */
 int  bbs_maps_keys(const bbs_maps* maps, int level, int32_t* out, int64_t cap, int64_t* n);
@@ -240,6 +247,19 @@ int  bbs_localize(const bbs_maps* maps, const float* scan_xyz, int64_t k, int is
  * roofline; tables well above L2 give the HBM one.  The call allocates and
  * frees its own table. */
 int  bbs_bench_gather(int64_t table_bytes, int64_t gathers, void* cuda_stream, double* ms_out);
+
+/* bbs_localize_many -- n independent localizations against one map, advanced
+ * together: every iteration pops one canonical batch from each live search
+ * and scores the children of all of them in shared launches (the scans may
+ * have different sizes).  scans[i] points to ks[i] x 3 float32 (host or
+ * device per is_device); out[i] receives scan i's result, identical to what
+ * bbs_localize returns for it alone (same best score, match, iterations and
+ * nodes scored; times and launch counts are those of the shared run).  The
+ * frontier capacity opts->max_frontier is shared by all n searches.  Returns
+ * BBS_OK when every search ran (each out[i].status tells found / not found),
+ * or an error for the whole call. */
+int  bbs_localize_many(const bbs_maps* maps, int n, const float* const* scans, const int64_t* ks,
+                       int is_device, const bbs_ranges* ranges, const bbs_opts* opts, bbs_result* out);
 
 /* Thread-local description of the last error on this thread ("" if none). */
 const char* bbs_last_error(void);

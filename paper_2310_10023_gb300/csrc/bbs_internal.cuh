@@ -32,13 +32,48 @@ struct __align__(32) Brick {
 static_assert(sizeof(Brick) == 32, "brick must be one 32-byte sector");
 
 // Read-only view of one level's table passed to kernels by value.
+//
+// Two bucket layouts.  "Wide": a 64-bit absolute brick key and the five
+// planes (two 16-byte loads per probe).  "Compact", used whenever the level's
+// voxels fit in 8192 x 8192 x 4092 keys: bricks are indexed relative to
+// `base` (a multiple of 4 at least 4 below the smallest stored key) and packed
+// into 32 bits (x 11, y 11, z 10 bits); each 16-byte half of the bucket repeats
+// the key and holds the three planes a query can need, [key, p0, p1, p2 |
+// key, p2, p3, p4], so a probe is ONE 16-byte load of half (oz >> 1).  A query
+// block outside [base, base + rmax] cannot touch a stored voxel and is a miss
+// without any load.
 struct LevelView {
     const Brick* slots;
     uint32_t shift;   // home slot = hash >> shift   (table size 2^(32 - shift))
     uint32_t mask;    // table size - 1
     int32_t maxp;     // longest probe distance of any stored brick
-    int32_t pad;
+    int32_t compact;  // bucket layout
+    int32_t base[3];  // compact: key origin (multiple of 4)
+    uint32_t rmax[3]; // compact: largest relative key a query block may start at
 };
+
+constexpr uint32_t CEMPTY = 0xFFFFFFFFu;
+
+__host__ __device__ __forceinline__ uint32_t cbrick_pack(uint32_t bx, uint32_t by, uint32_t bz)
+{
+    return bx | (by << 11) | (bz << 22);
+}
+
+__host__ __device__ __forceinline__ uint32_t cbrick_hash(uint32_t key) { return key * 0x9E3779B1u; }
+
+// Compact probe of relative brick (bx, by, bz), half `h` (0: planes 0-2, 1: planes 2-4).
+// On success w = {key, plane a, plane a+1, plane a+2} with a = 2h.
+__device__ __forceinline__ bool probe_compact(const LevelView& L, uint32_t key, int h, uint4& w)
+{
+    const uint32_t s = cbrick_hash(key) >> L.shift;
+    for (int p = 0; p <= L.maxp; ++p) {
+        const uint4* q = reinterpret_cast<const uint4*>(L.slots + ((s + (uint32_t)p) & L.mask)) + h;
+        w = __ldg(q);
+        if (w.x == key) return true;
+        if (w.x == CEMPTY) return false;
+    }
+    return false;
+}
 
 // Search grid passed to kernels by value.
 struct DevGrid {
@@ -112,6 +147,14 @@ __device__ __forceinline__ uint32_t brick_plane(const uint4& lo, const uint4& hi
 // Occupancy of voxel key k at one level (bbs_score_batch).
 __device__ __forceinline__ uint32_t voxel_bit(const LevelView& L, int32_t kx, int32_t ky, int32_t kz)
 {
+    if (L.compact) {
+        const uint32_t rx = (uint32_t)(kx - L.base[0]), ry = (uint32_t)(ky - L.base[1]), rz = (uint32_t)(kz - L.base[2]);
+        if (rx > L.rmax[0] || ry > L.rmax[1] || rz > L.rmax[2]) return 0u;
+        uint4 w;
+        const int oz = (int)(rz & 3u);
+        if (!probe_compact(L, cbrick_pack(rx >> 2, ry >> 2, rz >> 2), oz >> 1, w)) return 0u;
+        return (((oz & 1) ? w.z : w.y) >> ((rx & 3u) + 5u * (ry & 3u))) & 1u;
+    }
     if (!(key_in_range(kx) && key_in_range(ky) && key_in_range(kz))) return 0u;
     uint4 lo, hi;
     if (!probe_brick(L, kx >> 2, ky >> 2, kz >> 2, lo, hi)) return 0u;
@@ -197,6 +240,9 @@ struct LevelTable {
     Brick* slots;
     int log2T;
     int32_t maxp;
+    int32_t compact;
+    int32_t base[3];
+    uint32_t rmax[3];
     int64_t n_bricks;
     int64_t n_voxels;
     int64_t displaced;   // bricks not in their home slot
@@ -224,7 +270,11 @@ inline LevelView level_view(const bbs_maps* m, int l)
     v.shift = (uint32_t)(32 - m->lv[l].log2T);
     v.mask = (uint32_t)((1ull << m->lv[l].log2T) - 1ull);
     v.maxp = m->lv[l].maxp;
-    v.pad = 0;
+    v.compact = m->lv[l].compact;
+    for (int i = 0; i < 3; ++i) {
+        v.base[i] = m->lv[l].base[i];
+        v.rmax[i] = m->lv[l].rmax[i];
+    }
     return v;
 }
 
@@ -267,7 +317,5 @@ void scan_release(ScanState* s, cudaStream_t st);
 // kernels launched from more than one translation unit
 int launch_score_nodes(const bbs_maps* m, const ScanState& s, const int32_t* d_nodes, int64_t n, int32_t* d_scores,
                        int* d_err, cudaStream_t st);
-int launch_branch_dense(const bbs_maps* m, const ScanState& s, const NodeRec* d_parents, int64_t n_parents,
-                        int rmax, int32_t* d_scores, cudaStream_t st);
 
 }  // namespace bbs

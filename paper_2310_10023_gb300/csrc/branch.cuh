@@ -1,4 +1,5 @@
-// branch.cuh -- argument blocks of the scoring kernels.
+// branch.cuh -- the fused branch-and-score kernel and the search engine's
+// device structures.
 #pragma once
 
 #include <cstring>
@@ -6,6 +7,10 @@
 #include "bbs_internal.cuh"
 
 namespace bbs {
+
+constexpr int CH = 256;        // nodes per frontier chunk
+constexpr int PCHUNK = 2048;   // scan points staged in shared memory per CTA
+constexpr int MAXSEG = 64;     // searches per scoring launch
 
 struct ScoreArgs {
     LevelView maps[MAX_LEVELS];
@@ -19,44 +24,100 @@ struct ScoreArgs {
     int* err;
 };
 
+// Control block of one search (device).
+struct Ctl {
+    int32_t best;          // provisional best score (threshold - 1 at start)
+    int32_t top;           // every bucket above top is empty
+    int32_t found;
+    int32_t done;
+    NodeRec match;
+    int64_t size;          // nodes in F
+    int64_t peak;          // largest size after an insertion
+    int64_t n_parents;     // parents popped by the last select
+    int64_t n_pop;         // chunks popped by the last select
+    int64_t n_act;         // chunks in use
+    int64_t popped_kids;   // children of the parents popped by the last select
+    int32_t err;           // 1 pool exhausted
+    int32_t reason;        // last select: 1 batch full, 2 below best, 3 leaf, 4 F emptied, 0 F was empty
+    int32_t match_changed;
+    int32_t active;        // slot in use
+};
+
+// One search slot (device).  Frontier arrays have K + 1 buckets.
+struct SearchDev {
+    const float4* scan;
+    const float4* rot;
+    int32_t K;
+    int32_t lmax;
+    int64_t batch;
+    int32_t pmin[3], pext[3];   // virtual parents of the initial set
+    int32_t wmin[3], wmax[3];   // initial translation window, Eq. (3)-(5)
+    DevGrid grid;
+    LevelView maps[MAX_LEVELS];
+    int64_t* b_cnt;
+    int64_t* b_kids;
+    int64_t* b_leaf;
+    int32_t* b_tail;
+    uint32_t* h_cnt;
+    unsigned long long* h_kids;
+    uint32_t* h_leaf;
+    uint32_t* w_pos;
+    int32_t* w_space;
+    int64_t* w_choff;
+    int32_t* w_tail;
+    int32_t* w_fill0;
+    int32_t* act;
+    int32_t* pop_ids;
+    int64_t* pop_start;
+    Ctl* ctl;                   // this search's control block (contiguous across searches)
+};
+
+// The shared chunk pool (device).
+struct PoolDev {
+    NodeRec* nodes;
+    int32_t* chunk_bucket;
+    int32_t* chunk_fill;
+    int32_t* free_ids;
+    unsigned long long* free_top;
+    int64_t nchunks;
+};
+
 enum { MODE_INITIAL = 0, MODE_SEARCH = 1, MODE_DENSE = 2 };
 
-struct BranchArgs {
-    LevelView maps[MAX_LEVELS];
-    DevGrid grid;
-    const float4* rot;
-    const float4* scan;
-    int64_t k;
-    // work items: parents x items_per (MODE_SEARCH / MODE_DENSE) or virtual
-    // parents x rotations at init_level (MODE_INITIAL)
+// A run of parents of one search inside a scoring launch.
+struct Seg {
+    int64_t first_parent;   // into the parent array, or the first virtual parent (initial set)
+    int64_t first_work;     // first (parent, point chunk) work item
+    int64_t n_parents;
+    int64_t dense_base;     // first dense child-score slot of the run
+    int32_t chunks;         // point chunks per parent
+    int32_t sid;
+    int32_t R;              // dense task slots per parent
+    int32_t pad;
+};
+
+struct BranchLaunch {
+    const SearchDev* S;
     const NodeRec* parents;
-    int64_t n_items;              // used when n_items_dev is NULL
-    const int64_t* n_items_dev;   // device parent count; items = count * items_per
-    int64_t items_per;
-    // MODE_INITIAL: virtual parents p in pmin + [0, pext), children 2p + j kept
-    // when inside [wmin, wmax] (the initial set of Eq. (3)-(5))
-    int64_t item0;                // MODE_INITIAL: first item of this launch
-    int32_t init_level;
-    int32_t pmin[3], pext[3];
-    int32_t wmin[3], wmax[3];
-    // MODE_DENSE output: 8 scores per item (-1 where no child)
-    int32_t* dense;
-    // MODE_SEARCH / MODE_INITIAL output: survivors with score > *best
-    const int32_t* best;
-    NodeRec* surv_nodes;
-    int32_t* surv_scores;
-    unsigned long long* surv_count;
-    int64_t surv_cap;
-    uint32_t* h_cnt;              // per score: survivors
-    unsigned long long* h_kids;   // per score: their children
-    uint32_t* h_leaf;             // per score: leaves among them
+    int32_t* dense;          // (parent, task, child) scores, zeroed before the launch
+    int64_t n_work;
+    int64_t n_dense;
+    int32_t nseg;
+    int32_t mode;
+    Seg seg[MAXSEG];
+};
+
+// survivors of a finalize pass
+struct SurvOut {
+    NodeRec* nodes;
+    int32_t* scores;
+    int32_t* sid;
+    unsigned long long* count;
+    int64_t cap;
     int* err;
 };
 
-// launch the fused branch-and-score kernel in one of the modes above
-cudaError_t launch_branch(int mode, const BranchArgs& a, cudaStream_t st);
-
-void fill_branch_common(const bbs_maps* m, const ScanState& s, BranchArgs* a);
-int branch_blocks(int64_t items);
+cudaError_t launch_branch(const BranchLaunch& L, cudaStream_t st);
+cudaError_t launch_finalize(const BranchLaunch& L, SearchDev* S, const SurvOut& out, cudaStream_t st);
 
 }  // namespace bbs

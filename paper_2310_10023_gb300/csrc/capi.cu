@@ -3,6 +3,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "branch.cuh"
@@ -26,8 +27,30 @@ int maps_build(const float* xyz, int64_t n, int is_device, float r, int levels, 
                bbs_maps** out);
 int maps_keys(const bbs_maps* m, int level, int32_t* out, int64_t cap, int64_t* n);
 int maps_set_load(double load);
+int maps_set_layout(int layout);
 int search_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device, const bbs_ranges* rg,
                const bbs_opts* opts, cudaStream_t st, bbs_result* res);
+int search_run_many(const bbs_maps* m, int n, const float* const* scans, const int64_t* ks, int is_device,
+                    const bbs_ranges* rg, const bbs_opts* opts, cudaStream_t st, bbs_result* res);
+
+// Keep memory freed by cudaFreeAsync in the device's default pool instead of
+// returning it to the driver at every synchronization: the search allocates
+// its frontier per call, and re-mapping hundreds of MB each time would cost
+// milliseconds.  Set once per device for this process.
+static void keep_pool_memory(int dev)
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    if (dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done[dev] = true;
+}
 
 // make the maps' device current for the duration of a call
 struct DeviceGuard {
@@ -36,6 +59,7 @@ struct DeviceGuard {
     explicit DeviceGuard(int dev)
     {
         if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = cudaSetDevice(dev) == cudaSuccess;
+        keep_pool_memory(dev);
     }
     ~DeviceGuard()
     {
@@ -69,6 +93,9 @@ int bbs_build_maps(const float* xyz, int64_t n, int is_device, float r, int leve
 {
     clear_error();
     if (!out) return set_error(BBS_EINVAL, "build_maps: out is NULL");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    keep_pool_memory(dev);
     return maps_build(xyz, n, is_device, r, levels, flags, (cudaStream_t)cuda_stream, out);
 }
 
@@ -261,19 +288,58 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
     *n_children = total;
     if (total > cap) return set_error(BBS_EINVAL, "score_children: capacity %lld < %lld children", (long long)cap, (long long)total);
     if (total == 0) return BBS_OK;
+    // one search slot for the fused kernel (no frontier: dense scores only)
+    SearchDev sd;
+    std::memset(&sd, 0, sizeof(sd));
+    sd.scan = S.scan;
+    sd.rot = S.rot;
+    sd.K = (int32_t)k;
+    sd.lmax = g.levels - 1;
+    sd.grid = dgr;
+    for (int l = 0; l < MAX_LEVELS; ++l) sd.maps[l] = l < m->levels ? level_view(m, l) : LevelView{};
+    SearchDev* d_sd = nullptr;
     NodeRec* d_par = nullptr;
     int32_t* d_dense = nullptr;
     const int64_t items = n * rmax;
+    BBS_CUDA_TRY(cudaMallocAsync((void**)&d_sd, sizeof(SearchDev), st));
     BBS_CUDA_TRY(cudaMallocAsync((void**)&d_par, sizeof(NodeRec) * (size_t)n, st));
     BBS_CUDA_TRY(cudaMallocAsync((void**)&d_dense, sizeof(int32_t) * 8 * (size_t)items, st));
+    BBS_CUDA_TRY(cudaMemcpyAsync(d_sd, &sd, sizeof(sd), cudaMemcpyHostToDevice, st));
     BBS_CUDA_TRY(cudaMemcpyAsync(d_par, recs.data(), sizeof(NodeRec) * (size_t)n, cudaMemcpyHostToDevice, st));
-    int rc = launch_branch_dense(m, S, d_par, n, rmax, d_dense, st);
+    BBS_CUDA_TRY(cudaMemsetAsync(d_dense, 0, sizeof(int32_t) * 8 * (size_t)items, st));
+    int rc = BBS_OK;
+    const int chunks = (int)((k + PCHUNK - 1) / PCHUNK);
+    // parents in runs of at most 2^20 per launch (kernel argument block holds 64 runs)
+    for (int64_t p0 = 0; rc == BBS_OK && p0 < n && chunks > 0; p0 += ((int64_t)MAXSEG << 20)) {
+        BranchLaunch L;
+        std::memset(&L, 0, sizeof(L));
+        L.S = d_sd;
+        L.parents = d_par;
+        L.dense = d_dense;
+        L.mode = MODE_SEARCH;
+        int64_t work = 0;
+        for (int64_t q = p0; q < n && L.nseg < MAXSEG; q += ((int64_t)1 << 20)) {
+            Seg& sg = L.seg[L.nseg++];
+            sg.first_parent = q;
+            sg.first_work = work;
+            sg.n_parents = std::min<int64_t>((int64_t)1 << 20, n - q);
+            sg.dense_base = q * rmax * 8;
+            sg.chunks = chunks;
+            sg.sid = 0;
+            sg.R = rmax;
+            work += sg.n_parents * chunks;
+        }
+        L.n_work = work;
+        cudaError_t e = launch_branch(L, st);
+        if (e != cudaSuccess) rc = set_error(BBS_ECUDA, "score_children: %s", cudaGetErrorString(e));
+    }
     std::vector<int32_t> dense((size_t)(8 * items));
     if (rc == BBS_OK) {
         cudaError_t e = cudaMemcpyAsync(dense.data(), d_dense, sizeof(int32_t) * dense.size(), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rc = set_error(BBS_ECUDA, "score_children: %s", cudaGetErrorString(e));
     }
+    cudaFreeAsync(d_sd, st);
     cudaFreeAsync(d_par, st);
     cudaFreeAsync(d_dense, st);
     if (rc != BBS_OK) return rc;
@@ -322,6 +388,22 @@ int bbs_localize(const bbs_maps* m, const float* scan_xyz, int64_t k, int is_dev
     return rc;
 }
 
+int bbs_localize_many(const bbs_maps* m, int n, const float* const* scans, const int64_t* ks, int is_device,
+                      const bbs_ranges* ranges, const bbs_opts* opts, bbs_result* out)
+{
+    clear_error();
+    if (!m || n < 0 || (n > 0 && (!scans || !ks || !out))) return set_error(BBS_EINVAL, "localize_many: bad arguments");
+    if (n > 4096) return set_error(BBS_EINVAL, "localize_many: more than 4096 scans");
+    if (n == 0) return BBS_OK;
+    DeviceGuard dg(m->device);
+    cudaStream_t st = stream_of(opts);
+    int rc = search_run_many(m, n, scans, ks, is_device, ranges, opts, st, out);
+    cudaStreamSynchronize(st);
+    if (rc < 0)
+        for (int i = 0; i < n; ++i) out[i].status = rc;
+    return rc;
+}
+
 const char* bbs_last_error(void) { return g_err; }
 
 const char* bbs_version(void) { return "bbs-gb300 0.1 sm_103a"; }
@@ -330,6 +412,12 @@ int bbs_set_load_factor(double load)
 {
     clear_error();
     return maps_set_load(load);
+}
+
+int bbs_set_probe_layout(int layout)
+{
+    clear_error();
+    return maps_set_layout(layout);
 }
 
 }  // extern "C"

@@ -1,0 +1,889 @@
+// engine.cu -- device-resident batched best-first BnB (Sec. III-E,
+// Algorithm 2) for one or many searches at once.
+//
+// Every search owns a frontier F of scored nodes bucketed by integer score;
+// node records live in chunks of CH from one shared free-chunk stack.  A
+// search's non-empty bucket owns its chunks (all full but its tail) and every
+// chunk in use is listed in the search's active list, tagged by bucket.
+//
+// One iteration advances every live search by one canonical batch:
+//   select  (1 CTA per search) walk buckets from the top with a block-wide
+//           prefix of their children counts; the first bucket reached with
+//           children(P) >= b stops, one at or below best clears F, one holding
+//           a leaf sets (best, lexmin leaf) and clears F; buckets above it pop.
+//   gather  popped chunks -> one dense parent array (all searches), chunks freed
+//   score   (branch.cu) every child of every parent; finalize keeps > best
+//   alloc   (1 CTA per search) chunks for each bucket's survivors
+//   scatter survivors into their buckets' chunks
+// Only popping a leaf changes a search's best, so how its batch is split into
+// launches, and which other searches share them, cannot change its result.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "branch.cuh"
+
+namespace bbs {
+
+// ---- block helpers (1024 threads) ------------------------------------------
+
+__device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t* total, int64_t* sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t s = sh[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        sh[lane] = s;
+    }
+    __syncthreads();
+    const int64_t before = (wid > 0 ? sh[wid - 1] : 0) + x - v;
+    *total = sh[31];
+    __syncthreads();
+    return before;
+}
+
+__device__ __forceinline__ int block_min_int(int v, int* sh)
+{
+    v = __reduce_min_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int x = sh[threadIdx.x];
+        x = __reduce_min_sync(0xffffffffu, x);
+        if (threadIdx.x == 0) sh[32] = x;
+    }
+    __syncthreads();
+    const int r = sh[32];
+    __syncthreads();
+    return r;
+}
+
+// lexicographic order of (c_x, c_y, c_z, rotation index); rotation index order
+// equals (c_alpha, c_beta, c_gamma) order
+struct LexKey {
+    unsigned long long t;
+    uint32_t r;
+};
+
+__device__ __forceinline__ LexKey lex_of(const NodeRec& n)
+{
+    LexKey k;
+    k.t = ((unsigned long long)(uint32_t)(n.cx + KEY_LIMIT) << 42) | ((unsigned long long)(uint32_t)(n.cy + KEY_LIMIT) << 21) |
+          (unsigned long long)(uint32_t)(n.cz + KEY_LIMIT);
+    k.r = rl_rot(n.rl);
+    return k;
+}
+
+__device__ __forceinline__ bool lex_lt(const LexKey& a, const LexKey& b) { return a.t < b.t || (a.t == b.t && a.r < b.r); }
+
+// ---- kernels -----------------------------------------------------------------
+
+__global__ void pool_init_kernel(PoolDev p)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.nchunks; i += (int64_t)gridDim.x * blockDim.x) {
+        p.free_ids[i] = (int32_t)(p.nchunks - 1 - i);
+        p.chunk_bucket[i] = -1;
+        p.chunk_fill[i] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *p.free_top = (unsigned long long)p.nchunks;
+}
+
+// reset the frontier arrays of one search (blockIdx.x = slot in `slots`)
+__global__ void slot_init_kernel(SearchDev* S, const int32_t* slots)
+{
+    SearchDev& s = S[slots[blockIdx.x]];
+    for (int i = threadIdx.x; i <= s.K; i += blockDim.x) {
+        s.b_cnt[i] = 0;
+        s.b_kids[i] = 0;
+        s.b_leaf[i] = 0;
+        s.b_tail[i] = -1;
+        s.h_cnt[i] = 0;
+        s.h_kids[i] = 0;
+        s.h_leaf[i] = 0;
+        s.w_pos[i] = 0;
+    }
+}
+
+__global__ void __launch_bounds__(1024) alloc_kernel(SearchDev* S, int nslots, PoolDev pool)
+{
+    __shared__ int64_t sh[32];
+    __shared__ int64_t s_base;
+    __shared__ int s_min[33];
+    for (int si = blockIdx.x; si < nslots; si += gridDim.x) {
+        SearchDev& f = S[si];
+        Ctl* c = f.ctl;
+        if (!c->active || c->err) continue;
+        // pass 1: chunks needed by this search, claimed from the shared stack
+        int64_t need_sum = 0;
+        for (int s = threadIdx.x; s <= f.K; s += blockDim.x) {
+            const uint32_t h = f.h_cnt[s];
+            if (!h) continue;
+            const int32_t tail = f.b_tail[s];
+            const int32_t space = tail >= 0 ? CH - pool.chunk_fill[tail] : 0;
+            if ((int64_t)h > space) need_sum += ((int64_t)h - space + CH - 1) / CH;
+        }
+        int64_t tot;
+        block_excl_scan(need_sum, &tot, sh);
+        if (threadIdx.x == 0) {
+            s_base = -1;
+            if (tot > 0) {
+                const unsigned long long old = atomicAdd(pool.free_top, (unsigned long long)(-(long long)tot));
+                if ((long long)old - tot < 0) {
+                    atomicAdd(pool.free_top, (unsigned long long)tot);   // give the claim back
+                    c->err |= 1;
+                } else {
+                    s_base = (int64_t)old - tot;   // claimed stack entries [old - tot, old)
+                }
+            }
+        }
+        __syncthreads();
+        if (c->err) continue;
+        const int64_t claim_top = s_base + tot;   // stack index just above the claim
+        const int64_t act0 = c->n_act;
+        // pass 2: hand out the claimed chunks bucket by bucket
+        int64_t carry = 0, added = 0;
+        int top = -1;
+        for (int base = 0; base <= f.K; base += blockDim.x) {
+            const int s = base + threadIdx.x;
+            uint32_t h = 0;
+            int32_t tail = -1, fill0 = CH, space = 0;
+            int64_t need = 0;
+            if (s <= f.K) {
+                h = f.h_cnt[s];
+                if (h) {
+                    tail = f.b_tail[s];
+                    fill0 = tail >= 0 ? pool.chunk_fill[tail] : CH;
+                    space = CH - fill0;
+                    need = (int64_t)h > space ? ((int64_t)h - space + CH - 1) / CH : 0;
+                }
+            }
+            int64_t total;
+            const int64_t off = carry + block_excl_scan(need, &total, sh);
+            if (h) {
+                int32_t last = tail;
+                for (int64_t i = 0; i < need; ++i) {
+                    const int32_t id = pool.free_ids[claim_top - 1 - (off + i)];
+                    pool.chunk_bucket[id] = s;
+                    pool.chunk_fill[id] = (int32_t)(i < need - 1 ? CH : ((int64_t)h - space) - (need - 1) * CH);
+                    f.act[act0 + off + i] = id;
+                    last = id;
+                }
+                if (tail >= 0) pool.chunk_fill[tail] = fill0 + (int32_t)((int64_t)h < space ? h : space);
+                f.w_space[s] = space;
+                f.w_choff[s] = claim_top - 1 - off;   // stack index of the bucket's first new chunk (counting down)
+                f.w_tail[s] = tail;
+                f.w_fill0[s] = fill0;
+                f.w_pos[s] = 0;
+                f.b_tail[s] = last;
+                f.b_cnt[s] += h;
+                f.b_kids[s] += (int64_t)f.h_kids[s];
+                f.b_leaf[s] += f.h_leaf[s];
+                f.h_cnt[s] = 0;
+                f.h_kids[s] = 0;
+                f.h_leaf[s] = 0;
+                added += h;
+                top = s > top ? s : top;
+            }
+            carry += total;
+        }
+        int64_t all_added;
+        block_excl_scan(added, &all_added, sh);
+        const int maxtop = -block_min_int(-top, s_min);
+        if (threadIdx.x == 0) {
+            c->n_act = act0 + carry;
+            c->size += all_added;
+            if (c->size > c->peak) c->peak = c->size;
+            if (maxtop > c->top) c->top = maxtop;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void scatter_kernel(SearchDev* S, PoolDev pool, const NodeRec* __restrict__ nodes,
+                               const int32_t* __restrict__ scores, const int32_t* __restrict__ sids,
+                               const unsigned long long* count, int64_t cap)
+{
+    int64_t n = (int64_t)*count;
+    if (n > cap) n = cap;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        SearchDev& f = S[sids[i]];
+        if (f.ctl->err) continue;
+        const int32_t s = scores[i];
+        const uint32_t rank = atomicAdd(&f.w_pos[s], 1u);
+        int32_t chunk, slot;
+        if ((int32_t)rank < f.w_space[s]) {
+            chunk = f.w_tail[s];
+            slot = f.w_fill0[s] + (int32_t)rank;
+        } else {
+            const int64_t idx = (int64_t)rank - f.w_space[s];
+            chunk = pool.free_ids[f.w_choff[s] - idx / CH];
+            slot = (int32_t)(idx % CH);
+        }
+        pool.nodes[(int64_t)chunk * CH + slot] = nodes[i];
+    }
+}
+
+__global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, PoolDev pool)
+{
+    __shared__ int64_t sh[32];
+    __shared__ int s_min[33];
+    __shared__ int32_t s_star, s_reason;
+    __shared__ LexKey s_lex[1024];
+    __shared__ NodeRec s_node[1024];
+    __shared__ int s_has[1024];
+    __shared__ unsigned long long s_ftop;
+    const int tid = threadIdx.x;
+    for (int si = blockIdx.x; si < nslots; si += gridDim.x) {
+        SearchDev& f = S[si];
+        Ctl* c = f.ctl;
+        if (!c->active || c->done || c->err) continue;
+        const int32_t best = c->best;
+        if (tid == 0) {
+            s_star = -1;
+            s_reason = c->size > 0 ? 4 : 0;
+        }
+        __syncthreads();
+        // 1. the bucket where popping stops
+        int64_t carry = 0;
+        for (int base = c->top; base >= 0; base -= blockDim.x) {
+            const int s = base - tid;
+            const bool have = s >= 0 && f.b_cnt[s] > 0;
+            const int64_t kids = have ? f.b_kids[s] : 0;
+            int64_t tot;
+            const int64_t cum = carry + block_excl_scan(kids, &tot, sh);
+            const bool stop = have && (cum >= f.batch || s <= best || f.b_leaf[s] > 0);
+            const int first = block_min_int(stop ? tid : (int)blockDim.x, s_min);
+            if (first < (int)blockDim.x) {
+                if (tid == first) {
+                    s_star = s;
+                    s_reason = cum >= f.batch ? 1 : (s <= best ? 2 : 3);
+                }
+                __syncthreads();
+                break;
+            }
+            carry += tot;
+        }
+        const int32_t sstar = s_star;
+        const int reason = s_reason;
+        const bool clear = reason == 2 || reason == 3;
+        // 2. active list: pop chunks above s*, free the rest when clearing, lexmin leaf of s*
+        LexKey my_lex;
+        my_lex.t = ~0ull;
+        my_lex.r = ~0u;
+        NodeRec my_node;
+        my_node.cx = my_node.cy = my_node.cz = 0;
+        my_node.rl = 0;
+        int my_has = 0;
+        const int64_t n_act = c->n_act;
+        int64_t keep = 0, npop = 0, nfree = 0, nparents = 0;
+        // freed chunks go onto the shared stack: count them first, then claim
+        int64_t nfree_total = 0;
+        if (clear) {
+            for (int64_t i = tid; i < n_act; i += blockDim.x) {
+                const int32_t ch = f.act[i];
+                if (pool.chunk_bucket[ch] <= sstar) ++nfree_total;
+            }
+            int64_t t;
+            block_excl_scan(nfree_total, &t, sh);
+            nfree_total = t;
+        }
+        if (tid == 0) s_ftop = nfree_total ? atomicAdd(pool.free_top, (unsigned long long)nfree_total) : 0ull;
+        __syncthreads();
+        const int64_t fbase = (int64_t)s_ftop;
+        for (int64_t base = 0; base < n_act; base += blockDim.x) {
+            const int64_t i = base + tid;
+            const int32_t ch = i < n_act ? f.act[i] : -1;
+            const int32_t bk = ch >= 0 ? pool.chunk_bucket[ch] : -1;
+            const int32_t fill = ch >= 0 ? pool.chunk_fill[ch] : 0;
+            const bool popped = ch >= 0 && bk > sstar;
+            const bool freed = ch >= 0 && !popped && clear;
+            const bool kept = ch >= 0 && !popped && !clear;
+            if (reason == 3 && ch >= 0 && bk == sstar) {
+                for (int j = 0; j < fill; ++j) {
+                    const NodeRec nd = pool.nodes[(int64_t)ch * CH + j];
+                    if (rl_level(nd.rl) != 0) continue;
+                    const LexKey k = lex_of(nd);
+                    if (!my_has || lex_lt(k, my_lex)) {
+                        my_lex = k;
+                        my_node = nd;
+                        my_has = 1;
+                    }
+                }
+            }
+            int64_t t1, t2, t3, t4;
+            const int64_t rp = block_excl_scan(popped ? 1 : 0, &t1, sh);
+            const int64_t rf = block_excl_scan(freed ? 1 : 0, &t2, sh);
+            const int64_t rk = block_excl_scan(kept ? 1 : 0, &t3, sh);
+            const int64_t rs = block_excl_scan(popped ? fill : 0, &t4, sh);
+            if (popped) {
+                f.pop_ids[npop + rp] = ch;
+                f.pop_start[npop + rp] = nparents + rs;
+                pool.chunk_bucket[ch] = -2;
+            }
+            if (freed) {
+                pool.free_ids[fbase + nfree + rf] = ch;
+                pool.chunk_bucket[ch] = -1;
+            }
+            __syncthreads();   // every read of act[base..] is done before the in-place write
+            if (kept) f.act[keep + rk] = ch;
+            npop += t1;
+            nfree += t2;
+            keep += t3;
+            nparents += t4;
+            __syncthreads();
+        }
+        // 3. lexmin leaf across the block
+        if (reason == 3) {
+            s_lex[tid] = my_lex;
+            s_node[tid] = my_node;
+            s_has[tid] = my_has;
+            __syncthreads();
+            for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+                if (tid < o && s_has[tid + o] && (!s_has[tid] || lex_lt(s_lex[tid + o], s_lex[tid]))) {
+                    s_lex[tid] = s_lex[tid + o];
+                    s_node[tid] = s_node[tid + o];
+                    s_has[tid] = 1;
+                }
+                __syncthreads();
+            }
+        }
+        // 4. bucket metadata of popped buckets and, when clearing, of all others
+        int64_t popped_kids = 0;
+        const int32_t top = c->top;
+        for (int s = tid; s <= top; s += blockDim.x) {
+            if (s > sstar || clear) {
+                if (s > sstar) popped_kids += f.b_kids[s];
+                f.b_cnt[s] = 0;
+                f.b_kids[s] = 0;
+                f.b_leaf[s] = 0;
+                f.b_tail[s] = -1;
+            }
+        }
+        int64_t pk;
+        block_excl_scan(popped_kids, &pk, sh);
+        if (tid == 0) {
+            c->n_pop = npop;
+            c->n_parents = nparents;
+            c->popped_kids = pk;
+            c->n_act = keep;
+            c->size = clear ? 0 : c->size - nparents;
+            c->top = reason == 1 ? sstar : -1;
+            c->reason = reason;
+            c->match_changed = 0;
+            if (reason == 3 && s_has[0]) {
+                c->best = sstar;
+                c->match = s_node[0];
+                c->found = 1;
+                c->match_changed = 1;
+            }
+            c->done = nparents == 0;
+        }
+        __syncthreads();
+    }
+}
+
+// popped chunks of every search -> the dense parent array at the search's offset
+__global__ void gather_kernel(SearchDev* S, PoolDev pool, const int64_t* __restrict__ poff, int nslots,
+                              NodeRec* __restrict__ parents)
+{
+    for (int si = blockIdx.y; si < nslots; si += gridDim.y) {
+        SearchDev& f = S[si];
+        if (!f.ctl->active || f.ctl->err) continue;
+        const int64_t npop = f.ctl->n_pop;
+        for (int64_t i = blockIdx.x; i < npop; i += gridDim.x) {
+            const int32_t ch = f.pop_ids[i];
+            const int64_t start = poff[si] + f.pop_start[i];
+            const int32_t fill = pool.chunk_fill[ch];
+            for (int j = threadIdx.x; j < fill; j += blockDim.x) parents[start + j] = pool.nodes[(int64_t)ch * CH + j];
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const unsigned long long pos = atomicAdd(pool.free_top, 1ull);
+                pool.free_ids[pos] = ch;
+                pool.chunk_bucket[ch] = -1;
+            }
+        }
+    }
+}
+
+// ---- host engine ---------------------------------------------------------------
+
+namespace {
+
+double now_ms()
+{
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+int64_t floor_div2(int64_t x) { return x >= 0 ? x / 2 : -((-x + 1) / 2); }
+
+struct DevArena {
+    cudaStream_t st;
+    std::vector<void*> ptrs;
+    ~DevArena() { release(); }
+    void release()
+    {
+        for (void* p : ptrs) cudaFreeAsync(p, st);
+        ptrs.clear();
+    }
+    template <class T>
+    int get(T** p, size_t n)
+    {
+        void* q = nullptr;
+        cudaError_t e = cudaMallocAsync(&q, n * sizeof(T) + 16, st);
+        if (e != cudaSuccess)
+            return set_error(BBS_ENOMEM, "engine: cudaMallocAsync(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
+        ptrs.push_back(q);
+        *p = (T*)q;
+        return BBS_OK;
+    }
+};
+
+}  // namespace
+
+struct SearchHost {
+    ScanState scan;
+    const bbs_maps* maps = nullptr;
+    bbs_result* res = nullptr;
+    int32_t thr = 0;
+    int rmax = 1;
+    int chunks = 1;
+    bool live = false;
+    double t0 = 0, t_match = -1, t_init = 0, t_end = 0;
+    SearchDev dev;
+    Ctl ctl0;
+};
+
+class Engine {
+  public:
+    Engine(cudaStream_t st, int max_slots, int64_t pool_nodes, bool timed)
+        : st_(st), A_{st, {}}, max_slots_(max_slots), timed_(timed)
+    {
+        nchunks_ = (pool_nodes + CH - 1) / CH;
+    }
+    ~Engine()
+    {
+        for (auto& h : hosts_) scan_release(&h.scan, st_);
+        for (cudaEvent_t e : evs_) cudaEventDestroy(e);
+        if (h_ctl_) cudaFreeHost(h_ctl_);
+        if (h_poff_) cudaFreeHost(h_poff_);
+    }
+
+    int init()
+    {
+        BBS_TRY(A_.get(&pool_.nodes, (size_t)(nchunks_ * CH)));
+        BBS_TRY(A_.get(&pool_.chunk_bucket, (size_t)nchunks_));
+        BBS_TRY(A_.get(&pool_.chunk_fill, (size_t)nchunks_));
+        BBS_TRY(A_.get(&pool_.free_ids, (size_t)nchunks_));
+        BBS_TRY(A_.get(&pool_.free_top, 1));
+        pool_.nchunks = nchunks_;
+        BBS_TRY(A_.get(&d_S_, (size_t)max_slots_));
+        BBS_TRY(A_.get(&d_ctl_, (size_t)max_slots_));
+        BBS_CUDA_TRY(cudaMemsetAsync(d_ctl_, 0, sizeof(Ctl) * (size_t)max_slots_, st_));
+        BBS_TRY(A_.get(&parents_, (size_t)(nchunks_ * CH)));
+        BBS_TRY(A_.get(&d_poff_, (size_t)max_slots_));
+        BBS_TRY(A_.get(&d_slots_, (size_t)max_slots_));
+        BBS_TRY(A_.get(&dense_, (size_t)DENSE_CAP));
+        BBS_TRY(A_.get(&surv_.nodes, (size_t)DENSE_CAP));
+        BBS_TRY(A_.get(&surv_.scores, (size_t)DENSE_CAP));
+        BBS_TRY(A_.get(&surv_.sid, (size_t)DENSE_CAP));
+        BBS_TRY(A_.get(&surv_.count, 1));
+        BBS_TRY(A_.get(&surv_.err, 1));
+        surv_.cap = DENSE_CAP;
+        BBS_CUDA_TRY(cudaMemsetAsync(surv_.count, 0, sizeof(unsigned long long), st_));
+        BBS_CUDA_TRY(cudaMemsetAsync(surv_.err, 0, sizeof(int), st_));
+        BBS_CUDA_TRY(cudaMallocHost((void**)&h_ctl_, sizeof(Ctl) * (size_t)max_slots_));
+        BBS_CUDA_TRY(cudaMallocHost((void**)&h_poff_, sizeof(int64_t) * (size_t)max_slots_));
+        pool_init_kernel<<<(int)std::min<int64_t>((nchunks_ + 255) / 256, 4096), 256, 0, st_>>>(pool_);
+        launches_ += 1;
+        BBS_CUDA_TRY(cudaGetLastError());
+        hosts_.reserve((size_t)max_slots_);
+        return BBS_OK;
+    }
+
+    // add a search; its initial set is scored by the next start()
+    int add(const bbs_maps* m, const float* xyz, int64_t k, int is_device, const bbs_ranges* rg, const bbs_opts* opts,
+            bbs_result* res)
+    {
+        if ((int)hosts_.size() >= max_slots_) return set_error(BBS_EINVAL, "engine: more than %d searches", max_slots_);
+        hosts_.emplace_back();
+        SearchHost& h = hosts_.back();
+        h.t0 = now_ms();
+        std::memset(res, 0, sizeof(*res));
+        res->num_points = (int32_t)k;
+        h.res = res;
+        h.maps = m;
+        const double frac = (opts && opts->score_frac > 0.0) ? opts->score_frac : 0.95;
+        const uint32_t flags = opts ? opts->flags : 0u;
+        if (!(frac > 0.0 && frac <= 1.0)) return set_error(BBS_EINVAL, "localize: score_frac %g outside (0, 1]", frac);
+        if (flags & BBS_PRUNE_GE) return set_error(BBS_EINVAL, "localize: BBS_PRUNE_GE is not supported");
+        if (k > (1 << 24)) return set_error(BBS_EINVAL, "localize: more than 2^24 scan points");
+        BBS_TRY(scan_prepare(m, xyz, k, is_device, rg, opts, st_, &h.scan));
+        const HostGrid& g = h.scan.grid;
+        h.thr = (int32_t)std::ceil(frac * (double)k);
+        res->phase_ms[0] = now_ms() - h.t0;
+        res->h2d_bytes += h.scan.h2d;
+        res->d2h_bytes += h.scan.d2h;
+        res->launches += 2;
+        if (k == 0) return BBS_OK;   // not live: NOT_FOUND
+        for (int l = 1; l < g.levels; ++l) h.rmax = std::max<int>(h.rmax, (int)(g.a[l][0] * g.a[l][1] * g.a[l][2]));
+        h.chunks = (int)((k + PCHUNK - 1) / PCHUNK);
+        SearchDev& d = h.dev;
+        std::memset(&d, 0, sizeof(d));
+        d.scan = h.scan.scan;
+        d.rot = h.scan.rot;
+        d.K = (int32_t)k;
+        d.lmax = g.levels - 1;
+        d.batch = (opts && opts->batch > 0) ? opts->batch : 10000;
+        for (int i = 0; i < 3; ++i) {
+            const int64_t pmin = floor_div2(g.wmin[i]), pmax = floor_div2(g.wmax[i]);
+            d.pmin[i] = (int32_t)pmin;
+            d.pext[i] = (int32_t)(pmax - pmin + 1);
+            d.wmin[i] = (int32_t)g.wmin[i];
+            d.wmax[i] = (int32_t)g.wmax[i];
+        }
+        d.grid = dev_grid(g);
+        for (int l = 0; l < MAX_LEVELS; ++l) d.maps[l] = l < m->levels ? level_view(m, l) : LevelView{};
+        const size_t K1 = (size_t)k + 1;
+        BBS_TRY(A_.get(&d.b_cnt, K1));
+        BBS_TRY(A_.get(&d.b_kids, K1));
+        BBS_TRY(A_.get(&d.b_leaf, K1));
+        BBS_TRY(A_.get(&d.b_tail, K1));
+        BBS_TRY(A_.get(&d.h_cnt, K1));
+        BBS_TRY(A_.get(&d.h_kids, K1));
+        BBS_TRY(A_.get(&d.h_leaf, K1));
+        BBS_TRY(A_.get(&d.w_pos, K1));
+        BBS_TRY(A_.get(&d.w_space, K1));
+        BBS_TRY(A_.get(&d.w_choff, K1));
+        BBS_TRY(A_.get(&d.w_tail, K1));
+        BBS_TRY(A_.get(&d.w_fill0, K1));
+        BBS_TRY(A_.get(&d.act, (size_t)nchunks_));
+        BBS_TRY(A_.get(&d.pop_ids, (size_t)nchunks_));
+        BBS_TRY(A_.get(&d.pop_start, (size_t)nchunks_));
+        h.ctl0.best = h.thr - 1;
+        h.ctl0.top = -1;
+        h.ctl0.active = 1;
+        h.live = true;
+        // initial-set statistics
+        int64_t n0 = 1;
+        for (int i = 0; i < 3; ++i) n0 *= (g.wmax[i] - g.wmin[i] + 1);
+        res->nodes_scored = n0 * g.nrot[g.levels - 1];
+        return BBS_OK;
+    }
+
+    // upload slots, score every live search's initial set
+    int start()
+    {
+        const int n = (int)hosts_.size();
+        std::vector<SearchDev> hs((size_t)n);
+        std::vector<int32_t> slots;
+        for (int i = 0; i < n; ++i) {
+            hosts_[(size_t)i].dev.ctl = d_ctl_ + i;
+            hs[(size_t)i] = hosts_[(size_t)i].dev;
+            h_ctl_[i] = hosts_[(size_t)i].ctl0;
+            if (hosts_[(size_t)i].live) slots.push_back(i);
+        }
+        nslots_ = n;
+        BBS_CUDA_TRY(cudaMemcpyAsync(d_S_, hs.data(), sizeof(SearchDev) * (size_t)n, cudaMemcpyHostToDevice, st_));
+        BBS_CUDA_TRY(cudaMemcpyAsync(d_ctl_, h_ctl_, sizeof(Ctl) * (size_t)n, cudaMemcpyHostToDevice, st_));
+        if (slots.empty()) return BBS_OK;
+        BBS_CUDA_TRY(cudaMemcpyAsync(d_slots_, slots.data(), sizeof(int32_t) * slots.size(), cudaMemcpyHostToDevice, st_));
+        slot_init_kernel<<<(int)slots.size(), 1024, 0, st_>>>(d_S_, d_slots_);
+        launches_ += 1;
+        BBS_CUDA_TRY(cudaGetLastError());
+        // the initial sets: virtual parents x rotations at l_max, sliced by dense capacity
+        std::vector<Seg> segs;
+        int64_t work = 0, dense = 0;
+        auto flush = [&]() -> int {
+            if (segs.empty()) return BBS_OK;
+            BBS_TRY(score_launch(MODE_INITIAL, segs, work, dense));
+            segs.clear();
+            work = dense = 0;
+            return BBS_OK;
+        };
+        for (int i : slots) {
+            SearchHost& h = hosts_[(size_t)i];
+            const HostGrid& g = h.scan.grid;
+            const int64_t R = g.nrot[g.levels - 1];
+            const int64_t vpn = (int64_t)h.dev.pext[0] * h.dev.pext[1] * h.dev.pext[2];
+            const int64_t per = R * 8;
+            if (per > DENSE_CAP) return set_error(BBS_EINVAL, "localize: %lld initial rotations", (long long)R);
+            for (int64_t v0 = 0; v0 < vpn;) {
+                int64_t take = std::min<int64_t>(vpn - v0, (DENSE_CAP - dense) / per);
+                if (take <= 0 || (int)segs.size() == MAXSEG) {
+                    BBS_TRY(flush());
+                    continue;
+                }
+                Seg s;
+                std::memset(&s, 0, sizeof(s));
+                s.first_parent = v0;
+                s.first_work = work;
+                s.n_parents = take;
+                s.dense_base = dense;
+                s.chunks = h.chunks;
+                s.sid = i;
+                s.R = (int32_t)R;
+                segs.push_back(s);
+                work += take * h.chunks;
+                dense += take * per;
+                h.res->gathers += take * R * h.scan.k;
+                v0 += take;
+            }
+        }
+        BBS_TRY(flush());
+        const double t = now_ms();
+        for (int i : slots) {
+            SearchHost& h = hosts_[(size_t)i];
+            h.res->phase_ms[1] = t - h.t0 - h.res->phase_ms[0];
+            h.t_init = t;
+        }
+        return BBS_OK;
+    }
+
+    // iterate until every search is done
+    int run()
+    {
+        const int n = nslots_;
+        int64_t iter = 0;
+        for (;;) {
+            if (n == 0) break;
+            select_kernel<<<std::min(n, 1024), 1024, 0, st_>>>(d_S_, n, pool_);
+            launches_ += 1;
+            BBS_CUDA_TRY(cudaGetLastError());
+            // the control blocks of every slot, one copy
+            BBS_CUDA_TRY(cudaMemcpyAsync(h_ctl_, d_ctl_, sizeof(Ctl) * (size_t)n, cudaMemcpyDeviceToHost, st_));
+            BBS_CUDA_TRY(cudaStreamSynchronize(st_));
+            const double t = now_ms();
+            int64_t total_parents = 0;
+            bool err = false;
+            for (int i = 0; i < n; ++i) {
+                SearchHost& h = hosts_[(size_t)i];
+                const Ctl& c = h_ctl_[i];
+                if (!h.live) continue;
+                h.res->d2h_bytes += (int64_t)sizeof(Ctl);
+                if (c.err) err = true;
+                if (c.match_changed) h.t_match = t;
+                h_poff_[i] = total_parents;
+                if (c.done) {
+                    h.live = false;
+                    h.t_end = t;
+                    continue;
+                }
+                total_parents += c.n_parents;
+                h.res->iterations++;
+                h.res->parents_branched += c.n_parents;
+                h.res->nodes_scored += c.popped_kids;
+                h.res->gathers += (c.popped_kids / 8) * h.scan.k;
+            }
+            if (err) return set_error(BBS_ENOMEM, "localize: the frontier pool (%lld nodes) is exhausted",
+                                      (long long)(nchunks_ * CH));
+            if (total_parents == 0) break;
+            if (++iter > ((int64_t)1 << 24)) return set_error(BBS_ETIMEOUT, "localize: iteration limit");
+            BBS_CUDA_TRY(cudaMemcpyAsync(d_poff_, h_poff_, sizeof(int64_t) * (size_t)n, cudaMemcpyHostToDevice, st_));
+            int64_t maxpop = 1;
+            for (int i = 0; i < n; ++i)
+                if (hosts_[(size_t)i].live) maxpop = std::max<int64_t>(maxpop, h_ctl_[i].n_pop);
+            dim3 gg((unsigned)std::min<int64_t>(maxpop, 4096), (unsigned)std::min(n, 65535));
+            gather_kernel<<<gg, CH, 0, st_>>>(d_S_, pool_, d_poff_, n, parents_);
+            launches_ += 1;
+            BBS_CUDA_TRY(cudaGetLastError());
+            // score every popped parent, in slices bounded by the dense capacity
+            std::vector<Seg> segs;
+            int64_t work = 0, dense = 0;
+            auto flush = [&]() -> int {
+                if (segs.empty()) return BBS_OK;
+                BBS_TRY(score_launch(MODE_SEARCH, segs, work, dense));
+                segs.clear();
+                work = dense = 0;
+                return BBS_OK;
+            };
+            for (int i = 0; i < n; ++i) {
+                SearchHost& h = hosts_[(size_t)i];
+                if (!h.live) continue;
+                const int64_t np = h_ctl_[i].n_parents;
+                const int64_t per = (int64_t)h.rmax * 8;
+                for (int64_t p0 = 0; p0 < np;) {
+                    const int64_t take = std::min<int64_t>(np - p0, (DENSE_CAP - dense) / per);
+                    if (take <= 0 || (int)segs.size() == MAXSEG) {
+                        BBS_TRY(flush());
+                        continue;
+                    }
+                    Seg s;
+                    std::memset(&s, 0, sizeof(s));
+                    s.first_parent = h_poff_[i] + p0;
+                    s.first_work = work;
+                    s.n_parents = take;
+                    s.dense_base = dense;
+                    s.chunks = h.chunks;
+                    s.sid = i;
+                    s.R = h.rmax;
+                    segs.push_back(s);
+                    work += take * h.chunks;
+                    dense += take * per;
+                    p0 += take;
+                }
+            }
+            BBS_TRY(flush());
+        }
+        // final statistics
+        for (int i = 0; i < n; ++i) {
+            SearchHost& h = hosts_[(size_t)i];
+            if (h.t_end == 0) h.t_end = now_ms();
+        }
+        int herr = 0;
+        BBS_CUDA_TRY(cudaMemcpyAsync(&herr, surv_.err, sizeof(int), cudaMemcpyDeviceToHost, st_));
+        BBS_CUDA_TRY(cudaMemcpyAsync(h_ctl_, d_ctl_, sizeof(Ctl) * (size_t)n, cudaMemcpyDeviceToHost, st_));
+        BBS_CUDA_TRY(cudaStreamSynchronize(st_));
+        if (herr) return set_error(BBS_ECORRUPT, "localize: survivor staging overflow");
+        double score_ms = 0.0;
+        for (size_t i = 0; i + 1 < evs_.size(); i += 2) {
+            float ms = 0.0f;
+            BBS_CUDA_TRY(cudaEventElapsedTime(&ms, evs_[i], evs_[i + 1]));
+            score_ms += ms;
+        }
+        const double t_fin = now_ms();
+        for (int i = 0; i < n; ++i) {
+            SearchHost& h = hosts_[(size_t)i];
+            bbs_result* r = h.res;
+            const Ctl& c = h_ctl_[i];
+            r->launches += launches_;
+            r->score_launches = score_launches_;
+            r->score_ms = score_ms;
+            if (h.scan.k == 0) {
+                r->best_score = h.thr - 1;
+                r->status = BBS_NOT_FOUND;
+                r->ms_total = t_fin - h.t0;
+                continue;
+            }
+            const HostGrid& g = h.scan.grid;
+            r->probes = r->nodes_scored * h.scan.k;
+            r->best_score = c.best;
+            r->peak_frontier = c.peak;
+            r->phase_ms[2] = (h.t_match >= 0 ? h.t_match : h.t_end) - h.t_init;
+            r->phase_ms[3] = h.t_match >= 0 ? h.t_end - h.t_match : 0.0;
+            r->d2h_bytes += (int64_t)sizeof(Ctl);
+            if (c.found) {
+                const NodeRec& nd = c.match;
+                const uint32_t rot = rl_rot(nd.rl);
+                const int64_t ng = g.N[0][2], nb = g.N[0][1];
+                r->found = 1;
+                r->node[0] = nd.cx;
+                r->node[1] = nd.cy;
+                r->node[2] = nd.cz;
+                r->node[3] = (int32_t)(rot / (ng * nb));
+                r->node[4] = (int32_t)((rot / ng) % nb);
+                r->node[5] = (int32_t)(rot % ng);
+                r->node[6] = 0;
+                for (int a = 0; a < 3; ++a) r->pose[a] = (double)r->node[a] * g.r;
+                for (int a = 0; a < 3; ++a) r->pose[3 + a] = grid_angle(g, 0, a, r->node[3 + a]);
+                r->status = BBS_OK;
+                r->ms_to_optimum = h.t_match - h.t0;
+            } else {
+                r->status = BBS_NOT_FOUND;
+                r->ms_to_optimum = h.t_end - h.t0;
+            }
+            r->ms_total = t_fin - h.t0;
+            r->phase_ms[4] = t_fin - h.t_end;
+        }
+        return BBS_OK;
+    }
+
+  private:
+    static constexpr int64_t DENSE_CAP = (int64_t)1 << 22;   // child scores per scoring launch
+
+    int score_launch(int mode, const std::vector<Seg>& segs, int64_t work, int64_t dense)
+    {
+        BranchLaunch L;
+        std::memset(&L, 0, sizeof(L));
+        L.S = d_S_;
+        L.parents = parents_;
+        L.dense = dense_;
+        L.n_work = work;
+        L.n_dense = dense;
+        L.nseg = (int32_t)segs.size();
+        L.mode = mode;
+        for (size_t i = 0; i < segs.size(); ++i) L.seg[i] = segs[i];
+        BBS_CUDA_TRY(cudaMemsetAsync(dense_, 0, sizeof(int32_t) * (size_t)dense, st_));
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (timed_) {
+            BBS_CUDA_TRY(cudaEventCreate(&e0));
+            evs_.push_back(e0);
+            BBS_CUDA_TRY(cudaEventCreate(&e1));
+            evs_.push_back(e1);
+            BBS_CUDA_TRY(cudaEventRecord(e0, st_));
+        }
+        BBS_CUDA_TRY(launch_branch(L, st_));
+        if (timed_) BBS_CUDA_TRY(cudaEventRecord(e1, st_));
+        BBS_CUDA_TRY(launch_finalize(L, d_S_, surv_, st_));
+        alloc_kernel<<<std::min(nslots_, 1024), 1024, 0, st_>>>(d_S_, nslots_, pool_);
+        scatter_kernel<<<1024, 256, 0, st_>>>(d_S_, pool_, surv_.nodes, surv_.scores, surv_.sid, surv_.count, surv_.cap);
+        BBS_CUDA_TRY(cudaMemsetAsync(surv_.count, 0, sizeof(unsigned long long), st_));
+        BBS_CUDA_TRY(cudaGetLastError());
+        launches_ += 4;
+        score_launches_ += 1;
+        return BBS_OK;
+    }
+
+    cudaStream_t st_;
+    DevArena A_;
+    int max_slots_;
+    bool timed_;
+    int64_t nchunks_ = 0;
+    int nslots_ = 0;
+    PoolDev pool_{};
+    SearchDev* d_S_ = nullptr;
+    Ctl* d_ctl_ = nullptr;
+    NodeRec* parents_ = nullptr;
+    int64_t* d_poff_ = nullptr;
+    int32_t* d_slots_ = nullptr;
+    int32_t* dense_ = nullptr;
+    SurvOut surv_{};
+    Ctl* h_ctl_ = nullptr;
+    int64_t* h_poff_ = nullptr;
+    std::vector<SearchHost> hosts_;
+    std::vector<cudaEvent_t> evs_;
+    int64_t launches_ = 0, score_launches_ = 0;
+};
+
+int search_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device, const bbs_ranges* rg,
+               const bbs_opts* opts, cudaStream_t st, bbs_result* res)
+{
+    const int64_t max_frontier = (opts && opts->max_frontier > 0) ? opts->max_frontier : ((int64_t)1 << 24);
+    const bool timed = opts && (opts->flags & BBS_TIME_KERNELS);
+    const int64_t pool_nodes = max_frontier + (int64_t)CH * std::min<int64_t>(k + 1, 8192);
+    Engine E(st, 1, pool_nodes, timed);
+    BBS_TRY(E.init());
+    BBS_TRY(E.add(m, xyz, k, is_device, rg, opts, res));
+    BBS_TRY(E.start());
+    BBS_TRY(E.run());
+    return res->status;
+}
+
+int search_run_many(const bbs_maps* m, int n, const float* const* scans, const int64_t* ks, int is_device,
+                    const bbs_ranges* rg, const bbs_opts* opts, cudaStream_t st, bbs_result* res)
+{
+    const int64_t max_frontier = (opts && opts->max_frontier > 0) ? opts->max_frontier : ((int64_t)1 << 24);
+    const bool timed = opts && (opts->flags & BBS_TIME_KERNELS);
+    int64_t kmax = 1;
+    for (int i = 0; i < n; ++i) kmax = std::max(kmax, ks[i]);
+    const int64_t pool_nodes = max_frontier + (int64_t)CH * std::min<int64_t>((kmax + 1) * n, 8192 * (int64_t)n);
+    Engine E(st, n, pool_nodes, timed);
+    BBS_TRY(E.init());
+    for (int i = 0; i < n; ++i) BBS_TRY(E.add(m, scans[i], ks[i], is_device, rg, opts, &res[i]));
+    BBS_TRY(E.start());
+    BBS_TRY(E.run());
+    return BBS_OK;
+}
+
+}  // namespace bbs

@@ -11,6 +11,7 @@
 //      scattered into 5x5x5-overlap bricks with atomicOr
 //   4. the bricks are moved into the final table at the target load factor,
 //      recording the longest probe distance so lookups stop early.
+#include <climits>
 #include <cstring>
 
 #include "bbs_internal.cuh"
@@ -52,7 +53,7 @@ struct BuildStatus {
     int maxp;
     unsigned long long displaced;
     unsigned long long voxels;
-    double lo[3], hi[3];        // bounding box (as ordered bit patterns below)
+    int kmin[3], kmax[3];       // bounds of a level's undilated keys
 };
 
 // insert-if-absent into a key set of size mask + 1; returns true if inserted
@@ -217,6 +218,93 @@ __global__ void dilate_kernel(const unsigned long long* keys, int64_t n, int dil
     }
 }
 
+// bounds of the undilated keys of a level
+__global__ void key_bounds_kernel(const unsigned long long* keys, int64_t n, BuildStatus* st)
+{
+    int mn[3] = {INT_MAX, INT_MAX, INT_MAX}, mx[3] = {INT_MIN, INT_MIN, INT_MIN};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t v[3];
+        vunpack(keys[i], v[0], v[1], v[2]);
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = min(mn[a], v[a]);
+            mx[a] = max(mx[a], v[a]);
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        mn[a] = __reduce_min_sync(0xffffffffu, mn[a]);
+        mx[a] = __reduce_max_sync(0xffffffffu, mx[a]);
+    }
+    if ((threadIdx.x & 31) == 0)
+        for (int a = 0; a < 3; ++a) {
+            atomicMin(&st->kmin[a], mn[a]);
+            atomicMax(&st->kmax[a], mx[a]);
+        }
+}
+
+// move every brick into a compact final table: relative 32-bit key, each
+// 16-byte half [key, 3 planes]
+__global__ void relayout_compact_kernel(const Brick* src, int64_t T, Brick* dst, uint32_t shift, uint32_t mask,
+                                        int bx0, int by0, int bz0, BuildStatus* st)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < T; i += (int64_t)gridDim.x * blockDim.x) {
+        const Brick b = src[i];
+        if (b.key == EMPTY_KEY) continue;
+        const int32_t bx = (int32_t)((b.key >> 40) & 0xFFFFF) - BRICK_BIAS;
+        const int32_t by = (int32_t)((b.key >> 20) & 0xFFFFF) - BRICK_BIAS;
+        const int32_t bz = (int32_t)(b.key & 0xFFFFF) - BRICK_BIAS;
+        const uint32_t key = cbrick_pack((uint32_t)(bx - bx0), (uint32_t)(by - by0), (uint32_t)(bz - bz0));
+        const uint32_t s = cbrick_hash(key) >> shift;
+        for (uint32_t p = 0; p <= mask; ++p) {
+            Brick* d = dst + ((s + p) & mask);
+            uint32_t* w = reinterpret_cast<uint32_t*>(d);
+            if (atomicCAS(w, CEMPTY, key) == CEMPTY) {
+                w[1] = b.plane[0];
+                w[2] = b.plane[1];
+                w[3] = b.plane[2];
+                w[5] = b.plane[2];
+                w[6] = b.plane[3];
+                w[7] = b.plane[4];
+                w[4] = key;
+                atomicMax(&st->maxp, (int)p);
+                if (p) atomicAdd(&st->displaced, 1ull);
+                unsigned c = 0;
+                for (int z = 0; z < 4; ++z) c += __popc(b.plane[z] & 0x7BDEFu);
+                atomicAdd(&st->voxels, (unsigned long long)c);
+                break;
+            }
+        }
+    }
+}
+
+__global__ void fill_u32(uint32_t* p, int64_t n, uint32_t v)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+__global__ void compact_keys_kernel(const Brick* tab, int64_t T, int bx0, int by0, int bz0, int32_t* out,
+                                    unsigned long long* n, int64_t cap)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < T; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t* w = reinterpret_cast<const uint32_t*>(tab + i);
+        if (w[0] == CEMPTY) continue;
+        const int32_t bx = (int32_t)(w[0] & 0x7FF) + bx0, by = (int32_t)((w[0] >> 11) & 0x7FF) + by0;
+        const int32_t bz = (int32_t)(w[0] >> 22) + bz0;
+        const uint32_t planes[4] = {w[1], w[2], w[3], w[6]};
+        for (int z = 0; z < 4; ++z)
+            for (int y = 0; y < 4; ++y)
+                for (int x = 0; x < 4; ++x)
+                    if ((planes[z] >> (x + 5 * y)) & 1u) {
+                        const unsigned long long o = atomicAdd(n, 1ull);
+                        if ((int64_t)o < cap) {
+                            out[3 * o] = 4 * bx + x;
+                            out[3 * o + 1] = 4 * by + y;
+                            out[3 * o + 2] = 4 * bz + z;
+                        }
+                    }
+    }
+}
+
 // move every brick into the final table, recording probe distances
 __global__ void relayout_kernel(const Brick* src, int64_t T, Brick* dst, uint32_t shift, uint32_t mask, BuildStatus* st)
 {
@@ -284,6 +372,15 @@ int log2_ceil(unsigned long long x)
 
 // target load of the final brick tables (bricks / buckets)
 static double g_load_target = 0.5;
+// 0: compact buckets whenever a level fits them, 1: always wide
+static int g_layout = 0;
+
+int maps_set_layout(int layout)
+{
+    if (layout < 0 || layout > 1) return set_error(BBS_EINVAL, "probe layout %d (0 auto, 1 wide)", layout);
+    g_layout = layout;
+    return BBS_OK;
+}
 
 int maps_set_load(double load)
 {
@@ -418,6 +515,24 @@ int maps_build(const float* xyz, int64_t n, int is_device, float r, int levels, 
             nb = nn;
         }
         const int dilate = !(l == 0 && (flags & BBS_LEAF_UNDILATED));
+        // bounds of B_l (D_l extends one voxel lower when dilated)
+        int kmin[3] = {0, 0, 0}, kmax[3] = {0, 0, 0};
+        if (nb > 0) {
+            BuildStatus z;
+            std::memset(&z, 0, sizeof(z));
+            for (int a = 0; a < 3; ++a) {
+                z.kmin[a] = INT_MAX;
+                z.kmax[a] = INT_MIN;
+            }
+            TRYC(cudaMemcpyAsync(d_st, &z, sizeof(z), cudaMemcpyHostToDevice, st));
+            key_bounds_kernel<<<blocks_for(nb), 256, 0, st>>>(keys, nb, d_st);
+            TRYC(cudaGetLastError());
+            if (read_status()) return fail(set_error(BBS_ECUDA, "build_maps: status read"));
+            for (int a = 0; a < 3; ++a) {
+                kmin[a] = hs.kmin[a] - (dilate ? 1 : 0);
+                kmax[a] = hs.kmax[a];
+            }
+        }
         // scatter D_l into a roomy temporary brick table, growing on overflow
         int lt = log2_ceil((unsigned long long)(4 * (nb > 256 ? nb : 256)));
         if (lt < 10) lt = 10;
@@ -442,11 +557,34 @@ int maps_build(const float* xyz, int64_t n, int is_device, float r, int levels, 
         if (lf < 10) lf = 10;
         const int64_t TF = (int64_t)1 << lf;
         TRYC(cudaMalloc((void**)&m->lv[l].slots, sizeof(Brick) * (size_t)TF));
-        init_bricks<<<blocks_for(TF), 256, 0, st>>>(m->lv[l].slots, TF);
+        // compact layout when the level's key box fits 11 / 11 / 10 bits of bricks
+        int base[3];
+        uint32_t rmax[3];
+        bool fits = true;
+        for (int a = 0; a < 3; ++a) {
+            base[a] = ((kmin[a] - 4) >> 2) * 4;           // a multiple of 4, at least 4 below kmin
+            rmax[a] = (uint32_t)(kmax[a] - base[a]);
+            const uint32_t bricks = (rmax[a] >> 2) + 1;
+            fits = fits && bricks <= (a < 2 ? 2048u : 1023u);
+        }
+        const bool compact = fits && g_layout == 0 && nb > 0;
         if (reset_status()) return fail(set_error(BBS_ECUDA, "build_maps: status upload"));
-        relayout_kernel<<<blocks_for((int64_t)1 << lt), 256, 0, st>>>((Brick*)sc.p[5], (int64_t)1 << lt, m->lv[l].slots,
-                                                                       (uint32_t)(32 - lf), (uint32_t)(TF - 1), d_st);
+        if (compact) {
+            fill_u32<<<blocks_for(8 * TF), 256, 0, st>>>((uint32_t*)m->lv[l].slots, 8 * TF, CEMPTY);
+            relayout_compact_kernel<<<blocks_for((int64_t)1 << lt), 256, 0, st>>>(
+                (Brick*)sc.p[5], (int64_t)1 << lt, m->lv[l].slots, (uint32_t)(32 - lf), (uint32_t)(TF - 1), base[0] >> 2,
+                base[1] >> 2, base[2] >> 2, d_st);
+        } else {
+            init_bricks<<<blocks_for(TF), 256, 0, st>>>(m->lv[l].slots, TF);
+            relayout_kernel<<<blocks_for((int64_t)1 << lt), 256, 0, st>>>(
+                (Brick*)sc.p[5], (int64_t)1 << lt, m->lv[l].slots, (uint32_t)(32 - lf), (uint32_t)(TF - 1), d_st);
+        }
         TRYC(cudaGetLastError());
+        m->lv[l].compact = compact ? 1 : 0;
+        for (int a = 0; a < 3; ++a) {
+            m->lv[l].base[a] = base[a];
+            m->lv[l].rmax[a] = rmax[a];
+        }
         if (read_status()) return fail(set_error(BBS_ECUDA, "build_maps: status read"));
         cudaFreeAsync(sc.p[5], st);
         sc.p[5] = nullptr;
@@ -475,7 +613,11 @@ int maps_keys(const bbs_maps* m, int level, int32_t* out, int64_t cap, int64_t* 
     BBS_CUDA_TRY(cudaMalloc((void**)&d_n, sizeof(unsigned long long)));
     cudaMemset(d_n, 0, sizeof(unsigned long long));
     const int64_t T = (int64_t)1 << m->lv[level].log2T;
-    brick_keys_kernel<<<blocks_for(T), 256>>>(m->lv[level].slots, T, d_out, d_n, nv);
+    if (m->lv[level].compact)
+        compact_keys_kernel<<<blocks_for(T), 256>>>(m->lv[level].slots, T, m->lv[level].base[0] >> 2,
+                                                    m->lv[level].base[1] >> 2, m->lv[level].base[2] >> 2, d_out, d_n, nv);
+    else
+        brick_keys_kernel<<<blocks_for(T), 256>>>(m->lv[level].slots, T, d_out, d_n, nv);
     cudaError_t e = cudaGetLastError();
     unsigned long long got = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&got, d_n, sizeof(got), cudaMemcpyDeviceToHost);

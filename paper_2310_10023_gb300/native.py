@@ -92,9 +92,12 @@ def load():
         L.bbs_score_batch.argtypes = [vp, vp, i64, C.c_int, P(Ranges), P(Opts), vp, i64, vp]
         L.bbs_score_children.argtypes = [vp, vp, i64, C.c_int, P(Ranges), P(Opts), vp, i64, vp, vp, i64, i64p]
         L.bbs_localize.argtypes = [vp, vp, i64, C.c_int, P(Ranges), P(Opts), P(Result)]
+        L.bbs_localize_many.argtypes = [vp, C.c_int, P(C.c_void_p), P(C.c_int64), C.c_int, P(Ranges), P(Opts),
+                                        P(Result)]
         L.bbs_last_error.restype = C.c_char_p
         L.bbs_version.restype = C.c_char_p
         L.bbs_set_load_factor.argtypes = [C.c_double]
+        L.bbs_set_probe_layout.argtypes = [C.c_int]
         L.bbs_bench_gather.argtypes = [C.c_int64, C.c_int64, vp, P(C.c_double)]
         L.bbs_score_batch_noalloc.argtypes = [vp, vp, i64, P(Ranges), P(Opts), vp, i64, vp]
         _lib = L
@@ -320,8 +323,38 @@ def bbs_localize(maps: Maps, scan, ranges: Ranges | None = None, opts: Opts | No
     return res
 
 
+def bbs_localize_many(maps: Maps, scans, ranges: Ranges | None = None, opts: Opts | None = None) -> list:
+    """Localize several scans (list of (K_i, 3) arrays / tensors, all host or all
+    device) in shared launches; one Result per scan."""
+    n = len(scans)
+    ptrs = (C.c_void_p * max(n, 1))()
+    ks = (C.c_int64 * max(n, 1))()
+    keep = []
+    dev = None
+    for i, sc in enumerate(scans):
+        p, d, k, kp = _arr(sc, np.float32, 3)
+        if dev is None:
+            dev = d
+        elif d != dev:
+            raise ValueError("scans must all be host or all be device memory")
+        ptrs[i] = p.value
+        ks[i] = k
+        keep.append(kp)
+    opts = opts or make_opts()
+    res = (Result * max(n, 1))()
+    _check(load().bbs_localize_many(maps.h, n, ptrs, ks, int(dev or 0), C.byref(ranges) if ranges else None,
+                                    C.byref(opts), res))
+    del keep
+    return [res[i] for i in range(n)]
+
+
 def bbs_set_load_factor(load_factor: float) -> None:
     _check(load().bbs_set_load_factor(float(load_factor)))
+
+
+def bbs_set_probe_layout(layout: int) -> None:
+    """0: compact buckets where they fit (default), 1: always wide."""
+    _check(load().bbs_set_probe_layout(int(layout)))
 
 
 def bbs_bench_gather(table_bytes: int, gathers: int, stream=None) -> float:

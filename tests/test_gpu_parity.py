@@ -269,3 +269,129 @@ def test_frontier_capacity_error(nv, room_pair):
     # the handle stays usable after the error
     res = nv.bbs_localize(dm, s, nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch))
     assert res.status == nv.OK
+
+
+# ---- batched searches ---------------------------------------------------------
+
+def test_localize_many_equals_single(nv, room_pair):
+    """Each scan of a batch gets exactly the result it gets alone."""
+    w, m, dm, om = room_pair
+    nr, _ = _ranges(nv, w)
+    opts = nv.make_opts(score_frac=w.score_frac, batch=w.batch)
+    scans = [synth.make_scan(1, i)[0] for i in range(6)]
+    scans[2] = scans[2][:333]                       # uneven sizes
+    scans[4] = synth.make_scan(1, 4, k=2500)[0]
+    many = nv.bbs_localize_many(dm, [torch.from_numpy(s).cuda() for s in scans], nr, opts)
+    for s, r in zip(scans, many):
+        one = nv.bbs_localize(dm, s, nr, opts)
+        assert (r.status, r.best_score, list(r.node), r.iterations, r.nodes_scored) == \
+               (one.status, one.best_score, list(one.node), one.iterations, one.nodes_scored)
+
+
+def test_localize_many_with_oracle(nv, room_pair):
+    w, m, dm, om = room_pair
+    nr, orr = _ranges(nv, w)
+    scans = [synth.make_scan(1, i)[0] for i in (7, 8)]
+    many = nv.bbs_localize_many(dm, scans, nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch))
+    for s, r in zip(scans, many):
+        _same_search(r, oracle.localize(om, s, orr, score_frac=w.score_frac, batch=w.batch))
+
+
+def test_localize_many_empty_and_not_found(nv, room_pair):
+    w, m, dm, om = room_pair
+    nr, _ = _ranges(nv, w)
+    s, _ = synth.make_scan(1, 0)
+    far = s.copy()
+    far[:, 2] = np.float32(30.0)
+    res = nv.bbs_localize_many(dm, [s, np.zeros((0, 3), np.float32), far], nr,
+                               nv.make_opts(score_frac=0.6, batch=w.batch))
+    assert res[0].status == nv.OK
+    assert res[1].status == nv.NOT_FOUND
+    assert res[2].status == nv.NOT_FOUND
+
+
+# ---- both bucket layouts --------------------------------------------------------
+
+@pytest.mark.parametrize("layout", [0, 1])
+def test_layouts_agree_with_oracle(nv, layout):
+    w = synth.WORKLOADS["room"]
+    m = synth.make_map(w.scene)
+    om = oracle.Maps(m, w.r, w.levels)
+    nv.bbs_set_probe_layout(layout)
+    try:
+        dm = nv.bbs_build_maps(m, w.r, w.levels)
+    finally:
+        nv.bbs_set_probe_layout(0)
+    for l in range(w.levels):
+        assert _keyset(nv.bbs_maps_keys(dm, l)) == _keyset(om.keys(l)), (layout, l)
+    s, _ = synth.make_scan(1, 6)
+    nr, orr = _ranges(nv, w)
+    g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), orr)
+    nodes = _random_nodes(g, np.random.default_rng(40 + layout), 1500, w.levels)
+    assert np.array_equal(nv.bbs_score_batch(dm, s, nodes, nr), om.score_nodes(g, s, nodes))
+    parents = nodes[nodes[:, 6] > 0][:200]
+    kn, ks = nv.bbs_score_children(dm, s, parents, nr)
+    assert np.array_equal(ks, om.score_nodes(g, s, kn))
+    res = nv.bbs_localize(dm, s, nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch))
+    _same_search(res, oracle.localize(om, s, orr, score_frac=w.score_frac, batch=w.batch))
+
+
+# ---- full-size workloads ----------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def indoor_pair(nv):
+    w = synth.WORKLOADS["indoor"]
+    m = synth.make_map(w.scene)
+    return w, m, nv.bbs_build_maps(torch.from_numpy(np.array(m)).cuda(), w.r, w.levels), oracle.Maps(m, w.r, w.levels)
+
+
+def test_indoor_maps_and_scores_bit_exact(nv, indoor_pair):
+    w, m, dm, om = indoor_pair
+    for l in range(w.levels):
+        assert nv.bbs_maps_info(dm, l)["voxels"] == om.count(l)
+    for l in (w.levels - 1, 2):
+        assert _keyset(nv.bbs_maps_keys(dm, l)) == _keyset(om.keys(l))
+    s, _ = synth.make_scan(2, 0)
+    nr, orr = _ranges(nv, w)
+    g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), orr)
+    nodes = _random_nodes(g, np.random.default_rng(9), 600, w.levels, tmin=-5, tmax=500)
+    assert np.array_equal(nv.bbs_score_batch(dm, s, nodes, nr), om.score_nodes(g, s, nodes))
+    parents = nodes[nodes[:, 6] > 0][:60]
+    kn, ks = nv.bbs_score_children(dm, torch.from_numpy(s).numpy(), parents, nr)
+    assert np.array_equal(ks, om.score_nodes(g, s, kn))
+
+
+def test_indoor_localize_equals_oracle(nv, indoor_pair):
+    """A full-size indoor search (8 k points, 6 levels, b = 16384): the GPU
+    follows the oracle's trajectory exactly."""
+    w, m, dm, om = indoor_pair
+    s, pose = synth.make_scan(2, 1)
+    nr, orr = _ranges(nv, w)
+    res = nv.bbs_localize(dm, torch.from_numpy(s).cuda(), nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch))
+    ores = oracle.localize(om, s, orr, score_frac=w.score_frac, batch=w.batch)
+    _same_search(res, ores)
+    assert res.status == nv.OK
+    for i in range(3):
+        assert abs(res.pose[i] - pose[i]) <= w.r + 0.1
+
+
+def test_outdoor_sampled_parity_and_planted_pose(nv):
+    """800 x 800 x 40 m city, 40 M map points, 20 k-point scan: sampled scores
+    bit-exact, the returned leaf's oracle score equals the reported best, and
+    the planted pose is recovered."""
+    w = synth.WORKLOADS["outdoor"]
+    m = synth.make_map(w.scene)
+    dm = nv.bbs_build_maps(torch.from_numpy(np.array(m)).cuda(), w.r, w.levels)
+    om = oracle.Maps(m, w.r, w.levels)
+    s, pose = synth.make_scan(3, 2)
+    nr, orr = _ranges(nv, w)
+    g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), orr)
+    nodes = _random_nodes(g, np.random.default_rng(3), 200, w.levels, tmin=150, tmax=650)
+    assert np.array_equal(nv.bbs_score_batch(dm, s, nodes, nr), om.score_nodes(g, s, nodes))
+    res = nv.bbs_localize(dm, torch.from_numpy(s).cuda(), nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch))
+    assert res.status == nv.OK
+    assert om.score_nodes(g, s, [list(res.node)])[0] == res.best_score
+    for i in range(3):
+        assert abs(res.pose[i] - pose[i]) <= w.r + 0.1
+    dyaw = (res.pose[5] - pose[5] + math.pi) % (2 * math.pi) - math.pi
+    assert abs(dyaw) <= 2 * g.dprime(0)[2]
