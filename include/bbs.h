@@ -50,6 +50,8 @@ extern "C" {
 #define BBS_ETIMEOUT   -4   /* a bounded device wait or the iteration limit ran out               */
 #define BBS_EKEYRANGE  -5   /* a voxel key or translation index beyond +-2^20 fine voxels         */
 #define BBS_ECORRUPT   -6   /* an internal consistency check failed                               */
+#define BBS_ECANCELED  -7   /* the request was cancelled (server)                                 */
+#define BBS_PENDING     2   /* server: the request is queued or running                           */
 
 /* ---- flags (bbs_build_maps and bbs_opts.flags) ------------------------- */
 /* every level uses the level-0 angle grid and only translations branch
@@ -260,6 +262,51 @@ int  bbs_bench_gather(int64_t table_bytes, int64_t gathers, void* cuda_stream, d
  * or an error for the whole call. */
 int  bbs_localize_many(const bbs_maps* maps, int n, const float* const* scans, const int64_t* ks,
                        int is_device, const bbs_ranges* ranges, const bbs_opts* opts, bbs_result* out);
+
+/* ---- serving: continuous batching --------------------------------------------
+ * A server owns a worker thread, a CUDA stream and a search engine on the
+ * device current at bbs_server_create.  Requests (a map handle, a host scan
+ * that is copied at submission, ranges, options) queue up; between search
+ * iterations the worker admits them in arrival order into free search slots
+ * while the device-memory budget allows (the shared frontier pool is charged
+ * once; each admitted search its scan, rotation tables and frontier arrays),
+ * so a request that arrives while others run joins the next iteration and
+ * shares its launches.  Finished searches release their slot and memory
+ * immediately.  Each result equals what bbs_localize returns for the same
+ * request alone (times excepted: ms_total is submission to result).
+ * Requests whose memory estimate exceeds the whole budget finish at once
+ * with BBS_ENOMEM.  opts->cuda_stream and BBS_TIME_KERNELS are ignored. */
+typedef struct bbs_server bbs_server;
+
+typedef struct {
+    size_t  mem_budget;     /* device bytes for the pool plus admitted searches; 0 = 8 GiB  */
+    int32_t max_active;     /* searches advanced together; 0 = 32, at most 1024             */
+    int64_t max_frontier;   /* shared frontier pool in nodes; 0 = 2^24                      */
+} bbs_server_opts;
+
+typedef struct {
+    int64_t submitted, completed, active, queued, rejected;
+    int64_t peak_active;               /* most searches advanced in one iteration            */
+    double  p50_ms, p99_ms, mean_ms;   /* submission-to-result latency of completed requests */
+    double  throughput_rps;            /* completed / (last completion - first submission)   */
+    double  probes_per_s;              /* point-probes of completed requests over that span  */
+    size_t  mem_in_use, mem_budget;
+} bbs_server_counters;
+
+int  bbs_server_create(const bbs_server_opts* opts, bbs_server** out);
+/* queue a request; *ticket identifies it.  BBS_OK once queued. */
+int  bbs_server_submit(bbs_server* server, const bbs_maps* maps, const float* scan_xyz, int64_t k,
+                       const bbs_ranges* ranges, const bbs_opts* opts, uint64_t* ticket);
+/* wait up to wait_ms (0: do not wait, negative: until done) for a ticket.
+ * Returns BBS_PENDING while queued or running; otherwise the request's status
+ * (BBS_OK, BBS_NOT_FOUND or an error), with its result in *out, and forgets
+ * the ticket. */
+int  bbs_server_poll(bbs_server* server, uint64_t ticket, int wait_ms, bbs_result* out);
+/* cancel a queued or running request; its result reports BBS_ECANCELED */
+int  bbs_server_cancel(bbs_server* server, uint64_t ticket);
+int  bbs_server_stats(bbs_server* server, bbs_server_counters* out);
+/* stops the worker after its current iteration; unfinished requests are dropped */
+void bbs_server_destroy(bbs_server* server);
 
 /* Thread-local description of the last error on this thread ("" if none). */
 const char* bbs_last_error(void);

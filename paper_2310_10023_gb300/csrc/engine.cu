@@ -21,9 +21,10 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
-#include "branch.cuh"
+#include "engine.cuh"
 
 namespace bbs {
 
@@ -394,6 +395,28 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
     }
 }
 
+// push every chunk a search still holds back onto the shared stack
+__global__ void slot_release_kernel(SearchDev* S, int slot, PoolDev pool)
+{
+    SearchDev& f = S[slot];
+    Ctl* c = f.ctl;
+    const int64_t n = c->n_act;
+    __shared__ unsigned long long base;
+    if (threadIdx.x == 0) base = n > 0 ? atomicAdd(pool.free_top, (unsigned long long)n) : 0ull;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const int32_t ch = f.act[i];
+        pool.free_ids[base + i] = ch;
+        pool.chunk_bucket[ch] = -1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        c->n_act = 0;
+        c->size = 0;
+        c->active = 0;
+    }
+}
+
 // popped chunks of every search -> the dense parent array at the search's offset
 __global__ void gather_kernel(SearchDev* S, PoolDev pool, const int64_t* __restrict__ poff, int nslots,
                               NodeRec* __restrict__ parents)
@@ -428,433 +451,506 @@ double now_ms()
 
 int64_t floor_div2(int64_t x) { return x >= 0 ? x / 2 : -((-x + 1) / 2); }
 
-struct DevArena {
-    cudaStream_t st;
-    std::vector<void*> ptrs;
-    ~DevArena() { release(); }
-    void release()
-    {
-        for (void* p : ptrs) cudaFreeAsync(p, st);
-        ptrs.clear();
-    }
-    template <class T>
-    int get(T** p, size_t n)
-    {
-        void* q = nullptr;
-        cudaError_t e = cudaMallocAsync(&q, n * sizeof(T) + 16, st);
-        if (e != cudaSuccess)
-            return set_error(BBS_ENOMEM, "engine: cudaMallocAsync(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
-        ptrs.push_back(q);
-        *p = (T*)q;
-        return BBS_OK;
-    }
-};
-
 }  // namespace
 
-struct SearchHost {
-    ScanState scan;
-    const bbs_maps* maps = nullptr;
-    bbs_result* res = nullptr;
-    int32_t thr = 0;
-    int rmax = 1;
-    int chunks = 1;
-    bool live = false;
-    double t0 = 0, t_match = -1, t_init = 0, t_end = 0;
-    SearchDev dev;
-    Ctl ctl0;
-};
+Engine::Engine(cudaStream_t st, int max_slots, int64_t pool_nodes, bool timed)
+    : st_(st), max_slots_(max_slots), timed_(timed)
+{
+    nchunks_ = (pool_nodes + CH - 1) / CH;
+    hosts_.resize((size_t)max_slots);
+}
 
-class Engine {
-  public:
-    Engine(cudaStream_t st, int max_slots, int64_t pool_nodes, bool timed)
-        : st_(st), A_{st, {}}, max_slots_(max_slots), timed_(timed)
-    {
-        nchunks_ = (pool_nodes + CH - 1) / CH;
-    }
-    ~Engine()
-    {
-        for (auto& h : hosts_) scan_release(&h.scan, st_);
-        for (cudaEvent_t e : evs_) cudaEventDestroy(e);
-        if (h_ctl_) cudaFreeHost(h_ctl_);
-        if (h_poff_) cudaFreeHost(h_poff_);
-    }
+Engine::~Engine()
+{
+    for (size_t i = 0; i < hosts_.size(); ++i)
+        if (hosts_[i].used) release((int)i);
+    for (void* p : fixed_) cudaFreeAsync(p, st_);
+    for (cudaEvent_t e : evs_) cudaEventDestroy(e);
+    if (h_ctl_) cudaFreeHost(h_ctl_);
+    if (h_poff_) cudaFreeHost(h_poff_);
+}
 
-    int init()
-    {
-        BBS_TRY(A_.get(&pool_.nodes, (size_t)(nchunks_ * CH)));
-        BBS_TRY(A_.get(&pool_.chunk_bucket, (size_t)nchunks_));
-        BBS_TRY(A_.get(&pool_.chunk_fill, (size_t)nchunks_));
-        BBS_TRY(A_.get(&pool_.free_ids, (size_t)nchunks_));
-        BBS_TRY(A_.get(&pool_.free_top, 1));
-        pool_.nchunks = nchunks_;
-        BBS_TRY(A_.get(&d_S_, (size_t)max_slots_));
-        BBS_TRY(A_.get(&d_ctl_, (size_t)max_slots_));
-        BBS_CUDA_TRY(cudaMemsetAsync(d_ctl_, 0, sizeof(Ctl) * (size_t)max_slots_, st_));
-        BBS_TRY(A_.get(&parents_, (size_t)(nchunks_ * CH)));
-        BBS_TRY(A_.get(&d_poff_, (size_t)max_slots_));
-        BBS_TRY(A_.get(&d_slots_, (size_t)max_slots_));
-        BBS_TRY(A_.get(&dense_, (size_t)DENSE_CAP));
-        BBS_TRY(A_.get(&surv_.nodes, (size_t)DENSE_CAP));
-        BBS_TRY(A_.get(&surv_.scores, (size_t)DENSE_CAP));
-        BBS_TRY(A_.get(&surv_.sid, (size_t)DENSE_CAP));
-        BBS_TRY(A_.get(&surv_.count, 1));
-        BBS_TRY(A_.get(&surv_.err, 1));
-        surv_.cap = DENSE_CAP;
-        BBS_CUDA_TRY(cudaMemsetAsync(surv_.count, 0, sizeof(unsigned long long), st_));
-        BBS_CUDA_TRY(cudaMemsetAsync(surv_.err, 0, sizeof(int), st_));
-        BBS_CUDA_TRY(cudaMallocHost((void**)&h_ctl_, sizeof(Ctl) * (size_t)max_slots_));
-        BBS_CUDA_TRY(cudaMallocHost((void**)&h_poff_, sizeof(int64_t) * (size_t)max_slots_));
-        pool_init_kernel<<<(int)std::min<int64_t>((nchunks_ + 255) / 256, 4096), 256, 0, st_>>>(pool_);
-        launches_ += 1;
-        BBS_CUDA_TRY(cudaGetLastError());
-        hosts_.reserve((size_t)max_slots_);
+int Engine::init()
+{
+    auto get = [&](auto** p, size_t n) -> int {
+        using T = typename std::remove_pointer<typename std::remove_reference<decltype(p)>::type>::type;
+        void* q = nullptr;
+        const size_t bytes = n * sizeof(**p) + 16;
+        cudaError_t e = cudaMallocAsync(&q, bytes, st_);
+        if (e != cudaSuccess)
+            return set_error(BBS_ENOMEM, "engine: cudaMallocAsync(%zu bytes): %s", bytes, cudaGetErrorString(e));
+        fixed_.push_back(q);
+        fixed_bytes_ += bytes;
+        *p = (T)q;
         return BBS_OK;
+    };
+    BBS_TRY(get(&pool_.nodes, (size_t)(nchunks_ * CH)));
+    BBS_TRY(get(&pool_.chunk_bucket, (size_t)nchunks_));
+    BBS_TRY(get(&pool_.chunk_fill, (size_t)nchunks_));
+    BBS_TRY(get(&pool_.free_ids, (size_t)nchunks_));
+    BBS_TRY(get(&pool_.free_top, 1));
+    pool_.nchunks = nchunks_;
+    BBS_TRY(get(&d_S_, (size_t)max_slots_));
+    BBS_TRY(get(&d_ctl_, (size_t)max_slots_));
+    BBS_TRY(get(&parents_, (size_t)(nchunks_ * CH)));
+    BBS_TRY(get(&d_poff_, (size_t)max_slots_));
+    BBS_TRY(get(&d_slots_, (size_t)max_slots_));
+    BBS_TRY(get(&dense_, (size_t)DENSE_CAP));
+    BBS_TRY(get(&surv_.nodes, (size_t)DENSE_CAP));
+    BBS_TRY(get(&surv_.scores, (size_t)DENSE_CAP));
+    BBS_TRY(get(&surv_.sid, (size_t)DENSE_CAP));
+    BBS_TRY(get(&surv_.count, 1));
+    BBS_TRY(get(&surv_.err, 1));
+    surv_.cap = DENSE_CAP;
+    BBS_CUDA_TRY(cudaMemsetAsync(d_ctl_, 0, sizeof(Ctl) * (size_t)max_slots_, st_));
+    BBS_CUDA_TRY(cudaMemsetAsync(d_S_, 0, sizeof(SearchDev) * (size_t)max_slots_, st_));
+    BBS_CUDA_TRY(cudaMemsetAsync(surv_.count, 0, sizeof(unsigned long long), st_));
+    BBS_CUDA_TRY(cudaMemsetAsync(surv_.err, 0, sizeof(int), st_));
+    BBS_CUDA_TRY(cudaMallocHost((void**)&h_ctl_, sizeof(Ctl) * (size_t)max_slots_));
+    BBS_CUDA_TRY(cudaMallocHost((void**)&h_poff_, sizeof(int64_t) * (size_t)max_slots_));
+    std::memset(h_ctl_, 0, sizeof(Ctl) * (size_t)max_slots_);
+    // every slot's record points at its control block even while unused
+    std::vector<SearchDev> blank((size_t)max_slots_);
+    for (int i = 0; i < max_slots_; ++i) {
+        std::memset(&blank[(size_t)i], 0, sizeof(SearchDev));
+        blank[(size_t)i].ctl = d_ctl_ + i;
     }
+    BBS_CUDA_TRY(cudaMemcpyAsync(d_S_, blank.data(), sizeof(SearchDev) * blank.size(), cudaMemcpyHostToDevice, st_));
+    BBS_CUDA_TRY(cudaStreamSynchronize(st_));   // the host copy above must outlive its transfer
+    pool_init_kernel<<<(int)std::min<int64_t>((nchunks_ + 255) / 256, 4096), 256, 0, st_>>>(pool_);
+    launches_ += 1;
+    BBS_CUDA_TRY(cudaGetLastError());
+    return BBS_OK;
+}
 
-    // add a search; its initial set is scored by the next start()
-    int add(const bbs_maps* m, const float* xyz, int64_t k, int is_device, const bbs_ranges* rg, const bbs_opts* opts,
-            bbs_result* res)
-    {
-        if ((int)hosts_.size() >= max_slots_) return set_error(BBS_EINVAL, "engine: more than %d searches", max_slots_);
-        hosts_.emplace_back();
-        SearchHost& h = hosts_.back();
-        h.t0 = now_ms();
-        std::memset(res, 0, sizeof(*res));
-        res->num_points = (int32_t)k;
-        h.res = res;
-        h.maps = m;
-        const double frac = (opts && opts->score_frac > 0.0) ? opts->score_frac : 0.95;
-        const uint32_t flags = opts ? opts->flags : 0u;
-        if (!(frac > 0.0 && frac <= 1.0)) return set_error(BBS_EINVAL, "localize: score_frac %g outside (0, 1]", frac);
-        if (flags & BBS_PRUNE_GE) return set_error(BBS_EINVAL, "localize: BBS_PRUNE_GE is not supported");
-        if (k > (1 << 24)) return set_error(BBS_EINVAL, "localize: more than 2^24 scan points");
-        BBS_TRY(scan_prepare(m, xyz, k, is_device, rg, opts, st_, &h.scan));
+template <class T>
+int Engine::slot_get(SearchHost& h, T** p, size_t n)
+{
+    void* q = nullptr;
+    const size_t bytes = n * sizeof(T) + 16;
+    cudaError_t e = cudaMallocAsync(&q, bytes, st_);
+    if (e != cudaSuccess) return set_error(BBS_ENOMEM, "engine: cudaMallocAsync(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    h.bufs.push_back(q);
+    h.bytes += bytes;
+    *p = (T*)q;
+    return BBS_OK;
+}
+
+size_t Engine::estimate_bytes(int64_t k, const HostGrid& g) const
+{
+    const size_t K1 = (size_t)k + 1;
+    return sizeof(float4) * (size_t)(k > 0 ? k : 1) + sizeof(float4) * 3 * (size_t)g.total_rot + 68 * K1 +
+           16 * (size_t)nchunks_ + 1024;
+}
+
+int Engine::free_slot() const
+{
+    for (size_t i = 0; i < hosts_.size(); ++i)
+        if (!hosts_[i].used) return (int)i;
+    return -1;
+}
+
+int Engine::live_count() const
+{
+    int n = 0;
+    for (const auto& h : hosts_) n += h.live ? 1 : 0;
+    return n;
+}
+
+int Engine::used_count() const
+{
+    int n = 0;
+    for (const auto& h : hosts_) n += h.used ? 1 : 0;
+    return n;
+}
+
+int Engine::upload_slot(int i)
+{
+    SearchHost& h = hosts_[(size_t)i];
+    h.dev.ctl = d_ctl_ + i;
+    h_ctl_[i] = h.ctl0;
+    BBS_CUDA_TRY(cudaMemcpyAsync(d_S_ + i, &h.dev, sizeof(SearchDev), cudaMemcpyHostToDevice, st_));
+    BBS_CUDA_TRY(cudaMemcpyAsync(d_ctl_ + i, &h_ctl_[i], sizeof(Ctl), cudaMemcpyHostToDevice, st_));
+    return BBS_OK;
+}
+
+int Engine::add(const bbs_maps* m, const float* xyz, int64_t k, int is_device, const bbs_ranges* rg,
+                const bbs_opts* opts, uint64_t tag, int* slot)
+{
+    const int i = free_slot();
+    if (i < 0) return set_error(BBS_EINVAL, "engine: all %d search slots are in use", max_slots_);
+    SearchHost& h = hosts_[(size_t)i];
+    h = SearchHost();
+    h.used = true;
+    h.tag = tag;
+    h.t0 = now_ms();
+    h.res.num_points = (int32_t)k;
+    h.maps = m;
+    *slot = i;
+    const double frac = (opts && opts->score_frac > 0.0) ? opts->score_frac : 0.95;
+    const uint32_t flags = opts ? opts->flags : 0u;
+    int rc = BBS_OK;
+    if (!(frac > 0.0 && frac <= 1.0)) rc = set_error(BBS_EINVAL, "localize: score_frac %g outside (0, 1]", frac);
+    else if (flags & BBS_PRUNE_GE) rc = set_error(BBS_EINVAL, "localize: BBS_PRUNE_GE is not supported");
+    else if (k > (1 << 24)) rc = set_error(BBS_EINVAL, "localize: more than 2^24 scan points");
+    if (rc == BBS_OK) rc = scan_prepare(m, xyz, k, is_device, rg, opts, st_, &h.scan);
+    if (rc < 0) {
+        release(i);
+        return rc;
+    }
+    const HostGrid& g = h.scan.grid;
+    h.bytes += estimate_bytes(k, g) - (68 * ((size_t)k + 1) + 16 * (size_t)nchunks_ + 1024);
+    h.thr = (int32_t)std::ceil(frac * (double)k);
+    h.res.phase_ms[0] = now_ms() - h.t0;
+    h.res.h2d_bytes += h.scan.h2d;
+    h.res.d2h_bytes += h.scan.d2h;
+    h.res.launches += 2;
+    if (k == 0) return BBS_OK;   // never live: reported as not found
+    for (int l = 1; l < g.levels; ++l) h.rmax = std::max<int>(h.rmax, (int)(g.a[l][0] * g.a[l][1] * g.a[l][2]));
+    h.chunks = (int)((k + PCHUNK - 1) / PCHUNK);
+    SearchDev& d = h.dev;
+    std::memset(&d, 0, sizeof(d));
+    d.scan = h.scan.scan;
+    d.rot = h.scan.rot;
+    d.K = (int32_t)k;
+    d.lmax = g.levels - 1;
+    d.batch = (opts && opts->batch > 0) ? opts->batch : 10000;
+    for (int a = 0; a < 3; ++a) {
+        const int64_t pmin = floor_div2(g.wmin[a]), pmax = floor_div2(g.wmax[a]);
+        d.pmin[a] = (int32_t)pmin;
+        d.pext[a] = (int32_t)(pmax - pmin + 1);
+        d.wmin[a] = (int32_t)g.wmin[a];
+        d.wmax[a] = (int32_t)g.wmax[a];
+    }
+    d.grid = dev_grid(g);
+    for (int l = 0; l < MAX_LEVELS; ++l) d.maps[l] = l < m->levels ? level_view(m, l) : LevelView{};
+    const size_t K1 = (size_t)k + 1;
+    rc = BBS_OK;
+    if (rc == BBS_OK) rc = slot_get(h, &d.b_cnt, K1);
+    if (rc == BBS_OK) rc = slot_get(h, &d.b_kids, K1);
+    if (rc == BBS_OK) rc = slot_get(h, &d.b_leaf, K1);
+    if (rc == BBS_OK) rc = slot_get(h, &d.b_tail, K1);
+    if (rc == BBS_OK) rc = slot_get(h, &d.h_cnt, K1);
+    if (rc == BBS_OK) rc = slot_get(h, &d.h_kids, K1);
+    if (rc == BBS_OK) rc = slot_get(h, &d.h_leaf, K1);
+    if (rc == BBS_OK) rc = slot_get(h, &d.w_pos, K1);
+    if (rc == BBS_OK) rc = slot_get(h, &d.w_space, K1);
+    if (rc == BBS_OK) rc = slot_get(h, &d.w_choff, K1);
+    if (rc == BBS_OK) rc = slot_get(h, &d.w_tail, K1);
+    if (rc == BBS_OK) rc = slot_get(h, &d.w_fill0, K1);
+    if (rc == BBS_OK) rc = slot_get(h, &d.act, (size_t)nchunks_);
+    if (rc == BBS_OK) rc = slot_get(h, &d.pop_ids, (size_t)nchunks_);
+    if (rc == BBS_OK) rc = slot_get(h, &d.pop_start, (size_t)nchunks_);
+    if (rc < 0) {
+        release(i);
+        return rc;
+    }
+    h.ctl0 = Ctl();
+    h.ctl0.best = h.thr - 1;
+    h.ctl0.top = -1;
+    h.ctl0.active = 1;
+    h.live = true;
+    h.fresh = true;
+    int64_t n0 = 1;
+    for (int a = 0; a < 3; ++a) n0 *= (g.wmax[a] - g.wmin[a] + 1);
+    h.res.nodes_scored = n0 * g.nrot[g.levels - 1];
+    rc = upload_slot(i);
+    if (rc < 0) {
+        release(i);
+        return rc;
+    }
+    return BBS_OK;
+}
+
+int Engine::start()
+{
+    std::vector<int32_t> slots;
+    for (int i = 0; i < max_slots_; ++i)
+        if (hosts_[(size_t)i].fresh) slots.push_back(i);
+    if (slots.empty()) return BBS_OK;
+    BBS_CUDA_TRY(cudaMemcpyAsync(d_slots_, slots.data(), sizeof(int32_t) * slots.size(), cudaMemcpyHostToDevice, st_));
+    slot_init_kernel<<<(int)slots.size(), 1024, 0, st_>>>(d_S_, d_slots_);
+    launches_ += 1;
+    BBS_CUDA_TRY(cudaGetLastError());
+    // the initial sets: virtual parents x rotations at l_max, in launches
+    // bounded by the dense capacity
+    std::vector<Seg> segs;
+    int64_t work = 0, dense = 0;
+    auto flush = [&]() -> int {
+        if (segs.empty()) return BBS_OK;
+        BBS_TRY(score_launch(MODE_INITIAL, segs, work, dense));
+        segs.clear();
+        work = dense = 0;
+        return BBS_OK;
+    };
+    for (int i : slots) {
+        SearchHost& h = hosts_[(size_t)i];
         const HostGrid& g = h.scan.grid;
-        h.thr = (int32_t)std::ceil(frac * (double)k);
-        res->phase_ms[0] = now_ms() - h.t0;
-        res->h2d_bytes += h.scan.h2d;
-        res->d2h_bytes += h.scan.d2h;
-        res->launches += 2;
-        if (k == 0) return BBS_OK;   // not live: NOT_FOUND
-        for (int l = 1; l < g.levels; ++l) h.rmax = std::max<int>(h.rmax, (int)(g.a[l][0] * g.a[l][1] * g.a[l][2]));
-        h.chunks = (int)((k + PCHUNK - 1) / PCHUNK);
-        SearchDev& d = h.dev;
-        std::memset(&d, 0, sizeof(d));
-        d.scan = h.scan.scan;
-        d.rot = h.scan.rot;
-        d.K = (int32_t)k;
-        d.lmax = g.levels - 1;
-        d.batch = (opts && opts->batch > 0) ? opts->batch : 10000;
-        for (int i = 0; i < 3; ++i) {
-            const int64_t pmin = floor_div2(g.wmin[i]), pmax = floor_div2(g.wmax[i]);
-            d.pmin[i] = (int32_t)pmin;
-            d.pext[i] = (int32_t)(pmax - pmin + 1);
-            d.wmin[i] = (int32_t)g.wmin[i];
-            d.wmax[i] = (int32_t)g.wmax[i];
-        }
-        d.grid = dev_grid(g);
-        for (int l = 0; l < MAX_LEVELS; ++l) d.maps[l] = l < m->levels ? level_view(m, l) : LevelView{};
-        const size_t K1 = (size_t)k + 1;
-        BBS_TRY(A_.get(&d.b_cnt, K1));
-        BBS_TRY(A_.get(&d.b_kids, K1));
-        BBS_TRY(A_.get(&d.b_leaf, K1));
-        BBS_TRY(A_.get(&d.b_tail, K1));
-        BBS_TRY(A_.get(&d.h_cnt, K1));
-        BBS_TRY(A_.get(&d.h_kids, K1));
-        BBS_TRY(A_.get(&d.h_leaf, K1));
-        BBS_TRY(A_.get(&d.w_pos, K1));
-        BBS_TRY(A_.get(&d.w_space, K1));
-        BBS_TRY(A_.get(&d.w_choff, K1));
-        BBS_TRY(A_.get(&d.w_tail, K1));
-        BBS_TRY(A_.get(&d.w_fill0, K1));
-        BBS_TRY(A_.get(&d.act, (size_t)nchunks_));
-        BBS_TRY(A_.get(&d.pop_ids, (size_t)nchunks_));
-        BBS_TRY(A_.get(&d.pop_start, (size_t)nchunks_));
-        h.ctl0.best = h.thr - 1;
-        h.ctl0.top = -1;
-        h.ctl0.active = 1;
-        h.live = true;
-        // initial-set statistics
-        int64_t n0 = 1;
-        for (int i = 0; i < 3; ++i) n0 *= (g.wmax[i] - g.wmin[i] + 1);
-        res->nodes_scored = n0 * g.nrot[g.levels - 1];
-        return BBS_OK;
-    }
-
-    // upload slots, score every live search's initial set
-    int start()
-    {
-        const int n = (int)hosts_.size();
-        std::vector<SearchDev> hs((size_t)n);
-        std::vector<int32_t> slots;
-        for (int i = 0; i < n; ++i) {
-            hosts_[(size_t)i].dev.ctl = d_ctl_ + i;
-            hs[(size_t)i] = hosts_[(size_t)i].dev;
-            h_ctl_[i] = hosts_[(size_t)i].ctl0;
-            if (hosts_[(size_t)i].live) slots.push_back(i);
-        }
-        nslots_ = n;
-        BBS_CUDA_TRY(cudaMemcpyAsync(d_S_, hs.data(), sizeof(SearchDev) * (size_t)n, cudaMemcpyHostToDevice, st_));
-        BBS_CUDA_TRY(cudaMemcpyAsync(d_ctl_, h_ctl_, sizeof(Ctl) * (size_t)n, cudaMemcpyHostToDevice, st_));
-        if (slots.empty()) return BBS_OK;
-        BBS_CUDA_TRY(cudaMemcpyAsync(d_slots_, slots.data(), sizeof(int32_t) * slots.size(), cudaMemcpyHostToDevice, st_));
-        slot_init_kernel<<<(int)slots.size(), 1024, 0, st_>>>(d_S_, d_slots_);
-        launches_ += 1;
-        BBS_CUDA_TRY(cudaGetLastError());
-        // the initial sets: virtual parents x rotations at l_max, sliced by dense capacity
-        std::vector<Seg> segs;
-        int64_t work = 0, dense = 0;
-        auto flush = [&]() -> int {
-            if (segs.empty()) return BBS_OK;
-            BBS_TRY(score_launch(MODE_INITIAL, segs, work, dense));
-            segs.clear();
-            work = dense = 0;
-            return BBS_OK;
-        };
-        for (int i : slots) {
-            SearchHost& h = hosts_[(size_t)i];
-            const HostGrid& g = h.scan.grid;
-            const int64_t R = g.nrot[g.levels - 1];
-            const int64_t vpn = (int64_t)h.dev.pext[0] * h.dev.pext[1] * h.dev.pext[2];
-            const int64_t per = R * 8;
-            if (per > DENSE_CAP) return set_error(BBS_EINVAL, "localize: %lld initial rotations", (long long)R);
-            for (int64_t v0 = 0; v0 < vpn;) {
-                int64_t take = std::min<int64_t>(vpn - v0, (DENSE_CAP - dense) / per);
-                if (take <= 0 || (int)segs.size() == MAXSEG) {
-                    BBS_TRY(flush());
-                    continue;
-                }
-                Seg s;
-                std::memset(&s, 0, sizeof(s));
-                s.first_parent = v0;
-                s.first_work = work;
-                s.n_parents = take;
-                s.dense_base = dense;
-                s.chunks = h.chunks;
-                s.sid = i;
-                s.R = (int32_t)R;
-                segs.push_back(s);
-                work += take * h.chunks;
-                dense += take * per;
-                h.res->gathers += take * R * h.scan.k;
-                v0 += take;
-            }
-        }
-        BBS_TRY(flush());
-        const double t = now_ms();
-        for (int i : slots) {
-            SearchHost& h = hosts_[(size_t)i];
-            h.res->phase_ms[1] = t - h.t0 - h.res->phase_ms[0];
-            h.t_init = t;
-        }
-        return BBS_OK;
-    }
-
-    // iterate until every search is done
-    int run()
-    {
-        const int n = nslots_;
-        int64_t iter = 0;
-        for (;;) {
-            if (n == 0) break;
-            select_kernel<<<std::min(n, 1024), 1024, 0, st_>>>(d_S_, n, pool_);
-            launches_ += 1;
-            BBS_CUDA_TRY(cudaGetLastError());
-            // the control blocks of every slot, one copy
-            BBS_CUDA_TRY(cudaMemcpyAsync(h_ctl_, d_ctl_, sizeof(Ctl) * (size_t)n, cudaMemcpyDeviceToHost, st_));
-            BBS_CUDA_TRY(cudaStreamSynchronize(st_));
-            const double t = now_ms();
-            int64_t total_parents = 0;
-            bool err = false;
-            for (int i = 0; i < n; ++i) {
-                SearchHost& h = hosts_[(size_t)i];
-                const Ctl& c = h_ctl_[i];
-                if (!h.live) continue;
-                h.res->d2h_bytes += (int64_t)sizeof(Ctl);
-                if (c.err) err = true;
-                if (c.match_changed) h.t_match = t;
-                h_poff_[i] = total_parents;
-                if (c.done) {
-                    h.live = false;
-                    h.t_end = t;
-                    continue;
-                }
-                total_parents += c.n_parents;
-                h.res->iterations++;
-                h.res->parents_branched += c.n_parents;
-                h.res->nodes_scored += c.popped_kids;
-                h.res->gathers += (c.popped_kids / 8) * h.scan.k;
-            }
-            if (err) return set_error(BBS_ENOMEM, "localize: the frontier pool (%lld nodes) is exhausted",
-                                      (long long)(nchunks_ * CH));
-            if (total_parents == 0) break;
-            if (++iter > ((int64_t)1 << 24)) return set_error(BBS_ETIMEOUT, "localize: iteration limit");
-            BBS_CUDA_TRY(cudaMemcpyAsync(d_poff_, h_poff_, sizeof(int64_t) * (size_t)n, cudaMemcpyHostToDevice, st_));
-            int64_t maxpop = 1;
-            for (int i = 0; i < n; ++i)
-                if (hosts_[(size_t)i].live) maxpop = std::max<int64_t>(maxpop, h_ctl_[i].n_pop);
-            dim3 gg((unsigned)std::min<int64_t>(maxpop, 4096), (unsigned)std::min(n, 65535));
-            gather_kernel<<<gg, CH, 0, st_>>>(d_S_, pool_, d_poff_, n, parents_);
-            launches_ += 1;
-            BBS_CUDA_TRY(cudaGetLastError());
-            // score every popped parent, in slices bounded by the dense capacity
-            std::vector<Seg> segs;
-            int64_t work = 0, dense = 0;
-            auto flush = [&]() -> int {
-                if (segs.empty()) return BBS_OK;
-                BBS_TRY(score_launch(MODE_SEARCH, segs, work, dense));
-                segs.clear();
-                work = dense = 0;
-                return BBS_OK;
-            };
-            for (int i = 0; i < n; ++i) {
-                SearchHost& h = hosts_[(size_t)i];
-                if (!h.live) continue;
-                const int64_t np = h_ctl_[i].n_parents;
-                const int64_t per = (int64_t)h.rmax * 8;
-                for (int64_t p0 = 0; p0 < np;) {
-                    const int64_t take = std::min<int64_t>(np - p0, (DENSE_CAP - dense) / per);
-                    if (take <= 0 || (int)segs.size() == MAXSEG) {
-                        BBS_TRY(flush());
-                        continue;
-                    }
-                    Seg s;
-                    std::memset(&s, 0, sizeof(s));
-                    s.first_parent = h_poff_[i] + p0;
-                    s.first_work = work;
-                    s.n_parents = take;
-                    s.dense_base = dense;
-                    s.chunks = h.chunks;
-                    s.sid = i;
-                    s.R = h.rmax;
-                    segs.push_back(s);
-                    work += take * h.chunks;
-                    dense += take * per;
-                    p0 += take;
-                }
-            }
-            BBS_TRY(flush());
-        }
-        // final statistics
-        for (int i = 0; i < n; ++i) {
-            SearchHost& h = hosts_[(size_t)i];
-            if (h.t_end == 0) h.t_end = now_ms();
-        }
-        int herr = 0;
-        BBS_CUDA_TRY(cudaMemcpyAsync(&herr, surv_.err, sizeof(int), cudaMemcpyDeviceToHost, st_));
-        BBS_CUDA_TRY(cudaMemcpyAsync(h_ctl_, d_ctl_, sizeof(Ctl) * (size_t)n, cudaMemcpyDeviceToHost, st_));
-        BBS_CUDA_TRY(cudaStreamSynchronize(st_));
-        if (herr) return set_error(BBS_ECORRUPT, "localize: survivor staging overflow");
-        double score_ms = 0.0;
-        for (size_t i = 0; i + 1 < evs_.size(); i += 2) {
-            float ms = 0.0f;
-            BBS_CUDA_TRY(cudaEventElapsedTime(&ms, evs_[i], evs_[i + 1]));
-            score_ms += ms;
-        }
-        const double t_fin = now_ms();
-        for (int i = 0; i < n; ++i) {
-            SearchHost& h = hosts_[(size_t)i];
-            bbs_result* r = h.res;
-            const Ctl& c = h_ctl_[i];
-            r->launches += launches_;
-            r->score_launches = score_launches_;
-            r->score_ms = score_ms;
-            if (h.scan.k == 0) {
-                r->best_score = h.thr - 1;
-                r->status = BBS_NOT_FOUND;
-                r->ms_total = t_fin - h.t0;
+        const int64_t R = g.nrot[g.levels - 1];
+        const int64_t vpn = (int64_t)h.dev.pext[0] * h.dev.pext[1] * h.dev.pext[2];
+        const int64_t per = R * 8;
+        if (per > DENSE_CAP) return set_error(BBS_EINVAL, "localize: %lld initial rotations", (long long)R);
+        for (int64_t v0 = 0; v0 < vpn;) {
+            const int64_t take = std::min<int64_t>(vpn - v0, (DENSE_CAP - dense) / per);
+            if (take <= 0 || (int)segs.size() == MAXSEG) {
+                BBS_TRY(flush());
                 continue;
             }
-            const HostGrid& g = h.scan.grid;
-            r->probes = r->nodes_scored * h.scan.k;
-            r->best_score = c.best;
-            r->peak_frontier = c.peak;
-            r->phase_ms[2] = (h.t_match >= 0 ? h.t_match : h.t_end) - h.t_init;
-            r->phase_ms[3] = h.t_match >= 0 ? h.t_end - h.t_match : 0.0;
-            r->d2h_bytes += (int64_t)sizeof(Ctl);
-            if (c.found) {
-                const NodeRec& nd = c.match;
-                const uint32_t rot = rl_rot(nd.rl);
-                const int64_t ng = g.N[0][2], nb = g.N[0][1];
-                r->found = 1;
-                r->node[0] = nd.cx;
-                r->node[1] = nd.cy;
-                r->node[2] = nd.cz;
-                r->node[3] = (int32_t)(rot / (ng * nb));
-                r->node[4] = (int32_t)((rot / ng) % nb);
-                r->node[5] = (int32_t)(rot % ng);
-                r->node[6] = 0;
-                for (int a = 0; a < 3; ++a) r->pose[a] = (double)r->node[a] * g.r;
-                for (int a = 0; a < 3; ++a) r->pose[3 + a] = grid_angle(g, 0, a, r->node[3 + a]);
-                r->status = BBS_OK;
-                r->ms_to_optimum = h.t_match - h.t0;
-            } else {
-                r->status = BBS_NOT_FOUND;
-                r->ms_to_optimum = h.t_end - h.t0;
+            Seg sg;
+            std::memset(&sg, 0, sizeof(sg));
+            sg.first_parent = v0;
+            sg.first_work = work;
+            sg.n_parents = take;
+            sg.dense_base = dense;
+            sg.chunks = h.chunks;
+            sg.sid = i;
+            sg.R = (int32_t)R;
+            segs.push_back(sg);
+            work += take * h.chunks;
+            dense += take * per;
+            h.res.gathers += take * R * h.scan.k;
+            v0 += take;
+        }
+    }
+    BBS_TRY(flush());
+    const double t = now_ms();
+    for (int i : slots) {
+        SearchHost& h = hosts_[(size_t)i];
+        h.res.phase_ms[1] = t - h.t0 - h.res.phase_ms[0];
+        h.t_init = t;
+        h.fresh = false;
+    }
+    return BBS_OK;
+}
+
+int Engine::step(std::vector<int>* finished)
+{
+    const int n = max_slots_;
+    // searches that never went live (no points, or failed) finish at once
+    for (int i = 0; i < n; ++i) {
+        SearchHost& h = hosts_[(size_t)i];
+        if (h.used && !h.live && h.t_end == 0) {
+            h.t_end = now_ms();
+            finished->push_back(i);
+        }
+    }
+    if (live_count() == 0) return BBS_OK;
+    select_kernel<<<n, 1024, 0, st_>>>(d_S_, n, pool_);
+    launches_ += 1;
+    BBS_CUDA_TRY(cudaGetLastError());
+    BBS_CUDA_TRY(cudaMemcpyAsync(h_ctl_, d_ctl_, sizeof(Ctl) * (size_t)n, cudaMemcpyDeviceToHost, st_));
+    BBS_CUDA_TRY(cudaStreamSynchronize(st_));
+    const double t = now_ms();
+    int64_t total_parents = 0;
+    for (int i = 0; i < n; ++i) {
+        SearchHost& h = hosts_[(size_t)i];
+        h_poff_[i] = total_parents;
+        if (!h.live) continue;
+        const Ctl& c = h_ctl_[i];
+        h.res.d2h_bytes += (int64_t)sizeof(Ctl);
+        if (c.err) {
+            // the shared pool ran out while this search inserted: it fails alone
+            h.status = set_error(BBS_ENOMEM, "localize: the frontier pool (%lld nodes) is exhausted",
+                                 (long long)(nchunks_ * CH));
+            h.live = false;
+            h.t_end = t;
+            finished->push_back(i);
+            continue;
+        }
+        if (c.match_changed) h.t_match = t;
+        if (c.done) {
+            h.live = false;
+            h.t_end = t;
+            finished->push_back(i);
+            continue;
+        }
+        total_parents += c.n_parents;
+        h.res.iterations++;
+        h.res.parents_branched += c.n_parents;
+        h.res.nodes_scored += c.popped_kids;
+        h.res.gathers += (c.popped_kids / 8) * h.scan.k;
+    }
+    if (total_parents == 0) return BBS_OK;
+    BBS_CUDA_TRY(cudaMemcpyAsync(d_poff_, h_poff_, sizeof(int64_t) * (size_t)n, cudaMemcpyHostToDevice, st_));
+    int64_t maxpop = 1;
+    for (int i = 0; i < n; ++i)
+        if (hosts_[(size_t)i].live) maxpop = std::max<int64_t>(maxpop, h_ctl_[i].n_pop);
+    dim3 gg((unsigned)std::min<int64_t>(maxpop, 4096), (unsigned)std::min(n, 65535));
+    gather_kernel<<<gg, CH, 0, st_>>>(d_S_, pool_, d_poff_, n, parents_);
+    launches_ += 1;
+    BBS_CUDA_TRY(cudaGetLastError());
+    std::vector<Seg> segs;
+    int64_t work = 0, dense = 0;
+    auto flush = [&]() -> int {
+        if (segs.empty()) return BBS_OK;
+        BBS_TRY(score_launch(MODE_SEARCH, segs, work, dense));
+        segs.clear();
+        work = dense = 0;
+        return BBS_OK;
+    };
+    for (int i = 0; i < n; ++i) {
+        SearchHost& h = hosts_[(size_t)i];
+        if (!h.live) continue;
+        const int64_t np = h_ctl_[i].n_parents;
+        const int64_t per = (int64_t)h.rmax * 8;
+        for (int64_t p0 = 0; p0 < np;) {
+            const int64_t take = std::min<int64_t>(np - p0, (DENSE_CAP - dense) / per);
+            if (take <= 0 || (int)segs.size() == MAXSEG) {
+                BBS_TRY(flush());
+                continue;
             }
-            r->ms_total = t_fin - h.t0;
-            r->phase_ms[4] = t_fin - h.t_end;
+            Seg sg;
+            std::memset(&sg, 0, sizeof(sg));
+            sg.first_parent = h_poff_[i] + p0;
+            sg.first_work = work;
+            sg.n_parents = take;
+            sg.dense_base = dense;
+            sg.chunks = h.chunks;
+            sg.sid = i;
+            sg.R = h.rmax;
+            segs.push_back(sg);
+            work += take * h.chunks;
+            dense += take * per;
+            p0 += take;
         }
-        return BBS_OK;
     }
+    BBS_TRY(flush());
+    return BBS_OK;
+}
 
-  private:
-    static constexpr int64_t DENSE_CAP = (int64_t)1 << 22;   // child scores per scoring launch
-
-    int score_launch(int mode, const std::vector<Seg>& segs, int64_t work, int64_t dense)
-    {
-        BranchLaunch L;
-        std::memset(&L, 0, sizeof(L));
-        L.S = d_S_;
-        L.parents = parents_;
-        L.dense = dense_;
-        L.n_work = work;
-        L.n_dense = dense;
-        L.nseg = (int32_t)segs.size();
-        L.mode = mode;
-        for (size_t i = 0; i < segs.size(); ++i) L.seg[i] = segs[i];
-        BBS_CUDA_TRY(cudaMemsetAsync(dense_, 0, sizeof(int32_t) * (size_t)dense, st_));
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (timed_) {
-            BBS_CUDA_TRY(cudaEventCreate(&e0));
-            evs_.push_back(e0);
-            BBS_CUDA_TRY(cudaEventCreate(&e1));
-            evs_.push_back(e1);
-            BBS_CUDA_TRY(cudaEventRecord(e0, st_));
+int Engine::finalize(int i, bbs_result* out)
+{
+    SearchHost& h = hosts_[(size_t)i];
+    int herr = 0;
+    Ctl c;
+    std::memset(&c, 0, sizeof(c));
+    BBS_CUDA_TRY(cudaMemcpyAsync(&herr, surv_.err, sizeof(int), cudaMemcpyDeviceToHost, st_));
+    if (h.scan.k > 0) BBS_CUDA_TRY(cudaMemcpyAsync(&c, d_ctl_ + i, sizeof(Ctl), cudaMemcpyDeviceToHost, st_));
+    BBS_CUDA_TRY(cudaStreamSynchronize(st_));
+    for (size_t e = 0; e + 1 < evs_.size(); e += 2) {
+        float ms = 0.0f;
+        BBS_CUDA_TRY(cudaEventElapsedTime(&ms, evs_[e], evs_[e + 1]));
+        score_ms_ += ms;
+    }
+    for (cudaEvent_t e : evs_) cudaEventDestroy(e);
+    evs_.clear();
+    bbs_result* r = &h.res;
+    const double t_fin = now_ms();
+    if (h.t_end == 0) h.t_end = t_fin;
+    r->launches += launches_;
+    r->score_launches = score_launches_;
+    r->score_ms = score_ms_;
+    int status;
+    if (herr) {
+        status = set_error(BBS_ECORRUPT, "localize: survivor staging overflow");
+    } else if (h.status < 0) {
+        status = h.status;
+    } else if (h.scan.k == 0) {
+        r->best_score = h.thr - 1;
+        status = BBS_NOT_FOUND;
+    } else {
+        const HostGrid& g = h.scan.grid;
+        r->probes = r->nodes_scored * h.scan.k;
+        r->best_score = c.best;
+        r->peak_frontier = c.peak;
+        r->phase_ms[2] = (h.t_match >= 0 ? h.t_match : h.t_end) - h.t_init;
+        r->phase_ms[3] = h.t_match >= 0 ? h.t_end - h.t_match : 0.0;
+        r->d2h_bytes += (int64_t)sizeof(Ctl);
+        if (c.found) {
+            const NodeRec& nd = c.match;
+            const uint32_t rot = rl_rot(nd.rl);
+            const int64_t ng = g.N[0][2], nb = g.N[0][1];
+            r->found = 1;
+            r->node[0] = nd.cx;
+            r->node[1] = nd.cy;
+            r->node[2] = nd.cz;
+            r->node[3] = (int32_t)(rot / (ng * nb));
+            r->node[4] = (int32_t)((rot / ng) % nb);
+            r->node[5] = (int32_t)(rot % ng);
+            r->node[6] = 0;
+            for (int a = 0; a < 3; ++a) r->pose[a] = (double)r->node[a] * g.r;
+            for (int a = 0; a < 3; ++a) r->pose[3 + a] = grid_angle(g, 0, a, r->node[3 + a]);
+            r->ms_to_optimum = h.t_match - h.t0;
+            status = BBS_OK;
+        } else {
+            r->ms_to_optimum = h.t_end - h.t0;
+            status = BBS_NOT_FOUND;
         }
-        BBS_CUDA_TRY(launch_branch(L, st_));
-        if (timed_) BBS_CUDA_TRY(cudaEventRecord(e1, st_));
-        BBS_CUDA_TRY(launch_finalize(L, d_S_, surv_, st_));
-        alloc_kernel<<<std::min(nslots_, 1024), 1024, 0, st_>>>(d_S_, nslots_, pool_);
-        scatter_kernel<<<1024, 256, 0, st_>>>(d_S_, pool_, surv_.nodes, surv_.scores, surv_.sid, surv_.count, surv_.cap);
-        BBS_CUDA_TRY(cudaMemsetAsync(surv_.count, 0, sizeof(unsigned long long), st_));
-        BBS_CUDA_TRY(cudaGetLastError());
-        launches_ += 4;
-        score_launches_ += 1;
-        return BBS_OK;
     }
+    r->status = status;
+    r->ms_total = t_fin - h.t0;
+    r->phase_ms[4] = t_fin - h.t_end;
+    if (out) *out = *r;
+    BBS_TRY(release(i));
+    return status;
+}
 
-    cudaStream_t st_;
-    DevArena A_;
-    int max_slots_;
-    bool timed_;
-    int64_t nchunks_ = 0;
-    int nslots_ = 0;
-    PoolDev pool_{};
-    SearchDev* d_S_ = nullptr;
-    Ctl* d_ctl_ = nullptr;
-    NodeRec* parents_ = nullptr;
-    int64_t* d_poff_ = nullptr;
-    int32_t* d_slots_ = nullptr;
-    int32_t* dense_ = nullptr;
-    SurvOut surv_{};
-    Ctl* h_ctl_ = nullptr;
-    int64_t* h_poff_ = nullptr;
-    std::vector<SearchHost> hosts_;
-    std::vector<cudaEvent_t> evs_;
-    int64_t launches_ = 0, score_launches_ = 0;
-};
+int Engine::cancel(int i, int code, bbs_result* out)
+{
+    SearchHost& h = hosts_[(size_t)i];
+    if (h.live) {
+        h.live = false;
+        h.status = code;
+        h.t_end = now_ms();
+    }
+    return finalize(i, out);
+}
+
+int Engine::release(int i)
+{
+    SearchHost& h = hosts_[(size_t)i];
+    if (!h.used) return BBS_OK;
+    // chunks still held (a search stopped early) go back to the pool
+    if (h.dev.K > 0 && d_S_) {
+        slot_release_kernel<<<1, 1024, 0, st_>>>(d_S_, i, pool_);
+        launches_ += 1;
+    }
+    Ctl z;
+    std::memset(&z, 0, sizeof(z));
+    h_ctl_[i] = z;
+    if (d_ctl_) cudaMemcpyAsync(d_ctl_ + i, &h_ctl_[i], sizeof(Ctl), cudaMemcpyHostToDevice, st_);
+    for (void* p : h.bufs) cudaFreeAsync(p, st_);
+    scan_release(&h.scan, st_);
+    cudaError_t e = cudaStreamSynchronize(st_);   // the zeroed control block must land before the slot is reused
+    h = SearchHost();
+    if (e != cudaSuccess) return set_error(BBS_ECUDA, "engine: %s", cudaGetErrorString(e));
+    return BBS_OK;
+}
+
+int Engine::score_launch(int mode, const std::vector<Seg>& segs, int64_t work, int64_t dense)
+{
+    BranchLaunch L;
+    std::memset(&L, 0, sizeof(L));
+    L.S = d_S_;
+    L.parents = parents_;
+    L.dense = dense_;
+    L.n_work = work;
+    L.n_dense = dense;
+    L.nseg = (int32_t)segs.size();
+    L.mode = mode;
+    for (size_t i = 0; i < segs.size(); ++i) L.seg[i] = segs[i];
+    BBS_CUDA_TRY(cudaMemsetAsync(dense_, 0, sizeof(int32_t) * (size_t)dense, st_));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (timed_) {
+        BBS_CUDA_TRY(cudaEventCreate(&e0));
+        evs_.push_back(e0);
+        BBS_CUDA_TRY(cudaEventCreate(&e1));
+        evs_.push_back(e1);
+        BBS_CUDA_TRY(cudaEventRecord(e0, st_));
+    }
+    BBS_CUDA_TRY(launch_branch(L, st_));
+    if (timed_) BBS_CUDA_TRY(cudaEventRecord(e1, st_));
+    BBS_CUDA_TRY(launch_finalize(L, d_S_, surv_, st_));
+    alloc_kernel<<<max_slots_, 1024, 0, st_>>>(d_S_, max_slots_, pool_);
+    scatter_kernel<<<1024, 256, 0, st_>>>(d_S_, pool_, surv_.nodes, surv_.scores, surv_.sid, surv_.count, surv_.cap);
+    BBS_CUDA_TRY(cudaMemsetAsync(surv_.count, 0, sizeof(unsigned long long), st_));
+    BBS_CUDA_TRY(cudaGetLastError());
+    launches_ += 4;
+    score_launches_ += 1;
+    return BBS_OK;
+}
+
+// ---- the one-shot entry points ------------------------------------------------------
 
 int search_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device, const bbs_ranges* rg,
                const bbs_opts* opts, cudaStream_t st, bbs_result* res)
@@ -862,11 +958,18 @@ int search_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device, co
     const int64_t max_frontier = (opts && opts->max_frontier > 0) ? opts->max_frontier : ((int64_t)1 << 24);
     const bool timed = opts && (opts->flags & BBS_TIME_KERNELS);
     const int64_t pool_nodes = max_frontier + (int64_t)CH * std::min<int64_t>(k + 1, 8192);
+    std::memset(res, 0, sizeof(*res));
     Engine E(st, 1, pool_nodes, timed);
     BBS_TRY(E.init());
-    BBS_TRY(E.add(m, xyz, k, is_device, rg, opts, res));
+    int slot = -1;
+    BBS_TRY(E.add(m, xyz, k, is_device, rg, opts, 0, &slot));
     BBS_TRY(E.start());
-    BBS_TRY(E.run());
+    std::vector<int> fin;
+    while (E.used_count() > 0) {
+        fin.clear();
+        BBS_TRY(E.step(&fin));
+        for (int i : fin) E.finalize(i, res);
+    }
     return res->status;
 }
 
@@ -880,9 +983,18 @@ int search_run_many(const bbs_maps* m, int n, const float* const* scans, const i
     const int64_t pool_nodes = max_frontier + (int64_t)CH * std::min<int64_t>((kmax + 1) * n, 8192 * (int64_t)n);
     Engine E(st, n, pool_nodes, timed);
     BBS_TRY(E.init());
-    for (int i = 0; i < n; ++i) BBS_TRY(E.add(m, scans[i], ks[i], is_device, rg, opts, &res[i]));
+    std::vector<int> slot_of((size_t)n, -1);
+    for (int i = 0; i < n; ++i) {
+        std::memset(&res[i], 0, sizeof(res[i]));
+        BBS_TRY(E.add(m, scans[i], ks[i], is_device, rg, opts, (uint64_t)i, &slot_of[(size_t)i]));
+    }
     BBS_TRY(E.start());
-    BBS_TRY(E.run());
+    std::vector<int> fin;
+    while (E.used_count() > 0) {
+        fin.clear();
+        BBS_TRY(E.step(&fin));
+        for (int s : fin) E.finalize(s, &res[E.tag(s)]);
+    }
     return BBS_OK;
 }
 

@@ -1,0 +1,100 @@
+// engine.cuh -- host side of the batched best-first search engine (engine.cu).
+//
+// An Engine owns one shared chunk pool and up to max_slots search slots.  A
+// search is added into a free slot (scan uploaded, grid and rotation tables
+// built, frontier arrays allocated), its initial set is scored by start(),
+// and every step() advances every live search by one canonical batch.  A
+// search that finishes is reported by step() and released by finalize(),
+// which also writes its bbs_result.  Slots can be added between steps, so the
+// same engine serves one call (bbs_localize), a batch (bbs_localize_many) or
+// a stream of requests (the server).  A search's trajectory depends only on
+// its own batches, never on which other searches share the launches.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "branch.cuh"
+
+namespace bbs {
+
+struct SearchHost {
+    bool used = false;     // the slot holds a search
+    bool live = false;     // the search is still iterating
+    bool fresh = false;    // its initial set is not scored yet
+    ScanState scan{};
+    const bbs_maps* maps = nullptr;
+    bbs_result res{};
+    int32_t thr = 0;
+    int rmax = 1;
+    int chunks = 1;
+    int status = 0;        // error status when the search failed on its own
+    double t0 = 0, t_match = -1, t_init = 0, t_end = 0;
+    SearchDev dev{};
+    Ctl ctl0{};
+    std::vector<void*> bufs;
+    size_t bytes = 0;      // device bytes held by the search
+    uint64_t tag = 0;
+};
+
+class Engine {
+  public:
+    Engine(cudaStream_t st, int max_slots, int64_t pool_nodes, bool timed);
+    ~Engine();
+    Engine(const Engine&) = delete;
+    Engine& operator=(const Engine&) = delete;
+
+    int init();
+    // a new search in a free slot; *slot receives its index
+    int add(const bbs_maps* m, const float* xyz, int64_t k, int is_device, const bbs_ranges* rg, const bbs_opts* opts,
+            uint64_t tag, int* slot);
+    // score the initial sets of every search added since the last call
+    int start();
+    // one iteration of every live search; searches that finished are appended to *finished
+    int step(std::vector<int>* finished);
+    // the search's result; the slot and its memory are released
+    int finalize(int slot, bbs_result* out);
+    // stop a search early and release it (its result reports status `code`)
+    int cancel(int slot, int code, bbs_result* out);
+
+    int live_count() const;
+    int used_count() const;
+    int free_slot() const;
+    size_t fixed_bytes() const { return fixed_bytes_; }
+    size_t slot_bytes(int slot) const { return hosts_[(size_t)slot].bytes; }
+    uint64_t tag(int slot) const { return hosts_[(size_t)slot].tag; }
+    int64_t pool_nodes() const { return nchunks_ * CH; }
+    // device bytes a search of k points with this grid would hold
+    size_t estimate_bytes(int64_t k, const HostGrid& g) const;
+
+  private:
+    static constexpr int64_t DENSE_CAP = (int64_t)1 << 22;   // child scores per scoring launch
+    int score_launch(int mode, const std::vector<Seg>& segs, int64_t work, int64_t dense);
+    int upload_slot(int slot);
+    int release(int slot);
+    template <class T>
+    int slot_get(SearchHost& h, T** p, size_t n);
+
+    cudaStream_t st_;
+    int max_slots_;
+    bool timed_;
+    int64_t nchunks_ = 0;
+    size_t fixed_bytes_ = 0;
+    PoolDev pool_{};
+    SearchDev* d_S_ = nullptr;
+    Ctl* d_ctl_ = nullptr;
+    NodeRec* parents_ = nullptr;
+    int64_t* d_poff_ = nullptr;
+    int32_t* d_slots_ = nullptr;
+    int32_t* dense_ = nullptr;
+    SurvOut surv_{};
+    Ctl* h_ctl_ = nullptr;
+    int64_t* h_poff_ = nullptr;
+    std::vector<void*> fixed_;
+    std::vector<SearchHost> hosts_;
+    std::vector<cudaEvent_t> evs_;
+    double score_ms_ = 0.0;
+    int64_t launches_ = 0, score_launches_ = 0;
+};
+
+}  // namespace bbs

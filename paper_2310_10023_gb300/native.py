@@ -18,6 +18,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libbbs.so")
 
 OK, NOT_FOUND, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EKEYRANGE, ECORRUPT = 0, 1, -1, -2, -3, -4, -5, -6
+ECANCELED, PENDING = -7, 2
 TRANSLATION_ONLY, LEAF_UNDILATED, PRUNE_GE, ANGLE_LOWER_EDGE, CHILD_LITERAL = 0x1, 0x2, 0x4, 0x8, 0x10
 TIME_KERNELS = 0x100
 MAX_LEVELS = 16
@@ -65,6 +66,20 @@ class Result(C.Structure):
         }
 
 
+class ServerOpts(C.Structure):
+    _fields_ = [("mem_budget", C.c_size_t), ("max_active", C.c_int32), ("max_frontier", C.c_int64)]
+
+
+class ServerCounters(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("active", C.c_int64), ("queued", C.c_int64),
+                ("rejected", C.c_int64), ("peak_active", C.c_int64), ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
+                ("throughput_rps", C.c_double), ("probes_per_s", C.c_double), ("mem_in_use", C.c_size_t),
+                ("mem_budget", C.c_size_t)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 EXPORTS = ("bbs_build_maps", "bbs_free_maps", "bbs_maps_bbox", "bbs_maps_info", "bbs_maps_keys",
            "bbs_pose_grid", "bbs_score_batch", "bbs_score_children", "bbs_localize", "bbs_last_error",
            "bbs_version")
@@ -98,6 +113,13 @@ def load():
         L.bbs_version.restype = C.c_char_p
         L.bbs_set_load_factor.argtypes = [C.c_double]
         L.bbs_set_probe_layout.argtypes = [C.c_int]
+        L.bbs_server_create.argtypes = [P(ServerOpts), P(C.c_void_p)]
+        L.bbs_server_submit.argtypes = [vp, vp, vp, i64, P(Ranges), P(Opts), P(C.c_uint64)]
+        L.bbs_server_poll.argtypes = [vp, C.c_uint64, C.c_int, P(Result)]
+        L.bbs_server_cancel.argtypes = [vp, C.c_uint64]
+        L.bbs_server_stats.argtypes = [vp, P(ServerCounters)]
+        L.bbs_server_destroy.argtypes = [vp]
+        L.bbs_server_destroy.restype = None
         L.bbs_bench_gather.argtypes = [C.c_int64, C.c_int64, vp, P(C.c_double)]
         L.bbs_score_batch_noalloc.argtypes = [vp, vp, i64, P(Ranges), P(Opts), vp, i64, vp]
         _lib = L
@@ -346,6 +368,68 @@ def bbs_localize_many(maps: Maps, scans, ranges: Ranges | None = None, opts: Opt
                                     C.byref(opts), res))
     del keep
     return [res[i] for i in range(n)]
+
+
+class Server:
+    """Owning handle of a continuous-batching server (bbs_server_*)."""
+
+    def __init__(self, h):
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().bbs_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+
+def bbs_server_create(mem_budget: int = 0, max_active: int = 0, max_frontier: int = 0) -> Server:
+    o = ServerOpts(int(mem_budget), int(max_active), int(max_frontier))
+    h = C.c_void_p()
+    _check(load().bbs_server_create(C.byref(o), C.byref(h)))
+    return Server(h)
+
+
+def bbs_server_submit(server: Server, maps: Maps, scan, ranges: Ranges | None = None,
+                      opts: Opts | None = None) -> int:
+    p, dev, k, keep = _arr(scan, np.float32, 3)
+    if dev:
+        raise ValueError("bbs_server_submit takes a host scan (it is copied)")
+    t = C.c_uint64()
+    _check(load().bbs_server_submit(server.h, maps.h, p, k, C.byref(ranges) if ranges else None,
+                                    C.byref(opts or make_opts(stream=0)), C.byref(t)))
+    del keep
+    return t.value
+
+
+def bbs_server_poll(server: Server, ticket: int, wait_ms: int = -1):
+    """-> (status, Result or None); status PENDING while queued or running."""
+    res = Result()
+    rc = load().bbs_server_poll(server.h, int(ticket), int(wait_ms), C.byref(res))
+    if rc == PENDING:
+        return rc, None
+    if rc == EINVAL and res.status == 0 and res.num_points == 0:
+        _check(rc)
+    return rc, res
+
+
+def bbs_server_cancel(server: Server, ticket: int) -> None:
+    _check(load().bbs_server_cancel(server.h, int(ticket)))
+
+
+def bbs_server_stats(server: Server) -> dict:
+    c = ServerCounters()
+    _check(load().bbs_server_stats(server.h, C.byref(c)))
+    return c.as_dict()
+
+
+def bbs_server_destroy(server: Server) -> None:
+    server.close()
 
 
 def bbs_set_load_factor(load_factor: float) -> None:

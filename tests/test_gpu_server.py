@@ -1,0 +1,114 @@
+"""The continuous-batching server: requests against two resident maps arrive
+while others run, share launches, and each result equals the same request
+localized alone; admission follows the device-memory budget."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2310_10023_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def nv():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_10023_gb300 import build, native
+    build.build()
+    native.load()
+    return native
+
+
+@pytest.fixture(scope="module")
+def two_maps(nv):
+    out = {}
+    for name in ("room", "indoor"):
+        w = synth.WORKLOADS[name]
+        m = synth.make_map(w.scene)
+        out[name] = (w, nv.bbs_build_maps(m, w.r, w.levels))
+    return out
+
+
+def _args(nv, w):
+    return nv.make_ranges(w.lo, w.hi, w.ang_lo, w.ang_hi), nv.make_opts(score_frac=w.score_frac, batch=w.batch,
+                                                                       stream=0)
+
+
+def _same(a, b):
+    return (a.status, a.best_score, list(a.node), a.iterations, a.nodes_scored) == \
+           (b.status, b.best_score, list(b.node), b.iterations, b.nodes_scored)
+
+
+def test_served_results_equal_alone(nv, two_maps):
+    srv = nv.bbs_server_create(max_active=8, max_frontier=1 << 22)
+    ks = synth.loguniform_sizes(11, 12, 2000, 12000)
+    work = []
+    for i in range(12):
+        name = "room" if i % 3 == 0 else "indoor"
+        w, dm = two_maps[name]
+        s, _ = synth.make_scan(w.scene, 40 + i, k=int(ks[i]) if name == "indoor" else 0)
+        work.append((name, s) + _args(nv, w))
+    reqs = []
+    for name, s, rg, op in work:
+        reqs.append((name, s, rg, op, nv.bbs_server_submit(srv, two_maps[name][1], s, rg, op)))
+        time.sleep(0.0003)                   # arrivals while earlier requests run
+    results = {}
+    while len(results) < len(reqs):
+        for name, s, rg, op, t in reqs:
+            if t in results:
+                continue
+            st, r = nv.bbs_server_poll(srv, t, 0)
+            if st != nv.PENDING:
+                results[t] = r
+        time.sleep(0.0005)
+    stats = nv.bbs_server_stats(srv)
+    srv.close()
+    assert stats["completed"] == len(reqs) and stats["p99_ms"] >= stats["p50_ms"] > 0
+    assert stats["peak_active"] >= 2         # requests really ran together
+    for name, s, rg, op, t in reqs:
+        w, dm = two_maps[name]
+        alone = nv.bbs_localize(dm, s, rg, nv.make_opts(score_frac=w.score_frac, batch=w.batch))
+        assert _same(results[t], alone), name
+
+
+def test_budget_admission_and_rejection(nv, two_maps):
+    w, dm = two_maps["indoor"]
+    rg, op = _args(nv, w)
+    s, _ = synth.make_scan(2, 3)
+    # budget: the pool plus room for about one indoor search at a time
+    probe = nv.bbs_server_create(mem_budget=1 << 40, max_active=4, max_frontier=1 << 20)
+    fixed = nv.bbs_server_stats(probe)["mem_in_use"]
+    probe.close()
+    srv = nv.bbs_server_create(mem_budget=fixed + (120 << 20), max_active=4, max_frontier=1 << 20)
+    tickets = [nv.bbs_server_submit(srv, dm, s, rg, op) for _ in range(3)]
+    saw_queue = nv.bbs_server_stats(srv)["queued"] > 0
+    res = [nv.bbs_server_poll(srv, t, -1) for t in tickets]
+    assert all(st == nv.OK for st, _ in res)
+    assert len({(r.best_score, tuple(r.node)) for _, r in res}) == 1
+    assert saw_queue or nv.bbs_server_stats(srv)["completed"] == 3
+    # a request that can never fit fails at once: three times the range gives
+    # about 27 times the rotations (Eq. (2)), far beyond the budget
+    big = (s * np.float32(3.0)).astype(np.float32)
+    t = nv.bbs_server_submit(srv, dm, big, rg, op)
+    st, r = nv.bbs_server_poll(srv, t, 10000)
+    assert st == nv.ENOMEM
+    srv.close()
+
+
+def test_cancel_queued(nv, two_maps):
+    w, dm = two_maps["indoor"]
+    rg, op = _args(nv, w)
+    srv = nv.bbs_server_create(max_active=1, max_frontier=1 << 21)
+    scans = [synth.make_scan(2, 60 + i)[0] for i in range(4)]
+    tickets = [nv.bbs_server_submit(srv, dm, s, rg, op) for s in scans]
+    nv.bbs_server_cancel(srv, tickets[-1])           # still queued behind the others
+    st, r = nv.bbs_server_poll(srv, tickets[-1], -1)
+    assert st == nv.ECANCELED
+    for t in tickets[:-1]:
+        st, r = nv.bbs_server_poll(srv, t, -1)
+        assert st in (nv.OK, nv.NOT_FOUND)
+    srv.close()
