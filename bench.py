@@ -26,6 +26,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -42,6 +44,7 @@ def _args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--scans", type=int, default=8, help="distinct scans cycled by the steps")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-forms", action="store_true", help="skip the batched and served forms")
     return p.parse_args()
 
 
@@ -194,6 +197,90 @@ def run_reference(a):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def run_batched(nv, torch, maps, w, stream, n=64, seed=4):
+    """64 indoor scans (K log-uniform in [2k, 30k]) localized in one
+    bbs_localize_many call vs the same scans one bbs_localize at a time."""
+    from paper_2310_10023_gb300 import synth
+    ks = synth.loguniform_sizes(seed, n, 2000, 30000)
+    scans = [torch.from_numpy(synth.make_scan(w.scene, 500 + i, k=int(k))[0]).cuda() for i, k in enumerate(ks)]
+    a = nv.workload_args(w, stream=stream.cuda_stream)
+    nv.bbs_localize_many(maps, scans[:8], a.ranges, a.opts)
+    for s_ in scans[:4]:
+        nv.bbs_localize(maps, s_, a.ranges, a.opts)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    many = nv.bbs_localize_many(maps, scans, a.ranges, a.opts)
+    e1.record(stream)
+    e1.synchronize()
+    t_many = e0.elapsed_time(e1)
+    e0.record(stream)
+    plain = [nv.bbs_localize(maps, s_, a.ranges, a.opts) for s_ in scans]
+    e1.record(stream)
+    e1.synchronize()
+    t_plain = e0.elapsed_time(e1)
+    pm = sum(r.probes for r in many)
+    same = sum((r.best_score, list(r.node)) == (q.best_score, list(q.node)) for r, q in zip(many, plain))
+    return {"workload": f"{n} indoor scans, K log-uniform 2k-30k (mean {statistics.mean(int(k) for k in ks):.0f})",
+            "probes_per_s": pm / (t_many / 1e3), "plain_probes_per_s": pm / (t_plain / 1e3),
+            "speedup_vs_plain": t_plain / t_many, "wall_ms": t_many, "plain_wall_ms": t_plain,
+            "ms_to_optimum_mean": statistics.mean(r.ms_to_optimum for r in many),
+            "plain_ms_to_optimum_mean": statistics.mean(r.ms_to_optimum for r in plain),
+            "found": sum(r.status == nv.OK for r in many), "results_equal_plain": f"{same}/{n}"}
+
+
+def run_served(nv, torch, lam=200.0, n=64, seed=9):
+    """Poisson arrivals (rate lam) of requests with 2k-30k-point scans against
+    two resident maps (room and indoor), served by the continuous-batching
+    server, vs one-at-a-time plain BnB on the same arrival trace (FIFO)."""
+    from paper_2310_10023_gb300 import synth
+    maps = {}
+    for name in ("room", "indoor"):
+        w = synth.WORKLOADS[name]
+        maps[name] = (w, nv.bbs_build_maps(torch.from_numpy(np.array(synth.make_map(w.scene))).cuda(), w.r, w.levels))
+    arr, ks = synth.poisson_trace(seed, lam, n, 2000, 30000)
+    reqs = []
+    for i in range(n):
+        name = "room" if i % 2 == 0 else "indoor"
+        w, dm = maps[name]
+        s = synth.make_scan(w.scene, 900 + i, k=int(ks[i]))[0]
+        a = nv.workload_args(w, stream=0)
+        reqs.append((dm, s, a.ranges, a.opts))
+    # one-at-a-time service times (device synchronized per request)
+    torch.cuda.synchronize()
+    for dm, s, rg, op in reqs[:4]:
+        nv.bbs_localize(dm, s, rg, op)
+    svc = []
+    for dm, s, rg, op in reqs:
+        t = time.perf_counter()
+        nv.bbs_localize(dm, s, rg, op)
+        svc.append((time.perf_counter() - t) * 1e3)
+    fifo, free_at = [], 0.0
+    for t_arr, d in zip(arr * 1e3, svc):
+        start = max(t_arr, free_at)
+        free_at = start + d
+        fifo.append(free_at - t_arr)
+    srv = nv.bbs_server_create(max_active=32)
+    tickets = []
+    t0 = time.perf_counter()
+    for (dm, s, rg, op), t_arr in zip(reqs, arr):
+        while time.perf_counter() - t0 < t_arr:
+            pass
+        tickets.append(nv.bbs_server_submit(srv, dm, s, rg, op))
+    out = [nv.bbs_server_poll(srv, t, -1) for t in tickets]
+    st = nv.bbs_server_stats(srv)
+    srv.close()
+    q = sorted(fifo)
+    pct = lambda v, p: v[min(len(v) - 1, int(round(p * (len(v) - 1))))]
+    return {"workload": f"{n} requests, Poisson {lam:.0f}/s, K log-uniform 2k-30k, maps room + indoor resident",
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "throughput_rps": st["throughput_rps"],
+            "probes_per_s": st["probes_per_s"], "peak_active": st["peak_active"],
+            "found": sum(o[0] == nv.OK for o in out),
+            "plain_fifo_p50_ms": pct(q, 0.5), "plain_fifo_p99_ms": pct(q, 0.99),
+            "plain_throughput_rps": n / (max(free_at, arr[-1] * 1e3) / 1e3),
+            "plain_mean_service_ms": statistics.mean(svc)}
+
+
 def _kernel_hash():
     h = hashlib.sha256()
     for f in ("score.cu", "bbs_internal.cuh", "branch.cuh"):
@@ -337,6 +424,10 @@ def run_ours(a):
         vals = torch.cat([mx, sm])
     total_ms, e2e_total, probes_all, e2e_probes_all = vals.tolist()
 
+    batched = served = None
+    if rank == 0 and ws == 1 and not a.no_forms:
+        batched = run_batched(nv, torch, maps, w, stream)
+        served = run_served(nv, torch)
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         rate, n, dt = cpu_probe_rate(w, m, scans[0])
@@ -366,6 +457,8 @@ def run_ours(a):
                           "note": "32 B per unit vs random 32-byte gathers over a "
                                   f"{max(table_bytes, 1 << 22) >> 20} MiB L2-resident table (bbs_bench_gather, "
                                   "this run); L1 hits let the kernel exceed the random-gather plateau"},
+            "batched": batched,
+            "served": served,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_probes_all / (e2e_total / 1e3), "unit": "probes/s",
                     "h2d_bytes_per_step": h2d // a.steps, "d2h_bytes_per_step": d2h // a.steps},

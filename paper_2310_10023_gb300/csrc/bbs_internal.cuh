@@ -66,7 +66,10 @@ __host__ __device__ __forceinline__ uint32_t cbrick_hash(uint32_t key) { return 
 __device__ __forceinline__ bool probe_compact(const LevelView& L, uint32_t key, int h, uint4& w)
 {
     const uint32_t s = cbrick_hash(key) >> L.shift;
-    for (int p = 0; p <= L.maxp; ++p) {
+    w = __ldg(reinterpret_cast<const uint4*>(L.slots + s) + h);   // the home bucket: almost every probe ends here
+    if (w.x == key) return true;
+    if (w.x == CEMPTY) return false;
+    for (int p = 1; p <= L.maxp; ++p) {
         const uint4* q = reinterpret_cast<const uint4*>(L.slots + ((s + (uint32_t)p) & L.mask)) + h;
         w = __ldg(q);
         if (w.x == key) return true;

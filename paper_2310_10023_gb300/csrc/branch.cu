@@ -83,32 +83,33 @@ __device__ __forceinline__ void child_bits(const LevelView& L, int32_t kx, int32
     }
 }
 
-// One task (rotational child) over the staged points: two points per step.
-// The exact floor of q is the bit pattern of fl_rd(q + 1.5 * 2^23) minus that
-// of 1.5 * 2^23 (valid for |q| < 2^22); that offset is a multiple of 2^22, so
-// the level shift can be applied to the raw bit pattern and the offset (and
-// the translation, and the compact origin) folded into one per-axis constant.
+// One task (rotational child) over the staged points, two points per step.
+// The chunk is staged as pairs: sxy[j] = (x_2j, x_2j+1, y_2j, y_2j+1) and
+// sz[j] = (z_2j, z_2j+1), so each coordinate pair is one 64-bit register for
+// the f32x2 operations.  The exact floor of q is the bit pattern of
+// fl_rd(q + 1.5 * 2^23) minus that of 1.5 * 2^23 (valid for |q| < 2^22); that
+// offset is a multiple of 2^22, so the level shift applies to the raw bit
+// pattern and the offset, the translation and the compact origin fold into
+// one per-axis constant.
 template <bool COMPACT>
-__device__ __forceinline__ void score_task(const float4* sp, int n, const LevelView& L, int m, const Row2& r0,
-                                           const Row2& r1, const Row2& r2, int32_t cx, int32_t cy, int32_t cz,
-                                           uint32_t& acc0, uint32_t& acc1)
+__device__ __forceinline__ void score_task(const ulonglong2* sxy, const f2* sz, int n, const LevelView& L, int m,
+                                           const Row2& r0, const Row2& r1, const Row2& r2, int32_t cx, int32_t cy,
+                                           int32_t cz, uint32_t& acc0, uint32_t& acc1)
 {
     const f2 C = pk2(12582912.0f, 12582912.0f);
-    const int nt = blockDim.x;
-    for (int i = threadIdx.x; i < n; i += 2 * nt) {
-        const bool v2 = i + nt < n;
-        const float4 s1 = sp[i];
-        const float4 s2 = v2 ? sp[i + nt] : s1;
-        const f2 X = pk2(s1.x, s2.x), Y = pk2(s1.y, s2.y), Z = pk2(s1.z, s2.z);
+    const int np = (n + 1) >> 1;
+    for (int j = threadIdx.x; j < np; j += blockDim.x) {
+        const ulonglong2 xy = sxy[j];
+        const f2 Z = sz[j];
         int32_t bx1, bx2, by1, by2, bz1, bz2;
-        up2(add2rm(rot2(r0, X, Y, Z), C), bx1, bx2);
-        up2(add2rm(rot2(r1, X, Y, Z), C), by1, by2);
-        up2(add2rm(rot2(r2, X, Y, Z), C), bz1, bz2);
+        up2(add2rm(rot2(r0, xy.x, xy.y, Z), C), bx1, bx2);
+        up2(add2rm(rot2(r1, xy.x, xy.y, Z), C), by1, by2);
+        up2(add2rm(rot2(r2, xy.x, xy.y, Z), C), bz1, bz2);
         uint32_t w0, w1;
         child_bits<COMPACT>(L, (bx1 >> m) + cx, (by1 >> m) + cy, (bz1 >> m) + cz, w0, w1);
         acc0 += spread4(w0);
         acc1 += spread4(w1);
-        if (v2) {
+        if (2 * j + 1 < n) {
             child_bits<COMPACT>(L, (bx2 >> m) + cx, (by2 >> m) + cy, (bz2 >> m) + cz, w0, w1);
             acc0 += spread4(w0);
             acc1 += spread4(w1);
@@ -154,12 +155,17 @@ __device__ __forceinline__ void parent_ranges(const DevGrid& g, int l, uint32_t 
 
 }  // namespace
 
+constexpr int TB = 64;   // tasks reduced per barrier round
+
 template <int MODE>
-__global__ void __launch_bounds__(256) branch2_kernel(const __grid_constant__ BranchLaunch L)
+__global__ void __launch_bounds__(256, 5) branch2_kernel(const __grid_constant__ BranchLaunch L)
 {
-    __shared__ float4 sp[PCHUNK];
-    __shared__ uint32_t red[2][8][4];
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    __shared__ ulonglong2 sxy[PCHUNK / 2];
+    __shared__ f2 sz[PCHUNK / 2];
+    __shared__ uint32_t red[TB][4];
+    const int tid = threadIdx.x, lane = tid & 31;
+    float* fxy = reinterpret_cast<float*>(sxy);
+    float* fz = reinterpret_cast<float*>(sz);
     for (int64_t w = blockIdx.x; w < L.n_work; w += gridDim.x) {
         const Seg& g = L.seg[find_seg(L, w)];
         const SearchDev& S = L.S[g.sid];
@@ -167,8 +173,14 @@ __global__ void __launch_bounds__(256) branch2_kernel(const __grid_constant__ Br
         const int64_t pi = local / g.chunks;
         const int32_t k0 = (int32_t)(local - pi * g.chunks) * PCHUNK;
         const int32_t n = min(PCHUNK, S.K - k0);
-        __syncthreads();   // the previous item's readers of sp are done
-        for (int i = tid; i < n; i += blockDim.x) sp[i] = __ldg(S.scan + k0 + i);
+        __syncthreads();   // the previous item's readers of the staged points are done
+        for (int i = tid; i < n; i += blockDim.x) {
+            const float4 p = __ldg(S.scan + k0 + i);
+            const int j = i >> 1, h = i & 1;
+            fxy[4 * j + h] = p.x;
+            fxy[4 * j + 2 + h] = p.y;
+            fz[2 * j + h] = p.z;
+        }
         int m, T;
         int32_t tx, ty, tz;
         int32_t lo[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
@@ -192,55 +204,59 @@ __global__ void __launch_bounds__(256) branch2_kernel(const __grid_constant__ Br
             ty = 2 * par.cy;
             tz = 2 * par.cz;
         }
-        __syncthreads();   // sp is staged
-        if (m < 0) continue;
+        if (m < 0) continue;   // uniform: a leaf has no children (staging reads nothing more)
         const LevelView Lv = S.maps[m];
         const int64_t roff = S.grid.rot_off[m];
         const int32_t Nb = S.grid.N[m][1], Ng = S.grid.N[m][2];
-        for (int t = 0; t < T; ++t) {
-            uint32_t crot;
-            if (MODE == MODE_INITIAL) {
-                crot = (uint32_t)t;
-            } else {
-                const int32_t ja = t / (ext[1] * ext[2]), jb = (t / ext[2]) % ext[1], jg = t % ext[2];
-                crot = (uint32_t)(((int64_t)(lo[0] + ja) * Nb + (lo[1] + jb)) * Ng + (lo[2] + jg));
+        const int32_t off = 0x4B400000 >> m;   // the floor offset after the level shift
+        for (int t0 = 0; t0 < T; t0 += TB) {
+            const int tb = min(TB, T - t0);
+            for (int i = tid; i < 4 * TB; i += blockDim.x) (&red[0][0])[i] = 0u;
+            __syncthreads();   // staged points and zeroed partials visible
+            for (int tt = 0; tt < tb; ++tt) {
+                const int t = t0 + tt;
+                uint32_t crot;
+                if (MODE == MODE_INITIAL) {
+                    crot = (uint32_t)t;
+                } else {
+                    const int32_t ja = t / (ext[1] * ext[2]), jb = (t / ext[2]) % ext[1], jg = t % ext[2];
+                    crot = (uint32_t)(((int64_t)(lo[0] + ja) * Nb + (lo[1] + jb)) * Ng + (lo[2] + jg));
+                }
+                const float4* A = S.rot + 3 * (roff + (int64_t)crot);
+                const float4 a0 = __ldg(A), a1 = __ldg(A + 1), a2 = __ldg(A + 2);
+                const Row2 r0{pk2(a0.x, a0.x), pk2(a0.y, a0.y), pk2(a0.z, a0.z)};
+                const Row2 r1{pk2(a1.x, a1.x), pk2(a1.y, a1.y), pk2(a1.z, a1.z)};
+                const Row2 r2{pk2(a2.x, a2.x), pk2(a2.y, a2.y), pk2(a2.z, a2.z)};
+                uint32_t acc0 = 0, acc1 = 0;   // bytes: children (0,4,2,6) and (1,5,3,7)
+                if (Lv.compact)
+                    score_task<true>(sxy, sz, n, Lv, m, r0, r1, r2, tx - off - Lv.base[0], ty - off - Lv.base[1],
+                                     tz - off - Lv.base[2], acc0, acc1);
+                else
+                    score_task<false>(sxy, sz, n, Lv, m, r0, r1, r2, tx - off, ty - off, tz - off, acc0, acc1);
+                // 16-bit fields: at most 8 points per thread x 32 lanes, x 8 warps, per field
+                uint32_t e0 = acc0 & 0x00FF00FFu, o0 = (acc0 >> 8) & 0x00FF00FFu;
+                uint32_t e1 = acc1 & 0x00FF00FFu, o1 = (acc1 >> 8) & 0x00FF00FFu;
+                e0 = __reduce_add_sync(0xffffffffu, e0);
+                o0 = __reduce_add_sync(0xffffffffu, o0);
+                e1 = __reduce_add_sync(0xffffffffu, e1);
+                o1 = __reduce_add_sync(0xffffffffu, o1);
+                if (lane == 0) {
+                    atomicAdd(&red[tt][0], e0);
+                    atomicAdd(&red[tt][1], o0);
+                    atomicAdd(&red[tt][2], e1);
+                    atomicAdd(&red[tt][3], o1);
+                }
             }
-            const float4* A = S.rot + 3 * (roff + (int64_t)crot);
-            const float4 a0 = __ldg(A), a1 = __ldg(A + 1), a2 = __ldg(A + 2);
-            const Row2 r0{pk2(a0.x, a0.x), pk2(a0.y, a0.y), pk2(a0.z, a0.z)};
-            const Row2 r1{pk2(a1.x, a1.x), pk2(a1.y, a1.y), pk2(a1.z, a1.z)};
-            const Row2 r2{pk2(a2.x, a2.x), pk2(a2.y, a2.y), pk2(a2.z, a2.z)};
-            const int32_t off = 0x4B400000 >> m;   // the floor offset after the level shift
-            uint32_t acc0 = 0, acc1 = 0;   // bytes: children (0,4,2,6) and (1,5,3,7)
-            if (Lv.compact)
-                score_task<true>(sp, n, Lv, m, r0, r1, r2, tx - off - Lv.base[0], ty - off - Lv.base[1],
-                                 tz - off - Lv.base[2], acc0, acc1);
-            else
-                score_task<false>(sp, n, Lv, m, r0, r1, r2, tx - off, ty - off, tz - off, acc0, acc1);
-            // 16-bit fields: at most 8 points per thread x 32 lanes per field
-            uint32_t e0 = acc0 & 0x00FF00FFu, o0 = (acc0 >> 8) & 0x00FF00FFu;
-            uint32_t e1 = acc1 & 0x00FF00FFu, o1 = (acc1 >> 8) & 0x00FF00FFu;
-            e0 = __reduce_add_sync(0xffffffffu, e0);
-            o0 = __reduce_add_sync(0xffffffffu, o0);
-            e1 = __reduce_add_sync(0xffffffffu, e1);
-            o1 = __reduce_add_sync(0xffffffffu, o1);
-            const int b = t & 1;
-            if (lane == 0) {
-                red[b][wid][0] = e0;
-                red[b][wid][1] = o0;
-                red[b][wid][2] = e1;
-                red[b][wid][3] = o1;
-            }
-            __syncthreads();
-            if (tid < 8) {
-                // child j = 4 jx + 2 jy + jz: word (jz ? 2 : 0) + jx, half jy
-                const int jx = tid >> 2, jy = (tid >> 1) & 1, jz = tid & 1;
-                const int word = (jz ? 2 : 0) + jx;
-                uint32_t sum = 0;
-                for (int v = 0; v < (int)(blockDim.x >> 5); ++v) sum += red[b][v][word];
+            __syncthreads();   // every warp's partial sums are in
+            for (int i = tid; i < 8 * tb; i += blockDim.x) {
+                // child j = 4 jx + 2 jy + jz of task tt: word (jz ? 2 : 0) + jx, half jy
+                const int tt = i >> 3, j = i & 7;
+                const int jx = j >> 2, jy = (j >> 1) & 1, jz = j & 1;
+                const uint32_t sum = red[tt][(jz ? 2 : 0) + jx];
                 const uint32_t cnt = jy ? (sum >> 16) : (sum & 0xFFFFu);
-                if (cnt) atomicAdd(&L.dense[g.dense_base + (pi * g.R + t) * 8 + tid], (int32_t)cnt);
+                if (cnt) atomicAdd(&L.dense[g.dense_base + (pi * g.R + t0 + tt) * 8 + j], (int32_t)cnt);
             }
+            __syncthreads();   // the partials are read before the next round zeroes them
         }
     }
 }

@@ -21,6 +21,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <type_traits>
 #include <vector>
 
@@ -126,9 +127,11 @@ __global__ void __launch_bounds__(1024) alloc_kernel(SearchDev* S, int nslots, P
         SearchDev& f = S[si];
         Ctl* c = f.ctl;
         if (!c->active || c->err) continue;
+        // survivors score above best: only those buckets can have new nodes
+        const int lo = c->best + 1 > 0 ? c->best + 1 : 0;
         // pass 1: chunks needed by this search, claimed from the shared stack
         int64_t need_sum = 0;
-        for (int s = threadIdx.x; s <= f.K; s += blockDim.x) {
+        for (int s = lo + (int)threadIdx.x; s <= f.K; s += blockDim.x) {
             const uint32_t h = f.h_cnt[s];
             if (!h) continue;
             const int32_t tail = f.b_tail[s];
@@ -156,7 +159,7 @@ __global__ void __launch_bounds__(1024) alloc_kernel(SearchDev* S, int nslots, P
         // pass 2: hand out the claimed chunks bucket by bucket
         int64_t carry = 0, added = 0;
         int top = -1;
-        for (int base = 0; base <= f.K; base += blockDim.x) {
+        for (int base = lo; base <= f.K; base += blockDim.x) {
             const int s = base + threadIdx.x;
             uint32_t h = 0;
             int32_t tail = -1, fill0 = CH, space = 0;
@@ -520,6 +523,20 @@ int Engine::init()
     pool_init_kernel<<<(int)std::min<int64_t>((nchunks_ + 255) / 256, 4096), 256, 0, st_>>>(pool_);
     launches_ += 1;
     BBS_CUDA_TRY(cudaGetLastError());
+    return BBS_OK;
+}
+
+int Engine::begin_run(cudaStream_t st, bool timed)
+{
+    st_ = st;
+    timed_ = timed;
+    score_ms_ = 0.0;
+    launches_ = 0;
+    score_launches_ = 0;
+    for (cudaEvent_t e : evs_) cudaEventDestroy(e);
+    evs_.clear();
+    BBS_CUDA_TRY(cudaMemsetAsync(surv_.err, 0, sizeof(int), st_));
+    BBS_CUDA_TRY(cudaMemsetAsync(surv_.count, 0, sizeof(unsigned long long), st_));
     return BBS_OK;
 }
 
@@ -951,6 +968,68 @@ int Engine::score_launch(int mode, const std::vector<Seg>& segs, int64_t work, i
 }
 
 // ---- the one-shot entry points ------------------------------------------------------
+//
+// Engines (their chunk pool and staging buffers, hundreds of MB) are kept per
+// device and reused by later calls: a finished run leaves the pool full and
+// every slot released.  A call takes an idle engine with enough slots and pool
+// or builds one; at most four idle engines per device are kept.
+
+namespace {
+
+struct CachedEngine {
+    int device;
+    int slots;
+    int64_t pool_nodes;
+    Engine* e;
+    bool busy;
+};
+
+std::mutex g_engine_mu;
+std::vector<CachedEngine> g_engines;
+
+Engine* acquire_engine(int slots, int64_t pool_nodes, cudaStream_t st, bool timed, int* rc)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lock(g_engine_mu);
+        for (auto& c : g_engines)
+            if (!c.busy && c.device == dev && c.slots >= slots && c.pool_nodes >= pool_nodes &&
+                c.pool_nodes <= 4 * pool_nodes + ((int64_t)1 << 22) && c.slots <= 4 * slots + 16) {
+                c.busy = true;
+                *rc = c.e->begin_run(st, timed);
+                return c.e;
+            }
+    }
+    Engine* e = new Engine(st, slots, pool_nodes, timed);
+    *rc = e->init();
+    if (*rc < 0) {
+        delete e;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(g_engine_mu);
+    g_engines.push_back(CachedEngine{dev, slots, pool_nodes, e, true});
+    return e;
+}
+
+void release_engine(Engine* e, bool healthy)
+{
+    std::lock_guard<std::mutex> lock(g_engine_mu);
+    for (size_t i = 0; i < g_engines.size(); ++i)
+        if (g_engines[i].e == e) {
+            int idle = 0;
+            for (auto& c : g_engines) idle += (!c.busy && c.device == g_engines[i].device) ? 1 : 0;
+            if (!healthy || idle >= 4) {
+                delete e;
+                g_engines.erase(g_engines.begin() + (long)i);
+            } else {
+                g_engines[i].busy = false;
+            }
+            return;
+        }
+}
+
+}  // namespace
 
 int search_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device, const bbs_ranges* rg,
                const bbs_opts* opts, cudaStream_t st, bbs_result* res)
@@ -959,18 +1038,20 @@ int search_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device, co
     const bool timed = opts && (opts->flags & BBS_TIME_KERNELS);
     const int64_t pool_nodes = max_frontier + (int64_t)CH * std::min<int64_t>(k + 1, 8192);
     std::memset(res, 0, sizeof(*res));
-    Engine E(st, 1, pool_nodes, timed);
-    BBS_TRY(E.init());
+    int rc = BBS_OK;
+    Engine* E = acquire_engine(1, pool_nodes, st, timed, &rc);
+    if (!E) return rc;
     int slot = -1;
-    BBS_TRY(E.add(m, xyz, k, is_device, rg, opts, 0, &slot));
-    BBS_TRY(E.start());
+    if (rc == BBS_OK) rc = E->add(m, xyz, k, is_device, rg, opts, 0, &slot);
+    if (rc == BBS_OK) rc = E->start();
     std::vector<int> fin;
-    while (E.used_count() > 0) {
+    while (rc == BBS_OK && E->used_count() > 0) {
         fin.clear();
-        BBS_TRY(E.step(&fin));
-        for (int i : fin) E.finalize(i, res);
+        rc = E->step(&fin);
+        for (int i : fin) E->finalize(i, res);
     }
-    return res->status;
+    release_engine(E, rc == BBS_OK);
+    return rc == BBS_OK ? res->status : rc;
 }
 
 int search_run_many(const bbs_maps* m, int n, const float* const* scans, const int64_t* ks, int is_device,
@@ -981,21 +1062,23 @@ int search_run_many(const bbs_maps* m, int n, const float* const* scans, const i
     int64_t kmax = 1;
     for (int i = 0; i < n; ++i) kmax = std::max(kmax, ks[i]);
     const int64_t pool_nodes = max_frontier + (int64_t)CH * std::min<int64_t>((kmax + 1) * n, 8192 * (int64_t)n);
-    Engine E(st, n, pool_nodes, timed);
-    BBS_TRY(E.init());
+    int rc = BBS_OK;
+    Engine* E = acquire_engine(n, pool_nodes, st, timed, &rc);
+    if (!E) return rc;
     std::vector<int> slot_of((size_t)n, -1);
-    for (int i = 0; i < n; ++i) {
+    for (int i = 0; i < n && rc == BBS_OK; ++i) {
         std::memset(&res[i], 0, sizeof(res[i]));
-        BBS_TRY(E.add(m, scans[i], ks[i], is_device, rg, opts, (uint64_t)i, &slot_of[(size_t)i]));
+        rc = E->add(m, scans[i], ks[i], is_device, rg, opts, (uint64_t)i, &slot_of[(size_t)i]);
     }
-    BBS_TRY(E.start());
+    if (rc == BBS_OK) rc = E->start();
     std::vector<int> fin;
-    while (E.used_count() > 0) {
+    while (rc == BBS_OK && E->used_count() > 0) {
         fin.clear();
-        BBS_TRY(E.step(&fin));
-        for (int s : fin) E.finalize(s, &res[E.tag(s)]);
+        rc = E->step(&fin);
+        for (int s_ : fin) E->finalize(s_, &res[E->tag(s_)]);
     }
-    return BBS_OK;
+    release_engine(E, rc == BBS_OK);
+    return rc;
 }
 
 }  // namespace bbs

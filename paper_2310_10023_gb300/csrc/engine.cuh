@@ -45,6 +45,8 @@ class Engine {
     Engine& operator=(const Engine&) = delete;
 
     int init();
+    // reuse for a new run on `st` (the previous run has completed)
+    int begin_run(cudaStream_t st, bool timed);
     // a new search in a free slot; *slot receives its index
     int add(const bbs_maps* m, const float* xyz, int64_t k, int is_device, const bbs_ranges* rg, const bbs_opts* opts,
             uint64_t tag, int* slot);

@@ -276,8 +276,8 @@ int scan_prepare(const bbs_maps* m, const float* xyz, int64_t k, int is_device, 
     rotation_table_kernel<<<grid_blocks(g.total_rot, 256), 256, 0, st>>>(d_cs, dev_grid(g), d_off, g.total_rot,
                                                                           (double)m->r, out->rot);
     BBS_CUDA_TRY(cudaGetLastError());
-    // host vectors must outlive the asynchronous copies
-    BBS_CUDA_TRY(cudaStreamSynchronize(st));
+    // the host vectors may go: a copy from pageable memory has staged its
+    // source by the time cudaMemcpyAsync returns
     cudaFreeAsync(d_cs, st);
     cudaFreeAsync(d_off, st);
     return BBS_OK;
