@@ -71,6 +71,10 @@ extern "C" {
 /* time every launch of the scoring kernel with CUDA events on the call's
  * stream (bbs_result.score_ms); off by default */
 #define BBS_TIME_KERNELS      0x100u
+/* drive every search iteration from the host (one synchronization per
+ * iteration) instead of the device-side loop of a captured CUDA graph;
+ * results are identical, only the overhead differs */
+#define BBS_HOST_DRIVEN       0x200u
 
 #define BBS_MAX_LEVELS 16
 

@@ -117,23 +117,23 @@ __device__ __forceinline__ void score_task(const ulonglong2* sxy, const f2* sz, 
     }
 }
 
-__device__ __forceinline__ int find_seg(const BranchLaunch& L, int64_t w)
+__device__ __forceinline__ int find_seg(const Plan* P, int64_t w)
 {
-    int lo = 0, hi = L.nseg - 1;
+    int lo = 0, hi = P->nseg - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (L.seg[mid].first_work <= w) lo = mid;
+        if (P->seg[mid].first_work <= w) lo = mid;
         else hi = mid - 1;
     }
     return lo;
 }
 
-__device__ __forceinline__ int find_dense_seg(const BranchLaunch& L, int64_t d)
+__device__ __forceinline__ int find_dense_seg(const Plan* P, int64_t d)
 {
-    int lo = 0, hi = L.nseg - 1;
+    int lo = 0, hi = P->nseg - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (L.seg[mid].dense_base <= d) lo = mid;
+        if (P->seg[mid].dense_base <= d) lo = mid;
         else hi = mid - 1;
     }
     return lo;
@@ -158,17 +158,20 @@ __device__ __forceinline__ void parent_ranges(const DevGrid& g, int l, uint32_t 
 constexpr int TB = 64;   // tasks reduced per barrier round
 
 template <int MODE>
-__global__ void __launch_bounds__(256, 5) branch2_kernel(const __grid_constant__ BranchLaunch L)
+__global__ void __launch_bounds__(256, 5) branch2_kernel(const Plan* __restrict__ P, const SearchDev* __restrict__ Sall,
+                                                         const NodeRec* __restrict__ parents, int32_t* dense)
 {
+    if (P->status != PLAN_OK) return;
+    const int64_t n_work = P->n_work;
     __shared__ ulonglong2 sxy[PCHUNK / 2];
     __shared__ f2 sz[PCHUNK / 2];
     __shared__ uint32_t red[TB][4];
     const int tid = threadIdx.x, lane = tid & 31;
     float* fxy = reinterpret_cast<float*>(sxy);
     float* fz = reinterpret_cast<float*>(sz);
-    for (int64_t w = blockIdx.x; w < L.n_work; w += gridDim.x) {
-        const Seg& g = L.seg[find_seg(L, w)];
-        const SearchDev& S = L.S[g.sid];
+    for (int64_t w = blockIdx.x; w < n_work; w += gridDim.x) {
+        const Seg g = P->seg[find_seg(P, w)];
+        const SearchDev& S = Sall[g.sid];
         const int64_t local = w - g.first_work;
         const int64_t pi = local / g.chunks;
         const int32_t k0 = (int32_t)(local - pi * g.chunks) * PCHUNK;
@@ -195,7 +198,7 @@ __global__ void __launch_bounds__(256, 5) branch2_kernel(const __grid_constant__
             m = S.lmax;
             T = S.grid.N[m][0] * S.grid.N[m][1] * S.grid.N[m][2];
         } else {
-            const NodeRec par = L.parents[g.first_parent + pi];
+            const NodeRec par = parents[g.first_parent + pi];
             const int l = rl_level(par.rl);
             m = l - 1;
             parent_ranges(S.grid, l, rl_rot(par.rl), lo, ext);
@@ -254,7 +257,7 @@ __global__ void __launch_bounds__(256, 5) branch2_kernel(const __grid_constant__
                 const int jx = j >> 2, jy = (j >> 1) & 1, jz = j & 1;
                 const uint32_t sum = red[tt][(jz ? 2 : 0) + jx];
                 const uint32_t cnt = jy ? (sum >> 16) : (sum & 0xFFFFu);
-                if (cnt) atomicAdd(&L.dense[g.dense_base + (pi * g.R + t0 + tt) * 8 + j], (int32_t)cnt);
+                if (cnt) atomicAdd(&dense[g.dense_base + (pi * g.R + t0 + tt) * 8 + j], (int32_t)cnt);
             }
             __syncthreads();   // the partials are read before the next round zeroes them
         }
@@ -264,12 +267,14 @@ __global__ void __launch_bounds__(256, 5) branch2_kernel(const __grid_constant__
 // survivors: children scoring above their search's best, staged with per-score
 // histograms (count, children, leaves) for the frontier insertion
 template <int MODE>
-__global__ void __launch_bounds__(256) finalize_kernel(const __grid_constant__ BranchLaunch L, SearchDev* S,
-                                                       SurvOut out)
+__global__ void __launch_bounds__(256) finalize_kernel(const Plan* __restrict__ P, SearchDev* S,
+                                                       const NodeRec* __restrict__ parents, int32_t* dense, SurvOut out)
 {
+    if (P->status != PLAN_OK) return;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t n_round = (L.n_dense + 31) & ~(int64_t)31;
+    const int64_t n_dense = P->n_dense;
+    const int64_t n_round = (n_dense + 31) & ~(int64_t)31;
     for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < n_round; d += stride) {
         bool surv = false;
         int32_t score = 0, sid = 0;
@@ -278,8 +283,8 @@ __global__ void __launch_bounds__(256) finalize_kernel(const __grid_constant__ B
         nd.rl = 0;
         int m = 0;
         uint32_t crot = 0;
-        if (d < L.n_dense) {
-            const Seg& g = L.seg[find_dense_seg(L, d)];
+        if (d < n_dense) {
+            const Seg g = P->seg[find_dense_seg(P, d)];
             sid = g.sid;
             const SearchDev& s = S[sid];
             const int64_t local = d - g.dense_base;
@@ -302,7 +307,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(const __grid_constant__ B
                 m = s.lmax;
                 crot = (uint32_t)t;
             } else if (valid) {
-                const NodeRec par = L.parents[g.first_parent + pi];
+                const NodeRec par = parents[g.first_parent + pi];
                 const int l = rl_level(par.rl);
                 m = l - 1;
                 int32_t lo[3], ext[3];
@@ -317,8 +322,11 @@ __global__ void __launch_bounds__(256) finalize_kernel(const __grid_constant__ B
                     tz = 2 * par.cz + (j & 1);
                 }
             }
+            // the dense array must be zero for the next round: consume it
+            const int32_t dv = dense[d];
+            if (dv) dense[d] = 0;
             if (valid) {
-                score = L.dense[d];
+                score = dv;
                 surv = score > s.ctl->best;
                 nd.cx = tx;
                 nd.cy = ty;
@@ -350,22 +358,21 @@ __global__ void __launch_bounds__(256) finalize_kernel(const __grid_constant__ B
     }
 }
 
-cudaError_t launch_branch(const BranchLaunch& L, cudaStream_t st)
+cudaError_t launch_branch(int mode, const Plan* P, const SearchDev* S, const NodeRec* parents, int32_t* dense,
+                          int blocks, cudaStream_t st)
 {
-    if (L.n_work <= 0) return cudaSuccess;
-    const int blocks = (int)(L.n_work < 152 * 64 ? L.n_work : 152 * 64);
-    if (L.mode == MODE_INITIAL) branch2_kernel<MODE_INITIAL><<<blocks, 256, 0, st>>>(L);
-    else branch2_kernel<MODE_SEARCH><<<blocks, 256, 0, st>>>(L);
+    if (blocks <= 0) return cudaSuccess;
+    if (mode == MODE_INITIAL) branch2_kernel<MODE_INITIAL><<<blocks, 256, 0, st>>>(P, S, parents, dense);
+    else branch2_kernel<MODE_SEARCH><<<blocks, 256, 0, st>>>(P, S, parents, dense);
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const BranchLaunch& L, SearchDev* S, const SurvOut& out, cudaStream_t st)
+cudaError_t launch_finalize(int mode, const Plan* P, SearchDev* S, const NodeRec* parents, int32_t* dense,
+                            const SurvOut& out, int blocks, cudaStream_t st)
 {
-    if (L.n_dense <= 0) return cudaSuccess;
-    int64_t blocks = (L.n_dense + 255) / 256;
-    if (blocks > 152 * 32) blocks = 152 * 32;
-    if (L.mode == MODE_INITIAL) finalize_kernel<MODE_INITIAL><<<(int)blocks, 256, 0, st>>>(L, S, out);
-    else finalize_kernel<MODE_SEARCH><<<(int)blocks, 256, 0, st>>>(L, S, out);
+    if (blocks <= 0) return cudaSuccess;
+    if (mode == MODE_INITIAL) finalize_kernel<MODE_INITIAL><<<blocks, 256, 0, st>>>(P, S, parents, dense, out);
+    else finalize_kernel<MODE_SEARCH><<<blocks, 256, 0, st>>>(P, S, parents, dense, out);
     return cudaGetLastError();
 }
 

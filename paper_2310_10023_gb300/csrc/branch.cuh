@@ -10,7 +10,7 @@ namespace bbs {
 
 constexpr int CH = 256;        // nodes per frontier chunk
 constexpr int PCHUNK = 2048;   // scan points staged in shared memory per CTA
-constexpr int MAXSEG = 64;     // searches per scoring launch
+constexpr int MAXSEG = 256;    // parent runs per scoring launch
 
 struct ScoreArgs {
     LevelView maps[MAX_LEVELS];
@@ -41,6 +41,9 @@ struct Ctl {
     int32_t reason;        // last select: 1 batch full, 2 below best, 3 leaf, 4 F emptied, 0 F was empty
     int32_t match_changed;
     int32_t active;        // slot in use
+    // statistics kept on the device (the search loop may run without the host)
+    int64_t st_iters, st_parents, st_nodes, st_gathers;
+    unsigned long long t_start_ns, t_match_ns, t_end_ns;   // %globaltimer
 };
 
 // One search slot (device).  Frontier arrays have K + 1 buckets.
@@ -50,6 +53,8 @@ struct SearchDev {
     int32_t K;
     int32_t lmax;
     int64_t batch;
+    int32_t rmax;               // dense task slots per parent (most rotational children)
+    int32_t chunks;             // point chunks per parent
     int32_t pmin[3], pext[3];   // virtual parents of the initial set
     int32_t wmin[3], wmax[3];   // initial translation window, Eq. (3)-(5)
     DevGrid grid;
@@ -96,14 +101,19 @@ struct Seg {
     int32_t pad;
 };
 
-struct BranchLaunch {
-    const SearchDev* S;
-    const NodeRec* parents;
-    int32_t* dense;          // (parent, task, child) scores, zeroed before the launch
-    int64_t n_work;
-    int64_t n_dense;
+enum { PLAN_OK = 0, PLAN_EMPTY = 1, PLAN_OVERFLOW = 2 };
+
+// The plan of one scoring round, in device memory: written by the host (host
+// path) or by plan_kernel (device-driven iterations).
+struct Plan {
+    int64_t n_work;          // (parent, point chunk) work items
+    int64_t n_dense;         // dense (parent, task, child) score slots, at most the dense capacity
     int32_t nseg;
     int32_t mode;
+    int32_t status;          // PLAN_*: the kernels of a round run only when PLAN_OK
+    int32_t iters;           // iterations of the current device-driven loop
+    int32_t max_iters;       // the device-driven loop stops after this many
+    int32_t pad;
     Seg seg[MAXSEG];
 };
 
@@ -117,7 +127,11 @@ struct SurvOut {
     int* err;
 };
 
-cudaError_t launch_branch(const BranchLaunch& L, cudaStream_t st);
-cudaError_t launch_finalize(const BranchLaunch& L, SearchDev* S, const SurvOut& out, cudaStream_t st);
+// scoring and survivor kernels of one round; `blocks` is the grid (the
+// kernels stride over the plan's work), each skips unless the plan is PLAN_OK
+cudaError_t launch_branch(int mode, const Plan* P, const SearchDev* S, const NodeRec* parents, int32_t* dense,
+                          int blocks, cudaStream_t st);
+cudaError_t launch_finalize(int mode, const Plan* P, SearchDev* S, const NodeRec* parents, int32_t* dense,
+                            const SurvOut& out, int blocks, cudaStream_t st);
 
 }  // namespace bbs

@@ -309,17 +309,18 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
     BBS_CUDA_TRY(cudaMemsetAsync(d_dense, 0, sizeof(int32_t) * 8 * (size_t)items, st));
     int rc = BBS_OK;
     const int chunks = (int)((k + PCHUNK - 1) / PCHUNK);
-    // parents in runs of at most 2^20 per launch (kernel argument block holds 64 runs)
+    Plan* d_plan = nullptr;
+    BBS_CUDA_TRY(cudaMallocAsync((void**)&d_plan, sizeof(Plan), st));
+    std::vector<Plan> plans;
+    // parents in runs of at most 2^20 per segment, at most MAXSEG segments per launch
     for (int64_t p0 = 0; rc == BBS_OK && p0 < n && chunks > 0; p0 += ((int64_t)MAXSEG << 20)) {
-        BranchLaunch L;
-        std::memset(&L, 0, sizeof(L));
-        L.S = d_sd;
-        L.parents = d_par;
-        L.dense = d_dense;
-        L.mode = MODE_SEARCH;
+        Plan P;
+        std::memset(&P, 0, sizeof(P));
+        P.mode = MODE_SEARCH;
+        P.status = PLAN_OK;
         int64_t work = 0;
-        for (int64_t q = p0; q < n && L.nseg < MAXSEG; q += ((int64_t)1 << 20)) {
-            Seg& sg = L.seg[L.nseg++];
+        for (int64_t q = p0; q < n && P.nseg < MAXSEG; q += ((int64_t)1 << 20)) {
+            Seg& sg = P.seg[P.nseg++];
             sg.first_parent = q;
             sg.first_work = work;
             sg.n_parents = std::min<int64_t>((int64_t)1 << 20, n - q);
@@ -329,10 +330,13 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
             sg.R = rmax;
             work += sg.n_parents * chunks;
         }
-        L.n_work = work;
-        cudaError_t e = launch_branch(L, st);
+        P.n_work = work;
+        cudaError_t e = cudaMemcpyAsync(d_plan, &P, sizeof(P), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = launch_branch(MODE_SEARCH, d_plan, d_sd, d_par, d_dense, (int)std::min<int64_t>(work, 152 * 64), st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // P is reused by the next launch
         if (e != cudaSuccess) rc = set_error(BBS_ECUDA, "score_children: %s", cudaGetErrorString(e));
     }
+    cudaFreeAsync(d_plan, st);
     std::vector<int32_t> dense((size_t)(8 * items));
     if (rc == BBS_OK) {
         cudaError_t e = cudaMemcpyAsync(dense.data(), d_dense, sizeof(int32_t) * dense.size(), cudaMemcpyDeviceToHost, st);

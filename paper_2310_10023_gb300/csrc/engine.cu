@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 #include <type_traits>
@@ -92,6 +93,13 @@ __device__ __forceinline__ bool lex_lt(const LexKey& a, const LexKey& b) { retur
 
 // ---- kernels -----------------------------------------------------------------
 
+__device__ __forceinline__ unsigned long long gtimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 __global__ void pool_init_kernel(PoolDev p)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.nchunks; i += (int64_t)gridDim.x * blockDim.x) {
@@ -106,6 +114,7 @@ __global__ void pool_init_kernel(PoolDev p)
 __global__ void slot_init_kernel(SearchDev* S, const int32_t* slots)
 {
     SearchDev& s = S[slots[blockIdx.x]];
+    if (threadIdx.x == 0) s.ctl->t_start_ns = gtimer_ns();
     for (int i = threadIdx.x; i <= s.K; i += blockDim.x) {
         s.b_cnt[i] = 0;
         s.b_kids[i] = 0;
@@ -118,8 +127,9 @@ __global__ void slot_init_kernel(SearchDev* S, const int32_t* slots)
     }
 }
 
-__global__ void __launch_bounds__(1024) alloc_kernel(SearchDev* S, int nslots, PoolDev pool)
+__global__ void __launch_bounds__(1024) alloc_kernel(SearchDev* S, int nslots, PoolDev pool, const Plan* P)
 {
+    if (P->status != PLAN_OK) return;
     __shared__ int64_t sh[32];
     __shared__ int64_t s_base;
     __shared__ int s_min[33];
@@ -393,6 +403,16 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
                 c->match_changed = 1;
             }
             c->done = nparents == 0;
+            // statistics
+            const unsigned long long now = gtimer_ns();
+            if (nparents > 0) {
+                c->st_iters += 1;
+                c->st_parents += nparents;
+                c->st_nodes += pk;
+                c->st_gathers += (pk / 8) * (int64_t)f.K;
+            }
+            if (c->match_changed) c->t_match_ns = now;
+            if (c->done) c->t_end_ns = now;
         }
         __syncthreads();
     }
@@ -422,8 +442,9 @@ __global__ void slot_release_kernel(SearchDev* S, int slot, PoolDev pool)
 
 // popped chunks of every search -> the dense parent array at the search's offset
 __global__ void gather_kernel(SearchDev* S, PoolDev pool, const int64_t* __restrict__ poff, int nslots,
-                              NodeRec* __restrict__ parents)
+                              NodeRec* __restrict__ parents, const Plan* P)
 {
+    if (P->status != PLAN_OK) return;
     for (int si = blockIdx.y; si < nslots; si += gridDim.y) {
         SearchDev& f = S[si];
         if (!f.ctl->active || f.ctl->err) continue;
@@ -440,6 +461,69 @@ __global__ void gather_kernel(SearchDev* S, PoolDev pool, const int64_t* __restr
                 pool.chunk_bucket[ch] = -1;
             }
         }
+    }
+}
+
+// The plan of the next scoring round, built on the device from every live
+// search's popped parents: per-search parent offsets, (parent, point chunk)
+// work ranges and dense score ranges.  It ends the device-driven loop (sets
+// the graph's while condition to 0) when no search popped anything, when the
+// round does not fit the dense capacity or the run table (the host finishes
+// that round), or after P->max_iters iterations.
+__global__ void __launch_bounds__(1024) plan_kernel(SearchDev* S, int nslots, Plan* P, int64_t* poff,
+                                                    unsigned long long* surv_count, int64_t dense_cap,
+                                                    cudaGraphConditionalHandle cond)
+{
+    __shared__ int64_t sh[32];
+    const int tid = threadIdx.x;
+    if (tid == 0) *surv_count = 0;
+    int64_t cp = 0, cw = 0, cd = 0, cn = 0;
+    for (int base = 0; base < nslots; base += blockDim.x) {
+        const int s = base + tid;
+        int64_t np = 0, w = 0, d = 0, has = 0;
+        if (s < nslots) {
+            const Ctl* c = S[s].ctl;
+            if (c->active && !c->done && !c->err) np = c->n_parents;
+            w = np * S[s].chunks;
+            d = np * S[s].rmax * 8;
+            has = np > 0;
+        }
+        int64_t tp, tw, td, tn;
+        const int64_t ep = block_excl_scan(np, &tp, sh);
+        const int64_t ew = block_excl_scan(w, &tw, sh);
+        const int64_t ed = block_excl_scan(d, &td, sh);
+        const int64_t en = block_excl_scan(has, &tn, sh);
+        if (s < nslots) {
+            poff[s] = cp + ep;
+            const int64_t si = cn + en;
+            if (has && si < MAXSEG) {
+                Seg& g = P->seg[si];
+                g.first_parent = cp + ep;
+                g.first_work = cw + ew;
+                g.n_parents = np;
+                g.dense_base = cd + ed;
+                g.chunks = S[s].chunks;
+                g.sid = s;
+                g.R = S[s].rmax;
+                g.pad = 0;
+            }
+        }
+        cp += tp;
+        cw += tw;
+        cd += td;
+        cn += tn;
+    }
+    if (tid == 0) {
+        P->nseg = (int32_t)(cn < MAXSEG ? cn : MAXSEG);
+        P->n_work = cw;
+        P->n_dense = cd;
+        P->mode = MODE_SEARCH;
+        int st = PLAN_OK;
+        if (cp == 0) st = PLAN_EMPTY;
+        else if (cn > MAXSEG || cd > dense_cap) st = PLAN_OVERFLOW;
+        P->status = st;
+        P->iters += 1;
+        if (st != PLAN_OK || P->iters >= P->max_iters) cudaGraphSetConditional(cond, 0);
     }
 }
 
@@ -467,6 +551,7 @@ Engine::~Engine()
 {
     for (size_t i = 0; i < hosts_.size(); ++i)
         if (hosts_[i].used) release((int)i);
+    if (exec_) cudaGraphExecDestroy(exec_);
     for (void* p : fixed_) cudaFreeAsync(p, st_);
     for (cudaEvent_t e : evs_) cudaEventDestroy(e);
     if (h_ctl_) cudaFreeHost(h_ctl_);
@@ -497,6 +582,7 @@ int Engine::init()
     BBS_TRY(get(&d_ctl_, (size_t)max_slots_));
     BBS_TRY(get(&parents_, (size_t)(nchunks_ * CH)));
     BBS_TRY(get(&d_poff_, (size_t)max_slots_));
+    BBS_TRY(get(&d_plan_, 1));
     BBS_TRY(get(&d_slots_, (size_t)max_slots_));
     BBS_TRY(get(&dense_, (size_t)DENSE_CAP));
     BBS_TRY(get(&surv_.nodes, (size_t)DENSE_CAP));
@@ -509,6 +595,8 @@ int Engine::init()
     BBS_CUDA_TRY(cudaMemsetAsync(d_S_, 0, sizeof(SearchDev) * (size_t)max_slots_, st_));
     BBS_CUDA_TRY(cudaMemsetAsync(surv_.count, 0, sizeof(unsigned long long), st_));
     BBS_CUDA_TRY(cudaMemsetAsync(surv_.err, 0, sizeof(int), st_));
+    BBS_CUDA_TRY(cudaMemsetAsync(d_plan_, 0, sizeof(Plan), st_));
+    BBS_CUDA_TRY(cudaMemsetAsync(dense_, 0, sizeof(int32_t) * (size_t)DENSE_CAP, st_));
     BBS_CUDA_TRY(cudaMallocHost((void**)&h_ctl_, sizeof(Ctl) * (size_t)max_slots_));
     BBS_CUDA_TRY(cudaMallocHost((void**)&h_poff_, sizeof(int64_t) * (size_t)max_slots_));
     std::memset(h_ctl_, 0, sizeof(Ctl) * (size_t)max_slots_);
@@ -632,6 +720,8 @@ int Engine::add(const bbs_maps* m, const float* xyz, int64_t k, int is_device, c
     d.K = (int32_t)k;
     d.lmax = g.levels - 1;
     d.batch = (opts && opts->batch > 0) ? opts->batch : 10000;
+    d.rmax = h.rmax;
+    d.chunks = h.chunks;
     for (int a = 0; a < 3; ++a) {
         const int64_t pmin = floor_div2(g.wmin[a]), pmax = floor_div2(g.wmax[a]);
         d.pmin[a] = (int32_t)pmin;
@@ -740,31 +830,34 @@ int Engine::start()
     return BBS_OK;
 }
 
-int Engine::step(std::vector<int>* finished)
+void Engine::finish_never_live(std::vector<int>* finished)
 {
-    const int n = max_slots_;
     // searches that never went live (no points, or failed) finish at once
-    for (int i = 0; i < n; ++i) {
+    for (int i = 0; i < max_slots_; ++i) {
         SearchHost& h = hosts_[(size_t)i];
         if (h.used && !h.live && h.t_end == 0) {
             h.t_end = now_ms();
             finished->push_back(i);
         }
     }
-    if (live_count() == 0) return BBS_OK;
-    select_kernel<<<n, 1024, 0, st_>>>(d_S_, n, pool_);
-    launches_ += 1;
-    BBS_CUDA_TRY(cudaGetLastError());
-    BBS_CUDA_TRY(cudaMemcpyAsync(h_ctl_, d_ctl_, sizeof(Ctl) * (size_t)n, cudaMemcpyDeviceToHost, st_));
+}
+
+int Engine::read_ctl()
+{
+    BBS_CUDA_TRY(cudaMemcpyAsync(h_ctl_, d_ctl_, sizeof(Ctl) * (size_t)max_slots_, cudaMemcpyDeviceToHost, st_));
     BBS_CUDA_TRY(cudaStreamSynchronize(st_));
+    for (int i = 0; i < max_slots_; ++i)
+        if (hosts_[(size_t)i].live) hosts_[(size_t)i].res.d2h_bytes += (int64_t)sizeof(Ctl);
+    return BBS_OK;
+}
+
+void Engine::mark_finished(std::vector<int>* finished)
+{
     const double t = now_ms();
-    int64_t total_parents = 0;
-    for (int i = 0; i < n; ++i) {
+    for (int i = 0; i < max_slots_; ++i) {
         SearchHost& h = hosts_[(size_t)i];
-        h_poff_[i] = total_parents;
         if (!h.live) continue;
         const Ctl& c = h_ctl_[i];
-        h.res.d2h_bytes += (int64_t)sizeof(Ctl);
         if (c.err) {
             // the shared pool ran out while this search inserted: it fails alone
             h.status = set_error(BBS_ENOMEM, "localize: the frontier pool (%lld nodes) is exhausted",
@@ -772,28 +865,32 @@ int Engine::step(std::vector<int>* finished)
             h.live = false;
             h.t_end = t;
             finished->push_back(i);
-            continue;
-        }
-        if (c.match_changed) h.t_match = t;
-        if (c.done) {
+        } else if (c.done) {
             h.live = false;
             h.t_end = t;
             finished->push_back(i);
-            continue;
         }
-        total_parents += c.n_parents;
-        h.res.iterations++;
-        h.res.parents_branched += c.n_parents;
-        h.res.nodes_scored += c.popped_kids;
-        h.res.gathers += (c.popped_kids / 8) * h.scan.k;
+    }
+}
+
+// host-side scoring of the parents the last select popped (h_ctl_ is current)
+int Engine::process_popped()
+{
+    const int n = max_slots_;
+    int64_t total_parents = 0, maxpop = 1;
+    for (int i = 0; i < n; ++i) {
+        h_poff_[i] = total_parents;
+        if (!hosts_[(size_t)i].live) continue;
+        total_parents += h_ctl_[i].n_parents;
+        maxpop = std::max<int64_t>(maxpop, h_ctl_[i].n_pop);
     }
     if (total_parents == 0) return BBS_OK;
     BBS_CUDA_TRY(cudaMemcpyAsync(d_poff_, h_poff_, sizeof(int64_t) * (size_t)n, cudaMemcpyHostToDevice, st_));
-    int64_t maxpop = 1;
-    for (int i = 0; i < n; ++i)
-        if (hosts_[(size_t)i].live) maxpop = std::max<int64_t>(maxpop, h_ctl_[i].n_pop);
+    h_plan_.status = PLAN_OK;
+    h_plan_.nseg = 0;
+    BBS_CUDA_TRY(cudaMemcpyAsync(d_plan_, &h_plan_, offsetof(Plan, seg), cudaMemcpyHostToDevice, st_));
     dim3 gg((unsigned)std::min<int64_t>(maxpop, 4096), (unsigned)std::min(n, 65535));
-    gather_kernel<<<gg, CH, 0, st_>>>(d_S_, pool_, d_poff_, n, parents_);
+    gather_kernel<<<gg, CH, 0, st_>>>(d_S_, pool_, d_poff_, n, parents_, d_plan_);
     launches_ += 1;
     BBS_CUDA_TRY(cudaGetLastError());
     std::vector<Seg> segs;
@@ -831,7 +928,83 @@ int Engine::step(std::vector<int>* finished)
             p0 += take;
         }
     }
-    BBS_TRY(flush());
+    return flush();
+}
+
+int Engine::step(std::vector<int>* finished)
+{
+    finish_never_live(finished);
+    if (live_count() == 0) return BBS_OK;
+    select_kernel<<<max_slots_, 1024, 0, st_>>>(d_S_, max_slots_, pool_);
+    launches_ += 1;
+    BBS_CUDA_TRY(cudaGetLastError());
+    BBS_TRY(read_ctl());
+    mark_finished(finished);
+    return process_popped();
+}
+
+int Engine::build_graph()
+{
+    const int n = max_slots_;
+    cudaStream_t cs;
+    BBS_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    cudaGraphConditionalHandle cond = 0;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+    alignas(cudaGraphNodeParams) unsigned char np_buf[sizeof(cudaGraphNodeParams)];
+    std::memset(np_buf, 0, sizeof(np_buf));
+    cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(np_buf);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    cudaGraph_t body = e == cudaSuccess ? np.conditional.phGraph_out[0] : nullptr;
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        // one iteration: select, plan, gather, score, survivors, insert
+        select_kernel<<<n, 1024, 0, cs>>>(d_S_, n, pool_);
+        plan_kernel<<<1, 1024, 0, cs>>>(d_S_, n, d_plan_, d_poff_, surv_.count, DENSE_CAP, cond);
+        gather_kernel<<<dim3(256, (unsigned)std::min(n, 65535)), CH, 0, cs>>>(d_S_, pool_, d_poff_, n, parents_, d_plan_);
+        launch_branch(MODE_SEARCH, d_plan_, d_S_, parents_, dense_, 152 * 20, cs);
+        launch_finalize(MODE_SEARCH, d_plan_, d_S_, parents_, dense_, surv_, 152 * 8, cs);
+        alloc_kernel<<<n, 1024, 0, cs>>>(d_S_, n, pool_, d_plan_);
+        scatter_kernel<<<1024, 256, 0, cs>>>(d_S_, pool_, surv_.nodes, surv_.scores, surv_.sid, surv_.count, surv_.cap);
+        cudaGraph_t out = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &out);
+        e = e2 != cudaSuccess ? e2 : cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec_, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        exec_ = nullptr;
+        return set_error(BBS_ECUDA, "engine: building the iteration graph: %s", cudaGetErrorString(e));
+    }
+    return BBS_OK;
+}
+
+int Engine::iterate(int max_iters, std::vector<int>* finished)
+{
+    // CUDA events cannot sit inside the graph's loop body: timed runs take
+    // the host-driven path, whose scoring launches are the same kernels
+    if (host_driven_ || timed_) return step(finished);
+    finish_never_live(finished);
+    if (live_count() == 0) return BBS_OK;
+    if (!exec_) BBS_TRY(build_graph());
+    h_plan_.iters = 0;
+    h_plan_.max_iters = max_iters > 0 ? max_iters : 1;
+    BBS_CUDA_TRY(cudaMemcpyAsync(&d_plan_->iters, &h_plan_.iters, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, st_));
+    BBS_CUDA_TRY(cudaGraphLaunch(exec_, st_));
+    int32_t st2[2] = {0, 0};   // status, iterations the device loop ran
+    BBS_CUDA_TRY(cudaMemcpyAsync(st2, &d_plan_->status, sizeof(st2), cudaMemcpyDeviceToHost, st_));
+    BBS_TRY(read_ctl());
+    const int32_t status = st2[0];
+    launches_ += 7 * (int64_t)st2[1];   // every iteration of the loop runs the body's 7 kernels
+    mark_finished(finished);
+    if (status == PLAN_OVERFLOW) return process_popped();   // the selected round did not fit on the device
     return BBS_OK;
 }
 
@@ -867,11 +1040,20 @@ int Engine::finalize(int i, bbs_result* out)
         status = BBS_NOT_FOUND;
     } else {
         const HostGrid& g = h.scan.grid;
+        r->iterations = c.st_iters;
+        r->parents_branched = c.st_parents;
+        r->nodes_scored += c.st_nodes;
+        r->gathers += c.st_gathers;
         r->probes = r->nodes_scored * h.scan.k;
         r->best_score = c.best;
         r->peak_frontier = c.peak;
-        r->phase_ms[2] = (h.t_match >= 0 ? h.t_match : h.t_end) - h.t_init;
-        r->phase_ms[3] = h.t_match >= 0 ? h.t_end - h.t_match : 0.0;
+        // device timestamps: the initial set starts at t_start_ns
+        const double dev_end = c.t_end_ns > c.t_start_ns ? (double)(c.t_end_ns - c.t_start_ns) / 1e6 : 0.0;
+        const double dev_match = c.found && c.t_match_ns > c.t_start_ns ? (double)(c.t_match_ns - c.t_start_ns) / 1e6 : -1.0;
+        const double init_ms = r->phase_ms[1];
+        r->phase_ms[2] = (dev_match >= 0 ? dev_match : dev_end) - init_ms;
+        r->phase_ms[3] = dev_match >= 0 ? dev_end - dev_match : 0.0;
+        if (r->phase_ms[2] < 0) r->phase_ms[2] = 0;
         r->d2h_bytes += (int64_t)sizeof(Ctl);
         if (c.found) {
             const NodeRec& nd = c.match;
@@ -887,10 +1069,10 @@ int Engine::finalize(int i, bbs_result* out)
             r->node[6] = 0;
             for (int a = 0; a < 3; ++a) r->pose[a] = (double)r->node[a] * g.r;
             for (int a = 0; a < 3; ++a) r->pose[3 + a] = grid_angle(g, 0, a, r->node[3 + a]);
-            r->ms_to_optimum = h.t_match - h.t0;
+            r->ms_to_optimum = r->phase_ms[0] + dev_match;
             status = BBS_OK;
         } else {
-            r->ms_to_optimum = h.t_end - h.t0;
+            r->ms_to_optimum = r->phase_ms[0] + dev_end;
             status = BBS_NOT_FOUND;
         }
     }
@@ -936,17 +1118,15 @@ int Engine::release(int i)
 
 int Engine::score_launch(int mode, const std::vector<Seg>& segs, int64_t work, int64_t dense)
 {
-    BranchLaunch L;
-    std::memset(&L, 0, sizeof(L));
-    L.S = d_S_;
-    L.parents = parents_;
-    L.dense = dense_;
-    L.n_work = work;
-    L.n_dense = dense;
-    L.nseg = (int32_t)segs.size();
-    L.mode = mode;
-    for (size_t i = 0; i < segs.size(); ++i) L.seg[i] = segs[i];
-    BBS_CUDA_TRY(cudaMemsetAsync(dense_, 0, sizeof(int32_t) * (size_t)dense, st_));
+    h_plan_.n_work = work;
+    h_plan_.n_dense = dense;
+    h_plan_.nseg = (int32_t)segs.size();
+    h_plan_.mode = mode;
+    h_plan_.status = PLAN_OK;
+    for (size_t i = 0; i < segs.size(); ++i) h_plan_.seg[i] = segs[i];
+    // pageable source: staged before cudaMemcpyAsync returns, so h_plan_ may be rewritten
+    BBS_CUDA_TRY(cudaMemcpyAsync(d_plan_, &h_plan_, offsetof(Plan, seg) + sizeof(Seg) * segs.size(),
+                                 cudaMemcpyHostToDevice, st_));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (timed_) {
         BBS_CUDA_TRY(cudaEventCreate(&e0));
@@ -955,10 +1135,12 @@ int Engine::score_launch(int mode, const std::vector<Seg>& segs, int64_t work, i
         evs_.push_back(e1);
         BBS_CUDA_TRY(cudaEventRecord(e0, st_));
     }
-    BBS_CUDA_TRY(launch_branch(L, st_));
+    const int bb = (int)std::min<int64_t>(work, 152 * 64);
+    BBS_CUDA_TRY(launch_branch(mode, d_plan_, d_S_, parents_, dense_, bb, st_));
     if (timed_) BBS_CUDA_TRY(cudaEventRecord(e1, st_));
-    BBS_CUDA_TRY(launch_finalize(L, d_S_, surv_, st_));
-    alloc_kernel<<<max_slots_, 1024, 0, st_>>>(d_S_, max_slots_, pool_);
+    const int fb = (int)std::min<int64_t>((dense + 255) / 256, 152 * 32);
+    BBS_CUDA_TRY(launch_finalize(mode, d_plan_, d_S_, parents_, dense_, surv_, fb, st_));
+    alloc_kernel<<<max_slots_, 1024, 0, st_>>>(d_S_, max_slots_, pool_, d_plan_);
     scatter_kernel<<<1024, 256, 0, st_>>>(d_S_, pool_, surv_.nodes, surv_.scores, surv_.sid, surv_.count, surv_.cap);
     BBS_CUDA_TRY(cudaMemsetAsync(surv_.count, 0, sizeof(unsigned long long), st_));
     BBS_CUDA_TRY(cudaGetLastError());
@@ -1044,10 +1226,11 @@ int search_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device, co
     int slot = -1;
     if (rc == BBS_OK) rc = E->add(m, xyz, k, is_device, rg, opts, 0, &slot);
     if (rc == BBS_OK) rc = E->start();
+    E->set_host_driven(opts && (opts->flags & BBS_HOST_DRIVEN));
     std::vector<int> fin;
     while (rc == BBS_OK && E->used_count() > 0) {
         fin.clear();
-        rc = E->step(&fin);
+        rc = E->iterate(1 << 20, &fin);
         for (int i : fin) E->finalize(i, res);
     }
     release_engine(E, rc == BBS_OK);
@@ -1071,10 +1254,11 @@ int search_run_many(const bbs_maps* m, int n, const float* const* scans, const i
         rc = E->add(m, scans[i], ks[i], is_device, rg, opts, (uint64_t)i, &slot_of[(size_t)i]);
     }
     if (rc == BBS_OK) rc = E->start();
+    E->set_host_driven(opts && (opts->flags & BBS_HOST_DRIVEN));
     std::vector<int> fin;
     while (rc == BBS_OK && E->used_count() > 0) {
         fin.clear();
-        rc = E->step(&fin);
+        rc = E->iterate(1 << 20, &fin);
         for (int s_ : fin) E->finalize(s_, &res[E->tag(s_)]);
     }
     release_engine(E, rc == BBS_OK);

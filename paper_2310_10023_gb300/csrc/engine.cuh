@@ -52,8 +52,15 @@ class Engine {
             uint64_t tag, int* slot);
     // score the initial sets of every search added since the last call
     int start();
-    // one iteration of every live search; searches that finished are appended to *finished
+    // one host-driven iteration of every live search (one synchronization);
+    // searches that finished are appended to *finished
     int step(std::vector<int>* finished);
+    // advance every live search: by default a captured CUDA graph loops over
+    // up to max_iters iterations on the device without the host (a while
+    // node whose condition the planning kernel clears); with BBS_HOST_DRIVEN
+    // one host-driven step.  Results are identical either way.
+    int iterate(int max_iters, std::vector<int>* finished);
+    void set_host_driven(bool v) { host_driven_ = v; }
     // the search's result; the slot and its memory are released
     int finalize(int slot, bbs_result* out);
     // stop a search early and release it (its result reports status `code`)
@@ -72,6 +79,11 @@ class Engine {
   private:
     static constexpr int64_t DENSE_CAP = (int64_t)1 << 22;   // child scores per scoring launch
     int score_launch(int mode, const std::vector<Seg>& segs, int64_t work, int64_t dense);
+    int read_ctl();
+    void finish_never_live(std::vector<int>* finished);
+    void mark_finished(std::vector<int>* finished);
+    int process_popped();
+    int build_graph();
     int upload_slot(int slot);
     int release(int slot);
     template <class T>
@@ -92,6 +104,10 @@ class Engine {
     SurvOut surv_{};
     Ctl* h_ctl_ = nullptr;
     int64_t* h_poff_ = nullptr;
+    Plan* d_plan_ = nullptr;
+    Plan h_plan_{};
+    cudaGraphExec_t exec_ = nullptr;
+    bool host_driven_ = false;
     std::vector<void*> fixed_;
     std::vector<SearchHost> hosts_;
     std::vector<cudaEvent_t> evs_;

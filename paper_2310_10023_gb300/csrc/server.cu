@@ -167,7 +167,7 @@ void worker_main(bbs_server* S)
         }
         int rc = S->engine->start();
         fin.clear();
-        if (rc >= 0) rc = S->engine->step(&fin);
+        if (rc >= 0) rc = S->engine->iterate(4, &fin);   // a few device iterations, then admission again
         if (rc < 0) {
             std::lock_guard<std::mutex> lock(S->mu);
             S->fatal = rc;

@@ -395,3 +395,26 @@ def test_outdoor_sampled_parity_and_planted_pose(nv):
         assert abs(res.pose[i] - pose[i]) <= w.r + 0.1
     dyaw = (res.pose[5] - pose[5] + math.pi) % (2 * math.pi) - math.pi
     assert abs(dyaw) <= 2 * g.dprime(0)[2]
+
+
+# ---- the device-driven iteration loop --------------------------------------------
+
+def test_graph_loop_equals_host_loop(nv, room_pair, indoor_pair):
+    """The captured-graph loop (default) and the host-driven loop follow the
+    same trajectory: identical results, iterations and nodes scored."""
+    for (w, m, dm, om), idx in ((room_pair, 3), (indoor_pair, 4)):
+        s, _ = synth.make_scan(w.scene, idx)
+        nr, _ = _ranges(nv, w)
+        a = nv.bbs_localize(dm, s, nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch))
+        b = nv.bbs_localize(dm, s, nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch, flags=nv.HOST_DRIVEN))
+        assert (a.status, a.best_score, list(a.node), a.iterations, a.nodes_scored, a.peak_frontier) == \
+               (b.status, b.best_score, list(b.node), b.iterations, b.nodes_scored, b.peak_frontier)
+    w, m, dm, om = indoor_pair
+    nr, _ = _ranges(nv, w)
+    scans = [synth.make_scan(2, 70 + i, k=3000 + 2500 * i)[0] for i in range(5)]
+    many = nv.bbs_localize_many(dm, scans, nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch))
+    many_h = nv.bbs_localize_many(dm, scans, nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch,
+                                                              flags=nv.HOST_DRIVEN))
+    for a, b in zip(many, many_h):
+        assert (a.status, a.best_score, list(a.node), a.iterations, a.nodes_scored) == \
+               (b.status, b.best_score, list(b.node), b.iterations, b.nodes_scored)
