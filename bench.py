@@ -45,6 +45,8 @@ def _args():
     p.add_argument("--scans", type=int, default=8, help="distinct scans cycled by the steps")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip the batched and served forms")
+    p.add_argument("--host-driven", action="store_true",
+                   help="iterate searches from the host instead of the device-driven graph loop")
     return p.parse_args()
 
 
@@ -283,7 +285,7 @@ def run_served(nv, torch, lam=200.0, n=64, seed=9):
 
 def _kernel_hash():
     h = hashlib.sha256()
-    for f in ("score.cu", "bbs_internal.cuh", "branch.cuh"):
+    for f in ("branch.cu", "bbs_internal.cuh", "branch.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2310_10023_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -339,7 +341,8 @@ def run_ours(a):
     scans = [synth.make_scan(w.scene, rank * a.scans + i)[0] for i in range(a.scans)]
     scans_d = [torch.from_numpy(s).to(dev) for s in scans]
     args = nv.workload_args(w, stream=stream.cuda_stream, flags=nv.TIME_KERNELS)
-    args_plain = nv.workload_args(w, stream=stream.cuda_stream)
+    args_plain = nv.workload_args(w, stream=stream.cuda_stream,
+                                  flags=nv.HOST_DRIVEN if a.host_driven else 0)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
     def barrier():
@@ -453,7 +456,7 @@ def run_ours(a):
             "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Gop/s",
                          "frac": alu_achieved / alu_peak,
                          "traffic": _traffic_from_profile(),
-                         "kernel": "branch2_kernel (fused branch + Eq. (11) scoring)",
+                         "kernel": "branch3_kernel (fused branch + Eq. (11) scoring)",
                          "algorithmic_ops": f"{ALG_OPS_PER_UNIT} per scan point per rotational child "
                                             "(rotation 15, floor 3, level key 6, 8 child counts)",
                          "units_per_s": units_per_s, "launches": score_launches, "kernel_ms": score_ms,

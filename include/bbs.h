@@ -14,7 +14,7 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  * - Return value: BBS_OK (0), BBS_NOT_FOUND (1: no leaf reached the score
- *   threshold; Algorithm 2 returns a match only "when set"), or a negative
+ *   threshold, so Algorithm 2 has no match to return), or a negative
  *   error code.  Errors never abort the process; bbs_last_error() gives a
  *   thread-local description of the last failure on the calling thread.
  * - Point clouds are K x 3 float32, row-major (x, y, z), metres.
@@ -154,9 +154,10 @@ int  bbs_maps_info(const bbs_maps* maps, int level, int64_t* n_voxels, int64_t* 
                    int64_t* table_size, int32_t* max_probe, double* collision_rate);
 
 /* Target load (buckets in use / buckets) of the tables built by later
- * bbs_build_maps calls in this process; default 0.5.  Sec. III-C sizes T_l
- * "until the hash collision rate becomes small"; the load trades that rate
- * against the table's footprint in L2.  BBS_EINVAL outside (0.01, 0.9]. */
+ * bbs_build_maps calls in this process; default 0.25.  Sec. III-C enlarges
+ * T_l until few keys collide; the load trades the collision rate (probe
+ * length) against the table's footprint in L2.  BBS_EINVAL outside
+ * (0.01, 0.9]. */
 int  bbs_set_load_factor(double load);
 
 /* Bucket layout of the tables built by later bbs_build_maps calls in this

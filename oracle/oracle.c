@@ -52,7 +52,7 @@ double orc_delta(double r, double d_max)
     return acos(x);
 }
 
-/* d_max reading: "the maximum scan range" is taken from the data, as the
+/* d_max reading: the maximum range of the scan is taken from the data, as the
  * largest Euclidean norm of a scan point (FP64, fixed order). */
 double orc_scan_dmax(const float* s, int64_t k)
 {

@@ -1,16 +1,18 @@
 // branch.cu -- fused branch-and-score kernel (Eq. (13) children, Eq. (11)
 // scores) and the survivor pass of the search.
 //
-// Work unit: (parent, chunk of PCHUNK scan points).  A CTA stages its chunk of
-// the scan in shared memory once, then walks the parent's rotational children
-// (the "tasks"); for each task every thread rotates its points (FP32, fixed
+// Work: every rotational child ("task") of every parent of a launch, over
+// every point of its search's scan.  The launch's work is cut into slices
+// (task, block of PBLK points) and each CTA of one resident wave takes an
+// equal contiguous range of them, so the SMs finish together whatever the mix
+// of parents.  For each task, every thread rotates its points (FP32, fixed
 // order, no FMA), floors them exactly, and makes ONE brick probe per point
 // that answers all 8 translational children 2c + j (Sec. III-C layout, see
 // bbs_internal.cuh).  The 8 child counts are kept as two byte-packed
 // registers (4 counts each), reduced per warp with redux.sync on 16-bit
-// fields, summed across warps through double-buffered shared memory (one
-// barrier per task), and added to a dense (parent, task, child) score array.
-// The survivor pass then keeps children scoring above their search's best.
+// fields, summed across warps in shared memory, and added to a dense
+// (task, child) score array.  The survivor pass then keeps children scoring
+// above their search's best.
 #include "branch.cuh"
 
 namespace bbs {
@@ -83,22 +85,22 @@ __device__ __forceinline__ void child_bits(const LevelView& L, int32_t kx, int32
     }
 }
 
-// One task (rotational child) over the staged points, two points per step.
-// The chunk is staged as pairs: sxy[j] = (x_2j, x_2j+1, y_2j, y_2j+1) and
-// sz[j] = (z_2j, z_2j+1), so each coordinate pair is one 64-bit register for
-// the f32x2 operations.  The exact floor of q is the bit pattern of
+// One run (a rotational child over blocks of the staged chunk), two points
+// per step.  The chunk is staged as pairs: sxy[j] = (x_2j, x_2j+1, y_2j,
+// y_2j+1) and sz[j] = (z_2j, z_2j+1), so each coordinate pair is one 64-bit
+// register for the f32x2 operations; thread t takes pairs jlo + t, jlo + t +
+// blockDim, ... below jhi.  The exact floor of q is the bit pattern of
 // fl_rd(q + 1.5 * 2^23) minus that of 1.5 * 2^23 (valid for |q| < 2^22); that
 // offset is a multiple of 2^22, so the level shift applies to the raw bit
 // pattern and the offset, the translation and the compact origin fold into
 // one per-axis constant.
 template <bool COMPACT>
-__device__ __forceinline__ void score_task(const ulonglong2* sxy, const f2* sz, int n, const LevelView& L, int m,
-                                           const Row2& r0, const Row2& r1, const Row2& r2, int32_t cx, int32_t cy,
-                                           int32_t cz, uint32_t& acc0, uint32_t& acc1)
+__device__ __forceinline__ void score_run(const ulonglong2* sxy, const f2* sz, int n, int jlo, int jhi,
+                                          const LevelView& L, int m, const Row2& r0, const Row2& r1, const Row2& r2,
+                                          int32_t cx, int32_t cy, int32_t cz, uint32_t& acc0, uint32_t& acc1)
 {
     const f2 C = pk2(12582912.0f, 12582912.0f);
-    const int np = (n + 1) >> 1;
-    for (int j = threadIdx.x; j < np; j += blockDim.x) {
+    for (int j = jlo + threadIdx.x; j < jhi; j += blockDim.x) {
         const ulonglong2 xy = sxy[j];
         const f2 Z = sz[j];
         int32_t bx1, bx2, by1, by2, bz1, bz2;
@@ -117,150 +119,249 @@ __device__ __forceinline__ void score_task(const ulonglong2* sxy, const f2* sz, 
     }
 }
 
-__device__ __forceinline__ int find_seg(const Plan* P, int64_t w)
+// the segment holding launch-local slice w (segments in slice order)
+__device__ __forceinline__ int find_slice_seg(const Plan* P, int64_t w)
 {
     int lo = 0, hi = P->nseg - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (P->seg[mid].first_work <= w) lo = mid;
+        if (P->seg[mid].first_slice <= w) lo = mid;
         else hi = mid - 1;
     }
     return lo;
 }
 
-__device__ __forceinline__ int find_dense_seg(const Plan* P, int64_t d)
+// the segment holding launch-local task u (segments in task order)
+__device__ __forceinline__ int find_task_seg(const Plan* P, int64_t u)
 {
     int lo = 0, hi = P->nseg - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (P->seg[mid].dense_base <= d) lo = mid;
+        if (P->seg[mid].first_task <= u) lo = mid;
         else hi = mid - 1;
     }
     return lo;
 }
 
-// rotational-child ranges of a parent at level l (decoded from its rotation index)
-__device__ __forceinline__ void parent_ranges(const DevGrid& g, int l, uint32_t prot, int32_t lo[3], int32_t ext[3])
+// translation of virtual parent vp of the initial set (Eq. (3)-(5) window at l_max)
+__device__ __forceinline__ void virtual_parent(const SearchDev& S, int64_t vp, int32_t& px, int32_t& py, int32_t& pz)
 {
-    const int32_t ng = g.N[l][2], nb = g.N[l][1];
-    const int32_t c[3] = {(int32_t)(prot / ((uint32_t)ng * (uint32_t)nb)), (int32_t)((prot / (uint32_t)ng) % (uint32_t)nb),
-                          (int32_t)(prot % (uint32_t)ng)};
-    for (int i = 0; i < 3; ++i) {
-        int32_t a, b;
-        child_range(g, l, i, c[i], a, b);
-        lo[i] = a;
-        ext[i] = b - a;
-    }
+    pz = S.pmin[2] + (int32_t)(vp % S.pext[2]);
+    py = S.pmin[1] + (int32_t)((vp / S.pext[2]) % S.pext[1]);
+    px = S.pmin[0] + (int32_t)(vp / ((int64_t)S.pext[2] * S.pext[1]));
 }
+
+// A run: one task over blocks [b0, b1) of point chunk c, described in shared
+// memory for the whole CTA.
+struct __align__(16) RunDesc {
+    f2 a[9];          // rotation entries A_ik, each duplicated for the paired lanes
+    int32_t kc[3];    // per-axis key constant: translation - floor offset (- compact origin)
+    int32_t m;        // child level
+    int32_t c;        // point chunk
+    int32_t b0, b1;   // PBLK-point blocks [b0, b1) of the chunk
+    int32_t sid;      // search
+    int64_t task;     // launch-local task index
+};
+
+constexpr int NRUN = 32;   // runs described per round of a CTA
+constexpr int STATIC_NUM = 3, STATIC_DEN = 4;   // share of a launch's slices split statically
+constexpr int64_t GRAB_MIN = 4;                 // smallest dynamic grab (slices)
 
 }  // namespace
 
-constexpr int TB = 64;   // tasks reduced per barrier round
-
+// Fused branch + score.  The launch's slices (task, PBLK-point block) are
+// split into gridDim.x equal contiguous ranges, one per CTA; a CTA walks its
+// range in rounds of at most NRUN runs (maximal pieces of one task over one
+// chunk), describing every run of a round in parallel (task record, parent,
+// rotation rows), staging a chunk of the scan only when the chunk changes,
+// and adding each run's 8 child counts to the dense scores at the round's end.
 template <int MODE>
-__global__ void __launch_bounds__(256, 5) branch2_kernel(const Plan* __restrict__ P, const SearchDev* __restrict__ Sall,
-                                                         const NodeRec* __restrict__ parents, int32_t* dense)
+__global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
+    branch3_kernel(Plan* __restrict__ P, const SearchDev* __restrict__ Sall, const NodeRec* __restrict__ parents,
+                   const TaskRec* __restrict__ tasks, int32_t* dense)
 {
     if (P->status != PLAN_OK) return;
-    const int64_t n_work = P->n_work;
     __shared__ ulonglong2 sxy[PCHUNK / 2];
     __shared__ f2 sz[PCHUNK / 2];
-    __shared__ uint32_t red[TB][4];
+    __shared__ RunDesc rd[NRUN];
+    __shared__ uint32_t red[NRUN][4];
+    // the CTA's walk, kept in shared memory (uniform; frees registers for the runs)
+    __shared__ int64_t s_cur, s_end, s_next;
+    __shared__ int32_t s_gi, s_nrun, s_staged_sid, s_staged_c;
     const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t n_slices = P->n_slices;
+    // the first STATIC_NUM / STATIC_DEN of the slices in equal static shares;
+    // the rest handed out in shrinking grabs as CTAs finish
+    const int64_t n_static = n_slices * STATIC_NUM / STATIC_DEN;
+    if (tid == 0) {
+        s_cur = n_static * blockIdx.x / gridDim.x;
+        s_end = n_static * (blockIdx.x + 1) / gridDim.x;
+        s_gi = -1;
+        s_staged_sid = -1;
+        s_staged_c = -1;
+    }
+    for (int i = tid; i < 4 * NRUN; i += blockDim.x) (&red[0][0])[i] = 0u;
     float* fxy = reinterpret_cast<float*>(sxy);
     float* fz = reinterpret_cast<float*>(sz);
-    for (int64_t w = blockIdx.x; w < n_work; w += gridDim.x) {
-        const Seg g = P->seg[find_seg(P, w)];
-        const SearchDev& S = Sall[g.sid];
-        const int64_t local = w - g.first_work;
-        const int64_t pi = local / g.chunks;
-        const int32_t k0 = (int32_t)(local - pi * g.chunks) * PCHUNK;
-        const int32_t n = min(PCHUNK, S.K - k0);
-        __syncthreads();   // the previous item's readers of the staged points are done
-        for (int i = tid; i < n; i += blockDim.x) {
-            const float4 p = __ldg(S.scan + k0 + i);
-            const int j = i >> 1, h = i & 1;
-            fxy[4 * j + h] = p.x;
-            fxy[4 * j + 2 + h] = p.y;
-            fz[2 * j + h] = p.z;
-        }
-        int m, T;
-        int32_t tx, ty, tz;
-        int32_t lo[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
-        if (MODE == MODE_INITIAL) {
-            const int64_t vp = g.first_parent + pi;
-            const int32_t pz = (int32_t)(vp % S.pext[2]);
-            const int32_t py = (int32_t)((vp / S.pext[2]) % S.pext[1]);
-            const int32_t px = (int32_t)(vp / ((int64_t)S.pext[2] * S.pext[1]));
-            tx = 2 * (S.pmin[0] + px);
-            ty = 2 * (S.pmin[1] + py);
-            tz = 2 * (S.pmin[2] + pz);
-            m = S.lmax;
-            T = S.grid.N[m][0] * S.grid.N[m][1] * S.grid.N[m][2];
-        } else {
-            const NodeRec par = parents[g.first_parent + pi];
-            const int l = rl_level(par.rl);
-            m = l - 1;
-            parent_ranges(S.grid, l, rl_rot(par.rl), lo, ext);
-            T = m >= 0 ? ext[0] * ext[1] * ext[2] : 0;
-            tx = 2 * par.cx;
-            ty = 2 * par.cy;
-            tz = 2 * par.cz;
-        }
-        if (m < 0) continue;   // uniform: a leaf has no children (staging reads nothing more)
-        const LevelView Lv = S.maps[m];
-        const int64_t roff = S.grid.rot_off[m];
-        const int32_t Nb = S.grid.N[m][1], Ng = S.grid.N[m][2];
-        const int32_t off = 0x4B400000 >> m;   // the floor offset after the level shift
-        for (int t0 = 0; t0 < T; t0 += TB) {
-            const int tb = min(TB, T - t0);
-            for (int i = tid; i < 4 * TB; i += blockDim.x) (&red[0][0])[i] = 0u;
-            __syncthreads();   // staged points and zeroed partials visible
-            for (int tt = 0; tt < tb; ++tt) {
-                const int t = t0 + tt;
-                uint32_t crot;
-                if (MODE == MODE_INITIAL) {
-                    crot = (uint32_t)t;
-                } else {
-                    const int32_t ja = t / (ext[1] * ext[2]), jb = (t / ext[2]) % ext[1], jg = t % ext[2];
-                    crot = (uint32_t)(((int64_t)(lo[0] + ja) * Nb + (lo[1] + jb)) * Ng + (lo[2] + jg));
-                }
-                const float4* A = S.rot + 3 * (roff + (int64_t)crot);
-                const float4 a0 = __ldg(A), a1 = __ldg(A + 1), a2 = __ldg(A + 2);
-                const Row2 r0{pk2(a0.x, a0.x), pk2(a0.y, a0.y), pk2(a0.z, a0.z)};
-                const Row2 r1{pk2(a1.x, a1.x), pk2(a1.y, a1.y), pk2(a1.z, a1.z)};
-                const Row2 r2{pk2(a2.x, a2.x), pk2(a2.y, a2.y), pk2(a2.z, a2.z)};
-                uint32_t acc0 = 0, acc1 = 0;   // bytes: children (0,4,2,6) and (1,5,3,7)
-                if (Lv.compact)
-                    score_task<true>(sxy, sz, n, Lv, m, r0, r1, r2, tx - off - Lv.base[0], ty - off - Lv.base[1],
-                                     tz - off - Lv.base[2], acc0, acc1);
-                else
-                    score_task<false>(sxy, sz, n, Lv, m, r0, r1, r2, tx - off, ty - off, tz - off, acc0, acc1);
-                // 16-bit fields: at most 8 points per thread x 32 lanes, x 8 warps, per field
-                uint32_t e0 = acc0 & 0x00FF00FFu, o0 = (acc0 >> 8) & 0x00FF00FFu;
-                uint32_t e1 = acc1 & 0x00FF00FFu, o1 = (acc1 >> 8) & 0x00FF00FFu;
-                e0 = __reduce_add_sync(0xffffffffu, e0);
-                o0 = __reduce_add_sync(0xffffffffu, o0);
-                e1 = __reduce_add_sync(0xffffffffu, e1);
-                o1 = __reduce_add_sync(0xffffffffu, o1);
-                if (lane == 0) {
-                    atomicAdd(&red[tt][0], e0);
-                    atomicAdd(&red[tt][1], o0);
-                    atomicAdd(&red[tt][2], e1);
-                    atomicAdd(&red[tt][3], o1);
-                }
+    for (;;) {
+        __syncthreads();   // the walk state is current; the previous round's descriptors and partials are consumed
+        if (s_cur >= s_end) {   // uniform: this range is done, take the next grab
+            if (tid == 0) {
+                const unsigned long long seen = *(volatile unsigned long long*)&P->next_slice;
+                const int64_t left = n_slices - n_static - (int64_t)seen;
+                int64_t want = left / (2 * (int64_t)gridDim.x);
+                if (want < GRAB_MIN) want = GRAB_MIN;
+                const int64_t got = n_static + (int64_t)atomicAdd(&P->next_slice, (unsigned long long)want);
+                s_cur = got;
+                s_end = min(got + want, n_slices);
+                s_gi = -1;
             }
-            __syncthreads();   // every warp's partial sums are in
-            for (int i = tid; i < 8 * tb; i += blockDim.x) {
-                // child j = 4 jx + 2 jy + jz of task tt: word (jz ? 2 : 0) + jx, half jy
-                const int tt = i >> 3, j = i & 7;
-                const int jx = j >> 2, jy = (j >> 1) & 1, jz = j & 1;
-                const uint32_t sum = red[tt][(jz ? 2 : 0) + jx];
-                const uint32_t cnt = jy ? (sum >> 16) : (sum & 0xFFFFu);
-                if (cnt) atomicAdd(&dense[g.dense_base + (pi * g.R + t0 + tt) * 8 + j], (int32_t)cnt);
-            }
-            __syncthreads();   // the partials are read before the next round zeroes them
+            __syncthreads();
+            if (s_cur >= s_end) break;   // uniform: every slice is handed out
         }
+        const int64_t s1 = s_end;
+        const int64_t cur = s_cur;
+        int gi = s_gi >= 0 ? s_gi : find_slice_seg(P, cur);
+        const Seg* g = &P->seg[gi];
+        int64_t seg_end = g->first_slice + g->n_tasks * g->nblk;
+        while (cur >= seg_end) {   // the range continues in a later segment
+            g = &P->seg[++gi];
+            seg_end = g->first_slice + g->n_tasks * g->nblk;
+        }
+        const int64_t nt = g->n_tasks;
+        const int nchunk = (g->nblk + 3) >> 2;
+        const int nbl = g->nblk - 4 * (nchunk - 1);   // blocks of the last chunk
+        // seg-relative slices: chunk c holds tasks 0..nt-1 of nbc(c) blocks each
+        const int64_t x0 = cur - g->first_slice, xh = min(s1, seg_end) - g->first_slice;
+        auto tc_of = [&](int64_t x) -> int64_t {   // (chunk * nt + task) of slice x
+            int64_t c = x / (4 * nt);
+            if (c > nchunk - 1) c = nchunk - 1;
+            const int nbc = c < nchunk - 1 ? 4 : nbl;
+            return c * nt + (x - c * 4 * nt) / nbc;
+        };
+        auto tc_first = [&](int64_t v) -> int64_t {   // first slice of (chunk * nt + task) v
+            const int64_t c = v / nt;
+            const int nbc = c < nchunk - 1 ? 4 : nbl;
+            return c * 4 * nt + (v - c * nt) * nbc;
+        };
+        const int64_t v0 = tc_of(x0), vh = tc_of(xh - 1);
+        const int nrun = (int)(vh - v0 + 1 < NRUN ? vh - v0 + 1 : NRUN);
+        const int64_t xe = v0 + nrun <= vh ? tc_first(v0 + nrun) : xh;   // this round ends at slice xe
+        if (tid < nrun) {
+            const SearchDev& S = Sall[g->sid];
+            const int64_t v = v0 + tid;
+            const int64_t c = v / nt, u = v - c * nt;
+            const int nbc = c < nchunk - 1 ? 4 : nbl;
+            const int64_t rs = c * 4 * nt + u * nbc;
+            int m;
+            uint32_t crot;
+            int32_t tx, ty, tz;
+            if (MODE == MODE_INITIAL) {
+                virtual_parent(S, g->first_parent + u / g->R, tx, ty, tz);
+                tx *= 2;
+                ty *= 2;
+                tz *= 2;
+                crot = (uint32_t)(u % g->R);
+                m = S.lmax;
+            } else {
+                const TaskRec tr = tasks[g->first_task + u];
+                const NodeRec par = parents[tr.parent];
+                m = rl_level(tr.rl);
+                crot = rl_rot(tr.rl);
+                tx = 2 * par.cx;
+                ty = 2 * par.cy;
+                tz = 2 * par.cz;
+            }
+            const LevelView& L = S.maps[m];
+            const int32_t off = 0x4B400000 >> m;   // the floor offset after the level shift
+            const bool cmp = L.compact != 0;
+            RunDesc& d = rd[tid];
+            d.kc[0] = tx - off - (cmp ? L.base[0] : 0);
+            d.kc[1] = ty - off - (cmp ? L.base[1] : 0);
+            d.kc[2] = tz - off - (cmp ? L.base[2] : 0);
+            const float4* A = S.rot + 3 * (S.grid.rot_off[m] + (int64_t)crot);
+            const float4 a0 = __ldg(A), a1 = __ldg(A + 1), a2 = __ldg(A + 2);
+            d.a[0] = pk2(a0.x, a0.x);
+            d.a[1] = pk2(a0.y, a0.y);
+            d.a[2] = pk2(a0.z, a0.z);
+            d.a[3] = pk2(a1.x, a1.x);
+            d.a[4] = pk2(a1.y, a1.y);
+            d.a[5] = pk2(a1.z, a1.z);
+            d.a[6] = pk2(a2.x, a2.x);
+            d.a[7] = pk2(a2.y, a2.y);
+            d.a[8] = pk2(a2.z, a2.z);
+            d.m = m;
+            d.c = (int32_t)c;
+            d.sid = g->sid;
+            d.b0 = (int32_t)(max(rs, x0) - rs);
+            d.b1 = (int32_t)(min(rs + nbc, xe) - rs);
+            d.task = g->first_task + u;
+        }
+        if (tid == 0) {
+            s_nrun = nrun;
+            s_next = g->first_slice + xe;
+            s_gi = gi;
+        }
+        __syncthreads();   // descriptors visible
+        for (int r = 0; r < s_nrun; ++r) {
+            const RunDesc& d = rd[r];
+            const SearchDev& S = Sall[d.sid];
+            if (d.sid != s_staged_sid || d.c != s_staged_c) {   // uniform
+                __syncthreads();   // the previous chunk's readers are done
+                const int32_t k0 = d.c * PCHUNK;
+                const int32_t n = min(PCHUNK, S.K - k0);
+                for (int i = tid; i < n; i += blockDim.x) {
+                    const float4 p = __ldg(S.scan + k0 + i);
+                    const int j = i >> 1, h = i & 1;
+                    fxy[4 * j + h] = p.x;
+                    fxy[4 * j + 2 + h] = p.y;
+                    fz[2 * j + h] = p.z;
+                }
+                __syncthreads();   // every thread has compared against the old chunk
+                if (tid == 0) {
+                    s_staged_sid = d.sid;
+                    s_staged_c = d.c;
+                }
+                __syncthreads();   // staged points and the new chunk tag visible
+            }
+            const int m = d.m;
+            const LevelView Lv = S.maps[m];
+            const Row2 r0{d.a[0], d.a[1], d.a[2]};
+            const Row2 r1{d.a[3], d.a[4], d.a[5]};
+            const Row2 r2{d.a[6], d.a[7], d.a[8]};
+            const int n = min(PCHUNK, S.K - d.c * PCHUNK);
+            const int jlo = d.b0 * (PBLK / 2), jhi = min(d.b1 * (PBLK / 2), (n + 1) >> 1);
+            uint32_t acc0 = 0, acc1 = 0;   // bytes: children (0,4,2,6) and (1,5,3,7)
+            if (Lv.compact)
+                score_run<true>(sxy, sz, n, jlo, jhi, Lv, m, r0, r1, r2, d.kc[0], d.kc[1], d.kc[2], acc0, acc1);
+            else
+                score_run<false>(sxy, sz, n, jlo, jhi, Lv, m, r0, r1, r2, d.kc[0], d.kc[1], d.kc[2], acc0, acc1);
+            // 16-bit fields: at most 8 points per thread x 32 lanes, x 8 warps, per field
+            uint32_t e0 = acc0 & 0x00FF00FFu, o0 = (acc0 >> 8) & 0x00FF00FFu;
+            uint32_t e1 = acc1 & 0x00FF00FFu, o1 = (acc1 >> 8) & 0x00FF00FFu;
+            e0 = __reduce_add_sync(0xffffffffu, e0);
+            o0 = __reduce_add_sync(0xffffffffu, o0);
+            e1 = __reduce_add_sync(0xffffffffu, e1);
+            o1 = __reduce_add_sync(0xffffffffu, o1);
+            if (lane == 0) {
+                if (e0) atomicAdd(&red[r][0], e0);
+                if (o0) atomicAdd(&red[r][1], o0);
+                if (e1) atomicAdd(&red[r][2], e1);
+                if (o1) atomicAdd(&red[r][3], o1);
+            }
+        }
+        __syncthreads();   // every warp's partial sums are in
+        for (int w = tid; w < 4 * s_nrun; w += blockDim.x) {
+            // word k of a run: children with jx = k & 1, jz = k >> 1; low half jy = 0, high half jy = 1
+            const int r = w >> 2, k = w & 3;
+            const uint32_t sum = red[r][k];
+            if (!sum) continue;
+            red[r][k] = 0u;
+            int32_t* dd = dense + rd[r].task * 8 + 4 * (k & 1) + (k >> 1);
+            if (sum & 0xFFFFu) atomicAdd(dd, (int32_t)(sum & 0xFFFFu));
+            if (sum >> 16) atomicAdd(dd + 2, (int32_t)(sum >> 16));
+        }
+        if (tid == 0) s_cur = s_next;
     }
 }
 
@@ -268,12 +369,13 @@ __global__ void __launch_bounds__(256, 5) branch2_kernel(const Plan* __restrict_
 // histograms (count, children, leaves) for the frontier insertion
 template <int MODE>
 __global__ void __launch_bounds__(256) finalize_kernel(const Plan* __restrict__ P, SearchDev* S,
-                                                       const NodeRec* __restrict__ parents, int32_t* dense, SurvOut out)
+                                                       const NodeRec* __restrict__ parents,
+                                                       const TaskRec* __restrict__ tasks, int32_t* dense, SurvOut out)
 {
     if (P->status != PLAN_OK) return;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t n_dense = P->n_dense;
+    const int64_t n_dense = P->n_tasks * 8;
     const int64_t n_round = (n_dense + 31) & ~(int64_t)31;
     for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < n_round; d += stride) {
         bool surv = false;
@@ -284,45 +386,33 @@ __global__ void __launch_bounds__(256) finalize_kernel(const Plan* __restrict__ 
         int m = 0;
         uint32_t crot = 0;
         if (d < n_dense) {
-            const Seg g = P->seg[find_dense_seg(P, d)];
+            const int64_t u = d >> 3;
+            const int j = (int)(d & 7);
+            const Seg g = P->seg[find_task_seg(P, u)];
             sid = g.sid;
             const SearchDev& s = S[sid];
-            const int64_t local = d - g.dense_base;
-            const int64_t per = (int64_t)g.R * 8;
-            const int64_t pi = local / per;
-            const int32_t rem = (int32_t)(local - pi * per);
-            const int32_t t = rem >> 3, j = rem & 7;
-            bool valid = pi < g.n_parents;
-            int32_t tx = 0, ty = 0, tz = 0;
-            if (valid && MODE == MODE_INITIAL) {
-                const int64_t vp = g.first_parent + pi;
-                const int32_t pz = (int32_t)(vp % s.pext[2]);
-                const int32_t py = (int32_t)((vp / s.pext[2]) % s.pext[1]);
-                const int32_t px = (int32_t)(vp / ((int64_t)s.pext[2] * s.pext[1]));
-                tx = 2 * (s.pmin[0] + px) + (j >> 2);
-                ty = 2 * (s.pmin[1] + py) + ((j >> 1) & 1);
-                tz = 2 * (s.pmin[2] + pz) + (j & 1);
+            bool valid = true;
+            int32_t tx, ty, tz;
+            if (MODE == MODE_INITIAL) {
+                const int64_t lu = u - g.first_task;
+                virtual_parent(s, g.first_parent + lu / g.R, tx, ty, tz);
+                tx = 2 * tx + (j >> 2);
+                ty = 2 * ty + ((j >> 1) & 1);
+                tz = 2 * tz + (j & 1);
                 valid = tx >= s.wmin[0] && tx <= s.wmax[0] && ty >= s.wmin[1] && ty <= s.wmax[1] && tz >= s.wmin[2] &&
                         tz <= s.wmax[2];
                 m = s.lmax;
-                crot = (uint32_t)t;
-            } else if (valid) {
-                const NodeRec par = parents[g.first_parent + pi];
-                const int l = rl_level(par.rl);
-                m = l - 1;
-                int32_t lo[3], ext[3];
-                parent_ranges(s.grid, l, rl_rot(par.rl), lo, ext);
-                valid = m >= 0 && t < ext[0] * ext[1] * ext[2];
-                if (valid) {
-                    const int32_t ja = t / (ext[1] * ext[2]), jb = (t / ext[2]) % ext[1], jg = t % ext[2];
-                    crot = (uint32_t)(((int64_t)(lo[0] + ja) * s.grid.N[m][1] + (lo[1] + jb)) * s.grid.N[m][2] +
-                                      (lo[2] + jg));
-                    tx = 2 * par.cx + (j >> 2);
-                    ty = 2 * par.cy + ((j >> 1) & 1);
-                    tz = 2 * par.cz + (j & 1);
-                }
+                crot = (uint32_t)(lu % g.R);
+            } else {
+                const TaskRec tr = tasks[u];
+                const NodeRec par = parents[tr.parent];
+                m = rl_level(tr.rl);
+                crot = rl_rot(tr.rl);
+                tx = 2 * par.cx + (j >> 2);
+                ty = 2 * par.cy + ((j >> 1) & 1);
+                tz = 2 * par.cz + (j & 1);
             }
-            // the dense array must be zero for the next round: consume it
+            // the dense array must be zero for the next launch: consume it
             const int32_t dv = dense[d];
             if (dv) dense[d] = 0;
             if (valid) {
@@ -342,37 +432,39 @@ __global__ void __launch_bounds__(256) finalize_kernel(const Plan* __restrict__ 
         const uint32_t key = surv ? (((uint32_t)sid << 24) | (uint32_t)score) : 0xFFFFFFFFu;
         const uint32_t peers = __match_any_sync(0xffffffffu, key);
         if (surv) {
+            SearchDev& s = S[sid];
+            const int64_t kids = node_children(s.grid, m, crot);
             const unsigned long long pos = base + __popc(ball & ((1u << lane) - 1u));
             if (pos < (unsigned long long)out.cap) {
                 out.nodes[pos] = nd;
                 out.scores[pos] = score;
                 out.sid[pos] = sid;
+                out.ntask[pos] = (int32_t)(kids >> 3);
             } else {
                 atomicOr(out.err, 2);
             }
-            SearchDev& s = S[sid];
             if ((__ffs(peers) - 1) == lane) atomicAdd(&s.h_cnt[score], (uint32_t)__popc(peers));
-            atomicAdd(&s.h_kids[score], (unsigned long long)node_children(s.grid, m, crot));
+            atomicAdd(&s.h_kids[score], (unsigned long long)kids);
             if (m == 0) atomicAdd(&s.h_leaf[score], 1u);
         }
     }
 }
 
-cudaError_t launch_branch(int mode, const Plan* P, const SearchDev* S, const NodeRec* parents, int32_t* dense,
-                          int blocks, cudaStream_t st)
+cudaError_t launch_branch(int mode, Plan* P, const SearchDev* S, const NodeRec* parents, const TaskRec* tasks,
+                          int32_t* dense, int blocks, cudaStream_t st)
 {
     if (blocks <= 0) return cudaSuccess;
-    if (mode == MODE_INITIAL) branch2_kernel<MODE_INITIAL><<<blocks, 256, 0, st>>>(P, S, parents, dense);
-    else branch2_kernel<MODE_SEARCH><<<blocks, 256, 0, st>>>(P, S, parents, dense);
+    if (mode == MODE_INITIAL) branch3_kernel<MODE_INITIAL><<<blocks, 256, 0, st>>>(P, S, parents, tasks, dense);
+    else branch3_kernel<MODE_SEARCH><<<blocks, 256, 0, st>>>(P, S, parents, tasks, dense);
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(int mode, const Plan* P, SearchDev* S, const NodeRec* parents, int32_t* dense,
-                            const SurvOut& out, int blocks, cudaStream_t st)
+cudaError_t launch_finalize(int mode, const Plan* P, SearchDev* S, const NodeRec* parents, const TaskRec* tasks,
+                            int32_t* dense, const SurvOut& out, int blocks, cudaStream_t st)
 {
     if (blocks <= 0) return cudaSuccess;
-    if (mode == MODE_INITIAL) finalize_kernel<MODE_INITIAL><<<blocks, 256, 0, st>>>(P, S, parents, dense, out);
-    else finalize_kernel<MODE_SEARCH><<<blocks, 256, 0, st>>>(P, S, parents, dense, out);
+    if (mode == MODE_INITIAL) finalize_kernel<MODE_INITIAL><<<blocks, 256, 0, st>>>(P, S, parents, tasks, dense, out);
+    else finalize_kernel<MODE_SEARCH><<<blocks, 256, 0, st>>>(P, S, parents, tasks, dense, out);
     return cudaGetLastError();
 }
 

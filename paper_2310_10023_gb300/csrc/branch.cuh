@@ -10,7 +10,9 @@ namespace bbs {
 
 constexpr int CH = 256;        // nodes per frontier chunk
 constexpr int PCHUNK = 2048;   // scan points staged in shared memory per CTA
-constexpr int MAXSEG = 256;    // parent runs per scoring launch
+constexpr int PBLK = 512;      // scan points per slice (one point pair per thread of a 256-thread CTA)
+constexpr int MAXSEG = 256;    // task runs per scoring launch
+constexpr int64_t TASK_CAP = (int64_t)1 << 19;   // rotational-child tasks per scoring launch
 
 struct ScoreArgs {
     LevelView maps[MAX_LEVELS];
@@ -37,7 +39,8 @@ struct Ctl {
     int64_t n_pop;         // chunks popped by the last select
     int64_t n_act;         // chunks in use
     int64_t popped_kids;   // children of the parents popped by the last select
-    int32_t err;           // 1 pool exhausted
+    int64_t n_tasks;       // rotational-child tasks of those parents (popped_kids / 8)
+    int32_t err;           // 1 pool exhausted, 4 inconsistent task counts
     int32_t reason;        // last select: 1 batch full, 2 below best, 3 leaf, 4 F emptied, 0 F was empty
     int32_t match_changed;
     int32_t active;        // slot in use
@@ -53,8 +56,8 @@ struct SearchDev {
     int32_t K;
     int32_t lmax;
     int64_t batch;
-    int32_t rmax;               // dense task slots per parent (most rotational children)
-    int32_t chunks;             // point chunks per parent
+    int32_t nblk;               // PBLK-point blocks of the scan
+    int32_t pad0;
     int32_t pmin[3], pext[3];   // virtual parents of the initial set
     int32_t wmin[3], wmax[3];   // initial translation window, Eq. (3)-(5)
     DevGrid grid;
@@ -73,7 +76,8 @@ struct SearchDev {
     int32_t* w_fill0;
     int32_t* act;
     int32_t* pop_ids;
-    int64_t* pop_start;
+    int64_t* pop_start;         // parent offset of each popped chunk in the search's parents
+    int64_t* pop_tstart;        // task offset of each popped chunk in the search's tasks
     Ctl* ctl;                   // this search's control block (contiguous across searches)
 };
 
@@ -82,6 +86,7 @@ struct PoolDev {
     NodeRec* nodes;
     int32_t* chunk_bucket;
     int32_t* chunk_fill;
+    int32_t* chunk_tasks;       // rotational-child tasks of the chunk's nodes
     int32_t* free_ids;
     unsigned long long* free_top;
     int64_t nchunks;
@@ -89,28 +94,41 @@ struct PoolDev {
 
 enum { MODE_INITIAL = 0, MODE_SEARCH = 1, MODE_DENSE = 2 };
 
-// A run of parents of one search inside a scoring launch.
+// One rotational child of a scoring round: its parent (index into the
+// round's parent array) and rl_pack(child rotation, child level).  Its 8
+// translational children are the dense scores 8 * task .. 8 * task + 7.
+struct TaskRec {
+    int32_t parent;
+    uint32_t rl;
+};
+
+// A run of tasks of one search inside a scoring launch.  The run's work is
+// split into slices (task, PBLK-point block of the scan), ordered by point
+// chunk, then task, then block, so that consecutive slices reuse the staged
+// chunk; each CTA of the launch takes an equal contiguous range of slices.
 struct Seg {
-    int64_t first_parent;   // into the parent array, or the first virtual parent (initial set)
-    int64_t first_work;     // first (parent, point chunk) work item
-    int64_t n_parents;
-    int64_t dense_base;     // first dense child-score slot of the run
-    int32_t chunks;         // point chunks per parent
+    int64_t first_parent;   // initial set: first virtual parent of the run
+    int64_t first_task;     // launch-local index of the run's first task
+    int64_t n_tasks;
+    int64_t first_slice;    // launch-local index of the run's first slice
     int32_t sid;
-    int32_t R;              // dense task slots per parent
+    int32_t nblk;           // PBLK-point blocks of the search's scan
+    int32_t R;              // initial set: rotations per virtual parent
     int32_t pad;
 };
 
-enum { PLAN_OK = 0, PLAN_EMPTY = 1, PLAN_OVERFLOW = 2 };
+enum { PLAN_OK = 0, PLAN_EMPTY = 1, PLAN_OVERFLOW = 2, PLAN_SPLIT = 3 };
 
-// The plan of one scoring round, in device memory: written by the host (host
-// path) or by plan_kernel (device-driven iterations).
+// The plan of one scoring launch, in device memory: written by the host (host
+// path) or by plan_kernel (device-driven iterations).  PLAN_SPLIT marks a
+// round gathered whole but scored in several host-planned launches.
 struct Plan {
-    int64_t n_work;          // (parent, point chunk) work items
-    int64_t n_dense;         // dense (parent, task, child) score slots, at most the dense capacity
+    int64_t n_slices;
+    int64_t n_tasks;         // dense child scores: 8 per task, at most 8 * TASK_CAP
+    unsigned long long next_slice;   // dynamic share: the next slice not yet handed out (0 at launch)
     int32_t nseg;
     int32_t mode;
-    int32_t status;          // PLAN_*: the kernels of a round run only when PLAN_OK
+    int32_t status;          // PLAN_*: the scoring kernels of a round run only when PLAN_OK
     int32_t iters;           // iterations of the current device-driven loop
     int32_t max_iters;       // the device-driven loop stops after this many
     int32_t pad;
@@ -122,16 +140,43 @@ struct SurvOut {
     NodeRec* nodes;
     int32_t* scores;
     int32_t* sid;
+    int32_t* ntask;         // rotational children of the survivor
     unsigned long long* count;
     int64_t cap;
     int* err;
 };
 
-// scoring and survivor kernels of one round; `blocks` is the grid (the
-// kernels stride over the plan's work), each skips unless the plan is PLAN_OK
-cudaError_t launch_branch(int mode, const Plan* P, const SearchDev* S, const NodeRec* parents, int32_t* dense,
-                          int blocks, cudaStream_t st);
-cudaError_t launch_finalize(int mode, const Plan* P, SearchDev* S, const NodeRec* parents, int32_t* dense,
-                            const SurvOut& out, int blocks, cudaStream_t st);
+// rotational children of a node at level l with rotation index rot, Eq. (13):
+// first child and count per axis at level l - 1; their number (0 at the leaf level)
+__host__ __device__ __forceinline__ int32_t rot_children(const DevGrid& g, int l, uint32_t rot, int32_t lo[3],
+                                                         int32_t ext[3])
+{
+    if (l <= 0) {
+        for (int i = 0; i < 3; ++i) lo[i] = ext[i] = 0;
+        return 0;
+    }
+    const uint32_t ng = (uint32_t)g.N[l][2], nb = (uint32_t)g.N[l][1];
+    const int32_t c[3] = {(int32_t)(rot / (ng * nb)), (int32_t)((rot / ng) % nb), (int32_t)(rot % ng)};
+    int32_t n = 1;
+    for (int i = 0; i < 3; ++i) {
+        int32_t a, b;
+        child_range(g, l, i, c[i], a, b);
+        lo[i] = a;
+        ext[i] = b - a;
+        n *= b - a;
+    }
+    return n;
+}
+
+// CTAs of a scoring launch: one resident wave (4 CTAs of 256 threads per SM, 64 registers a thread)
+constexpr int BRANCH_CTAS_PER_SM = 4;
+
+// scoring and survivor kernels of one launch; `blocks` is the grid (the
+// scoring kernel splits the plan's slices evenly over it, the survivor kernel
+// strides), each returns at once unless the plan is PLAN_OK
+cudaError_t launch_branch(int mode, Plan* P, const SearchDev* S, const NodeRec* parents, const TaskRec* tasks,
+                          int32_t* dense, int blocks, cudaStream_t st);
+cudaError_t launch_finalize(int mode, const Plan* P, SearchDev* S, const NodeRec* parents, const TaskRec* tasks,
+                            int32_t* dense, const SurvOut& out, int blocks, cudaStream_t st);
 
 }  // namespace bbs

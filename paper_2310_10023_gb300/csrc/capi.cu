@@ -257,7 +257,6 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
     std::vector<NodeRec> recs((size_t)n);
     std::vector<int32_t> cnt((size_t)n), lo((size_t)(3 * n)), ext((size_t)(3 * n));
     int64_t total = 0;
-    int rmax = 1;
     for (int64_t p = 0; p < n; ++p) {
         const int32_t* c = &hp[(size_t)(7 * p)];
         const int l = c[6];
@@ -270,24 +269,31 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
         if (!ok) return set_error(BBS_EINVAL, "score_children: parent %lld lies outside the pose grid", (long long)p);
         const uint32_t rot = (uint32_t)(((int64_t)c[3] * g.N[l][1] + c[4]) * g.N[l][2] + c[5]);
         recs[(size_t)p] = NodeRec{c[0], c[1], c[2], rl_pack(rot, l)};
-        int32_t count = 0;
-        if (l > 0) {
-            count = 1;
-            for (int i = 0; i < 3; ++i) {
-                int32_t a0, a1;
-                child_range(dgr, l, i, c[3 + i], a0, a1);
-                lo[(size_t)(3 * p + i)] = a0;
-                ext[(size_t)(3 * p + i)] = a1 - a0;
-                count *= (a1 - a0);
-            }
-        }
+        const int32_t count = rot_children(dgr, l, rot, &lo[(size_t)(3 * p)], &ext[(size_t)(3 * p)]);
         cnt[(size_t)p] = count;
         total += 8 * (int64_t)count;
-        rmax = std::max(rmax, count);
     }
     *n_children = total;
     if (total > cap) return set_error(BBS_EINVAL, "score_children: capacity %lld < %lld children", (long long)cap, (long long)total);
     if (total == 0) return BBS_OK;
+    // the tasks (rotational children) in parent order, child order ja, jb, jg
+    const int64_t ntask = total / 8;
+    std::vector<TaskRec> tk((size_t)ntask);
+    {
+        int64_t u = 0;
+        for (int64_t p = 0; p < n; ++p) {
+            const int l = recs[(size_t)p].rl & 31;
+            const int32_t* plo = &lo[(size_t)(3 * p)];
+            const int32_t* pex = &ext[(size_t)(3 * p)];
+            for (int32_t ja = 0; ja < pex[0]; ++ja)
+                for (int32_t jb = 0; jb < pex[1]; ++jb)
+                    for (int32_t jg = 0; jg < pex[2]; ++jg) {
+                        const uint32_t crot =
+                            (uint32_t)(((int64_t)(plo[0] + ja) * g.N[l - 1][1] + (plo[1] + jb)) * g.N[l - 1][2] + (plo[2] + jg));
+                        tk[(size_t)u++] = TaskRec{(int32_t)p, rl_pack(crot, l - 1)};
+                    }
+        }
+    }
     // one search slot for the fused kernel (no frontier: dense scores only)
     SearchDev sd;
     std::memset(&sd, 0, sizeof(sd));
@@ -295,77 +301,72 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
     sd.rot = S.rot;
     sd.K = (int32_t)k;
     sd.lmax = g.levels - 1;
+    sd.nblk = (int32_t)((k + PBLK - 1) / PBLK);
     sd.grid = dgr;
     for (int l = 0; l < MAX_LEVELS; ++l) sd.maps[l] = l < m->levels ? level_view(m, l) : LevelView{};
     SearchDev* d_sd = nullptr;
     NodeRec* d_par = nullptr;
+    TaskRec* d_tk = nullptr;
     int32_t* d_dense = nullptr;
-    const int64_t items = n * rmax;
+    Plan* d_plan = nullptr;
     BBS_CUDA_TRY(cudaMallocAsync((void**)&d_sd, sizeof(SearchDev), st));
     BBS_CUDA_TRY(cudaMallocAsync((void**)&d_par, sizeof(NodeRec) * (size_t)n, st));
-    BBS_CUDA_TRY(cudaMallocAsync((void**)&d_dense, sizeof(int32_t) * 8 * (size_t)items, st));
+    BBS_CUDA_TRY(cudaMallocAsync((void**)&d_tk, sizeof(TaskRec) * (size_t)ntask, st));
+    BBS_CUDA_TRY(cudaMallocAsync((void**)&d_dense, sizeof(int32_t) * (size_t)total, st));
+    BBS_CUDA_TRY(cudaMallocAsync((void**)&d_plan, sizeof(Plan), st));
+    Plan P;
+    std::memset(&P, 0, sizeof(P));
+    P.mode = MODE_SEARCH;
+    P.status = PLAN_OK;
+    P.nseg = 1;
+    P.n_tasks = ntask;
+    P.n_slices = ntask * sd.nblk;
+    P.seg[0].first_task = 0;
+    P.seg[0].n_tasks = ntask;
+    P.seg[0].first_slice = 0;
+    P.seg[0].sid = 0;
+    P.seg[0].nblk = sd.nblk;
     BBS_CUDA_TRY(cudaMemcpyAsync(d_sd, &sd, sizeof(sd), cudaMemcpyHostToDevice, st));
     BBS_CUDA_TRY(cudaMemcpyAsync(d_par, recs.data(), sizeof(NodeRec) * (size_t)n, cudaMemcpyHostToDevice, st));
-    BBS_CUDA_TRY(cudaMemsetAsync(d_dense, 0, sizeof(int32_t) * 8 * (size_t)items, st));
+    BBS_CUDA_TRY(cudaMemcpyAsync(d_tk, tk.data(), sizeof(TaskRec) * tk.size(), cudaMemcpyHostToDevice, st));
+    BBS_CUDA_TRY(cudaMemcpyAsync(d_plan, &P, offsetof(Plan, seg) + sizeof(Seg), cudaMemcpyHostToDevice, st));
+    BBS_CUDA_TRY(cudaMemsetAsync(d_dense, 0, sizeof(int32_t) * (size_t)total, st));
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     int rc = BBS_OK;
-    const int chunks = (int)((k + PCHUNK - 1) / PCHUNK);
-    Plan* d_plan = nullptr;
-    BBS_CUDA_TRY(cudaMallocAsync((void**)&d_plan, sizeof(Plan), st));
-    std::vector<Plan> plans;
-    // parents in runs of at most 2^20 per segment, at most MAXSEG segments per launch
-    for (int64_t p0 = 0; rc == BBS_OK && p0 < n && chunks > 0; p0 += ((int64_t)MAXSEG << 20)) {
-        Plan P;
-        std::memset(&P, 0, sizeof(P));
-        P.mode = MODE_SEARCH;
-        P.status = PLAN_OK;
-        int64_t work = 0;
-        for (int64_t q = p0; q < n && P.nseg < MAXSEG; q += ((int64_t)1 << 20)) {
-            Seg& sg = P.seg[P.nseg++];
-            sg.first_parent = q;
-            sg.first_work = work;
-            sg.n_parents = std::min<int64_t>((int64_t)1 << 20, n - q);
-            sg.dense_base = q * rmax * 8;
-            sg.chunks = chunks;
-            sg.sid = 0;
-            sg.R = rmax;
-            work += sg.n_parents * chunks;
-        }
-        P.n_work = work;
-        cudaError_t e = cudaMemcpyAsync(d_plan, &P, sizeof(P), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = launch_branch(MODE_SEARCH, d_plan, d_sd, d_par, d_dense, (int)std::min<int64_t>(work, 152 * 64), st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // P is reused by the next launch
-        if (e != cudaSuccess) rc = set_error(BBS_ECUDA, "score_children: %s", cudaGetErrorString(e));
-    }
+    cudaError_t e = launch_branch(MODE_SEARCH, d_plan, d_sd, d_par, d_tk, d_dense,
+                                  (int)std::min<int64_t>(P.n_slices, (int64_t)nsm * BRANCH_CTAS_PER_SM), st);
+    std::vector<int32_t> dense((size_t)total);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dense.data(), d_dense, sizeof(int32_t) * dense.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // the host copies of P and the tasks outlive their transfers
+    if (e != cudaSuccess) rc = set_error(BBS_ECUDA, "score_children: %s", cudaGetErrorString(e));
     cudaFreeAsync(d_plan, st);
-    std::vector<int32_t> dense((size_t)(8 * items));
-    if (rc == BBS_OK) {
-        cudaError_t e = cudaMemcpyAsync(dense.data(), d_dense, sizeof(int32_t) * dense.size(), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) rc = set_error(BBS_ECUDA, "score_children: %s", cudaGetErrorString(e));
-    }
     cudaFreeAsync(d_sd, st);
     cudaFreeAsync(d_par, st);
+    cudaFreeAsync(d_tk, st);
     cudaFreeAsync(d_dense, st);
     if (rc != BBS_OK) return rc;
     std::vector<int32_t> on((size_t)(7 * total)), os((size_t)total);
     int64_t o = 0;
-    for (int64_t p = 0; p < n; ++p) {
-        const int32_t* c = &hp[(size_t)(7 * p)];
-        const int32_t nb = ext[(size_t)(3 * p + 1)], ng = ext[(size_t)(3 * p + 2)];
-        for (int32_t j = 0; j < cnt[(size_t)p]; ++j) {
-            const int32_t ja = j / (nb * ng), jb = (j / ng) % nb, jg = j % ng;
-            for (int t = 0; t < 8; ++t) {
-                int32_t* d = &on[(size_t)(7 * o)];
-                d[0] = 2 * c[0] + (t >> 2);
-                d[1] = 2 * c[1] + ((t >> 1) & 1);
-                d[2] = 2 * c[2] + (t & 1);
-                d[3] = lo[(size_t)(3 * p)] + ja;
-                d[4] = lo[(size_t)(3 * p + 1)] + jb;
-                d[5] = lo[(size_t)(3 * p + 2)] + jg;
-                d[6] = c[6] - 1;
-                os[(size_t)o] = dense[(size_t)(8 * (p * rmax + j) + t)];
-                ++o;
-            }
+    for (int64_t u = 0; u < ntask; ++u) {
+        const TaskRec& r = tk[(size_t)u];
+        const int32_t* c = &hp[(size_t)(7 * r.parent)];
+        const int l = c[6];
+        const uint32_t crot = rl_rot(r.rl);
+        const int32_t ng = g.N[l - 1][2], nb = g.N[l - 1][1];
+        for (int t = 0; t < 8; ++t) {
+            int32_t* d = &on[(size_t)(7 * o)];
+            d[0] = 2 * c[0] + (t >> 2);
+            d[1] = 2 * c[1] + ((t >> 1) & 1);
+            d[2] = 2 * c[2] + (t & 1);
+            d[3] = (int32_t)(crot / (uint32_t)(ng * nb));
+            d[4] = (int32_t)((crot / (uint32_t)ng) % (uint32_t)nb);
+            d[5] = (int32_t)(crot % (uint32_t)ng);
+            d[6] = l - 1;
+            os[(size_t)o] = dense[(size_t)(8 * u + t)];
+            ++o;
         }
     }
     if (is_device) {

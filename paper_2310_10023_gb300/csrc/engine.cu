@@ -30,7 +30,7 @@
 
 namespace bbs {
 
-// ---- block helpers (1024 threads) ------------------------------------------
+// ---- block helpers (blocks of whole warps) ----------------------------------
 
 __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t* total, int64_t* sh)
 {
@@ -42,8 +42,9 @@ __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t* total, in
     }
     if (lane == 31) sh[wid] = x;
     __syncthreads();
+    const int nw = (int)(blockDim.x >> 5);
     if (wid == 0) {
-        int64_t s = sh[lane];
+        int64_t s = lane < nw ? sh[lane] : 0;
         for (int o = 1; o < 32; o <<= 1) {
             const int64_t y = __shfl_up_sync(0xffffffffu, s, o);
             if (lane >= o) s += y;
@@ -52,7 +53,7 @@ __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t* total, in
     }
     __syncthreads();
     const int64_t before = (wid > 0 ? sh[wid - 1] : 0) + x - v;
-    *total = sh[31];
+    *total = sh[nw - 1];
     __syncthreads();
     return before;
 }
@@ -106,6 +107,7 @@ __global__ void pool_init_kernel(PoolDev p)
         p.free_ids[i] = (int32_t)(p.nchunks - 1 - i);
         p.chunk_bucket[i] = -1;
         p.chunk_fill[i] = 0;
+        p.chunk_tasks[i] = 0;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *p.free_top = (unsigned long long)p.nchunks;
 }
@@ -191,6 +193,7 @@ __global__ void __launch_bounds__(1024) alloc_kernel(SearchDev* S, int nslots, P
                     const int32_t id = pool.free_ids[claim_top - 1 - (off + i)];
                     pool.chunk_bucket[id] = s;
                     pool.chunk_fill[id] = (int32_t)(i < need - 1 ? CH : ((int64_t)h - space) - (need - 1) * CH);
+                    pool.chunk_tasks[id] = 0;
                     f.act[act0 + off + i] = id;
                     last = id;
                 }
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(1024) alloc_kernel(SearchDev* S, int nslots, P
 
 __global__ void scatter_kernel(SearchDev* S, PoolDev pool, const NodeRec* __restrict__ nodes,
                                const int32_t* __restrict__ scores, const int32_t* __restrict__ sids,
-                               const unsigned long long* count, int64_t cap)
+                               const int32_t* __restrict__ ntask, const unsigned long long* count, int64_t cap)
 {
     int64_t n = (int64_t)*count;
     if (n > cap) n = cap;
@@ -246,6 +249,7 @@ __global__ void scatter_kernel(SearchDev* S, PoolDev pool, const NodeRec* __rest
             slot = (int32_t)(idx % CH);
         }
         pool.nodes[(int64_t)chunk * CH + slot] = nodes[i];
+        if (ntask[i]) atomicAdd(&pool.chunk_tasks[chunk], ntask[i]);
     }
 }
 
@@ -301,7 +305,7 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
         my_node.rl = 0;
         int my_has = 0;
         const int64_t n_act = c->n_act;
-        int64_t keep = 0, npop = 0, nfree = 0, nparents = 0;
+        int64_t keep = 0, npop = 0, nfree = 0, nparents = 0, ntasks = 0;
         // freed chunks go onto the shared stack: count them first, then claim
         int64_t nfree_total = 0;
         if (clear) {
@@ -321,6 +325,7 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
             const int32_t ch = i < n_act ? f.act[i] : -1;
             const int32_t bk = ch >= 0 ? pool.chunk_bucket[ch] : -1;
             const int32_t fill = ch >= 0 ? pool.chunk_fill[ch] : 0;
+            const int32_t ctasks = ch >= 0 ? pool.chunk_tasks[ch] : 0;
             const bool popped = ch >= 0 && bk > sstar;
             const bool freed = ch >= 0 && !popped && clear;
             const bool kept = ch >= 0 && !popped && !clear;
@@ -336,14 +341,16 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
                     }
                 }
             }
-            int64_t t1, t2, t3, t4;
+            int64_t t1, t2, t3, t4, t5;
             const int64_t rp = block_excl_scan(popped ? 1 : 0, &t1, sh);
             const int64_t rf = block_excl_scan(freed ? 1 : 0, &t2, sh);
             const int64_t rk = block_excl_scan(kept ? 1 : 0, &t3, sh);
             const int64_t rs = block_excl_scan(popped ? fill : 0, &t4, sh);
+            const int64_t rt = block_excl_scan(popped ? ctasks : 0, &t5, sh);
             if (popped) {
                 f.pop_ids[npop + rp] = ch;
                 f.pop_start[npop + rp] = nparents + rs;
+                f.pop_tstart[npop + rp] = ntasks + rt;
                 pool.chunk_bucket[ch] = -2;
             }
             if (freed) {
@@ -356,6 +363,7 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
             nfree += t2;
             keep += t3;
             nparents += t4;
+            ntasks += t5;
             __syncthreads();
         }
         // 3. lexmin leaf across the block
@@ -390,6 +398,7 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
         if (tid == 0) {
             c->n_pop = npop;
             c->n_parents = nparents;
+            c->n_tasks = ntasks;
             c->popped_kids = pk;
             c->n_act = keep;
             c->size = clear ? 0 : c->size - nparents;
@@ -440,11 +449,40 @@ __global__ void slot_release_kernel(SearchDev* S, int slot, PoolDev pool)
     }
 }
 
-// popped chunks of every search -> the dense parent array at the search's offset
-__global__ void gather_kernel(SearchDev* S, PoolDev pool, const int64_t* __restrict__ poff, int nslots,
-                              NodeRec* __restrict__ parents, const Plan* P)
+// the tasks (rotational children, Eq. (13)) of parent p, written at tasks[dst
+// + t] for the t in [t0, t1)
+__device__ __forceinline__ void write_tasks(const DevGrid& g, const NodeRec& nd, int64_t p, const int32_t lo[3],
+                                            const int32_t ext[3], int32_t t0, int32_t t1, TaskRec* tasks, int64_t dst)
 {
-    if (P->status != PLAN_OK) return;
+    const int l = rl_level(nd.rl);
+    const int64_t nb = g.N[l - 1][1], ng = g.N[l - 1][2];
+    int32_t t = 0;
+    for (int32_t ja = 0; ja < ext[0]; ++ja)
+        for (int32_t jb = 0; jb < ext[1]; ++jb)
+            for (int32_t jg = 0; jg < ext[2]; ++jg, ++t) {
+                if (t < t0 || t >= t1) continue;
+                const uint32_t crot = (uint32_t)(((int64_t)(lo[0] + ja) * nb + (lo[1] + jb)) * ng + (lo[2] + jg));
+                TaskRec r;
+                r.parent = (int32_t)p;
+                r.rl = rl_pack(crot, l - 1);
+                tasks[dst + t] = r;
+            }
+}
+
+// popped chunks of every search -> the parent array at the search's offset,
+// each parent's first task (its rotational children are numbered per
+// search in parent order, from toff[search]) and, when the round is scored
+// in one launch (PLAN_OK), the task records themselves.  One CTA of CH
+// threads per popped chunk (one node per thread); the chunks are freed.
+__global__ void __launch_bounds__(CH) gather_kernel(SearchDev* S, PoolDev pool, const int64_t* __restrict__ poff,
+                                                    const int64_t* __restrict__ toff, int nslots,
+                                                    NodeRec* __restrict__ parents, int64_t* __restrict__ pfirst,
+                                                    TaskRec* __restrict__ tasks, const Plan* P)
+{
+    const int status = P->status;
+    if (status != PLAN_OK && status != PLAN_SPLIT) return;
+    __shared__ int64_t sh[32];
+    const int j = threadIdx.x;
     for (int si = blockIdx.y; si < nslots; si += gridDim.y) {
         SearchDev& f = S[si];
         if (!f.ctl->active || f.ctl->err) continue;
@@ -452,10 +490,26 @@ __global__ void gather_kernel(SearchDev* S, PoolDev pool, const int64_t* __restr
         for (int64_t i = blockIdx.x; i < npop; i += gridDim.x) {
             const int32_t ch = f.pop_ids[i];
             const int64_t start = poff[si] + f.pop_start[i];
+            const int64_t tbase = toff[si] + f.pop_tstart[i];
             const int32_t fill = pool.chunk_fill[ch];
-            for (int j = threadIdx.x; j < fill; j += blockDim.x) parents[start + j] = pool.nodes[(int64_t)ch * CH + j];
-            __syncthreads();
-            if (threadIdx.x == 0) {
+            NodeRec nd;
+            int32_t lo[3], ext[3], T = 0;
+            if (j < fill) {
+                nd = pool.nodes[(int64_t)ch * CH + j];
+                T = rot_children(f.grid, rl_level(nd.rl), rl_rot(nd.rl), lo, ext);
+            }
+            int64_t tot;
+            const int64_t first = tbase + block_excl_scan(T, &tot, sh);   // synchronizes: every node is read
+            if (j < fill) {
+                parents[start + j] = nd;
+                pfirst[start + j] = first;
+                if (status == PLAN_OK && T > 0) {
+                    if (first + T <= TASK_CAP) write_tasks(f.grid, nd, start + j, lo, ext, 0, T, tasks, first);
+                    else atomicOr(&f.ctl->err, 4);   // task counts disagree with the nodes: fail the search
+                }
+            }
+            if (j == 0) {
+                if (tot != pool.chunk_tasks[ch]) atomicOr(&f.ctl->err, 4);   // the chunk's task count is stale
                 const unsigned long long pos = atomicAdd(pool.free_top, 1ull);
                 pool.free_ids[pos] = ch;
                 pool.chunk_bucket[ch] = -1;
@@ -464,63 +518,85 @@ __global__ void gather_kernel(SearchDev* S, PoolDev pool, const int64_t* __restr
     }
 }
 
+// the tasks [ga, gb) of one search's round (gathered parents [p0, p1), their
+// first tasks in pfirst) -> tasks[la ..]: a round scored in several launches
+__global__ void expand_kernel(const SearchDev* S, int sid, const NodeRec* __restrict__ parents,
+                              const int64_t* __restrict__ pfirst, int64_t p0, int64_t p1, int64_t ga, int64_t gb,
+                              int64_t la, TaskRec* __restrict__ tasks)
+{
+    const DevGrid& g = S[sid].grid;
+    for (int64_t p = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < p1; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = pfirst[p];
+        if (b >= gb) continue;
+        const NodeRec nd = parents[p];
+        int32_t lo[3], ext[3];
+        const int32_t T = rot_children(g, rl_level(nd.rl), rl_rot(nd.rl), lo, ext);
+        if (b + T <= ga) continue;
+        const int32_t t0 = (int32_t)(ga > b ? ga - b : 0), t1 = (int32_t)(gb < b + T ? gb - b : T);
+        write_tasks(g, nd, p, lo, ext, t0, t1, tasks, la + b - ga);
+    }
+}
+
 // The plan of the next scoring round, built on the device from every live
-// search's popped parents: per-search parent offsets, (parent, point chunk)
-// work ranges and dense score ranges.  It ends the device-driven loop (sets
-// the graph's while condition to 0) when no search popped anything, when the
-// round does not fit the dense capacity or the run table (the host finishes
-// that round), or after P->max_iters iterations.
-__global__ void __launch_bounds__(1024) plan_kernel(SearchDev* S, int nslots, Plan* P, int64_t* poff,
-                                                    unsigned long long* surv_count, int64_t dense_cap,
-                                                    cudaGraphConditionalHandle cond)
+// search's popped parents: per-search parent and task offsets and one task
+// run per search.  It ends the device-driven loop (sets the graph's while
+// condition to 0) when no search popped anything, when the round's tasks do
+// not fit one launch or the run table (the host finishes that round), or after
+// P->max_iters iterations.
+__global__ void __launch_bounds__(1024) plan_kernel(SearchDev* S, int nslots, Plan* P, int64_t* poff, int64_t* toff,
+                                                    unsigned long long* surv_count, cudaGraphConditionalHandle cond)
 {
     __shared__ int64_t sh[32];
     const int tid = threadIdx.x;
     if (tid == 0) *surv_count = 0;
-    int64_t cp = 0, cw = 0, cd = 0, cn = 0;
+    int64_t cp = 0, ct = 0, cs = 0, cn = 0;
     for (int base = 0; base < nslots; base += blockDim.x) {
         const int s = base + tid;
-        int64_t np = 0, w = 0, d = 0, has = 0;
+        int64_t np = 0, nt = 0, sl = 0, has = 0;
         if (s < nslots) {
             const Ctl* c = S[s].ctl;
-            if (c->active && !c->done && !c->err) np = c->n_parents;
-            w = np * S[s].chunks;
-            d = np * S[s].rmax * 8;
-            has = np > 0;
+            if (c->active && !c->done && !c->err) {
+                np = c->n_parents;
+                nt = c->n_tasks;
+            }
+            sl = nt * S[s].nblk;
+            has = nt > 0;
         }
-        int64_t tp, tw, td, tn;
+        int64_t tp, tt, ts, tn;
         const int64_t ep = block_excl_scan(np, &tp, sh);
-        const int64_t ew = block_excl_scan(w, &tw, sh);
-        const int64_t ed = block_excl_scan(d, &td, sh);
+        const int64_t et = block_excl_scan(nt, &tt, sh);
+        const int64_t es = block_excl_scan(sl, &ts, sh);
         const int64_t en = block_excl_scan(has, &tn, sh);
         if (s < nslots) {
             poff[s] = cp + ep;
+            toff[s] = ct + et;
             const int64_t si = cn + en;
             if (has && si < MAXSEG) {
                 Seg& g = P->seg[si];
                 g.first_parent = cp + ep;
-                g.first_work = cw + ew;
-                g.n_parents = np;
-                g.dense_base = cd + ed;
-                g.chunks = S[s].chunks;
+                g.first_task = ct + et;
+                g.n_tasks = nt;
+                g.first_slice = cs + es;
                 g.sid = s;
-                g.R = S[s].rmax;
+                g.nblk = S[s].nblk;
+                g.R = 0;
                 g.pad = 0;
             }
         }
         cp += tp;
-        cw += tw;
-        cd += td;
+        ct += tt;
+        cs += ts;
         cn += tn;
     }
     if (tid == 0) {
         P->nseg = (int32_t)(cn < MAXSEG ? cn : MAXSEG);
-        P->n_work = cw;
-        P->n_dense = cd;
+        P->n_slices = cs;
+        P->n_tasks = ct;
+        P->next_slice = 0;
         P->mode = MODE_SEARCH;
         int st = PLAN_OK;
         if (cp == 0) st = PLAN_EMPTY;
-        else if (cn > MAXSEG || cd > dense_cap) st = PLAN_OVERFLOW;
+        else if (cn > MAXSEG || ct > TASK_CAP) st = PLAN_OVERFLOW;
         P->status = st;
         P->iters += 1;
         if (st != PLAN_OK || P->iters >= P->max_iters) cudaGraphSetConditional(cond, 0);
@@ -556,6 +632,7 @@ Engine::~Engine()
     for (cudaEvent_t e : evs_) cudaEventDestroy(e);
     if (h_ctl_) cudaFreeHost(h_ctl_);
     if (h_poff_) cudaFreeHost(h_poff_);
+    if (h_toff_) cudaFreeHost(h_toff_);
 }
 
 int Engine::init()
@@ -575,19 +652,24 @@ int Engine::init()
     BBS_TRY(get(&pool_.nodes, (size_t)(nchunks_ * CH)));
     BBS_TRY(get(&pool_.chunk_bucket, (size_t)nchunks_));
     BBS_TRY(get(&pool_.chunk_fill, (size_t)nchunks_));
+    BBS_TRY(get(&pool_.chunk_tasks, (size_t)nchunks_));
     BBS_TRY(get(&pool_.free_ids, (size_t)nchunks_));
     BBS_TRY(get(&pool_.free_top, 1));
     pool_.nchunks = nchunks_;
     BBS_TRY(get(&d_S_, (size_t)max_slots_));
     BBS_TRY(get(&d_ctl_, (size_t)max_slots_));
     BBS_TRY(get(&parents_, (size_t)(nchunks_ * CH)));
+    BBS_TRY(get(&pfirst_, (size_t)(nchunks_ * CH)));
+    BBS_TRY(get(&tasks_, (size_t)TASK_CAP));
     BBS_TRY(get(&d_poff_, (size_t)max_slots_));
+    BBS_TRY(get(&d_toff_, (size_t)max_slots_));
     BBS_TRY(get(&d_plan_, 1));
     BBS_TRY(get(&d_slots_, (size_t)max_slots_));
     BBS_TRY(get(&dense_, (size_t)DENSE_CAP));
     BBS_TRY(get(&surv_.nodes, (size_t)DENSE_CAP));
     BBS_TRY(get(&surv_.scores, (size_t)DENSE_CAP));
     BBS_TRY(get(&surv_.sid, (size_t)DENSE_CAP));
+    BBS_TRY(get(&surv_.ntask, (size_t)DENSE_CAP));
     BBS_TRY(get(&surv_.count, 1));
     BBS_TRY(get(&surv_.err, 1));
     surv_.cap = DENSE_CAP;
@@ -599,6 +681,13 @@ int Engine::init()
     BBS_CUDA_TRY(cudaMemsetAsync(dense_, 0, sizeof(int32_t) * (size_t)DENSE_CAP, st_));
     BBS_CUDA_TRY(cudaMallocHost((void**)&h_ctl_, sizeof(Ctl) * (size_t)max_slots_));
     BBS_CUDA_TRY(cudaMallocHost((void**)&h_poff_, sizeof(int64_t) * (size_t)max_slots_));
+    BBS_CUDA_TRY(cudaMallocHost((void**)&h_toff_, sizeof(int64_t) * (size_t)max_slots_));
+    {
+        int dev = 0, nsm = 0;
+        BBS_CUDA_TRY(cudaGetDevice(&dev));
+        BBS_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        if (nsm > 0) nsm_ = nsm;
+    }
     std::memset(h_ctl_, 0, sizeof(Ctl) * (size_t)max_slots_);
     // every slot's record points at its control block even while unused
     std::vector<SearchDev> blank((size_t)max_slots_);
@@ -645,7 +734,7 @@ size_t Engine::estimate_bytes(int64_t k, const HostGrid& g) const
 {
     const size_t K1 = (size_t)k + 1;
     return sizeof(float4) * (size_t)(k > 0 ? k : 1) + sizeof(float4) * 3 * (size_t)g.total_rot + 68 * K1 +
-           16 * (size_t)nchunks_ + 1024;
+           24 * (size_t)nchunks_ + 1024;
 }
 
 int Engine::free_slot() const
@@ -704,15 +793,13 @@ int Engine::add(const bbs_maps* m, const float* xyz, int64_t k, int is_device, c
         return rc;
     }
     const HostGrid& g = h.scan.grid;
-    h.bytes += estimate_bytes(k, g) - (68 * ((size_t)k + 1) + 16 * (size_t)nchunks_ + 1024);
+    h.bytes += estimate_bytes(k, g) - (68 * ((size_t)k + 1) + 24 * (size_t)nchunks_ + 1024);
     h.thr = (int32_t)std::ceil(frac * (double)k);
     h.res.phase_ms[0] = now_ms() - h.t0;
     h.res.h2d_bytes += h.scan.h2d;
     h.res.d2h_bytes += h.scan.d2h;
     h.res.launches += 2;
     if (k == 0) return BBS_OK;   // never live: reported as not found
-    for (int l = 1; l < g.levels; ++l) h.rmax = std::max<int>(h.rmax, (int)(g.a[l][0] * g.a[l][1] * g.a[l][2]));
-    h.chunks = (int)((k + PCHUNK - 1) / PCHUNK);
     SearchDev& d = h.dev;
     std::memset(&d, 0, sizeof(d));
     d.scan = h.scan.scan;
@@ -720,8 +807,7 @@ int Engine::add(const bbs_maps* m, const float* xyz, int64_t k, int is_device, c
     d.K = (int32_t)k;
     d.lmax = g.levels - 1;
     d.batch = (opts && opts->batch > 0) ? opts->batch : 10000;
-    d.rmax = h.rmax;
-    d.chunks = h.chunks;
+    d.nblk = (int32_t)((k + PBLK - 1) / PBLK);
     for (int a = 0; a < 3; ++a) {
         const int64_t pmin = floor_div2(g.wmin[a]), pmax = floor_div2(g.wmax[a]);
         d.pmin[a] = (int32_t)pmin;
@@ -748,6 +834,7 @@ int Engine::add(const bbs_maps* m, const float* xyz, int64_t k, int is_device, c
     if (rc == BBS_OK) rc = slot_get(h, &d.act, (size_t)nchunks_);
     if (rc == BBS_OK) rc = slot_get(h, &d.pop_ids, (size_t)nchunks_);
     if (rc == BBS_OK) rc = slot_get(h, &d.pop_start, (size_t)nchunks_);
+    if (rc == BBS_OK) rc = slot_get(h, &d.pop_tstart, (size_t)nchunks_);
     if (rc < 0) {
         release(i);
         return rc;
@@ -780,14 +867,14 @@ int Engine::start()
     launches_ += 1;
     BBS_CUDA_TRY(cudaGetLastError());
     // the initial sets: virtual parents x rotations at l_max, in launches
-    // bounded by the dense capacity
+    // bounded by the task capacity
     std::vector<Seg> segs;
-    int64_t work = 0, dense = 0;
+    int64_t nsl = 0, ntk = 0;
     auto flush = [&]() -> int {
         if (segs.empty()) return BBS_OK;
-        BBS_TRY(score_launch(MODE_INITIAL, segs, work, dense));
+        BBS_TRY(score_launch(MODE_INITIAL, segs, nsl, ntk));
         segs.clear();
-        work = dense = 0;
+        nsl = ntk = 0;
         return BBS_OK;
     };
     for (int i : slots) {
@@ -795,10 +882,9 @@ int Engine::start()
         const HostGrid& g = h.scan.grid;
         const int64_t R = g.nrot[g.levels - 1];
         const int64_t vpn = (int64_t)h.dev.pext[0] * h.dev.pext[1] * h.dev.pext[2];
-        const int64_t per = R * 8;
-        if (per > DENSE_CAP) return set_error(BBS_EINVAL, "localize: %lld initial rotations", (long long)R);
+        if (R > TASK_CAP) return set_error(BBS_EINVAL, "localize: %lld initial rotations", (long long)R);
         for (int64_t v0 = 0; v0 < vpn;) {
-            const int64_t take = std::min<int64_t>(vpn - v0, (DENSE_CAP - dense) / per);
+            const int64_t take = std::min<int64_t>(vpn - v0, (TASK_CAP - ntk) / R);
             if (take <= 0 || (int)segs.size() == MAXSEG) {
                 BBS_TRY(flush());
                 continue;
@@ -806,15 +892,15 @@ int Engine::start()
             Seg sg;
             std::memset(&sg, 0, sizeof(sg));
             sg.first_parent = v0;
-            sg.first_work = work;
-            sg.n_parents = take;
-            sg.dense_base = dense;
-            sg.chunks = h.chunks;
+            sg.first_task = ntk;
+            sg.n_tasks = take * R;
+            sg.first_slice = nsl;
             sg.sid = i;
+            sg.nblk = h.dev.nblk;
             sg.R = (int32_t)R;
             segs.push_back(sg);
-            work += take * h.chunks;
-            dense += take * per;
+            ntk += take * R;
+            nsl += take * R * h.dev.nblk;
             h.res.gathers += take * R * h.scan.k;
             v0 += take;
         }
@@ -859,9 +945,12 @@ void Engine::mark_finished(std::vector<int>* finished)
         if (!h.live) continue;
         const Ctl& c = h_ctl_[i];
         if (c.err) {
-            // the shared pool ran out while this search inserted: it fails alone
-            h.status = set_error(BBS_ENOMEM, "localize: the frontier pool (%lld nodes) is exhausted",
-                                 (long long)(nchunks_ * CH));
+            // the shared pool ran out while this search inserted, or its
+            // bookkeeping failed a check: it fails alone
+            if (c.err & 4) h.status = set_error(BBS_ECORRUPT, "localize: frontier task counts are inconsistent");
+            else
+                h.status = set_error(BBS_ENOMEM, "localize: the frontier pool (%lld nodes) is exhausted",
+                                     (long long)(nchunks_ * CH));
             h.live = false;
             h.t_end = t;
             finished->push_back(i);
@@ -873,61 +962,74 @@ void Engine::mark_finished(std::vector<int>* finished)
     }
 }
 
-// host-side scoring of the parents the last select popped (h_ctl_ is current)
+// host-side scoring of the parents the last select popped (h_ctl_ is current):
+// one launch when the round's tasks fit, else launches over task windows
 int Engine::process_popped()
 {
     const int n = max_slots_;
-    int64_t total_parents = 0, maxpop = 1;
+    int64_t total_parents = 0, total_tasks = 0, maxpop = 1, nsearch = 0;
     for (int i = 0; i < n; ++i) {
         h_poff_[i] = total_parents;
+        h_toff_[i] = total_tasks;
         if (!hosts_[(size_t)i].live) continue;
         total_parents += h_ctl_[i].n_parents;
+        total_tasks += h_ctl_[i].n_tasks;
+        nsearch += h_ctl_[i].n_tasks > 0 ? 1 : 0;
         maxpop = std::max<int64_t>(maxpop, h_ctl_[i].n_pop);
     }
     if (total_parents == 0) return BBS_OK;
+    const bool one = total_tasks <= TASK_CAP && nsearch <= MAXSEG;
     BBS_CUDA_TRY(cudaMemcpyAsync(d_poff_, h_poff_, sizeof(int64_t) * (size_t)n, cudaMemcpyHostToDevice, st_));
-    h_plan_.status = PLAN_OK;
+    BBS_CUDA_TRY(cudaMemcpyAsync(d_toff_, h_toff_, sizeof(int64_t) * (size_t)n, cudaMemcpyHostToDevice, st_));
+    h_plan_.status = one ? PLAN_OK : PLAN_SPLIT;
     h_plan_.nseg = 0;
     BBS_CUDA_TRY(cudaMemcpyAsync(d_plan_, &h_plan_, offsetof(Plan, seg), cudaMemcpyHostToDevice, st_));
     dim3 gg((unsigned)std::min<int64_t>(maxpop, 4096), (unsigned)std::min(n, 65535));
-    gather_kernel<<<gg, CH, 0, st_>>>(d_S_, pool_, d_poff_, n, parents_, d_plan_);
+    gather_kernel<<<gg, CH, 0, st_>>>(d_S_, pool_, d_poff_, d_toff_, n, parents_, pfirst_, tasks_, d_plan_);
     launches_ += 1;
     BBS_CUDA_TRY(cudaGetLastError());
     std::vector<Seg> segs;
-    int64_t work = 0, dense = 0;
+    int64_t nsl = 0, ntk = 0;
     auto flush = [&]() -> int {
         if (segs.empty()) return BBS_OK;
-        BBS_TRY(score_launch(MODE_SEARCH, segs, work, dense));
+        BBS_TRY(score_launch(MODE_SEARCH, segs, nsl, ntk));
         segs.clear();
-        work = dense = 0;
+        nsl = ntk = 0;
         return BBS_OK;
     };
     for (int i = 0; i < n; ++i) {
         SearchHost& h = hosts_[(size_t)i];
         if (!h.live) continue;
-        const int64_t np = h_ctl_[i].n_parents;
-        const int64_t per = (int64_t)h.rmax * 8;
-        for (int64_t p0 = 0; p0 < np;) {
-            const int64_t take = std::min<int64_t>(np - p0, (DENSE_CAP - dense) / per);
+        const int64_t nt = h_ctl_[i].n_tasks;
+        for (int64_t t0 = 0; t0 < nt;) {
+            const int64_t take = std::min<int64_t>(nt - t0, TASK_CAP - ntk);
             if (take <= 0 || (int)segs.size() == MAXSEG) {
                 BBS_TRY(flush());
                 continue;
             }
+            if (!one) {   // the window's task records, from the gathered parents
+                const int64_t np = h_ctl_[i].n_parents;
+                const int blocks = (int)std::min<int64_t>((np + 255) / 256, 4096);
+                expand_kernel<<<blocks, 256, 0, st_>>>(d_S_, i, parents_, pfirst_, h_poff_[i], h_poff_[i] + np,
+                                                       h_toff_[i] + t0, h_toff_[i] + t0 + take, ntk, tasks_);
+                launches_ += 1;
+                BBS_CUDA_TRY(cudaGetLastError());
+            }
             Seg sg;
             std::memset(&sg, 0, sizeof(sg));
-            sg.first_parent = h_poff_[i] + p0;
-            sg.first_work = work;
-            sg.n_parents = take;
-            sg.dense_base = dense;
-            sg.chunks = h.chunks;
+            sg.first_parent = h_poff_[i];
+            sg.first_task = one ? h_toff_[i] + t0 : ntk;
+            sg.n_tasks = take;
+            sg.first_slice = nsl;
             sg.sid = i;
-            sg.R = h.rmax;
+            sg.nblk = h.dev.nblk;
             segs.push_back(sg);
-            work += take * h.chunks;
-            dense += take * per;
-            p0 += take;
+            ntk += take;
+            nsl += take * h.dev.nblk;
+            t0 += take;
         }
     }
+    if (one) ntk = total_tasks;
     return flush();
 }
 
@@ -966,12 +1068,14 @@ int Engine::build_graph()
     if (e == cudaSuccess) {
         // one iteration: select, plan, gather, score, survivors, insert
         select_kernel<<<n, 1024, 0, cs>>>(d_S_, n, pool_);
-        plan_kernel<<<1, 1024, 0, cs>>>(d_S_, n, d_plan_, d_poff_, surv_.count, DENSE_CAP, cond);
-        gather_kernel<<<dim3(256, (unsigned)std::min(n, 65535)), CH, 0, cs>>>(d_S_, pool_, d_poff_, n, parents_, d_plan_);
-        launch_branch(MODE_SEARCH, d_plan_, d_S_, parents_, dense_, 152 * 20, cs);
-        launch_finalize(MODE_SEARCH, d_plan_, d_S_, parents_, dense_, surv_, 152 * 8, cs);
+        plan_kernel<<<1, 1024, 0, cs>>>(d_S_, n, d_plan_, d_poff_, d_toff_, surv_.count, cond);
+        gather_kernel<<<dim3(256, (unsigned)std::min(n, 65535)), CH, 0, cs>>>(d_S_, pool_, d_poff_, d_toff_, n, parents_,
+                                                                              pfirst_, tasks_, d_plan_);
+        launch_branch(MODE_SEARCH, d_plan_, d_S_, parents_, tasks_, dense_, nsm_ * BRANCH_CTAS_PER_SM, cs);
+        launch_finalize(MODE_SEARCH, d_plan_, d_S_, parents_, tasks_, dense_, surv_, nsm_ * 8, cs);
         alloc_kernel<<<n, 1024, 0, cs>>>(d_S_, n, pool_, d_plan_);
-        scatter_kernel<<<1024, 256, 0, cs>>>(d_S_, pool_, surv_.nodes, surv_.scores, surv_.sid, surv_.count, surv_.cap);
+        scatter_kernel<<<1024, 256, 0, cs>>>(d_S_, pool_, surv_.nodes, surv_.scores, surv_.sid, surv_.ntask, surv_.count,
+                                             surv_.cap);
         cudaGraph_t out = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cs, &out);
         e = e2 != cudaSuccess ? e2 : cudaGetLastError();
@@ -1116,10 +1220,11 @@ int Engine::release(int i)
     return BBS_OK;
 }
 
-int Engine::score_launch(int mode, const std::vector<Seg>& segs, int64_t work, int64_t dense)
+int Engine::score_launch(int mode, const std::vector<Seg>& segs, int64_t n_slices, int64_t n_tasks)
 {
-    h_plan_.n_work = work;
-    h_plan_.n_dense = dense;
+    h_plan_.n_slices = n_slices;
+    h_plan_.n_tasks = n_tasks;
+    h_plan_.next_slice = 0;
     h_plan_.nseg = (int32_t)segs.size();
     h_plan_.mode = mode;
     h_plan_.status = PLAN_OK;
@@ -1135,13 +1240,16 @@ int Engine::score_launch(int mode, const std::vector<Seg>& segs, int64_t work, i
         evs_.push_back(e1);
         BBS_CUDA_TRY(cudaEventRecord(e0, st_));
     }
-    const int bb = (int)std::min<int64_t>(work, 152 * 64);
-    BBS_CUDA_TRY(launch_branch(mode, d_plan_, d_S_, parents_, dense_, bb, st_));
+    const int bb = (int)std::min<int64_t>(n_slices, (int64_t)nsm_ * BRANCH_CTAS_PER_SM);
+    BBS_CUDA_TRY(launch_branch(mode, d_plan_, d_S_, parents_, tasks_, dense_, bb, st_));
     if (timed_) BBS_CUDA_TRY(cudaEventRecord(e1, st_));
-    const int fb = (int)std::min<int64_t>((dense + 255) / 256, 152 * 32);
-    BBS_CUDA_TRY(launch_finalize(mode, d_plan_, d_S_, parents_, dense_, surv_, fb, st_));
+    // the device-driven loop leaves its last round's survivor count behind
+    BBS_CUDA_TRY(cudaMemsetAsync(surv_.count, 0, sizeof(unsigned long long), st_));
+    const int fb = (int)std::min<int64_t>((8 * n_tasks + 255) / 256, (int64_t)nsm_ * 32);
+    BBS_CUDA_TRY(launch_finalize(mode, d_plan_, d_S_, parents_, tasks_, dense_, surv_, fb, st_));
     alloc_kernel<<<max_slots_, 1024, 0, st_>>>(d_S_, max_slots_, pool_, d_plan_);
-    scatter_kernel<<<1024, 256, 0, st_>>>(d_S_, pool_, surv_.nodes, surv_.scores, surv_.sid, surv_.count, surv_.cap);
+    scatter_kernel<<<1024, 256, 0, st_>>>(d_S_, pool_, surv_.nodes, surv_.scores, surv_.sid, surv_.ntask, surv_.count,
+                                          surv_.cap);
     BBS_CUDA_TRY(cudaMemsetAsync(surv_.count, 0, sizeof(unsigned long long), st_));
     BBS_CUDA_TRY(cudaGetLastError());
     launches_ += 4;

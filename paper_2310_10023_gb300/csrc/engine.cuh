@@ -77,8 +77,9 @@ class Engine {
     size_t estimate_bytes(int64_t k, const HostGrid& g) const;
 
   private:
-    static constexpr int64_t DENSE_CAP = (int64_t)1 << 22;   // child scores per scoring launch
-    int score_launch(int mode, const std::vector<Seg>& segs, int64_t work, int64_t dense);
+    static constexpr int64_t DENSE_CAP = 8 * TASK_CAP;   // child scores per scoring launch
+    // one scoring launch (branch + finalize + alloc + scatter) of the given runs
+    int score_launch(int mode, const std::vector<Seg>& segs, int64_t n_slices, int64_t n_tasks);
     int read_ctl();
     void finish_never_live(std::vector<int>* finished);
     void mark_finished(std::vector<int>* finished);
@@ -98,12 +99,17 @@ class Engine {
     SearchDev* d_S_ = nullptr;
     Ctl* d_ctl_ = nullptr;
     NodeRec* parents_ = nullptr;
+    int64_t* pfirst_ = nullptr;   // first task of each gathered parent
+    TaskRec* tasks_ = nullptr;    // the launch's tasks
     int64_t* d_poff_ = nullptr;
+    int64_t* d_toff_ = nullptr;
     int32_t* d_slots_ = nullptr;
     int32_t* dense_ = nullptr;
     SurvOut surv_{};
     Ctl* h_ctl_ = nullptr;
     int64_t* h_poff_ = nullptr;
+    int64_t* h_toff_ = nullptr;
+    int nsm_ = 152;
     Plan* d_plan_ = nullptr;
     Plan h_plan_{};
     cudaGraphExec_t exec_ = nullptr;

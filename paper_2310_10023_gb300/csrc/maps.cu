@@ -371,7 +371,7 @@ int log2_ceil(unsigned long long x)
 }  // namespace
 
 // target load of the final brick tables (bricks / buckets)
-static double g_load_target = 0.5;
+static double g_load_target = 0.25;
 // 0: compact buckets whenever a level fits them, 1: always wide
 static int g_layout = 0;
 
