@@ -84,8 +84,74 @@ struct DevGrid {
     uint32_t flags;
     int32_t N[MAX_LEVELS][3];    // angle segments per level and axis
     int32_t a[MAX_LEVELS][3];    // Eq. (14) divisions (index l: from l to l-1)
-    int64_t rot_off[MAX_LEVELS]; // first rotation of level l in the rotation table
+    int32_t cs_off[MAX_LEVELS][3];   // first (cos, sin) entry of each level and axis
+    double r;                    // voxel size of level 0
+    double inv_r;                // fl64(1 / r)
 };
+
+// fl32(fl64(x / r)).  q = fl64(x * fl64(1/r)) lies within 3 units in the last
+// place of x / r, so fl32(q) is the float of the exact quotient unless q sits
+// near a float rounding midpoint (its low 29 bits within 64 of 2^28) or
+// outside the normal float range; those cases divide exactly.
+__device__ __forceinline__ float div_r_f32(double x, double r, double inv_r)
+{
+    const double q = __dmul_rn(x, inv_r);
+    const double aq = fabs(q);
+    const uint32_t lo = (uint32_t)__double2loint(q) & 0x1FFFFFFFu;
+    const uint32_t d = lo > 0x10000000u ? lo - 0x10000000u : 0x10000000u - lo;
+    if (d > 64u && aq >= 0x1p-120 && aq < 0x1p120) return __double2float_rn(q);
+    return __double2float_rn(__ddiv_rn(x, r));
+}
+
+// Entry e (row-major) of A = fl32(R / r) for rotation `rot` at level l: the
+// same products and sums as rotation_rows, one entry per call
+__device__ __forceinline__ float rotation_entry(const double2* __restrict__ cs, const DevGrid& g, int l, uint32_t rot, int e)
+{
+    const uint32_t ng = (uint32_t)g.N[l][2], nb = (uint32_t)g.N[l][1];
+    const uint32_t q1 = rot / ng, ig = rot - q1 * ng, ia = q1 / nb, ib = q1 - ia * nb;
+    const double2 A_ = cs[g.cs_off[l][0] + (int32_t)ia];
+    const double2 B_ = cs[g.cs_off[l][1] + (int32_t)ib];
+    const double2 G_ = cs[g.cs_off[l][2] + (int32_t)ig];
+    const double ca = A_.x, sa = A_.y, cb = B_.x, sb = B_.y, cg = G_.x, sg = G_.y;
+    double x;
+    switch (e) {
+        case 0: x = __dmul_rn(cg, cb); break;
+        case 1: x = __dsub_rn(__dmul_rn(__dmul_rn(cg, sb), sa), __dmul_rn(sg, ca)); break;
+        case 2: x = __dadd_rn(__dmul_rn(__dmul_rn(cg, sb), ca), __dmul_rn(sg, sa)); break;
+        case 3: x = __dmul_rn(sg, cb); break;
+        case 4: x = __dadd_rn(__dmul_rn(__dmul_rn(sg, sb), sa), __dmul_rn(cg, ca)); break;
+        case 5: x = __dsub_rn(__dmul_rn(__dmul_rn(sg, sb), ca), __dmul_rn(cg, sa)); break;
+        case 6: x = -sb; break;
+        case 7: x = __dmul_rn(cb, sa); break;
+        default: x = __dmul_rn(cb, ca); break;
+    }
+    return div_r_f32(x, g.r, g.inv_r);
+}
+
+// A = fl32(R / r) of rotation `rot` at level l (row-major, 9 entries), with
+// R = Rz(gamma) Ry(beta) Rx(alpha) of the segment angles (Sec. III-A) formed
+// in FP64 from the host cos / sin table cs, every product and sum rounded
+__device__ __forceinline__ void rotation_rows(const double2* __restrict__ cs, const DevGrid& g, int l, uint32_t rot,
+                                              float A[9])
+{
+    const uint32_t ng = (uint32_t)g.N[l][2], nb = (uint32_t)g.N[l][1];
+    const uint32_t q1 = rot / ng, ig = rot - q1 * ng, ia = q1 / nb, ib = q1 - ia * nb;
+    const double2 A_ = cs[g.cs_off[l][0] + (int32_t)ia];
+    const double2 B_ = cs[g.cs_off[l][1] + (int32_t)ib];
+    const double2 G_ = cs[g.cs_off[l][2] + (int32_t)ig];
+    const double ca = A_.x, sa = A_.y, cb = B_.x, sb = B_.y, cg = G_.x, sg = G_.y;
+    double R[9];
+    R[0] = __dmul_rn(cg, cb);
+    R[1] = __dsub_rn(__dmul_rn(__dmul_rn(cg, sb), sa), __dmul_rn(sg, ca));
+    R[2] = __dadd_rn(__dmul_rn(__dmul_rn(cg, sb), ca), __dmul_rn(sg, sa));
+    R[3] = __dmul_rn(sg, cb);
+    R[4] = __dadd_rn(__dmul_rn(__dmul_rn(sg, sb), sa), __dmul_rn(cg, ca));
+    R[5] = __dsub_rn(__dmul_rn(__dmul_rn(sg, sb), ca), __dmul_rn(cg, sa));
+    R[6] = -sb;
+    R[7] = __dmul_rn(cb, sa);
+    R[8] = __dmul_rn(cb, ca);
+    for (int i = 0; i < 9; ++i) A[i] = div_r_f32(R[i], g.r, g.inv_r);
+}
 
 // Node / task record in HBM: translation indices and (rotation index << 5 | level).
 struct __align__(16) NodeRec {
@@ -296,6 +362,8 @@ struct HostGrid {
     int64_t nrot[MAX_LEVELS];
     int64_t rot_off[MAX_LEVELS];
     int64_t total_rot;
+    int64_t cs_off[MAX_LEVELS][3];   // first (cos, sin) entry of each level and axis
+    int64_t n_cs;                    // segment angles of all levels and axes
 };
 
 int grid_build(double r, int levels, double d_max, const bbs_ranges* rg, uint32_t flags, HostGrid* g);
@@ -309,12 +377,15 @@ struct ScanState {
     int64_t k;
     double d_max;
     HostGrid grid;
-    float4* rot;       // 3 float4 rows per rotation, all levels
+    double2* cs;       // (cos, sin) of every segment angle, host libm, FP64
+    float4* rot;       // 3 float4 rows per rotation of the top level l_max
     int64_t h2d, d2h;  // bytes copied while preparing
 };
 
 int scan_prepare(const bbs_maps* m, const float* xyz, int64_t k, int is_device, const bbs_ranges* rg,
                  const bbs_opts* opts, cudaStream_t st, ScanState* out);
+// the 3 x float4 rows of every rotation of `level` -> out
+cudaError_t launch_level_rows(const ScanState& s, int level, float4* out, cudaStream_t st);
 void scan_release(ScanState* s, cudaStream_t st);
 
 // kernels launched from more than one translation unit

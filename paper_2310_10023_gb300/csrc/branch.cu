@@ -52,6 +52,14 @@ __device__ __forceinline__ f2 add2rm(f2 a, f2 b)
     return d;
 }
 
+// fl_rd(a * b + c) per lane, one rounding of the exact value
+__device__ __forceinline__ f2 fma2rm(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rm.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 struct Row2 {
     f2 x, y, z;
 };
@@ -59,23 +67,36 @@ struct Row2 {
 // ((a0 x + a1 y) + a2 z) for two points, the scalar order and rounding
 __device__ __forceinline__ f2 rot2(const Row2& r, f2 X, f2 Y, f2 Z) { return add2(add2(mul2(r.x, X), mul2(r.y, Y)), mul2(r.z, Z)); }
 
-// the 8 child bits of one point: key block at (kx, ky, kz) + {0,1}^3, where the
-// keys are relative to the compact origin (COMPACT) or absolute (wide)
+// Bit pattern of a floored key: for the per-axis constant C = 1.5 * 2^23 + d
+// (d an integer, |d| < 2^21), fl_rd(q * 2^-m + C) rounds the exact value once,
+// so while |floor(q / 2^m) + d| < 2^22 its bit pattern is KB + floor(q / 2^m) + d:
+// the level-m key of Eq. (11), offset by d, in the low 22 bits.  Outside that
+// range the pattern leaves [KB, KB + 2^22) and fails every range check below.
+constexpr uint32_t KB = 0x4B400000u;   // bit pattern of 1.5 * 2^23
+
+// the 8 child bits of one point from the bit patterns of its level-m key,
+// offset so that the key block (kx, ky, kz) + {0,1}^3 is relative to the
+// compact origin (COMPACT) or absolute (wide)
 template <bool COMPACT>
-__device__ __forceinline__ void child_bits(const LevelView& L, int32_t kx, int32_t ky, int32_t kz, uint32_t& w0,
+__device__ __forceinline__ void child_bits(const LevelView& L, uint32_t bx, uint32_t by, uint32_t bz, uint32_t& w0,
                                            uint32_t& w1)
 {
     w0 = w1 = 0;
     if (COMPACT) {
-        const uint32_t rx = (uint32_t)kx, ry = (uint32_t)ky, rz = (uint32_t)kz;
-        if (rx > L.rmax[0] || ry > L.rmax[1] || rz > L.rmax[2]) return;
-        const uint32_t oz = rz & 3u;
+        // relative keys in [0, 2^13) x [0, 2^13) x [0, 4092): 11 / 11 / 10-bit brick
+        // fields that cannot overflow, and never the empty tag (brick z <= 1022);
+        // bricks beyond the map's own box are simply absent
+        if (((bx ^ KB) | (by ^ KB)) >= (1u << 13) || (bz ^ KB) >= 4092u) return;
+        // brick key (rx >> 2) | (ry >> 2) << 11 | (rz >> 2) << 22 straight from the
+        // patterns: KB is 0 in every bit that lands in a field
+        const uint32_t key = ((bx >> 2) & 0x7FFu) | ((by << 9) & 0x3FF800u) | ((bz << 20) & 0xFFC00000u);
         uint4 w;
-        if (!probe_compact(L, cbrick_pack(rx >> 2, ry >> 2, rz >> 2), (int)(oz >> 1), w)) return;
-        const uint32_t sh = (rx & 3u) + 5u * (ry & 3u);
-        w0 = ((oz & 1u) ? w.z : w.y) >> sh;
-        w1 = ((oz & 1u) ? w.w : w.z) >> sh;
+        if (!probe_compact(L, key, (int)((bz >> 1) & 1u), w)) return;
+        const uint32_t sh = (bx & 3u) + 5u * (by & 3u);
+        w0 = ((bz & 1u) ? w.z : w.y) >> sh;
+        w1 = ((bz & 1u) ? w.w : w.z) >> sh;
     } else {
+        const int32_t kx = (int32_t)(bx - KB), ky = (int32_t)(by - KB), kz = (int32_t)(bz - KB);
         if (!(key_in_range(kx) && key_in_range(ky) && key_in_range(kz))) return;
         uint4 blo, bhi;
         if (!probe_brick(L, kx >> 2, ky >> 2, kz >> 2, blo, bhi)) return;
@@ -89,30 +110,27 @@ __device__ __forceinline__ void child_bits(const LevelView& L, int32_t kx, int32
 // per step.  The chunk is staged as pairs: sxy[j] = (x_2j, x_2j+1, y_2j,
 // y_2j+1) and sz[j] = (z_2j, z_2j+1), so each coordinate pair is one 64-bit
 // register for the f32x2 operations; thread t takes pairs jlo + t, jlo + t +
-// blockDim, ... below jhi.  The exact floor of q is the bit pattern of
-// fl_rd(q + 1.5 * 2^23) minus that of 1.5 * 2^23 (valid for |q| < 2^22); that
-// offset is a multiple of 2^22, so the level shift applies to the raw bit
-// pattern and the offset, the translation and the compact origin fold into
-// one per-axis constant.
+// blockDim, ... below jhi.  q = (A_i0 x + A_i1 y) + A_i2 z is rounded to FP32
+// after every product and sum (no FMA), as the oracle; the floor, the level
+// shift and the key offset are one fma.rm of that q (see KB).
 template <bool COMPACT>
 __device__ __forceinline__ void score_run(const ulonglong2* sxy, const f2* sz, int n, int jlo, int jhi,
-                                          const LevelView& L, int m, const Row2& r0, const Row2& r1, const Row2& r2,
-                                          int32_t cx, int32_t cy, int32_t cz, uint32_t& acc0, uint32_t& acc1)
+                                          const LevelView& L, const Row2& r0, const Row2& r1, const Row2& r2, f2 S,
+                                          f2 Cx, f2 Cy, f2 Cz, uint32_t& acc0, uint32_t& acc1)
 {
-    const f2 C = pk2(12582912.0f, 12582912.0f);
     for (int j = jlo + threadIdx.x; j < jhi; j += blockDim.x) {
         const ulonglong2 xy = sxy[j];
         const f2 Z = sz[j];
         int32_t bx1, bx2, by1, by2, bz1, bz2;
-        up2(add2rm(rot2(r0, xy.x, xy.y, Z), C), bx1, bx2);
-        up2(add2rm(rot2(r1, xy.x, xy.y, Z), C), by1, by2);
-        up2(add2rm(rot2(r2, xy.x, xy.y, Z), C), bz1, bz2);
+        up2(fma2rm(rot2(r0, xy.x, xy.y, Z), S, Cx), bx1, bx2);
+        up2(fma2rm(rot2(r1, xy.x, xy.y, Z), S, Cy), by1, by2);
+        up2(fma2rm(rot2(r2, xy.x, xy.y, Z), S, Cz), bz1, bz2);
         uint32_t w0, w1;
-        child_bits<COMPACT>(L, (bx1 >> m) + cx, (by1 >> m) + cy, (bz1 >> m) + cz, w0, w1);
+        child_bits<COMPACT>(L, (uint32_t)bx1, (uint32_t)by1, (uint32_t)bz1, w0, w1);
         acc0 += spread4(w0);
         acc1 += spread4(w1);
         if (2 * j + 1 < n) {
-            child_bits<COMPACT>(L, (bx2 >> m) + cx, (by2 >> m) + cy, (bz2 >> m) + cz, w0, w1);
+            child_bits<COMPACT>(L, (uint32_t)bx2, (uint32_t)by2, (uint32_t)bz2, w0, w1);
             acc0 += spread4(w0);
             acc1 += spread4(w1);
         }
@@ -155,7 +173,8 @@ __device__ __forceinline__ void virtual_parent(const SearchDev& S, int64_t vp, i
 // memory for the whole CTA.
 struct __align__(16) RunDesc {
     f2 a[9];          // rotation entries A_ik, each duplicated for the paired lanes
-    int32_t kc[3];    // per-axis key constant: translation - floor offset (- compact origin)
+    f2 kc[3];         // per-axis 1.5 * 2^23 + translation (- compact origin), paired
+    f2 s;             // 2^-m, paired
     int32_t m;        // child level
     int32_t c;        // point chunk
     int32_t b0, b1;   // PBLK-point blocks [b0, b1) of the chunk
@@ -165,7 +184,7 @@ struct __align__(16) RunDesc {
 
 constexpr int NRUN = 32;   // runs described per round of a CTA
 constexpr int STATIC_NUM = 3, STATIC_DEN = 4;   // share of a launch's slices split statically
-constexpr int64_t GRAB_MIN = 4;                 // smallest dynamic grab (slices)
+constexpr int64_t GRAB_MIN = 16;                // smallest dynamic grab (slices)
 
 }  // namespace
 
@@ -254,42 +273,42 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
             const int nbc = c < nchunk - 1 ? 4 : nbl;
             const int64_t rs = c * 4 * nt + u * nbc;
             int m;
-            uint32_t crot;
             int32_t tx, ty, tz;
+            float A[9];
             if (MODE == MODE_INITIAL) {
                 virtual_parent(S, g->first_parent + u / g->R, tx, ty, tz);
                 tx *= 2;
                 ty *= 2;
                 tz *= 2;
-                crot = (uint32_t)(u % g->R);
+                const float4* At = S.rot + 3 * (u % g->R);   // the top level's table
+                const float4 a0 = __ldg(At), a1 = __ldg(At + 1), a2 = __ldg(At + 2);
+                A[0] = a0.x, A[1] = a0.y, A[2] = a0.z, A[3] = a1.x, A[4] = a1.y, A[5] = a1.z;
+                A[6] = a2.x, A[7] = a2.y, A[8] = a2.z;
                 m = S.lmax;
             } else {
-                const TaskRec tr = tasks[g->first_task + u];
+                const TaskRec& tr = tasks[g->first_task + u];
                 const NodeRec par = parents[tr.parent];
                 m = rl_level(tr.rl);
-                crot = rl_rot(tr.rl);
+                for (int i = 0; i < 9; ++i) A[i] = tr.a[i];
                 tx = 2 * par.cx;
                 ty = 2 * par.cy;
                 tz = 2 * par.cz;
             }
             const LevelView& L = S.maps[m];
-            const int32_t off = 0x4B400000 >> m;   // the floor offset after the level shift
             const bool cmp = L.compact != 0;
             RunDesc& d = rd[tid];
-            d.kc[0] = tx - off - (cmp ? L.base[0] : 0);
-            d.kc[1] = ty - off - (cmp ? L.base[1] : 0);
-            d.kc[2] = tz - off - (cmp ? L.base[2] : 0);
-            const float4* A = S.rot + 3 * (S.grid.rot_off[m] + (int64_t)crot);
-            const float4 a0 = __ldg(A), a1 = __ldg(A + 1), a2 = __ldg(A + 2);
-            d.a[0] = pk2(a0.x, a0.x);
-            d.a[1] = pk2(a0.y, a0.y);
-            d.a[2] = pk2(a0.z, a0.z);
-            d.a[3] = pk2(a1.x, a1.x);
-            d.a[4] = pk2(a1.y, a1.y);
-            d.a[5] = pk2(a1.z, a1.z);
-            d.a[6] = pk2(a2.x, a2.x);
-            d.a[7] = pk2(a2.y, a2.y);
-            d.a[8] = pk2(a2.z, a2.z);
+            const int32_t t3[3] = {tx, ty, tz};
+            for (int i = 0; i < 3; ++i) {
+                // |offset| >= 2^21 puts every point of the run outside the key range
+                // (|floor(q / 2^m)| <= 2^18 by the scan bound), as the clamped one does
+                int32_t o = t3[i] - (cmp ? L.base[i] : 0);
+                o = o > (1 << 21) ? (1 << 21) : (o < -(1 << 21) ? -(1 << 21) : o);
+                const float c = 12582912.0f + (float)o;   // exact: an integer below 2^24
+                d.kc[i] = pk2(c, c);
+            }
+            const float sc = __int_as_float((127 - m) << 23);   // 2^-m
+            d.s = pk2(sc, sc);
+            for (int i = 0; i < 9; ++i) d.a[i] = pk2(A[i], A[i]);
             d.m = m;
             d.c = (int32_t)c;
             d.sid = g->sid;
@@ -324,8 +343,7 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
                 }
                 __syncthreads();   // staged points and the new chunk tag visible
             }
-            const int m = d.m;
-            const LevelView Lv = S.maps[m];
+            const LevelView Lv = S.maps[d.m];
             const Row2 r0{d.a[0], d.a[1], d.a[2]};
             const Row2 r1{d.a[3], d.a[4], d.a[5]};
             const Row2 r2{d.a[6], d.a[7], d.a[8]};
@@ -333,9 +351,9 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
             const int jlo = d.b0 * (PBLK / 2), jhi = min(d.b1 * (PBLK / 2), (n + 1) >> 1);
             uint32_t acc0 = 0, acc1 = 0;   // bytes: children (0,4,2,6) and (1,5,3,7)
             if (Lv.compact)
-                score_run<true>(sxy, sz, n, jlo, jhi, Lv, m, r0, r1, r2, d.kc[0], d.kc[1], d.kc[2], acc0, acc1);
+                score_run<true>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], acc0, acc1);
             else
-                score_run<false>(sxy, sz, n, jlo, jhi, Lv, m, r0, r1, r2, d.kc[0], d.kc[1], d.kc[2], acc0, acc1);
+                score_run<false>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], acc0, acc1);
             // 16-bit fields: at most 8 points per thread x 32 lanes, x 8 warps, per field
             uint32_t e0 = acc0 & 0x00FF00FFu, o0 = (acc0 >> 8) & 0x00FF00FFu;
             uint32_t e1 = acc1 & 0x00FF00FFu, o1 = (acc1 >> 8) & 0x00FF00FFu;
@@ -448,6 +466,30 @@ __global__ void __launch_bounds__(256) finalize_kernel(const Plan* __restrict__ 
             if (m == 0) atomicAdd(&s.h_leaf[score], 1u);
         }
     }
+}
+
+// the rotation rows of every task of a launch: warp e of a CTA forms entry e
+// of 32 tasks, so the FP64 chains are short and spread over the whole GPU
+__global__ void __launch_bounds__(288) task_rows_kernel(const Plan* __restrict__ P, const SearchDev* __restrict__ S,
+                                                        TaskRec* tasks)
+{
+    if (P->status != PLAN_OK) return;
+    const int64_t n = P->n_tasks;
+    const int e = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t u = (int64_t)blockIdx.x * 32 + lane; u - lane < n; u += (int64_t)gridDim.x * 32) {
+        if (u >= n) continue;
+        const SearchDev& f = S[P->seg[find_task_seg(P, u)].sid];
+        const uint32_t rl = tasks[u].rl;
+        tasks[u].a[e] = rotation_entry(f.cs, f.grid, rl_level(rl), rl_rot(rl), e);
+        if (e == 0) tasks[u].pad = 0.0f;
+    }
+}
+
+cudaError_t launch_task_rows(const Plan* P, const SearchDev* S, TaskRec* tasks, int blocks, cudaStream_t st)
+{
+    if (blocks <= 0) return cudaSuccess;
+    task_rows_kernel<<<blocks, 288, 0, st>>>(P, S, tasks);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_branch(int mode, Plan* P, const SearchDev* S, const NodeRec* parents, const TaskRec* tasks,

@@ -17,7 +17,7 @@ constexpr int64_t TASK_CAP = (int64_t)1 << 19;   // rotational-child tasks per s
 struct ScoreArgs {
     LevelView maps[MAX_LEVELS];
     DevGrid grid;
-    const float4* rot;
+    const double2* cs;
     const float4* scan;
     int64_t k;
     const int32_t* nodes;
@@ -52,7 +52,8 @@ struct Ctl {
 // One search slot (device).  Frontier arrays have K + 1 buckets.
 struct SearchDev {
     const float4* scan;
-    const float4* rot;
+    const float4* rot;          // rows of the top level's rotations
+    const double2* cs;          // (cos, sin) of every segment angle
     int32_t K;
     int32_t lmax;
     int64_t batch;
@@ -95,11 +96,14 @@ struct PoolDev {
 enum { MODE_INITIAL = 0, MODE_SEARCH = 1, MODE_DENSE = 2 };
 
 // One rotational child of a scoring round: its parent (index into the
-// round's parent array) and rl_pack(child rotation, child level).  Its 8
+// round's parent array), rl_pack(child rotation, child level) and the
+// rotation's rows (rotation_rows).  Its 8
 // translational children are the dense scores 8 * task .. 8 * task + 7.
-struct TaskRec {
+struct __align__(16) TaskRec {
     int32_t parent;
     uint32_t rl;
+    float a[9];             // the child rotation's A = fl32(R / r), row-major
+    float pad;
 };
 
 // A run of tasks of one search inside a scoring launch.  The run's work is
@@ -167,6 +171,9 @@ __host__ __device__ __forceinline__ int32_t rot_children(const DevGrid& g, int l
     }
     return n;
 }
+
+// the rotation rows of the launch's task records from their rl; skips unless PLAN_OK
+cudaError_t launch_task_rows(const Plan* P, const SearchDev* S, TaskRec* tasks, int blocks, cudaStream_t st);
 
 // CTAs of a scoring launch: one resident wave (4 CTAs of 256 threads per SM, 64 registers a thread)
 constexpr int BRANCH_CTAS_PER_SM = 4;

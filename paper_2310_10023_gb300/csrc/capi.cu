@@ -166,8 +166,12 @@ int bbs_pose_grid(const bbs_maps* m, const float* scan_xyz, int64_t k, int is_de
                 rc = set_error(BBS_EINVAL, "pose_grid: capacity %lld < %lld", (long long)cap, (long long)g.nrot[level]);
             } else {
                 std::vector<float4> h((size_t)(3 * g.nrot[level]));
-                cudaError_t e = cudaMemcpyAsync(h.data(), S.rot + 3 * g.rot_off[level], sizeof(float4) * h.size(),
-                                                cudaMemcpyDeviceToHost, st);
+                float4* d_rows = nullptr;
+                cudaError_t e = cudaMallocAsync((void**)&d_rows, sizeof(float4) * h.size(), st);
+                if (e == cudaSuccess) e = launch_level_rows(S, level, d_rows, st);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(h.data(), d_rows, sizeof(float4) * h.size(), cudaMemcpyDeviceToHost, st);
+                if (d_rows) cudaFreeAsync(d_rows, st);
                 if (e == cudaSuccess) e = cudaStreamSynchronize(st);
                 if (e != cudaSuccess) rc = set_error(BBS_ECUDA, "pose_grid: %s", cudaGetErrorString(e));
                 for (int64_t t = 0; rc == BBS_OK && t < g.nrot[level]; ++t)
@@ -290,7 +294,11 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
                     for (int32_t jg = 0; jg < pex[2]; ++jg) {
                         const uint32_t crot =
                             (uint32_t)(((int64_t)(plo[0] + ja) * g.N[l - 1][1] + (plo[1] + jb)) * g.N[l - 1][2] + (plo[2] + jg));
-                        tk[(size_t)u++] = TaskRec{(int32_t)p, rl_pack(crot, l - 1)};
+                        TaskRec r;
+                        std::memset(&r, 0, sizeof(r));
+                        r.parent = (int32_t)p;
+                        r.rl = rl_pack(crot, l - 1);
+                        tk[(size_t)u++] = r;   // rows filled on the device
                     }
         }
     }
@@ -299,6 +307,7 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
     std::memset(&sd, 0, sizeof(sd));
     sd.scan = S.scan;
     sd.rot = S.rot;
+    sd.cs = S.cs;
     sd.K = (int32_t)k;
     sd.lmax = g.levels - 1;
     sd.nblk = (int32_t)((k + PBLK - 1) / PBLK);
@@ -335,7 +344,9 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     int rc = BBS_OK;
-    cudaError_t e = launch_branch(MODE_SEARCH, d_plan, d_sd, d_par, d_tk, d_dense,
+    cudaError_t e = launch_task_rows(d_plan, d_sd, d_tk, (int)std::min<int64_t>((ntask + 31) / 32, 4096), st);
+    if (e == cudaSuccess)
+        e = launch_branch(MODE_SEARCH, d_plan, d_sd, d_par, d_tk, d_dense,
                                   (int)std::min<int64_t>(P.n_slices, (int64_t)nsm * BRANCH_CTAS_PER_SM), st);
     std::vector<int32_t> dense((size_t)total);
     if (e == cudaSuccess)

@@ -450,10 +450,11 @@ __global__ void slot_release_kernel(SearchDev* S, int slot, PoolDev pool)
 }
 
 // the tasks (rotational children, Eq. (13)) of parent p, written at tasks[dst
-// + t] for the t in [t0, t1)
-__device__ __forceinline__ void write_tasks(const DevGrid& g, const NodeRec& nd, int64_t p, const int32_t lo[3],
+// + t] for the t in [t0, t1): parent and rl (task_rows_kernel adds the rows)
+__device__ __forceinline__ void write_tasks(const SearchDev& f, const NodeRec& nd, int64_t p, const int32_t lo[3],
                                             const int32_t ext[3], int32_t t0, int32_t t1, TaskRec* tasks, int64_t dst)
 {
+    const DevGrid& g = f.grid;
     const int l = rl_level(nd.rl);
     const int64_t nb = g.N[l - 1][1], ng = g.N[l - 1][2];
     int32_t t = 0;
@@ -462,10 +463,9 @@ __device__ __forceinline__ void write_tasks(const DevGrid& g, const NodeRec& nd,
             for (int32_t jg = 0; jg < ext[2]; ++jg, ++t) {
                 if (t < t0 || t >= t1) continue;
                 const uint32_t crot = (uint32_t)(((int64_t)(lo[0] + ja) * nb + (lo[1] + jb)) * ng + (lo[2] + jg));
-                TaskRec r;
+                TaskRec& r = tasks[dst + t];   // the rows follow (task_rows_kernel)
                 r.parent = (int32_t)p;
                 r.rl = rl_pack(crot, l - 1);
-                tasks[dst + t] = r;
             }
 }
 
@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(CH) gather_kernel(SearchDev* S, PoolDev pool, 
                 parents[start + j] = nd;
                 pfirst[start + j] = first;
                 if (status == PLAN_OK && T > 0) {
-                    if (first + T <= TASK_CAP) write_tasks(f.grid, nd, start + j, lo, ext, 0, T, tasks, first);
+                    if (first + T <= TASK_CAP) write_tasks(f, nd, start + j, lo, ext, 0, T, tasks, first);
                     else atomicOr(&f.ctl->err, 4);   // task counts disagree with the nodes: fail the search
                 }
             }
@@ -524,7 +524,8 @@ __global__ void expand_kernel(const SearchDev* S, int sid, const NodeRec* __rest
                               const int64_t* __restrict__ pfirst, int64_t p0, int64_t p1, int64_t ga, int64_t gb,
                               int64_t la, TaskRec* __restrict__ tasks)
 {
-    const DevGrid& g = S[sid].grid;
+    const SearchDev& f = S[sid];
+    const DevGrid& g = f.grid;
     for (int64_t p = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < p1; p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = pfirst[p];
         if (b >= gb) continue;
@@ -533,7 +534,7 @@ __global__ void expand_kernel(const SearchDev* S, int sid, const NodeRec* __rest
         const int32_t T = rot_children(g, rl_level(nd.rl), rl_rot(nd.rl), lo, ext);
         if (b + T <= ga) continue;
         const int32_t t0 = (int32_t)(ga > b ? ga - b : 0), t1 = (int32_t)(gb < b + T ? gb - b : T);
-        write_tasks(g, nd, p, lo, ext, t0, t1, tasks, la + b - ga);
+        write_tasks(f, nd, p, lo, ext, t0, t1, tasks, la + b - ga);
     }
 }
 
@@ -733,7 +734,8 @@ int Engine::slot_get(SearchHost& h, T** p, size_t n)
 size_t Engine::estimate_bytes(int64_t k, const HostGrid& g) const
 {
     const size_t K1 = (size_t)k + 1;
-    return sizeof(float4) * (size_t)(k > 0 ? k : 1) + sizeof(float4) * 3 * (size_t)g.total_rot + 68 * K1 +
+    return sizeof(float4) * (size_t)(k > 0 ? k : 1) + sizeof(float4) * 3 * (size_t)g.nrot[g.levels - 1] +
+           sizeof(double2) * (size_t)g.n_cs + 68 * K1 +
            24 * (size_t)nchunks_ + 1024;
 }
 
@@ -804,6 +806,7 @@ int Engine::add(const bbs_maps* m, const float* xyz, int64_t k, int is_device, c
     std::memset(&d, 0, sizeof(d));
     d.scan = h.scan.scan;
     d.rot = h.scan.rot;
+    d.cs = h.scan.cs;
     d.K = (int32_t)k;
     d.lmax = g.levels - 1;
     d.batch = (opts && opts->batch > 0) ? opts->batch : 10000;
@@ -1071,6 +1074,7 @@ int Engine::build_graph()
         plan_kernel<<<1, 1024, 0, cs>>>(d_S_, n, d_plan_, d_poff_, d_toff_, surv_.count, cond);
         gather_kernel<<<dim3(256, (unsigned)std::min(n, 65535)), CH, 0, cs>>>(d_S_, pool_, d_poff_, d_toff_, n, parents_,
                                                                               pfirst_, tasks_, d_plan_);
+        launch_task_rows(d_plan_, d_S_, tasks_, nsm_ * 4, cs);
         launch_branch(MODE_SEARCH, d_plan_, d_S_, parents_, tasks_, dense_, nsm_ * BRANCH_CTAS_PER_SM, cs);
         launch_finalize(MODE_SEARCH, d_plan_, d_S_, parents_, tasks_, dense_, surv_, nsm_ * 8, cs);
         alloc_kernel<<<n, 1024, 0, cs>>>(d_S_, n, pool_, d_plan_);
@@ -1106,7 +1110,7 @@ int Engine::iterate(int max_iters, std::vector<int>* finished)
     BBS_CUDA_TRY(cudaMemcpyAsync(st2, &d_plan_->status, sizeof(st2), cudaMemcpyDeviceToHost, st_));
     BBS_TRY(read_ctl());
     const int32_t status = st2[0];
-    launches_ += 7 * (int64_t)st2[1];   // every iteration of the loop runs the body's 7 kernels
+    launches_ += 8 * (int64_t)st2[1];   // every iteration of the loop runs the body's 8 kernels
     mark_finished(finished);
     if (status == PLAN_OVERFLOW) return process_popped();   // the selected round did not fit on the device
     return BBS_OK;
@@ -1232,6 +1236,10 @@ int Engine::score_launch(int mode, const std::vector<Seg>& segs, int64_t n_slice
     // pageable source: staged before cudaMemcpyAsync returns, so h_plan_ may be rewritten
     BBS_CUDA_TRY(cudaMemcpyAsync(d_plan_, &h_plan_, offsetof(Plan, seg) + sizeof(Seg) * segs.size(),
                                  cudaMemcpyHostToDevice, st_));
+    if (mode == MODE_SEARCH) {
+        BBS_CUDA_TRY(launch_task_rows(d_plan_, d_S_, tasks_, (int)std::min<int64_t>((n_tasks + 31) / 32, 4 * nsm_), st_));
+        launches_ += 1;
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (timed_) {
         BBS_CUDA_TRY(cudaEventCreate(&e0));

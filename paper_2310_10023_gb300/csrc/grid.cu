@@ -1,10 +1,11 @@
 // grid.cu -- pose grid (Sec. III-B Eq. (2)-(5), Sec. III-D Eq. (12)-(14)),
 // scan upload and the per-level rotation tables.
 //
-// The grid is host FP64 arithmetic (a few hundred values).  The rotation
-// tables are built on the GPU from host cos/sin values with IEEE FP64
-// products, sums and a correctly rounded division (__dmul_rn, __dadd_rn,
-// __ddiv_rn), then rounded once to FP32: A = fl32(R / r).  Host code is
+// The grid is host FP64 arithmetic (a few hundred values).  Rotation rows
+// are formed on the GPU from host cos/sin values with IEEE FP64 products and
+// sums (__dmul_rn, __dadd_rn), then A = fl32(R / r) with the correctly
+// rounded quotient (rotation_rows, bbs_internal.cuh): the top level's table
+// here, every other level's rows as the search expands rotations.  Host code is
 // compiled with -ffp-contract=off and device code with -fmad=false, so every
 // FP64 operation rounds on its own.
 #include <cmath>
@@ -94,6 +95,13 @@ int grid_build(double r, int levels, double d_max, const bbs_ranges* rg, uint32_
     }
     if (off > ((int64_t)1 << 26)) return set_error(BBS_EINVAL, "grid: %lld rotations in total", (long long)off);
     g->total_rot = off;
+    int64_t cso = 0;
+    for (int l = 0; l < levels; ++l)
+        for (int i = 0; i < 3; ++i) {
+            g->cs_off[l][i] = cso;
+            cso += g->N[l][i];
+        }
+    g->n_cs = cso;
     return BBS_OK;
 }
 
@@ -117,8 +125,10 @@ DevGrid dev_grid(const HostGrid& g)
             d.N[l][i] = (int32_t)g.N[l][i];
             d.a[l][i] = (int32_t)g.a[l][i];
         }
-        d.rot_off[l] = g.rot_off[l];
+        for (int i = 0; i < 3; ++i) d.cs_off[l][i] = (int32_t)g.cs_off[l][i];
     }
+    d.r = g.r;
+    d.inv_r = 1.0 / g.r;
     return d;
 }
 
@@ -164,33 +174,12 @@ __global__ void scan_pack_kernel(const float* __restrict__ xyz, int64_t k, float
     }
 }
 
-// A = fl32(R / r), R = Rz(gamma) Ry(beta) Rx(alpha) (Sec. III-A angles);
-// cs holds (cos, sin) of every segment angle, per level and axis.
-__global__ void rotation_table_kernel(const double2* __restrict__ cs, DevGrid g, const int64_t* __restrict__ cs_off,
-                                      int64_t total, double r, float4* __restrict__ out)
+// the rows of every rotation of one level (rotation_rows)
+__global__ void level_rows_kernel(const double2* __restrict__ cs, DevGrid g, int level, int64_t n, float4* __restrict__ out)
 {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        int l = 0;
-        while (l + 1 < g.levels && t >= g.rot_off[l + 1]) ++l;
-        const int64_t rot = t - g.rot_off[l];
-        const int64_t ng = g.N[l][2], nb = g.N[l][1];
-        const int64_t ig = rot % ng, ib = (rot / ng) % nb, ia = rot / (ng * nb);
-        const double2 A_ = cs[cs_off[3 * l + 0] + ia];
-        const double2 B_ = cs[cs_off[3 * l + 1] + ib];
-        const double2 G_ = cs[cs_off[3 * l + 2] + ig];
-        const double ca = A_.x, sa = A_.y, cb = B_.x, sb = B_.y, cg = G_.x, sg = G_.y;
-        double R[9];
-        R[0] = __dmul_rn(cg, cb);
-        R[1] = __dsub_rn(__dmul_rn(__dmul_rn(cg, sb), sa), __dmul_rn(sg, ca));
-        R[2] = __dadd_rn(__dmul_rn(__dmul_rn(cg, sb), ca), __dmul_rn(sg, sa));
-        R[3] = __dmul_rn(sg, cb);
-        R[4] = __dadd_rn(__dmul_rn(__dmul_rn(sg, sb), sa), __dmul_rn(cg, ca));
-        R[5] = __dsub_rn(__dmul_rn(__dmul_rn(sg, sb), ca), __dmul_rn(cg, sa));
-        R[6] = -sb;
-        R[7] = __dmul_rn(cb, sa);
-        R[8] = __dmul_rn(cb, ca);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         float A[9];
-        for (int i = 0; i < 9; ++i) A[i] = __double2float_rn(__ddiv_rn(R[i], r));
+        rotation_rows(cs, g, level, (uint32_t)t, A);
         out[3 * t + 0] = make_float4(A[0], A[1], A[2], 0.0f);
         out[3 * t + 1] = make_float4(A[3], A[4], A[5], 0.0f);
         out[3 * t + 2] = make_float4(A[6], A[7], A[8], 0.0f);
@@ -253,42 +242,44 @@ int scan_prepare(const bbs_maps* m, const float* xyz, int64_t k, int is_device, 
         scan_release(out, st);
         return rc;
     }
-    // cos / sin of every segment angle (host libm, FP64)
+    // cos / sin of every segment angle (host libm, FP64), kept on the device:
+    // the search forms the rotation rows of the rotations it expands
     const HostGrid& g = out->grid;
-    std::vector<double2> cs;
-    std::vector<int64_t> cs_off(3 * MAX_LEVELS, 0);
+    std::vector<double2> cs((size_t)g.n_cs);
     for (int l = 0; l < g.levels; ++l)
-        for (int i = 0; i < 3; ++i) {
-            cs_off[3 * l + i] = (int64_t)cs.size();
+        for (int i = 0; i < 3; ++i)
             for (int64_t c = 0; c < g.N[l][i]; ++c) {
                 const double ang = grid_angle(g, l, i, c);
-                cs.push_back(make_double2(std::cos(ang), std::sin(ang)));
+                cs[(size_t)(g.cs_off[l][i] + c)] = make_double2(std::cos(ang), std::sin(ang));
             }
-        }
-    double2* d_cs = nullptr;
-    int64_t* d_off = nullptr;
-    BBS_CUDA_TRY(cudaMallocAsync((void**)&d_cs, sizeof(double2) * cs.size(), st));
-    BBS_CUDA_TRY(cudaMallocAsync((void**)&d_off, sizeof(int64_t) * cs_off.size(), st));
-    BBS_CUDA_TRY(cudaMemcpyAsync(d_cs, cs.data(), sizeof(double2) * cs.size(), cudaMemcpyHostToDevice, st));
-    BBS_CUDA_TRY(cudaMemcpyAsync(d_off, cs_off.data(), sizeof(int64_t) * cs_off.size(), cudaMemcpyHostToDevice, st));
-    out->h2d += (int64_t)(sizeof(double2) * cs.size() + sizeof(int64_t) * cs_off.size());
-    BBS_CUDA_TRY(cudaMallocAsync((void**)&out->rot, sizeof(float4) * 3 * (size_t)g.total_rot, st));
-    rotation_table_kernel<<<grid_blocks(g.total_rot, 256), 256, 0, st>>>(d_cs, dev_grid(g), d_off, g.total_rot,
-                                                                          (double)m->r, out->rot);
-    BBS_CUDA_TRY(cudaGetLastError());
-    // the host vectors may go: a copy from pageable memory has staged its
+    BBS_CUDA_TRY(cudaMallocAsync((void**)&out->cs, sizeof(double2) * cs.size(), st));
+    BBS_CUDA_TRY(cudaMemcpyAsync(out->cs, cs.data(), sizeof(double2) * cs.size(), cudaMemcpyHostToDevice, st));
+    out->h2d += (int64_t)(sizeof(double2) * cs.size());
+    // the top level's rows (the initial set scores every one of them)
+    const int top = g.levels - 1;
+    BBS_CUDA_TRY(cudaMallocAsync((void**)&out->rot, sizeof(float4) * 3 * (size_t)g.nrot[top], st));
+    BBS_CUDA_TRY(launch_level_rows(*out, top, out->rot, st));
+    // the host vector may go: a copy from pageable memory has staged its
     // source by the time cudaMemcpyAsync returns
-    cudaFreeAsync(d_cs, st);
-    cudaFreeAsync(d_off, st);
     return BBS_OK;
+}
+
+cudaError_t launch_level_rows(const ScanState& s, int level, float4* out, cudaStream_t st)
+{
+    const int64_t n = s.grid.nrot[level];
+    if (n <= 0) return cudaSuccess;
+    level_rows_kernel<<<grid_blocks(n, 256), 256, 0, st>>>(s.cs, dev_grid(s.grid), level, n, out);
+    return cudaGetLastError();
 }
 
 void scan_release(ScanState* s, cudaStream_t st)
 {
     if (s->scan) cudaFreeAsync(s->scan, st);
     if (s->rot) cudaFreeAsync(s->rot, st);
+    if (s->cs) cudaFreeAsync(s->cs, st);
     s->scan = nullptr;
     s->rot = nullptr;
+    s->cs = nullptr;
 }
 
 }  // namespace bbs

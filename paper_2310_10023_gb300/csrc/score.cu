@@ -29,8 +29,10 @@ __global__ void __launch_bounds__(256) score_nodes_kernel(ScoreArgs a)
             continue;
         }
         const int64_t rot = ((int64_t)c[3] * a.grid.N[l][1] + c[4]) * a.grid.N[l][2] + c[5];
-        const float4* A = a.rot + 3 * (a.grid.rot_off[l] + rot);
-        const float4 r0 = A[0], r1 = A[1], r2 = A[2];
+        float A[9];
+        rotation_rows(a.cs, a.grid, l, (uint32_t)rot, A);
+        const float4 r0 = make_float4(A[0], A[1], A[2], 0.0f), r1 = make_float4(A[3], A[4], A[5], 0.0f),
+                     r2 = make_float4(A[6], A[7], A[8], 0.0f);
         const LevelView L = a.maps[l];
         uint32_t hits = 0;
         for (int64_t k = lane; k < a.k; k += 32) {
@@ -52,7 +54,7 @@ int launch_score_nodes(const bbs_maps* m, const ScanState& s, const int32_t* d_n
     ScoreArgs a;
     for (int l = 0; l < MAX_LEVELS; ++l) a.maps[l] = l < m->levels ? level_view(m, l) : LevelView{};
     a.grid = dev_grid(s.grid);
-    a.rot = s.rot;
+    a.cs = s.cs;
     a.scan = s.scan;
     a.k = s.k;
     a.nodes = d_nodes;

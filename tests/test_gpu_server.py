@@ -78,21 +78,23 @@ def test_served_results_equal_alone(nv, two_maps):
 def test_budget_admission_and_rejection(nv, two_maps):
     w, dm = two_maps["indoor"]
     rg, op = _args(nv, w)
-    s, _ = synth.make_scan(2, 3)
-    # budget: the pool plus room for about one indoor search at a time
+    s0, _ = synth.make_scan(2, 3)
+    # a search holds about 84 bytes per scan point (the scan and K + 1 score
+    # buckets); 64 copies of the scan (~0.5 M points, ~43 MB) against room for
+    # 64 MB beyond the pool admit one search at a time
+    s = np.tile(s0, (64, 1))
     probe = nv.bbs_server_create(mem_budget=1 << 40, max_active=4, max_frontier=1 << 20)
     fixed = nv.bbs_server_stats(probe)["mem_in_use"]
     probe.close()
-    srv = nv.bbs_server_create(mem_budget=fixed + (120 << 20), max_active=4, max_frontier=1 << 20)
+    srv = nv.bbs_server_create(mem_budget=fixed + (64 << 20), max_active=4, max_frontier=1 << 20)
     tickets = [nv.bbs_server_submit(srv, dm, s, rg, op) for _ in range(3)]
     saw_queue = nv.bbs_server_stats(srv)["queued"] > 0
     res = [nv.bbs_server_poll(srv, t, -1) for t in tickets]
     assert all(st == nv.OK for st, _ in res)
     assert len({(r.best_score, tuple(r.node)) for _, r in res}) == 1
     assert saw_queue or nv.bbs_server_stats(srv)["completed"] == 3
-    # a request that can never fit fails at once: three times the range gives
-    # about 27 times the rotations (Eq. (2)), far beyond the budget
-    big = (s * np.float32(3.0)).astype(np.float32)
+    # a request that can never fit fails at once: four times the points
+    big = np.tile(s, (4, 1))
     t = nv.bbs_server_submit(srv, dm, big, rg, op)
     st, r = nv.bbs_server_poll(srv, t, 10000)
     assert st == nv.ENOMEM
