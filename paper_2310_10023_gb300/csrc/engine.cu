@@ -634,6 +634,7 @@ Engine::~Engine()
     if (h_ctl_) cudaFreeHost(h_ctl_);
     if (h_poff_) cudaFreeHost(h_poff_);
     if (h_toff_) cudaFreeHost(h_toff_);
+    if (h_misc_) cudaFreeHost(h_misc_);
 }
 
 int Engine::init()
@@ -683,6 +684,8 @@ int Engine::init()
     BBS_CUDA_TRY(cudaMallocHost((void**)&h_ctl_, sizeof(Ctl) * (size_t)max_slots_));
     BBS_CUDA_TRY(cudaMallocHost((void**)&h_poff_, sizeof(int64_t) * (size_t)max_slots_));
     BBS_CUDA_TRY(cudaMallocHost((void**)&h_toff_, sizeof(int64_t) * (size_t)max_slots_));
+    BBS_CUDA_TRY(cudaMallocHost((void**)&h_misc_, 4 * sizeof(int32_t)));
+    std::memset(h_misc_, 0, 4 * sizeof(int32_t));
     {
         int dev = 0, nsm = 0;
         BBS_CUDA_TRY(cudaGetDevice(&dev));
@@ -934,6 +937,7 @@ void Engine::finish_never_live(std::vector<int>* finished)
 int Engine::read_ctl()
 {
     BBS_CUDA_TRY(cudaMemcpyAsync(h_ctl_, d_ctl_, sizeof(Ctl) * (size_t)max_slots_, cudaMemcpyDeviceToHost, st_));
+    BBS_CUDA_TRY(cudaMemcpyAsync(&h_misc_[2], surv_.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
     BBS_CUDA_TRY(cudaStreamSynchronize(st_));
     for (int i = 0; i < max_slots_; ++i)
         if (hosts_[(size_t)i].live) hosts_[(size_t)i].res.d2h_bytes += (int64_t)sizeof(Ctl);
@@ -1106,11 +1110,11 @@ int Engine::iterate(int max_iters, std::vector<int>* finished)
     h_plan_.max_iters = max_iters > 0 ? max_iters : 1;
     BBS_CUDA_TRY(cudaMemcpyAsync(&d_plan_->iters, &h_plan_.iters, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, st_));
     BBS_CUDA_TRY(cudaGraphLaunch(exec_, st_));
-    int32_t st2[2] = {0, 0};   // status, iterations the device loop ran
-    BBS_CUDA_TRY(cudaMemcpyAsync(st2, &d_plan_->status, sizeof(st2), cudaMemcpyDeviceToHost, st_));
+    // status and the iterations the device loop ran, with the control blocks
+    BBS_CUDA_TRY(cudaMemcpyAsync(h_misc_, &d_plan_->status, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
     BBS_TRY(read_ctl());
-    const int32_t status = st2[0];
-    launches_ += 8 * (int64_t)st2[1];   // every iteration of the loop runs the body's 8 kernels
+    const int32_t status = h_misc_[0];
+    launches_ += 8 * (int64_t)h_misc_[1];   // every iteration of the loop runs the body's 8 kernels
     mark_finished(finished);
     if (status == PLAN_OVERFLOW) return process_popped();   // the selected round did not fit on the device
     return BBS_OK;
@@ -1119,12 +1123,13 @@ int Engine::iterate(int max_iters, std::vector<int>* finished)
 int Engine::finalize(int i, bbs_result* out)
 {
     SearchHost& h = hosts_[(size_t)i];
-    int herr = 0;
+    // the control block and the staging error flag as the last read_ctl saw
+    // them: a finished search's block no longer changes
+    const int herr = h_misc_[2];
     Ctl c;
     std::memset(&c, 0, sizeof(c));
-    BBS_CUDA_TRY(cudaMemcpyAsync(&herr, surv_.err, sizeof(int), cudaMemcpyDeviceToHost, st_));
-    if (h.scan.k > 0) BBS_CUDA_TRY(cudaMemcpyAsync(&c, d_ctl_ + i, sizeof(Ctl), cudaMemcpyDeviceToHost, st_));
-    BBS_CUDA_TRY(cudaStreamSynchronize(st_));
+    if (h.scan.k > 0) c = h_ctl_[i];
+    if (!evs_.empty()) BBS_CUDA_TRY(cudaEventSynchronize(evs_.back()));
     for (size_t e = 0; e + 1 < evs_.size(); e += 2) {
         float ms = 0.0f;
         BBS_CUDA_TRY(cudaEventElapsedTime(&ms, evs_[e], evs_[e + 1]));

@@ -109,6 +109,7 @@ class Engine {
     Ctl* h_ctl_ = nullptr;
     int64_t* h_poff_ = nullptr;
     int64_t* h_toff_ = nullptr;
+    int32_t* h_misc_ = nullptr;   // pinned: plan status, loop iterations, staging error
     int nsm_ = 152;
     Plan* d_plan_ = nullptr;
     Plan h_plan_{};
