@@ -160,6 +160,16 @@ struct __align__(16) NodeRec {
 };
 
 __host__ __device__ __forceinline__ uint32_t rl_pack(uint32_t rot, int level) { return (rot << 5) | (uint32_t)level; }
+
+// Lexicographic order of leaves (Algorithm 2's tie rule among equal scores):
+// translation indices (c_x, c_y, c_z) first, as one 63-bit key of biased
+// 21-bit fields (leaf translations lie in [-2^20, 2^20)), then the rotation
+// index, whose order equals (c_alpha, c_beta, c_gamma) order.
+__host__ __device__ __forceinline__ unsigned long long lex_translation(const NodeRec& n)
+{
+    return ((unsigned long long)(uint32_t)(n.cx + KEY_LIMIT) << 42) | ((unsigned long long)(uint32_t)(n.cy + KEY_LIMIT) << 21) |
+           (unsigned long long)(uint32_t)(n.cz + KEY_LIMIT);
+}
 __host__ __device__ __forceinline__ int rl_level(uint32_t rl) { return (int)(rl & 31u); }
 __host__ __device__ __forceinline__ uint32_t rl_rot(uint32_t rl) { return rl >> 5; }
 

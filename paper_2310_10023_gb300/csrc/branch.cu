@@ -196,8 +196,8 @@ constexpr int64_t GRAB_MIN = 16;                // smallest dynamic grab (slices
 // and adding each run's 8 child counts to the dense scores at the round's end.
 template <int MODE>
 __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
-    branch3_kernel(Plan* __restrict__ P, const SearchDev* __restrict__ Sall, const NodeRec* __restrict__ parents,
-                   const TaskRec* __restrict__ tasks, int32_t* dense)
+    branch3_kernel(Plan* __restrict__ P, const SearchDev* __restrict__ Sall, const TaskRec* __restrict__ tasks,
+                   int32_t* dense)
 {
     if (P->status != PLAN_OK) return;
     __shared__ ulonglong2 sxy[PCHUNK / 2];
@@ -287,12 +287,11 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
                 m = S.lmax;
             } else {
                 const TaskRec& tr = tasks[g->first_task + u];
-                const NodeRec par = parents[tr.parent];
                 m = rl_level(tr.rl);
                 for (int i = 0; i < 9; ++i) A[i] = tr.a[i];
-                tx = 2 * par.cx;
-                ty = 2 * par.cy;
-                tz = 2 * par.cz;
+                tx = tr.tx;
+                ty = tr.ty;
+                tz = tr.tz;
             }
             const LevelView& L = S.maps[m];
             const bool cmp = L.compact != 0;
@@ -383,15 +382,17 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
     }
 }
 
-// survivors: children scoring above their search's best, staged with per-score
-// histograms (count, children, leaves) for the frontier insertion
+// survivors: children scoring above their search's best, appended to the
+// frontier array the next iteration reads, with their bucket counts
+// (nodes, children, leaves) and the search's size and top bucket
 template <int MODE>
 __global__ void __launch_bounds__(256) finalize_kernel(const Plan* __restrict__ P, SearchDev* S,
-                                                       const NodeRec* __restrict__ parents,
-                                                       const TaskRec* __restrict__ tasks, int32_t* dense, SurvOut out)
+                                                       const TaskRec* __restrict__ tasks, int32_t* dense, FrontDev F,
+                                                       LoopState* LS)
 {
     if (P->status != PLAN_OK) return;
     const int lane = threadIdx.x & 31;
+    const int nxt = 1 - LS->cur;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t n_dense = P->n_tasks * 8;
     const int64_t n_round = (n_dense + 31) & ~(int64_t)31;
@@ -422,13 +423,12 @@ __global__ void __launch_bounds__(256) finalize_kernel(const Plan* __restrict__ 
                 m = s.lmax;
                 crot = (uint32_t)(lu % g.R);
             } else {
-                const TaskRec tr = tasks[u];
-                const NodeRec par = parents[tr.parent];
+                const TaskRec& tr = tasks[u];
                 m = rl_level(tr.rl);
                 crot = rl_rot(tr.rl);
-                tx = 2 * par.cx + (j >> 2);
-                ty = 2 * par.cy + ((j >> 1) & 1);
-                tz = 2 * par.cz + (j & 1);
+                tx = tr.tx + (j >> 2);
+                ty = tr.ty + ((j >> 1) & 1);
+                tz = tr.tz + (j & 1);
             }
             // the dense array must be zero for the next launch: consume it
             const int32_t dv = dense[d];
@@ -445,34 +445,52 @@ __global__ void __launch_bounds__(256) finalize_kernel(const Plan* __restrict__ 
         const uint32_t ball = __ballot_sync(0xffffffffu, surv);
         if (!ball) continue;
         unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(out.count, (unsigned long long)__popc(ball));
+        if (lane == 0) base = atomicAdd(&LS->fn[nxt], (unsigned long long)__popc(ball));
         base = __shfl_sync(0xffffffffu, base, 0);
         const uint32_t key = surv ? (((uint32_t)sid << 24) | (uint32_t)score) : 0xFFFFFFFFu;
-        const uint32_t peers = __match_any_sync(0xffffffffu, key);
+        const uint32_t peers = __match_any_sync(0xffffffffu, key);                 // same search and score
+        const uint32_t same = __match_any_sync(0xffffffffu, surv ? sid : -1);      // same search
         if (surv) {
             SearchDev& s = S[sid];
-            const int64_t kids = node_children(s.grid, m, crot);
             const unsigned long long pos = base + __popc(ball & ((1u << lane) - 1u));
-            if (pos < (unsigned long long)out.cap) {
-                out.nodes[pos] = nd;
-                out.scores[pos] = score;
-                out.sid[pos] = sid;
-                out.ntask[pos] = (int32_t)(kids >> 3);
+            if (pos < (unsigned long long)F.cap) {
+                F.nodes[nxt][pos] = nd;
+                F.keys[nxt][pos] = key;
+                const int64_t kids = node_children(s.grid, m, crot);
+                if ((__ffs(peers) - 1) == lane) {
+                    atomicAdd(&s.b_cnt[score], (unsigned long long)__popc(peers));
+                    atomicMax(&s.ctl->top, score);
+                }
+                atomicAdd(&s.b_kids[score], (unsigned long long)kids);
+                if (m == 0) atomicAdd(&s.b_leaf[score], 1ull);
+                if ((__ffs(same) - 1) == lane) atomicAdd((unsigned long long*)&s.ctl->size, (unsigned long long)__popc(same));
             } else {
-                atomicOr(out.err, 2);
+                atomicOr(&s.ctl->err, 1);   // the frontier is full: the search fails
             }
-            if ((__ffs(peers) - 1) == lane) atomicAdd(&s.h_cnt[score], (uint32_t)__popc(peers));
-            atomicAdd(&s.h_kids[score], (unsigned long long)kids);
-            if (m == 0) atomicAdd(&s.h_leaf[score], 1u);
         }
     }
 }
 
-// the rotation rows of every task of a launch: warp e of a CTA forms entry e
-// of 32 tasks, so the FP64 chains are short and spread over the whole GPU
+// The rotation rows of every task of a launch: warp e of a CTA forms entry e
+// of 32 tasks, so the FP64 chains are short and spread over the whole GPU.
+// First, when a search popped a leaf bucket, the second pass of its lexmin
+// leaf: the smallest rotation among the bucket's leaves at the smallest
+// translation key (the first pass, in the compaction, found that key).
 __global__ void __launch_bounds__(288) task_rows_kernel(const Plan* __restrict__ P, const SearchDev* __restrict__ S,
-                                                        TaskRec* tasks)
+                                                        TaskRec* tasks, FrontDev F, const LoopState* LS)
 {
+    if (LS && LS->lex_pass) {
+        const int cur = LS->cur;
+        const int64_t n = min((int64_t)LS->fn[cur], F.cap);   // appends past the capacity were not stored
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+            const uint32_t key = F.keys[cur][i];
+            Ctl* c = S[key >> 24].ctl;
+            if (c->reason != 3 || (int32_t)(key & 0xFFFFFFu) != c->sstar) continue;
+            const NodeRec nd = F.nodes[cur][i];
+            if (rl_level(nd.rl) != 0) continue;
+            if (lex_translation(nd) == c->lex_t) atomicMin(&c->lex_r, rl_rot(nd.rl));
+        }
+    }
     if (P->status != PLAN_OK) return;
     const int64_t n = P->n_tasks;
     const int e = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -481,32 +499,36 @@ __global__ void __launch_bounds__(288) task_rows_kernel(const Plan* __restrict__
         const SearchDev& f = S[P->seg[find_task_seg(P, u)].sid];
         const uint32_t rl = tasks[u].rl;
         tasks[u].a[e] = rotation_entry(f.cs, f.grid, rl_level(rl), rl_rot(rl), e);
-        if (e == 0) tasks[u].pad = 0.0f;
+        if (e == 0) tasks[u].pad[0] = tasks[u].pad[1] = tasks[u].pad[2] = 0.0f;
     }
 }
 
-cudaError_t launch_task_rows(const Plan* P, const SearchDev* S, TaskRec* tasks, int blocks, cudaStream_t st)
+cudaError_t launch_task_rows(const Plan* P, const SearchDev* S, TaskRec* tasks, const FrontDev* F, const LoopState* LS,
+                             int blocks, cudaStream_t st)
 {
     if (blocks <= 0) return cudaSuccess;
-    task_rows_kernel<<<blocks, 288, 0, st>>>(P, S, tasks);
+    FrontDev f;
+    std::memset(&f, 0, sizeof(f));
+    if (F) f = *F;
+    task_rows_kernel<<<blocks, 288, 0, st>>>(P, S, tasks, f, F ? LS : nullptr);
     return cudaGetLastError();
 }
 
-cudaError_t launch_branch(int mode, Plan* P, const SearchDev* S, const NodeRec* parents, const TaskRec* tasks,
-                          int32_t* dense, int blocks, cudaStream_t st)
+cudaError_t launch_branch(int mode, Plan* P, const SearchDev* S, const TaskRec* tasks, int32_t* dense, int blocks,
+                          cudaStream_t st)
 {
     if (blocks <= 0) return cudaSuccess;
-    if (mode == MODE_INITIAL) branch3_kernel<MODE_INITIAL><<<blocks, 256, 0, st>>>(P, S, parents, tasks, dense);
-    else branch3_kernel<MODE_SEARCH><<<blocks, 256, 0, st>>>(P, S, parents, tasks, dense);
+    if (mode == MODE_INITIAL) branch3_kernel<MODE_INITIAL><<<blocks, 256, 0, st>>>(P, S, tasks, dense);
+    else branch3_kernel<MODE_SEARCH><<<blocks, 256, 0, st>>>(P, S, tasks, dense);
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(int mode, const Plan* P, SearchDev* S, const NodeRec* parents, const TaskRec* tasks,
-                            int32_t* dense, const SurvOut& out, int blocks, cudaStream_t st)
+cudaError_t launch_finalize(int mode, const Plan* P, SearchDev* S, const TaskRec* tasks, int32_t* dense,
+                            const FrontDev& F, LoopState* LS, int blocks, cudaStream_t st)
 {
     if (blocks <= 0) return cudaSuccess;
-    if (mode == MODE_INITIAL) finalize_kernel<MODE_INITIAL><<<blocks, 256, 0, st>>>(P, S, parents, tasks, dense, out);
-    else finalize_kernel<MODE_SEARCH><<<blocks, 256, 0, st>>>(P, S, parents, tasks, dense, out);
+    if (mode == MODE_INITIAL) finalize_kernel<MODE_INITIAL><<<blocks, 256, 0, st>>>(P, S, tasks, dense, F, LS);
+    else finalize_kernel<MODE_SEARCH><<<blocks, 256, 0, st>>>(P, S, tasks, dense, F, LS);
     return cudaGetLastError();
 }
 

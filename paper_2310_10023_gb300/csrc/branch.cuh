@@ -32,24 +32,26 @@ struct Ctl {
     int32_t top;           // every bucket above top is empty
     int32_t found;
     int32_t done;
-    NodeRec match;
+    int32_t sstar;         // last select: buckets above sstar popped
+    int32_t clear;         // last select: every other node dropped
+    unsigned long long lex_t;   // lexmin leaf of a popped leaf bucket: translation key,
+    uint32_t lex_r;             // then rotation (Algorithm 2's tie rule)
+    int32_t err;           // 1 frontier full, 4 inconsistent counts
     int64_t size;          // nodes in F
-    int64_t peak;          // largest size after an insertion
+    int64_t peak;          // largest size seen by a select
     int64_t n_parents;     // parents popped by the last select
-    int64_t n_pop;         // chunks popped by the last select
-    int64_t n_act;         // chunks in use
-    int64_t popped_kids;   // children of the parents popped by the last select
-    int64_t n_tasks;       // rotational-child tasks of those parents (popped_kids / 8)
-    int32_t err;           // 1 pool exhausted, 4 inconsistent task counts
+    int64_t n_tasks;       // their rotational children (tasks)
+    int64_t popped_kids;   // their children (8 per task)
     int32_t reason;        // last select: 1 batch full, 2 below best, 3 leaf, 4 F emptied, 0 F was empty
     int32_t match_changed;
     int32_t active;        // slot in use
+    int32_t pad;
     // statistics kept on the device (the search loop may run without the host)
     int64_t st_iters, st_parents, st_nodes, st_gathers;
     unsigned long long t_start_ns, t_match_ns, t_end_ns;   // %globaltimer
 };
 
-// One search slot (device).  Frontier arrays have K + 1 buckets.
+// One search slot (device).  Bucket arrays have K + 1 entries (scores 0..K).
 struct SearchDev {
     const float4* scan;
     const float4* rot;          // rows of the top level's rotations
@@ -63,47 +65,41 @@ struct SearchDev {
     int32_t wmin[3], wmax[3];   // initial translation window, Eq. (3)-(5)
     DevGrid grid;
     LevelView maps[MAX_LEVELS];
-    int64_t* b_cnt;
-    int64_t* b_kids;
-    int64_t* b_leaf;
-    int32_t* b_tail;
-    uint32_t* h_cnt;
-    unsigned long long* h_kids;
-    uint32_t* h_leaf;
-    uint32_t* w_pos;
-    int32_t* w_space;
-    int64_t* w_choff;
-    int32_t* w_tail;
-    int32_t* w_fill0;
-    int32_t* act;
-    int32_t* pop_ids;
-    int64_t* pop_start;         // parent offset of each popped chunk in the search's parents
-    int64_t* pop_tstart;        // task offset of each popped chunk in the search's tasks
+    unsigned long long* b_cnt;  // nodes per score bucket
+    unsigned long long* b_kids; // their children
+    unsigned long long* b_leaf; // their leaves
     Ctl* ctl;                   // this search's control block (contiguous across searches)
 };
 
-// The shared chunk pool (device).
-struct PoolDev {
-    NodeRec* nodes;
-    int32_t* chunk_bucket;
-    int32_t* chunk_fill;
-    int32_t* chunk_tasks;       // rotational-child tasks of the chunk's nodes
-    int32_t* free_ids;
-    unsigned long long* free_top;
-    int64_t nchunks;
+// The frontier of every search: nodes with key score | search << 24, in two
+// arrays that swap roles each iteration (the current nodes are read, kept and
+// new ones are appended to the other).
+struct FrontDev {
+    NodeRec* nodes[2];
+    uint32_t* keys[2];
+    int64_t cap;
+};
+
+// Device state of the iteration loop.
+struct LoopState {
+    unsigned long long fn[2];   // nodes in each frontier array
+    int32_t cur;                // the array holding the current nodes
+    int32_t lex_pass;           // a search popped a leaf bucket this iteration
+    uint32_t select_done;       // select CTAs finished this iteration (the last one plans)
+    int32_t pad;
 };
 
 enum { MODE_INITIAL = 0, MODE_SEARCH = 1, MODE_DENSE = 2 };
 
-// One rotational child of a scoring round: its parent (index into the
-// round's parent array), rl_pack(child rotation, child level) and the
-// rotation's rows (rotation_rows).  Its 8
-// translational children are the dense scores 8 * task .. 8 * task + 7.
+// One rotational child of a scoring round: its parent's translation,
+// rl_pack(child rotation, child level) and the rotation's rows
+// (rotation_rows).  Its 8 translational children are the dense scores
+// 8 * task .. 8 * task + 7.
 struct __align__(16) TaskRec {
-    int32_t parent;
+    int32_t tx, ty, tz;     // 2 x the parent's translation indices (the children add {0,1}^3)
     uint32_t rl;
     float a[9];             // the child rotation's A = fl32(R / r), row-major
-    float pad;
+    float pad[3];
 };
 
 // A run of tasks of one search inside a scoring launch.  The run's work is
@@ -139,17 +135,6 @@ struct Plan {
     Seg seg[MAXSEG];
 };
 
-// survivors of a finalize pass
-struct SurvOut {
-    NodeRec* nodes;
-    int32_t* scores;
-    int32_t* sid;
-    int32_t* ntask;         // rotational children of the survivor
-    unsigned long long* count;
-    int64_t cap;
-    int* err;
-};
-
 // rotational children of a node at level l with rotation index rot, Eq. (13):
 // first child and count per axis at level l - 1; their number (0 at the leaf level)
 __host__ __device__ __forceinline__ int32_t rot_children(const DevGrid& g, int l, uint32_t rot, int32_t lo[3],
@@ -172,8 +157,11 @@ __host__ __device__ __forceinline__ int32_t rot_children(const DevGrid& g, int l
     return n;
 }
 
-// the rotation rows of the launch's task records from their rl; skips unless PLAN_OK
-cudaError_t launch_task_rows(const Plan* P, const SearchDev* S, TaskRec* tasks, int blocks, cudaStream_t st);
+// the rotation rows of the launch's task records from their rl (when the plan
+// is PLAN_OK); with LS, first the second pass of the lexmin leaf search over
+// the current frontier
+cudaError_t launch_task_rows(const Plan* P, const SearchDev* S, TaskRec* tasks, const FrontDev* F, const LoopState* LS,
+                             int blocks, cudaStream_t st);
 
 // CTAs of a scoring launch: one resident wave (4 CTAs of 256 threads per SM, 64 registers a thread)
 constexpr int BRANCH_CTAS_PER_SM = 4;
@@ -181,9 +169,11 @@ constexpr int BRANCH_CTAS_PER_SM = 4;
 // scoring and survivor kernels of one launch; `blocks` is the grid (the
 // scoring kernel splits the plan's slices evenly over it, the survivor kernel
 // strides), each returns at once unless the plan is PLAN_OK
-cudaError_t launch_branch(int mode, Plan* P, const SearchDev* S, const NodeRec* parents, const TaskRec* tasks,
-                          int32_t* dense, int blocks, cudaStream_t st);
-cudaError_t launch_finalize(int mode, const Plan* P, SearchDev* S, const NodeRec* parents, const TaskRec* tasks,
-                            int32_t* dense, const SurvOut& out, int blocks, cudaStream_t st);
+cudaError_t launch_branch(int mode, Plan* P, const SearchDev* S, const TaskRec* tasks, int32_t* dense, int blocks,
+                          cudaStream_t st);
+// survivors (score above their search's best) are appended to the frontier
+// array the next iteration reads, with their bucket counts
+cudaError_t launch_finalize(int mode, const Plan* P, SearchDev* S, const TaskRec* tasks, int32_t* dense,
+                            const FrontDev& F, LoopState* LS, int blocks, cudaStream_t st);
 
 }  // namespace bbs

@@ -283,6 +283,7 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
     // the tasks (rotational children) in parent order, child order ja, jb, jg
     const int64_t ntask = total / 8;
     std::vector<TaskRec> tk((size_t)ntask);
+    std::vector<int64_t> tk_parent((size_t)ntask);
     {
         int64_t u = 0;
         for (int64_t p = 0; p < n; ++p) {
@@ -296,8 +297,11 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
                             (uint32_t)(((int64_t)(plo[0] + ja) * g.N[l - 1][1] + (plo[1] + jb)) * g.N[l - 1][2] + (plo[2] + jg));
                         TaskRec r;
                         std::memset(&r, 0, sizeof(r));
-                        r.parent = (int32_t)p;
+                        r.tx = 2 * recs[(size_t)p].cx;
+                        r.ty = 2 * recs[(size_t)p].cy;
+                        r.tz = 2 * recs[(size_t)p].cz;
                         r.rl = rl_pack(crot, l - 1);
+                        tk_parent[(size_t)u] = p;
                         tk[(size_t)u++] = r;   // rows filled on the device
                     }
         }
@@ -314,12 +318,10 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
     sd.grid = dgr;
     for (int l = 0; l < MAX_LEVELS; ++l) sd.maps[l] = l < m->levels ? level_view(m, l) : LevelView{};
     SearchDev* d_sd = nullptr;
-    NodeRec* d_par = nullptr;
     TaskRec* d_tk = nullptr;
     int32_t* d_dense = nullptr;
     Plan* d_plan = nullptr;
     BBS_CUDA_TRY(cudaMallocAsync((void**)&d_sd, sizeof(SearchDev), st));
-    BBS_CUDA_TRY(cudaMallocAsync((void**)&d_par, sizeof(NodeRec) * (size_t)n, st));
     BBS_CUDA_TRY(cudaMallocAsync((void**)&d_tk, sizeof(TaskRec) * (size_t)ntask, st));
     BBS_CUDA_TRY(cudaMallocAsync((void**)&d_dense, sizeof(int32_t) * (size_t)total, st));
     BBS_CUDA_TRY(cudaMallocAsync((void**)&d_plan, sizeof(Plan), st));
@@ -336,7 +338,6 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
     P.seg[0].sid = 0;
     P.seg[0].nblk = sd.nblk;
     BBS_CUDA_TRY(cudaMemcpyAsync(d_sd, &sd, sizeof(sd), cudaMemcpyHostToDevice, st));
-    BBS_CUDA_TRY(cudaMemcpyAsync(d_par, recs.data(), sizeof(NodeRec) * (size_t)n, cudaMemcpyHostToDevice, st));
     BBS_CUDA_TRY(cudaMemcpyAsync(d_tk, tk.data(), sizeof(TaskRec) * tk.size(), cudaMemcpyHostToDevice, st));
     BBS_CUDA_TRY(cudaMemcpyAsync(d_plan, &P, offsetof(Plan, seg) + sizeof(Seg), cudaMemcpyHostToDevice, st));
     BBS_CUDA_TRY(cudaMemsetAsync(d_dense, 0, sizeof(int32_t) * (size_t)total, st));
@@ -344,10 +345,10 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     int rc = BBS_OK;
-    cudaError_t e = launch_task_rows(d_plan, d_sd, d_tk, (int)std::min<int64_t>((ntask + 31) / 32, 4096), st);
+    cudaError_t e = launch_task_rows(d_plan, d_sd, d_tk, nullptr, nullptr, (int)std::min<int64_t>((ntask + 31) / 32, 4096), st);
     if (e == cudaSuccess)
-        e = launch_branch(MODE_SEARCH, d_plan, d_sd, d_par, d_tk, d_dense,
-                                  (int)std::min<int64_t>(P.n_slices, (int64_t)nsm * BRANCH_CTAS_PER_SM), st);
+        e = launch_branch(MODE_SEARCH, d_plan, d_sd, d_tk, d_dense,
+                          (int)std::min<int64_t>(P.n_slices, (int64_t)nsm * BRANCH_CTAS_PER_SM), st);
     std::vector<int32_t> dense((size_t)total);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dense.data(), d_dense, sizeof(int32_t) * dense.size(), cudaMemcpyDeviceToHost, st);
@@ -355,7 +356,6 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
     if (e != cudaSuccess) rc = set_error(BBS_ECUDA, "score_children: %s", cudaGetErrorString(e));
     cudaFreeAsync(d_plan, st);
     cudaFreeAsync(d_sd, st);
-    cudaFreeAsync(d_par, st);
     cudaFreeAsync(d_tk, st);
     cudaFreeAsync(d_dense, st);
     if (rc != BBS_OK) return rc;
@@ -363,7 +363,7 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
     int64_t o = 0;
     for (int64_t u = 0; u < ntask; ++u) {
         const TaskRec& r = tk[(size_t)u];
-        const int32_t* c = &hp[(size_t)(7 * r.parent)];
+        const int32_t* c = &hp[(size_t)(7 * tk_parent[(size_t)u])];
         const int l = c[6];
         const uint32_t crot = rl_rot(r.rl);
         const int32_t ng = g.N[l - 1][2], nb = g.N[l - 1][1];

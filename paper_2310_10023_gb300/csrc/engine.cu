@@ -1,22 +1,29 @@
 // engine.cu -- device-resident batched best-first BnB (Sec. III-E,
 // Algorithm 2) for one or many searches at once.
 //
-// Every search owns a frontier F of scored nodes bucketed by integer score;
-// node records live in chunks of CH from one shared free-chunk stack.  A
-// search's non-empty bucket owns its chunks (all full but its tail) and every
-// chunk in use is listed in the search's active list, tagged by bucket.
+// Every search keeps its frontier F as per-score bucket counts (nodes,
+// children, leaves per integer score, K + 1 buckets) over node records that
+// all searches share: two arrays of (node, score | search << 24) that swap
+// roles every iteration.
 //
 // One iteration advances every live search by one canonical batch:
-//   select  (1 CTA per search) walk buckets from the top with a block-wide
-//           prefix of their children counts; the first bucket reached with
-//           children(P) >= b stops, one at or below best clears F, one holding
-//           a leaf sets (best, lexmin leaf) and clears F; buckets above it pop.
-//   gather  popped chunks -> one dense parent array (all searches), chunks freed
-//   score   (branch.cu) every child of every parent; finalize keeps > best
-//   alloc   (1 CTA per search) chunks for each bucket's survivors
-//   scatter survivors into their buckets' chunks
+//   select   (1 CTA per search) walk the buckets from the top with a block-wide
+//            prefix of their children counts: the first bucket s* reached with
+//            children >= b stops; one at or below best clears F; one holding a
+//            leaf sets best = s* and clears F (its lexmin leaf is the match);
+//            buckets above s* pop.  The last CTA to finish plans the round: the
+//            parent and task ranges of every search and the scoring launch's
+//            slice map; it ends the device loop when the round is empty or too
+//            large for one launch, or after the iteration cap.
+//   compact  the current node array: popped nodes become parents and tasks
+//            (their rotational children), kept ones move to the other array,
+//            cleared ones go; a popped leaf bucket's leaves give the lexmin key
+//   rows     rotation rows of every task (and the lexmin rotation)
+//   score    (branch.cu) every child of every task; survivors above best are
+//            appended to the other array with their bucket counts
 // Only popping a leaf changes a search's best, so how its batch is split into
-// launches, and which other searches share them, cannot change its result.
+// launches, and which other searches share them, cannot change its result;
+// node order inside F is free.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -74,23 +81,6 @@ __device__ __forceinline__ int block_min_int(int v, int* sh)
     return r;
 }
 
-// lexicographic order of (c_x, c_y, c_z, rotation index); rotation index order
-// equals (c_alpha, c_beta, c_gamma) order
-struct LexKey {
-    unsigned long long t;
-    uint32_t r;
-};
-
-__device__ __forceinline__ LexKey lex_of(const NodeRec& n)
-{
-    LexKey k;
-    k.t = ((unsigned long long)(uint32_t)(n.cx + KEY_LIMIT) << 42) | ((unsigned long long)(uint32_t)(n.cy + KEY_LIMIT) << 21) |
-          (unsigned long long)(uint32_t)(n.cz + KEY_LIMIT);
-    k.r = rl_rot(n.rl);
-    return k;
-}
-
-__device__ __forceinline__ bool lex_lt(const LexKey& a, const LexKey& b) { return a.t < b.t || (a.t == b.t && a.r < b.r); }
 
 // ---- kernels -----------------------------------------------------------------
 
@@ -101,18 +91,7 @@ __device__ __forceinline__ unsigned long long gtimer_ns()
     return t;
 }
 
-__global__ void pool_init_kernel(PoolDev p)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.nchunks; i += (int64_t)gridDim.x * blockDim.x) {
-        p.free_ids[i] = (int32_t)(p.nchunks - 1 - i);
-        p.chunk_bucket[i] = -1;
-        p.chunk_fill[i] = 0;
-        p.chunk_tasks[i] = 0;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *p.free_top = (unsigned long long)p.nchunks;
-}
-
-// reset the frontier arrays of one search (blockIdx.x = slot in `slots`)
+// reset the bucket arrays of one search (blockIdx.x = slot in `slots`)
 __global__ void slot_init_kernel(SearchDev* S, const int32_t* slots)
 {
     SearchDev& s = S[slots[blockIdx.x]];
@@ -121,152 +100,29 @@ __global__ void slot_init_kernel(SearchDev* S, const int32_t* slots)
         s.b_cnt[i] = 0;
         s.b_kids[i] = 0;
         s.b_leaf[i] = 0;
-        s.b_tail[i] = -1;
-        s.h_cnt[i] = 0;
-        s.h_kids[i] = 0;
-        s.h_leaf[i] = 0;
-        s.w_pos[i] = 0;
     }
 }
 
-__global__ void __launch_bounds__(1024) alloc_kernel(SearchDev* S, int nslots, PoolDev pool, const Plan* P)
-{
-    if (P->status != PLAN_OK) return;
-    __shared__ int64_t sh[32];
-    __shared__ int64_t s_base;
-    __shared__ int s_min[33];
-    for (int si = blockIdx.x; si < nslots; si += gridDim.x) {
-        SearchDev& f = S[si];
-        Ctl* c = f.ctl;
-        if (!c->active || c->err) continue;
-        // survivors score above best: only those buckets can have new nodes
-        const int lo = c->best + 1 > 0 ? c->best + 1 : 0;
-        // pass 1: chunks needed by this search, claimed from the shared stack
-        int64_t need_sum = 0;
-        for (int s = lo + (int)threadIdx.x; s <= f.K; s += blockDim.x) {
-            const uint32_t h = f.h_cnt[s];
-            if (!h) continue;
-            const int32_t tail = f.b_tail[s];
-            const int32_t space = tail >= 0 ? CH - pool.chunk_fill[tail] : 0;
-            if ((int64_t)h > space) need_sum += ((int64_t)h - space + CH - 1) / CH;
-        }
-        int64_t tot;
-        block_excl_scan(need_sum, &tot, sh);
-        if (threadIdx.x == 0) {
-            s_base = -1;
-            if (tot > 0) {
-                const unsigned long long old = atomicAdd(pool.free_top, (unsigned long long)(-(long long)tot));
-                if ((long long)old - tot < 0) {
-                    atomicAdd(pool.free_top, (unsigned long long)tot);   // give the claim back
-                    c->err |= 1;
-                } else {
-                    s_base = (int64_t)old - tot;   // claimed stack entries [old - tot, old)
-                }
-            }
-        }
-        __syncthreads();
-        if (c->err) continue;
-        const int64_t claim_top = s_base + tot;   // stack index just above the claim
-        const int64_t act0 = c->n_act;
-        // pass 2: hand out the claimed chunks bucket by bucket
-        int64_t carry = 0, added = 0;
-        int top = -1;
-        for (int base = lo; base <= f.K; base += blockDim.x) {
-            const int s = base + threadIdx.x;
-            uint32_t h = 0;
-            int32_t tail = -1, fill0 = CH, space = 0;
-            int64_t need = 0;
-            if (s <= f.K) {
-                h = f.h_cnt[s];
-                if (h) {
-                    tail = f.b_tail[s];
-                    fill0 = tail >= 0 ? pool.chunk_fill[tail] : CH;
-                    space = CH - fill0;
-                    need = (int64_t)h > space ? ((int64_t)h - space + CH - 1) / CH : 0;
-                }
-            }
-            int64_t total;
-            const int64_t off = carry + block_excl_scan(need, &total, sh);
-            if (h) {
-                int32_t last = tail;
-                for (int64_t i = 0; i < need; ++i) {
-                    const int32_t id = pool.free_ids[claim_top - 1 - (off + i)];
-                    pool.chunk_bucket[id] = s;
-                    pool.chunk_fill[id] = (int32_t)(i < need - 1 ? CH : ((int64_t)h - space) - (need - 1) * CH);
-                    pool.chunk_tasks[id] = 0;
-                    f.act[act0 + off + i] = id;
-                    last = id;
-                }
-                if (tail >= 0) pool.chunk_fill[tail] = fill0 + (int32_t)((int64_t)h < space ? h : space);
-                f.w_space[s] = space;
-                f.w_choff[s] = claim_top - 1 - off;   // stack index of the bucket's first new chunk (counting down)
-                f.w_tail[s] = tail;
-                f.w_fill0[s] = fill0;
-                f.w_pos[s] = 0;
-                f.b_tail[s] = last;
-                f.b_cnt[s] += h;
-                f.b_kids[s] += (int64_t)f.h_kids[s];
-                f.b_leaf[s] += f.h_leaf[s];
-                f.h_cnt[s] = 0;
-                f.h_kids[s] = 0;
-                f.h_leaf[s] = 0;
-                added += h;
-                top = s > top ? s : top;
-            }
-            carry += total;
-        }
-        int64_t all_added;
-        block_excl_scan(added, &all_added, sh);
-        const int maxtop = -block_min_int(-top, s_min);
-        if (threadIdx.x == 0) {
-            c->n_act = act0 + carry;
-            c->size += all_added;
-            if (c->size > c->peak) c->peak = c->size;
-            if (maxtop > c->top) c->top = maxtop;
-        }
-        __syncthreads();
-    }
-}
-
-__global__ void scatter_kernel(SearchDev* S, PoolDev pool, const NodeRec* __restrict__ nodes,
-                               const int32_t* __restrict__ scores, const int32_t* __restrict__ sids,
-                               const int32_t* __restrict__ ntask, const unsigned long long* count, int64_t cap)
-{
-    int64_t n = (int64_t)*count;
-    if (n > cap) n = cap;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        SearchDev& f = S[sids[i]];
-        if (f.ctl->err) continue;
-        const int32_t s = scores[i];
-        const uint32_t rank = atomicAdd(&f.w_pos[s], 1u);
-        int32_t chunk, slot;
-        if ((int32_t)rank < f.w_space[s]) {
-            chunk = f.w_tail[s];
-            slot = f.w_fill0[s] + (int32_t)rank;
-        } else {
-            const int64_t idx = (int64_t)rank - f.w_space[s];
-            chunk = pool.free_ids[f.w_choff[s] - idx / CH];
-            slot = (int32_t)(idx % CH);
-        }
-        pool.nodes[(int64_t)chunk * CH + slot] = nodes[i];
-        if (ntask[i]) atomicAdd(&pool.chunk_tasks[chunk], ntask[i]);
-    }
-}
-
-__global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, PoolDev pool)
+// Selection (1 CTA per slot) and, in the last CTA to finish, the plan of the
+// round: per-search parent / task offsets and one task run per search.
+__global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, Plan* P, LoopState* LS,
+                                                      int64_t* poff, int64_t* toff, unsigned long long* pcnt,
+                                                      unsigned long long* tcnt, cudaGraphConditionalHandle cond,
+                                                      int use_cond)
 {
     __shared__ int64_t sh[32];
     __shared__ int s_min[33];
     __shared__ int32_t s_star, s_reason;
-    __shared__ LexKey s_lex[1024];
-    __shared__ NodeRec s_node[1024];
-    __shared__ int s_has[1024];
-    __shared__ unsigned long long s_ftop;
+    __shared__ int s_last;
     const int tid = threadIdx.x;
     for (int si = blockIdx.x; si < nslots; si += gridDim.x) {
         SearchDev& f = S[si];
         Ctl* c = f.ctl;
-        if (!c->active || c->done || c->err) continue;
+        if (!c->active || c->err) continue;   // uniform
+        if (c->done) {   // finished earlier: nothing of it takes part in this round
+            if (tid == 0) c->match_changed = 0;
+            continue;
+        }
         const int32_t best = c->best;
         if (tid == 0) {
             s_star = -1;
@@ -275,10 +131,11 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
         __syncthreads();
         // 1. the bucket where popping stops
         int64_t carry = 0;
-        for (int base = c->top; base >= 0; base -= blockDim.x) {
+        const int32_t top = c->top;
+        for (int base = top; base >= 0; base -= blockDim.x) {
             const int s = base - tid;
             const bool have = s >= 0 && f.b_cnt[s] > 0;
-            const int64_t kids = have ? f.b_kids[s] : 0;
+            const int64_t kids = have ? (int64_t)f.b_kids[s] : 0;
             int64_t tot;
             const int64_t cum = carry + block_excl_scan(kids, &tot, sh);
             const bool stop = have && (cum >= f.batch || s <= best || f.b_leaf[s] > 0);
@@ -296,261 +153,63 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
         const int32_t sstar = s_star;
         const int reason = s_reason;
         const bool clear = reason == 2 || reason == 3;
-        // 2. active list: pop chunks above s*, free the rest when clearing, lexmin leaf of s*
-        LexKey my_lex;
-        my_lex.t = ~0ull;
-        my_lex.r = ~0u;
-        NodeRec my_node;
-        my_node.cx = my_node.cy = my_node.cz = 0;
-        my_node.rl = 0;
-        int my_has = 0;
-        const int64_t n_act = c->n_act;
-        int64_t keep = 0, npop = 0, nfree = 0, nparents = 0, ntasks = 0;
-        // freed chunks go onto the shared stack: count them first, then claim
-        int64_t nfree_total = 0;
-        if (clear) {
-            for (int64_t i = tid; i < n_act; i += blockDim.x) {
-                const int32_t ch = f.act[i];
-                if (pool.chunk_bucket[ch] <= sstar) ++nfree_total;
-            }
-            int64_t t;
-            block_excl_scan(nfree_total, &t, sh);
-            nfree_total = t;
-        }
-        if (tid == 0) s_ftop = nfree_total ? atomicAdd(pool.free_top, (unsigned long long)nfree_total) : 0ull;
-        __syncthreads();
-        const int64_t fbase = (int64_t)s_ftop;
-        for (int64_t base = 0; base < n_act; base += blockDim.x) {
-            const int64_t i = base + tid;
-            const int32_t ch = i < n_act ? f.act[i] : -1;
-            const int32_t bk = ch >= 0 ? pool.chunk_bucket[ch] : -1;
-            const int32_t fill = ch >= 0 ? pool.chunk_fill[ch] : 0;
-            const int32_t ctasks = ch >= 0 ? pool.chunk_tasks[ch] : 0;
-            const bool popped = ch >= 0 && bk > sstar;
-            const bool freed = ch >= 0 && !popped && clear;
-            const bool kept = ch >= 0 && !popped && !clear;
-            if (reason == 3 && ch >= 0 && bk == sstar) {
-                for (int j = 0; j < fill; ++j) {
-                    const NodeRec nd = pool.nodes[(int64_t)ch * CH + j];
-                    if (rl_level(nd.rl) != 0) continue;
-                    const LexKey k = lex_of(nd);
-                    if (!my_has || lex_lt(k, my_lex)) {
-                        my_lex = k;
-                        my_node = nd;
-                        my_has = 1;
-                    }
-                }
-            }
-            int64_t t1, t2, t3, t4, t5;
-            const int64_t rp = block_excl_scan(popped ? 1 : 0, &t1, sh);
-            const int64_t rf = block_excl_scan(freed ? 1 : 0, &t2, sh);
-            const int64_t rk = block_excl_scan(kept ? 1 : 0, &t3, sh);
-            const int64_t rs = block_excl_scan(popped ? fill : 0, &t4, sh);
-            const int64_t rt = block_excl_scan(popped ? ctasks : 0, &t5, sh);
-            if (popped) {
-                f.pop_ids[npop + rp] = ch;
-                f.pop_start[npop + rp] = nparents + rs;
-                f.pop_tstart[npop + rp] = ntasks + rt;
-                pool.chunk_bucket[ch] = -2;
-            }
-            if (freed) {
-                pool.free_ids[fbase + nfree + rf] = ch;
-                pool.chunk_bucket[ch] = -1;
-            }
-            __syncthreads();   // every read of act[base..] is done before the in-place write
-            if (kept) f.act[keep + rk] = ch;
-            npop += t1;
-            nfree += t2;
-            keep += t3;
-            nparents += t4;
-            ntasks += t5;
-            __syncthreads();
-        }
-        // 3. lexmin leaf across the block
-        if (reason == 3) {
-            s_lex[tid] = my_lex;
-            s_node[tid] = my_node;
-            s_has[tid] = my_has;
-            __syncthreads();
-            for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-                if (tid < o && s_has[tid + o] && (!s_has[tid] || lex_lt(s_lex[tid + o], s_lex[tid]))) {
-                    s_lex[tid] = s_lex[tid + o];
-                    s_node[tid] = s_node[tid + o];
-                    s_has[tid] = 1;
-                }
-                __syncthreads();
-            }
-        }
-        // 4. bucket metadata of popped buckets and, when clearing, of all others
-        int64_t popped_kids = 0;
-        const int32_t top = c->top;
+        // 2. buckets above s* pop (their nodes and children are the round's
+        // parents and tasks); when clearing, every bucket empties
+        int64_t np = 0, pk = 0;
         for (int s = tid; s <= top; s += blockDim.x) {
+            if (s > sstar) {
+                np += (int64_t)f.b_cnt[s];
+                pk += (int64_t)f.b_kids[s];
+            }
             if (s > sstar || clear) {
-                if (s > sstar) popped_kids += f.b_kids[s];
                 f.b_cnt[s] = 0;
                 f.b_kids[s] = 0;
                 f.b_leaf[s] = 0;
-                f.b_tail[s] = -1;
             }
         }
-        int64_t pk;
-        block_excl_scan(popped_kids, &pk, sh);
+        int64_t tnp, tpk;
+        block_excl_scan(np, &tnp, sh);
+        block_excl_scan(pk, &tpk, sh);
         if (tid == 0) {
-            c->n_pop = npop;
-            c->n_parents = nparents;
-            c->n_tasks = ntasks;
-            c->popped_kids = pk;
-            c->n_act = keep;
-            c->size = clear ? 0 : c->size - nparents;
-            c->top = reason == 1 ? sstar : -1;
+            const int64_t size = c->size;
+            if (size > c->peak) c->peak = size;
+            c->sstar = sstar;
+            c->clear = clear ? 1 : 0;
             c->reason = reason;
+            c->n_parents = tnp;
+            c->n_tasks = tpk / 8;
+            c->popped_kids = tpk;
+            c->size = clear ? 0 : size - tnp;
+            c->top = reason == 1 ? sstar : -1;
             c->match_changed = 0;
-            if (reason == 3 && s_has[0]) {
+            const unsigned long long now = gtimer_ns();
+            if (reason == 3) {
                 c->best = sstar;
-                c->match = s_node[0];
                 c->found = 1;
                 c->match_changed = 1;
+                c->lex_t = ~0ull;
+                c->lex_r = ~0u;
+                c->t_match_ns = now;
             }
-            c->done = nparents == 0;
-            // statistics
-            const unsigned long long now = gtimer_ns();
-            if (nparents > 0) {
+            c->done = tnp == 0;
+            if (tnp > 0) {
                 c->st_iters += 1;
-                c->st_parents += nparents;
-                c->st_nodes += pk;
-                c->st_gathers += (pk / 8) * (int64_t)f.K;
+                c->st_parents += tnp;
+                c->st_nodes += tpk;
+                c->st_gathers += (tpk / 8) * (int64_t)f.K;
             }
-            if (c->match_changed) c->t_match_ns = now;
             if (c->done) c->t_end_ns = now;
         }
         __syncthreads();
     }
-}
-
-// push every chunk a search still holds back onto the shared stack
-__global__ void slot_release_kernel(SearchDev* S, int slot, PoolDev pool)
-{
-    SearchDev& f = S[slot];
-    Ctl* c = f.ctl;
-    const int64_t n = c->n_act;
-    __shared__ unsigned long long base;
-    if (threadIdx.x == 0) base = n > 0 ? atomicAdd(pool.free_top, (unsigned long long)n) : 0ull;
+    // the last CTA to finish plans the round
+    __threadfence();
+    if (tid == 0) s_last = atomicAdd(&LS->select_done, 1u) == gridDim.x - 1;
     __syncthreads();
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const int32_t ch = f.act[i];
-        pool.free_ids[base + i] = ch;
-        pool.chunk_bucket[ch] = -1;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        c->n_act = 0;
-        c->size = 0;
-        c->active = 0;
-    }
-}
-
-// the tasks (rotational children, Eq. (13)) of parent p, written at tasks[dst
-// + t] for the t in [t0, t1): parent and rl (task_rows_kernel adds the rows)
-__device__ __forceinline__ void write_tasks(const SearchDev& f, const NodeRec& nd, int64_t p, const int32_t lo[3],
-                                            const int32_t ext[3], int32_t t0, int32_t t1, TaskRec* tasks, int64_t dst)
-{
-    const DevGrid& g = f.grid;
-    const int l = rl_level(nd.rl);
-    const int64_t nb = g.N[l - 1][1], ng = g.N[l - 1][2];
-    int32_t t = 0;
-    for (int32_t ja = 0; ja < ext[0]; ++ja)
-        for (int32_t jb = 0; jb < ext[1]; ++jb)
-            for (int32_t jg = 0; jg < ext[2]; ++jg, ++t) {
-                if (t < t0 || t >= t1) continue;
-                const uint32_t crot = (uint32_t)(((int64_t)(lo[0] + ja) * nb + (lo[1] + jb)) * ng + (lo[2] + jg));
-                TaskRec& r = tasks[dst + t];   // the rows follow (task_rows_kernel)
-                r.parent = (int32_t)p;
-                r.rl = rl_pack(crot, l - 1);
-            }
-}
-
-// popped chunks of every search -> the parent array at the search's offset,
-// each parent's first task (its rotational children are numbered per
-// search in parent order, from toff[search]) and, when the round is scored
-// in one launch (PLAN_OK), the task records themselves.  One CTA of CH
-// threads per popped chunk (one node per thread); the chunks are freed.
-__global__ void __launch_bounds__(CH) gather_kernel(SearchDev* S, PoolDev pool, const int64_t* __restrict__ poff,
-                                                    const int64_t* __restrict__ toff, int nslots,
-                                                    NodeRec* __restrict__ parents, int64_t* __restrict__ pfirst,
-                                                    TaskRec* __restrict__ tasks, const Plan* P)
-{
-    const int status = P->status;
-    if (status != PLAN_OK && status != PLAN_SPLIT) return;
-    __shared__ int64_t sh[32];
-    const int j = threadIdx.x;
-    for (int si = blockIdx.y; si < nslots; si += gridDim.y) {
-        SearchDev& f = S[si];
-        if (!f.ctl->active || f.ctl->err) continue;
-        const int64_t npop = f.ctl->n_pop;
-        for (int64_t i = blockIdx.x; i < npop; i += gridDim.x) {
-            const int32_t ch = f.pop_ids[i];
-            const int64_t start = poff[si] + f.pop_start[i];
-            const int64_t tbase = toff[si] + f.pop_tstart[i];
-            const int32_t fill = pool.chunk_fill[ch];
-            NodeRec nd;
-            int32_t lo[3], ext[3], T = 0;
-            if (j < fill) {
-                nd = pool.nodes[(int64_t)ch * CH + j];
-                T = rot_children(f.grid, rl_level(nd.rl), rl_rot(nd.rl), lo, ext);
-            }
-            int64_t tot;
-            const int64_t first = tbase + block_excl_scan(T, &tot, sh);   // synchronizes: every node is read
-            if (j < fill) {
-                parents[start + j] = nd;
-                pfirst[start + j] = first;
-                if (status == PLAN_OK && T > 0) {
-                    if (first + T <= TASK_CAP) write_tasks(f, nd, start + j, lo, ext, 0, T, tasks, first);
-                    else atomicOr(&f.ctl->err, 4);   // task counts disagree with the nodes: fail the search
-                }
-            }
-            if (j == 0) {
-                if (tot != pool.chunk_tasks[ch]) atomicOr(&f.ctl->err, 4);   // the chunk's task count is stale
-                const unsigned long long pos = atomicAdd(pool.free_top, 1ull);
-                pool.free_ids[pos] = ch;
-                pool.chunk_bucket[ch] = -1;
-            }
-        }
-    }
-}
-
-// the tasks [ga, gb) of one search's round (gathered parents [p0, p1), their
-// first tasks in pfirst) -> tasks[la ..]: a round scored in several launches
-__global__ void expand_kernel(const SearchDev* S, int sid, const NodeRec* __restrict__ parents,
-                              const int64_t* __restrict__ pfirst, int64_t p0, int64_t p1, int64_t ga, int64_t gb,
-                              int64_t la, TaskRec* __restrict__ tasks)
-{
-    const SearchDev& f = S[sid];
-    const DevGrid& g = f.grid;
-    for (int64_t p = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < p1; p += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = pfirst[p];
-        if (b >= gb) continue;
-        const NodeRec nd = parents[p];
-        int32_t lo[3], ext[3];
-        const int32_t T = rot_children(g, rl_level(nd.rl), rl_rot(nd.rl), lo, ext);
-        if (b + T <= ga) continue;
-        const int32_t t0 = (int32_t)(ga > b ? ga - b : 0), t1 = (int32_t)(gb < b + T ? gb - b : T);
-        write_tasks(f, nd, p, lo, ext, t0, t1, tasks, la + b - ga);
-    }
-}
-
-// The plan of the next scoring round, built on the device from every live
-// search's popped parents: per-search parent and task offsets and one task
-// run per search.  It ends the device-driven loop (sets the graph's while
-// condition to 0) when no search popped anything, when the round's tasks do
-// not fit one launch or the run table (the host finishes that round), or after
-// P->max_iters iterations.
-__global__ void __launch_bounds__(1024) plan_kernel(SearchDev* S, int nslots, Plan* P, int64_t* poff, int64_t* toff,
-                                                    unsigned long long* surv_count, cudaGraphConditionalHandle cond)
-{
-    __shared__ int64_t sh[32];
-    const int tid = threadIdx.x;
-    if (tid == 0) *surv_count = 0;
+    if (!s_last) return;
+    __threadfence();
     int64_t cp = 0, ct = 0, cs = 0, cn = 0;
+    int any3 = 0;
     for (int base = 0; base < nslots; base += blockDim.x) {
         const int s = base + tid;
         int64_t np = 0, nt = 0, sl = 0, has = 0;
@@ -560,8 +219,12 @@ __global__ void __launch_bounds__(1024) plan_kernel(SearchDev* S, int nslots, Pl
                 np = c->n_parents;
                 nt = c->n_tasks;
             }
+            // a leaf bucket popped in this round (the search may have finished with it)
+            if (c->active && !c->err && c->match_changed) any3 = 1;
             sl = nt * S[s].nblk;
             has = nt > 0;
+            pcnt[s] = 0;
+            tcnt[s] = 0;
         }
         int64_t tp, tt, ts, tn;
         const int64_t ep = block_excl_scan(np, &tp, sh);
@@ -589,6 +252,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(SearchDev* S, int nslots, Pl
         cs += ts;
         cn += tn;
     }
+    any3 = __syncthreads_or(any3);
     if (tid == 0) {
         P->nseg = (int32_t)(cn < MAXSEG ? cn : MAXSEG);
         P->n_slices = cs;
@@ -600,9 +264,159 @@ __global__ void __launch_bounds__(1024) plan_kernel(SearchDev* S, int nslots, Pl
         else if (cn > MAXSEG || ct > TASK_CAP) st = PLAN_OVERFLOW;
         P->status = st;
         P->iters += 1;
-        if (st != PLAN_OK || P->iters >= P->max_iters) cudaGraphSetConditional(cond, 0);
+        // the nodes the last round appended become current; the other array
+        // receives the kept and the new nodes
+        const int cur = 1 - LS->cur;
+        LS->cur = cur;
+        LS->fn[1 - cur] = 0;
+        LS->lex_pass = any3;
+        LS->select_done = 0;
+        if (use_cond && (st != PLAN_OK || P->iters >= P->max_iters)) cudaGraphSetConditional(cond, 0);
     }
 }
+
+// the tasks (rotational children, Eq. (13)) of parent nd for t in [t0, t1),
+// written at tasks[dst + t]: translation and rl (task_rows_kernel adds the rows)
+__device__ __forceinline__ void write_tasks(const DevGrid& g, const NodeRec& nd, const int32_t lo[3],
+                                            const int32_t ext[3], int32_t t0, int32_t t1, TaskRec* tasks, int64_t dst)
+{
+    const int l = rl_level(nd.rl);
+    const int64_t nb = g.N[l - 1][1], ng = g.N[l - 1][2];
+    int32_t t = 0;
+    for (int32_t ja = 0; ja < ext[0]; ++ja)
+        for (int32_t jb = 0; jb < ext[1]; ++jb)
+            for (int32_t jg = 0; jg < ext[2]; ++jg, ++t) {
+                if (t < t0 || t >= t1) continue;
+                const uint32_t crot = (uint32_t)(((int64_t)(lo[0] + ja) * nb + (lo[1] + jb)) * ng + (lo[2] + jg));
+                TaskRec& r = tasks[dst + t];
+                r.tx = 2 * nd.cx;
+                r.ty = 2 * nd.cy;
+                r.tz = 2 * nd.cz;
+                r.rl = rl_pack(crot, l - 1);
+            }
+}
+
+// The current node array after select: popped nodes become the round's
+// parents (their first task in pfirst) and, when the round scores in one
+// launch, task records; kept nodes move to the other array; cleared nodes,
+// and those of failed or released searches, go.  Leaves of a popped leaf
+// bucket take part in the first lexmin pass (smallest translation key).
+__global__ void __launch_bounds__(256) compact_kernel(SearchDev* S, FrontDev F, LoopState* LS, const Plan* P,
+                                                      NodeRec* __restrict__ parents, int64_t* __restrict__ pfirst,
+                                                      TaskRec* __restrict__ tasks, const int64_t* __restrict__ poff,
+                                                      const int64_t* __restrict__ toff, unsigned long long* pcnt,
+                                                      unsigned long long* tcnt)
+{
+    const int cur = LS->cur, nxt = 1 - cur;
+    // appends past the capacity were not stored (their searches failed): the
+    // count is clamped wherever it is read
+    const int64_t n = min((int64_t)LS->fn[cur], F.cap);
+    const bool emit = P->status == PLAN_OK;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n_round = (n + 31) & ~(int64_t)31;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
+        bool keep = false;
+        uint32_t key = 0;
+        NodeRec nd;
+        nd.cx = nd.cy = nd.cz = 0;
+        nd.rl = 0;
+        if (i < n) {
+            key = F.keys[cur][i];
+            nd = F.nodes[cur][i];
+            const int sid = (int)(key >> 24);
+            const int32_t score = (int32_t)(key & 0xFFFFFFu);
+            SearchDev& f = S[sid];
+            Ctl* c = f.ctl;
+            if (c->active && !c->err) {
+                const int32_t sstar = c->sstar;
+                if (score > sstar) {
+                    const unsigned long long p = atomicAdd(&pcnt[sid], 1ull);
+                    int32_t lo[3], ext[3];
+                    const int l = rl_level(nd.rl);
+                    const int32_t T = rot_children(f.grid, l, rl_rot(nd.rl), lo, ext);
+                    const unsigned long long t0 = T ? atomicAdd(&tcnt[sid], (unsigned long long)T) : 0ull;
+                    if ((int64_t)p < c->n_parents && (int64_t)(t0 + T) <= c->n_tasks) {
+                        const int64_t pi = poff[sid] + (int64_t)p;
+                        parents[pi] = nd;
+                        pfirst[pi] = toff[sid] + (int64_t)t0;
+                        if (emit && T > 0) write_tasks(f.grid, nd, lo, ext, 0, T, tasks, toff[sid] + (int64_t)t0);
+                    } else {
+                        atomicOr(&c->err, 4);   // bucket counts disagree with the nodes: fail the search
+                    }
+                } else {
+                    keep = !c->clear;
+                    if (c->reason == 3 && score == sstar && rl_level(nd.rl) == 0)
+                        atomicMin(&c->lex_t, lex_translation(nd));
+                }
+            }
+        }
+        const uint32_t ball = __ballot_sync(0xffffffffu, keep);
+        if (!ball) continue;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&LS->fn[nxt], (unsigned long long)__popc(ball));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (keep) {
+            const unsigned long long pos = base + __popc(ball & ((1u << lane) - 1u));
+            F.nodes[nxt][pos] = nd;
+            F.keys[nxt][pos] = key;
+        }
+    }
+}
+
+// the tasks [ga, gb) of one search's round (gathered parents [p0, p1), their
+// first tasks in pfirst) -> tasks[la ..]: a round scored in several launches
+__global__ void expand_kernel(const SearchDev* S, int sid, const NodeRec* __restrict__ parents,
+                              const int64_t* __restrict__ pfirst, int64_t p0, int64_t p1, int64_t ga, int64_t gb,
+                              int64_t la, TaskRec* __restrict__ tasks)
+{
+    const DevGrid& g = S[sid].grid;
+    for (int64_t p = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < p1; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = pfirst[p];
+        if (b >= gb) continue;
+        const NodeRec nd = parents[p];
+        int32_t lo[3], ext[3];
+        const int32_t T = rot_children(g, rl_level(nd.rl), rl_rot(nd.rl), lo, ext);
+        if (b + T <= ga) continue;
+        const int32_t t0 = (int32_t)(ga > b ? ga - b : 0), t1 = (int32_t)(gb < b + T ? gb - b : T);
+        write_tasks(g, nd, lo, ext, t0, t1, tasks, la + b - ga);
+    }
+}
+
+// Removing the nodes of one slot (a search stopped early): the incoming array
+// 1 - cur is copied, without them, into array cur, which then becomes the
+// incoming one.  Three launches: reset the target, copy, swap.
+__global__ void purge_reset_kernel(LoopState* LS) { LS->fn[LS->cur] = 0; }
+
+__global__ void purge_kernel(FrontDev F, LoopState* LS, int slot)
+{
+    const int in = 1 - LS->cur, out = LS->cur;
+    const int64_t n = min((int64_t)LS->fn[in], F.cap);   // appends past the capacity were not stored
+    const int lane = threadIdx.x & 31;
+    const int64_t n_round = (n + 31) & ~(int64_t)31;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_round; i += (int64_t)gridDim.x * blockDim.x) {
+        bool keep = false;
+        uint32_t key = 0;
+        NodeRec nd;
+        if (i < n) {
+            key = F.keys[in][i];
+            nd = F.nodes[in][i];
+            keep = (int)(key >> 24) != slot;
+        }
+        const uint32_t ball = __ballot_sync(0xffffffffu, keep);
+        if (!ball) continue;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&LS->fn[out], (unsigned long long)__popc(ball));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (keep) {
+            const unsigned long long pos = base + __popc(ball & ((1u << lane) - 1u));
+            F.nodes[out][pos] = nd;
+            F.keys[out][pos] = key;
+        }
+    }
+}
+
+__global__ void purge_swap_kernel(LoopState* LS) { LS->cur = 1 - LS->cur; }
 
 // ---- host engine ---------------------------------------------------------------
 
@@ -618,9 +432,8 @@ int64_t floor_div2(int64_t x) { return x >= 0 ? x / 2 : -((-x + 1) / 2); }
 }  // namespace
 
 Engine::Engine(cudaStream_t st, int max_slots, int64_t pool_nodes, bool timed)
-    : st_(st), max_slots_(max_slots), timed_(timed)
+    : st_(st), max_slots_(max_slots), timed_(timed), fcap_(pool_nodes)
 {
-    nchunks_ = (pool_nodes + CH - 1) / CH;
     hosts_.resize((size_t)max_slots);
 }
 
@@ -632,9 +445,9 @@ Engine::~Engine()
     for (void* p : fixed_) cudaFreeAsync(p, st_);
     for (cudaEvent_t e : evs_) cudaEventDestroy(e);
     if (h_ctl_) cudaFreeHost(h_ctl_);
-    if (h_poff_) cudaFreeHost(h_poff_);
-    if (h_toff_) cudaFreeHost(h_toff_);
+    if (h_off_) cudaFreeHost(h_off_);
     if (h_misc_) cudaFreeHost(h_misc_);
+    if (h_zero_) cudaFreeHost(h_zero_);
 }
 
 int Engine::init()
@@ -651,48 +464,45 @@ int Engine::init()
         *p = (T)q;
         return BBS_OK;
     };
-    BBS_TRY(get(&pool_.nodes, (size_t)(nchunks_ * CH)));
-    BBS_TRY(get(&pool_.chunk_bucket, (size_t)nchunks_));
-    BBS_TRY(get(&pool_.chunk_fill, (size_t)nchunks_));
-    BBS_TRY(get(&pool_.chunk_tasks, (size_t)nchunks_));
-    BBS_TRY(get(&pool_.free_ids, (size_t)nchunks_));
-    BBS_TRY(get(&pool_.free_top, 1));
-    pool_.nchunks = nchunks_;
+    if (max_slots_ < 1 || max_slots_ > 256) return set_error(BBS_EINVAL, "engine: %d slots (1..256)", max_slots_);
+    for (int b = 0; b < 2; ++b) {
+        BBS_TRY(get(&front_.nodes[b], (size_t)fcap_));
+        BBS_TRY(get(&front_.keys[b], (size_t)fcap_));
+    }
+    front_.cap = fcap_;
+    BBS_TRY(get(&d_ls_, 1));
     BBS_TRY(get(&d_S_, (size_t)max_slots_));
     BBS_TRY(get(&d_ctl_, (size_t)max_slots_));
-    BBS_TRY(get(&parents_, (size_t)(nchunks_ * CH)));
-    BBS_TRY(get(&pfirst_, (size_t)(nchunks_ * CH)));
+    BBS_TRY(get(&parents_, (size_t)fcap_));
+    BBS_TRY(get(&pfirst_, (size_t)fcap_));
     BBS_TRY(get(&tasks_, (size_t)TASK_CAP));
     BBS_TRY(get(&d_poff_, (size_t)max_slots_));
     BBS_TRY(get(&d_toff_, (size_t)max_slots_));
+    BBS_TRY(get(&d_pcnt_, (size_t)max_slots_));
+    BBS_TRY(get(&d_tcnt_, (size_t)max_slots_));
     BBS_TRY(get(&d_plan_, 1));
     BBS_TRY(get(&d_slots_, (size_t)max_slots_));
     BBS_TRY(get(&dense_, (size_t)DENSE_CAP));
-    BBS_TRY(get(&surv_.nodes, (size_t)DENSE_CAP));
-    BBS_TRY(get(&surv_.scores, (size_t)DENSE_CAP));
-    BBS_TRY(get(&surv_.sid, (size_t)DENSE_CAP));
-    BBS_TRY(get(&surv_.ntask, (size_t)DENSE_CAP));
-    BBS_TRY(get(&surv_.count, 1));
-    BBS_TRY(get(&surv_.err, 1));
-    surv_.cap = DENSE_CAP;
     BBS_CUDA_TRY(cudaMemsetAsync(d_ctl_, 0, sizeof(Ctl) * (size_t)max_slots_, st_));
     BBS_CUDA_TRY(cudaMemsetAsync(d_S_, 0, sizeof(SearchDev) * (size_t)max_slots_, st_));
-    BBS_CUDA_TRY(cudaMemsetAsync(surv_.count, 0, sizeof(unsigned long long), st_));
-    BBS_CUDA_TRY(cudaMemsetAsync(surv_.err, 0, sizeof(int), st_));
+    BBS_CUDA_TRY(cudaMemsetAsync(d_ls_, 0, sizeof(LoopState), st_));
+    BBS_CUDA_TRY(cudaMemsetAsync(d_pcnt_, 0, sizeof(unsigned long long) * (size_t)max_slots_, st_));
+    BBS_CUDA_TRY(cudaMemsetAsync(d_tcnt_, 0, sizeof(unsigned long long) * (size_t)max_slots_, st_));
     BBS_CUDA_TRY(cudaMemsetAsync(d_plan_, 0, sizeof(Plan), st_));
     BBS_CUDA_TRY(cudaMemsetAsync(dense_, 0, sizeof(int32_t) * (size_t)DENSE_CAP, st_));
     BBS_CUDA_TRY(cudaMallocHost((void**)&h_ctl_, sizeof(Ctl) * (size_t)max_slots_));
-    BBS_CUDA_TRY(cudaMallocHost((void**)&h_poff_, sizeof(int64_t) * (size_t)max_slots_));
-    BBS_CUDA_TRY(cudaMallocHost((void**)&h_toff_, sizeof(int64_t) * (size_t)max_slots_));
+    BBS_CUDA_TRY(cudaMallocHost((void**)&h_off_, 2 * sizeof(int64_t) * (size_t)max_slots_));
     BBS_CUDA_TRY(cudaMallocHost((void**)&h_misc_, 4 * sizeof(int32_t)));
+    BBS_CUDA_TRY(cudaMallocHost((void**)&h_zero_, sizeof(Ctl)));
+    std::memset(h_ctl_, 0, sizeof(Ctl) * (size_t)max_slots_);
     std::memset(h_misc_, 0, 4 * sizeof(int32_t));
+    std::memset(h_zero_, 0, sizeof(Ctl));
     {
         int dev = 0, nsm = 0;
         BBS_CUDA_TRY(cudaGetDevice(&dev));
         BBS_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         if (nsm > 0) nsm_ = nsm;
     }
-    std::memset(h_ctl_, 0, sizeof(Ctl) * (size_t)max_slots_);
     // every slot's record points at its control block even while unused
     std::vector<SearchDev> blank((size_t)max_slots_);
     for (int i = 0; i < max_slots_; ++i) {
@@ -701,9 +511,6 @@ int Engine::init()
     }
     BBS_CUDA_TRY(cudaMemcpyAsync(d_S_, blank.data(), sizeof(SearchDev) * blank.size(), cudaMemcpyHostToDevice, st_));
     BBS_CUDA_TRY(cudaStreamSynchronize(st_));   // the host copy above must outlive its transfer
-    pool_init_kernel<<<(int)std::min<int64_t>((nchunks_ + 255) / 256, 4096), 256, 0, st_>>>(pool_);
-    launches_ += 1;
-    BBS_CUDA_TRY(cudaGetLastError());
     return BBS_OK;
 }
 
@@ -716,8 +523,9 @@ int Engine::begin_run(cudaStream_t st, bool timed)
     score_launches_ = 0;
     for (cudaEvent_t e : evs_) cudaEventDestroy(e);
     evs_.clear();
-    BBS_CUDA_TRY(cudaMemsetAsync(surv_.err, 0, sizeof(int), st_));
-    BBS_CUDA_TRY(cudaMemsetAsync(surv_.count, 0, sizeof(unsigned long long), st_));
+    // a finished run leaves no nodes; start from empty arrays all the same
+    BBS_CUDA_TRY(cudaMemsetAsync(d_ls_, 0, sizeof(LoopState), st_));
+    h_misc_[2] = 0;
     return BBS_OK;
 }
 
@@ -738,8 +546,7 @@ size_t Engine::estimate_bytes(int64_t k, const HostGrid& g) const
 {
     const size_t K1 = (size_t)k + 1;
     return sizeof(float4) * (size_t)(k > 0 ? k : 1) + sizeof(float4) * 3 * (size_t)g.nrot[g.levels - 1] +
-           sizeof(double2) * (size_t)g.n_cs + 68 * K1 +
-           24 * (size_t)nchunks_ + 1024;
+           sizeof(double2) * (size_t)g.n_cs + 3 * sizeof(unsigned long long) * K1 + 1024;
 }
 
 int Engine::free_slot() const
@@ -791,14 +598,14 @@ int Engine::add(const bbs_maps* m, const float* xyz, int64_t k, int is_device, c
     int rc = BBS_OK;
     if (!(frac > 0.0 && frac <= 1.0)) rc = set_error(BBS_EINVAL, "localize: score_frac %g outside (0, 1]", frac);
     else if (flags & BBS_PRUNE_GE) rc = set_error(BBS_EINVAL, "localize: BBS_PRUNE_GE is not supported");
-    else if (k > (1 << 24)) rc = set_error(BBS_EINVAL, "localize: more than 2^24 scan points");
+    else if (k > (1 << 24) - 1) rc = set_error(BBS_EINVAL, "localize: at least 2^24 scan points");
     if (rc == BBS_OK) rc = scan_prepare(m, xyz, k, is_device, rg, opts, st_, &h.scan);
     if (rc < 0) {
         release(i);
         return rc;
     }
     const HostGrid& g = h.scan.grid;
-    h.bytes += estimate_bytes(k, g) - (68 * ((size_t)k + 1) + 24 * (size_t)nchunks_ + 1024);
+    h.bytes += estimate_bytes(k, g) - (3 * sizeof(unsigned long long) * ((size_t)k + 1) + 1024);
     h.thr = (int32_t)std::ceil(frac * (double)k);
     h.res.phase_ms[0] = now_ms() - h.t0;
     h.res.h2d_bytes += h.scan.h2d;
@@ -828,19 +635,6 @@ int Engine::add(const bbs_maps* m, const float* xyz, int64_t k, int is_device, c
     if (rc == BBS_OK) rc = slot_get(h, &d.b_cnt, K1);
     if (rc == BBS_OK) rc = slot_get(h, &d.b_kids, K1);
     if (rc == BBS_OK) rc = slot_get(h, &d.b_leaf, K1);
-    if (rc == BBS_OK) rc = slot_get(h, &d.b_tail, K1);
-    if (rc == BBS_OK) rc = slot_get(h, &d.h_cnt, K1);
-    if (rc == BBS_OK) rc = slot_get(h, &d.h_kids, K1);
-    if (rc == BBS_OK) rc = slot_get(h, &d.h_leaf, K1);
-    if (rc == BBS_OK) rc = slot_get(h, &d.w_pos, K1);
-    if (rc == BBS_OK) rc = slot_get(h, &d.w_space, K1);
-    if (rc == BBS_OK) rc = slot_get(h, &d.w_choff, K1);
-    if (rc == BBS_OK) rc = slot_get(h, &d.w_tail, K1);
-    if (rc == BBS_OK) rc = slot_get(h, &d.w_fill0, K1);
-    if (rc == BBS_OK) rc = slot_get(h, &d.act, (size_t)nchunks_);
-    if (rc == BBS_OK) rc = slot_get(h, &d.pop_ids, (size_t)nchunks_);
-    if (rc == BBS_OK) rc = slot_get(h, &d.pop_start, (size_t)nchunks_);
-    if (rc == BBS_OK) rc = slot_get(h, &d.pop_tstart, (size_t)nchunks_);
     if (rc < 0) {
         release(i);
         return rc;
@@ -848,6 +642,7 @@ int Engine::add(const bbs_maps* m, const float* xyz, int64_t k, int is_device, c
     h.ctl0 = Ctl();
     h.ctl0.best = h.thr - 1;
     h.ctl0.top = -1;
+    h.ctl0.sstar = -1;
     h.ctl0.active = 1;
     h.live = true;
     h.fresh = true;
@@ -878,7 +673,7 @@ int Engine::start()
     int64_t nsl = 0, ntk = 0;
     auto flush = [&]() -> int {
         if (segs.empty()) return BBS_OK;
-        BBS_TRY(score_launch(MODE_INITIAL, segs, nsl, ntk));
+        BBS_TRY(score_launch(MODE_INITIAL, &segs, nsl, ntk));
         segs.clear();
         nsl = ntk = 0;
         return BBS_OK;
@@ -937,7 +732,6 @@ void Engine::finish_never_live(std::vector<int>* finished)
 int Engine::read_ctl()
 {
     BBS_CUDA_TRY(cudaMemcpyAsync(h_ctl_, d_ctl_, sizeof(Ctl) * (size_t)max_slots_, cudaMemcpyDeviceToHost, st_));
-    BBS_CUDA_TRY(cudaMemcpyAsync(&h_misc_[2], surv_.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
     BBS_CUDA_TRY(cudaStreamSynchronize(st_));
     for (int i = 0; i < max_slots_; ++i)
         if (hosts_[(size_t)i].live) hosts_[(size_t)i].res.d2h_bytes += (int64_t)sizeof(Ctl);
@@ -952,12 +746,10 @@ void Engine::mark_finished(std::vector<int>* finished)
         if (!h.live) continue;
         const Ctl& c = h_ctl_[i];
         if (c.err) {
-            // the shared pool ran out while this search inserted, or its
-            // bookkeeping failed a check: it fails alone
-            if (c.err & 4) h.status = set_error(BBS_ECORRUPT, "localize: frontier task counts are inconsistent");
-            else
-                h.status = set_error(BBS_ENOMEM, "localize: the frontier pool (%lld nodes) is exhausted",
-                                     (long long)(nchunks_ * CH));
+            // the frontier filled while this search inserted, or its counts
+            // failed a check: it fails alone
+            if (c.err & 4) h.status = set_error(BBS_ECORRUPT, "localize: frontier counts are inconsistent");
+            else h.status = set_error(BBS_ENOMEM, "localize: the frontier (%lld nodes) is full", (long long)fcap_);
             h.live = false;
             h.t_end = t;
             finished->push_back(i);
@@ -969,37 +761,54 @@ void Engine::mark_finished(std::vector<int>* finished)
     }
 }
 
-// host-side scoring of the parents the last select popped (h_ctl_ is current):
-// one launch when the round's tasks fit, else launches over task windows
-int Engine::process_popped()
+void Engine::launch_select(cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond)
+{
+    select_kernel<<<max_slots_, 1024, 0, s>>>(d_S_, max_slots_, d_plan_, d_ls_, d_poff_, d_toff_, d_pcnt_, d_tcnt_, cond,
+                                             use_cond);
+}
+
+void Engine::launch_compact(cudaStream_t s)
+{
+    compact_kernel<<<nsm_ * 4, 256, 0, s>>>(d_S_, front_, d_ls_, d_plan_, parents_, pfirst_, tasks_, d_poff_, d_toff_,
+                                           d_pcnt_, d_tcnt_);
+}
+
+// one host-driven iteration: select (+ plan), compaction and rows on the
+// device, then one synchronization; the scoring launch follows the plan
+int Engine::step(std::vector<int>* finished)
+{
+    finish_never_live(finished);
+    if (live_count() == 0) return BBS_OK;
+    h_plan_.iters = 0;
+    h_plan_.max_iters = 1 << 30;
+    BBS_CUDA_TRY(cudaMemcpyAsync(&d_plan_->iters, &h_plan_.iters, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, st_));
+    launch_select(st_, 0, 0);
+    launch_compact(st_);
+    BBS_CUDA_TRY(launch_task_rows(d_plan_, d_S_, tasks_, &front_, d_ls_, nsm_ * 4, st_));
+    launches_ += 3;
+    BBS_CUDA_TRY(cudaGetLastError());
+    BBS_CUDA_TRY(cudaMemcpyAsync(h_misc_, &d_plan_->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
+    BBS_TRY(read_ctl());
+    mark_finished(finished);
+    const int32_t status = h_misc_[0];
+    if (status == PLAN_OK) return score_launch(MODE_SEARCH, nullptr, 0, 0);
+    if (status == PLAN_OVERFLOW) return score_overflow();
+    return BBS_OK;
+}
+
+// a round too large for one launch: its parents were gathered by the
+// compaction; tasks are expanded and scored in windows
+int Engine::score_overflow()
 {
     const int n = max_slots_;
-    int64_t total_parents = 0, total_tasks = 0, maxpop = 1, nsearch = 0;
-    for (int i = 0; i < n; ++i) {
-        h_poff_[i] = total_parents;
-        h_toff_[i] = total_tasks;
-        if (!hosts_[(size_t)i].live) continue;
-        total_parents += h_ctl_[i].n_parents;
-        total_tasks += h_ctl_[i].n_tasks;
-        nsearch += h_ctl_[i].n_tasks > 0 ? 1 : 0;
-        maxpop = std::max<int64_t>(maxpop, h_ctl_[i].n_pop);
-    }
-    if (total_parents == 0) return BBS_OK;
-    const bool one = total_tasks <= TASK_CAP && nsearch <= MAXSEG;
-    BBS_CUDA_TRY(cudaMemcpyAsync(d_poff_, h_poff_, sizeof(int64_t) * (size_t)n, cudaMemcpyHostToDevice, st_));
-    BBS_CUDA_TRY(cudaMemcpyAsync(d_toff_, h_toff_, sizeof(int64_t) * (size_t)n, cudaMemcpyHostToDevice, st_));
-    h_plan_.status = one ? PLAN_OK : PLAN_SPLIT;
-    h_plan_.nseg = 0;
-    BBS_CUDA_TRY(cudaMemcpyAsync(d_plan_, &h_plan_, offsetof(Plan, seg), cudaMemcpyHostToDevice, st_));
-    dim3 gg((unsigned)std::min<int64_t>(maxpop, 4096), (unsigned)std::min(n, 65535));
-    gather_kernel<<<gg, CH, 0, st_>>>(d_S_, pool_, d_poff_, d_toff_, n, parents_, pfirst_, tasks_, d_plan_);
-    launches_ += 1;
-    BBS_CUDA_TRY(cudaGetLastError());
+    BBS_CUDA_TRY(cudaMemcpyAsync(h_off_, d_poff_, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost, st_));
+    BBS_CUDA_TRY(cudaMemcpyAsync(h_off_ + n, d_toff_, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost, st_));
+    BBS_CUDA_TRY(cudaStreamSynchronize(st_));
     std::vector<Seg> segs;
     int64_t nsl = 0, ntk = 0;
     auto flush = [&]() -> int {
         if (segs.empty()) return BBS_OK;
-        BBS_TRY(score_launch(MODE_SEARCH, segs, nsl, ntk));
+        BBS_TRY(score_launch(MODE_SEARCH, &segs, nsl, ntk));
         segs.clear();
         nsl = ntk = 0;
         return BBS_OK;
@@ -1007,25 +816,21 @@ int Engine::process_popped()
     for (int i = 0; i < n; ++i) {
         SearchHost& h = hosts_[(size_t)i];
         if (!h.live) continue;
-        const int64_t nt = h_ctl_[i].n_tasks;
+        const int64_t nt = h_ctl_[i].n_tasks, np = h_ctl_[i].n_parents;
         for (int64_t t0 = 0; t0 < nt;) {
             const int64_t take = std::min<int64_t>(nt - t0, TASK_CAP - ntk);
             if (take <= 0 || (int)segs.size() == MAXSEG) {
                 BBS_TRY(flush());
                 continue;
             }
-            if (!one) {   // the window's task records, from the gathered parents
-                const int64_t np = h_ctl_[i].n_parents;
-                const int blocks = (int)std::min<int64_t>((np + 255) / 256, 4096);
-                expand_kernel<<<blocks, 256, 0, st_>>>(d_S_, i, parents_, pfirst_, h_poff_[i], h_poff_[i] + np,
-                                                       h_toff_[i] + t0, h_toff_[i] + t0 + take, ntk, tasks_);
-                launches_ += 1;
-                BBS_CUDA_TRY(cudaGetLastError());
-            }
+            const int blocks = (int)std::min<int64_t>((np + 255) / 256, 4096);
+            expand_kernel<<<std::max(blocks, 1), 256, 0, st_>>>(d_S_, i, parents_, pfirst_, h_off_[i], h_off_[i] + np,
+                                                                 h_off_[n + i] + t0, h_off_[n + i] + t0 + take, ntk, tasks_);
+            launches_ += 1;
+            BBS_CUDA_TRY(cudaGetLastError());
             Seg sg;
             std::memset(&sg, 0, sizeof(sg));
-            sg.first_parent = h_poff_[i];
-            sg.first_task = one ? h_toff_[i] + t0 : ntk;
+            sg.first_task = ntk;
             sg.n_tasks = take;
             sg.first_slice = nsl;
             sg.sid = i;
@@ -1036,25 +841,11 @@ int Engine::process_popped()
             t0 += take;
         }
     }
-    if (one) ntk = total_tasks;
     return flush();
-}
-
-int Engine::step(std::vector<int>* finished)
-{
-    finish_never_live(finished);
-    if (live_count() == 0) return BBS_OK;
-    select_kernel<<<max_slots_, 1024, 0, st_>>>(d_S_, max_slots_, pool_);
-    launches_ += 1;
-    BBS_CUDA_TRY(cudaGetLastError());
-    BBS_TRY(read_ctl());
-    mark_finished(finished);
-    return process_popped();
 }
 
 int Engine::build_graph()
 {
-    const int n = max_slots_;
     cudaStream_t cs;
     BBS_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
@@ -1073,17 +864,12 @@ int Engine::build_graph()
     cudaGraph_t body = e == cudaSuccess ? np.conditional.phGraph_out[0] : nullptr;
     if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        // one iteration: select, plan, gather, score, survivors, insert
-        select_kernel<<<n, 1024, 0, cs>>>(d_S_, n, pool_);
-        plan_kernel<<<1, 1024, 0, cs>>>(d_S_, n, d_plan_, d_poff_, d_toff_, surv_.count, cond);
-        gather_kernel<<<dim3(256, (unsigned)std::min(n, 65535)), CH, 0, cs>>>(d_S_, pool_, d_poff_, d_toff_, n, parents_,
-                                                                              pfirst_, tasks_, d_plan_);
-        launch_task_rows(d_plan_, d_S_, tasks_, nsm_ * 4, cs);
-        launch_branch(MODE_SEARCH, d_plan_, d_S_, parents_, tasks_, dense_, nsm_ * BRANCH_CTAS_PER_SM, cs);
-        launch_finalize(MODE_SEARCH, d_plan_, d_S_, parents_, tasks_, dense_, surv_, nsm_ * 8, cs);
-        alloc_kernel<<<n, 1024, 0, cs>>>(d_S_, n, pool_, d_plan_);
-        scatter_kernel<<<1024, 256, 0, cs>>>(d_S_, pool_, surv_.nodes, surv_.scores, surv_.sid, surv_.ntask, surv_.count,
-                                             surv_.cap);
+        // one iteration: select (+ plan), compaction, rows, score (+ survivors)
+        launch_select(cs, cond, 1);
+        launch_compact(cs);
+        launch_task_rows(d_plan_, d_S_, tasks_, &front_, d_ls_, nsm_ * 4, cs);
+        launch_branch(MODE_SEARCH, d_plan_, d_S_, tasks_, dense_, nsm_ * BRANCH_CTAS_PER_SM, cs);
+        launch_finalize(MODE_SEARCH, d_plan_, d_S_, tasks_, dense_, front_, d_ls_, nsm_ * 8, cs);
         cudaGraph_t out = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cs, &out);
         e = e2 != cudaSuccess ? e2 : cudaGetLastError();
@@ -1114,18 +900,17 @@ int Engine::iterate(int max_iters, std::vector<int>* finished)
     BBS_CUDA_TRY(cudaMemcpyAsync(h_misc_, &d_plan_->status, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
     BBS_TRY(read_ctl());
     const int32_t status = h_misc_[0];
-    launches_ += 8 * (int64_t)h_misc_[1];   // every iteration of the loop runs the body's 8 kernels
+    launches_ += 5 * (int64_t)h_misc_[1];   // every iteration of the loop runs the body's 5 kernels
     mark_finished(finished);
-    if (status == PLAN_OVERFLOW) return process_popped();   // the selected round did not fit on the device
+    if (status == PLAN_OVERFLOW) return score_overflow();   // the selected round did not fit one launch
     return BBS_OK;
 }
 
 int Engine::finalize(int i, bbs_result* out)
 {
     SearchHost& h = hosts_[(size_t)i];
-    // the control block and the staging error flag as the last read_ctl saw
-    // them: a finished search's block no longer changes
-    const int herr = h_misc_[2];
+    // the control block as the last read_ctl saw it: a finished search's
+    // block no longer changes
     Ctl c;
     std::memset(&c, 0, sizeof(c));
     if (h.scan.k > 0) c = h_ctl_[i];
@@ -1144,9 +929,7 @@ int Engine::finalize(int i, bbs_result* out)
     r->score_launches = score_launches_;
     r->score_ms = score_ms_;
     int status;
-    if (herr) {
-        status = set_error(BBS_ECORRUPT, "localize: survivor staging overflow");
-    } else if (h.status < 0) {
+    if (h.status < 0) {
         status = h.status;
     } else if (h.scan.k == 0) {
         r->best_score = h.thr - 1;
@@ -1168,14 +951,14 @@ int Engine::finalize(int i, bbs_result* out)
         r->phase_ms[3] = dev_match >= 0 ? dev_end - dev_match : 0.0;
         if (r->phase_ms[2] < 0) r->phase_ms[2] = 0;
         r->d2h_bytes += (int64_t)sizeof(Ctl);
-        if (c.found) {
-            const NodeRec& nd = c.match;
-            const uint32_t rot = rl_rot(nd.rl);
+        if (c.found && c.lex_t != ~0ull) {
+            // the lexmin leaf: biased 21-bit translation fields, then the rotation
+            const uint32_t rot = c.lex_r;
             const int64_t ng = g.N[0][2], nb = g.N[0][1];
             r->found = 1;
-            r->node[0] = nd.cx;
-            r->node[1] = nd.cy;
-            r->node[2] = nd.cz;
+            r->node[0] = (int32_t)((c.lex_t >> 42) & 0x1FFFFF) - KEY_LIMIT;
+            r->node[1] = (int32_t)((c.lex_t >> 21) & 0x1FFFFF) - KEY_LIMIT;
+            r->node[2] = (int32_t)(c.lex_t & 0x1FFFFF) - KEY_LIMIT;
             r->node[3] = (int32_t)(rot / (ng * nb));
             r->node[4] = (int32_t)((rot / ng) % nb);
             r->node[5] = (int32_t)(rot % ng);
@@ -1184,6 +967,8 @@ int Engine::finalize(int i, bbs_result* out)
             for (int a = 0; a < 3; ++a) r->pose[3 + a] = grid_angle(g, 0, a, r->node[3 + a]);
             r->ms_to_optimum = r->phase_ms[0] + dev_match;
             status = BBS_OK;
+        } else if (c.found) {
+            status = set_error(BBS_ECORRUPT, "localize: a leaf bucket was popped without a leaf");
         } else {
             r->ms_to_optimum = r->phase_ms[0] + dev_end;
             status = BBS_NOT_FOUND;
@@ -1212,38 +997,46 @@ int Engine::release(int i)
 {
     SearchHost& h = hosts_[(size_t)i];
     if (!h.used) return BBS_OK;
-    // chunks still held (a search stopped early) go back to the pool
-    if (h.dev.K > 0 && d_S_) {
-        slot_release_kernel<<<1, 1024, 0, st_>>>(d_S_, i, pool_);
-        launches_ += 1;
+    // a search stopped before it finished may still have nodes: remove them
+    // before the slot can be reused
+    const bool may_hold = h.dev.K > 0 && h_ctl_[i].active && !h_ctl_[i].done;
+    if (may_hold && d_ls_) {
+        purge_reset_kernel<<<1, 1, 0, st_>>>(d_ls_);
+        purge_kernel<<<nsm_ * 4, 256, 0, st_>>>(front_, d_ls_, i);
+        purge_swap_kernel<<<1, 1, 0, st_>>>(d_ls_);
+        launches_ += 3;
     }
-    Ctl z;
-    std::memset(&z, 0, sizeof(z));
-    h_ctl_[i] = z;
-    if (d_ctl_) cudaMemcpyAsync(d_ctl_ + i, &h_ctl_[i], sizeof(Ctl), cudaMemcpyHostToDevice, st_);
+    // the zeroed control block comes from a pinned block the host never rewrites
+    if (d_ctl_) cudaMemcpyAsync(d_ctl_ + i, h_zero_, sizeof(Ctl), cudaMemcpyHostToDevice, st_);
+    std::memset(&h_ctl_[i], 0, sizeof(Ctl));
     for (void* p : h.bufs) cudaFreeAsync(p, st_);
     scan_release(&h.scan, st_);
-    cudaError_t e = cudaStreamSynchronize(st_);   // the zeroed control block must land before the slot is reused
     h = SearchHost();
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(BBS_ECUDA, "engine: %s", cudaGetErrorString(e));
     return BBS_OK;
 }
 
-int Engine::score_launch(int mode, const std::vector<Seg>& segs, int64_t n_slices, int64_t n_tasks)
+// One scoring launch.  With segs: a host plan (the initial set, or a window of
+// a large round) is uploaded; without: the device plan of the last select.
+int Engine::score_launch(int mode, const std::vector<Seg>* segs, int64_t n_slices, int64_t n_tasks)
 {
-    h_plan_.n_slices = n_slices;
-    h_plan_.n_tasks = n_tasks;
-    h_plan_.next_slice = 0;
-    h_plan_.nseg = (int32_t)segs.size();
-    h_plan_.mode = mode;
-    h_plan_.status = PLAN_OK;
-    for (size_t i = 0; i < segs.size(); ++i) h_plan_.seg[i] = segs[i];
-    // pageable source: staged before cudaMemcpyAsync returns, so h_plan_ may be rewritten
-    BBS_CUDA_TRY(cudaMemcpyAsync(d_plan_, &h_plan_, offsetof(Plan, seg) + sizeof(Seg) * segs.size(),
-                                 cudaMemcpyHostToDevice, st_));
-    if (mode == MODE_SEARCH) {
-        BBS_CUDA_TRY(launch_task_rows(d_plan_, d_S_, tasks_, (int)std::min<int64_t>((n_tasks + 31) / 32, 4 * nsm_), st_));
-        launches_ += 1;
+    if (segs) {
+        h_plan_.n_slices = n_slices;
+        h_plan_.n_tasks = n_tasks;
+        h_plan_.next_slice = 0;
+        h_plan_.nseg = (int32_t)segs->size();
+        h_plan_.mode = mode;
+        h_plan_.status = PLAN_OK;
+        for (size_t i = 0; i < segs->size(); ++i) h_plan_.seg[i] = (*segs)[i];
+        // pageable source: staged before cudaMemcpyAsync returns, so h_plan_ may be rewritten
+        BBS_CUDA_TRY(cudaMemcpyAsync(d_plan_, &h_plan_, offsetof(Plan, seg) + sizeof(Seg) * segs->size(),
+                                     cudaMemcpyHostToDevice, st_));
+        if (mode == MODE_SEARCH) {
+            BBS_CUDA_TRY(launch_task_rows(d_plan_, d_S_, tasks_, nullptr, nullptr,
+                                          (int)std::min<int64_t>((n_tasks + 31) / 32, 4 * nsm_), st_));
+            launches_ += 1;
+        }
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (timed_) {
@@ -1253,19 +1046,11 @@ int Engine::score_launch(int mode, const std::vector<Seg>& segs, int64_t n_slice
         evs_.push_back(e1);
         BBS_CUDA_TRY(cudaEventRecord(e0, st_));
     }
-    const int bb = (int)std::min<int64_t>(n_slices, (int64_t)nsm_ * BRANCH_CTAS_PER_SM);
-    BBS_CUDA_TRY(launch_branch(mode, d_plan_, d_S_, parents_, tasks_, dense_, bb, st_));
+    BBS_CUDA_TRY(launch_branch(mode, d_plan_, d_S_, tasks_, dense_, nsm_ * BRANCH_CTAS_PER_SM, st_));
     if (timed_) BBS_CUDA_TRY(cudaEventRecord(e1, st_));
-    // the device-driven loop leaves its last round's survivor count behind
-    BBS_CUDA_TRY(cudaMemsetAsync(surv_.count, 0, sizeof(unsigned long long), st_));
-    const int fb = (int)std::min<int64_t>((8 * n_tasks + 255) / 256, (int64_t)nsm_ * 32);
-    BBS_CUDA_TRY(launch_finalize(mode, d_plan_, d_S_, parents_, tasks_, dense_, surv_, fb, st_));
-    alloc_kernel<<<max_slots_, 1024, 0, st_>>>(d_S_, max_slots_, pool_, d_plan_);
-    scatter_kernel<<<1024, 256, 0, st_>>>(d_S_, pool_, surv_.nodes, surv_.scores, surv_.sid, surv_.ntask, surv_.count,
-                                          surv_.cap);
-    BBS_CUDA_TRY(cudaMemsetAsync(surv_.count, 0, sizeof(unsigned long long), st_));
+    BBS_CUDA_TRY(launch_finalize(mode, d_plan_, d_S_, tasks_, dense_, front_, d_ls_, nsm_ * 8, st_));
     BBS_CUDA_TRY(cudaGetLastError());
-    launches_ += 4;
+    launches_ += 2;
     score_launches_ += 1;
     return BBS_OK;
 }

@@ -1,6 +1,6 @@
 // engine.cuh -- host side of the batched best-first search engine (engine.cu).
 //
-// An Engine owns one shared chunk pool and up to max_slots search slots.  A
+// An Engine owns the shared frontier arrays and up to max_slots search slots.  A
 // search is added into a free slot (scan uploaded, grid and rotation tables
 // built, frontier arrays allocated), its initial set is scored by start(),
 // and every step() advances every live search by one canonical batch.  A
@@ -57,7 +57,7 @@ class Engine {
     int step(std::vector<int>* finished);
     // advance every live search: by default a captured CUDA graph loops over
     // up to max_iters iterations on the device without the host (a while
-    // node whose condition the planning kernel clears); with BBS_HOST_DRIVEN
+    // node whose condition the planning select clears); with BBS_HOST_DRIVEN
     // one host-driven step.  Results are identical either way.
     int iterate(int max_iters, std::vector<int>* finished);
     void set_host_driven(bool v) { host_driven_ = v; }
@@ -72,18 +72,19 @@ class Engine {
     size_t fixed_bytes() const { return fixed_bytes_; }
     size_t slot_bytes(int slot) const { return hosts_[(size_t)slot].bytes; }
     uint64_t tag(int slot) const { return hosts_[(size_t)slot].tag; }
-    int64_t pool_nodes() const { return nchunks_ * CH; }
+    int64_t pool_nodes() const { return fcap_; }
     // device bytes a search of k points with this grid would hold
     size_t estimate_bytes(int64_t k, const HostGrid& g) const;
 
   private:
     static constexpr int64_t DENSE_CAP = 8 * TASK_CAP;   // child scores per scoring launch
-    // one scoring launch (branch + finalize + alloc + scatter) of the given runs
-    int score_launch(int mode, const std::vector<Seg>& segs, int64_t n_slices, int64_t n_tasks);
+    int score_launch(int mode, const std::vector<Seg>* segs, int64_t n_slices, int64_t n_tasks);
+    int score_overflow();
+    void launch_select(cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond);
+    void launch_compact(cudaStream_t s);
     int read_ctl();
     void finish_never_live(std::vector<int>* finished);
     void mark_finished(std::vector<int>* finished);
-    int process_popped();
     int build_graph();
     int upload_slot(int slot);
     int release(int slot);
@@ -93,26 +94,28 @@ class Engine {
     cudaStream_t st_;
     int max_slots_;
     bool timed_;
-    int64_t nchunks_ = 0;
+    int64_t fcap_;                 // frontier capacity (nodes, all searches)
     size_t fixed_bytes_ = 0;
-    PoolDev pool_{};
+    FrontDev front_{};
+    LoopState* d_ls_ = nullptr;
     SearchDev* d_S_ = nullptr;
     Ctl* d_ctl_ = nullptr;
-    NodeRec* parents_ = nullptr;
-    int64_t* pfirst_ = nullptr;   // first task of each gathered parent
-    TaskRec* tasks_ = nullptr;    // the launch's tasks
+    NodeRec* parents_ = nullptr;   // popped nodes of a round (per search at poff)
+    int64_t* pfirst_ = nullptr;    // first task of each popped node
+    TaskRec* tasks_ = nullptr;     // the launch's tasks
     int64_t* d_poff_ = nullptr;
     int64_t* d_toff_ = nullptr;
+    unsigned long long* d_pcnt_ = nullptr;
+    unsigned long long* d_tcnt_ = nullptr;
     int32_t* d_slots_ = nullptr;
     int32_t* dense_ = nullptr;
-    SurvOut surv_{};
-    Ctl* h_ctl_ = nullptr;
-    int64_t* h_poff_ = nullptr;
-    int64_t* h_toff_ = nullptr;
-    int32_t* h_misc_ = nullptr;   // pinned: plan status, loop iterations, staging error
-    int nsm_ = 152;
+    Ctl* h_ctl_ = nullptr;         // pinned
+    int64_t* h_off_ = nullptr;     // pinned: parent and task offsets of an overflowing round
+    int32_t* h_misc_ = nullptr;    // pinned: plan status, loop iterations
+    Ctl* h_zero_ = nullptr;        // pinned, all zero
     Plan* d_plan_ = nullptr;
     Plan h_plan_{};
+    int nsm_ = 152;
     cudaGraphExec_t exec_ = nullptr;
     bool host_driven_ = false;
     std::vector<void*> fixed_;

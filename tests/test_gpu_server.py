@@ -79,14 +79,14 @@ def test_budget_admission_and_rejection(nv, two_maps):
     w, dm = two_maps["indoor"]
     rg, op = _args(nv, w)
     s0, _ = synth.make_scan(2, 3)
-    # a search holds about 84 bytes per scan point (the scan and K + 1 score
-    # buckets); 64 copies of the scan (~0.5 M points, ~43 MB) against room for
-    # 64 MB beyond the pool admit one search at a time
+    # a search holds about 40 bytes per scan point (the scan and K + 1 score
+    # buckets of three counts); 64 copies of the scan (~0.5 M points, ~21 MB)
+    # against room for 32 MB beyond the engine admit one search at a time
     s = np.tile(s0, (64, 1))
     probe = nv.bbs_server_create(mem_budget=1 << 40, max_active=4, max_frontier=1 << 20)
     fixed = nv.bbs_server_stats(probe)["mem_in_use"]
     probe.close()
-    srv = nv.bbs_server_create(mem_budget=fixed + (64 << 20), max_active=4, max_frontier=1 << 20)
+    srv = nv.bbs_server_create(mem_budget=fixed + (32 << 20), max_active=4, max_frontier=1 << 20)
     tickets = [nv.bbs_server_submit(srv, dm, s, rg, op) for _ in range(3)]
     saw_queue = nv.bbs_server_stats(srv)["queued"] > 0
     res = [nv.bbs_server_poll(srv, t, -1) for t in tickets]
