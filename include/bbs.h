@@ -242,6 +242,7 @@ int  bbs_score_batch_noalloc(const bbs_maps* maps, const float* scan_xyz, int64_
  * leaf of that bucket) and clears F; the popped parents are branched
  * (Eq. (13)) and children scoring above best join F.  ranges NULL: map
  * bounding box, roll/pitch (-0.02, 0.02), yaw (0, 2 pi).  opts may be NULL.
+ * K is at most 2^24 - 2 (BBS_EINVAL beyond).
  * Returns BBS_OK, BBS_NOT_FOUND, or an error (also in out->status). */
 int  bbs_localize(const bbs_maps* maps, const float* scan_xyz, int64_t k, int is_device,
                   const bbs_ranges* ranges, const bbs_opts* opts, bbs_result* out);

@@ -453,20 +453,23 @@ __global__ void __launch_bounds__(256) finalize_kernel(const Plan* __restrict__ 
         if (surv) {
             SearchDev& s = S[sid];
             const unsigned long long pos = base + __popc(ball & ((1u << lane) - 1u));
+            // bucket counts, one atomic per (search, score) group of the warp
+            const uint32_t kids = (uint32_t)node_children(s.grid, m, crot);
+            const uint32_t gk = __reduce_add_sync(peers, kids);
+            const uint32_t gl = __reduce_add_sync(peers, m == 0 ? 1u : 0u);
             if (pos < (unsigned long long)F.cap) {
                 F.nodes[nxt][pos] = nd;
                 F.keys[nxt][pos] = key;
-                const int64_t kids = node_children(s.grid, m, crot);
-                if ((__ffs(peers) - 1) == lane) {
-                    atomicAdd(&s.b_cnt[score], (unsigned long long)__popc(peers));
-                    atomicMax(&s.ctl->top, score);
-                }
-                atomicAdd(&s.b_kids[score], (unsigned long long)kids);
-                if (m == 0) atomicAdd(&s.b_leaf[score], 1ull);
-                if ((__ffs(same) - 1) == lane) atomicAdd((unsigned long long*)&s.ctl->size, (unsigned long long)__popc(same));
             } else {
                 atomicOr(&s.ctl->err, 1);   // the frontier is full: the search fails
             }
+            if ((__ffs(peers) - 1) == lane) {
+                atomicAdd(&s.b_cnt[score], (unsigned long long)__popc(peers));
+                atomicAdd(&s.b_kids[score], (unsigned long long)gk);
+                if (gl) atomicAdd(&s.b_leaf[score], (unsigned long long)gl);
+                atomicMax(&s.ctl->top, score);
+            }
+            if ((__ffs(same) - 1) == lane) atomicAdd((unsigned long long*)&s.ctl->size, (unsigned long long)__popc(same));
         }
     }
 }

@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
     __shared__ int64_t sh[32];
     __shared__ int s_min[33];
     __shared__ int32_t s_star, s_reason;
+    __shared__ int64_t s_cnt, s_kids;
     __shared__ int s_last;
     const int tid = threadIdx.x;
     for (int si = blockIdx.x; si < nslots; si += gridDim.x) {
@@ -129,47 +130,64 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
             s_reason = c->size > 0 ? 4 : 0;
         }
         __syncthreads();
-        // 1. the bucket where popping stops
-        int64_t carry = 0;
+        // 1. the bucket where popping stops, walking down from the top: the
+        // buckets passed are the popped ones, emptied on the way
+        int64_t carry = 0, ncarry = 0;
         const int32_t top = c->top;
         for (int base = top; base >= 0; base -= blockDim.x) {
             const int s = base - tid;
-            const bool have = s >= 0 && f.b_cnt[s] > 0;
+            const int64_t cnt = s >= 0 ? (int64_t)f.b_cnt[s] : 0;
+            const bool have = cnt > 0;
             const int64_t kids = have ? (int64_t)f.b_kids[s] : 0;
-            int64_t tot;
+            int64_t tot, ntot;
             const int64_t cum = carry + block_excl_scan(kids, &tot, sh);
+            block_excl_scan(cnt, &ntot, sh);
             const bool stop = have && (cum >= f.batch || s <= best || f.b_leaf[s] > 0);
             const int first = block_min_int(stop ? tid : (int)blockDim.x, s_min);
             if (first < (int)blockDim.x) {
                 if (tid == first) {
                     s_star = s;
                     s_reason = cum >= f.batch ? 1 : (s <= best ? 2 : 3);
+                    s_kids = cum;   // children of the buckets above s*
+                }
+                // parents above s*: this pass's buckets before `first`, and the earlier passes
+                const int64_t cnt_above = tid < first ? cnt : 0;
+                int64_t ca;
+                block_excl_scan(cnt_above, &ca, sh);
+                if (tid == 0) s_cnt = ncarry + ca;
+                if (have && tid < first) {
+                    f.b_cnt[s] = 0;
+                    f.b_kids[s] = 0;
+                    f.b_leaf[s] = 0;
                 }
                 __syncthreads();
                 break;
             }
-            carry += tot;
-        }
-        const int32_t sstar = s_star;
-        const int reason = s_reason;
-        const bool clear = reason == 2 || reason == 3;
-        // 2. buckets above s* pop (their nodes and children are the round's
-        // parents and tasks); when clearing, every bucket empties
-        int64_t np = 0, pk = 0;
-        for (int s = tid; s <= top; s += blockDim.x) {
-            if (s > sstar) {
-                np += (int64_t)f.b_cnt[s];
-                pk += (int64_t)f.b_kids[s];
-            }
-            if (s > sstar || clear) {
+            if (have) {   // the whole pass is above the stop bucket: popped
                 f.b_cnt[s] = 0;
                 f.b_kids[s] = 0;
                 f.b_leaf[s] = 0;
             }
+            carry += tot;
+            ncarry += ntot;
         }
-        int64_t tnp, tpk;
-        block_excl_scan(np, &tnp, sh);
-        block_excl_scan(pk, &tpk, sh);
+        if (tid == 0 && s_star < 0) {   // no stop: every bucket popped
+            s_kids = carry;
+            s_cnt = ncarry;
+        }
+        __syncthreads();
+        const int32_t sstar = s_star;
+        const int reason = s_reason;
+        const bool clear = reason == 2 || reason == 3;
+        // 2. when clearing, every bucket at or below s* empties as well
+        if (clear)
+            for (int s = tid; s <= sstar; s += blockDim.x) {
+                f.b_cnt[s] = 0;
+                f.b_kids[s] = 0;
+                f.b_leaf[s] = 0;
+            }
+        const int64_t tnp = s_cnt, tpk = s_kids;
+
         if (tid == 0) {
             const int64_t size = c->size;
             if (size > c->peak) c->peak = size;
@@ -316,38 +334,69 @@ __global__ void __launch_bounds__(256) compact_kernel(SearchDev* S, FrontDev F, 
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t n_round = (n + 31) & ~(int64_t)31;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
-        bool keep = false;
+        bool keep = false, popped = false;
         uint32_t key = 0;
+        int sid = 0;
+        int32_t T = 0, lo[3], ext[3];
         NodeRec nd;
         nd.cx = nd.cy = nd.cz = 0;
         nd.rl = 0;
+        Ctl* c = nullptr;
         if (i < n) {
             key = F.keys[cur][i];
             nd = F.nodes[cur][i];
-            const int sid = (int)(key >> 24);
+            sid = (int)(key >> 24);
             const int32_t score = (int32_t)(key & 0xFFFFFFu);
             SearchDev& f = S[sid];
-            Ctl* c = f.ctl;
+            c = f.ctl;
             if (c->active && !c->err) {
                 const int32_t sstar = c->sstar;
                 if (score > sstar) {
-                    const unsigned long long p = atomicAdd(&pcnt[sid], 1ull);
-                    int32_t lo[3], ext[3];
-                    const int l = rl_level(nd.rl);
-                    const int32_t T = rot_children(f.grid, l, rl_rot(nd.rl), lo, ext);
-                    const unsigned long long t0 = T ? atomicAdd(&tcnt[sid], (unsigned long long)T) : 0ull;
-                    if ((int64_t)p < c->n_parents && (int64_t)(t0 + T) <= c->n_tasks) {
-                        const int64_t pi = poff[sid] + (int64_t)p;
-                        parents[pi] = nd;
-                        pfirst[pi] = toff[sid] + (int64_t)t0;
-                        if (emit && T > 0) write_tasks(f.grid, nd, lo, ext, 0, T, tasks, toff[sid] + (int64_t)t0);
-                    } else {
-                        atomicOr(&c->err, 4);   // bucket counts disagree with the nodes: fail the search
-                    }
+                    popped = true;
+                    T = rot_children(f.grid, rl_level(nd.rl), rl_rot(nd.rl), lo, ext);
                 } else {
                     keep = !c->clear;
                     if (c->reason == 3 && score == sstar && rl_level(nd.rl) == 0)
                         atomicMin(&c->lex_t, lex_translation(nd));
+                }
+            }
+        }
+        // popped nodes: a parent index and a task range each, from the search's
+        // counters; one atomic per warp when the warp's popped nodes share a search
+        const uint32_t pball = __ballot_sync(0xffffffffu, popped);
+        if (pball) {
+            int32_t incl = popped ? T : 0;   // inclusive warp scan of the task counts
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int lead = __ffs(pball) - 1;
+            const int lead_sid = __shfl_sync(0xffffffffu, sid, lead);
+            const bool one = __all_sync(0xffffffffu, !popped || sid == lead_sid);
+            unsigned long long p = 0, t0 = 0;
+            if (one) {   // warp-uniform
+                const int32_t tsum = __shfl_sync(0xffffffffu, incl, 31);
+                unsigned long long pb = 0, tb = 0;
+                if (lane == lead) {
+                    pb = atomicAdd(&pcnt[sid], (unsigned long long)__popc(pball));
+                    tb = atomicAdd(&tcnt[sid], (unsigned long long)tsum);
+                }
+                pb = __shfl_sync(0xffffffffu, pb, lead);
+                tb = __shfl_sync(0xffffffffu, tb, lead);
+                p = pb + __popc(pball & ((1u << lane) - 1u));
+                t0 = tb + (unsigned long long)(incl - (popped ? T : 0));
+            } else if (popped) {
+                p = atomicAdd(&pcnt[sid], 1ull);
+                t0 = T ? atomicAdd(&tcnt[sid], (unsigned long long)T) : 0ull;
+            }
+            if (popped) {
+                if ((int64_t)p < c->n_parents && (int64_t)(t0 + T) <= c->n_tasks) {
+                    const int64_t pi = poff[sid] + (int64_t)p;
+                    parents[pi] = nd;
+                    pfirst[pi] = toff[sid] + (int64_t)t0;
+                    if (emit && T > 0) write_tasks(S[sid].grid, nd, lo, ext, 0, T, tasks, toff[sid] + (int64_t)t0);
+                } else {
+                    atomicOr(&c->err, 4);   // bucket counts disagree with the nodes: fail the search
                 }
             }
         }
@@ -598,7 +647,7 @@ int Engine::add(const bbs_maps* m, const float* xyz, int64_t k, int is_device, c
     int rc = BBS_OK;
     if (!(frac > 0.0 && frac <= 1.0)) rc = set_error(BBS_EINVAL, "localize: score_frac %g outside (0, 1]", frac);
     else if (flags & BBS_PRUNE_GE) rc = set_error(BBS_EINVAL, "localize: BBS_PRUNE_GE is not supported");
-    else if (k > (1 << 24) - 1) rc = set_error(BBS_EINVAL, "localize: at least 2^24 scan points");
+    else if (k > (1 << 24) - 2) rc = set_error(BBS_EINVAL, "localize: more than 2^24 - 2 scan points");
     if (rc == BBS_OK) rc = scan_prepare(m, xyz, k, is_device, rg, opts, st_, &h.scan);
     if (rc < 0) {
         release(i);
