@@ -292,9 +292,9 @@ def _kernel_hash():
 
 def _traffic_from_profile():
     """DRAM bytes per launch of the scoring kernel from the committed ncu
-    summary (profiles/branch_kernel_indoor.md, 'key: value' lines), if it was
+    summary (profiles/branch3_kernel_indoor.md, "key: value" lines), if it was
     taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "branch_kernel_indoor.md")
+    p = os.path.join(ROOT, "profiles", "branch3_kernel_indoor.md")
     if not os.path.exists(p):
         return None
     kv = {}
