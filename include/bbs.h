@@ -167,6 +167,28 @@ int  bbs_set_load_factor(double load);
  * otherwise; 1 always uses the wide layout.  Scores do not depend on it. */
 int  bbs_set_probe_layout(int layout);
 
+/* Launch shape of the search, for every engine and launch made after the
+ * call (results never depend on it).  Zero fields take the defaults:
+ *   launch_tasks  most rotational-child tasks per scoring launch, 1..2^19
+ *                 (default 2^19); a round with more is scored in several
+ *                 launches planned on the host;
+ *   static_pm     per-mille of a launch's (task, 512-point block) slices split
+ *                 evenly over the scoring CTAs before the rest is handed out
+ *                 in shrinking grabs, 1..1000 (default 750);
+ *   grab_min      smallest grab in slices, 1..2^20 (default 16);
+ *   ctas_per_sm   scoring CTAs per SM, 1..4 (default 4).
+ * NULL restores every default.  BBS_EINVAL for a field out of range. */
+typedef struct {
+    int64_t launch_tasks;
+    int32_t static_pm;
+    int32_t grab_min;
+    int32_t ctas_per_sm;
+    int32_t reserved;
+} bbs_tuning;
+int  bbs_set_tuning(const bbs_tuning* t);
+/* The tuning in effect (defaults filled in). */
+int  bbs_get_tuning(bbs_tuning* t);
+
 /* All voxel keys of level `level` (n_voxels x 3 int32) into the host buffer
  * out (capacity cap keys); *n receives the count.  BBS_EINVAL if cap is short. */
 int  bbs_maps_keys(const bbs_maps* maps, int level, int32_t* out, int64_t cap, int64_t* n);

@@ -1,0 +1,154 @@
+"""Launch-shape autotuner for the batched search (the tile / layout choices
+of the scoring path), with a JSON cache keyed by GPU and workload shape.
+
+What is tuned never changes a result: the table load factor of the level
+maps (probe length vs footprint), the share of a scoring launch split
+statically over the CTAs, the smallest dynamic grab, and the scoring CTAs per
+SM.  The batch size b is part of the search's definition (it changes the
+trajectory, Algorithm 2) and is not tuned.  Every candidate's results are
+compared with the first candidate's; a candidate that differs is an error.
+
+Coordinate descent: each knob in turn, the others held at their best so far;
+the time of a candidate is the median over `reps` passes of bbs_localize on
+the given device-resident scans.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import statistics
+import time
+
+from . import native as nv
+
+DEFAULT = {"load_factor": 0.25, "static_pm": 750, "grab_min": 16, "ctas_per_sm": 4}
+SPACE = {
+    "load_factor": [0.5, 0.35, 0.25, 0.15],
+    "static_pm": [500, 750, 875],
+    "grab_min": [8, 16, 32],
+    "ctas_per_sm": [3, 4],
+}
+
+
+def cache_path() -> str:
+    p = os.environ.get("BBS_TUNING_CACHE")
+    if p:
+        return p
+    return os.path.join(os.path.expanduser("~"), ".cache", "paper_2310_10023_gb300", "tuning.json")
+
+
+def workload_key(gpu: str, sms: int, r: float, levels: int, batch: int, ks) -> str:
+    """GPU name and SM count, voxel size, levels, batch and the scan-size
+    range (log2 buckets): tunings transfer between workloads of one shape."""
+    kmin, kmax = min(ks), max(ks)
+    shape = f"r={r:.6g};L={levels};b={batch};k={kmin.bit_length()}-{kmax.bit_length()}"
+    return f"{gpu}|{sms}|{hashlib.sha1(shape.encode()).hexdigest()[:12]}|{shape}"
+
+
+def load_cache(path: str | None = None) -> dict:
+    path = path or cache_path()
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def store(key: str, entry: dict, path: str | None = None) -> None:
+    path = path or cache_path()
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    data = load_cache(path)
+    data[key] = entry
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def apply(cfg: dict) -> None:
+    """Make cfg the library's launch shape and map load factor (maps built
+    after this call use the load factor)."""
+    nv.bbs_set_load_factor(float(cfg.get("load_factor", DEFAULT["load_factor"])))
+    nv.bbs_set_tuning(static_pm=int(cfg.get("static_pm", DEFAULT["static_pm"])),
+                      grab_min=int(cfg.get("grab_min", DEFAULT["grab_min"])),
+                      ctas_per_sm=int(cfg.get("ctas_per_sm", DEFAULT["ctas_per_sm"])))
+
+
+def _result_key(r) -> tuple:
+    return (r.status, r.best_score, tuple(r.node), r.iterations, r.nodes_scored)
+
+
+def search(build_maps, scans, ranges, opts, reps: int = 3, space: dict | None = None, timer=None,
+           sync=None) -> dict:
+    """Coordinate descent over `space` (default SPACE).
+
+    build_maps() -> maps handle (called again whenever the load factor
+    changes); scans: device-resident point arrays; timer/sync: clock and
+    device synchronization (defaults: time.perf_counter and
+    torch.cuda.synchronize).  Returns {"best": cfg, "ms": per-pass ms,
+    "trials": [...]}.
+    """
+    space = space or SPACE
+    if sync is None:
+        import torch
+        sync = torch.cuda.synchronize
+    timer = timer or time.perf_counter
+    best = dict(DEFAULT)
+    ref = None
+    trials = []
+    maps_cache = {}
+
+    def maps_for(lf):
+        if lf not in maps_cache:
+            nv.bbs_set_load_factor(lf)
+            maps_cache[lf] = build_maps()
+        return maps_cache[lf]
+
+    def run(cfg):
+        nonlocal ref
+        apply(cfg)
+        m = maps_for(cfg["load_factor"])
+        keys = [_result_key(nv.bbs_localize(m, s, ranges, opts)) for s in scans]   # warm-up + check
+        if ref is None:
+            ref = keys
+        elif keys != ref:
+            raise RuntimeError(f"autotune: launch shape {cfg} changed a result")
+        times = []
+        for _ in range(reps):
+            sync()
+            t = timer()
+            for s in scans:
+                nv.bbs_localize(m, s, ranges, opts)
+            sync()
+            times.append((timer() - t) * 1e3)
+        ms = statistics.median(times)
+        trials.append({"cfg": dict(cfg), "ms": ms})
+        return ms
+
+    best_ms = run(best)
+    for knob, values in space.items():
+        for v in values:
+            if v == best[knob]:
+                continue
+            cand = dict(best, **{knob: v})
+            ms = run(cand)
+            if ms < best_ms:
+                best, best_ms = cand, ms
+    apply(best)
+    return {"best": best, "ms": best_ms, "trials": trials}
+
+
+def tuned(gpu: str, sms: int, build_maps, scans, ranges, opts, r: float, levels: int, ks, path: str | None = None,
+          **kw) -> dict:
+    """The cached launch shape for this GPU and workload shape, searched and
+    stored on a miss; applied before returning."""
+    key = workload_key(gpu, sms, r, levels, int(opts.batch), ks)
+    hit = load_cache(path).get(key)
+    if hit is not None:
+        apply(hit["best"])
+        return dict(hit, cached=True)
+    out = search(build_maps, scans, ranges, opts, **kw)
+    entry = {"best": out["best"], "ms": out["ms"], "trials": out["trials"]}
+    store(key, entry, path)
+    return dict(entry, cached=False)

@@ -183,8 +183,6 @@ struct __align__(16) RunDesc {
 };
 
 constexpr int NRUN = 32;   // runs described per round of a CTA
-constexpr int STATIC_NUM = 3, STATIC_DEN = 4;   // share of a launch's slices split statically
-constexpr int64_t GRAB_MIN = 16;                // smallest dynamic grab (slices)
 
 }  // namespace
 
@@ -209,9 +207,10 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
     __shared__ int32_t s_gi, s_nrun, s_staged_sid, s_staged_c;
     const int tid = threadIdx.x, lane = tid & 31;
     const int64_t n_slices = P->n_slices;
-    // the first STATIC_NUM / STATIC_DEN of the slices in equal static shares;
-    // the rest handed out in shrinking grabs as CTAs finish
-    const int64_t n_static = n_slices * STATIC_NUM / STATIC_DEN;
+    // the first static_pm / 1000 of the slices in equal static shares; the
+    // rest handed out in shrinking grabs (at least grab_min) as CTAs finish
+    const int64_t n_static = n_slices * P->static_pm / 1000;
+    const int64_t grab_min = P->grab_min > 0 ? P->grab_min : 1;
     if (tid == 0) {
         s_cur = n_static * blockIdx.x / gridDim.x;
         s_end = n_static * (blockIdx.x + 1) / gridDim.x;
@@ -229,7 +228,7 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
                 const unsigned long long seen = *(volatile unsigned long long*)&P->next_slice;
                 const int64_t left = n_slices - n_static - (int64_t)seen;
                 int64_t want = left / (2 * (int64_t)gridDim.x);
-                if (want < GRAB_MIN) want = GRAB_MIN;
+                if (want < grab_min) want = grab_min;
                 const int64_t got = n_static + (int64_t)atomicAdd(&P->next_slice, (unsigned long long)want);
                 s_cur = got;
                 s_end = min(got + want, n_slices);

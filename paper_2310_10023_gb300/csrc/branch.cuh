@@ -126,6 +126,8 @@ struct Plan {
     int64_t n_slices;
     int64_t n_tasks;         // dense child scores: 8 per task, at most 8 * TASK_CAP
     unsigned long long next_slice;   // dynamic share: the next slice not yet handed out (0 at launch)
+    int32_t static_pm;       // per-mille of the slices split statically over the CTAs
+    int32_t grab_min;        // smallest dynamic grab (slices)
     int32_t nseg;
     int32_t mode;
     int32_t status;          // PLAN_*: the scoring kernels of a round run only when PLAN_OK
@@ -162,6 +164,21 @@ __host__ __device__ __forceinline__ int32_t rot_children(const DevGrid& g, int l
 // the current frontier
 cudaError_t launch_task_rows(const Plan* P, const SearchDev* S, TaskRec* tasks, const FrontDev* F, const LoopState* LS,
                              int blocks, cudaStream_t st);
+
+// launch shape (bbs_tuning), resolved: every field in range
+struct Tuning {
+    int64_t launch_tasks = TASK_CAP;
+    int32_t static_pm = 750;
+    int32_t grab_min = 16;
+    int32_t ctas_per_sm = 4;
+    bool operator==(const Tuning& o) const
+    {
+        return launch_tasks == o.launch_tasks && static_pm == o.static_pm && grab_min == o.grab_min &&
+               ctas_per_sm == o.ctas_per_sm;
+    }
+};
+Tuning current_tuning();
+int set_tuning(const bbs_tuning* t);   // validates; NULL restores the defaults
 
 // CTAs of a scoring launch: one resident wave (4 CTAs of 256 threads per SM, 64 registers a thread)
 constexpr int BRANCH_CTAS_PER_SM = 4;

@@ -332,6 +332,11 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
     P.nseg = 1;
     P.n_tasks = ntask;
     P.n_slices = ntask * sd.nblk;
+    {
+        const Tuning tn = current_tuning();
+        P.static_pm = tn.static_pm;
+        P.grab_min = tn.grab_min;
+    }
     P.seg[0].first_task = 0;
     P.seg[0].n_tasks = ntask;
     P.seg[0].first_slice = 0;
@@ -434,6 +439,25 @@ int bbs_set_probe_layout(int layout)
 {
     clear_error();
     return maps_set_layout(layout);
+}
+
+int bbs_set_tuning(const bbs_tuning* t)
+{
+    clear_error();
+    return set_tuning(t);
+}
+
+int bbs_get_tuning(bbs_tuning* t)
+{
+    clear_error();
+    if (!t) return set_error(BBS_EINVAL, "get_tuning: NULL");
+    const Tuning v = current_tuning();
+    std::memset(t, 0, sizeof(*t));
+    t->launch_tasks = v.launch_tasks;
+    t->static_pm = v.static_pm;
+    t->grab_min = v.grab_min;
+    t->ctas_per_sm = v.ctas_per_sm;
+    return BBS_OK;
 }
 
 }  // extern "C"

@@ -82,6 +82,40 @@ __device__ __forceinline__ int block_min_int(int v, int* sh)
 }
 
 
+// ---- launch shape ---------------------------------------------------------------
+
+namespace {
+std::mutex g_tuning_mu;
+Tuning g_tuning;
+}  // namespace
+
+Tuning current_tuning()
+{
+    std::lock_guard<std::mutex> lock(g_tuning_mu);
+    return g_tuning;
+}
+
+int set_tuning(const bbs_tuning* t)
+{
+    Tuning v;
+    if (t) {
+        if (t->launch_tasks) v.launch_tasks = t->launch_tasks;
+        if (t->static_pm) v.static_pm = t->static_pm;
+        if (t->grab_min) v.grab_min = t->grab_min;
+        if (t->ctas_per_sm) v.ctas_per_sm = t->ctas_per_sm;
+        if (v.launch_tasks < 1 || v.launch_tasks > TASK_CAP)
+            return set_error(BBS_EINVAL, "tuning: launch_tasks %lld outside 1..%lld", (long long)v.launch_tasks,
+                             (long long)TASK_CAP);
+        if (v.static_pm < 1 || v.static_pm > 1000) return set_error(BBS_EINVAL, "tuning: static_pm %d outside 1..1000", v.static_pm);
+        if (v.grab_min < 1 || v.grab_min > (1 << 20)) return set_error(BBS_EINVAL, "tuning: grab_min %d outside 1..2^20", v.grab_min);
+        if (v.ctas_per_sm < 1 || v.ctas_per_sm > BRANCH_CTAS_PER_SM)
+            return set_error(BBS_EINVAL, "tuning: ctas_per_sm %d outside 1..%d", v.ctas_per_sm, BRANCH_CTAS_PER_SM);
+    }
+    std::lock_guard<std::mutex> lock(g_tuning_mu);
+    g_tuning = v;
+    return BBS_OK;
+}
+
 // ---- kernels -----------------------------------------------------------------
 
 __device__ __forceinline__ unsigned long long gtimer_ns()
@@ -108,7 +142,7 @@ __global__ void slot_init_kernel(SearchDev* S, const int32_t* slots)
 __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, Plan* P, LoopState* LS,
                                                       int64_t* poff, int64_t* toff, unsigned long long* pcnt,
                                                       unsigned long long* tcnt, cudaGraphConditionalHandle cond,
-                                                      int use_cond)
+                                                      int use_cond, Tuning tune)
 {
     __shared__ int64_t sh[32];
     __shared__ int s_min[33];
@@ -276,10 +310,12 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
         P->n_slices = cs;
         P->n_tasks = ct;
         P->next_slice = 0;
+        P->static_pm = tune.static_pm;
+        P->grab_min = tune.grab_min;
         P->mode = MODE_SEARCH;
         int st = PLAN_OK;
         if (cp == 0) st = PLAN_EMPTY;
-        else if (cn > MAXSEG || ct > TASK_CAP) st = PLAN_OVERFLOW;
+        else if (cn > MAXSEG || ct > tune.launch_tasks) st = PLAN_OVERFLOW;
         P->status = st;
         P->iters += 1;
         // the nodes the last round appended become current; the other array
@@ -481,7 +517,7 @@ int64_t floor_div2(int64_t x) { return x >= 0 ? x / 2 : -((-x + 1) / 2); }
 }  // namespace
 
 Engine::Engine(cudaStream_t st, int max_slots, int64_t pool_nodes, bool timed)
-    : st_(st), max_slots_(max_slots), timed_(timed), fcap_(pool_nodes)
+    : st_(st), max_slots_(max_slots), timed_(timed), fcap_(pool_nodes), tune_(current_tuning())
 {
     hosts_.resize((size_t)max_slots);
 }
@@ -567,6 +603,12 @@ int Engine::begin_run(cudaStream_t st, bool timed)
 {
     st_ = st;
     timed_ = timed;
+    const Tuning t = current_tuning();
+    if (!(t == tune_) && exec_) {   // the graph holds the launch shape it was captured with
+        cudaGraphExecDestroy(exec_);
+        exec_ = nullptr;
+    }
+    tune_ = t;
     score_ms_ = 0.0;
     launches_ = 0;
     score_launches_ = 0;
@@ -733,8 +775,9 @@ int Engine::start()
         const int64_t R = g.nrot[g.levels - 1];
         const int64_t vpn = (int64_t)h.dev.pext[0] * h.dev.pext[1] * h.dev.pext[2];
         if (R > TASK_CAP) return set_error(BBS_EINVAL, "localize: %lld initial rotations", (long long)R);
+        const int64_t cap = std::max<int64_t>(tune_.launch_tasks, R);
         for (int64_t v0 = 0; v0 < vpn;) {
-            const int64_t take = std::min<int64_t>(vpn - v0, (TASK_CAP - ntk) / R);
+            const int64_t take = std::min<int64_t>(vpn - v0, (cap - ntk) / R);
             if (take <= 0 || (int)segs.size() == MAXSEG) {
                 BBS_TRY(flush());
                 continue;
@@ -813,7 +856,7 @@ void Engine::mark_finished(std::vector<int>* finished)
 void Engine::launch_select(cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond)
 {
     select_kernel<<<max_slots_, 1024, 0, s>>>(d_S_, max_slots_, d_plan_, d_ls_, d_poff_, d_toff_, d_pcnt_, d_tcnt_, cond,
-                                             use_cond);
+                                             use_cond, tune_);
 }
 
 void Engine::launch_compact(cudaStream_t s)
@@ -867,7 +910,7 @@ int Engine::score_overflow()
         if (!h.live) continue;
         const int64_t nt = h_ctl_[i].n_tasks, np = h_ctl_[i].n_parents;
         for (int64_t t0 = 0; t0 < nt;) {
-            const int64_t take = std::min<int64_t>(nt - t0, TASK_CAP - ntk);
+            const int64_t take = std::min<int64_t>(nt - t0, tune_.launch_tasks - ntk);
             if (take <= 0 || (int)segs.size() == MAXSEG) {
                 BBS_TRY(flush());
                 continue;
@@ -917,7 +960,7 @@ int Engine::build_graph()
         launch_select(cs, cond, 1);
         launch_compact(cs);
         launch_task_rows(d_plan_, d_S_, tasks_, &front_, d_ls_, nsm_ * 4, cs);
-        launch_branch(MODE_SEARCH, d_plan_, d_S_, tasks_, dense_, nsm_ * BRANCH_CTAS_PER_SM, cs);
+        launch_branch(MODE_SEARCH, d_plan_, d_S_, tasks_, dense_, nsm_ * tune_.ctas_per_sm, cs);
         launch_finalize(MODE_SEARCH, d_plan_, d_S_, tasks_, dense_, front_, d_ls_, nsm_ * 8, cs);
         cudaGraph_t out = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cs, &out);
@@ -1074,6 +1117,8 @@ int Engine::score_launch(int mode, const std::vector<Seg>* segs, int64_t n_slice
         h_plan_.n_slices = n_slices;
         h_plan_.n_tasks = n_tasks;
         h_plan_.next_slice = 0;
+        h_plan_.static_pm = tune_.static_pm;
+        h_plan_.grab_min = tune_.grab_min;
         h_plan_.nseg = (int32_t)segs->size();
         h_plan_.mode = mode;
         h_plan_.status = PLAN_OK;
@@ -1095,7 +1140,7 @@ int Engine::score_launch(int mode, const std::vector<Seg>* segs, int64_t n_slice
         evs_.push_back(e1);
         BBS_CUDA_TRY(cudaEventRecord(e0, st_));
     }
-    BBS_CUDA_TRY(launch_branch(mode, d_plan_, d_S_, tasks_, dense_, nsm_ * BRANCH_CTAS_PER_SM, st_));
+    BBS_CUDA_TRY(launch_branch(mode, d_plan_, d_S_, tasks_, dense_, nsm_ * tune_.ctas_per_sm, st_));
     if (timed_) BBS_CUDA_TRY(cudaEventRecord(e1, st_));
     BBS_CUDA_TRY(launch_finalize(mode, d_plan_, d_S_, tasks_, dense_, front_, d_ls_, nsm_ * 8, st_));
     BBS_CUDA_TRY(cudaGetLastError());

@@ -95,6 +95,7 @@ class Engine {
     int max_slots_;
     bool timed_;
     int64_t fcap_;                 // frontier capacity (nodes, all searches)
+    Tuning tune_;                  // launch shape of this run
     size_t fixed_bytes_ = 0;
     FrontDev front_{};
     LoopState* d_ls_ = nullptr;

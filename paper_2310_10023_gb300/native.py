@@ -66,6 +66,16 @@ class Result(C.Structure):
         }
 
 
+class Tuning(C.Structure):
+    """bbs_tuning: launch shape of the search (0 = default)."""
+    _fields_ = [("launch_tasks", C.c_int64), ("static_pm", C.c_int32), ("grab_min", C.c_int32),
+                ("ctas_per_sm", C.c_int32), ("reserved", C.c_int32)]
+
+    def as_dict(self):
+        return {"launch_tasks": self.launch_tasks, "static_pm": self.static_pm, "grab_min": self.grab_min,
+                "ctas_per_sm": self.ctas_per_sm}
+
+
 class ServerOpts(C.Structure):
     _fields_ = [("mem_budget", C.c_size_t), ("max_active", C.c_int32), ("max_frontier", C.c_int64)]
 
@@ -113,6 +123,8 @@ def load():
         L.bbs_version.restype = C.c_char_p
         L.bbs_set_load_factor.argtypes = [C.c_double]
         L.bbs_set_probe_layout.argtypes = [C.c_int]
+        L.bbs_set_tuning.argtypes = [C.c_void_p]
+        L.bbs_get_tuning.argtypes = [C.c_void_p]
         L.bbs_server_create.argtypes = [P(ServerOpts), P(C.c_void_p)]
         L.bbs_server_submit.argtypes = [vp, vp, vp, i64, P(Ranges), P(Opts), P(C.c_uint64)]
         L.bbs_server_poll.argtypes = [vp, C.c_uint64, C.c_int, P(Result)]
@@ -430,6 +442,22 @@ def bbs_server_stats(server: Server) -> dict:
 
 def bbs_server_destroy(server: Server) -> None:
     server.close()
+
+
+def bbs_set_tuning(launch_tasks: int = 0, static_pm: int = 0, grab_min: int = 0, ctas_per_sm: int = 0,
+                   reset: bool = False) -> None:
+    """Launch shape of later searches (0 = default); reset=True restores every default."""
+    if reset:
+        _check(load().bbs_set_tuning(None))
+        return
+    t = Tuning(int(launch_tasks), int(static_pm), int(grab_min), int(ctas_per_sm), 0)
+    _check(load().bbs_set_tuning(C.byref(t)))
+
+
+def bbs_get_tuning() -> dict:
+    t = Tuning()
+    _check(load().bbs_get_tuning(C.byref(t)))
+    return t.as_dict()
 
 
 def bbs_set_load_factor(load_factor: float) -> None:

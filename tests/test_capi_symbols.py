@@ -3,6 +3,8 @@
 import os
 import re
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -32,3 +34,17 @@ def test_binding_wraps_every_declared_function():
 def test_version_string():
     from paper_2310_10023_gb300 import native
     assert "sm_103a" in native.bbs_version()
+
+
+def test_tuning_validation_without_gpu():
+    """bbs_set_tuning checks its ranges on the host (no device work)."""
+    from paper_2310_10023_gb300 import native as nv
+    nv.load()
+    for bad in ({"launch_tasks": (1 << 19) + 1}, {"static_pm": 1001}, {"grab_min": -3}, {"ctas_per_sm": 5}):
+        with pytest.raises(nv.BBSError) as e:
+            nv.bbs_set_tuning(**bad)
+        assert e.value.code == nv.EINVAL
+    nv.bbs_set_tuning(launch_tasks=100, static_pm=500)
+    assert nv.bbs_get_tuning() == {"launch_tasks": 100, "static_pm": 500, "grab_min": 16, "ctas_per_sm": 4}
+    nv.bbs_set_tuning(reset=True)
+    assert nv.bbs_get_tuning()["launch_tasks"] == 1 << 19

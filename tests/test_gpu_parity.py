@@ -418,3 +418,39 @@ def test_graph_loop_equals_host_loop(nv, room_pair, indoor_pair):
     for a, b in zip(many, many_h):
         assert (a.status, a.best_score, list(a.node), a.iterations, a.nodes_scored) == \
                (b.status, b.best_score, list(b.node), b.iterations, b.nodes_scored)
+
+
+def test_launch_shape_does_not_change_results(nv, room_pair, indoor_pair):
+    """Rounds split into many small launches (the host-planned windows of a
+    round above the launch capacity), other static shares, grab sizes and CTA
+    counts: every result, iteration count and node count is unchanged, on the
+    graph loop and the host loop, for one search and for several at once."""
+    def key(r):
+        return (r.status, r.best_score, list(r.node), r.iterations, r.nodes_scored, r.peak_frontier)
+
+    w, m, dm, om = indoor_pair
+    nr, _ = _ranges(nv, w)
+    scans = [synth.make_scan(2, 90 + i, k=2500 + 2000 * i)[0] for i in range(3)]
+    rw, rm, rdm, rom = room_pair
+    rnr, _ = _ranges(nv, rw)
+    rscan = synth.make_scan(rw.scene, 5)[0]
+    opts = nv.make_opts(score_frac=w.score_frac, batch=w.batch)
+    ropts = nv.make_opts(score_frac=rw.score_frac, batch=rw.batch)
+    base = [key(nv.bbs_localize(dm, s, nr, opts)) for s in scans] + [key(nv.bbs_localize(rdm, rscan, rnr, ropts))]
+    base_many = [key(r) for r in nv.bbs_localize_many(dm, scans, nr, opts)]
+    try:
+        for shape in ({"launch_tasks": 64}, {"launch_tasks": 1000, "static_pm": 1, "grab_min": 1},
+                      {"static_pm": 1000, "ctas_per_sm": 1}, {"launch_tasks": 333, "grab_min": 4096, "ctas_per_sm": 3}):
+            nv.bbs_set_tuning(**shape)
+            got = nv.bbs_get_tuning()
+            for k, v in shape.items():
+                assert got[k] == v
+            for flags in (0, nv.HOST_DRIVEN):
+                o = nv.make_opts(score_frac=w.score_frac, batch=w.batch, flags=flags)
+                ro = nv.make_opts(score_frac=rw.score_frac, batch=rw.batch, flags=flags)
+                res = [key(nv.bbs_localize(dm, s, nr, o)) for s in scans] + [key(nv.bbs_localize(rdm, rscan, rnr, ro))]
+                assert res == base, (shape, flags)
+                assert [key(r) for r in nv.bbs_localize_many(dm, scans, nr, o)] == base_many, (shape, flags)
+    finally:
+        nv.bbs_set_tuning(reset=True)
+    assert nv.bbs_get_tuning() == {"launch_tasks": 1 << 19, "static_pm": 750, "grab_min": 16, "ctas_per_sm": 4}
