@@ -233,6 +233,30 @@ def run_batched(nv, torch, maps, w, stream, n=64, seed=4):
             "found": sum(r.status == nv.OK for r in many), "results_equal_plain": f"{same}/{n}"}
 
 
+def run_exact(nv, torch, maps, w, m, scans_d, stream):
+    """The exact-bound mode (maps widened so that every node's score bounds its
+    leaves' under rotation too): nodes scored, time per scan and best scores
+    vs the approximate (default) bound on the same scans."""
+    a = nv.workload_args(w, stream=stream.cuda_stream)
+    e = max(nv.bbs_exact_dilation(maps, s_, a.ranges, a.opts) for s_ in scans_d)
+    md = torch.from_numpy(np.array(m)).cuda()
+    em = nv.bbs_build_maps(md, w.r, w.levels, nv.exact_bound_flags(e))
+    out = {"extra_dilation": e}
+    for name, mp in (("approximate", maps), ("exact", em)):
+        nv.bbs_localize(mp, scans_d[0], a.ranges, a.opts)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = [nv.bbs_localize(mp, s_, a.ranges, a.opts) for s_ in scans_d]
+        e1.record(stream)
+        e1.synchronize()
+        out[name] = {"ms_per_scan": e0.elapsed_time(e1) / len(scans_d),
+                     "nodes_scored_mean": statistics.mean(r.nodes_scored for r in res),
+                     "best_scores": [r.best_score for r in res]}
+    out["same_best_score"] = f"{sum(x == y for x, y in zip(out['approximate']['best_scores'], out['exact']['best_scores']))}/{len(scans_d)}"
+    return out
+
+
 def run_served(nv, torch, lam=200.0, n=64, seed=9):
     """Poisson arrivals (rate lam) of requests with 2k-30k-point scans against
     two resident maps (room and indoor), served by the continuous-batching
@@ -443,10 +467,11 @@ def run_ours(a):
         vals = torch.cat([mx, sm])
     total_ms, e2e_total, probes_all, e2e_probes_all = vals.tolist()
 
-    batched = served = None
+    batched = served = exact = None
     if rank == 0 and ws == 1 and not a.no_forms:
         batched = run_batched(nv, torch, maps, w, stream)
         served = run_served(nv, torch)
+        exact = run_exact(nv, torch, maps, w, m, scans_d, stream)
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         rate, n, dt = cpu_probe_rate(w, m, scans[0])
@@ -479,6 +504,7 @@ def run_ours(a):
                                   "this run); L1 hits let the kernel exceed the random-gather plateau"},
             "batched": batched,
             "served": served,
+            "exact_bound": exact,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_probes_all / (e2e_total / 1e3), "unit": "probes/s",
                     "h2d_bytes_per_step": h2d // a.steps, "d2h_bytes_per_step": d2h // a.steps},

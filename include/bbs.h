@@ -68,6 +68,17 @@ extern "C" {
 /* rotational children a*c + j literally as printed in Eq. (13) instead of
  * the finer segments whose centres lie inside the parent's segment */
 #define BBS_CHILD_LITERAL     0x10u
+/* exact-bound mode (pass BBS_EXACT_BOUND_E(e) to bbs_build_maps, e in 1..15):
+ * every level above the leaves also stores the keys within e voxels around
+ * its dilation ({v - j, j in [-e, 1 + e]^3} instead of {0,1}^3), which covers
+ * the displacement of any scan point between a node's rotation and any leaf
+ * rotation below it; each node's score then bounds its leaves' scores and the
+ * search returns the exhaustive optimum under roto-translational branching
+ * too.  bbs_localize refuses (BBS_EINVAL) a scan whose grid needs more than e
+ * (bbs_exact_dilation gives the need; e = 3 suffices for the workloads here)
+ * or the BBS_CHILD_LITERAL reading, under which no e bounds the children */
+#define BBS_EXACT_BOUND       0x20u
+#define BBS_EXACT_BOUND_E(e)  (BBS_EXACT_BOUND | ((uint32_t)(e) << 12))
 /* time every launch of the scoring kernel with CUDA events on the call's
  * stream (bbs_result.score_ms); off by default */
 #define BBS_TIME_KERNELS      0x100u
@@ -192,6 +203,15 @@ int  bbs_get_tuning(bbs_tuning* t);
 /* All voxel keys of level `level` (n_voxels x 3 int32) into the host buffer
  * out (capacity cap keys); *n receives the count.  BBS_EINVAL if cap is short. */
 int  bbs_maps_keys(const bbs_maps* maps, int level, int32_t* out, int64_t cap, int64_t* n);
+
+/* The extra dilation the exact-bound mode needs for this scan and search
+ * ranges (*e; -1 when no dilation can give the bound): over the levels
+ * l >= 1, ceil((theta_l d / r + 2) / 2^l), where theta_l sums, over the three
+ * axes and the levels 1..l, half a segment (a whole one with
+ * BBS_ANGLE_LOWER_EDGE) -- how far a leaf's angles can lie from a level-l
+ * node's -- and d is the larger of the scan's largest point norm and d_max. */
+int  bbs_exact_dilation(const bbs_maps* maps, const float* scan_xyz, int64_t k, int is_device,
+                        const bbs_ranges* ranges, const bbs_opts* opts, int32_t* e);
 
 /* ---- pose grid: Sec. III-B Eq. (2)-(5), Sec. III-D Eq. (12)-(14) --------
  * Fills, for one (map, scan, ranges, opts) tuple and one level:

@@ -29,6 +29,12 @@ _lib = None
 
 OK, NOT_FOUND, EINVAL, ENOMEM, EKEYRANGE = 0, 1, -1, -2, -5
 TRANSLATION_ONLY, LEAF_UNDILATED, PRUNE_GE, ANGLE_LOWER_EDGE, CHILD_LITERAL = 0x1, 0x2, 0x4, 0x8, 0x10
+EXACT_BOUND = 0x20
+
+
+def exact_flags(e: int) -> int:
+    """Map flags of the exact-bound mode with extra dilation e (1..15)."""
+    return EXACT_BOUND | (int(e) << 12)
 MAX_LEVELS = 16
 
 
@@ -89,6 +95,8 @@ def _load():
         L.orc_grid_build.argtypes = [C.c_double, C.c_int, C.c_double, P(Ranges), C.c_uint32, P(GridT)]
         L.orc_angle.restype = C.c_double
         L.orc_angle.argtypes = [P(GridT), C.c_int, C.c_int, C.c_int64]
+        L.orc_exact_dilation.restype = C.c_int
+        L.orc_exact_dilation.argtypes = [P(GridT), C.c_double]
         L.orc_rotation.restype = None
         L.orc_rotation.argtypes = [P(GridT), C.c_int, C.c_int64, C.c_int64, C.c_int64, f32p]
         L.orc_num_children.restype = C.c_int64
@@ -196,6 +204,10 @@ class Grid:
     def num_children(self, node) -> int:
         n, p = _i32(node)
         return _load().orc_num_children(C.byref(self.g), p)
+
+    def exact_dilation(self, scan_norm_max: float = 0.0) -> int:
+        """Extra dilation the exact-bound mode needs for this grid (-1: none can)."""
+        return _load().orc_exact_dilation(C.byref(self.g), float(scan_norm_max))
 
     def children(self, node) -> np.ndarray:
         n, p = _i32(node)

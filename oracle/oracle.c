@@ -407,8 +407,12 @@ int orc_maps_build(const float* xyz, int64_t n, float r_f, int levels, uint32_t 
     set_keys(&b0, k0);
     free(b0.slot);
 
+    /* exact-bound mode: a wider dilation at every level above the leaves */
+    const int ee = (flags & ORC_EXACT_BOUND) ? ORC_EXACT_E(flags) : 0;
+    if ((flags & ORC_EXACT_BOUND) && ee < 1) { free(k0); free(m); return ORC_EINVAL; }
     for (int l = 0; l < levels && rc == ORC_OK; ++l) {
         int dilate = !(l == 0 && (flags & ORC_LEAF_UNDILATED));
+        const int jlo = l > 0 ? -ee : 0, jhi = l > 0 ? 1 + ee : 1;
         orc_table d;
         if (table_init(&d, 1023)) { rc = ORC_ENOMEM; break; }
         for (int64_t i = 0; i < nb0 && rc == ORC_OK; ++i) {
@@ -416,9 +420,9 @@ int orc_maps_build(const float* xyz, int64_t n, float r_f, int levels, uint32_t 
             int32_t vy = (int32_t)floordiv_pow2(k0[3 * i + 1], l);
             int32_t vz = (int32_t)floordiv_pow2(k0[3 * i + 2], l);
             if (!dilate) { rc = set_add(&d, vx, vy, vz); continue; }
-            for (int jx = 0; jx < 2 && rc == ORC_OK; ++jx)
-                for (int jy = 0; jy < 2 && rc == ORC_OK; ++jy)
-                    for (int jz = 0; jz < 2 && rc == ORC_OK; ++jz)
+            for (int jx = jlo; jx <= jhi && rc == ORC_OK; ++jx)
+                for (int jy = jlo; jy <= jhi && rc == ORC_OK; ++jy)
+                    for (int jz = jlo; jz <= jhi && rc == ORC_OK; ++jz)
                         rc = set_add(&d, vx - jx, vy - jy, vz - jz);
         }
         if (rc != ORC_OK) { free(d.slot); break; }
@@ -434,6 +438,40 @@ int orc_maps_build(const float* xyz, int64_t n, float r_f, int levels, uint32_t 
     if (rc != ORC_OK) { orc_maps_free(m); return rc; }
     *out = m;
     return ORC_OK;
+}
+
+/* Exact-bound mode.  A node at level l with rotation R_p (segment-centre
+ * angles) and any leaf below it with rotation R_d: along the chain of
+ * ancestors each child's angle lies within half a parent segment of the
+ * parent's (centre reading; a whole segment with the lower-edge reading), so
+ * per axis |angle_d - angle_p| <= sum_{k=1..l} delta'_k / 2 and the rotation
+ * between them is at most the sum over the three axes, theta_l (the angle of
+ * R_p^T R_d is bounded by the sum of the axis angles).  A scan point s then
+ * moves by at most theta_l |s| <= theta_l d_max in metres (d_max: the larger of
+ * the grid's and the scan's largest norm), theta_l d_max / r fine voxels;
+ * the floors and the FP32 rounding of the keys add less than 2.  With the
+ * translational offset t in [0, 2^l) of the leaf, the parent's level-l key is
+ * the leaf's minus j with j in [-e, 1 + e] per axis, e = ceil((theta_l d_max / r
+ * + 2) / 2^l): the dilation {v - j} then keeps every leaf hit a parent hit. */
+int orc_exact_dilation(const orc_grid* g, double scan_norm_max)
+{
+    const double dmax = scan_norm_max > g->d_max ? scan_norm_max : g->d_max;
+    if (g->flags & ORC_CHILD_LITERAL) return -1;
+    const double half = (g->flags & ORC_ANGLE_LOWER_EDGE) ? 1.0 : 0.5;
+    int e = 0;
+    double sum[3] = {0.0, 0.0, 0.0};
+    for (int l = 1; l < g->levels; ++l) {
+        double theta = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            /* a single segment at both levels: the child is the parent's angle */
+            if (!(g->N[l][i] == 1 && g->N[l - 1][i] == 1)) sum[i] += half * g->dprime[l][i];
+            theta += sum[i];
+        }
+        const double E = theta * dmax / g->r + 2.0;
+        const int el = (int)ceil(E / ldexp(1.0, l));
+        if (el > e) e = el;
+    }
+    return e;
 }
 
 void orc_maps_free(orc_maps* m)
@@ -624,6 +662,10 @@ int orc_localize(const orc_maps* m, const float* scan, int64_t k, const orc_rang
     orc_grid g;
     int rc = orc_grid_build(m->r, m->levels, dm, rg, flags, &g);
     if (rc) return res->status = rc;
+    if (m->flags & ORC_EXACT_BOUND) {   /* the maps' dilation must cover this grid */
+        const int need = orc_exact_dilation(&g, orc_scan_dmax(scan, k));
+        if (need < 0 || need > ORC_EXACT_E(m->flags)) return res->status = ORC_EINVAL;
+    }
 
     const int lmax = m->levels - 1;
     int32_t best = (int32_t)ceil(score_frac * (double)k) - 1;

@@ -36,6 +36,11 @@ extern "C" {
 #define ORC_PRUNE_GE           0x4u  /* reserved: Algorithm 2's '<' pruning (not implemented) */
 #define ORC_ANGLE_LOWER_EDGE   0x8u  /* angle of index c is W_min + c*delta' (not the segment centre) */
 #define ORC_CHILD_LITERAL      0x10u /* rotational children a*c + j literally (Eq. (13)), not by segment nesting */
+/* exact-bound mode (map flag): levels l >= 1 store {v - j, j in [-e, 1+e]^3},
+ * e in 1..15 in bits 12..15, so that a node's score bounds every leaf below
+ * it under rotation as well (see orc_exact_dilation) */
+#define ORC_EXACT_BOUND        0x20u
+#define ORC_EXACT_E(flags)     ((int)(((flags) >> 12) & 15u))
 
 #define ORC_MAX_LEVELS 16
 
@@ -81,6 +86,11 @@ double orc_scan_dmax(const float* scan_xyz, int64_t k);
 int  orc_grid_build(double r, int levels, double d_max, const orc_ranges* rg,
                     uint32_t flags, orc_grid* g);
 double orc_angle(const orc_grid* g, int level, int axis, int64_t c);
+/* The extra dilation e that makes every node's score an upper bound on its
+ * leaves' scores under this grid for scan points of norm at most
+ * scan_norm_max (exact-bound mode); -1 when no e can (the literal Eq. (13)
+ * children) */
+int orc_exact_dilation(const orc_grid* g, double scan_norm_max);
 /* A = fl32(R(alpha, beta, gamma) / r) row-major, R = Rz(gamma) Ry(beta) Rx(alpha) */
 void orc_rotation(const orc_grid* g, int level, int64_t ia, int64_t ib, int64_t ig, float A[9]);
 int64_t orc_num_children(const orc_grid* g, const int32_t node[7]);

@@ -386,6 +386,7 @@ struct ScanState {
     float4* scan;      // K points, w = 0
     int64_t k;
     double d_max;
+    double norm_max;   // the scan's largest point norm
     HostGrid grid;
     double2* cs;       // (cos, sin) of every segment angle, host libm, FP64
     float4* rot;       // 3 float4 rows per rotation of the top level l_max
@@ -394,6 +395,8 @@ struct ScanState {
 
 int scan_prepare(const bbs_maps* m, const float* xyz, int64_t k, int is_device, const bbs_ranges* rg,
                  const bbs_opts* opts, cudaStream_t st, ScanState* out);
+// extra dilation the exact-bound mode needs for this grid and scan (-1: none can)
+int exact_dilation_needed(const HostGrid& g, double norm_max);
 // the 3 x float4 rows of every rotation of `level` -> out
 cudaError_t launch_level_rows(const ScanState& s, int level, float4* out, cudaStream_t st);
 void scan_release(ScanState* s, cudaStream_t st);

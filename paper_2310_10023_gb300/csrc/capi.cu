@@ -441,6 +441,21 @@ int bbs_set_probe_layout(int layout)
     return maps_set_layout(layout);
 }
 
+int bbs_exact_dilation(const bbs_maps* m, const float* scan_xyz, int64_t k, int is_device, const bbs_ranges* ranges,
+                       const bbs_opts* opts, int32_t* e)
+{
+    clear_error();
+    if (!m || !e) return set_error(BBS_EINVAL, "exact_dilation: NULL argument");
+    DeviceGuard g(m->device);
+    cudaStream_t st = opts ? (cudaStream_t)opts->cuda_stream : nullptr;
+    ScanState S;
+    BBS_TRY(scan_prepare(m, scan_xyz, k, is_device, ranges, opts, st, &S));
+    *e = exact_dilation_needed(S.grid, S.norm_max);
+    scan_release(&S, st);
+    BBS_CUDA_TRY(cudaStreamSynchronize(st));
+    return BBS_OK;
+}
+
 int bbs_set_tuning(const bbs_tuning* t)
 {
     clear_error();

@@ -696,6 +696,16 @@ int Engine::add(const bbs_maps* m, const float* xyz, int64_t k, int is_device, c
         return rc;
     }
     const HostGrid& g = h.scan.grid;
+    if ((m->flags & BBS_EXACT_BOUND) && k > 0) {   // the maps' widening must cover this scan's grid
+        const int need = exact_dilation_needed(g, h.scan.norm_max);
+        const int have = (int)((m->flags >> 12) & 15u);
+        if (need < 0 || need > have) {
+            rc = need < 0 ? set_error(BBS_EINVAL, "localize: the exact bound does not hold for BBS_CHILD_LITERAL")
+                          : set_error(BBS_EINVAL, "localize: exact-bound maps widened by %d, this scan needs %d", have, need);
+            release(i);
+            return rc;
+        }
+    }
     h.bytes += estimate_bytes(k, g) - (3 * sizeof(unsigned long long) * ((size_t)k + 1) + 1024);
     h.thr = (int32_t)std::ceil(frac * (double)k);
     h.res.phase_ms[0] = now_ms() - h.t0;

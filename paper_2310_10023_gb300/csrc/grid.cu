@@ -14,6 +14,8 @@
 #include <cstring>
 #include <vector>
 
+#include <algorithm>
+
 #include "bbs_internal.cuh"
 
 namespace bbs {
@@ -235,6 +237,7 @@ int scan_prepare(const bbs_maps* m, const float* xyz, int64_t k, int is_device, 
     }
     double dm;
     std::memcpy(&dm, &aux.dmax, sizeof(dm));
+    out->norm_max = dm;
     out->d_max = (opts && opts->d_max > 0.0) ? opts->d_max : dm;
     const uint32_t flags = opts ? opts->flags : 0u;
     int rc = grid_build((double)m->r, m->levels, out->d_max, &rg, flags, &out->grid);
@@ -270,6 +273,32 @@ cudaError_t launch_level_rows(const ScanState& s, int level, float4* out, cudaSt
     if (n <= 0) return cudaSuccess;
     level_rows_kernel<<<grid_blocks(n, 256), 256, 0, st>>>(s.cs, dev_grid(s.grid), level, n, out);
     return cudaGetLastError();
+}
+
+// Extra dilation the exact-bound mode needs (BBS_EXACT_BOUND in bbs.h): a
+// leaf's angle lies within sum_{k=1..l} w delta'_k of a level-l node's per
+// axis (w = 1/2, a whole segment with the lower-edge angles; nothing where a
+// level and its finer one both have a single segment), so the rotation
+// between them is at most theta_l, the sum over the axes, and a point of norm
+// at most d moves by theta_l d / r fine voxels; with 2 for the floors and the
+// FP32 keys, e = max over l >= 1 of ceil((theta_l d / r + 2) / 2^l).
+int exact_dilation_needed(const HostGrid& g, double norm_max)
+{
+    if (g.flags & BBS_CHILD_LITERAL) return -1;
+    const double w = (g.flags & BBS_ANGLE_LOWER_EDGE) ? 1.0 : 0.5;
+    const double d = norm_max > g.d_max ? norm_max : g.d_max;
+    double acc[3] = {0.0, 0.0, 0.0};
+    int need = 0;
+    for (int l = 1; l < g.levels; ++l) {
+        double theta = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            if (g.N[l][a] != 1 || g.N[l - 1][a] != 1) acc[a] += w * g.dprime[l][a];
+            theta += acc[a];
+        }
+        const int e = (int)std::ceil((theta * d / g.r + 2.0) / std::ldexp(1.0, l));
+        need = std::max(need, e);
+    }
+    return need;
 }
 
 void scan_release(ScanState* s, cudaStream_t st)

@@ -203,18 +203,18 @@ __device__ __forceinline__ void set_voxel(Brick* tab, uint32_t shift, uint32_t m
             }
 }
 
-__global__ void dilate_kernel(const unsigned long long* keys, int64_t n, int dilate, Brick* tab, uint32_t shift,
+// D_l: every key minus j, j in [jlo, jhi]^3 ({0,1}^3 is the dilation of
+// Sec. III-C; the exact-bound mode widens it; jlo = jhi = 0 stores B_l)
+__global__ void dilate_kernel(const unsigned long long* keys, int64_t n, int jlo, int jhi, Brick* tab, uint32_t shift,
                               uint32_t mask, BuildStatus* st, unsigned long long limit)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         if (*(volatile int*)&st->overflow) return;
         int32_t x, y, z;
         vunpack(keys[i], x, y, z);
-        if (!dilate) {
-            set_voxel(tab, shift, mask, x, y, z, st, limit);
-            continue;
-        }
-        for (int j = 0; j < 8; ++j) set_voxel(tab, shift, mask, x - (j >> 2), y - ((j >> 1) & 1), z - (j & 1), st, limit);
+        for (int jx = jlo; jx <= jhi; ++jx)
+            for (int jy = jlo; jy <= jhi; ++jy)
+                for (int jz = jlo; jz <= jhi; ++jz) set_voxel(tab, shift, mask, x - jx, y - jy, z - jz, st, limit);
     }
 }
 
@@ -396,7 +396,11 @@ int maps_build(const float* xyz, int64_t n, int is_device, float r, int levels, 
     if (!(r > 0.0f) || !isfinite(r)) return set_error(BBS_EINVAL, "build_maps: r must be positive and finite");
     if (levels < 1 || levels > MAX_LEVELS) return set_error(BBS_EINVAL, "build_maps: levels %d outside 1..16", levels);
     if (n < 0 || (n > 0 && !xyz)) return set_error(BBS_EINVAL, "build_maps: bad point array");
-    if (flags & ~(uint32_t)BBS_LEAF_UNDILATED) return set_error(BBS_EINVAL, "build_maps: unsupported flags 0x%x", flags);
+    if (flags & ~(uint32_t)(BBS_LEAF_UNDILATED | BBS_EXACT_BOUND | (15u << 12)))
+        return set_error(BBS_EINVAL, "build_maps: unsupported flags 0x%x", flags);
+    const int exact_e = (flags & BBS_EXACT_BOUND) ? (int)((flags >> 12) & 15u) : 0;
+    if ((flags & BBS_EXACT_BOUND) ? exact_e < 1 : ((flags >> 12) & 15u) != 0)
+        return set_error(BBS_EINVAL, "build_maps: BBS_EXACT_BOUND needs an extra dilation e in 1..15");
 
     bbs_maps* m = new bbs_maps;
     std::memset(m, 0, sizeof(*m));
@@ -515,6 +519,8 @@ int maps_build(const float* xyz, int64_t n, int is_device, float r, int levels, 
             nb = nn;
         }
         const int dilate = !(l == 0 && (flags & BBS_LEAF_UNDILATED));
+        const int ee = l > 0 ? exact_e : 0;                  // exact-bound widening above the leaves
+        const int jlo = dilate ? -ee : 0, jhi = dilate ? 1 + ee : 0;
         // bounds of B_l (D_l extends one voxel lower when dilated)
         int kmin[3] = {0, 0, 0}, kmax[3] = {0, 0, 0};
         if (nb > 0) {
@@ -529,8 +535,8 @@ int maps_build(const float* xyz, int64_t n, int is_device, float r, int levels, 
             TRYC(cudaGetLastError());
             if (read_status()) return fail(set_error(BBS_ECUDA, "build_maps: status read"));
             for (int a = 0; a < 3; ++a) {
-                kmin[a] = hs.kmin[a] - (dilate ? 1 : 0);
-                kmax[a] = hs.kmax[a];
+                kmin[a] = hs.kmin[a] - jhi;
+                kmax[a] = hs.kmax[a] - jlo;
             }
         }
         // scatter D_l into a roomy temporary brick table, growing on overflow
@@ -543,7 +549,7 @@ int maps_build(const float* xyz, int64_t n, int is_device, float r, int levels, 
             init_bricks<<<blocks_for(T), 256, 0, st>>>((Brick*)sc.p[5], T);
             if (reset_status()) return fail(set_error(BBS_ECUDA, "build_maps: status upload"));
             if (nb > 0)
-                dilate_kernel<<<blocks_for(nb), 256, 0, st>>>(keys, nb, dilate, (Brick*)sc.p[5], (uint32_t)(32 - lt),
+                dilate_kernel<<<blocks_for(nb), 256, 0, st>>>(keys, nb, jlo, jhi, (Brick*)sc.p[5], (uint32_t)(32 - lt),
                                                              (uint32_t)(T - 1), d_st, (unsigned long long)(T / 2));
             TRYC(cudaGetLastError());
             if (read_status()) return fail(set_error(BBS_ECUDA, "build_maps: status read"));

@@ -21,6 +21,12 @@ OK, NOT_FOUND, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EKEYRANGE, ECORRUPT = 0, 1, -1, 
 ECANCELED, PENDING = -7, 2
 TRANSLATION_ONLY, LEAF_UNDILATED, PRUNE_GE, ANGLE_LOWER_EDGE, CHILD_LITERAL = 0x1, 0x2, 0x4, 0x8, 0x10
 TIME_KERNELS, HOST_DRIVEN = 0x100, 0x200
+EXACT_BOUND = 0x20
+
+
+def exact_bound_flags(e: int) -> int:
+    """bbs_build_maps flags of the exact-bound mode with extra dilation e (1..15)."""
+    return EXACT_BOUND | (int(e) << 12)
 MAX_LEVELS = 16
 
 _lock = threading.Lock()
@@ -124,6 +130,7 @@ def load():
         L.bbs_set_load_factor.argtypes = [C.c_double]
         L.bbs_set_probe_layout.argtypes = [C.c_int]
         L.bbs_set_tuning.argtypes = [C.c_void_p]
+        L.bbs_exact_dilation.argtypes = [vp, vp, i64, C.c_int, vp, vp, i32p]
         L.bbs_get_tuning.argtypes = [C.c_void_p]
         L.bbs_server_create.argtypes = [P(ServerOpts), P(C.c_void_p)]
         L.bbs_server_submit.argtypes = [vp, vp, vp, i64, P(Ranges), P(Opts), P(C.c_uint64)]
@@ -442,6 +449,16 @@ def bbs_server_stats(server: Server) -> dict:
 
 def bbs_server_destroy(server: Server) -> None:
     server.close()
+
+
+def bbs_exact_dilation(maps: Maps, scan, ranges=None, opts=None) -> int:
+    """Extra dilation the exact-bound mode needs for this scan (-1: none can)."""
+    p, dev, n, keep = _arr(scan, np.float32, 3)
+    e = C.c_int32()
+    _check(load().bbs_exact_dilation(maps.h, p, n, dev, C.byref(ranges) if ranges is not None else None,
+                                     C.byref(opts) if opts is not None else None, C.byref(e)))
+    del keep
+    return int(e.value)
 
 
 def bbs_set_tuning(launch_tasks: int = 0, static_pm: int = 0, grab_min: int = 0, ctas_per_sm: int = 0,

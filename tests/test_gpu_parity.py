@@ -454,3 +454,45 @@ def test_launch_shape_does_not_change_results(nv, room_pair, indoor_pair):
     finally:
         nv.bbs_set_tuning(reset=True)
     assert nv.bbs_get_tuning() == {"launch_tasks": 1 << 19, "static_pm": 750, "grab_min": 16, "ctas_per_sm": 4}
+
+
+# ---- exact-bound mode --------------------------------------------------------
+
+def _window(pose, half_yaw=0.12, rp=0.02):
+    x0 = math.floor(pose[0] / 2.0) * 2.0 - 2.0
+    y0 = math.floor(pose[1] / 2.0) * 2.0 - 2.0
+    return (x0, y0, 0.0), (x0 + 3.9, y0 + 3.9, 1.9), (-rp, -rp, pose[5] - half_yaw), (rp, rp, pose[5] + half_yaw)
+
+
+@pytest.mark.parametrize("leaf", [0, oracle.LEAF_UNDILATED])
+def test_exact_bound_maps_and_search_equal_oracle(nv, leaf):
+    """Exact-bound maps: every level's key set equals the oracle's (levels above
+    the leaves widened by e); the requirement the library reports equals the
+    oracle's; localize on a window equals the oracle's exact BnB (which the
+    oracle pins equal to the exhaustive maximum); a map widened too little is
+    refused."""
+    w = synth.WORKLOADS["room"]
+    m = synth.make_map(w.scene)
+    s, pose = synth.make_scan(1, 0)
+    s = s[:200]
+    lo, hi, alo, ahi = _window(pose)
+    nr, orr = nv.make_ranges(lo, hi, alo, ahi), oracle.make_ranges(lo, hi, alo, ahi)
+    g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), orr, leaf)
+    e = g.exact_dilation(oracle.scan_dmax(s))
+    dm = nv.bbs_build_maps(m, w.r, w.levels, leaf | nv.exact_bound_flags(e))
+    om = oracle.Maps(m, w.r, w.levels, leaf | oracle.exact_flags(e))
+    for l in range(w.levels):
+        assert _keyset(nv.bbs_maps_keys(dm, l)) == _keyset(om.keys(l)), l
+    assert nv.bbs_exact_dilation(dm, s, nr, nv.make_opts(flags=leaf)) == e
+    for batch in (1, 1000):
+        r = nv.bbs_localize(dm, s, nr, nv.make_opts(score_frac=0.3, batch=batch, flags=leaf))
+        o = oracle.localize(om, s, orr, score_frac=0.3, batch=batch, flags=leaf)
+        assert (r.status, r.best_score, list(r.node), r.iterations, r.nodes_scored) == \
+               (o.status, o.best_score, list(o.node), o.iterations, o.nodes_scored), batch
+    small = nv.bbs_build_maps(m, w.r, w.levels, leaf | nv.exact_bound_flags(e - 1))
+    with pytest.raises(nv.BBSError) as ex:
+        nv.bbs_localize(small, s, nr, nv.make_opts(score_frac=0.3, flags=leaf))
+    assert ex.value.code == nv.EINVAL
+    with pytest.raises(nv.BBSError) as ex:
+        nv.bbs_localize(dm, s, nr, nv.make_opts(score_frac=0.3, flags=leaf | nv.CHILD_LITERAL))
+    assert ex.value.code == nv.EINVAL

@@ -148,3 +148,48 @@ def test_tie_break_is_lexmin_leaf():
                                 for jx in (0, 1) for jy in (0, 1) for jz in (0, 1)])
     tied = int((s == len(scan)).sum())
     assert tied == 8
+
+
+@pytest.mark.parametrize("scan_index", [0, 1, 2])
+@pytest.mark.parametrize("batch", [1, 1000])
+@pytest.mark.parametrize("leaf", [0, oracle.LEAF_UNDILATED])
+def test_exact_bound_roto_bnb_equals_brute_force(room, scan_index, batch, leaf):
+    """Exact-bound mode: levels above the leaves dilated by the rotational
+    displacement bound (orc_exact_dilation), so every node's score bounds its
+    leaves' scores under rotation too, and BnB returns the exhaustive maximum
+    over the same leaf set with roto-translational branching."""
+    w, m, _, _ = room
+    s, pose = synth.make_scan(1, scan_index)
+    s = s[:200]
+    rg = _window_ranges(pose)
+    g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), rg, leaf)
+    e = g.exact_dilation(oracle.scan_dmax(s))
+    assert 1 <= e <= 15
+    M = oracle.Maps(m, w.r, w.levels, leaf | oracle.exact_flags(e))
+    res = oracle.localize(M, s, rg, score_frac=0.3, batch=batch, flags=leaf)
+    best, node = oracle.brute_force(M, g, s)
+    assert res.status == oracle.OK
+    assert res.best_score == best
+    assert M.score_nodes(g, s, [list(res.node)])[0] == best and res.node[6] == 0
+    # the level-0 map (the leaf objective) is the ordinary one
+    M0 = oracle.Maps(m, w.r, w.levels, leaf)
+    assert M0.count(0) == M.count(0) and M.count(1) > M0.count(1)
+
+
+def test_exact_bound_requires_enough_dilation(room):
+    """A map whose extra dilation is below what the scan's grid needs is
+    refused (the bound would not hold), as is the literal Eq. (13) reading."""
+    w, m, _, _ = room
+    s, pose = synth.make_scan(1, 0)
+    s = s[:200]
+    rg = _window_ranges(pose)
+    g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), rg)
+    e = g.exact_dilation(oracle.scan_dmax(s))
+    assert e >= 2
+    small = oracle.Maps(m, w.r, w.levels, oracle.exact_flags(e - 1))
+    assert oracle.localize(small, s, rg, score_frac=0.5, batch=100).status == oracle.EINVAL
+    gl = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), rg, oracle.CHILD_LITERAL)
+    assert gl.exact_dilation(oracle.scan_dmax(s)) == -1
+    # the requirement grows with the scan's reach: points twice as far need more
+    far = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), rg).exact_dilation(4.0 * oracle.scan_dmax(s))
+    assert far > e
