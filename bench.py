@@ -266,6 +266,28 @@ def run_exact(nv, torch, stream, n_scans=4):
     return out
 
 
+def run_host_queue(nv, torch, maps, w, scans_d, stream):
+    """The same searches with the frontier on the host (Algorithm 2's own
+    layout: host buckets, per-batch copies) vs the device-resident engine."""
+    a = nv.workload_args(w, stream=stream.cuda_stream)
+    out = {}
+    for name, fn in (("device_frontier", nv.bbs_localize), ("host_frontier", nv.bbs_localize_hostqueue)):
+        fn(maps, scans_d[0], a.ranges, a.opts)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        res = [fn(maps, s_, a.ranges, a.opts) for s_ in scans_d]
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t) * 1e3
+        out[name] = {"ms_per_scan": ms / len(scans_d), "probes_per_s": sum(r.probes for r in res) / (ms / 1e3),
+                     "h2d_bytes_per_scan": statistics.mean(r.h2d_bytes for r in res),
+                     "d2h_bytes_per_scan": statistics.mean(r.d2h_bytes for r in res), "keys": [
+                         (r.best_score, tuple(r.node), r.nodes_scored) for r in res]}
+    same = sum(x == y for x, y in zip(out["device_frontier"].pop("keys"), out["host_frontier"].pop("keys")))
+    out["results_equal"] = f"{same}/{len(scans_d)}"
+    out["speedup_device_vs_host"] = out["host_frontier"]["ms_per_scan"] / out["device_frontier"]["ms_per_scan"]
+    return out
+
+
 def _form(fn, *args):
     """An optional form: its failure is reported in the line, not raised."""
     try:
@@ -518,12 +540,13 @@ def run_ours(a):
         vals = torch.cat([mx, sm])
     total_ms, e2e_total, probes_all, e2e_probes_all = vals.tolist()
 
-    batched = served = exact = outdoor = None
+    batched = served = exact = outdoor = host_queue = None
     if rank == 0 and ws == 1 and not a.no_forms:
         batched = _form(run_batched, nv, torch, maps, w, stream)
         served = _form(run_served, nv, torch)
         exact = _form(run_exact, nv, torch, stream)
         outdoor = _form(run_outdoor, nv, torch, stream)
+        host_queue = _form(run_host_queue, nv, torch, maps, w, scans_d, stream)
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         rate, n, dt = cpu_probe_rate(w, m, scans[0])
@@ -558,6 +581,7 @@ def run_ours(a):
             "served": served,
             "exact_bound": exact,
             "outdoor": outdoor,
+            "host_queue": host_queue,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_probes_all / (e2e_total / 1e3), "unit": "probes/s",
                     "h2d_bytes_per_step": h2d // a.steps, "d2h_bytes_per_step": d2h // a.steps},

@@ -289,6 +289,15 @@ int  bbs_score_batch_noalloc(const bbs_maps* maps, const float* scan_xyz, int64_
 int  bbs_localize(const bbs_maps* maps, const float* scan_xyz, int64_t k, int is_device,
                   const bbs_ranges* ranges, const bbs_opts* opts, bbs_result* out);
 
+/* bbs_localize with the frontier kept on the host, as Algorithm 2 lays it
+ * out (Sec. III-E): a host priority structure; per batch the popped parents'
+ * rotational children are copied to the GPU, scored by the same kernels, and
+ * their children's scores copied back for the host to keep those above best.
+ * Same canonical iteration, so the same results as bbs_localize; it measures
+ * what keeping the frontier on the device buys. */
+int  bbs_localize_hostqueue(const bbs_maps* maps, const float* scan_xyz, int64_t k, int is_device,
+                            const bbs_ranges* ranges, const bbs_opts* opts, bbs_result* out);
+
 /* ---- measurement ----------------------------------------------------------
  * bbs_bench_gather -- device time (ms, CUDA events on cuda_stream) of
  * `gathers` random 32-byte bucket reads, issued as the scoring kernel's probes

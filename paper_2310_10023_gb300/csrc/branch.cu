@@ -45,13 +45,6 @@ __device__ __forceinline__ f2 add2(f2 a, f2 b)
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
-__device__ __forceinline__ f2 add2rm(f2 a, f2 b)
-{
-    f2 d;
-    asm("add.rm.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-
 // fl_rd(a * b + c) per lane, one rounding of the exact value
 __device__ __forceinline__ f2 fma2rm(f2 a, f2 b, f2 c)
 {

@@ -179,6 +179,9 @@ struct Tuning {
 };
 Tuning current_tuning();
 int set_tuning(const bbs_tuning* t);   // validates; NULL restores the defaults
+// the search with its frontier on the host (hostqueue.cu)
+int hostqueue_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device, const bbs_ranges* rg,
+                  const bbs_opts* opts, cudaStream_t st, bbs_result* res);
 
 // CTAs of a scoring launch: one resident wave (4 CTAs of 256 threads per SM, 64 registers a thread)
 constexpr int BRANCH_CTAS_PER_SM = 4;

@@ -396,6 +396,15 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
     return BBS_OK;
 }
 
+int bbs_localize_hostqueue(const bbs_maps* m, const float* scan_xyz, int64_t k, int is_device,
+                           const bbs_ranges* ranges, const bbs_opts* opts, bbs_result* out)
+{
+    clear_error();
+    if (!m || !out) return set_error(BBS_EINVAL, "localize_hostqueue: NULL argument");
+    DeviceGuard g(m->device);
+    return hostqueue_run(m, scan_xyz, k, is_device, ranges, opts, stream_of(opts), out);
+}
+
 int bbs_localize(const bbs_maps* m, const float* scan_xyz, int64_t k, int is_device, const bbs_ranges* ranges,
                  const bbs_opts* opts, bbs_result* out)
 {

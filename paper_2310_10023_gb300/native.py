@@ -130,6 +130,7 @@ def load():
         L.bbs_set_load_factor.argtypes = [C.c_double]
         L.bbs_set_probe_layout.argtypes = [C.c_int]
         L.bbs_set_tuning.argtypes = [C.c_void_p]
+        L.bbs_localize_hostqueue.argtypes = [vp, vp, i64, C.c_int, vp, vp, vp]
         L.bbs_exact_dilation.argtypes = [vp, vp, i64, C.c_int, vp, vp, i32p]
         L.bbs_get_tuning.argtypes = [C.c_void_p]
         L.bbs_server_create.argtypes = [P(ServerOpts), P(C.c_void_p)]
@@ -360,6 +361,18 @@ def bbs_localize(maps: Maps, scan, ranges: Ranges | None = None, opts: Opts | No
     res = Result()
     _check(load().bbs_localize(maps.h, p, k, dev, C.byref(ranges) if ranges else None, C.byref(opts),
                                C.byref(res)), allow_not_found=True)
+    del keep
+    return res
+
+
+def bbs_localize_hostqueue(maps: Maps, scan, ranges: Ranges | None = None, opts: Opts | None = None) -> Result:
+    """bbs_localize with the frontier on the host (Algorithm 2's own layout):
+    same results, per-batch copies to and from the GPU."""
+    p, dev, k, keep = _arr(scan, np.float32, 3)
+    opts = opts or make_opts()
+    res = Result()
+    _check(load().bbs_localize_hostqueue(maps.h, p, k, dev, C.byref(ranges) if ranges else None, C.byref(opts),
+                                         C.byref(res)), allow_not_found=True)
     del keep
     return res
 

@@ -496,3 +496,33 @@ def test_exact_bound_maps_and_search_equal_oracle(nv, leaf):
     with pytest.raises(nv.BBSError) as ex:
         nv.bbs_localize(dm, s, nr, nv.make_opts(score_frac=0.3, flags=leaf | nv.CHILD_LITERAL))
     assert ex.value.code == nv.EINVAL
+
+
+# ---- the frontier on the host (Algorithm 2's own layout) -----------------------
+
+def test_host_queue_equals_device_frontier(nv, room_pair, indoor_pair):
+    """The host-queue search (per-batch copies, host buckets) follows the same
+    canonical iteration as the device-resident engine: identical results and
+    counts, also when rounds are split into small launches."""
+    def key(r):
+        return (r.status, r.best_score, list(r.node), r.iterations, r.nodes_scored, r.peak_frontier)
+
+    cases = []
+    w, m, dm, om = room_pair
+    nr, _ = _ranges(nv, w)
+    for i in (0, 3):
+        cases.append((dm, synth.make_scan(w.scene, i)[0], nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch)))
+    w, m, dm, om = indoor_pair
+    nr, _ = _ranges(nv, w)
+    cases.append((dm, synth.make_scan(w.scene, 2)[0], nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch)))
+    for maps, s, rg, op in cases:
+        a = nv.bbs_localize(maps, s, rg, op)
+        b = nv.bbs_localize_hostqueue(maps, s, rg, op)
+        assert key(a) == key(b)
+        assert b.h2d_bytes > a.h2d_bytes and b.d2h_bytes > a.d2h_bytes   # the per-batch copies
+    try:
+        nv.bbs_set_tuning(launch_tasks=100)
+        maps, s, rg, op = cases[0]
+        assert key(nv.bbs_localize_hostqueue(maps, s, rg, op)) == key(nv.bbs_localize(maps, s, rg, op))
+    finally:
+        nv.bbs_set_tuning(reset=True)
