@@ -158,11 +158,20 @@ void bbs_free_maps(bbs_maps* maps);
 /* Map bounding box of the input cloud (the paper's default translation range). */
 int  bbs_maps_bbox(const bbs_maps* maps, double lo[3], double hi[3]);
 
-/* Statistics of level `level`: stored voxels |H^l|, hash buckets in use,
- * buckets in the table (T_l), longest probe sequence, and the fraction of
- * buckets not in their home slot (the collision rate of Sec. III-C). */
+/* Statistics of level `level`: stored voxels |H^l|, buckets (4^3-voxel
+ * bricks) in use, buckets in the table (T_l; for a dense level every brick of
+ * its box), longest probe sequence, and the fraction of buckets not in their
+ * home slot (the collision rate of Sec. III-C; 0 for a dense level). */
 int  bbs_maps_info(const bbs_maps* maps, int level, int64_t* n_voxels, int64_t* n_buckets,
                    int64_t* table_size, int32_t* max_probe, double* collision_rate);
+
+/* Layout of level `level`'s table: BBS_LAYOUT_WIDE, BBS_LAYOUT_COMPACT or
+ * BBS_LAYOUT_DENSE (see bbs_set_probe_layout).  BBS_EINVAL for a bad handle
+ * or level. */
+#define BBS_LAYOUT_WIDE    0
+#define BBS_LAYOUT_COMPACT 1
+#define BBS_LAYOUT_DENSE   2
+int  bbs_maps_layout(const bbs_maps* maps, int level, int32_t* layout);
 
 /* Target load (buckets in use / buckets) of the tables built by later
  * bbs_build_maps calls in this process; default 0.25.  Sec. III-C enlarges
@@ -172,10 +181,17 @@ int  bbs_maps_info(const bbs_maps* maps, int level, int64_t* n_voxels, int64_t* 
 int  bbs_set_load_factor(double load);
 
 /* Bucket layout of the tables built by later bbs_build_maps calls in this
- * process: 0 (default) uses the compact layout -- a 32-bit key relative to the
- * level's key box and one 16-byte load per probe -- for every level whose box
- * fits 8192 x 8192 x 4092 voxels, the wide layout (64-bit key, 32-byte probe)
- * otherwise; 1 always uses the wide layout.  Scores do not depend on it. */
+ * process (scores never depend on it):
+ *   0 (default)  dense -- every brick of the level's key box at a computed
+ *                index, no key, one 16-byte load per query -- where the box
+ *                holds at most 2^24 bricks, at most 64 x the occupied bricks
+ *                + 2^16, and under 2^20 voxels per axis; else compact -- a
+ *                32-bit key relative to the box, one 16-byte load per probe --
+ *                where the box fits 8192 x 8192 x 4092 voxels; else wide
+ *                (64-bit key, 32-byte probe);
+ *   1            always wide;
+ *   2            hashed only: compact where it fits, else wide.
+ * BBS_EINVAL for any other value. */
 int  bbs_set_probe_layout(int layout);
 
 /* Launch shape of the search, for every engine and launch made after the

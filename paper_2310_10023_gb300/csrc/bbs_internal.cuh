@@ -47,10 +47,18 @@ struct LevelView {
     uint32_t shift;   // home slot = hash >> shift   (table size 2^(32 - shift))
     uint32_t mask;    // table size - 1
     int32_t maxp;     // longest probe distance of any stored brick
-    int32_t compact;  // bucket layout
-    int32_t base[3];  // compact: key origin (multiple of 4)
-    uint32_t rmax[3]; // compact: largest relative key a query block may start at
+    int32_t layout;   // LAYOUT_WIDE, LAYOUT_COMPACT or LAYOUT_DENSE
+    int32_t base[3];  // compact, dense: key origin (multiple of 4)
+    uint32_t rmax[3]; // compact, dense: largest relative key a query block may start at
+    uint32_t nby, nbz; // dense: bricks along y and z (x: rmax[0] / 4 + 1)
 };
+
+// Level table layouts.  Wide: open addressing over 32-byte bricks with a
+// 64-bit brick key.  Compact: open addressing, a 32-bit relative brick key
+// repeated in each 16-byte half.  Dense: every brick of the level's key box
+// at index (bx * nby + by) * nbz + bz (relative brick coordinates), no key:
+// one load per query; chosen when the box is small enough.
+enum { LAYOUT_WIDE = 0, LAYOUT_COMPACT = 1, LAYOUT_DENSE = 2 };
 
 constexpr uint32_t CEMPTY = 0xFFFFFFFFu;
 
@@ -226,7 +234,15 @@ __device__ __forceinline__ uint32_t brick_plane(const uint4& lo, const uint4& hi
 // Occupancy of voxel key k at one level (bbs_score_batch).
 __device__ __forceinline__ uint32_t voxel_bit(const LevelView& L, int32_t kx, int32_t ky, int32_t kz)
 {
-    if (L.compact) {
+    if (L.layout == LAYOUT_DENSE) {
+        const uint32_t rx = (uint32_t)(kx - L.base[0]), ry = (uint32_t)(ky - L.base[1]), rz = (uint32_t)(kz - L.base[2]);
+        if (rx > L.rmax[0] || ry > L.rmax[1] || rz > L.rmax[2]) return 0u;
+        const uint32_t idx = ((rx >> 2) * L.nby + (ry >> 2)) * L.nbz + (rz >> 2);
+        const int oz = (int)(rz & 3u);
+        const uint4 w = __ldg(reinterpret_cast<const uint4*>(L.slots + idx) + (oz >> 1));
+        return (((oz & 1) ? w.z : w.y) >> ((rx & 3u) + 5u * (ry & 3u))) & 1u;
+    }
+    if (L.layout == LAYOUT_COMPACT) {
         const uint32_t rx = (uint32_t)(kx - L.base[0]), ry = (uint32_t)(ky - L.base[1]), rz = (uint32_t)(kz - L.base[2]);
         if (rx > L.rmax[0] || ry > L.rmax[1] || rz > L.rmax[2]) return 0u;
         uint4 w;
@@ -319,9 +335,11 @@ struct LevelTable {
     Brick* slots;
     int log2T;
     int32_t maxp;
-    int32_t compact;
+    int32_t layout;
     int32_t base[3];
     uint32_t rmax[3];
+    uint32_t nby, nbz;
+    int64_t n_slots;     // buckets (hashed layouts) or bricks of the box (dense)
     int64_t n_bricks;
     int64_t n_voxels;
     int64_t displaced;   // bricks not in their home slot
@@ -349,11 +367,13 @@ inline LevelView level_view(const bbs_maps* m, int l)
     v.shift = (uint32_t)(32 - m->lv[l].log2T);
     v.mask = (uint32_t)((1ull << m->lv[l].log2T) - 1ull);
     v.maxp = m->lv[l].maxp;
-    v.compact = m->lv[l].compact;
+    v.layout = m->lv[l].layout;
     for (int i = 0; i < 3; ++i) {
         v.base[i] = m->lv[l].base[i];
         v.rmax[i] = m->lv[l].rmax[i];
     }
+    v.nby = m->lv[l].nby;
+    v.nbz = m->lv[l].nbz;
     return v;
 }
 

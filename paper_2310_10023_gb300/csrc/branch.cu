@@ -69,13 +69,23 @@ constexpr uint32_t KB = 0x4B400000u;   // bit pattern of 1.5 * 2^23
 
 // the 8 child bits of one point from the bit patterns of its level-m key,
 // offset so that the key block (kx, ky, kz) + {0,1}^3 is relative to the
-// compact origin (COMPACT) or absolute (wide)
-template <bool COMPACT>
+// level's box origin (compact, dense) or absolute (wide)
+template <int LAYOUT>
 __device__ __forceinline__ void child_bits(const LevelView& L, uint32_t bx, uint32_t by, uint32_t bz, uint32_t& w0,
                                            uint32_t& w1)
 {
     w0 = w1 = 0;
-    if (COMPACT) {
+    if (LAYOUT == LAYOUT_DENSE) {
+        // relative keys: a pattern outside [KB, KB + 2^22) differs from KB above
+        // bit 21 and so exceeds every rmax (< 2^22)
+        const uint32_t rx = bx ^ KB, ry = by ^ KB, rz = bz ^ KB;
+        if (rx > L.rmax[0] || ry > L.rmax[1] || rz > L.rmax[2]) return;
+        const uint32_t idx = ((rx >> 2) * L.nby + (ry >> 2)) * L.nbz + (rz >> 2);
+        const uint4 w = __ldg(reinterpret_cast<const uint4*>(L.slots + idx) + ((rz >> 1) & 1u));
+        const uint32_t sh = (rx & 3u) + 5u * (ry & 3u);
+        w0 = ((rz & 1u) ? w.z : w.y) >> sh;
+        w1 = ((rz & 1u) ? w.w : w.z) >> sh;
+    } else if (LAYOUT == LAYOUT_COMPACT) {
         // relative keys in [0, 2^13) x [0, 2^13) x [0, 4092): 11 / 11 / 10-bit brick
         // fields that cannot overflow, and never the empty tag (brick z <= 1022);
         // bricks beyond the map's own box are simply absent
@@ -106,7 +116,7 @@ __device__ __forceinline__ void child_bits(const LevelView& L, uint32_t bx, uint
 // blockDim, ... below jhi.  q = (A_i0 x + A_i1 y) + A_i2 z is rounded to FP32
 // after every product and sum (no FMA), as the oracle; the floor, the level
 // shift and the key offset are one fma.rm of that q (see KB).
-template <bool COMPACT>
+template <int LAYOUT>
 __device__ __forceinline__ void score_run(const ulonglong2* sxy, const f2* sz, int n, int jlo, int jhi,
                                           const LevelView& L, const Row2& r0, const Row2& r1, const Row2& r2, f2 S,
                                           f2 Cx, f2 Cy, f2 Cz, uint32_t& acc0, uint32_t& acc1)
@@ -119,11 +129,11 @@ __device__ __forceinline__ void score_run(const ulonglong2* sxy, const f2* sz, i
         up2(fma2rm(rot2(r1, xy.x, xy.y, Z), S, Cy), by1, by2);
         up2(fma2rm(rot2(r2, xy.x, xy.y, Z), S, Cz), bz1, bz2);
         uint32_t w0, w1;
-        child_bits<COMPACT>(L, (uint32_t)bx1, (uint32_t)by1, (uint32_t)bz1, w0, w1);
+        child_bits<LAYOUT>(L, (uint32_t)bx1, (uint32_t)by1, (uint32_t)bz1, w0, w1);
         acc0 += spread4(w0);
         acc1 += spread4(w1);
         if (2 * j + 1 < n) {
-            child_bits<COMPACT>(L, (uint32_t)bx2, (uint32_t)by2, (uint32_t)bz2, w0, w1);
+            child_bits<LAYOUT>(L, (uint32_t)bx2, (uint32_t)by2, (uint32_t)bz2, w0, w1);
             acc0 += spread4(w0);
             acc1 += spread4(w1);
         }
@@ -166,7 +176,7 @@ __device__ __forceinline__ void virtual_parent(const SearchDev& S, int64_t vp, i
 // memory for the whole CTA.
 struct __align__(16) RunDesc {
     f2 a[9];          // rotation entries A_ik, each duplicated for the paired lanes
-    f2 kc[3];         // per-axis 1.5 * 2^23 + translation (- compact origin), paired
+    f2 kc[3];         // per-axis 1.5 * 2^23 + translation (- box origin), paired
     f2 s;             // 2^-m, paired
     int32_t m;        // child level
     int32_t c;        // point chunk
@@ -286,7 +296,7 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
                 tz = tr.tz;
             }
             const LevelView& L = S.maps[m];
-            const bool cmp = L.compact != 0;
+            const bool cmp = L.layout != LAYOUT_WIDE;
             RunDesc& d = rd[tid];
             const int32_t t3[3] = {tx, ty, tz};
             for (int i = 0; i < 3; ++i) {
@@ -341,10 +351,15 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
             const int n = min(PCHUNK, S.K - d.c * PCHUNK);
             const int jlo = d.b0 * (PBLK / 2), jhi = min(d.b1 * (PBLK / 2), (n + 1) >> 1);
             uint32_t acc0 = 0, acc1 = 0;   // bytes: children (0,4,2,6) and (1,5,3,7)
-            if (Lv.compact)
-                score_run<true>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], acc0, acc1);
+            if (Lv.layout == LAYOUT_DENSE)
+                score_run<LAYOUT_DENSE>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], acc0,
+                                        acc1);
+            else if (Lv.layout == LAYOUT_COMPACT)
+                score_run<LAYOUT_COMPACT>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], acc0,
+                                          acc1);
             else
-                score_run<false>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], acc0, acc1);
+                score_run<LAYOUT_WIDE>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], acc0,
+                                       acc1);
             // 16-bit fields: at most 8 points per thread x 32 lanes, x 8 warps, per field
             uint32_t e0 = acc0 & 0x00FF00FFu, o0 = (acc0 >> 8) & 0x00FF00FFu;
             uint32_t e1 = acc1 & 0x00FF00FFu, o1 = (acc1 >> 8) & 0x00FF00FFu;

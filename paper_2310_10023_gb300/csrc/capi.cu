@@ -127,9 +127,17 @@ int bbs_maps_info(const bbs_maps* m, int level, int64_t* n_voxels, int64_t* n_bu
     const LevelTable& t = m->lv[level];
     if (n_voxels) *n_voxels = t.n_voxels;
     if (n_buckets) *n_buckets = t.n_bricks;
-    if (table_size) *table_size = (int64_t)1 << t.log2T;
+    if (table_size) *table_size = t.n_slots;
     if (max_probe) *max_probe = t.maxp;
     if (collision_rate) *collision_rate = t.n_bricks ? (double)t.displaced / (double)t.n_bricks : 0.0;
+    return BBS_OK;
+}
+
+int bbs_maps_layout(const bbs_maps* m, int level, int32_t* layout)
+{
+    clear_error();
+    if (!m || !layout || level < 0 || level >= m->levels) return set_error(BBS_EINVAL, "maps_layout: bad argument");
+    *layout = m->lv[level].layout;
     return BBS_OK;
 }
 

@@ -276,6 +276,58 @@ __global__ void relayout_compact_kernel(const Brick* src, int64_t T, Brick* dst,
     }
 }
 
+// move every brick to its index in a dense table over the level's brick box
+// (relative brick coordinates, x slowest): 16-byte halves [0, 3 planes];
+// bricks of the box that hold no voxel stay zero
+__global__ void relayout_dense_kernel(const Brick* src, int64_t T, Brick* dst, int bx0, int by0, int bz0, uint32_t nby,
+                                      uint32_t nbz, BuildStatus* st)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < T; i += (int64_t)gridDim.x * blockDim.x) {
+        const Brick b = src[i];
+        if (b.key == EMPTY_KEY) continue;
+        const int32_t bx = (int32_t)((b.key >> 40) & 0xFFFFF) - BRICK_BIAS;
+        const int32_t by = (int32_t)((b.key >> 20) & 0xFFFFF) - BRICK_BIAS;
+        const int32_t bz = (int32_t)(b.key & 0xFFFFF) - BRICK_BIAS;
+        const int64_t idx = ((int64_t)(bx - bx0) * nby + (uint32_t)(by - by0)) * nbz + (uint32_t)(bz - bz0);
+        uint32_t* w = reinterpret_cast<uint32_t*>(dst + idx);
+        w[0] = 0u;
+        w[1] = b.plane[0];
+        w[2] = b.plane[1];
+        w[3] = b.plane[2];
+        w[4] = 0u;
+        w[5] = b.plane[2];
+        w[6] = b.plane[3];
+        w[7] = b.plane[4];
+        unsigned c = 0;
+        for (int z = 0; z < 4; ++z) c += __popc(b.plane[z] & 0x7BDEFu);
+        atomicAdd(&st->voxels, (unsigned long long)c);
+    }
+}
+
+// the voxels of a dense table (brick index -> relative brick coordinates)
+__global__ void dense_keys_kernel(const Brick* tab, int64_t T, int bx0, int by0, int bz0, uint32_t nby, uint32_t nbz,
+                                  int32_t* out, unsigned long long* n, int64_t cap)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < T; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t* w = reinterpret_cast<const uint32_t*>(tab + i);
+        const uint32_t planes[4] = {w[1], w[2], w[3], w[6]};
+        if (!(planes[0] | planes[1] | planes[2] | planes[3])) continue;
+        const int32_t bz = (int32_t)(i % nbz) + bz0, by = (int32_t)((i / nbz) % nby) + by0;
+        const int32_t bx = (int32_t)(i / ((int64_t)nbz * nby)) + bx0;
+        for (int z = 0; z < 4; ++z)
+            for (int y = 0; y < 4; ++y)
+                for (int x = 0; x < 4; ++x)
+                    if ((planes[z] >> (x + 5 * y)) & 1u) {
+                        const unsigned long long o = atomicAdd(n, 1ull);
+                        if ((int64_t)o < cap) {
+                            out[3 * o] = 4 * bx + x;
+                            out[3 * o + 1] = 4 * by + y;
+                            out[3 * o + 2] = 4 * bz + z;
+                        }
+                    }
+    }
+}
+
 __global__ void fill_u32(uint32_t* p, int64_t n, uint32_t v)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -372,12 +424,19 @@ int log2_ceil(unsigned long long x)
 
 // target load of the final brick tables (bricks / buckets)
 static double g_load_target = 0.25;
-// 0: compact buckets whenever a level fits them, 1: always wide
+// 0: dense where a level's brick box is small enough, else compact where it
+// fits, else wide; 1: always wide; 2: hashed only (compact where it fits)
 static int g_layout = 0;
+// a dense table holds at most this many bricks, and at most DENSE_RATIO times
+// the level's occupied bricks plus DENSE_SLACK (small maps always qualify)
+constexpr int64_t DENSE_MAX = (int64_t)1 << 24;
+constexpr int64_t DENSE_RATIO = 64;
+constexpr int64_t DENSE_SLACK = (int64_t)1 << 16;
 
 int maps_set_layout(int layout)
 {
-    if (layout < 0 || layout > 1) return set_error(BBS_EINVAL, "probe layout %d (0 auto, 1 wide)", layout);
+    if (layout < 0 || layout > 2)
+        return set_error(BBS_EINVAL, "probe layout %d (0 auto, 1 wide, 2 hashed)", layout);
     g_layout = layout;
     return BBS_OK;
 }
@@ -559,23 +618,34 @@ int maps_build(const float* xyz, int64_t n, int is_device, float r, int levels, 
             lt += 2;
         }
         const int64_t nbricks = (int64_t)hs.count;
+        // the level's brick box: origin a multiple of 4 at least 4 below kmin
+        int base[3];
+        uint32_t rmax[3], nbk[3];
+        for (int a = 0; a < 3; ++a) {
+            base[a] = ((kmin[a] - 4) >> 2) * 4;
+            rmax[a] = (uint32_t)(kmax[a] - base[a]);
+            nbk[a] = (rmax[a] >> 2) + 1;
+        }
+        const int64_t nbox = (int64_t)nbk[0] * nbk[1] * nbk[2];
+        // compact keys when the box fits 11 / 11 / 10 bits of bricks
+        const bool fits = nbk[0] <= 2048u && nbk[1] <= 2048u && nbk[2] <= 1023u;
+        // dense: every relative key below 2^20, so that a key offset clamped to
+        // +-2^21 (a run far outside the map) still lands outside the box
+        const bool short_axes = rmax[0] < (1u << 20) && rmax[1] < (1u << 20) && rmax[2] < (1u << 20);
+        const bool dense = g_layout == 0 && nb > 0 && short_axes && nbox <= DENSE_MAX &&
+                           nbox <= DENSE_RATIO * nbricks + DENSE_SLACK;
+        const bool compact = !dense && fits && g_layout != 1 && nb > 0;
         int lf = log2_ceil((unsigned long long)((double)(nbricks > 0 ? nbricks : 1) / g_load_target + 0.5));
         if (lf < 10) lf = 10;
-        const int64_t TF = (int64_t)1 << lf;
+        const int64_t TF = dense ? nbox : (int64_t)1 << lf;
         TRYC(cudaMalloc((void**)&m->lv[l].slots, sizeof(Brick) * (size_t)TF));
-        // compact layout when the level's key box fits 11 / 11 / 10 bits of bricks
-        int base[3];
-        uint32_t rmax[3];
-        bool fits = true;
-        for (int a = 0; a < 3; ++a) {
-            base[a] = ((kmin[a] - 4) >> 2) * 4;           // a multiple of 4, at least 4 below kmin
-            rmax[a] = (uint32_t)(kmax[a] - base[a]);
-            const uint32_t bricks = (rmax[a] >> 2) + 1;
-            fits = fits && bricks <= (a < 2 ? 2048u : 1023u);
-        }
-        const bool compact = fits && g_layout == 0 && nb > 0;
         if (reset_status()) return fail(set_error(BBS_ECUDA, "build_maps: status upload"));
-        if (compact) {
+        if (dense) {
+            TRYC(cudaMemsetAsync(m->lv[l].slots, 0, sizeof(Brick) * (size_t)TF, st));
+            relayout_dense_kernel<<<blocks_for((int64_t)1 << lt), 256, 0, st>>>(
+                (Brick*)sc.p[5], (int64_t)1 << lt, m->lv[l].slots, base[0] >> 2, base[1] >> 2, base[2] >> 2, nbk[1],
+                nbk[2], d_st);
+        } else if (compact) {
             fill_u32<<<blocks_for(8 * TF), 256, 0, st>>>((uint32_t*)m->lv[l].slots, 8 * TF, CEMPTY);
             relayout_compact_kernel<<<blocks_for((int64_t)1 << lt), 256, 0, st>>>(
                 (Brick*)sc.p[5], (int64_t)1 << lt, m->lv[l].slots, (uint32_t)(32 - lf), (uint32_t)(TF - 1), base[0] >> 2,
@@ -586,11 +656,14 @@ int maps_build(const float* xyz, int64_t n, int is_device, float r, int levels, 
                 (Brick*)sc.p[5], (int64_t)1 << lt, m->lv[l].slots, (uint32_t)(32 - lf), (uint32_t)(TF - 1), d_st);
         }
         TRYC(cudaGetLastError());
-        m->lv[l].compact = compact ? 1 : 0;
+        m->lv[l].layout = dense ? LAYOUT_DENSE : (compact ? LAYOUT_COMPACT : LAYOUT_WIDE);
         for (int a = 0; a < 3; ++a) {
             m->lv[l].base[a] = base[a];
             m->lv[l].rmax[a] = rmax[a];
         }
+        m->lv[l].nby = nbk[1];
+        m->lv[l].nbz = nbk[2];
+        m->lv[l].n_slots = TF;
         if (read_status()) return fail(set_error(BBS_ECUDA, "build_maps: status read"));
         cudaFreeAsync(sc.p[5], st);
         sc.p[5] = nullptr;
@@ -618,12 +691,16 @@ int maps_keys(const bbs_maps* m, int level, int32_t* out, int64_t cap, int64_t* 
     BBS_CUDA_TRY(cudaMalloc((void**)&d_out, sizeof(int32_t) * 3 * (size_t)nv));
     BBS_CUDA_TRY(cudaMalloc((void**)&d_n, sizeof(unsigned long long)));
     cudaMemset(d_n, 0, sizeof(unsigned long long));
-    const int64_t T = (int64_t)1 << m->lv[level].log2T;
-    if (m->lv[level].compact)
-        compact_keys_kernel<<<blocks_for(T), 256>>>(m->lv[level].slots, T, m->lv[level].base[0] >> 2,
-                                                    m->lv[level].base[1] >> 2, m->lv[level].base[2] >> 2, d_out, d_n, nv);
+    const LevelTable& t = m->lv[level];
+    const int64_t T = t.n_slots;
+    if (t.layout == LAYOUT_DENSE)
+        dense_keys_kernel<<<blocks_for(T), 256>>>(t.slots, T, t.base[0] >> 2, t.base[1] >> 2, t.base[2] >> 2, t.nby,
+                                                  t.nbz, d_out, d_n, nv);
+    else if (t.layout == LAYOUT_COMPACT)
+        compact_keys_kernel<<<blocks_for(T), 256>>>(t.slots, T, t.base[0] >> 2, t.base[1] >> 2, t.base[2] >> 2, d_out,
+                                                    d_n, nv);
     else
-        brick_keys_kernel<<<blocks_for(T), 256>>>(m->lv[level].slots, T, d_out, d_n, nv);
+        brick_keys_kernel<<<blocks_for(T), 256>>>(t.slots, T, d_out, d_n, nv);
     cudaError_t e = cudaGetLastError();
     unsigned long long got = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&got, d_n, sizeof(got), cudaMemcpyDeviceToHost);

@@ -119,6 +119,7 @@ def load():
         L.bbs_maps_bbox.argtypes = [vp, dp, dp]
         L.bbs_maps_info.argtypes = [vp, C.c_int, i64p, i64p, i64p, i32p, dp]
         L.bbs_maps_keys.argtypes = [vp, C.c_int, vp, i64, i64p]
+        L.bbs_maps_layout.argtypes = [vp, C.c_int, i32p]
         L.bbs_pose_grid.argtypes = [vp, vp, i64, C.c_int, P(Ranges), P(Opts), C.c_int, i64p, vp, i64, i64p]
         L.bbs_score_batch.argtypes = [vp, vp, i64, C.c_int, P(Ranges), P(Opts), vp, i64, vp]
         L.bbs_score_children.argtypes = [vp, vp, i64, C.c_int, P(Ranges), P(Opts), vp, i64, vp, vp, i64, i64p]
@@ -258,7 +259,18 @@ def bbs_maps_info(maps: Maps, level: int) -> dict:
     mp, cr = C.c_int32(), C.c_double()
     _check(load().bbs_maps_info(maps.h, int(level), C.byref(nv), C.byref(nb), C.byref(ts), C.byref(mp), C.byref(cr)))
     return {"voxels": nv.value, "buckets": nb.value, "table_size": ts.value, "max_probe": mp.value,
-            "collision_rate": cr.value}
+            "collision_rate": cr.value, "layout": bbs_maps_layout(maps, level)}
+
+
+LAYOUT_WIDE, LAYOUT_COMPACT, LAYOUT_DENSE = 0, 1, 2
+LAYOUT_NAMES = {LAYOUT_WIDE: "wide", LAYOUT_COMPACT: "compact", LAYOUT_DENSE: "dense"}
+
+
+def bbs_maps_layout(maps: Maps, level: int) -> int:
+    """Table layout of one level: LAYOUT_WIDE, LAYOUT_COMPACT or LAYOUT_DENSE."""
+    out = C.c_int32()
+    _check(load().bbs_maps_layout(maps.h, int(level), C.byref(out)))
+    return out.value
 
 
 def bbs_maps_keys(maps: Maps, level: int) -> np.ndarray:
@@ -495,7 +507,8 @@ def bbs_set_load_factor(load_factor: float) -> None:
 
 
 def bbs_set_probe_layout(layout: int) -> None:
-    """0: compact buckets where they fit (default), 1: always wide."""
+    """0 (default): dense where a level's brick box is small enough, else
+    compact where it fits, else wide; 1: always wide; 2: hashed only."""
     _check(load().bbs_set_probe_layout(int(layout)))
 
 

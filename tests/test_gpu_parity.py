@@ -310,9 +310,9 @@ def test_localize_many_empty_and_not_found(nv, room_pair):
     assert res[2].status == nv.NOT_FOUND
 
 
-# ---- both bucket layouts --------------------------------------------------------
+# ---- every bucket layout --------------------------------------------------------
 
-@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("layout", [0, 1, 2])
 def test_layouts_agree_with_oracle(nv, layout):
     w = synth.WORKLOADS["room"]
     m = synth.make_map(w.scene)
@@ -322,6 +322,9 @@ def test_layouts_agree_with_oracle(nv, layout):
         dm = nv.bbs_build_maps(m, w.r, w.levels)
     finally:
         nv.bbs_set_probe_layout(0)
+    # the room's boxes are small: dense by default, compact when hashed, wide when forced
+    want = {0: nv.LAYOUT_DENSE, 1: nv.LAYOUT_WIDE, 2: nv.LAYOUT_COMPACT}[layout]
+    assert [nv.bbs_maps_layout(dm, l) for l in range(w.levels)] == [want] * w.levels
     for l in range(w.levels):
         assert _keyset(nv.bbs_maps_keys(dm, l)) == _keyset(om.keys(l)), (layout, l)
     s, _ = synth.make_scan(1, 6)
