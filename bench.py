@@ -521,10 +521,12 @@ def run_ours(a):
     sm_mhz = (kclocks or clocks or {}).get("sm_mhz") or 2070.0
     alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e9          # Gop/s
     alu_achieved = units_per_s * ALG_OPS_PER_UNIT / 1e9
-    # L2 gather: 32-byte buckets per unit against random gathers over an
-    # L2-resident table of the same size (the plateau of bbs_bench_gather)
+    # L2 gather: one 32-byte sector per unit (a byte-grid cell or a bucket
+    # half lives in one sector) against random 32-byte gathers over an
+    # L2-resident table of the level-0 table's size (the plateau of
+    # bbs_bench_gather)
     lvl0 = nv.bbs_maps_info(maps, 0)
-    table_bytes = lvl0["table_size"] * 32
+    table_bytes = lvl0["table_size"] * (1 if lvl0["layout"] == nv.LAYOUT_BYTES else 32)
     gb = 1 << 27
     peak_ms = min(nv.bbs_bench_gather(max(table_bytes, 1 << 22), gb, stream.cuda_stream) for _ in range(3))
     peak_gbs = gb * 32 / peak_ms / 1e6
@@ -559,7 +561,8 @@ def run_ours(a):
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(_workload_desc(w, len(m), statistics.mean(len(s) for s in scans), a.scans),
-                           launch_shape=tuning or dict(nv.bbs_get_tuning(), load_factor=0.25, source="defaults")),
+                           launch_shape=tuning or dict(nv.bbs_get_tuning(), load_factor=0.25, source="defaults"),
+                           map_layout=sorted({nv.LAYOUT_NAMES[nv.bbs_maps_layout(maps, l)] for l in range(w.levels)})),
             "ms_to_optimum": to_opt,
             "ms_total_per_scan": total_ms / a.steps,
             "found": f"{found}/{a.steps}",

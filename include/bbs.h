@@ -160,17 +160,18 @@ int  bbs_maps_bbox(const bbs_maps* maps, double lo[3], double hi[3]);
 
 /* Statistics of level `level`: stored voxels |H^l|, buckets (4^3-voxel
  * bricks) in use, buckets in the table (T_l; for a dense level every brick of
- * its box), longest probe sequence, and the fraction of buckets not in their
+ * its box and one zero brick), longest probe sequence, and the fraction of buckets not in their
  * home slot (the collision rate of Sec. III-C; 0 for a dense level). */
 int  bbs_maps_info(const bbs_maps* maps, int level, int64_t* n_voxels, int64_t* n_buckets,
                    int64_t* table_size, int32_t* max_probe, double* collision_rate);
 
-/* Layout of level `level`'s table: BBS_LAYOUT_WIDE, BBS_LAYOUT_COMPACT or
- * BBS_LAYOUT_DENSE (see bbs_set_probe_layout).  BBS_EINVAL for a bad handle
+/* Layout of level `level`'s table: BBS_LAYOUT_WIDE, BBS_LAYOUT_COMPACT,
+ * BBS_LAYOUT_DENSE or BBS_LAYOUT_BYTES (see bbs_set_probe_layout).  BBS_EINVAL for a bad handle
  * or level. */
 #define BBS_LAYOUT_WIDE    0
 #define BBS_LAYOUT_COMPACT 1
 #define BBS_LAYOUT_DENSE   2
+#define BBS_LAYOUT_BYTES   3
 int  bbs_maps_layout(const bbs_maps* maps, int level, int32_t* layout);
 
 /* Target load (buckets in use / buckets) of the tables built by later
@@ -182,15 +183,20 @@ int  bbs_set_load_factor(double load);
 
 /* Bucket layout of the tables built by later bbs_build_maps calls in this
  * process (scores never depend on it):
- *   0 (default)  dense -- every brick of the level's key box at a computed
- *                index, no key, one 16-byte load per query -- where the box
- *                holds at most 2^24 bricks, at most 64 x the occupied bricks
- *                + 2^16, and under 2^20 voxels per axis; else compact -- a
- *                32-bit key relative to the box, one 16-byte load per probe --
- *                where the box fits 8192 x 8192 x 4092 voxels; else wide
- *                (64-bit key, 32-byte probe);
+ *   0 (default)  byte grid -- one byte per key of the level's key box holding
+ *                the 8 child bits of that key (Eq. (13) children), one 1-byte
+ *                load per query -- where the box spans at most 2^24 4^3-key
+ *                bricks, at most 64 x the occupied bricks + 2^16, and under
+ *                2^20 keys per axis; else compact -- a 32-bit key relative to
+ *                the box, one 16-byte load per probe -- where the box fits
+ *                8192 x 8192 x 4092 keys; else wide (64-bit key, 32-byte
+ *                probe);
  *   1            always wide;
- *   2            hashed only: compact where it fits, else wide.
+ *   2            hashed only: compact where it fits, else wide;
+ *   3            dense bricks where the box qualifies: every brick of the
+ *                box at a computed index, no key, one 16-byte load per query;
+ *                else hashed;
+ *   4            byte grid where the box qualifies, else hashed.
  * BBS_EINVAL for any other value. */
 int  bbs_set_probe_layout(int layout);
 

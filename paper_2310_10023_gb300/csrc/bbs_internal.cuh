@@ -45,12 +45,12 @@ static_assert(sizeof(Brick) == 32, "brick must be one 32-byte sector");
 struct LevelView {
     const Brick* slots;
     uint32_t shift;   // home slot = hash >> shift   (table size 2^(32 - shift))
-    uint32_t mask;    // table size - 1
+    uint32_t mask;    // hashed: table size - 1; dense: index of the zero brick past the box
     int32_t maxp;     // longest probe distance of any stored brick
     int32_t layout;   // LAYOUT_WIDE, LAYOUT_COMPACT or LAYOUT_DENSE
     int32_t base[3];  // compact, dense: key origin (multiple of 4)
     uint32_t rmax[3]; // compact, dense: largest relative key a query block may start at
-    uint32_t nby, nbz; // dense: bricks along y and z (x: rmax[0] / 4 + 1)
+    uint32_t nby, nbz; // dense: bricks along y and z (x: rmax[0] / 4 + 1); bytes: keys (rmax + 2)
 };
 
 // Level table layouts.  Wide: open addressing over 32-byte bricks with a
@@ -58,7 +58,11 @@ struct LevelView {
 // repeated in each 16-byte half.  Dense: every brick of the level's key box
 // at index (bx * nby + by) * nbz + bz (relative brick coordinates), no key:
 // one load per query; chosen when the box is small enough.
-enum { LAYOUT_WIDE = 0, LAYOUT_COMPACT = 1, LAYOUT_DENSE = 2 };
+// Bytes: one byte per key of the box (x slowest), bit jx + 2 jy + 4 jz set
+// when key + (jx, jy, jz) is in the level's set: the 8 children of a key
+// block in one byte load; the box reaches one key past rmax on every axis,
+// an empty key that out-of-box queries are clamped to.
+enum { LAYOUT_WIDE = 0, LAYOUT_COMPACT = 1, LAYOUT_DENSE = 2, LAYOUT_BYTES = 3 };
 
 constexpr uint32_t CEMPTY = 0xFFFFFFFFu;
 
@@ -234,6 +238,12 @@ __device__ __forceinline__ uint32_t brick_plane(const uint4& lo, const uint4& hi
 // Occupancy of voxel key k at one level (bbs_score_batch).
 __device__ __forceinline__ uint32_t voxel_bit(const LevelView& L, int32_t kx, int32_t ky, int32_t kz)
 {
+    if (L.layout == LAYOUT_BYTES) {
+        const uint32_t rx = (uint32_t)(kx - L.base[0]), ry = (uint32_t)(ky - L.base[1]), rz = (uint32_t)(kz - L.base[2]);
+        if (rx > L.rmax[0] || ry > L.rmax[1] || rz > L.rmax[2]) return 0u;
+        const uint8_t* b = reinterpret_cast<const uint8_t*>(L.slots);
+        return __ldg(b + ((size_t)rx * L.nby + ry) * L.nbz + rz) & 1u;
+    }
     if (L.layout == LAYOUT_DENSE) {
         const uint32_t rx = (uint32_t)(kx - L.base[0]), ry = (uint32_t)(ky - L.base[1]), rz = (uint32_t)(kz - L.base[2]);
         if (rx > L.rmax[0] || ry > L.rmax[1] || rz > L.rmax[2]) return 0u;
@@ -339,7 +349,7 @@ struct LevelTable {
     int32_t base[3];
     uint32_t rmax[3];
     uint32_t nby, nbz;
-    int64_t n_slots;     // buckets (hashed layouts) or bricks of the box (dense)
+    int64_t n_slots;     // buckets (hashed), bricks of the box + 1 zero brick (dense), keys (bytes)
     int64_t n_bricks;
     int64_t n_voxels;
     int64_t displaced;   // bricks not in their home slot
@@ -365,7 +375,8 @@ inline LevelView level_view(const bbs_maps* m, int l)
     LevelView v;
     v.slots = m->lv[l].slots;
     v.shift = (uint32_t)(32 - m->lv[l].log2T);
-    v.mask = (uint32_t)((1ull << m->lv[l].log2T) - 1ull);
+    v.mask = m->lv[l].layout == LAYOUT_DENSE ? (uint32_t)(m->lv[l].n_slots - 1)
+                                             : (uint32_t)((1ull << m->lv[l].log2T) - 1ull);
     v.maxp = m->lv[l].maxp;
     v.layout = m->lv[l].layout;
     for (int i = 0; i < 3; ++i) {

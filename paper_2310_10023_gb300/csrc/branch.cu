@@ -78,9 +78,10 @@ __device__ __forceinline__ void child_bits(const LevelView& L, uint32_t bx, uint
     if (LAYOUT == LAYOUT_DENSE) {
         // relative keys: a pattern outside [KB, KB + 2^22) differs from KB above
         // bit 21 and so exceeds every rmax (< 2^22)
+        // (branch-free: a query outside the box reads the zero brick past it)
         const uint32_t rx = bx ^ KB, ry = by ^ KB, rz = bz ^ KB;
-        if (rx > L.rmax[0] || ry > L.rmax[1] || rz > L.rmax[2]) return;
-        const uint32_t idx = ((rx >> 2) * L.nby + (ry >> 2)) * L.nbz + (rz >> 2);
+        const bool in = rx <= L.rmax[0] && ry <= L.rmax[1] && rz <= L.rmax[2];
+        const uint32_t idx = in ? ((rx >> 2) * L.nby + (ry >> 2)) * L.nbz + (rz >> 2) : L.mask;
         const uint4 w = __ldg(reinterpret_cast<const uint4*>(L.slots + idx) + ((rz >> 1) & 1u));
         const uint32_t sh = (rx & 3u) + 5u * (ry & 3u);
         w0 = ((rz & 1u) ? w.z : w.y) >> sh;
@@ -109,6 +110,20 @@ __device__ __forceinline__ void child_bits(const LevelView& L, uint32_t bx, uint
     }
 }
 
+// The 8 child counts of one point from a byte grid (LAYOUT_BYTES): relative
+// keys clamped to the empty key past the box, one byte load, and each nibble
+// (children jz = 0, then jz = 1) spread to 4 byte counters by one multiply
+// (bit i of the nibble lands on bit 8 i; the other partial products fall on
+// distinct bits outside the mask, so no carry reaches a counter).
+__device__ __forceinline__ void bytes_acc(const LevelView& L, uint32_t bx, uint32_t by, uint32_t bz, uint32_t ex,
+                                          uint32_t ey, uint32_t ez, uint32_t& acc0, uint32_t& acc1)
+{
+    const uint32_t rx = min(bx ^ KB, ex), ry = min(by ^ KB, ey), rz = min(bz ^ KB, ez);
+    const uint32_t v = __ldg(reinterpret_cast<const uint8_t*>(L.slots) + ((rx * L.nby + ry) * L.nbz + rz));
+    acc0 += ((v & 0xFu) * 0x204081u) & 0x01010101u;
+    acc1 += ((v >> 4) * 0x204081u) & 0x01010101u;
+}
+
 // One run (a rotational child over blocks of the staged chunk), two points
 // per step.  The chunk is staged as pairs: sxy[j] = (x_2j, x_2j+1, y_2j,
 // y_2j+1) and sz[j] = (z_2j, z_2j+1), so each coordinate pair is one 64-bit
@@ -121,13 +136,19 @@ __device__ __forceinline__ void score_run(const ulonglong2* sxy, const f2* sz, i
                                           const LevelView& L, const Row2& r0, const Row2& r1, const Row2& r2, f2 S,
                                           f2 Cx, f2 Cy, f2 Cz, uint32_t& acc0, uint32_t& acc1)
 {
-    for (int j = jlo + threadIdx.x; j < jhi; j += blockDim.x) {
+    const uint32_t ex = L.rmax[0] + 1u, ey = L.rmax[1] + 1u, ez = L.rmax[2] + 1u;   // bytes: the empty key past the box
+    auto pair = [&](int j) {
         const ulonglong2 xy = sxy[j];
         const f2 Z = sz[j];
         int32_t bx1, bx2, by1, by2, bz1, bz2;
         up2(fma2rm(rot2(r0, xy.x, xy.y, Z), S, Cx), bx1, bx2);
         up2(fma2rm(rot2(r1, xy.x, xy.y, Z), S, Cy), by1, by2);
         up2(fma2rm(rot2(r2, xy.x, xy.y, Z), S, Cz), bz1, bz2);
+        if (LAYOUT == LAYOUT_BYTES) {
+            bytes_acc(L, (uint32_t)bx1, (uint32_t)by1, (uint32_t)bz1, ex, ey, ez, acc0, acc1);
+            if (2 * j + 1 < n) bytes_acc(L, (uint32_t)bx2, (uint32_t)by2, (uint32_t)bz2, ex, ey, ez, acc0, acc1);
+            return;
+        }
         uint32_t w0, w1;
         child_bits<LAYOUT>(L, (uint32_t)bx1, (uint32_t)by1, (uint32_t)bz1, w0, w1);
         acc0 += spread4(w0);
@@ -137,7 +158,14 @@ __device__ __forceinline__ void score_run(const ulonglong2* sxy, const f2* sz, i
             acc0 += spread4(w0);
             acc1 += spread4(w1);
         }
-    }
+    };
+    int j = jlo + threadIdx.x;
+    if (LAYOUT == LAYOUT_DENSE || LAYOUT == LAYOUT_BYTES)   // two pairs per step: four gathers in flight per thread
+        for (; j + (int)blockDim.x < jhi; j += 2 * blockDim.x) {
+            pair(j);
+            pair(j + blockDim.x);
+        }
+    for (; j < jhi; j += blockDim.x) pair(j);
 }
 
 // the segment holding launch-local slice w (segments in slice order)
@@ -351,7 +379,10 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
             const int n = min(PCHUNK, S.K - d.c * PCHUNK);
             const int jlo = d.b0 * (PBLK / 2), jhi = min(d.b1 * (PBLK / 2), (n + 1) >> 1);
             uint32_t acc0 = 0, acc1 = 0;   // bytes: children (0,4,2,6) and (1,5,3,7)
-            if (Lv.layout == LAYOUT_DENSE)
+            if (Lv.layout == LAYOUT_BYTES)
+                score_run<LAYOUT_BYTES>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], acc0,
+                                        acc1);
+            else if (Lv.layout == LAYOUT_DENSE)
                 score_run<LAYOUT_DENSE>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], acc0,
                                         acc1);
             else if (Lv.layout == LAYOUT_COMPACT)

@@ -304,6 +304,46 @@ __global__ void relayout_dense_kernel(const Brick* src, int64_t T, Brick* dst, i
     }
 }
 
+// byte grid from a dense brick table: cell (x, y, z) of nx x ny x nz (x
+// slowest) gets bit jx + 2 jy + 4 jz when key (x, y, z) + (jx, jy, jz) of the
+// box is in the set (the brick planes carry the +1 halo)
+__global__ void bytes_fill_kernel(const Brick* bricks, uint32_t nbx, uint32_t nby, uint32_t nbz, uint8_t* out,
+                                  uint32_t nx, uint32_t ny, uint32_t nz)
+{
+    const int64_t n = (int64_t)nx * ny * nz;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t z = (uint32_t)(i % nz), y = (uint32_t)((i / nz) % ny), x = (uint32_t)(i / ((int64_t)nz * ny));
+        uint32_t v = 0;
+        if ((x >> 2) < nbx && (y >> 2) < nby && (z >> 2) < nbz) {
+            const uint32_t* w =
+                reinterpret_cast<const uint32_t*>(bricks + ((int64_t)(x >> 2) * nby + (y >> 2)) * nbz + (z >> 2));
+            const uint32_t p[5] = {w[1], w[2], w[3], w[6], w[7]};
+            const uint32_t oz = z & 3u, sh = (x & 3u) + 5u * (y & 3u);
+            for (uint32_t jz = 0; jz < 2; ++jz)
+                for (uint32_t jy = 0; jy < 2; ++jy)
+                    for (uint32_t jx = 0; jx < 2; ++jx)
+                        v |= ((p[oz + jz] >> (sh + jx + 5u * jy)) & 1u) << (jx + 2u * jy + 4u * jz);
+        }
+        out[i] = (uint8_t)v;
+    }
+}
+
+// the voxels of a byte grid (bit 0 of each cell)
+__global__ void bytes_keys_kernel(const uint8_t* cells, uint32_t nx, uint32_t ny, uint32_t nz, int x0, int y0, int z0,
+                                  int32_t* out, unsigned long long* n, int64_t cap)
+{
+    const int64_t T = (int64_t)nx * ny * nz;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < T; i += (int64_t)gridDim.x * blockDim.x) {
+        if (!(cells[i] & 1u)) continue;
+        const unsigned long long o = atomicAdd(n, 1ull);
+        if ((int64_t)o < cap) {
+            out[3 * o] = (int32_t)(i / ((int64_t)nz * ny)) + x0;
+            out[3 * o + 1] = (int32_t)((i / nz) % ny) + y0;
+            out[3 * o + 2] = (int32_t)(i % nz) + z0;
+        }
+    }
+}
+
 // the voxels of a dense table (brick index -> relative brick coordinates)
 __global__ void dense_keys_kernel(const Brick* tab, int64_t T, int bx0, int by0, int bz0, uint32_t nby, uint32_t nbz,
                                   int32_t* out, unsigned long long* n, int64_t cap)
@@ -424,19 +464,22 @@ int log2_ceil(unsigned long long x)
 
 // target load of the final brick tables (bricks / buckets)
 static double g_load_target = 0.25;
-// 0: dense where a level's brick box is small enough, else compact where it
-// fits, else wide; 1: always wide; 2: hashed only (compact where it fits)
+// 0: byte grid where a level's box is small enough, else compact where it
+// fits, else wide; 1: always wide; 2: hashed only (compact where it fits);
+// 3: dense bricks where the box qualifies, else hashed; 4: byte grid where
+// the box qualifies, else hashed
 static int g_layout = 0;
-// a dense table holds at most this many bricks, and at most DENSE_RATIO times
-// the level's occupied bricks plus DENSE_SLACK (small maps always qualify)
+// a dense table (bricks or bytes) spans a box of at most this many bricks, and
+// at most DENSE_RATIO times the level's occupied bricks plus DENSE_SLACK
+// (small maps always qualify)
 constexpr int64_t DENSE_MAX = (int64_t)1 << 24;
 constexpr int64_t DENSE_RATIO = 64;
 constexpr int64_t DENSE_SLACK = (int64_t)1 << 16;
 
 int maps_set_layout(int layout)
 {
-    if (layout < 0 || layout > 2)
-        return set_error(BBS_EINVAL, "probe layout %d (0 auto, 1 wide, 2 hashed)", layout);
+    if (layout < 0 || layout > 4)
+        return set_error(BBS_EINVAL, "probe layout %d (0 auto, 1 wide, 2 hashed, 3 dense, 4 bytes)", layout);
     g_layout = layout;
     return BBS_OK;
 }
@@ -632,15 +675,29 @@ int maps_build(const float* xyz, int64_t n, int is_device, float r, int levels, 
         // dense: every relative key below 2^20, so that a key offset clamped to
         // +-2^21 (a run far outside the map) still lands outside the box
         const bool short_axes = rmax[0] < (1u << 20) && rmax[1] < (1u << 20) && rmax[2] < (1u << 20);
-        const bool dense = g_layout == 0 && nb > 0 && short_axes && nbox <= DENSE_MAX &&
-                           nbox <= DENSE_RATIO * nbricks + DENSE_SLACK;
-        const bool compact = !dense && fits && g_layout != 1 && nb > 0;
+        const bool box_ok = nb > 0 && short_axes && nbox < DENSE_MAX && nbox <= DENSE_RATIO * nbricks + DENSE_SLACK;
+        const uint32_t ncell[3] = {rmax[0] + 2u, rmax[1] + 2u, rmax[2] + 2u};   // bytes: one empty key past rmax
+        const int64_t cells = (int64_t)ncell[0] * ncell[1] * ncell[2];
+        const bool bytes = box_ok && (g_layout == 0 || g_layout == 4) && cells < ((int64_t)1 << 31);
+        const bool dense = box_ok && !bytes && (g_layout == 0 || g_layout == 3);
+        const bool compact = !dense && !bytes && fits && g_layout != 1 && nb > 0;
         int lf = log2_ceil((unsigned long long)((double)(nbricks > 0 ? nbricks : 1) / g_load_target + 0.5));
         if (lf < 10) lf = 10;
-        const int64_t TF = dense ? nbox : (int64_t)1 << lf;
-        TRYC(cudaMalloc((void**)&m->lv[l].slots, sizeof(Brick) * (size_t)TF));
+        const int64_t TF = bytes ? cells : (dense ? nbox + 1 : (int64_t)1 << lf);   // dense: + the zero brick
+        const size_t table_bytes = bytes ? (size_t)cells : sizeof(Brick) * (size_t)TF;
+        TRYC(cudaMalloc((void**)&m->lv[l].slots, table_bytes));
         if (reset_status()) return fail(set_error(BBS_ECUDA, "build_maps: status upload"));
-        if (dense) {
+        if (bytes) {
+            // dense bricks first (voxel count), then one byte per key of the box
+            TRYC(cudaMallocAsync(&sc.p[6], sizeof(Brick) * (size_t)nbox, st));
+            TRYC(cudaMemsetAsync(sc.p[6], 0, sizeof(Brick) * (size_t)nbox, st));
+            relayout_dense_kernel<<<blocks_for((int64_t)1 << lt), 256, 0, st>>>(
+                (Brick*)sc.p[5], (int64_t)1 << lt, (Brick*)sc.p[6], base[0] >> 2, base[1] >> 2, base[2] >> 2, nbk[1],
+                nbk[2], d_st);
+            bytes_fill_kernel<<<blocks_for(cells), 256, 0, st>>>((const Brick*)sc.p[6], nbk[0], nbk[1], nbk[2],
+                                                                 (uint8_t*)m->lv[l].slots, ncell[0], ncell[1],
+                                                                 ncell[2]);
+        } else if (dense) {
             TRYC(cudaMemsetAsync(m->lv[l].slots, 0, sizeof(Brick) * (size_t)TF, st));
             relayout_dense_kernel<<<blocks_for((int64_t)1 << lt), 256, 0, st>>>(
                 (Brick*)sc.p[5], (int64_t)1 << lt, m->lv[l].slots, base[0] >> 2, base[1] >> 2, base[2] >> 2, nbk[1],
@@ -656,23 +713,27 @@ int maps_build(const float* xyz, int64_t n, int is_device, float r, int levels, 
                 (Brick*)sc.p[5], (int64_t)1 << lt, m->lv[l].slots, (uint32_t)(32 - lf), (uint32_t)(TF - 1), d_st);
         }
         TRYC(cudaGetLastError());
-        m->lv[l].layout = dense ? LAYOUT_DENSE : (compact ? LAYOUT_COMPACT : LAYOUT_WIDE);
+        m->lv[l].layout = bytes ? LAYOUT_BYTES : (dense ? LAYOUT_DENSE : (compact ? LAYOUT_COMPACT : LAYOUT_WIDE));
         for (int a = 0; a < 3; ++a) {
             m->lv[l].base[a] = base[a];
             m->lv[l].rmax[a] = rmax[a];
         }
-        m->lv[l].nby = nbk[1];
-        m->lv[l].nbz = nbk[2];
+        m->lv[l].nby = bytes ? ncell[1] : nbk[1];
+        m->lv[l].nbz = bytes ? ncell[2] : nbk[2];
         m->lv[l].n_slots = TF;
         if (read_status()) return fail(set_error(BBS_ECUDA, "build_maps: status read"));
         cudaFreeAsync(sc.p[5], st);
         sc.p[5] = nullptr;
+        if (sc.p[6]) {
+            cudaFreeAsync(sc.p[6], st);
+            sc.p[6] = nullptr;
+        }
         m->lv[l].log2T = lf;
         m->lv[l].maxp = hs.maxp;
         m->lv[l].n_bricks = nbricks;
         m->lv[l].n_voxels = (int64_t)hs.voxels;
         m->lv[l].displaced = (int64_t)hs.displaced;
-        m->arena_bytes += sizeof(Brick) * (size_t)TF;
+        m->arena_bytes += table_bytes;
     }
 #undef TRYC
     *out = m;
@@ -693,7 +754,10 @@ int maps_keys(const bbs_maps* m, int level, int32_t* out, int64_t cap, int64_t* 
     cudaMemset(d_n, 0, sizeof(unsigned long long));
     const LevelTable& t = m->lv[level];
     const int64_t T = t.n_slots;
-    if (t.layout == LAYOUT_DENSE)
+    if (t.layout == LAYOUT_BYTES)
+        bytes_keys_kernel<<<blocks_for(T), 256>>>(reinterpret_cast<const uint8_t*>(t.slots), t.rmax[0] + 2u, t.nby,
+                                                  t.nbz, t.base[0], t.base[1], t.base[2], d_out, d_n, nv);
+    else if (t.layout == LAYOUT_DENSE)
         dense_keys_kernel<<<blocks_for(T), 256>>>(t.slots, T, t.base[0] >> 2, t.base[1] >> 2, t.base[2] >> 2, t.nby,
                                                   t.nbz, d_out, d_n, nv);
     else if (t.layout == LAYOUT_COMPACT)

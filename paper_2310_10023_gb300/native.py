@@ -262,12 +262,12 @@ def bbs_maps_info(maps: Maps, level: int) -> dict:
             "collision_rate": cr.value, "layout": bbs_maps_layout(maps, level)}
 
 
-LAYOUT_WIDE, LAYOUT_COMPACT, LAYOUT_DENSE = 0, 1, 2
-LAYOUT_NAMES = {LAYOUT_WIDE: "wide", LAYOUT_COMPACT: "compact", LAYOUT_DENSE: "dense"}
+LAYOUT_WIDE, LAYOUT_COMPACT, LAYOUT_DENSE, LAYOUT_BYTES = 0, 1, 2, 3
+LAYOUT_NAMES = {LAYOUT_WIDE: "wide", LAYOUT_COMPACT: "compact", LAYOUT_DENSE: "dense", LAYOUT_BYTES: "bytes"}
 
 
 def bbs_maps_layout(maps: Maps, level: int) -> int:
-    """Table layout of one level: LAYOUT_WIDE, LAYOUT_COMPACT or LAYOUT_DENSE."""
+    """Table layout of one level: LAYOUT_WIDE, LAYOUT_COMPACT, LAYOUT_DENSE or LAYOUT_BYTES."""
     out = C.c_int32()
     _check(load().bbs_maps_layout(maps.h, int(level), C.byref(out)))
     return out.value
@@ -507,8 +507,9 @@ def bbs_set_load_factor(load_factor: float) -> None:
 
 
 def bbs_set_probe_layout(layout: int) -> None:
-    """0 (default): dense where a level's brick box is small enough, else
-    compact where it fits, else wide; 1: always wide; 2: hashed only."""
+    """0 (default): byte grid where a level's box is small enough, else
+    compact where it fits, else wide; 1: always wide; 2: hashed only;
+    3: dense bricks where the box qualifies; 4: byte grid where it does."""
     _check(load().bbs_set_probe_layout(int(layout)))
 
 

@@ -48,3 +48,20 @@ def test_tuning_validation_without_gpu():
     assert nv.bbs_get_tuning() == {"launch_tasks": 100, "static_pm": 500, "grab_min": 16, "ctas_per_sm": 4}
     nv.bbs_set_tuning(reset=True)
     assert nv.bbs_get_tuning()["launch_tasks"] == 1 << 19
+
+
+def test_layout_and_load_validation_without_gpu():
+    """bbs_set_probe_layout and bbs_set_load_factor check their ranges on the host."""
+    from paper_2310_10023_gb300 import native as nv
+    nv.load()
+    for bad in (-1, 5):
+        with pytest.raises(nv.BBSError) as e:
+            nv.bbs_set_probe_layout(bad)
+        assert e.value.code == nv.EINVAL
+    for bad in (0.0, 0.01, 0.95, float("nan")):
+        with pytest.raises(nv.BBSError) as e:
+            nv.bbs_set_load_factor(bad)
+        assert e.value.code == nv.EINVAL
+    for ok in (1, 2, 3, 4, 0):
+        nv.bbs_set_probe_layout(ok)
+    nv.bbs_set_load_factor(0.25)

@@ -312,7 +312,7 @@ def test_localize_many_empty_and_not_found(nv, room_pair):
 
 # ---- every bucket layout --------------------------------------------------------
 
-@pytest.mark.parametrize("layout", [0, 1, 2])
+@pytest.mark.parametrize("layout", [0, 1, 2, 3, 4])
 def test_layouts_agree_with_oracle(nv, layout):
     w = synth.WORKLOADS["room"]
     m = synth.make_map(w.scene)
@@ -322,8 +322,8 @@ def test_layouts_agree_with_oracle(nv, layout):
         dm = nv.bbs_build_maps(m, w.r, w.levels)
     finally:
         nv.bbs_set_probe_layout(0)
-    # the room's boxes are small: dense by default, compact when hashed, wide when forced
-    want = {0: nv.LAYOUT_DENSE, 1: nv.LAYOUT_WIDE, 2: nv.LAYOUT_COMPACT}[layout]
+    # the room's boxes are small: every layout applies
+    want = {0: nv.LAYOUT_BYTES, 1: nv.LAYOUT_WIDE, 2: nv.LAYOUT_COMPACT, 3: nv.LAYOUT_DENSE, 4: nv.LAYOUT_BYTES}[layout]
     assert [nv.bbs_maps_layout(dm, l) for l in range(w.levels)] == [want] * w.levels
     for l in range(w.levels):
         assert _keyset(nv.bbs_maps_keys(dm, l)) == _keyset(om.keys(l)), (layout, l)
