@@ -45,7 +45,7 @@ static_assert(sizeof(Brick) == 32, "brick must be one 32-byte sector");
 struct LevelView {
     const Brick* slots;
     uint32_t shift;   // home slot = hash >> shift   (table size 2^(32 - shift))
-    uint32_t mask;    // hashed: table size - 1; dense: index of the zero brick past the box
+    uint32_t mask;    // hashed: table size - 1; dense: index of the zero brick past the box; bytes: last cell
     int32_t maxp;     // longest probe distance of any stored brick
     int32_t layout;   // LAYOUT_WIDE, LAYOUT_COMPACT or LAYOUT_DENSE
     int32_t base[3];  // compact, dense: key origin (multiple of 4)
@@ -375,8 +375,9 @@ inline LevelView level_view(const bbs_maps* m, int l)
     LevelView v;
     v.slots = m->lv[l].slots;
     v.shift = (uint32_t)(32 - m->lv[l].log2T);
-    v.mask = m->lv[l].layout == LAYOUT_DENSE ? (uint32_t)(m->lv[l].n_slots - 1)
-                                             : (uint32_t)((1ull << m->lv[l].log2T) - 1ull);
+    v.mask = (m->lv[l].layout == LAYOUT_DENSE || m->lv[l].layout == LAYOUT_BYTES)
+                 ? (uint32_t)(m->lv[l].n_slots - 1)
+                 : (uint32_t)((1ull << m->lv[l].log2T) - 1ull);
     v.maxp = m->lv[l].maxp;
     v.layout = m->lv[l].layout;
     for (int i = 0; i < 3; ++i) {
@@ -413,8 +414,13 @@ DevGrid dev_grid(const HostGrid& g);
 void default_ranges(const bbs_maps* m, bbs_ranges* rg);
 
 // Per-call scan + grid state on the device.
+// Scan points staged per CTA by the scoring kernel; the scan's chunk boxes
+// are kept at this granularity.
+constexpr int SCAN_CHUNK = 2048;
+
 struct ScanState {
     float4* scan;      // K points, w = 0
+    float4* cbox;      // per SCAN_CHUNK-point chunk: (min x, y, z, 0), (max x, y, z, 0)
     int64_t k;
     double d_max;
     double norm_max;   // the scan's largest point norm

@@ -115,13 +115,27 @@ __device__ __forceinline__ void child_bits(const LevelView& L, uint32_t bx, uint
 // (children jz = 0, then jz = 1) spread to 4 byte counters by one multiply
 // (bit i of the nibble lands on bit 8 i; the other partial products fall on
 // distinct bits outside the mask, so no carry reaches a counter).
+__device__ __forceinline__ void bytes_count(uint32_t v, uint32_t& acc0, uint32_t& acc1)
+{
+    acc0 += ((v & 0xFu) * 0x204081u) & 0x01010101u;
+    acc1 += ((v >> 4) * 0x204081u) & 0x01010101u;
+}
 __device__ __forceinline__ void bytes_acc(const LevelView& L, uint32_t bx, uint32_t by, uint32_t bz, uint32_t ex,
                                           uint32_t ey, uint32_t ez, uint32_t& acc0, uint32_t& acc1)
 {
     const uint32_t rx = min(bx ^ KB, ex), ry = min(by ^ KB, ey), rz = min(bz ^ KB, ez);
-    const uint32_t v = __ldg(reinterpret_cast<const uint8_t*>(L.slots) + ((rx * L.nby + ry) * L.nbz + rz));
-    acc0 += ((v & 0xFu) * 0x204081u) & 0x01010101u;
-    acc1 += ((v >> 4) * 0x204081u) & 0x01010101u;
+    bytes_count(__ldg(reinterpret_cast<const uint8_t*>(L.slots) + ((rx * L.nby + ry) * L.nbz + rz)), acc0, acc1);
+}
+// The same for a run whose every point is known to land inside the grid (the
+// chunk-box test of the run): no per-axis clamp, and the -KB of the three
+// patterns folded into one constant, cfix = -KB (ny nz + nz + 1) mod 2^32 --
+// the index is exact because its true value is below 2^31.  One min against
+// the last cell (L.mask) keeps every load inside the grid whatever the test.
+__device__ __forceinline__ void bytes_acc_inside(const LevelView& L, uint32_t bx, uint32_t by, uint32_t bz,
+                                                 uint32_t cfix, uint32_t& acc0, uint32_t& acc1)
+{
+    const uint32_t idx = min((bx * L.nby + by) * L.nbz + bz + cfix, L.mask);
+    bytes_count(__ldg(reinterpret_cast<const uint8_t*>(L.slots) + idx), acc0, acc1);
 }
 
 // One run (a rotational child over blocks of the staged chunk), two points
@@ -131,12 +145,13 @@ __device__ __forceinline__ void bytes_acc(const LevelView& L, uint32_t bx, uint3
 // blockDim, ... below jhi.  q = (A_i0 x + A_i1 y) + A_i2 z is rounded to FP32
 // after every product and sum (no FMA), as the oracle; the floor, the level
 // shift and the key offset are one fma.rm of that q (see KB).
-template <int LAYOUT>
+template <int LAYOUT, bool INSIDE = false>
 __device__ __forceinline__ void score_run(const ulonglong2* sxy, const f2* sz, int n, int jlo, int jhi,
                                           const LevelView& L, const Row2& r0, const Row2& r1, const Row2& r2, f2 S,
                                           f2 Cx, f2 Cy, f2 Cz, uint32_t& acc0, uint32_t& acc1)
 {
     const uint32_t ex = L.rmax[0] + 1u, ey = L.rmax[1] + 1u, ez = L.rmax[2] + 1u;   // bytes: the empty key past the box
+    const uint32_t cfix = 0u - KB * (L.nby * L.nbz + L.nbz + 1u);
     auto pair = [&](int j) {
         const ulonglong2 xy = sxy[j];
         const f2 Z = sz[j];
@@ -144,6 +159,11 @@ __device__ __forceinline__ void score_run(const ulonglong2* sxy, const f2* sz, i
         up2(fma2rm(rot2(r0, xy.x, xy.y, Z), S, Cx), bx1, bx2);
         up2(fma2rm(rot2(r1, xy.x, xy.y, Z), S, Cy), by1, by2);
         up2(fma2rm(rot2(r2, xy.x, xy.y, Z), S, Cz), bz1, bz2);
+        if (LAYOUT == LAYOUT_BYTES && INSIDE) {
+            bytes_acc_inside(L, (uint32_t)bx1, (uint32_t)by1, (uint32_t)bz1, cfix, acc0, acc1);
+            if (2 * j + 1 < n) bytes_acc_inside(L, (uint32_t)bx2, (uint32_t)by2, (uint32_t)bz2, cfix, acc0, acc1);
+            return;
+        }
         if (LAYOUT == LAYOUT_BYTES) {
             bytes_acc(L, (uint32_t)bx1, (uint32_t)by1, (uint32_t)bz1, ex, ey, ez, acc0, acc1);
             if (2 * j + 1 < n) bytes_acc(L, (uint32_t)bx2, (uint32_t)by2, (uint32_t)bz2, ex, ey, ez, acc0, acc1);
@@ -200,6 +220,43 @@ __device__ __forceinline__ void virtual_parent(const SearchDev& S, int64_t vp, i
     px = S.pmin[0] + (int32_t)(vp / ((int64_t)S.pext[2] * S.pext[1]));
 }
 
+// Whether every point of run d lands inside its level's byte grid L.  The
+// key of axis i is floor(q_i / 2^m) + o_i (o_i = t_i - base_i, the run's key
+// offset) with q_i the FP32 value of sum_k A_ik x_k.  Over the chunk's box
+// the exact sum lies in [lo, hi] (per term the smaller and larger of the
+// corner products).  Here lo and hi are formed in FP32 (three products, two
+// sums: within 3u / (1 - 3u) of mag = sum_k |A_ik| max |x_k|, u = 2^-24), and
+// each point's FP32 q_i lies within as much again of its exact value, so
+// widening by 2e-6 mag (which also covers the rounding of mag and of the
+// widening) bounds every q_i.  Inside: every key in [0, rmax_i + 1].  A
+// clamped offset (|o| = 2^21) never passes.  FP32 throughout: FP64 runs at a
+// small fraction of the FP32 rate on this part.
+template <typename RD>
+__device__ __forceinline__ bool run_inside(const RD& d, const float4* __restrict__ box, const LevelView& L)
+{
+    const float4 blo = __ldg(box), bhi = __ldg(box + 1);
+    const float lo3[3] = {blo.x, blo.y, blo.z}, hi3[3] = {bhi.x, bhi.y, bhi.z};
+    const float s = __int_as_float((127 - d.m) << 23);   // 2^-m
+    bool in = true;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float qlo = 0.0f, qhi = 0.0f, mag = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float a = __int_as_float((int)(uint32_t)d.a[3 * i + k]);
+            const float p1 = __fmul_rn(a, lo3[k]), p2 = __fmul_rn(a, hi3[k]);
+            qlo = __fadd_rn(qlo, fminf(p1, p2));
+            qhi = __fadd_rn(qhi, fmaxf(p1, p2));
+            mag = __fadd_rn(mag, __fmul_rn(fabsf(a), fmaxf(fabsf(lo3[k]), fabsf(hi3[k]))));
+        }
+        const float marg = __fadd_rn(__fmul_rn(2e-6f, mag), 1e-30f);
+        const float o = __int_as_float((int)(uint32_t)d.kc[i]) - 12582912.0f;
+        in = in && floorf(__fmul_rn(__fsub_rn(qlo, marg), s)) + o >= 0.0f &&
+             floorf(__fmul_rn(__fadd_rn(qhi, marg), s)) + o <= (float)L.rmax[i] + 1.0f;
+    }
+    return in;
+}
+
 // A run: one task over blocks [b0, b1) of point chunk c, described in shared
 // memory for the whole CTA.
 struct __align__(16) RunDesc {
@@ -210,6 +267,7 @@ struct __align__(16) RunDesc {
     int32_t c;        // point chunk
     int32_t b0, b1;   // PBLK-point blocks [b0, b1) of the chunk
     int32_t sid;      // search
+    int32_t inside;   // every point of the run lands inside the level's byte grid
     int64_t task;     // launch-local task index
 };
 
@@ -345,6 +403,12 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
             d.b1 = (int32_t)(min(rs + nbc, xe) - rs);
             d.task = g->first_task + u;
         }
+        if (tid < nrun) {   // the byte grid's inside test, from the descriptor just written
+            RunDesc& d = rd[tid];
+            const SearchDev& S = Sall[d.sid];
+            const LevelView& L = S.maps[d.m];
+            d.inside = L.layout == LAYOUT_BYTES ? (int32_t)run_inside(d, S.cbox + 2 * d.c, L) : 0;
+        }
         if (tid == 0) {
             s_nrun = nrun;
             s_next = g->first_slice + xe;
@@ -379,7 +443,10 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
             const int n = min(PCHUNK, S.K - d.c * PCHUNK);
             const int jlo = d.b0 * (PBLK / 2), jhi = min(d.b1 * (PBLK / 2), (n + 1) >> 1);
             uint32_t acc0 = 0, acc1 = 0;   // bytes: children (0,4,2,6) and (1,5,3,7)
-            if (Lv.layout == LAYOUT_BYTES)
+            if (Lv.layout == LAYOUT_BYTES && d.inside)
+                score_run<LAYOUT_BYTES, true>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2],
+                                              acc0, acc1);
+            else if (Lv.layout == LAYOUT_BYTES)
                 score_run<LAYOUT_BYTES>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], acc0,
                                         acc1);
             else if (Lv.layout == LAYOUT_DENSE)

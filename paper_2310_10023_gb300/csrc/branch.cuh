@@ -10,6 +10,7 @@ namespace bbs {
 
 constexpr int CH = 256;        // nodes per frontier chunk
 constexpr int PCHUNK = 2048;   // scan points staged in shared memory per CTA
+static_assert(PCHUNK == SCAN_CHUNK, "chunk boxes are kept per staged chunk");
 constexpr int PBLK = 512;      // scan points per slice (one point pair per thread of a 256-thread CTA)
 constexpr int MAXSEG = 256;    // task runs per scoring launch
 constexpr int64_t TASK_CAP = (int64_t)1 << 19;   // rotational-child tasks per scoring launch
@@ -54,6 +55,7 @@ struct Ctl {
 // One search slot (device).  Bucket arrays have K + 1 entries (scores 0..K).
 struct SearchDev {
     const float4* scan;
+    const float4* cbox;         // per PCHUNK-point chunk of the scan: min, max corner
     const float4* rot;          // rows of the top level's rotations
     const double2* cs;          // (cos, sin) of every segment angle
     int32_t K;

@@ -318,6 +318,7 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
     SearchDev sd;
     std::memset(&sd, 0, sizeof(sd));
     sd.scan = S.scan;
+    sd.cbox = S.cbox;
     sd.rot = S.rot;
     sd.cs = S.cs;
     sd.K = (int32_t)k;

@@ -716,6 +716,7 @@ int Engine::add(const bbs_maps* m, const float* xyz, int64_t k, int is_device, c
     SearchDev& d = h.dev;
     std::memset(&d, 0, sizeof(d));
     d.scan = h.scan.scan;
+    d.cbox = h.scan.cbox;
     d.rot = h.scan.rot;
     d.cs = h.scan.cs;
     d.K = (int32_t)k;

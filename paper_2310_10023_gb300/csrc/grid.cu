@@ -150,12 +150,21 @@ void default_ranges(const bbs_maps* m, bbs_ranges* rg)
 // scan upload: K x 3 float -> K float4; d_max and validation in FP64
 // ---------------------------------------------------------------------------
 
-__global__ void scan_pack_kernel(const float* __restrict__ xyz, int64_t k, float4* __restrict__ out, double bound,
-                                 unsigned long long* __restrict__ dmax_bits, int* __restrict__ bad)
+// One CTA per chunk of SCAN_CHUNK points: pack xyz into float4, check the
+// coordinate bound, track the largest norm, and write the chunk's box (the
+// scoring kernel tests a run against it to drop the per-point range checks).
+__global__ void __launch_bounds__(256) scan_pack_kernel(const float* __restrict__ xyz, int64_t k,
+                                                        float4* __restrict__ out, float4* __restrict__ cbox,
+                                                        double bound, unsigned long long* __restrict__ dmax_bits,
+                                                        int* __restrict__ bad)
 {
+    __shared__ float red[6][8];
+    const int64_t c = blockIdx.x;
+    const int64_t e = min(k, (c + 1) * SCAN_CHUNK);
     double m = 0.0;
     int b = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
+    float v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = c * SCAN_CHUNK + threadIdx.x; i < e; i += blockDim.x) {
         const float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
         out[i] = make_float4(x, y, z, 0.0f);
         const double dx = x, dy = y, dz = z;
@@ -163,16 +172,35 @@ __global__ void scan_pack_kernel(const float* __restrict__ xyz, int64_t k, float
         // sqrt((x^2 + y^2) + z^2) with each operation rounded on its own
         const double d = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
         if (d > m) m = d;
+        v[0] = fminf(v[0], x), v[1] = fminf(v[1], y), v[2] = fminf(v[2], z);
+        v[3] = fmaxf(v[3], x), v[4] = fmaxf(v[4], y), v[5] = fmaxf(v[5], z);
     }
     // non-negative doubles order like their bit patterns
     for (int o = 16; o > 0; o >>= 1) {
         const double t = __shfl_down_sync(0xffffffffu, m, o);
         m = t > m ? t : m;
         b |= __shfl_down_sync(0xffffffffu, b, o);
+        for (int a = 0; a < 6; ++a) {
+            const float t2 = __shfl_xor_sync(0xffffffffu, v[a], o);
+            v[a] = a < 3 ? fminf(v[a], t2) : fmaxf(v[a], t2);
+        }
     }
-    if ((threadIdx.x & 31) == 0) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
         if (b) atomicOr(bad, 1);
         atomicMax(dmax_bits, (unsigned long long)__double_as_longlong(m));
+        for (int a = 0; a < 6; ++a) red[a][w] = v[a];
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        float* dst = reinterpret_cast<float*>(cbox + 2 * c);
+        const int a = threadIdx.x - (threadIdx.x >= 4);   // slots 0-2 min, 4-6 max, 3 and 7 zero
+        float r = 0.0f;
+        if (threadIdx.x != 3 && threadIdx.x != 7) {
+            r = red[a][0];
+            for (int j = 1; j < (int)(blockDim.x >> 5); ++j) r = a < 3 ? fminf(r, red[a][j]) : fmaxf(r, red[a][j]);
+        }
+        dst[threadIdx.x] = r;
     }
 }
 
@@ -208,6 +236,8 @@ int scan_prepare(const bbs_maps* m, const float* xyz, int64_t k, int is_device, 
     out->k = k;
     const int64_t kk = k > 0 ? k : 1;
     BBS_CUDA_TRY(cudaMallocAsync((void**)&out->scan, sizeof(float4) * (size_t)kk, st));
+    BBS_CUDA_TRY(cudaMallocAsync((void**)&out->cbox, sizeof(float4) * 2 * (size_t)((kk + SCAN_CHUNK - 1) / SCAN_CHUNK), st));
+    if (k == 0) BBS_CUDA_TRY(cudaMemsetAsync(out->cbox, 0, sizeof(float4) * 2, st));
     struct Aux { unsigned long long dmax; int bad; int pad; };
     Aux* d_aux = nullptr;
     float* d_xyz = nullptr;
@@ -222,7 +252,8 @@ int scan_prepare(const bbs_maps* m, const float* xyz, int64_t k, int is_device, 
     }
     const double bound = std::ldexp((double)m->r, 18);
     if (k > 0) {
-        scan_pack_kernel<<<grid_blocks(k, 256), 256, 0, st>>>(src, k, out->scan, bound, &d_aux->dmax, &d_aux->bad);
+        scan_pack_kernel<<<(unsigned)((k + SCAN_CHUNK - 1) / SCAN_CHUNK), 256, 0, st>>>(src, k, out->scan, out->cbox,
+                                                                                    bound, &d_aux->dmax, &d_aux->bad);
         BBS_CUDA_TRY(cudaGetLastError());
     }
     Aux aux;
@@ -306,6 +337,8 @@ void scan_release(ScanState* s, cudaStream_t st)
     if (s->scan) cudaFreeAsync(s->scan, st);
     if (s->rot) cudaFreeAsync(s->rot, st);
     if (s->cs) cudaFreeAsync(s->cs, st);
+    if (s->cbox) cudaFreeAsync(s->cbox, st);
+    s->cbox = nullptr;
     s->scan = nullptr;
     s->rot = nullptr;
     s->cs = nullptr;

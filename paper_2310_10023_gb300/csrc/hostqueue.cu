@@ -109,6 +109,7 @@ int hostqueue_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device,
     SearchDev sd;
     std::memset(&sd, 0, sizeof(sd));
     sd.scan = S.scan;
+    sd.cbox = S.cbox;
     sd.rot = S.rot;
     sd.cs = S.cs;
     sd.K = (int32_t)k;
