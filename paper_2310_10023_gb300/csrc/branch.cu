@@ -293,6 +293,9 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
     __shared__ uint32_t red[NRUN][4];
     // the CTA's walk, kept in shared memory (uniform; frees registers for the runs)
     __shared__ int64_t s_cur, s_end, s_next;
+    // the staged chunk is (s_staged_sid, s_staged_c) between rounds; within a
+    // round, run 0's chunk is staged before the runs and run r's chunk after
+    // run r - 1 (the tag is written only at the round's end)
     __shared__ int32_t s_gi, s_nrun, s_staged_sid, s_staged_c;
     const int tid = threadIdx.x, lane = tid & 31;
     const int64_t n_slices = P->n_slices;
@@ -354,6 +357,23 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
         const int64_t v0 = tc_of(x0), vh = tc_of(xh - 1);
         const int nrun = (int)(vh - v0 + 1 < NRUN ? vh - v0 + 1 : NRUN);
         const int64_t xe = v0 + nrun <= vh ? tc_first(v0 + nrun) : xh;   // this round ends at slice xe
+        // the round's first chunk is staged by every thread while the descriptors
+        // are formed (the top barrier ended the previous chunk's readers)
+        {
+            const int32_t c0 = (int32_t)(v0 / nt);
+            if (g->sid != s_staged_sid || c0 != s_staged_c) {   // uniform
+                const SearchDev& S0 = Sall[g->sid];
+                const int32_t k0 = c0 * PCHUNK;
+                const int32_t n0 = min(PCHUNK, S0.K - k0);
+                for (int i = tid; i < n0; i += blockDim.x) {
+                    const float4 p = __ldg(S0.scan + k0 + i);
+                    const int j = i >> 1, h = i & 1;
+                    fxy[4 * j + h] = p.x;
+                    fxy[4 * j + 2 + h] = p.y;
+                    fz[2 * j + h] = p.z;
+                }
+            }
+        }
         if (tid < nrun) {
             const SearchDev& S = Sall[g->sid];
             const int64_t v = v0 + tid;
@@ -402,12 +422,7 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
             d.b0 = (int32_t)(max(rs, x0) - rs);
             d.b1 = (int32_t)(min(rs + nbc, xe) - rs);
             d.task = g->first_task + u;
-        }
-        if (tid < nrun) {   // the byte grid's inside test, from the descriptor just written
-            RunDesc& d = rd[tid];
-            const SearchDev& S = Sall[d.sid];
-            const LevelView& L = S.maps[d.m];
-            d.inside = L.layout == LAYOUT_BYTES ? (int32_t)run_inside(d, S.cbox + 2 * d.c, L) : 0;
+            d.inside = L.layout == LAYOUT_BYTES ? (int32_t)run_inside(d, S.cbox + 2 * c, L) : 0;
         }
         if (tid == 0) {
             s_nrun = nrun;
@@ -418,7 +433,7 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
         for (int r = 0; r < s_nrun; ++r) {
             const RunDesc& d = rd[r];
             const SearchDev& S = Sall[d.sid];
-            if (d.sid != s_staged_sid || d.c != s_staged_c) {   // uniform
+            if (r > 0 && (d.sid != rd[r - 1].sid || d.c != rd[r - 1].c)) {   // uniform
                 __syncthreads();   // the previous chunk's readers are done
                 const int32_t k0 = d.c * PCHUNK;
                 const int32_t n = min(PCHUNK, S.K - k0);
@@ -429,12 +444,7 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
                     fxy[4 * j + 2 + h] = p.y;
                     fz[2 * j + h] = p.z;
                 }
-                __syncthreads();   // every thread has compared against the old chunk
-                if (tid == 0) {
-                    s_staged_sid = d.sid;
-                    s_staged_c = d.c;
-                }
-                __syncthreads();   // staged points and the new chunk tag visible
+                __syncthreads();   // staged points visible
             }
             const LevelView Lv = S.maps[d.m];
             const Row2 r0{d.a[0], d.a[1], d.a[2]};
@@ -483,7 +493,11 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
             if (sum & 0xFFFFu) atomicAdd(dd, (int32_t)(sum & 0xFFFFu));
             if (sum >> 16) atomicAdd(dd + 2, (int32_t)(sum >> 16));
         }
-        if (tid == 0) s_cur = s_next;
+        if (tid == 0) {
+            s_cur = s_next;
+            s_staged_sid = rd[s_nrun - 1].sid;
+            s_staged_c = rd[s_nrun - 1].c;
+        }
     }
 }
 

@@ -151,57 +151,77 @@ void default_ranges(const bbs_maps* m, bbs_ranges* rg)
 // ---------------------------------------------------------------------------
 
 // One CTA per chunk of SCAN_CHUNK points: pack xyz into float4, check the
-// coordinate bound, track the largest norm, and write the chunk's box (the
-// scoring kernel tests a run against it to drop the per-point range checks).
-__global__ void __launch_bounds__(256) scan_pack_kernel(const float* __restrict__ xyz, int64_t k,
-                                                        float4* __restrict__ out, float4* __restrict__ cbox,
-                                                        double bound, unsigned long long* __restrict__ dmax_bits,
-                                                        int* __restrict__ bad)
+// coordinate bound, write the chunk's box (the scoring kernel tests a run
+// against it to drop the per-point range checks), and raise smax_bits to the
+// chunk's largest s = (x^2 + y^2) + z^2 in FP64, each operation rounded on
+// its own (the norm is sqrt of the maximum: sqrt rounds monotonically).
+// FP64 is slow on this part, so s is formed in FP64 only for the points
+// whose FP32 estimate lies within 1e-6 of the chunk's largest estimate (the
+// two differ by under 4e-7 relative, so the FP64 maximum is among them).
+constexpr int PACK_THREADS = 256;
+constexpr int PACK_PER = SCAN_CHUNK / PACK_THREADS;
+__global__ void __launch_bounds__(PACK_THREADS) scan_pack_kernel(const float* __restrict__ xyz, int64_t k,
+                                                                 float4* __restrict__ out, float4* __restrict__ cbox,
+                                                                 float bound, unsigned long long* __restrict__ smax_bits,
+                                                                 int* __restrict__ bad)
 {
-    __shared__ float red[6][8];
-    const int64_t c = blockIdx.x;
-    const int64_t e = min(k, (c + 1) * SCAN_CHUNK);
-    double m = 0.0;
+    __shared__ float red[7][PACK_THREADS / 32];
+    const int64_t c0 = (int64_t)blockIdx.x * SCAN_CHUNK;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int b = 0;
-    float v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
-    for (int64_t i = c * SCAN_CHUNK + threadIdx.x; i < e; i += blockDim.x) {
-        const float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
-        out[i] = make_float4(x, y, z, 0.0f);
-        const double dx = x, dy = y, dz = z;
-        if (!(fabs(dx) <= bound && fabs(dy) <= bound && fabs(dz) <= bound)) b = 1;   // also catches NaN
-        // sqrt((x^2 + y^2) + z^2) with each operation rounded on its own
-        const double d = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
-        if (d > m) m = d;
-        v[0] = fminf(v[0], x), v[1] = fminf(v[1], y), v[2] = fminf(v[2], z);
-        v[3] = fmaxf(v[3], x), v[4] = fmaxf(v[4], y), v[5] = fmaxf(v[5], z);
-    }
-    // non-negative doubles order like their bit patterns
-    for (int o = 16; o > 0; o >>= 1) {
-        const double t = __shfl_down_sync(0xffffffffu, m, o);
-        m = t > m ? t : m;
-        b |= __shfl_down_sync(0xffffffffu, b, o);
-        for (int a = 0; a < 6; ++a) {
-            const float t2 = __shfl_xor_sync(0xffffffffu, v[a], o);
-            v[a] = a < 3 ? fminf(v[a], t2) : fmaxf(v[a], t2);
+    float v[7] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0f};   // box, largest s
+    float px[PACK_PER], py[PACK_PER], pz[PACK_PER], ps[PACK_PER];
+#pragma unroll
+    for (int j = 0; j < PACK_PER; ++j) {
+        const int64_t i = c0 + threadIdx.x + (int64_t)j * PACK_THREADS;
+        ps[j] = -1.0f;
+        if (i < k) {
+            const float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+            out[i] = make_float4(x, y, z, 0.0f);
+            if (!(fabsf(x) <= bound && fabsf(y) <= bound && fabsf(z) <= bound)) b = 1;   // also catches NaN
+            px[j] = x, py[j] = y, pz[j] = z;
+            ps[j] = __fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z));
+            v[0] = fminf(v[0], x), v[1] = fminf(v[1], y), v[2] = fminf(v[2], z);
+            v[3] = fmaxf(v[3], x), v[4] = fmaxf(v[4], y), v[5] = fmaxf(v[5], z);
+            v[6] = fmaxf(v[6], ps[j]);
         }
     }
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int o = 16; o > 0; o >>= 1) {
+        b |= __shfl_xor_sync(0xffffffffu, b, o);
+        for (int a = 0; a < 7; ++a) {
+            const float t = __shfl_xor_sync(0xffffffffu, v[a], o);
+            v[a] = a < 3 ? fminf(v[a], t) : fmaxf(v[a], t);
+        }
+    }
     if (lane == 0) {
         if (b) atomicOr(bad, 1);
-        atomicMax(dmax_bits, (unsigned long long)__double_as_longlong(m));
-        for (int a = 0; a < 6; ++a) red[a][w] = v[a];
+        for (int a = 0; a < 7; ++a) red[a][w] = v[a];
     }
     __syncthreads();
-    if (threadIdx.x < 8) {
-        float* dst = reinterpret_cast<float*>(cbox + 2 * c);
-        const int a = threadIdx.x - (threadIdx.x >= 4);   // slots 0-2 min, 4-6 max, 3 and 7 zero
-        float r = 0.0f;
-        if (threadIdx.x != 3 && threadIdx.x != 7) {
-            r = red[a][0];
-            for (int j = 1; j < (int)(blockDim.x >> 5); ++j) r = a < 3 ? fminf(r, red[a][j]) : fmaxf(r, red[a][j]);
-        }
-        dst[threadIdx.x] = r;
+    float r[7];
+    for (int a = 0; a < 7; ++a) {
+        r[a] = red[a][0];
+        for (int j = 1; j < PACK_THREADS / 32; ++j) r[a] = a < 3 ? fminf(r[a], red[a][j]) : fmaxf(r[a], red[a][j]);
     }
+    if (threadIdx.x == 0) {
+        cbox[2 * blockIdx.x] = make_float4(r[0], r[1], r[2], 0.0f);
+        cbox[2 * blockIdx.x + 1] = make_float4(r[3], r[4], r[5], 0.0f);
+    }
+    const float thr = __fmul_rn(r[6], 0.999999f);
+    double m = 0.0;
+#pragma unroll
+    for (int j = 0; j < PACK_PER; ++j)
+        if (ps[j] >= thr && ps[j] >= 0.0f) {
+            const double dx = px[j], dy = py[j], dz = pz[j];
+            const double sd = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+            m = sd > m ? sd : m;
+        }
+    // non-negative doubles order like their bit patterns
+    for (int o = 16; o > 0; o >>= 1) {
+        const double t = __shfl_xor_sync(0xffffffffu, m, o);
+        m = t > m ? t : m;
+    }
+    if (lane == 0 && m > 0.0) atomicMax(smax_bits, (unsigned long long)__double_as_longlong(m));
 }
 
 // the rows of every rotation of one level (rotation_rows)
@@ -251,9 +271,11 @@ int scan_prepare(const bbs_maps* m, const float* xyz, int64_t k, int is_device, 
         src = d_xyz;
     }
     const double bound = std::ldexp((double)m->r, 18);
+    float bound_f = (float)bound;   // the largest float <= bound: |x| <= bound_f iff |x| <= bound
+    if ((double)bound_f > bound) bound_f = std::nextafter(bound_f, 0.0f);
     if (k > 0) {
         scan_pack_kernel<<<(unsigned)((k + SCAN_CHUNK - 1) / SCAN_CHUNK), 256, 0, st>>>(src, k, out->scan, out->cbox,
-                                                                                    bound, &d_aux->dmax, &d_aux->bad);
+                                                                                    bound_f, &d_aux->dmax, &d_aux->bad);
         BBS_CUDA_TRY(cudaGetLastError());
     }
     Aux aux;
@@ -266,8 +288,9 @@ int scan_prepare(const bbs_maps* m, const float* xyz, int64_t k, int is_device, 
         scan_release(out, st);
         return set_error(BBS_EINVAL, "scan: a coordinate is not finite or exceeds 2^18 r");
     }
-    double dm;
-    std::memcpy(&dm, &aux.dmax, sizeof(dm));
+    double smax;
+    std::memcpy(&smax, &aux.dmax, sizeof(smax));
+    const double dm = std::sqrt(smax);   // correctly rounded, as the per-point sqrt
     out->norm_max = dm;
     out->d_max = (opts && opts->d_max > 0.0) ? opts->d_max : dm;
     const uint32_t flags = opts ? opts->flags : 0u;
