@@ -30,6 +30,7 @@ _lib = None
 OK, NOT_FOUND, EINVAL, ENOMEM, EKEYRANGE = 0, 1, -1, -2, -5
 TRANSLATION_ONLY, LEAF_UNDILATED, PRUNE_GE, ANGLE_LOWER_EDGE, CHILD_LITERAL = 0x1, 0x2, 0x4, 0x8, 0x10
 EXACT_BOUND = 0x20
+SEARCH_DFS = 0x40          # depth-first batched order (localize only)
 
 
 def exact_flags(e: int) -> int:

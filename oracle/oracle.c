@@ -645,6 +645,98 @@ static void fr_clear(frontier* f)
  *
  * Only popping a leaf changes best, so the order in which a batch's children
  * are scored and inserted cannot change the outcome. */
+/* Depth-first batched iteration (Table I's DFS search strategy; the paper
+ * gives no batched form of it, so this reading fixes one): F is kept per
+ * level, and nodes are taken deepest level first and, within a level,
+ * highest score first, in whole (level, score) buckets.
+ *
+ *   best = ceil(theta K) - 1, match unset, F = { c in C_lmax : score(c) > best }
+ *   repeat:
+ *     if F holds leaves: s = their highest score (> best), best = s,
+ *       match = lexmin leaf of score s; drop every node of F with score <= best
+ *       (every leaf among them)
+ *     P = {}
+ *     for l = 1 .. l_max, and within l for s from the highest score down,
+ *       while children(P) < b: P = P + the nodes of F at (l, s) (removed)
+ *     if P is empty: done
+ *     score every child of P (Eq. 13); keep those with score > best in F
+ *
+ * best changes only at the start of an iteration, so the order in which a
+ * batch's children are scored and inserted cannot change the outcome.  Every
+ * node kept scores above best, so with an exact bound the result's score is
+ * the exhaustive optimum, as for the best-first order; the match may differ
+ * among equal scores. */
+static int dfs_search(const orc_maps* m, const orc_grid* g, const float* scan, int64_t k, int64_t batch,
+                      int64_t max_frontier, frontier* FL, int32_t* best_io, int32_t match[7], int* found,
+                      orc_result* res)
+{
+    const int L = g->levels;
+    int32_t best = *best_io;
+    nodevec P = {0}, kids = {0};
+    int rc = ORC_OK;
+    for (;;) {
+        int64_t size = 0;
+        for (int l = 0; l < L; ++l) size += FL[l].size;
+        if (size > res->peak_frontier) res->peak_frontier = size;
+        if (max_frontier > 0 && size > max_frontier) { rc = ORC_ENOMEM; break; }
+        /* leaves first: the best of them sets best and the match */
+        if (FL[0].size > 0) {
+            while (FL[0].top >= 0 && FL[0].b[FL[0].top].n == 0) FL[0].top--;
+            const int32_t s = (int32_t)FL[0].top;
+            const nodevec* B = &FL[0].b[s];
+            int32_t lm[7];
+            for (int64_t i = 0; i < B->n; ++i)
+                if (i == 0 || lex_less(B->v[i].c, lm)) memcpy(lm, B->v[i].c, sizeof(lm));
+            best = s;
+            memcpy(match, lm, sizeof(lm));
+            *found = 1;
+            for (int l = 0; l < L; ++l)
+                for (int64_t t = 0; t <= best && t <= FL[l].K; ++t) {
+                    FL[l].size -= FL[l].b[t].n;
+                    FL[l].b[t].n = 0;
+                }
+        }
+        /* parents: deepest level first, highest score first */
+        P.n = 0;
+        int64_t nchild = 0;
+        for (int l = 1; l < L && nchild < batch && !rc; ++l) {
+            frontier* F = &FL[l];
+            for (int64_t s = F->top; s > best && nchild < batch && !rc; --s) {
+                nodevec* B = &F->b[s];
+                if (B->n == 0) continue;
+                for (int64_t i = 0; i < B->n && !rc; ++i) {
+                    rc = vec_push(&P, B->v[i].c);
+                    nchild += orc_num_children(g, B->v[i].c);
+                }
+                F->size -= B->n;
+                B->n = 0;
+            }
+        }
+        if (rc || P.n == 0) break;
+        res->iterations++;
+        res->parents_branched += P.n;
+        for (int64_t i = 0; i < P.n && !rc; ++i) {
+            int64_t nk = orc_num_children(g, P.v[i].c);
+            if (kids.cap < nk) {
+                node7* nv = (node7*)realloc(kids.v, sizeof(node7) * (size_t)nk);
+                if (!nv) { rc = ORC_ENOMEM; break; }
+                kids.v = nv;
+                kids.cap = nk;
+            }
+            orc_children(g, P.v[i].c, &kids.v[0].c[0], nk);
+            for (int64_t j = 0; j < nk && !rc; ++j) {
+                int32_t s = orc_score(m, g, scan, k, kids.v[j].c);
+                res->nodes_scored++;
+                if (s > best) rc = fr_push(&FL[kids.v[j].c[6]], s, kids.v[j].c);
+            }
+        }
+    }
+    free(P.v);
+    free(kids.v);
+    *best_io = best;
+    return rc;
+}
+
 int orc_localize(const orc_maps* m, const float* scan, int64_t k, const orc_ranges* rg,
                  double score_frac, int64_t batch, double d_max, uint32_t flags,
                  int64_t max_frontier, orc_result* res)
@@ -672,12 +764,21 @@ int orc_localize(const orc_maps* m, const float* scan, int64_t k, const orc_rang
     int32_t match[7] = {0};
     int found = 0;
 
-    frontier F;
-    F.K = k;
-    F.size = 0;
-    F.top = -1;
-    F.b = (nodevec*)calloc((size_t)k + 1, sizeof(nodevec));
-    if (!F.b) return res->status = ORC_ENOMEM;
+    const int dfs = (flags & ORC_SEARCH_DFS) != 0;
+    const int nfr = dfs ? m->levels : 1;   /* depth-first: one frontier per level */
+    frontier* FL = (frontier*)calloc((size_t)nfr, sizeof(frontier));
+    if (!FL) return res->status = ORC_ENOMEM;
+    for (int l = 0; l < nfr; ++l) {
+        FL[l].K = k;
+        FL[l].top = -1;
+        FL[l].b = (nodevec*)calloc((size_t)k + 1, sizeof(nodevec));
+        if (!FL[l].b) {
+            for (int j = 0; j < l; ++j) free(FL[j].b);
+            free(FL);
+            return res->status = ORC_ENOMEM;
+        }
+    }
+    frontier F = FL[0];   /* best-first: the one frontier */
     nodevec P = {0}, kids = {0};
 
     /* initial set C_lmax (Sec. III-D): all translations of Eq. (3)-(5) times
@@ -694,11 +795,12 @@ int orc_localize(const orc_maps* m, const float* scan, int64_t k, const orc_rang
                             c[3] = (int32_t)ia; c[4] = (int32_t)ib; c[5] = (int32_t)ig;
                             int32_t s = orc_score(m, &g, scan, k, c);
                             res->nodes_scored++;
-                            if (s > best) rc = fr_push(&F, s, c);
+                            if (s > best) rc = fr_push(dfs ? &FL[lmax] : &F, s, c);
                         }
     if (F.size > res->peak_frontier) res->peak_frontier = F.size;
 
-    while (!rc) {
+    if (dfs && !rc) rc = dfs_search(m, &g, scan, k, batch, max_frontier, FL, &best, match, &found, res);
+    while (!rc && !dfs) {
         if (max_frontier > 0 && F.size > max_frontier) { rc = ORC_ENOMEM; break; }
         P.n = 0;
         int64_t nchild = 0;
@@ -749,8 +851,12 @@ int orc_localize(const orc_maps* m, const float* scan, int64_t k, const orc_rang
         if (F.size > res->peak_frontier) res->peak_frontier = F.size;
     }
 
-    for (int64_t s = 0; s <= k; ++s) free(F.b[s].v);
-    free(F.b);
+    if (!dfs) FL[0] = F;
+    for (int l = 0; l < nfr; ++l) {
+        for (int64_t s = 0; s <= k; ++s) free(FL[l].b[s].v);
+        free(FL[l].b);
+    }
+    free(FL);
     free(P.v);
     free(kids.v);
     res->probes = res->nodes_scored * k;

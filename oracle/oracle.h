@@ -40,6 +40,9 @@ extern "C" {
  * e in 1..15 in bits 12..15, so that a node's score bounds every leaf below
  * it under rotation as well (see orc_exact_dilation) */
 #define ORC_EXACT_BOUND        0x20u
+/* depth-first batched order (Table I's DFS strategy): deepest level first,
+ * then highest score (orc_localize only) */
+#define ORC_SEARCH_DFS         0x40u
 #define ORC_EXACT_E(flags)     ((int)(((flags) >> 12) & 15u))
 
 #define ORC_MAX_LEVELS 16
