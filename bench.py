@@ -268,23 +268,30 @@ def run_exact(nv, torch, stream, n_scans=4):
 
 def run_host_queue(nv, torch, maps, w, scans_d, stream):
     """The same searches with the frontier on the host (Algorithm 2's own
-    layout: host buckets, per-batch copies) vs the device-resident engine."""
+    layout: host buckets, per-batch copies) vs the device-resident engine,
+    and the depth-first order (Table I's DFS strategy) on the host queue."""
     a = nv.workload_args(w, stream=stream.cuda_stream)
+    d = nv.workload_args(w, stream=stream.cuda_stream, flags=nv.SEARCH_DFS)
     out = {}
-    for name, fn in (("device_frontier", nv.bbs_localize), ("host_frontier", nv.bbs_localize_hostqueue)):
-        fn(maps, scans_d[0], a.ranges, a.opts)
+    for name, fn, ar in (("device_frontier", nv.bbs_localize, a), ("host_frontier", nv.bbs_localize_hostqueue, a),
+                         ("host_frontier_dfs", nv.bbs_localize_hostqueue, d)):
+        fn(maps, scans_d[0], ar.ranges, ar.opts)
         torch.cuda.synchronize()
         t = time.perf_counter()
-        res = [fn(maps, s_, a.ranges, a.opts) for s_ in scans_d]
+        res = [fn(maps, s_, ar.ranges, ar.opts) for s_ in scans_d]
         torch.cuda.synchronize()
         ms = (time.perf_counter() - t) * 1e3
         out[name] = {"ms_per_scan": ms / len(scans_d), "probes_per_s": sum(r.probes for r in res) / (ms / 1e3),
+                     "iterations_mean": statistics.mean(r.iterations for r in res),
+                     "nodes_scored_mean": statistics.mean(r.nodes_scored for r in res),
                      "h2d_bytes_per_scan": statistics.mean(r.h2d_bytes for r in res),
                      "d2h_bytes_per_scan": statistics.mean(r.d2h_bytes for r in res), "keys": [
                          (r.best_score, tuple(r.node), r.nodes_scored) for r in res]}
-    same = sum(x == y for x, y in zip(out["device_frontier"].pop("keys"), out["host_frontier"].pop("keys")))
-    out["results_equal"] = f"{same}/{len(scans_d)}"
+    dev, host, dfs = (out[k].pop("keys") for k in ("device_frontier", "host_frontier", "host_frontier_dfs"))
+    out["results_equal"] = f"{sum(x == y for x, y in zip(dev, host))}/{len(scans_d)}"
+    out["dfs_same_best_score"] = f"{sum(x[0] == y[0] for x, y in zip(dev, dfs))}/{len(scans_d)}"
     out["speedup_device_vs_host"] = out["host_frontier"]["ms_per_scan"] / out["device_frontier"]["ms_per_scan"]
+    out["dfs_vs_bfs_nodes"] = out["host_frontier_dfs"]["nodes_scored_mean"] / out["host_frontier"]["nodes_scored_mean"]
     return out
 
 

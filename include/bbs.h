@@ -79,6 +79,15 @@ extern "C" {
  * or the BBS_CHILD_LITERAL reading, under which no e bounds the children */
 #define BBS_EXACT_BOUND       0x20u
 #define BBS_EXACT_BOUND_E(e)  (BBS_EXACT_BOUND | ((uint32_t)(e) << 12))
+/* depth-first batched order (Table I's DFS search strategy), for
+ * bbs_localize_hostqueue: the frontier is kept per level and taken deepest
+ * level first, then highest score, in whole (level, score) buckets until the
+ * popped parents have b children; the best leaf found at the start of a round
+ * sets best and the match (lexmin among its score) and every node at or below
+ * best goes.  With an exact bound the score equals the best-first one; the
+ * match may differ among equal scores.  bbs_localize and the server refuse it
+ * (BBS_EINVAL). */
+#define BBS_SEARCH_DFS        0x40u
 /* time every launch of the scoring kernel with CUDA events on the call's
  * stream (bbs_result.score_ms); off by default */
 #define BBS_TIME_KERNELS      0x100u
@@ -316,7 +325,8 @@ int  bbs_localize(const bbs_maps* maps, const float* scan_xyz, int64_t k, int is
  * rotational children are copied to the GPU, scored by the same kernels, and
  * their children's scores copied back for the host to keep those above best.
  * Same canonical iteration, so the same results as bbs_localize; it measures
- * what keeping the frontier on the device buys. */
+ * what keeping the frontier on the device buys.  With BBS_SEARCH_DFS in
+ * opts->flags it runs the depth-first order instead (Table I's DFS). */
 int  bbs_localize_hostqueue(const bbs_maps* maps, const float* scan_xyz, int64_t k, int is_device,
                             const bbs_ranges* ranges, const bbs_opts* opts, bbs_result* out);
 

@@ -689,6 +689,8 @@ int Engine::add(const bbs_maps* m, const float* xyz, int64_t k, int is_device, c
     int rc = BBS_OK;
     if (!(frac > 0.0 && frac <= 1.0)) rc = set_error(BBS_EINVAL, "localize: score_frac %g outside (0, 1]", frac);
     else if (flags & BBS_PRUNE_GE) rc = set_error(BBS_EINVAL, "localize: BBS_PRUNE_GE is not supported");
+    else if (flags & BBS_SEARCH_DFS)
+        rc = set_error(BBS_EINVAL, "localize: the depth-first order runs in bbs_localize_hostqueue");
     else if (k > (1 << 24) - 2) rc = set_error(BBS_EINVAL, "localize: more than 2^24 - 2 scan points");
     if (rc == BBS_OK) rc = scan_prepare(m, xyz, k, is_device, rg, opts, st_, &h.scan);
     if (rc < 0) {

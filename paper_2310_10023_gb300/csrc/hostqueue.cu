@@ -163,18 +163,31 @@ int hostqueue_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device,
         return BBS_OK;
     };
 
-    std::vector<HostBucket> F((size_t)k + 1);
+    // best-first: one frontier of score buckets; depth-first: one per level
+    const bool dfs = (flags & BBS_SEARCH_DFS) != 0;
+    const int nfr = dfs ? g.levels : 1;
+    std::vector<std::vector<HostBucket>> FL((size_t)nfr, std::vector<HostBucket>((size_t)k + 1));
+    std::vector<int32_t> ltop((size_t)nfr, -1);
+    std::vector<int64_t> lsize((size_t)nfr, 0);
+    std::vector<HostBucket>& F = FL[0];
     int64_t size = 0, peak = 0;
     int32_t top = -1, best = thr - 1;
     bool found = false;
     NodeRec match{};
     auto insert = [&](const NodeRec& nd, int32_t score) {
-        HostBucket& b = F[(size_t)score];
+        const int f = dfs ? rl_level(nd.rl) : 0;
+        HostBucket& b = FL[(size_t)f][(size_t)score];
         b.nodes.push_back(nd);
         b.kids += node_children(dg, rl_level(nd.rl), rl_rot(nd.rl));
         b.leaves += rl_level(nd.rl) == 0 ? 1 : 0;
         top = std::max(top, score);
+        ltop[(size_t)f] = std::max(ltop[(size_t)f], score);
+        lsize[(size_t)f] += 1;
         ++size;
+    };
+    auto lex_before = [](const NodeRec& a, const NodeRec& b) {
+        return lex_translation(a) < lex_translation(b) ||
+               (lex_translation(a) == lex_translation(b) && rl_rot(a.rl) < rl_rot(b.rl));
     };
 
     // the initial set: every translation of the Eq. (3)-(5) window times every
@@ -224,11 +237,91 @@ int hostqueue_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device,
         res->phase_ms[1] = ms_now() - t0 - res->phase_ms[0];
     }
 
-    // the canonical best-first iteration
+    // the popped parents' rotational children (Eq. (13)), scored in launches of
+    // at most the tuning's task count; children above best join the frontier
     std::vector<NodeRec> parents;
+    auto branch_parents = [&](int64_t pk) -> int {
+        res->iterations += 1;
+        res->parents_branched += (int64_t)parents.size();
+        res->nodes_scored += pk;
+        res->gathers += (pk / 8) * k;
+        tk.clear();
+        for (const NodeRec& nd : parents) {
+            const int l = rl_level(nd.rl);
+            int32_t lo[3], ext[3];
+            if (rot_children(dg, l, rl_rot(nd.rl), lo, ext) == 0) continue;
+            const int64_t nb = g.N[l - 1][1], ng = g.N[l - 1][2];
+            for (int32_t ja = 0; ja < ext[0]; ++ja)
+                for (int32_t jb = 0; jb < ext[1]; ++jb)
+                    for (int32_t jg = 0; jg < ext[2]; ++jg) {
+                        TaskRec t;
+                        std::memset(&t, 0, sizeof(t));
+                        t.tx = 2 * nd.cx;
+                        t.ty = 2 * nd.cy;
+                        t.tz = 2 * nd.cz;
+                        t.rl = rl_pack((uint32_t)(((int64_t)(lo[0] + ja) * nb + (lo[1] + jb)) * ng + (lo[2] + jg)), l - 1);
+                        tk.push_back(t);
+                    }
+        }
+        std::vector<TaskRec> all;
+        all.swap(tk);
+        for (size_t u0 = 0; u0 < all.size(); u0 += (size_t)tn.launch_tasks) {
+            const size_t u1 = std::min(all.size(), u0 + (size_t)tn.launch_tasks);
+            tk.assign(all.begin() + (long)u0, all.begin() + (long)u1);
+            BBS_TRY(score_tasks(MODE_SEARCH));
+            for (size_t u = 0; u < tk.size(); ++u)
+                for (int j = 0; j < 8; ++j) {
+                    const int32_t sc = dense[8 * u + j];
+                    if (sc <= best) continue;
+                    insert(NodeRec{tk[u].tx + (j >> 2), tk[u].ty + ((j >> 1) & 1), tk[u].tz + (j & 1), tk[u].rl}, sc);
+                }
+        }
+        return BBS_OK;
+    };
     const double t_search = ms_now();
     double t_match = -1.0;
-    for (;;) {
+
+    // the depth-first order: leaves first (the best sets best and the match,
+    // and every node at or below it goes), then whole (level, score) buckets,
+    // deepest level first, highest score first, until the children reach b
+    while (dfs) {
+        peak = std::max(peak, size);
+        if (lsize[0] > 0) {
+            int32_t s0 = ltop[0];
+            while (s0 >= 0 && FL[0][(size_t)s0].nodes.empty()) --s0;
+            const HostBucket& b = FL[0][(size_t)s0];
+            match = b.nodes[0];
+            for (const NodeRec& nd : b.nodes)
+                if (lex_before(nd, match)) match = nd;
+            best = s0;
+            found = true;
+            t_match = ms_now();
+            for (int l = 0; l < nfr; ++l)
+                for (int32_t t = 0; t <= best && t <= ltop[(size_t)l]; ++t) {
+                    HostBucket& hb = FL[(size_t)l][(size_t)t];
+                    lsize[(size_t)l] -= (int64_t)hb.nodes.size();
+                    size -= (int64_t)hb.nodes.size();
+                    hb = HostBucket();
+                }
+        }
+        parents.clear();
+        int64_t pk = 0;
+        for (int l = 1; l < nfr && pk < batch; ++l)
+            for (int32_t t = ltop[(size_t)l]; t > best && pk < batch; --t) {
+                HostBucket& hb = FL[(size_t)l][(size_t)t];
+                if (hb.nodes.empty()) continue;
+                pk += hb.kids;
+                parents.insert(parents.end(), hb.nodes.begin(), hb.nodes.end());
+                lsize[(size_t)l] -= (int64_t)hb.nodes.size();
+                size -= (int64_t)hb.nodes.size();
+                hb = HostBucket();
+            }
+        if (parents.empty()) break;
+        BBS_TRY(branch_parents(pk));
+    }
+
+    // the canonical best-first iteration
+    while (!dfs) {
         peak = std::max(peak, size);
         int32_t sstar = -1;
         int reason = size > 0 ? 4 : 0;
@@ -272,43 +365,7 @@ int hostqueue_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device,
         size = clear ? 0 : size - (int64_t)parents.size();
         top = reason == 1 ? sstar : -1;
         if (parents.empty()) break;
-        res->iterations += 1;
-        res->parents_branched += (int64_t)parents.size();
-        res->nodes_scored += pk;
-        res->gathers += (pk / 8) * k;
-        // the popped parents' rotational children (Eq. (13)), scored in
-        // launches of at most the tuning's task count
-        tk.clear();
-        for (const NodeRec& nd : parents) {
-            const int l = rl_level(nd.rl);
-            int32_t lo[3], ext[3];
-            if (rot_children(dg, l, rl_rot(nd.rl), lo, ext) == 0) continue;
-            const int64_t nb = g.N[l - 1][1], ng = g.N[l - 1][2];
-            for (int32_t ja = 0; ja < ext[0]; ++ja)
-                for (int32_t jb = 0; jb < ext[1]; ++jb)
-                    for (int32_t jg = 0; jg < ext[2]; ++jg) {
-                        TaskRec t;
-                        std::memset(&t, 0, sizeof(t));
-                        t.tx = 2 * nd.cx;
-                        t.ty = 2 * nd.cy;
-                        t.tz = 2 * nd.cz;
-                        t.rl = rl_pack((uint32_t)(((int64_t)(lo[0] + ja) * nb + (lo[1] + jb)) * ng + (lo[2] + jg)), l - 1);
-                        tk.push_back(t);
-                    }
-        }
-        std::vector<TaskRec> all;
-        all.swap(tk);
-        for (size_t u0 = 0; u0 < all.size(); u0 += (size_t)tn.launch_tasks) {
-            const size_t u1 = std::min(all.size(), u0 + (size_t)tn.launch_tasks);
-            tk.assign(all.begin() + (long)u0, all.begin() + (long)u1);
-            BBS_TRY(score_tasks(MODE_SEARCH));
-            for (size_t u = 0; u < tk.size(); ++u)
-                for (int j = 0; j < 8; ++j) {
-                    const int32_t sc = dense[8 * u + j];
-                    if (sc <= best) continue;
-                    insert(NodeRec{tk[u].tx + (j >> 2), tk[u].ty + ((j >> 1) & 1), tk[u].tz + (j & 1), tk[u].rl}, sc);
-                }
-        }
+        BBS_TRY(branch_parents(pk));
     }
     const double t_end = ms_now();
     res->best_score = best;

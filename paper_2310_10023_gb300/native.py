@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_PKG, "libbbs.so")
 OK, NOT_FOUND, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EKEYRANGE, ECORRUPT = 0, 1, -1, -2, -3, -4, -5, -6
 ECANCELED, PENDING = -7, 2
 TRANSLATION_ONLY, LEAF_UNDILATED, PRUNE_GE, ANGLE_LOWER_EDGE, CHILD_LITERAL = 0x1, 0x2, 0x4, 0x8, 0x10
+SEARCH_DFS = 0x40          # depth-first batched order (bbs_localize_hostqueue)
 TIME_KERNELS, HOST_DRIVEN = 0x100, 0x200
 EXACT_BOUND = 0x20
 

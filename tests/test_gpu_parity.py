@@ -529,3 +529,59 @@ def test_host_queue_equals_device_frontier(nv, room_pair, indoor_pair):
         assert key(nv.bbs_localize_hostqueue(maps, s, rg, op)) == key(nv.bbs_localize(maps, s, rg, op))
     finally:
         nv.bbs_set_tuning(reset=True)
+
+
+# ---- depth-first order (Table I's DFS), host queue ------------------------------
+
+def _dfs_cases(nv, room_pair):
+    w, m, dm, om = room_pair
+    nr, orr = _ranges(nv, w)
+    cases = [("room scan 1, b 1000", dm, om, synth.make_scan(1, 1)[0], nr, orr, w.score_frac, 1000, 0),
+             ("room scan 0, b 10000", dm, om, synth.make_scan(1, 0)[0], nr, orr, w.score_frac, w.batch, 0)]
+    s, pose = synth.make_scan(1, 2)
+    s = s[:200]
+    lo, hi, alo, ahi = _window(pose)
+    wnr, worr = _ranges(nv, w, lo, hi, alo, ahi)
+    for b in (1, 64):
+        cases.append((f"window, translation only, b {b}", dm, om, s, wnr, worr, 0.5, b, oracle.TRANSLATION_ONLY))
+    return cases
+
+
+@pytest.mark.parametrize("idx", [0, 1, 2, 3])
+def test_dfs_host_queue_equals_oracle(nv, room_pair, idx):
+    """The depth-first order of the host-queue search reproduces the oracle's:
+    same match, best, rounds, nodes scored and peak frontier."""
+    name, dm, om, s, nr, orr, frac, batch, flags = _dfs_cases(nv, room_pair)[idx]
+    res = nv.bbs_localize_hostqueue(dm, s, nr, nv.make_opts(score_frac=frac, batch=batch, flags=flags | nv.SEARCH_DFS))
+    ores = oracle.localize(om, s, orr, score_frac=frac, batch=batch, flags=flags | oracle.SEARCH_DFS)
+    _same_search(res, ores)
+    assert res.peak_frontier == ores.peak_frontier, name
+    assert res.status == nv.OK
+
+
+def test_dfs_exact_bound_equals_brute_force_on_gpu(nv, room_pair):
+    """Exact-bound maps: the depth-first order on the GPU returns the
+    exhaustive optimum, as the oracle's does, and equals the oracle's run."""
+    w, m, dm, om = room_pair
+    s, pose = synth.make_scan(1, 0)
+    s = s[:200]
+    lo, hi, alo, ahi = _window(pose)
+    nr, orr = _ranges(nv, w, lo, hi, alo, ahi)
+    g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), orr)
+    e = g.exact_dilation(oracle.scan_dmax(s))
+    dme = nv.bbs_build_maps(m, w.r, w.levels, nv.exact_bound_flags(e))
+    ome = oracle.Maps(m, w.r, w.levels, oracle.exact_flags(e))
+    res = nv.bbs_localize_hostqueue(dme, s, nr, nv.make_opts(score_frac=0.3, batch=100, flags=nv.SEARCH_DFS))
+    ores = oracle.localize(ome, s, orr, score_frac=0.3, batch=100, flags=oracle.SEARCH_DFS)
+    best, _ = oracle.brute_force(ome, g, s)
+    _same_search(res, ores)
+    assert res.best_score == best
+
+
+def test_dfs_refused_by_device_engine(nv, room_pair):
+    w, m, dm, om = room_pair
+    s, _ = synth.make_scan(1, 0)
+    nr, _ = _ranges(nv, w)
+    with pytest.raises(nv.BBSError) as e:
+        nv.bbs_localize(dm, s, nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch, flags=nv.SEARCH_DFS))
+    assert e.value.code == nv.EINVAL
