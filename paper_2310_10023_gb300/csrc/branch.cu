@@ -503,19 +503,29 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
 
 // survivors: children scoring above their search's best, appended to the
 // frontier array the next iteration reads, with their bucket counts
-// (nodes, children, leaves) and the search's size and top bucket
+// (nodes, children, leaves) and the search's size and top bucket.  The
+// append position is claimed once per CTA (one atomic on the array's count
+// per 256 children instead of one per warp), and when the launch holds one
+// search its size and top bucket are raised once per CTA too.
 template <int MODE>
 __global__ void __launch_bounds__(256) finalize_kernel(const Plan* __restrict__ P, SearchDev* S,
                                                        const TaskRec* __restrict__ tasks, int32_t* dense, FrontDev F,
                                                        LoopState* LS)
 {
     if (P->status != PLAN_OK) return;
-    const int lane = threadIdx.x & 31;
+    __shared__ uint32_t s_woff[8];
+    __shared__ uint32_t s_total;
+    __shared__ unsigned long long s_base;
+    __shared__ int32_t s_top;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nxt = 1 - LS->cur;
+    const bool one = P->nseg == 1;   // every child of the launch belongs to one search
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t n_dense = P->n_tasks * 8;
-    const int64_t n_round = (n_dense + 31) & ~(int64_t)31;
-    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < n_round; d += stride) {
+    if (threadIdx.x == 0) s_top = -1;
+    __syncthreads();
+    for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < n_dense; b0 += stride) {   // uniform per CTA
+        const int64_t d = b0 + threadIdx.x;
         bool surv = false;
         int32_t score = 0, sid = 0;
         NodeRec nd;
@@ -526,12 +536,12 @@ __global__ void __launch_bounds__(256) finalize_kernel(const Plan* __restrict__ 
         if (d < n_dense) {
             const int64_t u = d >> 3;
             const int j = (int)(d & 7);
-            const Seg g = P->seg[find_task_seg(P, u)];
+            const Seg& g = P->seg[find_task_seg(P, u)];
             sid = g.sid;
-            const SearchDev& s = S[sid];
             bool valid = true;
             int32_t tx, ty, tz;
             if (MODE == MODE_INITIAL) {
+                const SearchDev& s = S[sid];
                 const int64_t lu = u - g.first_task;
                 virtual_parent(s, g.first_parent + lu / g.R, tx, ty, tz);
                 tx = 2 * tx + (j >> 2);
@@ -554,7 +564,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(const Plan* __restrict__ 
             if (dv) dense[d] = 0;
             if (valid) {
                 score = dv;
-                surv = score > s.ctl->best;
+                surv = score > g.best;
                 nd.cx = tx;
                 nd.cy = ty;
                 nd.cz = tz;
@@ -562,34 +572,57 @@ __global__ void __launch_bounds__(256) finalize_kernel(const Plan* __restrict__ 
             }
         }
         const uint32_t ball = __ballot_sync(0xffffffffu, surv);
-        if (!ball) continue;
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&LS->fn[nxt], (unsigned long long)__popc(ball));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        const uint32_t key = surv ? (((uint32_t)sid << 24) | (uint32_t)score) : 0xFFFFFFFFu;
-        const uint32_t peers = __match_any_sync(0xffffffffu, key);                 // same search and score
-        const uint32_t same = __match_any_sync(0xffffffffu, surv ? sid : -1);      // same search
-        if (surv) {
-            SearchDev& s = S[sid];
-            const unsigned long long pos = base + __popc(ball & ((1u << lane) - 1u));
-            // bucket counts, one atomic per (search, score) group of the warp
-            const uint32_t kids = (uint32_t)node_children(s.grid, m, crot);
-            const uint32_t gk = __reduce_add_sync(peers, kids);
-            const uint32_t gl = __reduce_add_sync(peers, m == 0 ? 1u : 0u);
-            if (pos < (unsigned long long)F.cap) {
-                F.nodes[nxt][pos] = nd;
-                F.keys[nxt][pos] = key;
-            } else {
-                atomicOr(&s.ctl->err, 1);   // the frontier is full: the search fails
-            }
-            if ((__ffs(peers) - 1) == lane) {
-                atomicAdd(&s.b_cnt[score], (unsigned long long)__popc(peers));
-                atomicAdd(&s.b_kids[score], (unsigned long long)gk);
-                if (gl) atomicAdd(&s.b_leaf[score], (unsigned long long)gl);
-                atomicMax(&s.ctl->top, score);
-            }
-            if ((__ffs(same) - 1) == lane) atomicAdd((unsigned long long*)&s.ctl->size, (unsigned long long)__popc(same));
+        if (lane == 0) s_woff[warp] = __popc(ball);
+        if (one && ball) {
+            const int32_t wtop = __reduce_max_sync(0xffffffffu, surv ? score : -1);
+            if (lane == 0) atomicMax(&s_top, wtop);
         }
+        __syncthreads();   // the warps' counts and top
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+            for (int w = 0; w < 8; ++w) {
+                const uint32_t c = s_woff[w];
+                s_woff[w] = t;
+                t += c;
+            }
+            s_total = t;
+            s_base = t ? atomicAdd(&LS->fn[nxt], (unsigned long long)t) : 0ull;
+            if (one && t) {
+                Ctl* c = S[P->seg[0].sid].ctl;
+                atomicAdd((unsigned long long*)&c->size, (unsigned long long)t);
+                atomicMax(&c->top, s_top);
+            }
+        }
+        __syncthreads();   // the CTA's base and the warps' offsets
+        if (s_total) {
+            const uint32_t key = surv ? (((uint32_t)sid << 24) | (uint32_t)score) : 0xFFFFFFFFu;
+            const uint32_t peers = __match_any_sync(0xffffffffu, key);                 // same search and score
+            const uint32_t same = __match_any_sync(0xffffffffu, surv ? sid : -1);      // same search
+            if (surv) {
+                SearchDev& s = S[sid];
+                const unsigned long long pos = s_base + s_woff[warp] + __popc(ball & ((1u << lane) - 1u));
+                // bucket counts, one atomic per (search, score) group of the warp
+                const uint32_t kids = (uint32_t)node_children(s.grid, m, crot);
+                const uint32_t gk = __reduce_add_sync(peers, kids);
+                const uint32_t gl = __reduce_add_sync(peers, m == 0 ? 1u : 0u);
+                if (pos < (unsigned long long)F.cap) {
+                    F.nodes[nxt][pos] = nd;
+                    F.keys[nxt][pos] = key;
+                } else {
+                    atomicOr(&s.ctl->err, 1);   // the frontier is full: the search fails
+                }
+                if ((__ffs(peers) - 1) == lane) {
+                    atomicAdd(&s.b_cnt[score], (unsigned long long)__popc(peers));
+                    atomicAdd(&s.b_kids[score], (unsigned long long)gk);
+                    if (gl) atomicAdd(&s.b_leaf[score], (unsigned long long)gl);
+                    if (!one) atomicMax(&s.ctl->top, score);
+                }
+                if (!one && (__ffs(same) - 1) == lane)
+                    atomicAdd((unsigned long long*)&s.ctl->size, (unsigned long long)__popc(same));
+            }
+        }
+        if (threadIdx.x == 0) s_top = -1;
+        __syncthreads();   // shared state consumed before the next pass
     }
 }
 

@@ -116,7 +116,7 @@ struct Seg {
     int32_t sid;
     int32_t nblk;           // PBLK-point blocks of the search's scan
     int32_t R;              // initial set: rotations per virtual parent
-    int32_t pad;
+    int32_t best;           // the search's best when the launch was planned: survivors score above it
 };
 
 enum { PLAN_OK = 0, PLAN_EMPTY = 1, PLAN_OVERFLOW = 2, PLAN_SPLIT = 3 };

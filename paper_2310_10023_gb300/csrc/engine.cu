@@ -39,48 +39,44 @@ namespace bbs {
 
 // ---- block helpers (blocks of whole warps) ----------------------------------
 
-__device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t* total, int64_t* sh)
+// Exclusive block prefix sums of N values at once (two barriers); totals in
+// `total`.  sh holds 32 * N values; the caller synchronizes before reusing it.
+template <int N>
+__device__ __forceinline__ void block_excl_scan_n(const int64_t (&v)[N], int64_t (&before)[N], int64_t (&total)[N],
+                                                  int64_t* sh)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int64_t x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) sh[wid] = x;
-    __syncthreads();
     const int nw = (int)(blockDim.x >> 5);
-    if (wid == 0) {
-        int64_t s = lane < nw ? sh[lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t y = __shfl_up_sync(0xffffffffu, s, o);
-            if (lane >= o) s += y;
+    int64_t x[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) x[k] = v[k];
+    for (int o = 1; o < 32; o <<= 1)
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, x[k], o);
+            if (lane >= o) x[k] += y;
         }
-        sh[lane] = s;
+    if (lane == 31)
+#pragma unroll
+        for (int k = 0; k < N; ++k) sh[32 * k + wid] = x[k];
+    __syncthreads();
+    if (wid == 0)
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            int64_t t = lane < nw ? sh[32 * k + lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            sh[32 * k + lane] = t;
+        }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        before[k] = (wid > 0 ? sh[32 * k + wid - 1] : 0) + x[k] - v[k];
+        total[k] = sh[32 * k + nw - 1];
     }
-    __syncthreads();
-    const int64_t before = (wid > 0 ? sh[wid - 1] : 0) + x - v;
-    *total = sh[nw - 1];
-    __syncthreads();
-    return before;
 }
-
-__device__ __forceinline__ int block_min_int(int v, int* sh)
-{
-    v = __reduce_min_sync(0xffffffffu, v);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        int x = sh[threadIdx.x];
-        x = __reduce_min_sync(0xffffffffu, x);
-        if (threadIdx.x == 0) sh[32] = x;
-    }
-    __syncthreads();
-    const int r = sh[32];
-    __syncthreads();
-    return r;
-}
-
 
 // ---- launch shape ---------------------------------------------------------------
 
@@ -144,8 +140,8 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
                                                       unsigned long long* tcnt, cudaGraphConditionalHandle cond,
                                                       int use_cond, Tuning tune)
 {
-    __shared__ int64_t sh[32];
-    __shared__ int s_min[33];
+    __shared__ int64_t sh[32 * 4];
+    __shared__ int s_first;
     __shared__ int32_t s_star, s_reason;
     __shared__ int64_t s_cnt, s_kids;
     __shared__ int s_last;
@@ -170,25 +166,31 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
         const int32_t top = c->top;
         for (int base = top; base >= 0; base -= blockDim.x) {
             const int s = base - tid;
-            const int64_t cnt = s >= 0 ? (int64_t)f.b_cnt[s] : 0;
+            int64_t cnt = 0, kids = 0, leaf = 0;
+            if (s >= 0) {   // three independent loads
+                cnt = (int64_t)f.b_cnt[s];
+                kids = (int64_t)f.b_kids[s];
+                leaf = (int64_t)f.b_leaf[s];
+            }
             const bool have = cnt > 0;
-            const int64_t kids = have ? (int64_t)f.b_kids[s] : 0;
-            int64_t tot, ntot;
-            const int64_t cum = carry + block_excl_scan(kids, &tot, sh);
-            block_excl_scan(cnt, &ntot, sh);
-            const bool stop = have && (cum >= f.batch || s <= best || f.b_leaf[s] > 0);
-            const int first = block_min_int(stop ? tid : (int)blockDim.x, s_min);
+            if (!have) kids = 0;
+            if (tid == 0) s_first = (int)blockDim.x;
+            // prefixes of the children and node counts from the top
+            const int64_t v2[2] = {kids, cnt};
+            int64_t ex[2], tot[2];
+            block_excl_scan_n<2>(v2, ex, tot, sh);
+            const int64_t cum = carry + ex[0];
+            const bool stop = have && (cum >= f.batch || s <= best || leaf > 0);
+            if (stop) atomicMin(&s_first, tid);
+            __syncthreads();
+            const int first = s_first;
             if (first < (int)blockDim.x) {
                 if (tid == first) {
                     s_star = s;
                     s_reason = cum >= f.batch ? 1 : (s <= best ? 2 : 3);
-                    s_kids = cum;   // children of the buckets above s*
+                    s_kids = cum;               // children of the buckets above s*
+                    s_cnt = ncarry + ex[1];     // and their nodes
                 }
-                // parents above s*: this pass's buckets before `first`, and the earlier passes
-                const int64_t cnt_above = tid < first ? cnt : 0;
-                int64_t ca;
-                block_excl_scan(cnt_above, &ca, sh);
-                if (tid == 0) s_cnt = ncarry + ca;
                 if (have && tid < first) {
                     f.b_cnt[s] = 0;
                     f.b_kids[s] = 0;
@@ -202,8 +204,9 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
                 f.b_kids[s] = 0;
                 f.b_leaf[s] = 0;
             }
-            carry += tot;
-            ncarry += ntot;
+            carry += tot[0];
+            ncarry += tot[1];
+            __syncthreads();   // s_first and sh read before the next pass
         }
         if (tid == 0 && s_star < 0) {   // no stop: every bucket popped
             s_kids = carry;
@@ -254,19 +257,23 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
         }
         __syncthreads();
     }
-    // the last CTA to finish plans the round
-    __threadfence();
-    if (tid == 0) s_last = atomicAdd(&LS->select_done, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+    // the last CTA to finish plans the round (a single CTA plans at once)
+    if (gridDim.x > 1) {
+        __threadfence();
+        if (tid == 0) s_last = atomicAdd(&LS->select_done, 1u) == gridDim.x - 1;
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+    }
     int64_t cp = 0, ct = 0, cs = 0, cn = 0;
     int any3 = 0;
     for (int base = 0; base < nslots; base += blockDim.x) {
         const int s = base + tid;
         int64_t np = 0, nt = 0, sl = 0, has = 0;
+        int32_t best = 0;
         if (s < nslots) {
             const Ctl* c = S[s].ctl;
+            best = c->best;
             if (c->active && !c->done && !c->err) {
                 np = c->n_parents;
                 nt = c->n_tasks;
@@ -278,11 +285,11 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
             pcnt[s] = 0;
             tcnt[s] = 0;
         }
-        int64_t tp, tt, ts, tn;
-        const int64_t ep = block_excl_scan(np, &tp, sh);
-        const int64_t et = block_excl_scan(nt, &tt, sh);
-        const int64_t es = block_excl_scan(sl, &ts, sh);
-        const int64_t en = block_excl_scan(has, &tn, sh);
+        const int64_t v4[4] = {np, nt, sl, has};
+        int64_t ex4[4], tot4[4];
+        block_excl_scan_n<4>(v4, ex4, tot4, sh);
+        const int64_t ep = ex4[0], et = ex4[1], es = ex4[2], en = ex4[3];
+        const int64_t tp = tot4[0], tt = tot4[1], ts = tot4[2], tn = tot4[3];
         if (s < nslots) {
             poff[s] = cp + ep;
             toff[s] = ct + et;
@@ -296,13 +303,14 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
                 g.sid = s;
                 g.nblk = S[s].nblk;
                 g.R = 0;
-                g.pad = 0;
+                g.best = best;
             }
         }
         cp += tp;
         ct += tt;
         cs += ts;
         cn += tn;
+        __syncthreads();   // sh read before the next pass
     }
     any3 = __syncthreads_or(any3);
     if (tid == 0) {
@@ -804,6 +812,7 @@ int Engine::start()
             sg.sid = i;
             sg.nblk = h.dev.nblk;
             sg.R = (int32_t)R;
+            sg.best = h.thr - 1;
             segs.push_back(sg);
             ntk += take * R;
             nsl += take * R * h.dev.nblk;
@@ -940,6 +949,7 @@ int Engine::score_overflow()
             sg.first_slice = nsl;
             sg.sid = i;
             sg.nblk = h.dev.nblk;
+            sg.best = h_ctl_[i].best;
             segs.push_back(sg);
             ntk += take;
             nsl += take * h.dev.nblk;
