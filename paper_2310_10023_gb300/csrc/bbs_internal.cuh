@@ -428,10 +428,15 @@ struct ScanState {
     double2* cs;       // (cos, sin) of every segment angle, host libm, FP64
     float4* rot;       // 3 float4 rows per rotation of the top level l_max
     int64_t h2d, d2h;  // bytes copied while preparing
+    int32_t angles_pending;   // the levels below the top still lack their (cos, sin) entries
 };
 
+// Pack the scan, build its pose grid, upload the (cos, sin) table and the top
+// level's rotation rows.  defer_lower leaves the levels below the top to
+// scan_finish_angles (they are needed from the first branching on).
 int scan_prepare(const bbs_maps* m, const float* xyz, int64_t k, int is_device, const bbs_ranges* rg,
-                 const bbs_opts* opts, cudaStream_t st, ScanState* out);
+                 const bbs_opts* opts, cudaStream_t st, ScanState* out, bool defer_lower = false);
+int scan_finish_angles(ScanState* s, cudaStream_t st);
 // extra dilation the exact-bound mode needs for this grid and scan (-1: none can)
 int exact_dilation_needed(const HostGrid& g, double norm_max);
 // the 3 x float4 rows of every rotation of `level` -> out

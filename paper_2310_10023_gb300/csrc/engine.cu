@@ -700,7 +700,7 @@ int Engine::add(const bbs_maps* m, const float* xyz, int64_t k, int is_device, c
     else if (flags & BBS_SEARCH_DFS)
         rc = set_error(BBS_EINVAL, "localize: the depth-first order runs in bbs_localize_hostqueue");
     else if (k > (1 << 24) - 2) rc = set_error(BBS_EINVAL, "localize: more than 2^24 - 2 scan points");
-    if (rc == BBS_OK) rc = scan_prepare(m, xyz, k, is_device, rg, opts, st_, &h.scan);
+    if (rc == BBS_OK) rc = scan_prepare(m, xyz, k, is_device, rg, opts, st_, &h.scan, true);
     if (rc < 0) {
         release(i);
         return rc;
@@ -821,6 +821,15 @@ int Engine::start()
         }
     }
     BBS_TRY(flush());
+    // the (cos, sin) entries of the levels below the top, formed on the host
+    // while the GPU scores the initial sets; stream order puts them before
+    // the first branching
+    for (int i : slots) {
+        SearchHost& h = hosts_[(size_t)i];
+        const int64_t before = h.scan.h2d;
+        BBS_TRY(scan_finish_angles(&h.scan, st_));
+        h.res.h2d_bytes += h.scan.h2d - before;
+    }
     const double t = now_ms();
     for (int i : slots) {
         SearchHost& h = hosts_[(size_t)i];

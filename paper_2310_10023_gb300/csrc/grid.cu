@@ -244,8 +244,36 @@ static int grid_blocks(int64_t n, int threads)
     return (int)b;
 }
 
+// cos / sin of the segment angles of levels [l0, l1), uploaded to their place
+// in s.cs (a copy from pageable memory has staged its source by the time
+// cudaMemcpyAsync returns, so the host vector may go)
+static cudaError_t upload_angles(ScanState& s, int l0, int l1, cudaStream_t st)
+{
+    const HostGrid& g = s.grid;
+    if (l0 >= l1) return cudaSuccess;
+    const int64_t a = g.cs_off[l0][0], b = l1 < g.levels ? g.cs_off[l1][0] : g.n_cs;
+    if (b <= a) return cudaSuccess;
+    std::vector<double2> cs((size_t)(b - a));
+    for (int l = l0; l < l1; ++l)
+        for (int i = 0; i < 3; ++i)
+            for (int64_t c = 0; c < g.N[l][i]; ++c) {
+                const double ang = grid_angle(g, l, i, c);
+                cs[(size_t)(g.cs_off[l][i] + c - a)] = make_double2(std::cos(ang), std::sin(ang));
+            }
+    s.h2d += (int64_t)(sizeof(double2) * cs.size());
+    return cudaMemcpyAsync(s.cs + a, cs.data(), sizeof(double2) * cs.size(), cudaMemcpyHostToDevice, st);
+}
+
+int scan_finish_angles(ScanState* s, cudaStream_t st)
+{
+    if (!s->angles_pending) return BBS_OK;
+    s->angles_pending = 0;
+    BBS_CUDA_TRY(upload_angles(*s, 0, s->grid.levels - 1, st));
+    return BBS_OK;
+}
+
 int scan_prepare(const bbs_maps* m, const float* xyz, int64_t k, int is_device, const bbs_ranges* rg_in,
-                 const bbs_opts* opts, cudaStream_t st, ScanState* out)
+                 const bbs_opts* opts, cudaStream_t st, ScanState* out, bool defer_lower)
 {
     std::memset(out, 0, sizeof(*out));
     if (k < 0) return set_error(BBS_EINVAL, "scan: k < 0");
@@ -300,20 +328,17 @@ int scan_prepare(const bbs_maps* m, const float* xyz, int64_t k, int is_device, 
         return rc;
     }
     // cos / sin of every segment angle (host libm, FP64), kept on the device:
-    // the search forms the rotation rows of the rotations it expands
+    // the search forms the rotation rows of the rotations it expands.  The
+    // top level's entries come first (the initial set needs only them); with
+    // defer_lower the other levels' follow in scan_finish_angles, which the
+    // engine calls while the GPU scores the initial set.
     const HostGrid& g = out->grid;
-    std::vector<double2> cs((size_t)g.n_cs);
-    for (int l = 0; l < g.levels; ++l)
-        for (int i = 0; i < 3; ++i)
-            for (int64_t c = 0; c < g.N[l][i]; ++c) {
-                const double ang = grid_angle(g, l, i, c);
-                cs[(size_t)(g.cs_off[l][i] + c)] = make_double2(std::cos(ang), std::sin(ang));
-            }
-    BBS_CUDA_TRY(cudaMallocAsync((void**)&out->cs, sizeof(double2) * cs.size(), st));
-    BBS_CUDA_TRY(cudaMemcpyAsync(out->cs, cs.data(), sizeof(double2) * cs.size(), cudaMemcpyHostToDevice, st));
-    out->h2d += (int64_t)(sizeof(double2) * cs.size());
-    // the top level's rows (the initial set scores every one of them)
     const int top = g.levels - 1;
+    BBS_CUDA_TRY(cudaMallocAsync((void**)&out->cs, sizeof(double2) * (size_t)g.n_cs, st));
+    BBS_CUDA_TRY(upload_angles(*out, top, g.levels, st));
+    if (defer_lower) out->angles_pending = 1;
+    else BBS_CUDA_TRY(upload_angles(*out, 0, top, st));
+    // the top level's rows (the initial set scores every one of them)
     BBS_CUDA_TRY(cudaMallocAsync((void**)&out->rot, sizeof(float4) * 3 * (size_t)g.nrot[top], st));
     BBS_CUDA_TRY(launch_level_rows(*out, top, out->rot, st));
     // the host vector may go: a copy from pageable memory has staged its
