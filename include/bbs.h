@@ -330,6 +330,70 @@ int  bbs_localize(const bbs_maps* maps, const float* scan_xyz, int64_t k, int is
 int  bbs_localize_hostqueue(const bbs_maps* maps, const float* scan_xyz, int64_t k, int is_device,
                             const bbs_ranges* ranges, const bbs_opts* opts, bbs_result* out);
 
+/* ---- local fine registration (GICP) after the BnB result --------------------
+ *
+ * Sec. IV seeds a generalized-ICP refinement with the BnB estimate; the
+ * paper fixes none of its internals, so these are the library's readings:
+ * the target is the map cloud grouped by fine voxel key
+ * u = floor(fl32(x fl32(1/r))) (the level-0 quantization), voxel u standing
+ * for the centroid of its points (sums of rint((x - u r) 2^32) in integers:
+ * exact and independent of order); a scan point p = R s + t corresponds to
+ * the nearest centroid of the occupied voxels of the 3 x 3 x 3 block around
+ * floor(p / r) (ties to the first in (dx, dy, dz) order), kept within tau;
+ * covariances are normalized, r^2 (S / tr S + eps I) with S the sample
+ * covariance of the centroids of the block around the target voxel, or of
+ * the scan points within rho of the scan point (r^2 I when S = 0);
+ * Gauss-Newton on sum d^T (C_t + R C_s R^T)^-1 d, d = centroid - p, with
+ * steps p -> Exp(w) p + v, until |w| < eps_rot and |v| < eps_trans or
+ * max_iters linearizations.  Transformed coordinates and distances are
+ * formed in FP64 with every operation rounded on its own. */
+typedef struct bbs_gicp_target bbs_gicp_target;   /* opaque: device-resident voxel centroids */
+
+/* Build the target from a map cloud (n x 3 float, host or device) at voxel
+ * size r.  BBS_EINVAL (n < 1, r <= 0, non-finite point), BBS_EKEYRANGE (a key
+ * beyond +-2^20), BBS_ENOMEM, BBS_ECUDA. */
+int  bbs_gicp_target_build(const float* xyz, int64_t n, int is_device, float r, void* cuda_stream,
+                           bbs_gicp_target** out);
+void bbs_gicp_target_free(bbs_gicp_target* target);
+/* occupied voxels, hash table slots, longest probe */
+int  bbs_gicp_target_info(const bbs_gicp_target* target, int64_t* n_voxels, int64_t* table_size,
+                          int32_t* max_probe);
+
+typedef struct {
+    int32_t max_iters;      /* linearizations (0: 30)                            */
+    int32_t pad;
+    double  tau;            /* correspondence distance, m (0: r)                 */
+    double  rho;            /* source neighbourhood radius, m (0: 2 r)           */
+    double  cov_eps;        /* covariance regularization (0: 1e-3)               */
+    double  eps_rot;        /* convergence on the step's rotation, rad (0: 1e-6) */
+    double  eps_trans;      /* and translation, m (0: 1e-6)                      */
+    void*   cuda_stream;
+} bbs_gicp_opts;
+
+typedef struct {
+    int32_t status;           /* BBS_OK or an error                              */
+    int32_t converged;        /* the last step was below both tolerances         */
+    int32_t iterations;       /* linearizations made                             */
+    int32_t correspondences;  /* kept at the last linearization (< 6 stops)      */
+    double  cost;             /* sum d^T M d at the last linearization           */
+    double  R[9], t[3];       /* refined pose: map point = R scan point + t      */
+    double  pose[6];          /* x, y, z, roll, pitch, yaw of (R, t), R = Rz Ry Rx */
+    double  ms;               /* wall time of the call                           */
+} bbs_gicp_result;
+
+/* Refine the pose (R0 row-major, t0) of a scan (k x 3 float, host or
+ * device).  BBS_EINVAL for k < 1, NULL arguments or non-finite options. */
+int  bbs_gicp(const bbs_gicp_target* target, const float* scan_xyz, int64_t k, int is_device, const double R0[9],
+              const double t0[3], const bbs_gicp_opts* opts, bbs_gicp_result* out);
+
+/* One linearization at (R, t): H (6 x 6 row-major, parameters w then v),
+ * g = sum J^T M d, cost, correspondences kept; with voxels (k x 3 int32) and
+ * found (k bytes) both non-NULL, each point's nearest block voxel and
+ * whether it was kept (host memory). */
+int  bbs_gicp_linearize(const bbs_gicp_target* target, const float* scan_xyz, int64_t k, int is_device,
+                        const double R[9], const double t[3], const bbs_gicp_opts* opts, double H[36], double g[6],
+                        double* cost, int64_t* n, int32_t* voxels, uint8_t* found);
+
 /* ---- measurement ----------------------------------------------------------
  * bbs_bench_gather -- device time (ms, CUDA events on cuda_stream) of
  * `gathers` random 32-byte bucket reads, issued as the scoring kernel's probes

@@ -6,18 +6,21 @@ and bench.py's CPU legs, never by the product path.
 The paper fixes none of GICP's internals; the readings here (shared with the
 GPU path, each stated where it is used):
 
-* Target: the map's level-0 voxel set; voxel v stands for its centre
-  (v + 1/2) r.
+* Target: the map points grouped by fine voxel key u = floor(fl32(x fl32(1/r)))
+  (the level-0 quantization of Sec. III-C); voxel u stands for the centroid of
+  its points, u r + (sum_i rint((x_i - u r) 2^32)) 2^-32 / n, the sum taken
+  in integers (exact, order-free), every other operation in FP64 rounded on
+  its own.
 * Correspondence of a transformed point p: among the occupied voxels of the
-  3 x 3 x 3 block around floor(p / r), the one whose centre is nearest
+  3 x 3 x 3 block around floor(p / r), the one whose centroid is nearest
   (squared distance ((dx dx + dy dy) + dz dz), ties to the first in
   (dx, dy, dz) order, each offset from -1 to 1), kept when that distance is
   at most tau^2.
 * Covariances, normalized and basis-free: C = r^2 (S / tr S + eps I) with S
-  the (biased) sample covariance of the neighbourhood (target: occupied
-  voxels of the 3 x 3 x 3 block around v, in voxel units; source: scan points
-  within radius rho of the point, in metres); tr S = 0 gives C = r^2 I.
-  Sums run over neighbours in index order.
+  the (biased) sample covariance of the neighbourhood (target: the centroids
+  of the occupied voxels of the 3 x 3 x 3 block around u; source: scan points
+  within radius rho of the point); tr S = 0 gives C = r^2 I.  Sums run over
+  neighbours in block or index order.
 * Pose T = (R, t), R = Rz(yaw) Ry(pitch) Rx(roll); a step (w, v) maps p to
   Exp(w) p + v, so the residual d = c - p has Jacobian [ [p]_x | -I ];
   Gauss-Newton on sum_i d_i^T M_i d_i with M_i = (C_t + R C_s R^T)^-1 held
@@ -43,17 +46,43 @@ def pack_keys(v: np.ndarray) -> np.ndarray:
     return (v[:, 0] << 42) | (v[:, 1] << 21) | v[:, 2]
 
 
-class VoxelSet:
-    """Membership test over a set of integer voxel keys (sorted codes)."""
+FIX = float(1 << 32)
 
-    def __init__(self, keys: np.ndarray):
-        self.codes = np.unique(pack_keys(np.asarray(keys).reshape(-1, 3)))
 
-    def contains(self, v: np.ndarray) -> np.ndarray:
+def fine_keys(xyz: np.ndarray, r: float) -> np.ndarray:
+    """u = floor(fl32(x fl32(1/r))) per axis (the level-0 quantization)."""
+    rho = np.float32(1.0 / r)
+    return np.floor(np.asarray(xyz, np.float32) * rho).astype(np.int64)
+
+
+class Target:
+    """The map points grouped by fine voxel key, each voxel standing for the
+    centroid of its points (fixed-point sums, exact)."""
+
+    def __init__(self, xyz: np.ndarray, r: float):
+        r = float(np.float32(r))   # the voxel size as the maps hold it (FP32)
+        x = np.asarray(xyz, np.float32).reshape(-1, 3)
+        u = fine_keys(x, r)
+        codes, inv, cnt = np.unique(pack_keys(u), return_inverse=True, return_counts=True)
+        rel = x.astype(np.float64) - u.astype(np.float64) * r
+        fx = np.rint(rel * FIX).astype(np.int64)
+        sums = np.zeros((len(codes), 3), np.int64)
+        np.add.at(sums, inv, fx)
+        first = np.zeros(len(codes), np.int64)
+        first[inv[::-1]] = np.arange(len(x))[::-1]
+        self.r = r
+        self.codes = codes
+        self.keys = u[first]
+        self.count = cnt.astype(np.int64)
+        self.centroid = self.keys.astype(np.float64) * r + (sums.astype(np.float64) / self.count[:, None]) / FIX
+
+    def lookup(self, v: np.ndarray):
+        """-> (found (n,) bool, centroid (n, 3)) for voxel keys v (n, 3)."""
         c = pack_keys(v)
         i = np.searchsorted(self.codes, c)
-        i = np.minimum(i, len(self.codes) - 1)
-        return self.codes[i] == c if len(self.codes) else np.zeros(len(c), bool)
+        i = np.minimum(i, max(len(self.codes) - 1, 0))
+        hit = (self.codes[i] == c) if len(self.codes) else np.zeros(len(c), bool)
+        return hit, np.where(hit[:, None], self.centroid[i] if len(self.codes) else 0.0, 0.0)
 
 
 def rot_zyx(roll: float, pitch: float, yaw: float) -> np.ndarray:
@@ -103,31 +132,26 @@ def _normalized(S: np.ndarray, r: float, eps: float) -> np.ndarray:
     return C
 
 
-def target_covariances(occ: VoxelSet, v: np.ndarray, r: float, eps: float) -> np.ndarray:
-    """C_t of voxels v (n, 3): occupied voxels of the 3 x 3 x 3 block, voxel units."""
+def target_covariances(tgt: Target, v: np.ndarray, r: float, eps: float) -> np.ndarray:
+    """C_t of voxels v (n, 3): centroids of the occupied voxels of the 3 x 3 x 3 block."""
     v = np.asarray(v, np.int64)
     n = len(v)
     cnt = np.zeros(n)
-    sx = np.zeros(n)
-    sy = np.zeros(n)
-    sz = np.zeros(n)
+    acc = np.zeros((n, 3))
     offs = [(dx, dy, dz) for dx in (-1, 0, 1) for dy in (-1, 0, 1) for dz in (-1, 0, 1)]
     hits = []
     for dx, dy, dz in offs:
-        w = v + np.array([dx, dy, dz])
-        h = occ.contains(w)
-        hits.append((h, w))
+        h, c = tgt.lookup(v + np.array([dx, dy, dz]))
+        hits.append((h, c))
         cnt += h
-        sx += np.where(h, w[:, 0], 0)
-        sy += np.where(h, w[:, 1], 0)
-        sz += np.where(h, w[:, 2], 0)
+        acc += np.where(h[:, None], c, 0.0)
     den = np.maximum(cnt, 1.0)
-    mx, my, mz = sx / den, sy / den, sz / den
+    mu = acc / den[:, None]
     S = np.zeros((n, 6))
-    for h, w in hits:
-        ex = np.where(h, w[:, 0] - mx, 0.0)
-        ey = np.where(h, w[:, 1] - my, 0.0)
-        ez = np.where(h, w[:, 2] - mz, 0.0)
+    for h, c in hits:
+        ex = np.where(h, c[:, 0] - mu[:, 0], 0.0)
+        ey = np.where(h, c[:, 1] - mu[:, 1], 0.0)
+        ez = np.where(h, c[:, 2] - mu[:, 2], 0.0)
         S[:, 0] += ex * ex
         S[:, 1] += ex * ey
         S[:, 2] += ex * ez
@@ -172,26 +196,27 @@ def source_covariances(s: np.ndarray, rho: float, r: float, eps: float) -> np.nd
     return _normalized(S, r, eps)
 
 
-def correspondences(occ: VoxelSet, p: np.ndarray, r: float, tau: float):
-    """-> (voxel keys (n, 3), squared distance (n,), found (n,) bool)."""
+def correspondences(tgt: Target, p: np.ndarray, r: float, tau: float):
+    """-> (voxel keys (n, 3), centroids (n, 3), squared distance (n,), found (n,) bool)."""
     p = np.asarray(p, np.float64)
     base = np.floor(p / r).astype(np.int64)
     n = len(p)
     best = np.full(n, np.inf)
     bv = np.zeros((n, 3), np.int64)
+    bc = np.zeros((n, 3))
     for dx in (-1, 0, 1):
         for dy in (-1, 0, 1):
             for dz in (-1, 0, 1):
                 w = base + np.array([dx, dy, dz])
-                h = occ.contains(w)
-                c = (w.astype(np.float64) + 0.5) * r
+                h, c = tgt.lookup(w)
                 ex, ey, ez = p[:, 0] - c[:, 0], p[:, 1] - c[:, 1], p[:, 2] - c[:, 2]
                 d2 = (ex * ex + ey * ey) + ez * ez
                 better = h & (d2 < best)
                 best = np.where(better, d2, best)
                 bv = np.where(better[:, None], w, bv)
+                bc = np.where(better[:, None], c, bc)
     found = best <= tau * tau
-    return bv, best, found
+    return bv, bc, best, found
 
 
 def skew(p: np.ndarray) -> np.ndarray:
@@ -212,19 +237,18 @@ class Linearization:
     found: np.ndarray
 
 
-def linearize(occ: VoxelSet, s: np.ndarray, Cs: np.ndarray, R: np.ndarray, t: np.ndarray, r: float, tau: float,
+def linearize(tgt: Target, s: np.ndarray, Cs: np.ndarray, R: np.ndarray, t: np.ndarray, r: float, tau: float,
               eps: float) -> Linearization:
     p = transform(R, t, s)
-    vox, _, found = correspondences(occ, p, r, tau)
+    vox, cen, _, found = correspondences(tgt, p, r, tau)
     H = np.zeros((6, 6))
     g = np.zeros(6)
     cost = 0.0
     idx = np.nonzero(found)[0]
     if len(idx):
         pk = p[idx]
-        c = (vox[idx].astype(np.float64) + 0.5) * r
-        d = c - pk
-        Ct = target_covariances(occ, vox[idx], r, eps)
+        d = cen[idx] - pk
+        Ct = target_covariances(tgt, vox[idx], r, eps)
         C = Ct + R @ Cs[idx] @ R.T
         M = np.linalg.inv(C)
         J = np.concatenate([skew(pk), -np.broadcast_to(np.eye(3), (len(idx), 3, 3))], axis=2)   # (n, 3, 6)
@@ -253,7 +277,7 @@ class GicpResult:
     converged: bool
 
 
-def gicp(occ: VoxelSet, s: np.ndarray, R0: np.ndarray, t0: np.ndarray, r: float, tau: float | None = None,
+def gicp(tgt: Target, s: np.ndarray, R0: np.ndarray, t0: np.ndarray, r: float, tau: float | None = None,
          rho: float | None = None, eps: float = 1e-3, max_iters: int = 30, eps_rot: float = 1e-6,
          eps_trans: float = 1e-6) -> GicpResult:
     tau = r if tau is None else tau
@@ -262,7 +286,7 @@ def gicp(occ: VoxelSet, s: np.ndarray, R0: np.ndarray, t0: np.ndarray, r: float,
     R, t = np.array(R0, np.float64), np.array(t0, np.float64)
     lin = None
     for it in range(1, max_iters + 1):
-        lin = linearize(occ, s, Cs, R, t, r, tau, eps)
+        lin = linearize(tgt, s, Cs, R, t, r, tau, eps)
         if lin.n < 6:
             return GicpResult(R, t, it, lin.cost, lin.n, False)
         delta = np.linalg.solve(lin.H, -lin.g)

@@ -443,6 +443,17 @@ int exact_dilation_needed(const HostGrid& g, double norm_max);
 cudaError_t launch_level_rows(const ScanState& s, int level, float4* out, cudaStream_t st);
 void scan_release(ScanState* s, cudaStream_t st);
 
+// GICP refinement (gicp.cu)
+int gicp_target_build(const float* xyz, int64_t n, int is_device, float r, cudaStream_t st, bbs_gicp_target** out);
+void gicp_target_free(bbs_gicp_target* t);
+int gicp_target_info(const bbs_gicp_target* t, int64_t* n_voxels, int64_t* table_size, int32_t* max_probe);
+int gicp_target_device(const bbs_gicp_target* t);
+int gicp_run(const bbs_gicp_target* tg, const float* xyz, int64_t k, int is_device, const double R0[9],
+             const double t0[3], const bbs_gicp_opts* o, bbs_gicp_result* res);
+int gicp_linearize(const bbs_gicp_target* tg, const float* xyz, int64_t k, int is_device, const double R[9],
+                   const double t[3], const bbs_gicp_opts* o, double H[36], double g[6], double* cost, int64_t* n,
+                   int32_t* vox, uint8_t* found);
+
 // kernels launched from more than one translation unit
 int launch_score_nodes(const bbs_maps* m, const ScanState& s, const int32_t* d_nodes, int64_t n, int32_t* d_scores,
                        int* d_err, cudaStream_t st);

@@ -133,6 +133,51 @@ int bbs_maps_info(const bbs_maps* m, int level, int64_t* n_voxels, int64_t* n_bu
     return BBS_OK;
 }
 
+int bbs_gicp_target_build(const float* xyz, int64_t n, int is_device, float r, void* cuda_stream,
+                          bbs_gicp_target** out)
+{
+    clear_error();
+    if (!out) return set_error(BBS_EINVAL, "gicp_target: NULL out");
+    *out = nullptr;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    DeviceGuard g(dev);
+    return gicp_target_build(xyz, n, is_device, r, (cudaStream_t)cuda_stream, out);
+}
+
+void bbs_gicp_target_free(bbs_gicp_target* t)
+{
+    if (!t) return;
+    DeviceGuard g(gicp_target_device(t));
+    gicp_target_free(t);
+}
+
+int bbs_gicp_target_info(const bbs_gicp_target* t, int64_t* n_voxels, int64_t* table_size, int32_t* max_probe)
+{
+    clear_error();
+    if (!t) return set_error(BBS_EINVAL, "gicp_target_info: NULL target");
+    return gicp_target_info(t, n_voxels, table_size, max_probe);
+}
+
+int bbs_gicp(const bbs_gicp_target* t, const float* scan_xyz, int64_t k, int is_device, const double R0[9],
+             const double t0[3], const bbs_gicp_opts* opts, bbs_gicp_result* out)
+{
+    clear_error();
+    if (!t || !out || !R0 || !t0) return set_error(BBS_EINVAL, "gicp: NULL argument");
+    DeviceGuard g(gicp_target_device(t));
+    return gicp_run(t, scan_xyz, k, is_device, R0, t0, opts, out);
+}
+
+int bbs_gicp_linearize(const bbs_gicp_target* t, const float* scan_xyz, int64_t k, int is_device, const double R[9],
+                       const double tr[3], const bbs_gicp_opts* opts, double H[36], double g[6], double* cost,
+                       int64_t* n, int32_t* voxels, uint8_t* found)
+{
+    clear_error();
+    if (!t || !R || !tr || !H || !g || !cost || !n) return set_error(BBS_EINVAL, "gicp_linearize: NULL argument");
+    DeviceGuard dg(gicp_target_device(t));
+    return gicp_linearize(t, scan_xyz, k, is_device, R, tr, opts, H, g, cost, n, voxels, found);
+}
+
 int bbs_maps_layout(const bbs_maps* m, int level, int32_t* layout)
 {
     clear_error();

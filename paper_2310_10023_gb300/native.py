@@ -73,6 +73,22 @@ class Result(C.Structure):
         }
 
 
+class GicpOpts(C.Structure):
+    """bbs_gicp_opts (0 = default)."""
+    _fields_ = [("max_iters", C.c_int32), ("pad", C.c_int32), ("tau", C.c_double), ("rho", C.c_double),
+                ("cov_eps", C.c_double), ("eps_rot", C.c_double), ("eps_trans", C.c_double),
+                ("cuda_stream", C.c_void_p)]
+
+
+class GicpResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("converged", C.c_int32), ("iterations", C.c_int32),
+                ("correspondences", C.c_int32), ("cost", C.c_double), ("R", C.c_double * 9), ("t", C.c_double * 3),
+                ("pose", C.c_double * 6), ("ms", C.c_double)]
+
+    def Rt(self):
+        return np.array(list(self.R)).reshape(3, 3), np.array(list(self.t))
+
+
 class Tuning(C.Structure):
     """bbs_tuning: launch shape of the search (0 = default)."""
     _fields_ = [("launch_tasks", C.c_int64), ("static_pm", C.c_int32), ("grab_min", C.c_int32),
@@ -121,6 +137,12 @@ def load():
         L.bbs_maps_info.argtypes = [vp, C.c_int, i64p, i64p, i64p, i32p, dp]
         L.bbs_maps_keys.argtypes = [vp, C.c_int, vp, i64, i64p]
         L.bbs_maps_layout.argtypes = [vp, C.c_int, i32p]
+        L.bbs_gicp_target_build.argtypes = [vp, i64, C.c_int, C.c_float, vp, P(C.c_void_p)]
+        L.bbs_gicp_target_free.argtypes = [vp]
+        L.bbs_gicp_target_free.restype = None
+        L.bbs_gicp_target_info.argtypes = [vp, i64p, i64p, i32p]
+        L.bbs_gicp.argtypes = [vp, vp, i64, C.c_int, vp, vp, P(GicpOpts), P(GicpResult)]
+        L.bbs_gicp_linearize.argtypes = [vp, vp, i64, C.c_int, vp, vp, P(GicpOpts), vp, vp, P(C.c_double), i64p, vp, vp]
         L.bbs_pose_grid.argtypes = [vp, vp, i64, C.c_int, P(Ranges), P(Opts), C.c_int, i64p, vp, i64, i64p]
         L.bbs_score_batch.argtypes = [vp, vp, i64, C.c_int, P(Ranges), P(Opts), vp, i64, vp]
         L.bbs_score_children.argtypes = [vp, vp, i64, C.c_int, P(Ranges), P(Opts), vp, i64, vp, vp, i64, i64p]
@@ -388,6 +410,80 @@ def bbs_localize_hostqueue(maps: Maps, scan, ranges: Ranges | None = None, opts:
                                          C.byref(res)), allow_not_found=True)
     del keep
     return res
+
+
+class GicpTarget:
+    """Owned bbs_gicp_target handle (freed on garbage collection)."""
+
+    def __init__(self, h):
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.bbs_gicp_target_free(self.h)
+            self.h = None
+
+
+def bbs_gicp_target_build(xyz, r: float, stream=None) -> GicpTarget:
+    """The GICP target of a map cloud: its points grouped by fine voxel key (centroids)."""
+    p, dev, n, keep = _arr(xyz, np.float32, 3)
+    h = C.c_void_p()
+    _check(load().bbs_gicp_target_build(p, n, dev, float(r), C.c_void_p(stream) if stream else None, C.byref(h)))
+    del keep
+    return GicpTarget(h)
+
+
+def bbs_gicp_target_free(t: GicpTarget) -> None:
+    """Free a target now (otherwise it is freed with the handle object)."""
+    if t.h:
+        load().bbs_gicp_target_free(t.h)
+        t.h = None
+
+
+def bbs_gicp_target_info(t: GicpTarget) -> dict:
+    nv_, ts, mp = C.c_int64(), C.c_int64(), C.c_int32()
+    _check(load().bbs_gicp_target_info(t.h, C.byref(nv_), C.byref(ts), C.byref(mp)))
+    return {"voxels": nv_.value, "table_size": ts.value, "max_probe": mp.value}
+
+
+def make_gicp_opts(max_iters=0, tau=0.0, rho=0.0, cov_eps=0.0, eps_rot=0.0, eps_trans=0.0, stream=None) -> GicpOpts:
+    o = GicpOpts()
+    o.max_iters, o.tau, o.rho, o.cov_eps = int(max_iters), float(tau), float(rho), float(cov_eps)
+    o.eps_rot, o.eps_trans = float(eps_rot), float(eps_trans)
+    o.cuda_stream = C.c_void_p(stream) if stream else None
+    return o
+
+
+def bbs_gicp(target: GicpTarget, scan, R0, t0, opts: GicpOpts | None = None) -> GicpResult:
+    """GICP refinement of a scan's pose (R0, t0) against a target's voxel centroids."""
+    p, dev, k, keep = _arr(scan, np.float32, 3)
+    R = np.ascontiguousarray(R0, np.float64).reshape(9)
+    t = np.ascontiguousarray(t0, np.float64).reshape(3)
+    res = GicpResult()
+    _check(load().bbs_gicp(target.h, p, k, dev, C.c_void_p(R.ctypes.data), C.c_void_p(t.ctypes.data),
+                           C.byref(opts or make_gicp_opts()), C.byref(res)))
+    del keep
+    return res
+
+
+def bbs_gicp_linearize(target: GicpTarget, scan, R, t, opts: GicpOpts | None = None, per_point: bool = True):
+    """One linearization at (R, t) -> (H 6x6, g 6, cost, n, voxels (k, 3), found (k,))."""
+    p, dev, k, keep = _arr(scan, np.float32, 3)
+    Ra = np.ascontiguousarray(R, np.float64).reshape(9)
+    ta = np.ascontiguousarray(t, np.float64).reshape(3)
+    H = np.zeros(36)
+    g = np.zeros(6)
+    cost = C.c_double()
+    n = C.c_int64()
+    vox = np.zeros((max(k, 1), 3), np.int32)
+    found = np.zeros(max(k, 1), np.uint8)
+    _check(load().bbs_gicp_linearize(target.h, p, k, dev, C.c_void_p(Ra.ctypes.data), C.c_void_p(ta.ctypes.data),
+                                     C.byref(opts or make_gicp_opts()), C.c_void_p(H.ctypes.data),
+                                     C.c_void_p(g.ctypes.data), C.byref(cost), C.byref(n),
+                                     C.c_void_p(vox.ctypes.data) if per_point else None,
+                                     C.c_void_p(found.ctypes.data) if per_point else None))
+    del keep
+    return H.reshape(6, 6), g, cost.value, n.value, vox[:k], found[:k].astype(bool)
 
 
 def bbs_localize_many(maps: Maps, scans, ranges: Ranges | None = None, opts: Opts | None = None) -> list:
