@@ -446,6 +446,18 @@ def bbs_gicp_target_info(t: GicpTarget) -> dict:
     return {"voxels": nv_.value, "table_size": ts.value, "max_probe": mp.value}
 
 
+def pose_to_rt(pose):
+    """(x, y, z, roll, pitch, yaw) -> (R, t) with R = Rz(yaw) Ry(pitch) Rx(roll),
+    the library's convention for bbs_result.pose and bbs_gicp."""
+    import math
+    x, y, z, a, b, g = [float(v) for v in pose]
+    ca, sa, cb, sb, cg, sg = math.cos(a), math.sin(a), math.cos(b), math.sin(b), math.cos(g), math.sin(g)
+    R = np.array([[cg * cb, cg * sb * sa - sg * ca, cg * sb * ca + sg * sa],
+                  [sg * cb, sg * sb * sa + cg * ca, sg * sb * ca - cg * sa],
+                  [-sb, cb * sa, cb * ca]])
+    return R, np.array([x, y, z])
+
+
 def make_gicp_opts(max_iters=0, tau=0.0, rho=0.0, cov_eps=0.0, eps_rot=0.0, eps_trans=0.0, stream=None) -> GicpOpts:
     o = GicpOpts()
     o.max_iters, o.tau, o.rho, o.cov_eps = int(max_iters), float(tau), float(rho), float(cov_eps)
