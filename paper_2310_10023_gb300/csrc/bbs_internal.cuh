@@ -389,6 +389,14 @@ inline LevelView level_view(const bbs_maps* m, int l)
     return v;
 }
 
+// every level a byte grid: the scoring kernel's byte-grid-only variant applies
+inline bool maps_all_bytes(const bbs_maps* m)
+{
+    for (int l = 0; l < m->levels; ++l)
+        if (m->lv[l].layout != LAYOUT_BYTES) return false;
+    return m->levels > 0;
+}
+
 // Host pose grid (Sec. III-B Eq. (2)-(5), Sec. III-D Eq. (12)-(14)).
 struct HostGrid {
     int levels;

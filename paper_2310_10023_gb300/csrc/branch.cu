@@ -281,7 +281,7 @@ constexpr int NRUN = 32;   // runs described per round of a CTA
 // chunk), describing every run of a round in parallel (task record, parent,
 // rotation rows), staging a chunk of the scan only when the chunk changes,
 // and adding each run's 8 child counts to the dense scores at the round's end.
-template <int MODE>
+template <int MODE, bool BYTES>
 __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
     branch3_kernel(Plan* __restrict__ P, const SearchDev* __restrict__ Sall, const TaskRec* __restrict__ tasks,
                    int32_t* dense)
@@ -453,7 +453,14 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
             const int n = min(PCHUNK, S.K - d.c * PCHUNK);
             const int jlo = d.b0 * (PBLK / 2), jhi = min(d.b1 * (PBLK / 2), (n + 1) >> 1);
             uint32_t acc0 = 0, acc1 = 0;   // bytes: children (0,4,2,6) and (1,5,3,7)
-            if (Lv.layout == LAYOUT_BYTES && d.inside)
+            if (BYTES) {   // every level of every search is a byte grid: only its path is compiled
+                if (d.inside)
+                    score_run<LAYOUT_BYTES, true>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1],
+                                                  d.kc[2], acc0, acc1);
+                else
+                    score_run<LAYOUT_BYTES>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], acc0,
+                                            acc1);
+            } else if (Lv.layout == LAYOUT_BYTES && d.inside)
                 score_run<LAYOUT_BYTES, true>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2],
                                               acc0, acc1);
             else if (Lv.layout == LAYOUT_BYTES)
@@ -670,11 +677,16 @@ cudaError_t launch_task_rows(const Plan* P, const SearchDev* S, TaskRec* tasks, 
 }
 
 cudaError_t launch_branch(int mode, Plan* P, const SearchDev* S, const TaskRec* tasks, int32_t* dense, int blocks,
-                          cudaStream_t st)
+                          cudaStream_t st, bool bytes_only)
 {
     if (blocks <= 0) return cudaSuccess;
-    if (mode == MODE_INITIAL) branch3_kernel<MODE_INITIAL><<<blocks, 256, 0, st>>>(P, S, tasks, dense);
-    else branch3_kernel<MODE_SEARCH><<<blocks, 256, 0, st>>>(P, S, tasks, dense);
+    if (mode == MODE_INITIAL) {
+        if (bytes_only) branch3_kernel<MODE_INITIAL, true><<<blocks, 256, 0, st>>>(P, S, tasks, dense);
+        else branch3_kernel<MODE_INITIAL, false><<<blocks, 256, 0, st>>>(P, S, tasks, dense);
+    } else {
+        if (bytes_only) branch3_kernel<MODE_SEARCH, true><<<blocks, 256, 0, st>>>(P, S, tasks, dense);
+        else branch3_kernel<MODE_SEARCH, false><<<blocks, 256, 0, st>>>(P, S, tasks, dense);
+    }
     return cudaGetLastError();
 }
 

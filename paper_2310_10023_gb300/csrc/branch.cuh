@@ -190,9 +190,11 @@ constexpr int BRANCH_CTAS_PER_SM = 4;
 
 // scoring and survivor kernels of one launch; `blocks` is the grid (the
 // scoring kernel splits the plan's slices evenly over it, the survivor kernel
-// strides), each returns at once unless the plan is PLAN_OK
+// strides), each returns at once unless the plan is PLAN_OK; bytes_only picks
+// the scoring kernel compiled for byte-grid levels alone (every level of
+// every search of the launch must be one: maps_all_bytes)
 cudaError_t launch_branch(int mode, Plan* P, const SearchDev* S, const TaskRec* tasks, int32_t* dense, int blocks,
-                          cudaStream_t st);
+                          cudaStream_t st, bool bytes_only);
 // survivors (score above their search's best) are appended to the frontier
 // array the next iteration reads, with their bucket counts
 cudaError_t launch_finalize(int mode, const Plan* P, SearchDev* S, const TaskRec* tasks, int32_t* dense,

@@ -407,7 +407,7 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
     cudaError_t e = launch_task_rows(d_plan, d_sd, d_tk, nullptr, nullptr, (int)std::min<int64_t>((ntask + 31) / 32, 4096), st);
     if (e == cudaSuccess)
         e = launch_branch(MODE_SEARCH, d_plan, d_sd, d_tk, d_dense,
-                          (int)std::min<int64_t>(P.n_slices, (int64_t)nsm * BRANCH_CTAS_PER_SM), st);
+                          (int)std::min<int64_t>(P.n_slices, (int64_t)nsm * BRANCH_CTAS_PER_SM), st, maps_all_bytes(m));
     std::vector<int32_t> dense((size_t)total);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dense.data(), d_dense, sizeof(int32_t) * dense.size(), cudaMemcpyDeviceToHost, st);

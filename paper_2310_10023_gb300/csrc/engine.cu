@@ -607,6 +607,18 @@ int Engine::init()
     return BBS_OK;
 }
 
+// every search in use scores against byte-grid levels only
+bool Engine::bytes_only() const
+{
+    bool any = false;
+    for (const SearchHost& h : hosts_) {
+        if (!(h.live || h.fresh) || !h.maps) continue;
+        if (!maps_all_bytes(h.maps)) return false;
+        any = true;
+    }
+    return any;
+}
+
 int Engine::begin_run(cudaStream_t st, bool timed)
 {
     st_ = st;
@@ -992,7 +1004,7 @@ int Engine::build_graph()
         launch_select(cs, cond, 1);
         launch_compact(cs);
         launch_task_rows(d_plan_, d_S_, tasks_, &front_, d_ls_, nsm_ * 4, cs);
-        launch_branch(MODE_SEARCH, d_plan_, d_S_, tasks_, dense_, nsm_ * tune_.ctas_per_sm, cs);
+        launch_branch(MODE_SEARCH, d_plan_, d_S_, tasks_, dense_, nsm_ * tune_.ctas_per_sm, cs, graph_bytes_);
         launch_finalize(MODE_SEARCH, d_plan_, d_S_, tasks_, dense_, front_, d_ls_, nsm_ * 8, cs);
         cudaGraph_t out = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cs, &out);
@@ -1015,7 +1027,15 @@ int Engine::iterate(int max_iters, std::vector<int>* finished)
     if (host_driven_ || timed_) return step(finished);
     finish_never_live(finished);
     if (live_count() == 0) return BBS_OK;
-    if (!exec_) BBS_TRY(build_graph());
+    const bool bo = bytes_only();
+    if (exec_ && bo != graph_bytes_) {   // the graph holds the scoring kernel variant it was captured with
+        cudaGraphExecDestroy(exec_);
+        exec_ = nullptr;
+    }
+    if (!exec_) {
+        graph_bytes_ = bo;
+        BBS_TRY(build_graph());
+    }
     h_plan_.iters = 0;
     h_plan_.max_iters = max_iters > 0 ? max_iters : 1;
     BBS_CUDA_TRY(cudaMemcpyAsync(&d_plan_->iters, &h_plan_.iters, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, st_));
@@ -1172,7 +1192,7 @@ int Engine::score_launch(int mode, const std::vector<Seg>* segs, int64_t n_slice
         evs_.push_back(e1);
         BBS_CUDA_TRY(cudaEventRecord(e0, st_));
     }
-    BBS_CUDA_TRY(launch_branch(mode, d_plan_, d_S_, tasks_, dense_, nsm_ * tune_.ctas_per_sm, st_));
+    BBS_CUDA_TRY(launch_branch(mode, d_plan_, d_S_, tasks_, dense_, nsm_ * tune_.ctas_per_sm, st_, bytes_only()));
     if (timed_) BBS_CUDA_TRY(cudaEventRecord(e1, st_));
     BBS_CUDA_TRY(launch_finalize(mode, d_plan_, d_S_, tasks_, dense_, front_, d_ls_, nsm_ * 8, st_));
     BBS_CUDA_TRY(cudaGetLastError());

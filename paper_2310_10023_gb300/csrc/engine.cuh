@@ -118,6 +118,8 @@ class Engine {
     Plan h_plan_{};
     int nsm_ = 152;
     cudaGraphExec_t exec_ = nullptr;
+    bool graph_bytes_ = false;     // the graph's scoring kernel is the byte-grid-only variant
+    bool bytes_only() const;
     bool host_driven_ = false;
     std::vector<void*> fixed_;
     std::vector<SearchHost> hosts_;

@@ -154,7 +154,8 @@ int hostqueue_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device,
                                           (int)std::min<int64_t>((n + 31) / 32, 4 * nsm), st));
         }
         BBS_CUDA_TRY(launch_branch(MODE_SEARCH, D.plan, D.sd, D.tasks, D.dense,
-                                   (int)std::min<int64_t>(P.n_slices, (int64_t)nsm * tn.ctas_per_sm), st));
+                                   (int)std::min<int64_t>(P.n_slices, (int64_t)nsm * tn.ctas_per_sm), st,
+                                   maps_all_bytes(m)));
         dense.resize((size_t)(8 * n));
         BBS_CUDA_TRY(cudaMemcpyAsync(dense.data(), D.dense, sizeof(int32_t) * dense.size(), cudaMemcpyDeviceToHost, st));
         BBS_CUDA_TRY(cudaStreamSynchronize(st));   // P, tk and dense are host memory of this call

@@ -585,3 +585,22 @@ def test_dfs_refused_by_device_engine(nv, room_pair):
     with pytest.raises(nv.BBSError) as e:
         nv.bbs_localize(dm, s, nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch, flags=nv.SEARCH_DFS))
     assert e.value.code == nv.EINVAL
+
+
+def test_engine_switches_kernel_variant_with_the_maps(nv, room_pair):
+    """Byte-grid maps and hashed maps used alternately by the cached engines:
+    the loop graph is recaptured with the matching scoring kernel each time,
+    and every result equals the oracle's."""
+    w, m, dm, om = room_pair
+    nv.bbs_set_probe_layout(2)
+    try:
+        hashed = nv.bbs_build_maps(m, w.r, w.levels)
+    finally:
+        nv.bbs_set_probe_layout(0)
+    assert nv.bbs_maps_layout(hashed, 0) == nv.LAYOUT_COMPACT and nv.bbs_maps_layout(dm, 0) == nv.LAYOUT_BYTES
+    nr, orr = _ranges(nv, w)
+    op = nv.make_opts(score_frac=w.score_frac, batch=w.batch)
+    for i, maps in enumerate([dm, hashed, dm, hashed]):
+        s, _ = synth.make_scan(1, i % 2)
+        ores = oracle.localize(om, s, orr, score_frac=w.score_frac, batch=w.batch)
+        _same_search(nv.bbs_localize(maps, s, nr, op), ores)
