@@ -20,7 +20,8 @@ GPU path, each stated where it is used):
   the (biased) sample covariance of the neighbourhood (target: the centroids
   of the occupied voxels of the 3 x 3 x 3 block around u; source: scan points
   within radius rho of the point); tr S = 0 gives C = r^2 I.  Sums run over
-  neighbours in block or index order.
+  neighbours in block or index order (the GPU sums the source neighbourhoods
+  in a different fixed order: those covariances agree to FP64 rounding).
 * Pose T = (R, t), R = Rz(yaw) Ry(pitch) Rx(roll); a step (w, v) maps p to
   Exp(w) p + v, so the residual d = c - p has Jacobian [ [p]_x | -I ];
   Gauss-Newton on sum_i d_i^T M_i d_i with M_i = (C_t + R C_s R^T)^-1 held

@@ -12,7 +12,7 @@
 // voxel, and add the point's Gauss-Newton terms (J^T M J, J^T M d, d^T M d
 // with J = [ [p]_x | -I ], M = (C_t + R C_s R^T)^-1) to per-CTA partial sums,
 // reduced in a fixed order.  The source covariances come once per scan from
-// the scan points within rho.  The host solves the 6 x 6 system and applies
+// the scan points within rho (one warp per point).  The host solves the 6 x 6 system and applies
 // the step p -> Exp(w) p + v.
 #include <chrono>
 #include <cmath>
@@ -25,13 +25,14 @@ namespace bbs {
 
 namespace {
 
-constexpr int GT = 256;         // threads per CTA
+constexpr int GT = 64;          // threads per CTA: a scan of 8 k points spreads over 128 SMs
 constexpr int NACC = 29;        // H (21 upper-triangle entries), g (6), cost, count
 constexpr double FIX = 4294967296.0;   // 2^32: fixed-point scale of the centroid sums
 constexpr unsigned long long GEMPTY = ~0ull;
 
 // one voxel of the target: key (21 bits per axis, offset 2^20), point count,
-// sums of rint((x - u r) 2^32) per axis
+// sums of rint((x - u r) 2^32) per axis while building, then the centroid
+// u r + (sum / count) 2^-32 in place of the sums
 struct GicpSlot {
     unsigned long long key;
     unsigned long long count;
@@ -71,10 +72,7 @@ __device__ __forceinline__ bool target_centroid(const TargetView& T, int32_t x, 
         const GicpSlot& q = T.slots[(s + (uint32_t)p) & T.mask];
         const unsigned long long k = q.key;
         if (k == key) {
-            const double n = (double)q.count;
-            const int32_t u[3] = {x, y, z};
-            for (int a = 0; a < 3; ++a)
-                c[a] = dadd(dmul((double)u[a], T.r), __ddiv_rn(__ddiv_rn((double)q.sum[a], n), FIX));
+            for (int a = 0; a < 3; ++a) c[a] = __longlong_as_double(q.sum[a]);
             return true;
         }
         if (k == GEMPTY) return false;
@@ -121,6 +119,20 @@ __global__ void target_insert_kernel(const float* __restrict__ xyz, int64_t n, f
     }
 }
 
+// the sums of every occupied slot replaced by the centroid
+__global__ void target_centroid_kernel(GicpSlot* slots, int64_t T, double r)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < T; i += (int64_t)gridDim.x * blockDim.x) {
+        GicpSlot& q = slots[i];
+        if (q.key == GEMPTY) continue;
+        const double n = (double)q.count;
+        const int32_t u[3] = {(int32_t)((q.key >> 42) & 0x1FFFFF) - KEY_LIMIT, (int32_t)((q.key >> 21) & 0x1FFFFF) - KEY_LIMIT,
+                              (int32_t)(q.key & 0x1FFFFF) - KEY_LIMIT};
+        for (int a = 0; a < 3; ++a)
+            q.sum[a] = __double_as_longlong(dadd(dmul((double)u[a], r), __ddiv_rn(__ddiv_rn((double)q.sum[a], n), FIX)));
+    }
+}
+
 __global__ void target_clear_kernel(GicpSlot* slots, int64_t T)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < T; i += (int64_t)gridDim.x * blockDim.x) {
@@ -149,62 +161,57 @@ __device__ __forceinline__ void normalized(const double S[6], double r, double e
 }
 
 // Source covariances: scan points within rho of point i (FP64 distance of the
-// exact coordinate differences, the point itself included), sums in index
-// order.  An FP32 distance prefilter skips pairs that lie clearly outside
-// (the FP32 value is within 1e-6 relative of the FP64 one).
-__global__ void __launch_bounds__(GT) source_cov_kernel(const float* __restrict__ xyz, int64_t k, double rho2,
-                                                        float rho2_skip, double r, double eps, double* __restrict__ Cs)
+// exact coordinate differences, the point itself included).  One warp per
+// point: lane l takes the points l, l + 32, ..., and the lanes' sums meet in
+// a fixed butterfly (deterministic; the order differs from a sequential sum
+// only by FP64 rounding).  An FP32 distance prefilter skips pairs that lie
+// clearly outside (the FP32 value is within 1e-6 relative of the FP64 one).
+__device__ __forceinline__ double warp_sum_d(double v)
 {
-    __shared__ float tile[GT * 3];
-    const int64_t i = (int64_t)blockIdx.x * GT + threadIdx.x;
-    const bool live = i < k;
-    float fx = 0.f, fy = 0.f, fz = 0.f;
-    if (live) fx = xyz[3 * i], fy = xyz[3 * i + 1], fz = xyz[3 * i + 2];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(256) source_cov_kernel(const float* __restrict__ xyz, int64_t k, double rho2,
+                                                         float rho2_skip, double r, double eps, double* __restrict__ Cs)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= k) return;   // uniform per warp
+    const float fx = xyz[3 * i], fy = xyz[3 * i + 1], fz = xyz[3 * i + 2];
     const double sx = fx, sy = fy, sz = fz;
-    // pass 1: count and sum; pass 2: the scatter about the mean
     double cnt = 0.0, ax = 0.0, ay = 0.0, az = 0.0;
-    double mx = 0.0, my = 0.0, mz = 0.0;
-    double S[6] = {0, 0, 0, 0, 0, 0};
-    for (int pass = 0; pass < 2; ++pass) {
-        for (int64_t j0 = 0; j0 < k; j0 += GT) {
-            __syncthreads();
-            for (int q = threadIdx.x; q < 3 * GT; q += GT) {
-                const int64_t g = 3 * j0 + q;
-                tile[q] = g < 3 * k ? xyz[g] : 0.f;
-            }
-            __syncthreads();
-            if (!live) continue;
-            const int nj = (int)min((int64_t)GT, k - j0);
-            for (int jj = 0; jj < nj; ++jj) {
-                const float tx = tile[3 * jj], ty = tile[3 * jj + 1], tz = tile[3 * jj + 2];
-                const float ex = fx - tx, ey = fy - ty, ez = fz - tz;
-                if (ex * ex + ey * ey + ez * ez > rho2_skip) continue;
-                const double dx = dsub(sx, (double)tx), dy = dsub(sy, (double)ty), dz = dsub(sz, (double)tz);
-                if (dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz)) > rho2) continue;
-                if (pass == 0) {
-                    cnt = dadd(cnt, 1.0);
-                    ax = dadd(ax, (double)tx);
-                    ay = dadd(ay, (double)ty);
-                    az = dadd(az, (double)tz);
-                } else {
-                    const double qx = dsub((double)tx, mx), qy = dsub((double)ty, my), qz = dsub((double)tz, mz);
-                    S[0] = dadd(S[0], dmul(qx, qx));
-                    S[1] = dadd(S[1], dmul(qx, qy));
-                    S[2] = dadd(S[2], dmul(qx, qz));
-                    S[3] = dadd(S[3], dmul(qy, qy));
-                    S[4] = dadd(S[4], dmul(qy, qz));
-                    S[5] = dadd(S[5], dmul(qz, qz));
-                }
-            }
-        }
-        if (pass == 0 && live) {
-            mx = __ddiv_rn(ax, cnt);
-            my = __ddiv_rn(ay, cnt);
-            mz = __ddiv_rn(az, cnt);
-        }
+    for (int64_t j = lane; j < k; j += 32) {
+        const float tx = xyz[3 * j], ty = xyz[3 * j + 1], tz = xyz[3 * j + 2];
+        const float ex = fx - tx, ey = fy - ty, ez = fz - tz;
+        if (ex * ex + ey * ey + ez * ez > rho2_skip) continue;
+        const double dx = dsub(sx, (double)tx), dy = dsub(sy, (double)ty), dz = dsub(sz, (double)tz);
+        if (dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz)) > rho2) continue;
+        cnt = dadd(cnt, 1.0);
+        ax = dadd(ax, (double)tx);
+        ay = dadd(ay, (double)ty);
+        az = dadd(az, (double)tz);
     }
-    if (!live) return;
-    for (int q = 0; q < 6; ++q) S[q] = __ddiv_rn(S[q], cnt);
+    cnt = warp_sum_d(cnt);
+    const double mx = __ddiv_rn(warp_sum_d(ax), cnt), my = __ddiv_rn(warp_sum_d(ay), cnt),
+                 mz = __ddiv_rn(warp_sum_d(az), cnt);
+    double S[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t j = lane; j < k; j += 32) {
+        const float tx = xyz[3 * j], ty = xyz[3 * j + 1], tz = xyz[3 * j + 2];
+        const float ex = fx - tx, ey = fy - ty, ez = fz - tz;
+        if (ex * ex + ey * ey + ez * ez > rho2_skip) continue;
+        const double dx = dsub(sx, (double)tx), dy = dsub(sy, (double)ty), dz = dsub(sz, (double)tz);
+        if (dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz)) > rho2) continue;
+        const double qx = dsub((double)tx, mx), qy = dsub((double)ty, my), qz = dsub((double)tz, mz);
+        S[0] = dadd(S[0], dmul(qx, qx));
+        S[1] = dadd(S[1], dmul(qx, qy));
+        S[2] = dadd(S[2], dmul(qx, qz));
+        S[3] = dadd(S[3], dmul(qy, qy));
+        S[4] = dadd(S[4], dmul(qy, qz));
+        S[5] = dadd(S[5], dmul(qz, qz));
+    }
+    for (int q = 0; q < 6; ++q) S[q] = __ddiv_rn(warp_sum_d(S[q]), cnt);
+    if (lane) return;
     double C[6];
     normalized(S, r, eps, C);
     for (int q = 0; q < 6; ++q) Cs[6 * i + q] = C[q];
@@ -485,7 +492,8 @@ int prepare(const float* xyz, int64_t k, int is_device, const Params& P, GicpBuf
     BBS_CUDA_TRY(cudaMallocAsync((void**)&B.partial, sizeof(double) * NACC * (size_t)nblk, B.st));
     BBS_CUDA_TRY(cudaMallocAsync((void**)&B.out, sizeof(double) * NACC, B.st));
     const double rho2 = P.rho * P.rho;
-    source_cov_kernel<<<nblk, GT, 0, B.st>>>(d_xyz, k, rho2, (float)(rho2 * (1.0 + 1e-5)), P.r, P.eps, B.Cs);
+    source_cov_kernel<<<(unsigned)((k * 32 + 255) / 256), 256, 0, B.st>>>(d_xyz, k, rho2, (float)(rho2 * (1.0 + 1e-5)),
+                                                                       P.r, P.eps, B.Cs);
     BBS_CUDA_TRY(cudaGetLastError());
     return BBS_OK;
 }
@@ -595,6 +603,11 @@ int gicp_target_build(const float* xyz, int64_t n, int is_device, float r, cudaS
             break;
         }
         if (hs[0]) continue;   // a probe ran past 64 slots: a larger table
+        target_centroid_kernel<<<blocks, 256, 0, st>>>(t->slots, T, (double)r);
+        if (cudaGetLastError() != cudaSuccess) {
+            rc = set_error(BBS_ECUDA, "gicp_target: centroids failed");
+            break;
+        }
         t->T = T;
         t->log2T = lt;
         t->maxp = hs[2];
