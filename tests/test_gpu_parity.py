@@ -78,6 +78,28 @@ def test_random_cloud_maps_with_negative_keys(nv, seed):
             assert _keyset(nv.bbs_maps_keys(dm, l)) == _keyset(om.keys(l)), (r, l)
 
 
+def test_sparse_map_falls_back_to_hashed_levels(nv, room_pair):
+    """The room map plus a copy 4.2 km away (3 km in x and y): the fine levels' boxes are then far
+    too sparse for a byte grid, so the default layout hashes them (the
+    coarsest levels may still qualify); key sets, scores and a search equal
+    the oracle's."""
+    w, m, _, _ = room_pair
+    far = m + np.array([3000.0, 3000.0, 0.0], np.float32)
+    both = np.concatenate([m, far]).astype(np.float32)
+    dm = nv.bbs_build_maps(both, w.r, w.levels)
+    om = oracle.Maps(both, w.r, w.levels)
+    assert nv.bbs_maps_layout(dm, 0) in (nv.LAYOUT_COMPACT, nv.LAYOUT_WIDE)
+    for l in range(w.levels):
+        assert _keyset(nv.bbs_maps_keys(dm, l)) == _keyset(om.keys(l)), l
+    s, _ = synth.make_scan(1, 0)
+    nr, orr = _ranges(nv, w)
+    g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), orr)
+    nodes = _random_nodes(g, np.random.default_rng(8), 800, w.levels)
+    assert np.array_equal(nv.bbs_score_batch(dm, s, nodes, nr), om.score_nodes(g, s, nodes))
+    res = nv.bbs_localize(dm, s, nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch))
+    _same_search(res, oracle.localize(om, s, orr, score_frac=w.score_frac, batch=w.batch))
+
+
 def test_map_errors(nv):
     with pytest.raises(nv.BBSError) as e:
         nv.bbs_build_maps(np.array([[np.nan, 0, 0]], np.float32), 0.5, 2)
