@@ -621,7 +621,7 @@ def run_ours(a):
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(_workload_desc(w, len(m), statistics.mean(len(s) for s in scans), a.scans),
-                           launch_shape=tuning or dict(nv.bbs_get_tuning(), load_factor=0.25, source="defaults"),
+                           launch_shape=tuning or dict(nv.bbs_get_tuning(), layout=0, load_factor=0.25, source="defaults"),
                            map_layout=sorted({nv.LAYOUT_NAMES[nv.bbs_maps_layout(maps, l)] for l in range(w.levels)})),
             "ms_to_optimum": to_opt,
             "ms_total_per_scan": total_ms / a.steps,

@@ -183,8 +183,9 @@ int  bbs_maps_info(const bbs_maps* maps, int level, int64_t* n_voxels, int64_t* 
 #define BBS_LAYOUT_BYTES   3
 int  bbs_maps_layout(const bbs_maps* maps, int level, int32_t* layout);
 
-/* Target load (buckets in use / buckets) of the tables built by later
- * bbs_build_maps calls in this process; default 0.25.  Sec. III-C enlarges
+/* Target load (buckets in use / buckets) of the hashed level tables built by
+ * later bbs_build_maps calls in this process (byte grids and dense bricks
+ * have none); default 0.25.  Sec. III-C enlarges
  * T_l until few keys collide; the load trades the collision rate (probe
  * length) against the table's footprint in L2.  BBS_EINVAL outside
  * (0.01, 0.9]. */

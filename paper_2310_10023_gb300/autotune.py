@@ -1,10 +1,11 @@
 """Launch-shape autotuner for the batched search (the tile / layout choices
 of the scoring path), with a JSON cache keyed by GPU and workload shape.
 
-What is tuned never changes a result: the table load factor of the level
-maps (probe length vs footprint), the share of a scoring launch split
-statically over the CTAs, the smallest dynamic grab, and the scoring CTAs per
-SM.  The batch size b is part of the search's definition (it changes the
+What is tuned never changes a result: the level maps' layout (byte grids
+where a level's box allows, or hashed bricks everywhere), the load factor of
+the hashed tables (probe length vs footprint; byte grids have none), the
+share of a scoring launch split statically over the CTAs, the smallest
+dynamic grab, and the scoring CTAs per SM.  The batch size b is part of the search's definition (it changes the
 trajectory, Algorithm 2) and is not tuned.  Every candidate's results are
 compared with the first candidate's; a candidate that differs is an error.
 
@@ -22,8 +23,9 @@ import time
 
 from . import native as nv
 
-DEFAULT = {"load_factor": 0.25, "static_pm": 750, "grab_min": 16, "ctas_per_sm": 4}
+DEFAULT = {"layout": 0, "load_factor": 0.25, "static_pm": 750, "grab_min": 16, "ctas_per_sm": 4}
 SPACE = {
+    "layout": [0, 2],
     "load_factor": [0.5, 0.35, 0.25, 0.15],
     "static_pm": [500, 750, 875],
     "grab_min": [8, 16, 32],
@@ -67,8 +69,9 @@ def store(key: str, entry: dict, path: str | None = None) -> None:
 
 
 def apply(cfg: dict) -> None:
-    """Make cfg the library's launch shape and map load factor (maps built
-    after this call use the load factor)."""
+    """Make cfg the library's launch shape, map layout and load factor (maps
+    built after this call use the layout and the load factor)."""
+    nv.bbs_set_probe_layout(int(cfg.get("layout", DEFAULT["layout"])))
     nv.bbs_set_load_factor(float(cfg.get("load_factor", DEFAULT["load_factor"])))
     nv.bbs_set_tuning(static_pm=int(cfg.get("static_pm", DEFAULT["static_pm"])),
                       grab_min=int(cfg.get("grab_min", DEFAULT["grab_min"])),
@@ -83,8 +86,8 @@ def search(build_maps, scans, ranges, opts, reps: int = 3, space: dict | None = 
            sync=None) -> dict:
     """Coordinate descent over `space` (default SPACE).
 
-    build_maps() -> maps handle (called again whenever the load factor
-    changes); scans: device-resident point arrays; timer/sync: clock and
+    build_maps() -> maps handle (called again whenever the layout or the
+    load factor changes); scans: device-resident point arrays; timer/sync: clock and
     device synchronization (defaults: time.perf_counter and
     torch.cuda.synchronize).  Returns {"best": cfg, "ms": per-pass ms,
     "trials": [...]}.
@@ -99,16 +102,17 @@ def search(build_maps, scans, ranges, opts, reps: int = 3, space: dict | None = 
     trials = []
     maps_cache = {}
 
-    def maps_for(lf):
-        if lf not in maps_cache:
+    def maps_for(layout, lf):
+        if (layout, lf) not in maps_cache:
+            nv.bbs_set_probe_layout(layout)
             nv.bbs_set_load_factor(lf)
-            maps_cache[lf] = build_maps()
-        return maps_cache[lf]
+            maps_cache[(layout, lf)] = build_maps()
+        return maps_cache[(layout, lf)]
 
     def run(cfg):
         nonlocal ref
         apply(cfg)
-        m = maps_for(cfg["load_factor"])
+        m = maps_for(cfg.get("layout", DEFAULT["layout"]), cfg["load_factor"])
         keys = [_result_key(nv.bbs_localize(m, s, ranges, opts)) for s in scans]   # warm-up + check
         if ref is None:
             ref = keys

@@ -34,7 +34,7 @@ def test_autotune_keeps_results(tmp_path):
     rg = nv.make_ranges(w.lo, w.hi, w.ang_lo, w.ang_hi)
     op = nv.make_opts(score_frac=w.score_frac, batch=w.batch)
     p = str(tmp_path / "tuning.json")
-    space = {"load_factor": [0.5, 0.25], "static_pm": [500, 750], "ctas_per_sm": [3, 4]}
+    space = {"layout": [0, 2], "load_factor": [0.5, 0.25], "static_pm": [500, 750], "ctas_per_sm": [3, 4]}
     try:
         out = autotune.tuned("gpu", 1, lambda: nv.bbs_build_maps(m, w.r, w.levels), scans, rg, op, w.r, w.levels,
                              [len(s) for s in scans], path=p, reps=1, space=space)
@@ -44,3 +44,4 @@ def test_autotune_keeps_results(tmp_path):
     finally:
         nv.bbs_set_tuning(reset=True)
         nv.bbs_set_load_factor(0.25)
+        nv.bbs_set_probe_layout(0)
