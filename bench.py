@@ -59,6 +59,25 @@ def _dist():
     return ws, rank, local
 
 
+def reduce_over_ranks(torch, ws, total_ms, e2e_ms, probes, e2e_probes, device):
+    """Whole-job figures of a replicas-only run: the slowest rank's times
+    (max) and every rank's probes (sum); identity on one rank."""
+    vals = torch.tensor([total_ms, e2e_ms, probes, e2e_probes], dtype=torch.float64, device=device)
+    if ws > 1:
+        mx = vals[:2].clone()
+        sm = vals[2:].clone()
+        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+        vals = torch.cat([mx, sm])
+    return tuple(vals.tolist())
+
+
+def rank_scans(rank: int, n: int) -> list:
+    """Scan indices of one rank: each rank localizes its own n scans (replicas
+    only, no data exchange)."""
+    return [rank * n + i for i in range(n)]
+
+
 def _workload_desc(w, m_points, k_mean, scans):
     return {"workload": f"indoor multi-room floor 100x60x10 m, {m_points / 1e6:.2f} M map points, "
                         f"r={w.r} m, {w.levels} levels; 16-beam scans of ~{k_mean:.0f} points",
@@ -490,7 +509,7 @@ def run_ours(a):
     w = synth.WORKLOADS[WORKLOAD]
     m = synth.make_map(w.scene)
     md = torch.from_numpy(np.array(m)).to(dev)
-    scans = [synth.make_scan(w.scene, rank * a.scans + i)[0] for i in range(a.scans)]
+    scans = [synth.make_scan(w.scene, i)[0] for i in rank_scans(rank, a.scans)]
     scans_d = [torch.from_numpy(s).to(dev) for s in scans]
     tuning = None
     if a.autotune:
@@ -592,14 +611,8 @@ def run_ours(a):
     achieved_gbs = units_per_s * 32 / 1e9
 
     # ---- reduce over ranks ----------------------------------------------------
-    vals = torch.tensor([total_ms, e2e_total, probes, e2e_probes], dtype=torch.float64, device=dev)
-    if ws > 1:
-        mx = vals[:2].clone()
-        sm = vals[2:].clone()
-        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
-        vals = torch.cat([mx, sm])
-    total_ms, e2e_total, probes_all, e2e_probes_all = vals.tolist()
+    total_ms, e2e_total, probes_all, e2e_probes_all = reduce_over_ranks(torch, ws, total_ms, e2e_total, probes,
+                                                                        e2e_probes, dev)
 
     batched = served = exact = outdoor = host_queue = refine = None
     if rank == 0 and ws == 1 and not a.no_forms:
