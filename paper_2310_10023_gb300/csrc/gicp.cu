@@ -31,8 +31,9 @@ constexpr double FIX = 4294967296.0;   // 2^32: fixed-point scale of the centroi
 constexpr unsigned long long GEMPTY = ~0ull;
 
 // one voxel of the target: key (21 bits per axis, offset 2^20), point count,
-// sums of rint((x - u r) 2^32) per axis while building, then the centroid
-// u r + (sum / count) 2^-32 in place of the sums
+// sums of rint((x - u r) 2^32) per axis while building; then the centroid
+// u r + (sum / count) 2^-32 in place of the sums, and in place of the count
+// the voxel's row of the covariance array
 struct GicpSlot {
     unsigned long long key;
     unsigned long long count;
@@ -41,6 +42,7 @@ struct GicpSlot {
 
 struct TargetView {
     const GicpSlot* slots;
+    const double* cov;   // per voxel: C_t (xx, xy, xz, yy, yz, zz), row in the slot's count word
     uint32_t shift, mask;
     int32_t maxp;
     int32_t pad;
@@ -62,22 +64,28 @@ __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a,
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
 
-// centroid of voxel (x, y, z): u r + (sum / n) 2^-32 per axis; false when empty
-__device__ __forceinline__ bool target_centroid(const TargetView& T, int32_t x, int32_t y, int32_t z, double c[3])
+// the slot of voxel (x, y, z), or null when the voxel is empty
+__device__ __forceinline__ const GicpSlot* target_slot(const TargetView& T, int32_t x, int32_t y, int32_t z)
 {
-    if (!(key_in_range(x) && key_in_range(y) && key_in_range(z))) return false;
+    if (!(key_in_range(x) && key_in_range(y) && key_in_range(z))) return nullptr;
     const unsigned long long key = voxel_pack(x, y, z);
     const uint32_t s = brick_hash(x, y, z) >> T.shift;
     for (int p = 0; p <= T.maxp; ++p) {
-        const GicpSlot& q = T.slots[(s + (uint32_t)p) & T.mask];
-        const unsigned long long k = q.key;
-        if (k == key) {
-            for (int a = 0; a < 3; ++a) c[a] = __longlong_as_double(q.sum[a]);
-            return true;
-        }
-        if (k == GEMPTY) return false;
+        const GicpSlot* q = T.slots + ((s + (uint32_t)p) & T.mask);
+        const unsigned long long k = q->key;
+        if (k == key) return q;
+        if (k == GEMPTY) return nullptr;
     }
-    return false;
+    return nullptr;
+}
+
+// centroid of voxel (x, y, z) (stored in the slot after the build); false when empty
+__device__ __forceinline__ bool target_centroid(const TargetView& T, int32_t x, int32_t y, int32_t z, double c[3])
+{
+    const GicpSlot* q = target_slot(T, x, y, z);
+    if (!q) return false;
+    for (int a = 0; a < 3; ++a) c[a] = __longlong_as_double(q->sum[a]);
+    return true;
 }
 
 // every map point into its voxel: key, count and fixed-point sums; st[0]
@@ -156,6 +164,65 @@ __device__ __forceinline__ void normalized(const double S[6], double r, double e
         } else {
             v = diag ? 1.0 : 0.0;
         }
+        C[k] = dmul(v, r2);
+    }
+}
+
+// Per occupied voxel of the target, the shape S / tr S of the centroids of
+// the occupied voxels of its 3 x 3 x 3 block (sums in (dx, dy, dz) order), or
+// -1 in the first entry when tr S = 0; written to its own row of `cov` and
+// the row stored in the slot's count word.  C_t = r^2 (shape + eps I) is
+// formed at use, so eps stays a per-call option.
+__global__ void target_cov_kernel(TargetView T, int64_t nslots, GicpSlot* slots, double* cov,
+                                  unsigned long long* rows)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nslots; i += (int64_t)gridDim.x * blockDim.x) {
+        GicpSlot& q = slots[i];
+        if (q.key == GEMPTY) continue;
+        const int32_t v[3] = {(int32_t)((q.key >> 42) & 0x1FFFFF) - KEY_LIMIT, (int32_t)((q.key >> 21) & 0x1FFFFF) - KEY_LIMIT,
+                              (int32_t)(q.key & 0x1FFFFF) - KEY_LIMIT};
+        double cnt = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+        for (int dx = -1; dx <= 1; ++dx)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dz = -1; dz <= 1; ++dz) {
+                    double c[3];
+                    if (!target_centroid(T, v[0] + dx, v[1] + dy, v[2] + dz, c)) continue;
+                    cnt = dadd(cnt, 1.0);
+                    sx = dadd(sx, c[0]);
+                    sy = dadd(sy, c[1]);
+                    sz = dadd(sz, c[2]);
+                }
+        const double mx = __ddiv_rn(sx, cnt), my = __ddiv_rn(sy, cnt), mz = __ddiv_rn(sz, cnt);
+        double S[6] = {0, 0, 0, 0, 0, 0};
+        for (int dx = -1; dx <= 1; ++dx)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dz = -1; dz <= 1; ++dz) {
+                    double c[3];
+                    if (!target_centroid(T, v[0] + dx, v[1] + dy, v[2] + dz, c)) continue;
+                    const double ex = dsub(c[0], mx), ey = dsub(c[1], my), ez = dsub(c[2], mz);
+                    S[0] = dadd(S[0], dmul(ex, ex));
+                    S[1] = dadd(S[1], dmul(ex, ey));
+                    S[2] = dadd(S[2], dmul(ex, ez));
+                    S[3] = dadd(S[3], dmul(ey, ey));
+                    S[4] = dadd(S[4], dmul(ey, ez));
+                    S[5] = dadd(S[5], dmul(ez, ez));
+                }
+        for (int k = 0; k < 6; ++k) S[k] = __ddiv_rn(S[k], cnt);
+        const double tr = dadd(dadd(S[0], S[3]), S[5]);
+        const unsigned long long row = atomicAdd(rows, 1ull);
+        for (int k = 0; k < 6; ++k) cov[6 * row + k] = tr > 0.0 ? __ddiv_rn(S[k], tr) : (k == 0 ? -1.0 : 0.0);
+        q.count = row;
+    }
+}
+
+// C_t = r^2 (shape + eps I), or r^2 I for an isolated voxel, as normalized() forms it
+__device__ __forceinline__ void target_cov_at_use(const double* shape, double r, double eps, double C[6])
+{
+    const double r2 = dmul(r, r);
+    const bool iso = shape[0] < 0.0;
+    for (int k = 0; k < 6; ++k) {
+        const bool diag = k == 0 || k == 3 || k == 5;
+        const double v = iso ? (diag ? 1.0 : 0.0) : (diag ? dadd(shape[k], eps) : shape[k]);
         C[k] = dmul(v, r2);
     }
 }
@@ -265,17 +332,20 @@ __global__ void __launch_bounds__(GT) linearize_kernel(TargetView TG, const floa
         double best = INFINITY;
         int32_t bv[3] = {0, 0, 0};
         double bc[3] = {0.0, 0.0, 0.0};
+        const GicpSlot* bslot = nullptr;
         for (int dx = -1; dx <= 1; ++dx)
             for (int dy = -1; dy <= 1; ++dy)
                 for (int dz = -1; dz <= 1; ++dz) {
                     const int32_t w[3] = {base[0] + dx, base[1] + dy, base[2] + dz};
-                    double c[3];
-                    if (!target_centroid(TG, w[0], w[1], w[2], c)) continue;
-                    double e[3];
+                    const GicpSlot* q = target_slot(TG, w[0], w[1], w[2]);
+                    if (!q) continue;
+                    double c[3], e[3];
+                    for (int a = 0; a < 3; ++a) c[a] = __longlong_as_double(q->sum[a]);
                     for (int a = 0; a < 3; ++a) e[a] = dsub(p[a], c[a]);
                     const double d2 = dadd(dadd(dmul(e[0], e[0]), dmul(e[1], e[1])), dmul(e[2], e[2]));
                     if (d2 < best) {
                         best = d2;
+                        bslot = q;
                         for (int a = 0; a < 3; ++a) bv[a] = w[a], bc[a] = c[a];
                     }
                 }
@@ -287,36 +357,9 @@ __global__ void __launch_bounds__(GT) linearize_kernel(TargetView TG, const floa
             found_out[i] = found ? 1 : 0;
         }
         if (found) {
-            // target covariance: the centroids of the occupied voxels of the block around bv
-            double cnt = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
-            double cen[27][3];
-            uint32_t occ = 0;
-            int bit = 0;
-            for (int dx = -1; dx <= 1; ++dx)
-                for (int dy = -1; dy <= 1; ++dy)
-                    for (int dz = -1; dz <= 1; ++dz, ++bit)
-                        if (target_centroid(TG, bv[0] + dx, bv[1] + dy, bv[2] + dz, cen[bit])) {
-                            occ |= 1u << bit;
-                            cnt = dadd(cnt, 1.0);
-                            sx = dadd(sx, cen[bit][0]);
-                            sy = dadd(sy, cen[bit][1]);
-                            sz = dadd(sz, cen[bit][2]);
-                        }
-            const double mx = __ddiv_rn(sx, cnt), my = __ddiv_rn(sy, cnt), mz = __ddiv_rn(sz, cnt);
-            double S[6] = {0, 0, 0, 0, 0, 0};
-            for (bit = 0; bit < 27; ++bit)
-                if (occ >> bit & 1u) {
-                    const double ex = dsub(cen[bit][0], mx), ey = dsub(cen[bit][1], my), ez = dsub(cen[bit][2], mz);
-                    S[0] = dadd(S[0], dmul(ex, ex));
-                    S[1] = dadd(S[1], dmul(ex, ey));
-                    S[2] = dadd(S[2], dmul(ex, ez));
-                    S[3] = dadd(S[3], dmul(ey, ey));
-                    S[4] = dadd(S[4], dmul(ey, ez));
-                    S[5] = dadd(S[5], dmul(ez, ez));
-                }
-            for (int q = 0; q < 6; ++q) S[q] = __ddiv_rn(S[q], cnt);
+            // target covariance: the voxel's shape, formed at the build
             double Ct[6];
-            normalized(S, r, eps, Ct);
+            target_cov_at_use(TG.cov + 6 * bslot->count, r, eps, Ct);
             // C = C_t + R C_s R^T
             const double* cs = Cs + 6 * i;
             const double Csf[3][3] = {{cs[0], cs[1], cs[2]}, {cs[1], cs[3], cs[4]}, {cs[2], cs[4], cs[5]}};
@@ -365,13 +408,16 @@ __global__ void __launch_bounds__(GT) linearize_kernel(TargetView TG, const floa
     }
 }
 
-// the CTAs' partial sums, in block order
-__global__ void reduce_partials_kernel(const double* __restrict__ partial, int nblk, double* __restrict__ out)
+// the CTAs' partial sums: warp q adds value q, lane l the CTAs l, l + 32, ...,
+// then the lanes in a fixed tree (deterministic)
+__global__ void __launch_bounds__(NACC * 32) reduce_partials_kernel(const double* __restrict__ partial, int nblk,
+                                                                   double* __restrict__ out)
 {
-    if (threadIdx.x >= NACC) return;
+    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double v = 0.0;
-    for (int b = 0; b < nblk; ++b) v += partial[(int64_t)b * NACC + threadIdx.x];
-    out[threadIdx.x] = v;
+    for (int b = lane; b < nblk; b += 32) v += partial[(int64_t)b * NACC + q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) out[q] = v;
 }
 
 // 6 x 6 solve H x = -g by Cholesky (H symmetric positive definite); false if not
@@ -444,6 +490,7 @@ struct bbs_gicp_target {
     int device;
     float r;
     bbs::GicpSlot* slots;
+    double* cov;        // per voxel: the shape of C_t (6 doubles)
     int64_t T;          // slots, a power of two
     int log2T;
     int32_t maxp;       // longest probe of any voxel
@@ -457,6 +504,7 @@ TargetView view_of(const bbs_gicp_target* t)
 {
     TargetView v;
     v.slots = t->slots;
+    v.cov = t->cov;
     v.shift = (uint32_t)(32 - t->log2T);
     v.mask = (uint32_t)(t->T - 1);
     v.maxp = t->maxp;
@@ -504,7 +552,7 @@ int linearize_once(const bbs_gicp_target* tg, const float* d_xyz, int64_t k, con
     const int nblk = (int)((k + GT - 1) / GT);
     linearize_kernel<<<nblk, GT, 0, B.st>>>(view_of(tg), d_xyz, B.Cs, k, T, P.r, P.tau * P.tau, P.eps, B.partial,
                                             want_vox ? B.vox : nullptr, want_vox ? B.found : nullptr);
-    reduce_partials_kernel<<<1, 32, 0, B.st>>>(B.partial, nblk, B.out);
+    reduce_partials_kernel<<<1, NACC * 32, 0, B.st>>>(B.partial, nblk, B.out);
     BBS_CUDA_TRY(cudaGetLastError());
     double acc[NACC];
     BBS_CUDA_TRY(cudaMemcpyAsync(acc, B.out, sizeof(acc), cudaMemcpyDeviceToHost, B.st));
@@ -540,6 +588,7 @@ int gicp_target_device(const bbs_gicp_target* t) { return t->device; }
 void gicp_target_free(bbs_gicp_target* t)
 {
     if (t->slots) cudaFree(t->slots);
+    if (t->cov) cudaFree(t->cov);
     delete t;
 }
 
@@ -604,14 +653,21 @@ int gicp_target_build(const float* xyz, int64_t n, int is_device, float r, cudaS
         }
         if (hs[0]) continue;   // a probe ran past 64 slots: a larger table
         target_centroid_kernel<<<blocks, 256, 0, st>>>(t->slots, T, (double)r);
-        if (cudaGetLastError() != cudaSuccess) {
-            rc = set_error(BBS_ECUDA, "gicp_target: centroids failed");
-            break;
-        }
         t->T = T;
         t->log2T = lt;
         t->maxp = hs[2];
         t->n_voxels = hs[3];
+        // every voxel's covariance shape, from the final centroids
+        if (cudaMalloc((void**)&t->cov, sizeof(double) * 6 * (size_t)std::max<int64_t>(t->n_voxels, 1)) != cudaSuccess) {
+            rc = set_error(BBS_ENOMEM, "gicp_target: covariance rows");
+            break;
+        }
+        cudaMemsetAsync(d_st, 0, sizeof(int) * 4, st);
+        target_cov_kernel<<<blocks, 256, 0, st>>>(view_of(t), T, t->slots, t->cov, (unsigned long long*)d_st);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+            rc = set_error(BBS_ECUDA, "gicp_target: centroids or covariances failed");
+            break;
+        }
         break;
     }
     cudaFreeAsync(d_st, st);
