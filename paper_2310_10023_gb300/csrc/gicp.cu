@@ -168,25 +168,48 @@ __device__ __forceinline__ void normalized(const double S[6], double r, double e
     }
 }
 
-// Per occupied voxel of the target, the shape S / tr S of the centroids of
-// the occupied voxels of its 3 x 3 x 3 block (sums in (dx, dy, dz) order), or
-// -1 in the first entry when tr S = 0; written to its own row of `cov` and
-// the row stored in the slot's count word.  C_t = r^2 (shape + eps I) is
-// formed at use, so eps stays a per-call option.
-__global__ void target_cov_kernel(TargetView T, int64_t nslots, GicpSlot* slots, double* cov,
-                                  unsigned long long* rows)
+// Every occupied slot its own row of the covariance array (one atomic per
+// warp); row_slot[row] = slot, and the row in the slot's count word.
+__global__ void target_rows_kernel(GicpSlot* slots, int64_t nslots, unsigned long long* rows, int64_t* row_slot)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nslots; i += (int64_t)gridDim.x * blockDim.x) {
-        GicpSlot& q = slots[i];
-        if (q.key == GEMPTY) continue;
+    const int lane = threadIdx.x & 31;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < nslots; i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
+        const bool occ = i < nslots && slots[i].key != GEMPTY;
+        const uint32_t ball = __ballot_sync(0xffffffffu, occ);
+        if (!ball) continue;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(rows, (unsigned long long)__popc(ball));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (occ) {
+            const unsigned long long row = base + __popc(ball & ((1u << lane) - 1u));
+            slots[i].count = row;
+            row_slot[row] = i;
+        }
+    }
+}
+
+// Per occupied voxel (one thread per row, so every lane of a warp has a
+// voxel: FP64 runs at a small fraction of the FP32 rate on this part), the
+// shape S / tr S of the centroids of the occupied voxels of its 3 x 3 x 3
+// block, sums in (dx, dy, dz) order, or -1 in the first entry when
+// tr S = 0.  C_t = r^2 (shape + eps I) is formed at use, so eps stays a
+// per-call option.
+__global__ void target_cov_kernel(TargetView T, const int64_t* __restrict__ row_slot, int64_t nrows, double* cov)
+{
+    for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < nrows; row += (int64_t)gridDim.x * blockDim.x) {
+        const GicpSlot& q = T.slots[row_slot[row]];
         const int32_t v[3] = {(int32_t)((q.key >> 42) & 0x1FFFFF) - KEY_LIMIT, (int32_t)((q.key >> 21) & 0x1FFFFF) - KEY_LIMIT,
                               (int32_t)(q.key & 0x1FFFFF) - KEY_LIMIT};
         double cnt = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+        uint32_t occ = 0;
+        int bit = 0;
         for (int dx = -1; dx <= 1; ++dx)
             for (int dy = -1; dy <= 1; ++dy)
-                for (int dz = -1; dz <= 1; ++dz) {
+                for (int dz = -1; dz <= 1; ++dz, ++bit) {
                     double c[3];
                     if (!target_centroid(T, v[0] + dx, v[1] + dy, v[2] + dz, c)) continue;
+                    occ |= 1u << bit;
                     cnt = dadd(cnt, 1.0);
                     sx = dadd(sx, c[0]);
                     sy = dadd(sy, c[1]);
@@ -194,11 +217,12 @@ __global__ void target_cov_kernel(TargetView T, int64_t nslots, GicpSlot* slots,
                 }
         const double mx = __ddiv_rn(sx, cnt), my = __ddiv_rn(sy, cnt), mz = __ddiv_rn(sz, cnt);
         double S[6] = {0, 0, 0, 0, 0, 0};
+        bit = 0;
         for (int dx = -1; dx <= 1; ++dx)
             for (int dy = -1; dy <= 1; ++dy)
-                for (int dz = -1; dz <= 1; ++dz) {
+                for (int dz = -1; dz <= 1; ++dz, ++bit) {
                     double c[3];
-                    if (!target_centroid(T, v[0] + dx, v[1] + dy, v[2] + dz, c)) continue;
+                    if (!(occ >> bit & 1u) || !target_centroid(T, v[0] + dx, v[1] + dy, v[2] + dz, c)) continue;
                     const double ex = dsub(c[0], mx), ey = dsub(c[1], my), ez = dsub(c[2], mz);
                     S[0] = dadd(S[0], dmul(ex, ex));
                     S[1] = dadd(S[1], dmul(ex, ey));
@@ -209,9 +233,7 @@ __global__ void target_cov_kernel(TargetView T, int64_t nslots, GicpSlot* slots,
                 }
         for (int k = 0; k < 6; ++k) S[k] = __ddiv_rn(S[k], cnt);
         const double tr = dadd(dadd(S[0], S[3]), S[5]);
-        const unsigned long long row = atomicAdd(rows, 1ull);
         for (int k = 0; k < 6; ++k) cov[6 * row + k] = tr > 0.0 ? __ddiv_rn(S[k], tr) : (k == 0 ? -1.0 : 0.0);
-        q.count = row;
     }
 }
 
@@ -658,12 +680,18 @@ int gicp_target_build(const float* xyz, int64_t n, int is_device, float r, cudaS
         t->maxp = hs[2];
         t->n_voxels = hs[3];
         // every voxel's covariance shape, from the final centroids
-        if (cudaMalloc((void**)&t->cov, sizeof(double) * 6 * (size_t)std::max<int64_t>(t->n_voxels, 1)) != cudaSuccess) {
+        const int64_t nv = std::max<int64_t>(t->n_voxels, 1);
+        int64_t* row_slot = nullptr;
+        if (cudaMalloc((void**)&t->cov, sizeof(double) * 6 * (size_t)nv) != cudaSuccess ||
+            cudaMallocAsync((void**)&row_slot, sizeof(int64_t) * (size_t)nv, st) != cudaSuccess) {
             rc = set_error(BBS_ENOMEM, "gicp_target: covariance rows");
             break;
         }
         cudaMemsetAsync(d_st, 0, sizeof(int) * 4, st);
-        target_cov_kernel<<<blocks, 256, 0, st>>>(view_of(t), T, t->slots, t->cov, (unsigned long long*)d_st);
+        target_rows_kernel<<<blocks, 256, 0, st>>>(t->slots, T, (unsigned long long*)d_st, row_slot);
+        target_cov_kernel<<<(unsigned)std::min<int64_t>((t->n_voxels + 255) / 256 + 1, 65535), 256, 0, st>>>(
+            view_of(t), row_slot, t->n_voxels, t->cov);
+        cudaFreeAsync(row_slot, st);
         if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
             rc = set_error(BBS_ECUDA, "gicp_target: centroids or covariances failed");
             break;
