@@ -134,3 +134,23 @@ def test_refines_the_bnb_estimate_indoor(nv):
         errs.append((round(float(e0), 4), round(float(e1), 4)))
         assert e1 < 0.05, errs
     assert better == 3, errs
+
+
+def test_degenerate_cases(nv, room):
+    """No correspondence (a scan far from the map) or fewer than six kept
+    (a tiny tau): one linearization, not converged, the pose unchanged;
+    bad voxel sizes are refused."""
+    r, dt, keys, occ = room
+    s, pose = synth.make_scan(1, 0)
+    R0, t0 = _start(pose)
+    far = nv.bbs_gicp(dt, s, R0, t0 + np.array([500.0, 0.0, 0.0]))
+    assert far.status == nv.OK and far.correspondences == 0 and far.iterations == 1 and not far.converged
+    Rg, tg = far.Rt()
+    assert np.array_equal(Rg, R0) and np.array_equal(tg, t0 + np.array([500.0, 0.0, 0.0]))
+    tiny = nv.bbs_gicp(dt, s[:20], R0, t0, nv.make_gicp_opts(tau=1e-6))
+    o = gicp.gicp(occ, s[:20].astype(np.float64), R0, t0, r, tau=1e-6)
+    assert tiny.correspondences == o.n < 6 and tiny.iterations == o.iterations == 1 and not tiny.converged
+    for bad in (0.0, -1.0, float("nan")):
+        with pytest.raises(nv.BBSError) as e:
+            nv.bbs_gicp_target_build(synth.make_map(1)[:100], bad)
+        assert e.value.code == nv.EINVAL
