@@ -1,0 +1,119 @@
+"""The integer and floating-point identities the scoring kernel relies on,
+checked on the CPU: the byte-counter spreads (exhaustive), the bit pattern of
+a floored level key, the folded index constant of clamp-free runs, and the
+FP32 bound of the per-run inside test (emulated with FP32 arithmetic, the
+tightest point placed on the bound)."""
+import math
+import struct
+from fractions import Fraction
+
+import numpy as np
+
+KB = 0x4B400000   # bit pattern of 1.5 * 2^23
+
+
+def test_nibble_spread_is_carry_free():
+    """((v & 0xF) * 0x204081) & 0x01010101 puts bit i of the nibble in byte i,
+    and the product is a sum of distinct powers of two (no carry can reach a
+    counter), for every byte and both nibbles."""
+    for v in range(256):
+        for nib in (v & 0xF, v >> 4):
+            prod = nib * 0x204081
+            assert bin(prod).count("1") == 4 * bin(nib).count("1")
+            spread = prod & 0x01010101
+            assert spread == sum(((nib >> i) & 1) << (8 * i) for i in range(4))
+
+
+def test_plane_spread_reaches_counters_exactly():
+    """((w & 0x63) * 0x40881) & 0x01010101 puts bits 0, 1, 5, 6 of a brick
+    plane (children jx + 5 jy) in bytes 0..3.  Partial products of bits 1 and
+    5 meet at bit 12, but the carry chain ends by bit 14, below the counter
+    bit of byte 2, so the masked result is exact for every plane."""
+    for w in range(1 << 7):
+        m = w & 0x63
+        prod = m * 0x40881
+        want = sum(((w >> b) & 1) << (8 * i) for i, b in enumerate((0, 1, 5, 6)))
+        assert prod & 0x01010101 == want
+        assert prod < 1 << 25
+
+
+def test_floored_key_bit_pattern():
+    """For C = 1.5 * 2^23 + d (|d| < 2^21) and |q / 2^m| < 2^18, the value
+    q 2^-m + C lies in [2^23, 2^24) where FP32 spacing is 1, so rounding down
+    gives its floor exactly and the bit pattern is KB + floor(q / 2^m) + d."""
+    rng = np.random.default_rng(0)
+    for _ in range(3000):
+        m = int(rng.integers(0, 12))
+        q = float(np.float32(rng.uniform(-(2.0 ** 18), 2.0 ** 18) * 2.0 ** m / 4))
+        d = int(rng.integers(-(2 ** 20), 2 ** 20))
+        x = Fraction(q) / 2 ** m + Fraction(3 * 2 ** 22 + d)
+        assert 2 ** 23 <= x < 2 ** 24
+        rd = math.floor(x)
+        bits = struct.unpack("<I", struct.pack("<f", float(rd)))[0]
+        assert bits == KB + math.floor(Fraction(q) / 2 ** m) + d
+
+
+def test_folded_index_constant():
+    """((bx ny + by) nz + bz + cfix) mod 2^32 with cfix = -KB (ny nz + nz + 1)
+    equals the relative index (rx ny + ry) nz + rz when b = KB + r and the
+    relative index is below 2^31."""
+    rng = np.random.default_rng(1)
+    M = 1 << 32
+    for _ in range(3000):
+        ny, nz = int(rng.integers(2, 4000)), int(rng.integers(2, 4000))
+        nx = int(rng.integers(2, max(3, (1 << 31) // (ny * nz))))
+        r = [int(rng.integers(0, n)) for n in (nx, ny, nz)]
+        b = [KB + x for x in r]
+        cfix = (-KB * (ny * nz + nz + 1)) % M
+        got = (((b[0] * ny + b[1]) % M * nz + b[2]) % M + cfix) % M
+        assert got == (r[0] * ny + r[1]) * nz + r[2]
+
+
+def _rot(ang, r):
+    ca, sa = np.cos(ang), np.sin(ang)
+    Rx = np.array([[1, 0, 0], [0, ca[0], -sa[0]], [0, sa[0], ca[0]]])
+    Ry = np.array([[ca[1], 0, sa[1]], [0, 1, 0], [-sa[1], 0, ca[1]]])
+    Rz = np.array([[ca[2], -sa[2], 0], [sa[2], ca[2], 0], [0, 0, 1]])
+    return (Rz @ Ry @ Rx / r).astype(np.float32)
+
+
+def test_inside_bound_has_no_false_positive():
+    """The run's inside test (FP32 corner products widened by 2e-6 of
+    sum |A| max |x|) never admits a run with a point whose FP32 key leaves
+    [0, rmax + 1], including runs placed with the extreme point exactly on
+    either bound."""
+    f32 = np.float32
+    rng = np.random.default_rng(2)
+    admitted = 0
+    for _ in range(1500):
+        r = float(rng.choice([0.05, 0.2, 0.5, 1.0]))
+        m = int(rng.integers(0, 8))
+        A = _rot(rng.uniform(-np.pi, np.pi, 3) * rng.choice([1.0, 0.05]), r)
+        n = int(rng.integers(1, 2049))
+        P = (rng.uniform(-1, 1, (n, 3)) * rng.uniform(0.1, 60.0, 3) + rng.uniform(-20, 20, 3)).astype(f32)
+        lo3, hi3 = P.min(0), P.max(0)
+        q = ((A[:, 0][None] * P[:, 0:1]).astype(f32) + (A[:, 1][None] * P[:, 1:2]).astype(f32)).astype(f32)
+        q = (q + (A[:, 2][None] * P[:, 2:3]).astype(f32)).astype(f32)
+        fl = np.floor(q.astype(np.float64) * 2.0 ** -m)
+        rmax = rng.integers(10, 5000, 3)
+        s = f32(2.0 ** -m)
+        for mode in range(3):
+            o = (-fl.min(0) if mode == 0 else (rmax + 1) - fl.max(0) if mode == 1
+                 else rng.integers(-100, 5000, 3).astype(np.float64))
+            inside = True
+            for i in range(3):
+                qlo = qhi = mag = f32(0)
+                for k in range(3):
+                    a = A[i, k]
+                    p1, p2 = f32(a * lo3[k]), f32(a * hi3[k])
+                    qlo, qhi = f32(qlo + min(p1, p2)), f32(qhi + max(p1, p2))
+                    mag = f32(mag + f32(abs(a) * max(abs(lo3[k]), abs(hi3[k]))))
+                marg = f32(f32(f32(2e-6) * mag) + f32(1e-30))
+                oi = f32(o[i])
+                inside &= bool(f32(np.floor(f32(f32(qlo - marg) * s))) + oi >= 0)
+                inside &= bool(f32(np.floor(f32(f32(qhi + marg) * s))) + oi <= f32(rmax[i]) + f32(1))
+            if inside:
+                admitted += 1
+                keys = fl + o[None, :]
+                assert keys.min() >= 0 and np.all(keys <= (rmax + 1)[None, :])
+    assert admitted > 100
