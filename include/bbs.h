@@ -275,7 +275,10 @@ int  bbs_score_batch(const bbs_maps* maps, const float* scan_xyz, int64_t k, int
  * parent in order, its children in the order (alpha, beta, gamma, x, y, z)
  * into child_nodes (cap x 7 int32) and child_scores (cap int32); *n_children
  * receives the total.  Leaves (level 0) have no children.  Pointers follow
- * is_device.  BBS_EINVAL if cap is short or a parent is outside the grid. */
+ * is_device; the output buffers may be NULL with cap = 0 (a size query:
+ * *n_children is set and BBS_EINVAL returned when there are children).
+ * BBS_EINVAL if cap is short, an output buffer is NULL, or a parent is
+ * outside the grid. */
 int  bbs_score_children(const bbs_maps* maps, const float* scan_xyz, int64_t k, int is_device,
                         const bbs_ranges* ranges, const bbs_opts* opts, const int32_t* parents,
                         int64_t n, int32_t* child_nodes, int32_t* child_scores, int64_t cap,
@@ -411,9 +414,11 @@ int  bbs_bench_gather(int64_t table_bytes, int64_t gathers, void* cuda_stream, d
  * device per is_device); out[i] receives scan i's result, identical to what
  * bbs_localize returns for it alone (same best score, match, iterations and
  * nodes scored; times and launch counts are those of the shared run).  The
- * frontier capacity opts->max_frontier is shared by all n searches.  Returns
- * BBS_OK when every search ran (each out[i].status tells found / not found),
- * or an error for the whole call. */
+ * frontier capacity opts->max_frontier is shared by all n searches.  At most
+ * 256 searches advance together (n <= 4096): the others take the slots of
+ * searches that finish, between iterations.  Returns BBS_OK when every search
+ * ran (each out[i].status tells found / not found), or an error for the whole
+ * call. */
 int  bbs_localize_many(const bbs_maps* maps, int n, const float* const* scans, const int64_t* ks,
                        int is_device, const bbs_ranges* ranges, const bbs_opts* opts, bbs_result* out);
 
@@ -434,7 +439,7 @@ typedef struct bbs_server bbs_server;
 
 typedef struct {
     size_t  mem_budget;     /* device bytes for the pool plus admitted searches; 0 = 8 GiB  */
-    int32_t max_active;     /* searches advanced together; 0 = 32, at most 1024             */
+    int32_t max_active;     /* searches advanced together; 0 = 32, at most 256              */
     int64_t max_frontier;   /* shared frontier pool in nodes; 0 = 2^24                      */
 } bbs_server_opts;
 
@@ -454,7 +459,9 @@ int  bbs_server_submit(bbs_server* server, const bbs_maps* maps, const float* sc
 /* wait up to wait_ms (0: do not wait, negative: until done) for a ticket.
  * Returns BBS_PENDING while queued or running; otherwise the request's status
  * (BBS_OK, BBS_NOT_FOUND or an error), with its result in *out, and forgets
- * the ticket. */
+ * the ticket: a later poll of it (or of a ticket never issued) returns
+ * BBS_EINVAL at once.  The maps handle of a request must stay alive until its
+ * result has been polled. */
 int  bbs_server_poll(bbs_server* server, uint64_t ticket, int wait_ms, bbs_result* out);
 /* cancel a queued or running request; its result reports BBS_ECANCELED */
 int  bbs_server_cancel(bbs_server* server, uint64_t ticket);

@@ -333,6 +333,7 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
     *n_children = total;
     if (total > cap) return set_error(BBS_EINVAL, "score_children: capacity %lld < %lld children", (long long)cap, (long long)total);
     if (total == 0) return BBS_OK;
+    if (!child_nodes || !child_scores) return set_error(BBS_EINVAL, "score_children: NULL output buffer");
     // the tasks (rotational children) in parent order, child order ja, jb, jg
     const int64_t ntask = total / 8;
     std::vector<TaskRec> tk((size_t)ntask);
@@ -375,6 +376,15 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
     TaskRec* d_tk = nullptr;
     int32_t* d_dense = nullptr;
     Plan* d_plan = nullptr;
+    struct Bufs {   // freed on every return below, in stream order
+        void** p[4];
+        cudaStream_t st;
+        ~Bufs()
+        {
+            for (void** q : p)
+                if (*q) cudaFreeAsync(*q, st);
+        }
+    } bufs{{(void**)&d_sd, (void**)&d_tk, (void**)&d_dense, (void**)&d_plan}, st};
     BBS_CUDA_TRY(cudaMallocAsync((void**)&d_sd, sizeof(SearchDev), st));
     BBS_CUDA_TRY(cudaMallocAsync((void**)&d_tk, sizeof(TaskRec) * (size_t)ntask, st));
     BBS_CUDA_TRY(cudaMallocAsync((void**)&d_dense, sizeof(int32_t) * (size_t)total, st));
@@ -413,10 +423,6 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
         e = cudaMemcpyAsync(dense.data(), d_dense, sizeof(int32_t) * dense.size(), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // the host copies of P and the tasks outlive their transfers
     if (e != cudaSuccess) rc = set_error(BBS_ECUDA, "score_children: %s", cudaGetErrorString(e));
-    cudaFreeAsync(d_plan, st);
-    cudaFreeAsync(d_sd, st);
-    cudaFreeAsync(d_tk, st);
-    cudaFreeAsync(d_dense, st);
     if (rc != BBS_OK) return rc;
     std::vector<int32_t> on((size_t)(7 * total)), os((size_t)total);
     int64_t o = 0;

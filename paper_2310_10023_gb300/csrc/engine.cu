@@ -557,7 +557,8 @@ int Engine::init()
         *p = (T)q;
         return BBS_OK;
     };
-    if (max_slots_ < 1 || max_slots_ > 256) return set_error(BBS_EINVAL, "engine: %d slots (1..256)", max_slots_);
+    if (max_slots_ < 1 || max_slots_ > MAX_SLOTS)
+        return set_error(BBS_EINVAL, "engine: %d slots (1..%d)", max_slots_, MAX_SLOTS);
     for (int b = 0; b < 2; ++b) {
         BBS_TRY(get(&front_.nodes[b], (size_t)fcap_));
         BBS_TRY(get(&front_.keys[b], (size_t)fcap_));
@@ -1296,22 +1297,31 @@ int search_run_many(const bbs_maps* m, int n, const float* const* scans, const i
     const bool timed = opts && (opts->flags & BBS_TIME_KERNELS);
     int64_t kmax = 1;
     for (int i = 0; i < n; ++i) kmax = std::max(kmax, ks[i]);
-    const int64_t pool_nodes = max_frontier + (int64_t)CH * std::min<int64_t>((kmax + 1) * n, 8192 * (int64_t)n);
+    // at most MAX_SLOTS searches advance together; the others take slots as
+    // searches finish (each result is the same either way)
+    const int slots = std::min(n, MAX_SLOTS);
+    const int64_t pool_nodes =
+        max_frontier + (int64_t)CH * std::min<int64_t>((kmax + 1) * slots, 8192 * (int64_t)slots);
     int rc = BBS_OK;
-    Engine* E = acquire_engine(n, pool_nodes, st, timed, &rc);
+    Engine* E = acquire_engine(slots, pool_nodes, st, timed, &rc);
     if (!E) return rc;
-    std::vector<int> slot_of((size_t)n, -1);
-    for (int i = 0; i < n && rc == BBS_OK; ++i) {
-        std::memset(&res[i], 0, sizeof(res[i]));
-        rc = E->add(m, scans[i], ks[i], is_device, rg, opts, (uint64_t)i, &slot_of[(size_t)i]);
-    }
-    if (rc == BBS_OK) rc = E->start();
+    int next = 0;
+    auto admit = [&]() {
+        for (int slot = -1; rc == BBS_OK && next < n && E->used_count() < slots; ++next) {
+            std::memset(&res[next], 0, sizeof(res[next]));
+            rc = E->add(m, scans[next], ks[next], is_device, rg, opts, (uint64_t)next, &slot);
+        }
+        if (rc == BBS_OK) rc = E->start();
+    };
+    admit();
     E->set_host_driven(opts && (opts->flags & BBS_HOST_DRIVEN));
     std::vector<int> fin;
     while (rc == BBS_OK && E->used_count() > 0) {
         fin.clear();
-        rc = E->iterate(1 << 20, &fin);
+        // with scans still waiting, return to the host every few iterations to refill freed slots
+        rc = E->iterate(next < n ? 4 : 1 << 20, &fin);
         for (int s_ : fin) E->finalize(s_, &res[E->tag(s_)]);
+        if (rc == BBS_OK && next < n) admit();
     }
     release_engine(E, rc == BBS_OK);
     return rc;

@@ -37,6 +37,9 @@ struct SearchHost {
     uint64_t tag = 0;
 };
 
+// search slots of one engine: a frontier key holds its search in the top byte
+constexpr int MAX_SLOTS = 256;
+
 class Engine {
   public:
     Engine(cudaStream_t st, int max_slots, int64_t pool_nodes, bool timed);

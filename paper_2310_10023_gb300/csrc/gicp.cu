@@ -629,13 +629,17 @@ int gicp_target_build(const float* xyz, int64_t n, int is_device, float r, cudaS
     if (n < 1 || !xyz) return set_error(BBS_EINVAL, "gicp_target: empty cloud");
     const float* d_xyz = xyz;
     float* owned = nullptr;
-    if (!is_device) {
-        BBS_CUDA_TRY(cudaMallocAsync((void**)&owned, sizeof(float) * 3 * (size_t)n, st));
-        BBS_CUDA_TRY(cudaMemcpyAsync(owned, xyz, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice, st));
-        d_xyz = owned;
-    }
     int* d_st = nullptr;
     BBS_CUDA_TRY(cudaMallocAsync((void**)&d_st, sizeof(int) * 4, st));
+    if (!is_device) {
+        if (cudaMallocAsync((void**)&owned, sizeof(float) * 3 * (size_t)n, st) != cudaSuccess ||
+            cudaMemcpyAsync(owned, xyz, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            if (owned) cudaFreeAsync(owned, st);
+            cudaFreeAsync(d_st, st);
+            return set_error(BBS_ENOMEM, "gicp_target: %lld points", (long long)n);
+        }
+        d_xyz = owned;
+    }
     bbs_gicp_target* t = new bbs_gicp_target;
     std::memset(t, 0, sizeof(*t));
     cudaGetDevice(&t->device);

@@ -68,6 +68,7 @@ struct bbs_server {
     std::unordered_map<uint64_t, int> running;        // ticket -> engine slot
     std::unordered_map<int, bbs::Request> slot_req;    // engine slot -> request (worker thread only)
     std::unordered_set<uint64_t> cancels;
+    std::unordered_set<uint64_t> uncollected;         // submitted tickets whose result has not been polled
     std::vector<double> latencies;
     uint64_t next_ticket = 1;
     int64_t submitted = 0, rejected = 0, peak_active = 0;
@@ -214,9 +215,9 @@ int bbs_server_create(const bbs_server_opts* o, bbs_server** out)
     cudaGetDevice(&S->device);
     S->budget = (o && o->mem_budget) ? o->mem_budget : ((size_t)8 << 30);
     S->max_active = (o && o->max_active > 0) ? o->max_active : 32;
-    if (S->max_active > 1024) {
+    if (S->max_active > MAX_SLOTS) {
         delete S;
-        return set_error(BBS_EINVAL, "server_create: max_active above 1024");
+        return set_error(BBS_EINVAL, "server_create: max_active above %d", MAX_SLOTS);
     }
     const int64_t pool = (o && o->max_frontier > 0) ? o->max_frontier : ((int64_t)1 << 24);
     if (cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking) != cudaSuccess) {
@@ -262,6 +263,7 @@ int bbs_server_submit(bbs_server* S, const bbs_maps* maps, const float* scan_xyz
     if (S->fatal) return set_error(S->fatal, "server: %s", S->fatal_msg);
     q.ticket = S->next_ticket++;
     *ticket = q.ticket;
+    S->uncollected.insert(q.ticket);
     S->submitted++;
     if (S->t_first < 0) S->t_first = q.t_submit;
     q.est_bytes = estimate_request(S, q);
@@ -286,8 +288,10 @@ int bbs_server_poll(bbs_server* S, uint64_t ticket, int wait_ms, bbs_result* out
     clear_error();
     if (!S || !out) return set_error(BBS_EINVAL, "server_poll: bad arguments");
     std::unique_lock<std::mutex> lock(S->mu);
-    if (ticket == 0 || ticket >= S->next_ticket) return set_error(BBS_EINVAL, "server_poll: unknown ticket %llu",
-                                                                  (unsigned long long)ticket);
+    // a ticket never issued, or whose result was already returned, would never be ready
+    if (!S->uncollected.count(ticket))
+        return set_error(BBS_EINVAL, "server_poll: ticket %llu is unknown or already collected",
+                         (unsigned long long)ticket);
     auto ready = [&] { return S->done.count(ticket) > 0 || S->fatal != 0; };
     if (!ready() && wait_ms != 0) {
         if (wait_ms < 0) S->cv_done.wait(lock, ready);
@@ -302,6 +306,7 @@ int bbs_server_poll(bbs_server* S, uint64_t ticket, int wait_ms, bbs_result* out
     out->ms_total = it->second.t_done - it->second.t_submit;   // submission to result
     const int st = out->status;
     S->done.erase(it);
+    S->uncollected.erase(ticket);
     if (st < 0) set_error(st, "server: request %llu failed", (unsigned long long)ticket);
     return st;
 }

@@ -65,3 +65,14 @@ def test_layout_and_load_validation_without_gpu():
     for ok in (1, 2, 3, 4, 0):
         nv.bbs_set_probe_layout(ok)
     nv.bbs_set_load_factor(0.25)
+
+
+def test_server_slot_limit_without_gpu():
+    """A server advances at most 256 searches together (the search id is the
+    top byte of a frontier key): a larger max_active is refused on the host."""
+    from paper_2310_10023_gb300 import native as nv
+    nv.load()
+    with pytest.raises(nv.BBSError) as e:
+        nv.bbs_server_create(max_active=257)
+    assert e.value.code == nv.EINVAL
+    assert "256" in nv.bbs_last_error()

@@ -188,6 +188,20 @@ def test_score_batch_rejects_bad_nodes(nv, room_pair):
     bad_scan[5, 2] = np.nan
     with pytest.raises(nv.BBSError):
         nv.bbs_score_batch(dm, bad_scan, np.zeros((1, 7), np.int32), nr)
+    # bbs_score_children: a size query (cap 0, no buffers) reports the count;
+    # a sufficient cap with no output buffers is refused, not dereferenced
+    import ctypes as C
+    parents = np.array([[0, 0, 0, 0, 0, 0, w.levels - 1]], np.int32)
+    sp = np.ascontiguousarray(s, np.float32)
+    opts = nv.make_opts()
+    cnt = C.c_int64(-1)
+    lib = nv.load()
+    args = (dm.h, C.c_void_p(sp.ctypes.data), len(sp), 0, C.byref(nr), C.byref(opts),
+            C.c_void_p(parents.ctypes.data), 1)
+    assert lib.bbs_score_children(*args, None, None, 0, C.byref(cnt)) == nv.EINVAL
+    assert cnt.value > 0
+    assert lib.bbs_score_children(*args, None, None, cnt.value, C.byref(cnt)) == nv.EINVAL
+    assert b"NULL output" in lib.bbs_last_error()
 
 
 @pytest.mark.parametrize("flags", [0, oracle.CHILD_LITERAL, oracle.TRANSLATION_ONLY])
@@ -304,6 +318,22 @@ def test_localize_many_equals_single(nv, room_pair):
     scans[2] = scans[2][:333]                       # uneven sizes
     scans[4] = synth.make_scan(1, 4, k=2500)[0]
     many = nv.bbs_localize_many(dm, [torch.from_numpy(s).cuda() for s in scans], nr, opts)
+    for s, r in zip(scans, many):
+        one = nv.bbs_localize(dm, s, nr, opts)
+        assert (r.status, r.best_score, list(r.node), r.iterations, r.nodes_scored) == \
+               (one.status, one.best_score, list(one.node), one.iterations, one.nodes_scored)
+
+
+def test_localize_many_more_scans_than_slots(nv, room_pair):
+    """300 scans: 256 advance together and the rest take the slots of
+    searches that finish; every result is still the one it gets alone."""
+    w, m, dm, om = room_pair
+    nr, _ = _ranges(nv, w)
+    opts = nv.make_opts(score_frac=w.score_frac, batch=w.batch)
+    base = [synth.make_scan(1, i)[0] for i in range(12)]
+    scans = [base[j % 12][: 200 + (37 * j) % 800] for j in range(300)]
+    many = nv.bbs_localize_many(dm, scans, nr, opts)
+    assert len(many) == 300
     for s, r in zip(scans, many):
         one = nv.bbs_localize(dm, s, nr, opts)
         assert (r.status, r.best_score, list(r.node), r.iterations, r.nodes_scored) == \

@@ -113,4 +113,9 @@ def test_cancel_queued(nv, two_maps):
     for t in tickets[:-1]:
         st, r = nv.bbs_server_poll(srv, t, -1)
         assert st in (nv.OK, nv.NOT_FOUND)
+    # a collected ticket (or one never issued) is refused at once, not waited on
+    for t in (tickets[0], tickets[-1], tickets[-1] + 100):
+        with pytest.raises(nv.BBSError) as e:
+            nv.bbs_server_poll(srv, t, 2000)
+        assert e.value.code == nv.EINVAL
     srv.close()
