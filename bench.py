@@ -547,6 +547,9 @@ def run_ours(a):
         with Clocks(torch.cuda.current_device()) as clk:
             for i in range(a.steps):
                 flush.zero_()
+                # the call's host work must not overlap the flush: the GPU is
+                # idle when the timed region starts
+                torch.cuda.synchronize()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
@@ -563,6 +566,9 @@ def run_ours(a):
     probes = sum(r["probes"] for r in results)
     launches = sum(r["launches"] for r in results)
     to_opt = statistics.mean(r["ms_to_optimum"] for r in results)
+    # where one scan's time goes (the library's own per-result phases, medians)
+    phase_names = ("setup", "initial_enqueue", "device_to_match", "device_after_match", "readback")
+    phases = {n: statistics.median(r["phase_ms"][j] for r in results) for j, n in enumerate(phase_names)}
     found = sum(r["status"] == nv.OK for r in results)
     # ---- timed again with every scoring launch bracketed by CUDA events on the
     # stream (host-driven iterations: the graph's loop body cannot hold events)
@@ -638,6 +644,10 @@ def run_ours(a):
                            map_layout=sorted({nv.LAYOUT_NAMES[nv.bbs_maps_layout(maps, l)] for l in range(w.levels)})),
             "ms_to_optimum": to_opt,
             "ms_total_per_scan": total_ms / a.steps,
+            "ms_per_scan_median": statistics.median(step_ms),
+            "phase_ms_median": dict(phases, note="setup: scan upload, d_max, pose grid, angle tables, slot; "
+                                                 "initial_enqueue: host time to launch the initial set; "
+                                                 "device_*: %globaltimer from the initial set's start"),
             "found": f"{found}/{a.steps}",
             "map_build_ms": build_ms,
             "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Gop/s",
