@@ -226,6 +226,35 @@ def test_branch_kernel_children_bit_exact(nv, room_pair, flags):
     assert np.array_equal(scores, om.score_nodes(g, s, want_nodes))
 
 
+@pytest.mark.parametrize("layout", [0, 2])
+def test_branch_kernel_chunk_edges(nv, layout):
+    """The fused kernel stages the scan in 2048-point chunks of 512-point
+    blocks, two points per thread: scans that end on, just before and just
+    after each of those boundaries (and the odd single point), under the
+    byte-grid and the hashed layout, score every child as the oracle does."""
+    w = synth.WORKLOADS["room"]
+    m = synth.make_map(w.scene)
+    om = oracle.Maps(m, w.r, w.levels)
+    nv.bbs_set_probe_layout(layout)
+    try:
+        dm = nv.bbs_build_maps(m, w.r, w.levels)
+    finally:
+        nv.bbs_set_probe_layout(0)
+    base, _ = synth.make_scan(1, 9, k=4200)
+    nr, orr = _ranges(nv, w)
+    for k in (1, 2, 3, 511, 512, 513, 1024, 2047, 2048, 2049, 4097):
+        sk = np.ascontiguousarray(base[:k])
+        g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(sk), orr)
+        parents = _random_nodes(g, np.random.default_rng(k), 24, w.levels)
+        parents[:, 6] = np.maximum(parents[:, 6], 1)
+        for i, p in enumerate(parents):
+            for a in range(3):
+                parents[i, 3 + a] = min(p[3 + a], g.N(p[6])[a] - 1)
+        nodes, scores = nv.bbs_score_children(dm, sk, parents, nr)
+        assert np.array_equal(nodes, np.concatenate([g.children(p) for p in parents])), k
+        assert np.array_equal(scores, om.score_nodes(g, sk, nodes)), (layout, k)
+
+
 # ---- search ----------------------------------------------------------------
 
 def _same_search(res, ores):
