@@ -275,6 +275,23 @@ constexpr int NRUN = 32;   // runs described per round of a CTA
 
 }  // namespace
 
+// The rotation rows (A = fl32(R / r)) of the runs of a round, from their
+// tasks' rl: entry e of run r is formed by thread e * nrun + r, so a warp
+// forms one entry of 32 runs and the short FP64 chains spread over every warp
+// of the CTA (kept out of line: the scoring loop keeps its registers).
+__device__ __noinline__ void form_rows(RunDesc* rd, const TaskRec* __restrict__ tasks, const SearchDev& S, int64_t v0,
+                                       int64_t nt, int nrun)
+{
+    for (int q = threadIdx.x; q < 9 * nrun; q += blockDim.x) {
+        const int e = q / nrun, r = q - e * nrun;
+        const int64_t v = v0 + r;
+        const int64_t u = v - (v / nt) * nt;
+        const uint32_t rl = __ldg(&tasks[u].rl);
+        const float a = rotation_entry(S.cs, S.grid, rl_level(rl), rl_rot(rl), e);
+        rd[r].a[e] = pk2(a, a);
+    }
+}
+
 // Fused branch + score.  The launch's slices (task, PBLK-point block) are
 // split into gridDim.x equal contiguous ranges, one per CTA; a CTA walks its
 // range in rounds of at most NRUN runs (maximal pieces of one task over one
@@ -382,7 +399,7 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
             const int64_t rs = c * 4 * nt + u * nbc;
             int m;
             int32_t tx, ty, tz;
-            float A[9];
+            RunDesc& d = rd[tid];
             if (MODE == MODE_INITIAL) {
                 virtual_parent(S, g->first_parent + u / g->R, tx, ty, tz);
                 tx *= 2;
@@ -390,20 +407,19 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
                 tz *= 2;
                 const float4* At = S.rot + 3 * (u % g->R);   // the top level's table
                 const float4 a0 = __ldg(At), a1 = __ldg(At + 1), a2 = __ldg(At + 2);
-                A[0] = a0.x, A[1] = a0.y, A[2] = a0.z, A[3] = a1.x, A[4] = a1.y, A[5] = a1.z;
-                A[6] = a2.x, A[7] = a2.y, A[8] = a2.z;
+                d.a[0] = pk2(a0.x, a0.x), d.a[1] = pk2(a0.y, a0.y), d.a[2] = pk2(a0.z, a0.z);
+                d.a[3] = pk2(a1.x, a1.x), d.a[4] = pk2(a1.y, a1.y), d.a[5] = pk2(a1.z, a1.z);
+                d.a[6] = pk2(a2.x, a2.x), d.a[7] = pk2(a2.y, a2.y), d.a[8] = pk2(a2.z, a2.z);
                 m = S.lmax;
             } else {
-                const TaskRec& tr = tasks[g->first_task + u];
+                const TaskRec tr = tasks[g->first_task + u];
                 m = rl_level(tr.rl);
-                for (int i = 0; i < 9; ++i) A[i] = tr.a[i];
                 tx = tr.tx;
                 ty = tr.ty;
                 tz = tr.tz;
             }
             const LevelView& L = S.maps[m];
             const bool cmp = L.layout != LAYOUT_WIDE;
-            RunDesc& d = rd[tid];
             const int32_t t3[3] = {tx, ty, tz};
             for (int i = 0; i < 3; ++i) {
                 // |offset| >= 2^21 puts every point of the run outside the key range
@@ -415,14 +431,24 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
             }
             const float sc = __int_as_float((127 - m) << 23);   // 2^-m
             d.s = pk2(sc, sc);
-            for (int i = 0; i < 9; ++i) d.a[i] = pk2(A[i], A[i]);
             d.m = m;
             d.c = (int32_t)c;
             d.sid = g->sid;
             d.b0 = (int32_t)(max(rs, x0) - rs);
             d.b1 = (int32_t)(min(rs + nbc, xe) - rs);
             d.task = g->first_task + u;
-            d.inside = L.layout == LAYOUT_BYTES ? (int32_t)run_inside(d, S.cbox + 2 * c, L) : 0;
+            if (MODE == MODE_INITIAL) d.inside = L.layout == LAYOUT_BYTES ? (int32_t)run_inside(d, S.cbox + 2 * c, L) : 0;
+        }
+        if (MODE != MODE_INITIAL) {
+            // the rotation rows of the round's tasks
+            const SearchDev& S = Sall[g->sid];
+            form_rows(rd, tasks + g->first_task, S, v0, nt, nrun);
+            __syncthreads();   // the rows are in
+            if (tid < nrun) {
+                RunDesc& d = rd[tid];
+                const LevelView& L = S.maps[d.m];
+                d.inside = L.layout == LAYOUT_BYTES ? (int32_t)run_inside(d, S.cbox + 2 * d.c, L) : 0;
+            }
         }
         if (tid == 0) {
             s_nrun = nrun;
@@ -508,18 +534,39 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
     }
 }
 
+// the second pass of the lexmin leaf over the current node array (kept out
+// of line: the survivor pass keeps its registers)
+__device__ __noinline__ void lex_rotation_pass(SearchDev* S, const FrontDev& F, const LoopState* LS)
+{
+    const int cur = LS->cur;
+    const int64_t n = min((int64_t)LS->fn[cur], F.cap);   // appends past the capacity were not stored
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t key = F.keys[cur][i];
+        Ctl* c = S[key >> 24].ctl;
+        if (c->reason != 3 || (int32_t)(key & 0xFFFFFFu) != c->sstar) continue;
+        const NodeRec nd = F.nodes[cur][i];
+        if (rl_level(nd.rl) != 0) continue;
+        if (lex_translation(nd) == c->lex_t) atomicMin(&c->lex_r, rl_rot(nd.rl));
+    }
+}
+
 // survivors: children scoring above their search's best, appended to the
 // frontier array the next iteration reads, with their bucket counts
 // (nodes, children, leaves) and the search's size and top bucket.  The
 // append position is claimed once per CTA (one atomic on the array's count
 // per 256 children instead of one per warp), and when the launch holds one
 // search its size and top bucket are raised once per CTA too.
+// First, when a search popped a leaf bucket this iteration, the second pass
+// of its lexmin leaf: the smallest rotation among the bucket's leaves at the
+// smallest translation key (the compaction's first pass found that key);
+// with lex_only nothing else.
 template <int MODE>
 __global__ void __launch_bounds__(256) finalize_kernel(const Plan* __restrict__ P, SearchDev* S,
                                                        const TaskRec* __restrict__ tasks, int32_t* dense, FrontDev F,
-                                                       LoopState* LS)
+                                                       LoopState* LS, int lex_only)
 {
-    if (P->status != PLAN_OK) return;
+    if (MODE == MODE_SEARCH && LS->lex_pass) lex_rotation_pass(S, F, LS);
+    if (lex_only || P->status != PLAN_OK) return;
     __shared__ uint32_t s_woff[8];
     __shared__ uint32_t s_total;
     __shared__ unsigned long long s_base;
@@ -633,49 +680,6 @@ __global__ void __launch_bounds__(256) finalize_kernel(const Plan* __restrict__ 
     }
 }
 
-// The rotation rows of every task of a launch: warp e of a CTA forms entry e
-// of 32 tasks, so the FP64 chains are short and spread over the whole GPU.
-// First, when a search popped a leaf bucket, the second pass of its lexmin
-// leaf: the smallest rotation among the bucket's leaves at the smallest
-// translation key (the first pass, in the compaction, found that key).
-__global__ void __launch_bounds__(288) task_rows_kernel(const Plan* __restrict__ P, const SearchDev* __restrict__ S,
-                                                        TaskRec* tasks, FrontDev F, const LoopState* LS)
-{
-    if (LS && LS->lex_pass) {
-        const int cur = LS->cur;
-        const int64_t n = min((int64_t)LS->fn[cur], F.cap);   // appends past the capacity were not stored
-        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-            const uint32_t key = F.keys[cur][i];
-            Ctl* c = S[key >> 24].ctl;
-            if (c->reason != 3 || (int32_t)(key & 0xFFFFFFu) != c->sstar) continue;
-            const NodeRec nd = F.nodes[cur][i];
-            if (rl_level(nd.rl) != 0) continue;
-            if (lex_translation(nd) == c->lex_t) atomicMin(&c->lex_r, rl_rot(nd.rl));
-        }
-    }
-    if (P->status != PLAN_OK) return;
-    const int64_t n = P->n_tasks;
-    const int e = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int64_t u = (int64_t)blockIdx.x * 32 + lane; u - lane < n; u += (int64_t)gridDim.x * 32) {
-        if (u >= n) continue;
-        const SearchDev& f = S[P->seg[find_task_seg(P, u)].sid];
-        const uint32_t rl = tasks[u].rl;
-        tasks[u].a[e] = rotation_entry(f.cs, f.grid, rl_level(rl), rl_rot(rl), e);
-        if (e == 0) tasks[u].pad[0] = tasks[u].pad[1] = tasks[u].pad[2] = 0.0f;
-    }
-}
-
-cudaError_t launch_task_rows(const Plan* P, const SearchDev* S, TaskRec* tasks, const FrontDev* F, const LoopState* LS,
-                             int blocks, cudaStream_t st)
-{
-    if (blocks <= 0) return cudaSuccess;
-    FrontDev f;
-    std::memset(&f, 0, sizeof(f));
-    if (F) f = *F;
-    task_rows_kernel<<<blocks, 288, 0, st>>>(P, S, tasks, f, F ? LS : nullptr);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_branch(int mode, Plan* P, const SearchDev* S, const TaskRec* tasks, int32_t* dense, int blocks,
                           cudaStream_t st, bool bytes_only)
 {
@@ -691,11 +695,11 @@ cudaError_t launch_branch(int mode, Plan* P, const SearchDev* S, const TaskRec* 
 }
 
 cudaError_t launch_finalize(int mode, const Plan* P, SearchDev* S, const TaskRec* tasks, int32_t* dense,
-                            const FrontDev& F, LoopState* LS, int blocks, cudaStream_t st)
+                            const FrontDev& F, LoopState* LS, int blocks, cudaStream_t st, bool lex_only)
 {
     if (blocks <= 0) return cudaSuccess;
-    if (mode == MODE_INITIAL) finalize_kernel<MODE_INITIAL><<<blocks, 256, 0, st>>>(P, S, tasks, dense, F, LS);
-    else finalize_kernel<MODE_SEARCH><<<blocks, 256, 0, st>>>(P, S, tasks, dense, F, LS);
+    if (mode == MODE_INITIAL) finalize_kernel<MODE_INITIAL><<<blocks, 256, 0, st>>>(P, S, tasks, dense, F, LS, 0);
+    else finalize_kernel<MODE_SEARCH><<<blocks, 256, 0, st>>>(P, S, tasks, dense, F, LS, lex_only ? 1 : 0);
     return cudaGetLastError();
 }
 

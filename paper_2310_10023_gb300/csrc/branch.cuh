@@ -93,15 +93,13 @@ struct LoopState {
 
 enum { MODE_INITIAL = 0, MODE_SEARCH = 1, MODE_DENSE = 2 };
 
-// One rotational child of a scoring round: its parent's translation,
-// rl_pack(child rotation, child level) and the rotation's rows
-// (rotation_rows).  Its 8 translational children are the dense scores
-// 8 * task .. 8 * task + 7.
+// One rotational child of a scoring round: its parent's translation and
+// rl_pack(child rotation, child level); the scoring kernel forms the
+// rotation's rows (rotation_entry) when it describes the task's runs.  Its 8
+// translational children are the dense scores 8 * task .. 8 * task + 7.
 struct __align__(16) TaskRec {
     int32_t tx, ty, tz;     // 2 x the parent's translation indices (the children add {0,1}^3)
     uint32_t rl;
-    float a[9];             // the child rotation's A = fl32(R / r), row-major
-    float pad[3];
 };
 
 // A run of tasks of one search inside a scoring launch.  The run's work is
@@ -161,12 +159,6 @@ __host__ __device__ __forceinline__ int32_t rot_children(const DevGrid& g, int l
     return n;
 }
 
-// the rotation rows of the launch's task records from their rl (when the plan
-// is PLAN_OK); with LS, first the second pass of the lexmin leaf search over
-// the current frontier
-cudaError_t launch_task_rows(const Plan* P, const SearchDev* S, TaskRec* tasks, const FrontDev* F, const LoopState* LS,
-                             int blocks, cudaStream_t st);
-
 // launch shape (bbs_tuning), resolved: every field in range
 struct Tuning {
     int64_t launch_tasks = TASK_CAP;
@@ -196,8 +188,9 @@ constexpr int BRANCH_CTAS_PER_SM = 4;
 cudaError_t launch_branch(int mode, Plan* P, const SearchDev* S, const TaskRec* tasks, int32_t* dense, int blocks,
                           cudaStream_t st, bool bytes_only);
 // survivors (score above their search's best) are appended to the frontier
-// array the next iteration reads, with their bucket counts
+// array the next iteration reads, with their bucket counts; in search mode
+// first the second lexmin pass of a popped leaf bucket (lex_only: that alone)
 cudaError_t launch_finalize(int mode, const Plan* P, SearchDev* S, const TaskRec* tasks, int32_t* dense,
-                            const FrontDev& F, LoopState* LS, int blocks, cudaStream_t st);
+                            const FrontDev& F, LoopState* LS, int blocks, cudaStream_t st, bool lex_only = false);
 
 }  // namespace bbs

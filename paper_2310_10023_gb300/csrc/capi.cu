@@ -356,7 +356,7 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
                         r.tz = 2 * recs[(size_t)p].cz;
                         r.rl = rl_pack(crot, l - 1);
                         tk_parent[(size_t)u] = p;
-                        tk[(size_t)u++] = r;   // rows filled on the device
+                        tk[(size_t)u++] = r;   // the scoring kernel forms the rows
                     }
         }
     }
@@ -414,10 +414,9 @@ int bbs_score_children(const bbs_maps* m, const float* scan_xyz, int64_t k, int 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     int rc = BBS_OK;
-    cudaError_t e = launch_task_rows(d_plan, d_sd, d_tk, nullptr, nullptr, (int)std::min<int64_t>((ntask + 31) / 32, 4096), st);
-    if (e == cudaSuccess)
-        e = launch_branch(MODE_SEARCH, d_plan, d_sd, d_tk, d_dense,
-                          (int)std::min<int64_t>(P.n_slices, (int64_t)nsm * BRANCH_CTAS_PER_SM), st, maps_all_bytes(m));
+    cudaError_t e = launch_branch(MODE_SEARCH, d_plan, d_sd, d_tk, d_dense,
+                                  (int)std::min<int64_t>(P.n_slices, (int64_t)nsm * BRANCH_CTAS_PER_SM), st,
+                                  maps_all_bytes(m));
     std::vector<int32_t> dense((size_t)total);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dense.data(), d_dense, sizeof(int32_t) * dense.size(), cudaMemcpyDeviceToHost, st);

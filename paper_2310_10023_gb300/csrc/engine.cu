@@ -18,9 +18,10 @@
 //   compact  the current node array: popped nodes become parents and tasks
 //            (their rotational children), kept ones move to the other array,
 //            cleared ones go; a popped leaf bucket's leaves give the lexmin key
-//   rows     rotation rows of every task (and the lexmin rotation)
-//   score    (branch.cu) every child of every task; survivors above best are
-//            appended to the other array with their bucket counts
+//   score    (branch.cu) every child of every task (the kernel forms each
+//            task's rotation rows); then the lexmin rotation of a popped leaf
+//            bucket, and survivors above best appended to the other array
+//            with their bucket counts
 // Only popping a leaf changes a search's best, so how its batch is split into
 // launches, and which other searches share them, cannot change its result;
 // node order inside F is free.
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
 }
 
 // the tasks (rotational children, Eq. (13)) of parent nd for t in [t0, t1),
-// written at tasks[dst + t]: translation and rl (task_rows_kernel adds the rows)
+// written at tasks[dst + t]: translation and rl (the scoring kernel forms the rows)
 __device__ __forceinline__ void write_tasks(const DevGrid& g, const NodeRec& nd, const int32_t lo[3],
                                             const int32_t ext[3], int32_t t0, int32_t t1, TaskRec* tasks, int64_t dst)
 {
@@ -909,8 +910,9 @@ void Engine::launch_compact(cudaStream_t s)
                                            d_pcnt_, d_tcnt_);
 }
 
-// one host-driven iteration: select (+ plan), compaction and rows on the
-// device, then one synchronization; the scoring launch follows the plan
+// one host-driven iteration: select (+ plan), compaction and the second
+// lexmin pass on the device, then one synchronization; the scoring launch
+// follows the plan
 int Engine::step(std::vector<int>* finished)
 {
     finish_never_live(finished);
@@ -920,7 +922,8 @@ int Engine::step(std::vector<int>* finished)
     BBS_CUDA_TRY(cudaMemcpyAsync(&d_plan_->iters, &h_plan_.iters, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, st_));
     launch_select(st_, 0, 0);
     launch_compact(st_);
-    BBS_CUDA_TRY(launch_task_rows(d_plan_, d_S_, tasks_, &front_, d_ls_, nsm_ * 4, st_));
+    // the lexmin leaf must be complete when the control blocks are read below
+    BBS_CUDA_TRY(launch_finalize(MODE_SEARCH, d_plan_, d_S_, tasks_, dense_, front_, d_ls_, nsm_ * 8, st_, true));
     launches_ += 3;
     BBS_CUDA_TRY(cudaGetLastError());
     BBS_CUDA_TRY(cudaMemcpyAsync(h_misc_, &d_plan_->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
@@ -1001,10 +1004,9 @@ int Engine::build_graph()
     cudaGraph_t body = e == cudaSuccess ? np.conditional.phGraph_out[0] : nullptr;
     if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        // one iteration: select (+ plan), compaction, rows, score (+ survivors)
+        // one iteration: select (+ plan), compaction, score (+ lexmin, survivors)
         launch_select(cs, cond, 1);
         launch_compact(cs);
-        launch_task_rows(d_plan_, d_S_, tasks_, &front_, d_ls_, nsm_ * 4, cs);
         launch_branch(MODE_SEARCH, d_plan_, d_S_, tasks_, dense_, nsm_ * tune_.ctas_per_sm, cs, graph_bytes_);
         launch_finalize(MODE_SEARCH, d_plan_, d_S_, tasks_, dense_, front_, d_ls_, nsm_ * 8, cs);
         cudaGraph_t out = nullptr;
@@ -1045,7 +1047,7 @@ int Engine::iterate(int max_iters, std::vector<int>* finished)
     BBS_CUDA_TRY(cudaMemcpyAsync(h_misc_, &d_plan_->status, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
     BBS_TRY(read_ctl());
     const int32_t status = h_misc_[0];
-    launches_ += 5 * (int64_t)h_misc_[1];   // every iteration of the loop runs the body's 5 kernels
+    launches_ += 4 * (int64_t)h_misc_[1];   // every iteration of the loop runs the body's 4 kernels
     mark_finished(finished);
     if (status == PLAN_OVERFLOW) return score_overflow();   // the selected round did not fit one launch
     return BBS_OK;
@@ -1179,11 +1181,6 @@ int Engine::score_launch(int mode, const std::vector<Seg>* segs, int64_t n_slice
         // pageable source: staged before cudaMemcpyAsync returns, so h_plan_ may be rewritten
         BBS_CUDA_TRY(cudaMemcpyAsync(d_plan_, &h_plan_, offsetof(Plan, seg) + sizeof(Seg) * segs->size(),
                                      cudaMemcpyHostToDevice, st_));
-        if (mode == MODE_SEARCH) {
-            BBS_CUDA_TRY(launch_task_rows(d_plan_, d_S_, tasks_, nullptr, nullptr,
-                                          (int)std::min<int64_t>((n_tasks + 31) / 32, 4 * nsm_), st_));
-            launches_ += 1;
-        }
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (timed_) {

@@ -130,7 +130,7 @@ int hostqueue_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device,
     // scores of the 8 translational children of every task, on the GPU
     std::vector<TaskRec> tk;
     std::vector<int32_t> dense;
-    auto score_tasks = [&](int mode) -> int {
+    auto score_tasks = [&]() -> int {
         const int64_t n = (int64_t)tk.size();
         if (n == 0) return BBS_OK;
         BBS_TRY(D.reserve(n));
@@ -149,10 +149,6 @@ int hostqueue_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device,
         BBS_CUDA_TRY(cudaMemcpyAsync(D.plan, &P, offsetof(Plan, seg) + sizeof(Seg), cudaMemcpyHostToDevice, st));
         BBS_CUDA_TRY(cudaMemsetAsync(D.dense, 0, sizeof(int32_t) * 8 * (size_t)n, st));
         res->h2d_bytes += (int64_t)(sizeof(TaskRec) * (size_t)n + offsetof(Plan, seg) + sizeof(Seg));
-        if (mode == MODE_SEARCH) {   // rows of the top level come from its table below
-            BBS_CUDA_TRY(launch_task_rows(D.plan, D.sd, D.tasks, nullptr, nullptr,
-                                          (int)std::min<int64_t>((n + 31) / 32, 4 * nsm), st));
-        }
         BBS_CUDA_TRY(launch_branch(MODE_SEARCH, D.plan, D.sd, D.tasks, D.dense,
                                    (int)std::min<int64_t>(P.n_slices, (int64_t)nsm * tn.ctas_per_sm), st,
                                    maps_all_bytes(m)));
@@ -201,10 +197,6 @@ int hostqueue_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device,
             pext[a] = floor_half(hg.wmax[a]) - pmin[a] + 1;
         }
         const int64_t R = hg.nrot[lmax];
-        // rows of the top level from its table (3 float4 per rotation)
-        std::vector<float4> rows((size_t)(3 * R));
-        BBS_CUDA_TRY(cudaMemcpyAsync(rows.data(), S.rot, sizeof(float4) * rows.size(), cudaMemcpyDeviceToHost, st));
-        BBS_CUDA_TRY(cudaStreamSynchronize(st));
         tk.clear();
         for (int64_t px = 0; px < pext[0]; ++px)
             for (int64_t py = 0; py < pext[1]; ++py)
@@ -216,12 +208,9 @@ int hostqueue_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device,
                         t.ty = (int32_t)(2 * (pmin[1] + py));
                         t.tz = (int32_t)(2 * (pmin[2] + pz));
                         t.rl = rl_pack((uint32_t)r, lmax);
-                        const float4* A = &rows[(size_t)(3 * r)];
-                        const float a9[9] = {A[0].x, A[0].y, A[0].z, A[1].x, A[1].y, A[1].z, A[2].x, A[2].y, A[2].z};
-                        std::memcpy(t.a, a9, sizeof(a9));
                         tk.push_back(t);
                     }
-        BBS_TRY(score_tasks(MODE_INITIAL));
+        BBS_TRY(score_tasks());
         int64_t n0 = 1;
         for (int a = 0; a < 3; ++a) n0 *= hg.wmax[a] - hg.wmin[a] + 1;
         res->nodes_scored = n0 * R;
@@ -269,7 +258,7 @@ int hostqueue_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device,
         for (size_t u0 = 0; u0 < all.size(); u0 += (size_t)tn.launch_tasks) {
             const size_t u1 = std::min(all.size(), u0 + (size_t)tn.launch_tasks);
             tk.assign(all.begin() + (long)u0, all.begin() + (long)u1);
-            BBS_TRY(score_tasks(MODE_SEARCH));
+            BBS_TRY(score_tasks());
             for (size_t u = 0; u < tk.size(); ++u)
                 for (int j = 0; j < 8; ++j) {
                     const int32_t sc = dense[8 * u + j];
