@@ -43,6 +43,8 @@ def _args():
     p.add_argument("--warmup", type=int, default=4)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--scans", type=int, default=8, help="distinct scans cycled by the steps")
+    p.add_argument("--workload", choices=["indoor", "outdoor"], default=WORKLOAD,
+                   help="the workload of the timed steps (indoor: the headline configuration)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip the batched and served forms")
     p.add_argument("--autotune", action="store_true",
@@ -79,8 +81,10 @@ def rank_scans(rank: int, n: int) -> list:
 
 
 def _workload_desc(w, m_points, k_mean, scans):
-    return {"workload": f"indoor multi-room floor 100x60x10 m, {m_points / 1e6:.2f} M map points, "
-                        f"r={w.r} m, {w.levels} levels; 16-beam scans of ~{k_mean:.0f} points",
+    scene = ("indoor multi-room floor 100x60x10 m" if w.name == "indoor" else "outdoor city 800x800x40 m")
+    beams = 16 if w.name == "indoor" else 64
+    return {"workload": f"{scene}, {m_points / 1e6:.2f} M map points, "
+                        f"r={w.r} m, {w.levels} levels; {beams}-beam scans of ~{k_mean:.0f} points",
             "form": "plain (one scan per bbs_localize)", "batch": w.batch, "score_frac": w.score_frac,
             "roll_pitch_range_deg": 6.0, "yaw_range": "0..2pi", "distinct_scans": scans,
             "l2": "flushed between timed steps (512 MiB write)"}
@@ -186,7 +190,7 @@ def run_reference(a):
     import numpy as np
 
     from paper_2310_10023_gb300 import synth
-    w = synth.WORKLOADS[WORKLOAD]
+    w = synth.WORKLOADS[a.workload]
     m = synth.make_map(w.scene)
     scan, _ = synth.make_scan(w.scene, 0)
     om, g, nodes = _oracle_sample(w, m, scan, 1000, 7)
@@ -467,11 +471,11 @@ def _kernel_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic_from_profile():
+def _traffic_from_profile(workload=WORKLOAD):
     """DRAM bytes per launch of the scoring kernel from the committed ncu
-    summary (profiles/branch3_kernel_indoor.md, "key: value" lines), if it was
-    taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "branch3_kernel_indoor.md")
+    summary of the workload (profiles/branch3_kernel_<workload>.md, "key:
+    value" lines), if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", f"branch3_kernel_{workload}.md")
     if not os.path.exists(p):
         return None
     kv = {}
@@ -506,7 +510,7 @@ def run_ours(a):
     nv.load()
     stream = torch.cuda.current_stream()
 
-    w = synth.WORKLOADS[WORKLOAD]
+    w = synth.WORKLOADS[a.workload]
     m = synth.make_map(w.scene)
     md = torch.from_numpy(np.array(m)).to(dev)
     scans = [synth.make_scan(w.scene, i)[0] for i in rank_scans(rank, a.scans)]
@@ -652,7 +656,7 @@ def run_ours(a):
             "map_build_ms": build_ms,
             "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Gop/s",
                          "frac": alu_achieved / alu_peak,
-                         "traffic": _traffic_from_profile(),
+                         "traffic": _traffic_from_profile(a.workload),
                          "kernel": "branch3_kernel (fused branch + Eq. (11) scoring)",
                          "algorithmic_ops": f"{ALG_OPS_PER_UNIT} per scan point per rotational child "
                                             "(rotation 15, floor 3, level key 6, 8 child counts)",
