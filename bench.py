@@ -49,6 +49,9 @@ def _args():
     p.add_argument("--no-forms", action="store_true", help="skip the batched and served forms")
     p.add_argument("--autotune", action="store_true",
                    help="choose the launch shape and table load with the autotuner (cached per GPU and workload)")
+    p.add_argument("--tune-batch", action="store_true",
+                   help="with --autotune, also choose the node batch (4k-64k) among those that keep every "
+                        "tuning scan's best score")
     p.add_argument("--host-driven", action="store_true",
                    help="iterate searches from the host instead of the device-driven graph loop")
     return p.parse_args()
@@ -80,12 +83,12 @@ def rank_scans(rank: int, n: int) -> list:
     return [rank * n + i for i in range(n)]
 
 
-def _workload_desc(w, m_points, k_mean, scans):
+def _workload_desc(w, m_points, k_mean, scans, batch=None):
     scene = ("indoor multi-room floor 100x60x10 m" if w.name == "indoor" else "outdoor city 800x800x40 m")
     beams = 16 if w.name == "indoor" else 64
     return {"workload": f"{scene}, {m_points / 1e6:.2f} M map points, "
                         f"r={w.r} m, {w.levels} levels; {beams}-beam scans of ~{k_mean:.0f} points",
-            "form": "plain (one scan per bbs_localize)", "batch": w.batch, "score_frac": w.score_frac,
+            "form": "plain (one scan per bbs_localize)", "batch": batch or w.batch, "score_frac": w.score_frac,
             "roll_pitch_range_deg": 6.0, "yaw_range": "0..2pi", "distinct_scans": scans,
             "l2": "flushed between timed steps (512 MiB write)"}
 
@@ -516,21 +519,26 @@ def run_ours(a):
     scans = [synth.make_scan(w.scene, i)[0] for i in rank_scans(rank, a.scans)]
     scans_d = [torch.from_numpy(s).to(dev) for s in scans]
     tuning = None
-    if a.autotune:
+    batch = w.batch
+    if a.autotune or a.tune_batch:
         from paper_2310_10023_gb300 import autotune
         props = torch.cuda.get_device_properties(dev)
         targs = nv.workload_args(w, stream=stream.cuda_stream)
         out = autotune.tuned(props.name, props.multi_processor_count, lambda: nv.bbs_build_maps(md, w.r, w.levels),
-                             scans_d[:4], targs.ranges, targs.opts, w.r, w.levels, [len(s) for s in scans])
+                             scans_d[:4], targs.ranges, targs.opts, w.r, w.levels, [len(s) for s in scans],
+                             tune_batch=a.tune_batch)
         tuning = dict(out["best"], cached=out["cached"])
+        if a.tune_batch:
+            batch = int(out["batch"])
+            tuning["batch"] = batch
     torch.cuda.synchronize()
     t = time.perf_counter()
     maps = nv.bbs_build_maps(md, w.r, w.levels)
     torch.cuda.synchronize()
     build_ms = (time.perf_counter() - t) * 1e3
     del md
-    args = nv.workload_args(w, stream=stream.cuda_stream, flags=nv.TIME_KERNELS)
-    args_plain = nv.workload_args(w, stream=stream.cuda_stream,
+    args = nv.workload_args(w, stream=stream.cuda_stream, flags=nv.TIME_KERNELS, batch=batch)
+    args_plain = nv.workload_args(w, stream=stream.cuda_stream, batch=batch,
                                   flags=nv.HOST_DRIVEN if a.host_driven else 0)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
@@ -643,7 +651,7 @@ def run_ours(a):
             "metric": METRIC, "value": probes_all / (total_ms / 1e3), "unit": "probes/s", "n_gpus": ws,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(_workload_desc(w, len(m), statistics.mean(len(s) for s in scans), a.scans),
+            "config": dict(_workload_desc(w, len(m), statistics.mean(len(s) for s in scans), a.scans, batch),
                            launch_shape=tuning or dict(nv.bbs_get_tuning(), layout=0, load_factor=0.25, source="defaults"),
                            map_layout=sorted({nv.LAYOUT_NAMES[nv.bbs_maps_layout(maps, l)] for l in range(w.levels)})),
             "ms_to_optimum": to_opt,

@@ -5,9 +5,15 @@ What is tuned never changes a result: the level maps' layout (byte grids
 where a level's box allows, or hashed bricks everywhere), the load factor of
 the hashed tables (probe length vs footprint; byte grids have none), the
 share of a scoring launch split statically over the CTAs, the smallest
-dynamic grab, and the scoring CTAs per SM.  The batch size b is part of the search's definition (it changes the
-trajectory, Algorithm 2) and is not tuned.  Every candidate's results are
+dynamic grab, and the scoring CTAs per SM.  Every candidate's results are
 compared with the first candidate's; a candidate that differs is an error.
+
+The node batch b is tuned only on request (search_batch, tuned(...,
+tune_batch=True)): b is part of the search's definition (it changes the
+trajectory, Algorithm 2) and, under the approximate rotational bound, can
+change the best score found.  A candidate b is accepted only when every
+tuning scan reaches the same best score as with the caller's b; the fastest
+accepted b is kept.
 
 Coordinate descent: each knob in turn, the others held at their best so far;
 the time of a candidate is the median over `reps` passes of bbs_localize on
@@ -143,16 +149,73 @@ def search(build_maps, scans, ranges, opts, reps: int = 3, space: dict | None = 
     return {"best": best, "ms": best_ms, "trials": trials}
 
 
+BATCHES = (4096, 8192, 16384, 32768, 65536)   # the node batches the workloads allow
+
+
+def search_batch(maps, scans, ranges, opts, batches=BATCHES, reps: int = 3, timer=None, sync=None,
+                 localize=None) -> dict:
+    """The fastest node batch b among `batches` that keeps every scan's best
+    score equal to the one reached with opts.batch (the reference).
+
+    Time of a candidate: the median over `reps` passes of localizing every
+    scan.  Returns {"batch": b, "ms": per-pass ms, "trials": [{"batch", "ms",
+    "best_scores", "nodes_scored", "accepted"}]}; with no accepted candidate
+    faster than the reference, the reference b.
+    """
+    if sync is None:
+        import torch
+        sync = torch.cuda.synchronize
+    timer = timer or time.perf_counter
+    localize = localize or nv.bbs_localize
+    ref_b = int(opts.batch)
+    trials = []
+
+    def run(b):
+        o = nv.Opts.from_buffer_copy(opts)   # the caller's options, this batch
+        o.batch = int(b)
+        res = [localize(maps, s, ranges, o) for s in scans]   # warm-up, and the scores compared
+        times = []
+        for _ in range(reps):
+            sync()
+            t = timer()
+            for s in scans:
+                localize(maps, s, ranges, o)
+            sync()
+            times.append((timer() - t) * 1e3)
+        return statistics.median(times), [r.best_score for r in res], sum(int(r.nodes_scored) for r in res)
+
+    ref_ms, ref_scores, ref_nodes = run(ref_b)
+    trials.append({"batch": ref_b, "ms": ref_ms, "best_scores": ref_scores, "nodes_scored": ref_nodes,
+                   "accepted": True})
+    best_b, best_ms = ref_b, ref_ms
+    for b in batches:
+        if int(b) == ref_b:
+            continue
+        ms, scores, nodes = run(b)
+        ok = scores == ref_scores
+        trials.append({"batch": int(b), "ms": ms, "best_scores": scores, "nodes_scored": nodes, "accepted": ok})
+        if ok and ms < best_ms:
+            best_b, best_ms = int(b), ms
+    return {"batch": best_b, "ms": best_ms, "trials": trials}
+
+
 def tuned(gpu: str, sms: int, build_maps, scans, ranges, opts, r: float, levels: int, ks, path: str | None = None,
-          **kw) -> dict:
+          tune_batch: bool = False, **kw) -> dict:
     """The cached launch shape for this GPU and workload shape, searched and
-    stored on a miss; applied before returning."""
-    key = workload_key(gpu, sms, r, levels, int(opts.batch), ks)
+    stored on a miss; applied before returning.  With tune_batch, the entry
+    also holds the node batch search_batch picked ("batch"; the caller sets
+    it in its options)."""
+    key = workload_key(gpu, sms, r, levels, int(opts.batch), ks) + (";tuned-b" if tune_batch else "")
     hit = load_cache(path).get(key)
     if hit is not None:
         apply(hit["best"])
         return dict(hit, cached=True)
     out = search(build_maps, scans, ranges, opts, **kw)
     entry = {"best": out["best"], "ms": out["ms"], "trials": out["trials"]}
+    if tune_batch:
+        m = build_maps()
+        bt = search_batch(m, scans, ranges, opts, reps=kw.get("reps", 3), timer=kw.get("timer"),
+                          sync=kw.get("sync"))
+        entry.update(batch=bt["batch"], batch_ms=bt["ms"], batch_trials=bt["trials"])
     store(key, entry, path)
     return dict(entry, cached=False)

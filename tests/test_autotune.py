@@ -45,3 +45,61 @@ def test_autotune_keeps_results(tmp_path):
         nv.bbs_set_tuning(reset=True)
         nv.bbs_set_load_factor(0.25)
         nv.bbs_set_probe_layout(0)
+
+
+def test_batch_search_keeps_the_best_score():
+    """search_batch takes the fastest batch among those that keep every
+    scan's best score (a faster batch that loses a point is refused)."""
+    from types import SimpleNamespace
+
+    from paper_2310_10023_gb300 import native as nv
+    # scripted searches: per batch, (best scores of the two scans, ms per localization)
+    script = {16384: ([950, 960], 1.0), 4096: ([950, 960], 0.9), 8192: ([950, 959], 0.5),
+              32768: ([950, 960], 0.8), 65536: ([950, 960], 1.2)}
+    clock = {"t": 0.0}
+
+    def localize(maps, scan, ranges, o):
+        scores, ms = script[int(o.batch)]
+        clock["t"] += ms / 1e3
+        return SimpleNamespace(best_score=scores[scan], nodes_scored=int(o.batch))
+
+    opts = nv.make_opts(batch=16384, stream=0)
+    out = autotune.search_batch(None, [0, 1], None, opts, reps=2, timer=lambda: clock["t"], sync=lambda: None,
+                                localize=localize)
+    assert out["batch"] == 32768                                  # 8192 is faster but changes a score
+    by_b = {t["batch"]: t for t in out["trials"]}
+    assert not by_b[8192]["accepted"] and by_b[4096]["accepted"] and by_b[65536]["accepted"]
+    assert by_b[16384]["ms"] == pytest.approx(2.0) and out["ms"] == pytest.approx(1.6)
+    assert opts.batch == 16384                                    # the caller's options are left alone
+
+
+@pytest.mark.gpu
+def test_tuned_batch_keeps_best_scores(tmp_path):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_10023_gb300 import build, native as nv
+    build.build()
+    nv.load()
+    w = synth.WORKLOADS["room"]
+    m = synth.make_map(w.scene)
+    scans = [torch.from_numpy(synth.make_scan(w.scene, i)[0]).cuda() for i in range(3)]
+    rg = nv.make_ranges(w.lo, w.hi, w.ang_lo, w.ang_hi)
+    op = nv.make_opts(score_frac=w.score_frac, batch=w.batch)
+    p = str(tmp_path / "tuning.json")
+    try:
+        out = autotune.tuned("gpu", 1, lambda: nv.bbs_build_maps(m, w.r, w.levels), scans, rg, op, w.r, w.levels,
+                             [len(s) for s in scans], path=p, reps=1, space={"static_pm": [500]}, tune_batch=True)
+        assert out["batch"] in set(autotune.BATCHES) | {w.batch}
+        assert {t["batch"] for t in out["batch_trials"]} == set(autotune.BATCHES) | {w.batch}
+        dm = nv.bbs_build_maps(m, w.r, w.levels)
+        ref = [nv.bbs_localize(dm, s, rg, op).best_score for s in scans]
+        tb = nv.make_opts(score_frac=w.score_frac, batch=out["batch"])
+        assert [nv.bbs_localize(dm, s, rg, tb).best_score for s in scans] == ref
+        again = autotune.tuned("gpu", 1, None, scans, rg, op, w.r, w.levels, [len(s) for s in scans], path=p,
+                               tune_batch=True)
+        assert again["cached"] and again["batch"] == out["batch"]
+    finally:
+        nv.bbs_set_tuning(reset=True)
+        nv.bbs_set_load_factor(0.25)
+        nv.bbs_set_probe_layout(0)
