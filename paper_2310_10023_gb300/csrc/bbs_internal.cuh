@@ -104,14 +104,17 @@ struct DevGrid {
 // fl32(fl64(x / r)).  q = fl64(x * fl64(1/r)) lies within 3 units in the last
 // place of x / r, so fl32(q) is the float of the exact quotient unless q sits
 // near a float rounding midpoint (its low 29 bits within 64 of 2^28) or
-// outside the normal float range; those cases divide exactly.
+// outside the normal float range; those cases divide exactly.  Both tests
+// read q's bits (integer work): |q| in [2^-120, 2^120) is a biased exponent
+// in [1023 - 120, 1023 + 120) (zero, subnormals, infinities and NaN fall
+// outside).
 __device__ __forceinline__ float div_r_f32(double x, double r, double inv_r)
 {
     const double q = __dmul_rn(x, inv_r);
-    const double aq = fabs(q);
     const uint32_t lo = (uint32_t)__double2loint(q) & 0x1FFFFFFFu;
     const uint32_t d = lo > 0x10000000u ? lo - 0x10000000u : 0x10000000u - lo;
-    if (d > 64u && aq >= 0x1p-120 && aq < 0x1p120) return __double2float_rn(q);
+    const uint32_t e = ((uint32_t)__double2hiint(q) >> 20) & 0x7FFu;
+    if (d > 64u && e - (1023u - 120u) < 240u) return __double2float_rn(q);
     return __double2float_rn(__ddiv_rn(x, r));
 }
 

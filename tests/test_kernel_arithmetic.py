@@ -117,3 +117,24 @@ def test_inside_bound_has_no_false_positive():
                 keys = fl + o[None, :]
                 assert keys.min() >= 0 and np.all(keys <= (rmax + 1)[None, :])
     assert admitted > 100
+
+
+def test_exponent_range_test():
+    """The FP32 rounding of R / r takes its fast path when |q| lies in
+    [2^-120, 2^120); testing the biased exponent e as the unsigned
+    (e - 903) mod 2^32 < 240 is the same test for every double, signed
+    zeros, subnormals, both bounds, infinities and NaN included."""
+    def by_value(q):
+        return abs(q) >= 2.0 ** -120 and abs(q) < 2.0 ** 120
+
+    def by_bits(q):
+        e = (struct.unpack("<Q", struct.pack("<d", q))[0] >> 52) & 0x7FF
+        return (e - (1023 - 120)) % (1 << 32) < 240
+
+    edge = [0.0, 5e-324, 2.0 ** -1022, 2.0 ** -120, 2.0 ** 120, 1.0, 1e300, math.inf, math.nan]
+    edge += [np.nextafter(v, d) for v in (2.0 ** -120, 2.0 ** 120) for d in (0.0, math.inf)]
+    rng = np.random.default_rng(3)
+    vals = edge + list(np.ldexp(rng.uniform(1, 2, 20000), rng.integers(-1074, 1024, 20000)))
+    for v in vals:
+        for q in (float(v), -float(v)):
+            assert by_value(q) == by_bits(q), q
