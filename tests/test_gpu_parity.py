@@ -324,6 +324,65 @@ def test_not_found_and_empty(nv, room_pair):
         nv.bbs_localize(dm, s, nr, nv.make_opts(flags=nv.PRUNE_GE))
 
 
+@pytest.mark.parametrize("levels", [1, 2])
+def test_shallow_pyramids_equal_oracle(nv, levels):
+    """Degenerate pyramids: with one level the initial set is the leaves
+    themselves (the first pop ends the search), with two the search branches
+    once; both follow the oracle exactly."""
+    w = synth.WORKLOADS["room"]
+    m = synth.make_map(w.scene)
+    s, pose = synth.make_scan(w.scene, 0)
+    s = np.ascontiguousarray(s[:300])
+    x0, y0 = math.floor(pose[0] / 2) * 2 - 1.0, math.floor(pose[1] / 2) * 2 - 1.0
+    lo, hi = (x0, y0, 0.0), (x0 + 3.9, y0 + 3.9, 2.9)
+    alo, ahi = (-0.03, -0.03, pose[5] - 0.2), (0.03, 0.03, pose[5] + 0.2)
+    dm = nv.bbs_build_maps(m, w.r, levels)
+    om = oracle.Maps(m, w.r, levels)
+    res = nv.bbs_localize(dm, s, nv.make_ranges(lo, hi, alo, ahi), nv.make_opts(score_frac=0.8, batch=2000))
+    ores = oracle.localize(om, s, oracle.make_ranges(lo, hi, alo, ahi), score_frac=0.8, batch=2000)
+    _same_search(res, ores)
+    assert res.status == nv.OK
+
+
+@pytest.mark.parametrize("kind", ["one_location", "origin_only"])
+def test_degenerate_scans_equal_oracle(nv, room_pair, kind):
+    """Scans whose points all sit at one location (every score is 0 or K)
+    and a single point at the sensor origin (d_max = 0: one angle segment per
+    axis at every level) follow the oracle exactly."""
+    w, m, dm, om = room_pair
+    s, pose = synth.make_scan(w.scene, 0)
+    sc = np.repeat(s[5:6], 64, axis=0) if kind == "one_location" else np.zeros((1, 3), np.float32)
+    x0, y0 = math.floor(pose[0] / 2) * 2 - 1.0, math.floor(pose[1] / 2) * 2 - 1.0
+    lo, hi = (x0, y0, 0.0), (x0 + 3.9, y0 + 3.9, 2.9)
+    alo, ahi = (-0.03, -0.03, pose[5] - 0.2), (0.03, 0.03, pose[5] + 0.2)
+    res = nv.bbs_localize(dm, sc, nv.make_ranges(lo, hi, alo, ahi), nv.make_opts(score_frac=0.8, batch=2000))
+    ores = oracle.localize(om, sc, oracle.make_ranges(lo, hi, alo, ahi), score_frac=0.8, batch=2000)
+    _same_search(res, ores)
+    assert res.status == nv.OK and res.best_score == len(sc)
+
+
+def test_size_limits(nv, room_pair):
+    """The largest inputs the ABI takes: a scan of more than 2^24 - 2 points
+    (its score must fit the frontier key's 24-bit field) and more than 4096
+    scans per bbs_localize_many call are refused before any device work, and
+    the handle stays usable."""
+    w, m, dm, om = room_pair
+    nr, _ = _ranges(nv, w)
+    big = torch.zeros(((1 << 24) - 1, 3), dtype=torch.float32, device="cuda")
+    for fn in (nv.bbs_localize, nv.bbs_localize_hostqueue):
+        with pytest.raises(nv.BBSError) as e:
+            fn(dm, big, nr)
+        assert e.value.code == nv.EINVAL and "2^24" in str(e.value), fn.__name__
+    del big
+    s, _ = synth.make_scan(1, 0)
+    tiny = torch.from_numpy(s[:4]).cuda()
+    with pytest.raises(nv.BBSError) as e:
+        nv.bbs_localize_many(dm, [tiny] * 4097, nr)
+    assert e.value.code == nv.EINVAL and "4096" in str(e.value)
+    res = nv.bbs_localize(dm, s, nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch))
+    assert res.status == nv.OK
+
+
 def test_frontier_capacity_error(nv, room_pair):
     w, m, dm, om = room_pair
     s, _ = synth.make_scan(1, 0)
