@@ -119,3 +119,31 @@ def test_cancel_queued(nv, two_maps):
             nv.bbs_server_poll(srv, t, 2000)
         assert e.value.code == nv.EINVAL
     srv.close()
+
+
+def test_cancel_running(nv, two_maps):
+    """A request cancelled while it runs stops (its nodes are purged from the
+    shared frontier between iterations) and the request running beside it
+    still gets exactly its result alone."""
+    w, dm = two_maps["indoor"]
+    rg, op = _args(nv, w)
+    slow = nv.make_opts(score_frac=0.5, batch=256, stream=0)     # many small rounds
+    srv = nv.bbs_server_create(max_active=4, max_frontier=1 << 22)
+    s_slow, s_norm = synth.make_scan(2, 70)[0], synth.make_scan(2, 71)[0]
+    t_slow = nv.bbs_server_submit(srv, dm, s_slow, rg, slow)
+    t_norm = nv.bbs_server_submit(srv, dm, s_norm, rg, op)
+    for _ in range(4000):                                       # until the worker has admitted it
+        if nv.bbs_server_stats(srv)["active"] >= 1:
+            break
+        time.sleep(0.0005)
+    try:
+        nv.bbs_server_cancel(srv, t_slow)
+    except nv.BBSError as e:                                    # it finished first
+        assert e.code == nv.EINVAL
+    st, r = nv.bbs_server_poll(srv, t_slow, 20000)
+    assert st in (nv.ECANCELED, nv.OK, nv.NOT_FOUND, nv.ENOMEM)
+    st2, r2 = nv.bbs_server_poll(srv, t_norm, 20000)
+    assert st2 in (nv.OK, nv.NOT_FOUND)
+    assert nv.bbs_server_stats(srv)["active"] == 0
+    srv.close()
+    assert _same(r2, nv.bbs_localize(dm, s_norm, rg, nv.make_opts(score_frac=w.score_frac, batch=w.batch)))
