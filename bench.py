@@ -345,7 +345,7 @@ def run_gicp(nv, torch, maps, w, stream, n_scans=8):
         res = nv.bbs_localize(maps, sd, a.ranges, a.opts)
         if res.status != nv.OK:
             continue
-        R0, t0 = nv.pose_to_rt(res.pose)
+        R0, t0 = nv.bbs_pose_matrix(res.pose)
         nv.bbs_gicp(target, sd, R0, t0, go)   # warm
         torch.cuda.synchronize()
         t = time.perf_counter()
@@ -354,7 +354,7 @@ def run_gicp(nv, torch, maps, w, stream, n_scans=8):
         ms.append((time.perf_counter() - t) * 1e3)
         its.append(g.iterations)
         ncorr.append(g.correspondences / len(s_))
-        Rt, tt = nv.pose_to_rt(pose)
+        Rt, tt = nv.bbs_pose_matrix(pose)
         Rg, tg = g.Rt()
         e0.append(float(np.linalg.norm(t0 - tt)))
         e1.append(float(np.linalg.norm(tg - tt)))

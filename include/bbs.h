@@ -147,6 +147,13 @@ typedef struct {
     int64_t d2h_bytes;      /* device-to-host bytes the call copied                           */
 } bbs_result;
 
+/* bbs_pose_matrix -- the rigid transform of a result pose (x, y, z, roll,
+ * pitch, yaw; Sec. III-A names the angles): R = Rz(yaw) Ry(pitch) Rx(roll),
+ * row-major 3 x 3 in FP64, the composition the pose grid's rotations use,
+ * and t = (x, y, z).  A scan point s maps to R s + t.  Host memory; feeds
+ * bbs_gicp's (R0, t0).  BBS_EINVAL for a NULL argument or a non-finite pose. */
+int  bbs_pose_matrix(const double pose[6], double R[9], double t[3]);
+
 /* ---- maps: Sec. III-C ---------------------------------------------------
  * bbs_build_maps -- build the per-level voxel maps H^l on the current device.
  *   xyz, n    : map cloud (n x 3 float32), host or device per is_device.
@@ -182,6 +189,10 @@ int  bbs_maps_info(const bbs_maps* maps, int level, int64_t* n_voxels, int64_t* 
 #define BBS_LAYOUT_DENSE   2
 #define BBS_LAYOUT_BYTES   3
 int  bbs_maps_layout(const bbs_maps* maps, int level, int32_t* layout);
+
+/* bbs_maps_device -- the CUDA device holding the maps' tables (the device
+ * current when bbs_build_maps ran).  BBS_EINVAL for a NULL argument. */
+int  bbs_maps_device(const bbs_maps* maps, int32_t* device);
 
 /* Target load (buckets in use / buckets) of the hashed level tables built by
  * later bbs_build_maps calls in this process (byte grids and dense bricks
@@ -289,19 +300,25 @@ int  bbs_score_children(const bbs_maps* maps, const float* scan_xyz, int64_t k, 
  * cannot allocate memory while they run: real-time control loops that must
  * not touch an allocator after start-up (unbounded latency, fragmentation),
  * frameworks that own all device memory through their own pool, and servers
- * that budget every byte up front.  The paper has no counterpart; this is a
- * deployment variant of the Eq. (11) scoring above.
+ * that budget every byte up front.  The paper has no counterpart.
  *   scan_xyz, nodes, scores : DEVICE memory on the maps' device (k x 3 float32,
- *                             n x 7 int32, n int32), as in bbs_score_batch.
+ *                             n x 7 int32, n int32), as in bbs_score_batch;
+ *                             any other pointer is BBS_EINVAL (checked with
+ *                             cudaPointerGetAttributes, which allocates nothing).
  * It calls no cudaMalloc/cudaFree and no allocating routine; its scratch
  * (the packed scan and the angle cosines/sines) is one file-scope device
  * array of 3 MiB + 4 KiB that every GPU loading the library keeps until the
  * process exits.  Limits: k <= BBS_NOALLOC_MAX_POINTS and at most
- * BBS_NOALLOC_MAX_ANGLES angle segments summed over levels and axes;
- * beyond them the call returns BBS_EINVAL and does no GPU work.  All calls
- * share the array and it keeps the last call's contents (the status words are
- * cleared at the start of each call), so calls that overlap on the GPU race:
- * serialize them.  The first call on a device looks up the array's device
+ * BBS_NOALLOC_MAX_ANGLES angle segments summed over levels and axes, both
+ * BBS_EINVAL beyond.  Bad arguments and k above the maximum are refused before
+ * any GPU work; the angle-segment limit and non-finite or too large scan
+ * coordinates are found after the scan has been packed into the array.  All
+ * calls share the array and it keeps the last call's contents (the status
+ * words are cleared at the start of each call), so calls that overlap on the
+ * GPU race; a process-wide lock held until each call's final stream
+ * synchronization keeps calls through this library from overlapping.  The
+ * call synchronizes its stream (the scan's d_max is read back before the pose
+ * grid is formed).  The first call on a device looks up the array's device
  * address with that device current; make it before any stream capture.
  * Same errors as bbs_score_batch. */
 #define BBS_NOALLOC_MAX_POINTS 131072

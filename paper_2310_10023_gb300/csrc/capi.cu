@@ -1,5 +1,6 @@
 // capi.cu -- the extern "C" entry points of libbbs (declared in include/bbs.h).
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -183,6 +184,38 @@ int bbs_maps_layout(const bbs_maps* m, int level, int32_t* layout)
     clear_error();
     if (!m || !layout || level < 0 || level >= m->levels) return set_error(BBS_EINVAL, "maps_layout: bad argument");
     *layout = m->lv[level].layout;
+    return BBS_OK;
+}
+
+int bbs_maps_device(const bbs_maps* m, int32_t* device)
+{
+    clear_error();
+    if (!m || !device) return set_error(BBS_EINVAL, "maps_device: NULL argument");
+    *device = m->device;
+    return BBS_OK;
+}
+
+// R = Rz(yaw) Ry(pitch) Rx(roll) of a result pose (Sec. III-A), the same
+// composition as the pose grid's rotations, FP64, row-major; t = (x, y, z)
+int bbs_pose_matrix(const double pose[6], double R[9], double t[3])
+{
+    clear_error();
+    if (!pose || !R || !t) return set_error(BBS_EINVAL, "pose_matrix: NULL argument");
+    for (int i = 0; i < 6; ++i)
+        if (!std::isfinite(pose[i])) return set_error(BBS_EINVAL, "pose_matrix: non-finite pose");
+    const double ca = std::cos(pose[3]), sa = std::sin(pose[3]);
+    const double cb = std::cos(pose[4]), sb = std::sin(pose[4]);
+    const double cg = std::cos(pose[5]), sg = std::sin(pose[5]);
+    R[0] = cg * cb;
+    R[1] = cg * sb * sa - sg * ca;
+    R[2] = cg * sb * ca + sg * sa;
+    R[3] = sg * cb;
+    R[4] = sg * sb * sa + cg * ca;
+    R[5] = sg * sb * ca - cg * sa;
+    R[6] = -sb;
+    R[7] = cb * sa;
+    R[8] = cb * ca;
+    for (int i = 0; i < 3; ++i) t[i] = pose[i];
     return BBS_OK;
 }
 

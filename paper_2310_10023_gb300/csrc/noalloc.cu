@@ -21,12 +21,17 @@
 //
 // The array lives in every GPU that loads the library until the process
 // exits.  Every call shares it and it keeps the last call's contents; the
-// status words are cleared at the start of each call.  Calls that overlap on
-// the GPU (other streams, other host threads) race on it: serialize them.
-// Host code cannot use the array's name as a device address, so the first
-// call on each device looks the address up with cudaGetSymbolAddress (with
-// that device current) and caches it; make that first call before any stream
-// capture.
+// status words are cleared at the start of each call.  Calls that overlapped
+// on the GPU would race on it; each call holds a process-wide mutex until its
+// final stream synchronization, so calls from several host threads run one
+// after the other.  Host code cannot use the array's name as a device
+// address, so the first call on each device looks the address up with
+// cudaGetSymbolAddress (with that device current) and caches it; make that
+// first call before any stream capture.  Only bad arguments and a scan above
+// BBS_NOALLOC_MAX_POINTS are refused before GPU work; the angle-segment limit
+// and bad coordinates are found after the scan has been packed into the
+// array.  The call synchronizes its stream twice (the scan's d_max is read
+// back before the pose grid is formed, and the status words at the end).
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -58,9 +63,7 @@ struct NaCtrl {
 
 struct NaArgs {
     LevelView maps[MAX_LEVELS];
-    DevGrid grid;
-    int64_t cs_off[MAX_LEVELS][3];   // first (cos, sin) entry of each level and axis
-    double r;
+    DevGrid grid;                    // its cs_off: first (cos, sin) entry of each level and axis
     const double2* cs;
     const float4* scan;
     int64_t k;
@@ -117,25 +120,13 @@ __global__ void __launch_bounds__(256) na_score_kernel(NaArgs a)
             }
             continue;
         }
-        const double2 A_ = a.cs[a.cs_off[l][0] + c[3]];
-        const double2 B_ = a.cs[a.cs_off[l][1] + c[4]];
-        const double2 G_ = a.cs[a.cs_off[l][2] + c[5]];
-        const double ca = A_.x, sa = A_.y, cb = B_.x, sb = B_.y, cg = G_.x, sg = G_.y;
-        const double R0 = __dmul_rn(cg, cb);
-        const double R1 = __dsub_rn(__dmul_rn(__dmul_rn(cg, sb), sa), __dmul_rn(sg, ca));
-        const double R2 = __dadd_rn(__dmul_rn(__dmul_rn(cg, sb), ca), __dmul_rn(sg, sa));
-        const double R3 = __dmul_rn(sg, cb);
-        const double R4 = __dadd_rn(__dmul_rn(__dmul_rn(sg, sb), sa), __dmul_rn(cg, ca));
-        const double R5 = __dsub_rn(__dmul_rn(__dmul_rn(sg, sb), ca), __dmul_rn(cg, sa));
-        const double R6 = -sb;
-        const double R7 = __dmul_rn(cb, sa);
-        const double R8 = __dmul_rn(cb, ca);
-        const float4 r0 = make_float4(__double2float_rn(__ddiv_rn(R0, a.r)), __double2float_rn(__ddiv_rn(R1, a.r)),
-                                      __double2float_rn(__ddiv_rn(R2, a.r)), 0.0f);
-        const float4 r1 = make_float4(__double2float_rn(__ddiv_rn(R3, a.r)), __double2float_rn(__ddiv_rn(R4, a.r)),
-                                      __double2float_rn(__ddiv_rn(R5, a.r)), 0.0f);
-        const float4 r2 = make_float4(__double2float_rn(__ddiv_rn(R6, a.r)), __double2float_rn(__ddiv_rn(R7, a.r)),
-                                      __double2float_rn(__ddiv_rn(R8, a.r)), 0.0f);
+        // A = fl32(R / r), the same FP64 operations as every other entry point
+        const uint32_t rot = (uint32_t)(((int64_t)c[3] * a.grid.N[l][1] + c[4]) * a.grid.N[l][2] + c[5]);
+        float A[9];
+        rotation_rows(a.cs, a.grid, l, rot, A);
+        const float4 r0 = make_float4(A[0], A[1], A[2], 0.0f);
+        const float4 r1 = make_float4(A[3], A[4], A[5], 0.0f);
+        const float4 r2 = make_float4(A[6], A[7], A[8], 0.0f);
         const LevelView L = a.maps[l];
         uint32_t hits = 0;
         for (int64_t k = lane; k < a.k; k += 32) {
@@ -169,6 +160,17 @@ int na_scratch(int dev, unsigned char** out)
     return BBS_OK;
 }
 
+// whether p is device (or managed) memory of device dev; the query allocates nothing
+bool on_device(const void* p, int dev)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();   // an unregistered host pointer: clear the sticky-free error
+        return false;
+    }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
+}
+
 }  // namespace
 
 }  // namespace bbs
@@ -196,6 +198,11 @@ extern "C" int bbs_score_batch_noalloc(const bbs_maps* m, const float* scan_xyz,
             if (prev >= 0 && prev != dev) cudaSetDevice(prev);
         }
     } restore{prev, m->device};
+
+    // every buffer must be memory the kernels can read on the maps' device
+    if ((k > 0 && !on_device(scan_xyz, m->device)) || !on_device(nodes, m->device) || !on_device(scores, m->device))
+        return set_error(BBS_EINVAL, "score_batch_noalloc: scan, nodes and scores must be device memory on device %d",
+                         m->device);
 
     std::lock_guard<std::mutex> lock(g_na_mutex);
     unsigned char* base = nullptr;
@@ -232,7 +239,7 @@ extern "C" int bbs_score_batch_noalloc(const bbs_maps* m, const float* scan_xyz,
     int64_t cnt = 0;
     for (int l = 0; l < g.levels; ++l)
         for (int i = 0; i < 3; ++i) {
-            a.cs_off[l][i] = cnt;
+            if (g.cs_off[l][i] != cnt) return set_error(BBS_ECORRUPT, "score_batch_noalloc: angle table layout");
             if (cnt + g.N[l][i] > BBS_NOALLOC_MAX_ANGLES)
                 return set_error(BBS_EINVAL, "score_batch_noalloc: more than %d angle segments in the grid",
                                  BBS_NOALLOC_MAX_ANGLES);
@@ -246,7 +253,6 @@ extern "C" int bbs_score_batch_noalloc(const bbs_maps* m, const float* scan_xyz,
     // 3. one warp per node
     for (int l = 0; l < MAX_LEVELS; ++l) a.maps[l] = l < m->levels ? level_view(m, l) : LevelView{};
     a.grid = dev_grid(g);
-    a.r = (double)m->r;
     a.cs = cs;
     a.scan = scan;
     a.k = k;
@@ -254,8 +260,10 @@ extern "C" int bbs_score_batch_noalloc(const bbs_maps* m, const float* scan_xyz,
     a.n = n;
     a.scores = scores;
     a.ctrl = ctrl;
+    int nsm = 0;
+    BBS_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
     int64_t blocks = (n + 7) / 8;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks > (int64_t)nsm * 64) blocks = (int64_t)nsm * 64;
     na_score_kernel<<<(int)blocks, 256, 0, st>>>(a);
     BBS_CUDA_TRY(cudaGetLastError());
     BBS_CUDA_TRY(cudaMemcpyAsync(&h, ctrl, sizeof(h), cudaMemcpyDeviceToHost, st));

@@ -137,6 +137,8 @@ def load():
         L.bbs_maps_info.argtypes = [vp, C.c_int, i64p, i64p, i64p, i32p, dp]
         L.bbs_maps_keys.argtypes = [vp, C.c_int, vp, i64, i64p]
         L.bbs_maps_layout.argtypes = [vp, C.c_int, i32p]
+        L.bbs_maps_device.argtypes = [vp, i32p]
+        L.bbs_pose_matrix.argtypes = [vp, vp, vp]
         L.bbs_gicp_target_build.argtypes = [vp, i64, C.c_int, C.c_float, vp, P(C.c_void_p)]
         L.bbs_gicp_target_free.argtypes = [vp]
         L.bbs_gicp_target_free.restype = None
@@ -296,6 +298,13 @@ def bbs_maps_layout(maps: Maps, level: int) -> int:
     return out.value
 
 
+def bbs_maps_device(maps: Maps) -> int:
+    """The CUDA device index holding the maps."""
+    out = C.c_int32()
+    _check(load().bbs_maps_device(maps.h, C.byref(out)))
+    return out.value
+
+
 def bbs_maps_keys(maps: Maps, level: int) -> np.ndarray:
     n = bbs_maps_info(maps, level)["voxels"]
     out = np.zeros((max(n, 1), 3), np.int32)
@@ -353,14 +362,21 @@ NOALLOC_MAX_ANGLES = 65536
 def bbs_score_batch_noalloc(maps: Maps, scan, nodes, scores, ranges: Ranges | None = None,
                             opts: Opts | None = None):
     """Scores of caller nodes into the caller's `scores`, with no allocation
-    inside the library: scan, nodes and scores must be device tensors.  For
-    callers that cannot allocate while they run (real-time loops, external
-    memory pools).  Overlapping calls race on the library's shared scratch."""
+    inside the library: scan, nodes and scores must be device tensors on the
+    maps' device, and scores contiguous (it is written in place).  For callers
+    that cannot allocate while they run (real-time loops, external memory
+    pools).  The library's scratch array is shared by every call."""
+    if not all(_is_torch(x) for x in (scan, nodes, scores)):
+        raise ValueError("bbs_score_batch_noalloc takes device tensors only")
+    dev = bbs_maps_device(maps)
+    for name, x in (("scan", scan), ("nodes", nodes), ("scores", scores)):
+        if not x.is_cuda or x.device.index != dev:
+            raise ValueError(f"{name} must be on cuda:{dev}, the maps' device (got {x.device})")
+    if not scores.is_contiguous():
+        raise ValueError("scores must be contiguous: it is written in place")
     sp, sdev, k, keep1 = _arr(scan, np.float32, 3)
     npt, ndev, n, keep2 = _arr(nodes, np.int32, 7)
     op, odev, no, keep3 = _arr(scores, np.int32)
-    if not (sdev and ndev and odev):
-        raise ValueError("bbs_score_batch_noalloc takes device tensors only")
     if no < n:
         raise ValueError("scores is shorter than nodes")
     opts = opts or make_opts()
@@ -446,16 +462,16 @@ def bbs_gicp_target_info(t: GicpTarget) -> dict:
     return {"voxels": nv_.value, "table_size": ts.value, "max_probe": mp.value}
 
 
-def pose_to_rt(pose):
-    """(x, y, z, roll, pitch, yaw) -> (R, t) with R = Rz(yaw) Ry(pitch) Rx(roll),
-    the library's convention for bbs_result.pose and bbs_gicp."""
-    import math
-    x, y, z, a, b, g = [float(v) for v in pose]
-    ca, sa, cb, sb, cg, sg = math.cos(a), math.sin(a), math.cos(b), math.sin(b), math.cos(g), math.sin(g)
-    R = np.array([[cg * cb, cg * sb * sa - sg * ca, cg * sb * ca + sg * sa],
-                  [sg * cb, sg * sb * sa + cg * ca, sg * sb * ca - cg * sa],
-                  [-sb, cb * sa, cb * ca]])
-    return R, np.array([x, y, z])
+def bbs_pose_matrix(pose):
+    """(x, y, z, roll, pitch, yaw) -> (R 3x3, t 3) in FP64: the library's pose
+    convention (the transform of bbs_result.pose and bbs_gicp's seed)."""
+    p = np.ascontiguousarray([float(v) for v in pose], np.float64)
+    if p.shape != (6,):
+        raise ValueError("a pose has 6 entries")
+    R = np.zeros(9)
+    t = np.zeros(3)
+    _check(load().bbs_pose_matrix(C.c_void_p(p.ctypes.data), C.c_void_p(R.ctypes.data), C.c_void_p(t.ctypes.data)))
+    return R.reshape(3, 3), t
 
 
 def make_gicp_opts(max_iters=0, tau=0.0, rho=0.0, cov_eps=0.0, eps_rot=0.0, eps_trans=0.0, stream=None) -> GicpOpts:

@@ -76,3 +76,24 @@ def test_server_slot_limit_without_gpu():
         nv.bbs_server_create(max_active=257)
     assert e.value.code == nv.EINVAL
     assert "256" in nv.bbs_last_error()
+
+
+def test_pose_matrix_is_intrinsic_zyx_euler_without_gpu():
+    """bbs_pose_matrix (host code in the library) composes R = Rz(yaw)
+    Ry(pitch) Rx(roll), Sec. III-A's angles; pinned against scipy's
+    intrinsic ZYX Euler rotation, an independent construction that catches a
+    wrong order, sign or transpose."""
+    Rotation = pytest.importorskip("scipy.spatial.transform").Rotation
+    import numpy as np
+    from paper_2310_10023_gb300 import native as nv
+    nv.load()
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        pose = np.concatenate([rng.uniform(-50, 50, 3), rng.uniform(-np.pi, np.pi, 3)])
+        R, t = nv.bbs_pose_matrix(pose)
+        want = Rotation.from_euler("ZYX", [pose[5], pose[4], pose[3]]).as_matrix()
+        assert np.allclose(R, want, atol=1e-14)
+        assert np.array_equal(t, pose[:3])
+    with pytest.raises(nv.BBSError) as e:
+        nv.bbs_pose_matrix([0, 0, 0, float("nan"), 0, 0])
+    assert e.value.code == nv.EINVAL
