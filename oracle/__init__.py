@@ -77,6 +77,7 @@ class ResultT(C.Structure):
         ("node", C.c_int32 * 7), ("pose", C.c_double * 6),
         ("nodes_scored", C.c_int64), ("probes", C.c_int64), ("iterations", C.c_int64),
         ("peak_frontier", C.c_int64), ("parents_branched", C.c_int64), ("ms_total", C.c_double),
+        ("children_scored", C.c_int64), ("bound_violations", C.c_int64), ("bound_excess", C.c_double),
     ]
 
 

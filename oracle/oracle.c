@@ -645,6 +645,19 @@ static void fr_clear(frontier* f)
  *
  * Only popping a leaf changes best, so the order in which a batch's children
  * are scored and inserted cannot change the outcome. */
+/* Sec. IV-A checks how often the approximate rotational bound fails: a
+ * child scoring above its parent (whose score was to bound it), and by how
+ * much relative to the child's score.  Counted over every child scored while
+ * branching. */
+static void bound_check(orc_result* res, int32_t parent, int32_t child)
+{
+    res->children_scored++;
+    if (child > parent) {
+        res->bound_violations++;
+        res->bound_excess += (double)(child - parent) / (double)child;
+    }
+}
+
 /* Depth-first batched iteration (Table I's DFS search strategy; the paper
  * gives no batched form of it, so this reading fixes one): F is kept per
  * level, and nodes are taken deepest level first and, within a level,
@@ -673,6 +686,8 @@ static int dfs_search(const orc_maps* m, const orc_grid* g, const float* scan, i
     const int L = g->levels;
     int32_t best = *best_io;
     nodevec P = {0}, kids = {0};
+    int32_t* Ps = NULL;   /* score of each popped parent */
+    int64_t Ps_cap = 0;
     int rc = ORC_OK;
     for (;;) {
         int64_t size = 0;
@@ -704,7 +719,15 @@ static int dfs_search(const orc_maps* m, const orc_grid* g, const float* scan, i
             for (int64_t s = F->top; s > best && nchild < batch && !rc; --s) {
                 nodevec* B = &F->b[s];
                 if (B->n == 0) continue;
+                if (Ps_cap < P.n + B->n) {
+                    int64_t nc = 2 * (P.n + B->n);
+                    int32_t* np = (int32_t*)realloc(Ps, sizeof(int32_t) * (size_t)nc);
+                    if (!np) { rc = ORC_ENOMEM; break; }
+                    Ps = np;
+                    Ps_cap = nc;
+                }
                 for (int64_t i = 0; i < B->n && !rc; ++i) {
+                    Ps[P.n] = (int32_t)s;
                     rc = vec_push(&P, B->v[i].c);
                     nchild += orc_num_children(g, B->v[i].c);
                 }
@@ -727,11 +750,13 @@ static int dfs_search(const orc_maps* m, const orc_grid* g, const float* scan, i
             for (int64_t j = 0; j < nk && !rc; ++j) {
                 int32_t s = orc_score(m, g, scan, k, kids.v[j].c);
                 res->nodes_scored++;
+                bound_check(res, Ps[i], s);
                 if (s > best) rc = fr_push(&FL[kids.v[j].c[6]], s, kids.v[j].c);
             }
         }
     }
     free(P.v);
+    free(Ps);
     free(kids.v);
     *best_io = best;
     return rc;
@@ -780,6 +805,8 @@ int orc_localize(const orc_maps* m, const float* scan, int64_t k, const orc_rang
     }
     frontier F = FL[0];   /* best-first: the one frontier */
     nodevec P = {0}, kids = {0};
+    int32_t* Ps = NULL;   /* score of each popped parent (the bucket it came from) */
+    int64_t Ps_cap = 0;
 
     /* initial set C_lmax (Sec. III-D): all translations of Eq. (3)-(5) times
      * all rotations at l_max */
@@ -823,7 +850,15 @@ int orc_localize(const orc_maps* m, const float* scan, int64_t k, const orc_rang
                 fr_clear(&F);
                 break;
             }
+            if (Ps_cap < P.n + B->n) {
+                int64_t nc = 2 * (P.n + B->n);
+                int32_t* np = (int32_t*)realloc(Ps, sizeof(int32_t) * (size_t)nc);
+                if (!np) { rc = ORC_ENOMEM; break; }
+                Ps = np;
+                Ps_cap = nc;
+            }
             for (int64_t i = 0; i < B->n && !rc; ++i) {
+                Ps[P.n] = s;
                 rc = vec_push(&P, B->v[i].c);
                 nchild += orc_num_children(&g, B->v[i].c);
             }
@@ -845,6 +880,7 @@ int orc_localize(const orc_maps* m, const float* scan, int64_t k, const orc_rang
             for (int64_t j = 0; j < nk && !rc; ++j) {
                 int32_t s = orc_score(m, &g, scan, k, kids.v[j].c);
                 res->nodes_scored++;
+                bound_check(res, Ps[i], s);
                 if (s > best) rc = fr_push(&F, s, kids.v[j].c);
             }
         }
@@ -858,6 +894,7 @@ int orc_localize(const orc_maps* m, const float* scan, int64_t k, const orc_rang
     }
     free(FL);
     free(P.v);
+    free(Ps);
     free(kids.v);
     res->probes = res->nodes_scored * k;
     res->ms_total = now_ms() - t0;

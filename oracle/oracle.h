@@ -81,6 +81,11 @@ typedef struct {
     double  pose[6];
     int64_t nodes_scored, probes, iterations, peak_frontier, parents_branched;
     double  ms_total;
+    /* Sec. IV-A's check of the approximate rotational bound: of the children
+     * scored while branching (initial set excluded), those scoring above
+     * their parent, and the sum over them of (child - parent) / child */
+    int64_t children_scored, bound_violations;
+    double  bound_excess;
 } orc_result;
 
 /* ---- grid ------------------------------------------------------------- */

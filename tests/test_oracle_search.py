@@ -193,3 +193,33 @@ def test_exact_bound_requires_enough_dilation(room):
     # the requirement grows with the scan's reach: points twice as far need more
     far = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), rg).exact_dilation(4.0 * oracle.scan_dmax(s))
     assert far > e
+
+
+@pytest.mark.parametrize("scan_index", [0, 2])
+def test_bound_check_statistic(room, scan_index):
+    """Sec. IV-A's check of the rotational bound, as the oracle counts it:
+    every child scored while branching is compared with its parent.  Under
+    translation-only branching the bound is exact (no child beats its
+    parent); under roto-translational branching some do, each adding
+    (child - parent) / child, a fraction in (0, 1].  The children counted are
+    exactly the nodes scored after the initial set."""
+    w, m, _, _ = room
+    s, pose = synth.make_scan(w.scene, scan_index)
+    x0 = math.floor(pose[0] / 2.0) * 2.0 - 2.0
+    y0 = math.floor(pose[1] / 2.0) * 2.0 - 2.0
+    rp = 0.0523599
+    rg = oracle.make_ranges((x0, y0, 0.0), (x0 + 5.9, y0 + 5.9, 1.9), (-rp, -rp, pose[5] - 0.3),
+                            (rp, rp, pose[5] + 0.3))
+    M = oracle.Maps(m, w.r, w.levels)
+    for flags in (0, oracle.TRANSLATION_ONLY):
+        res = oracle.localize(M, s, rg, score_frac=0.95, batch=w.batch, flags=flags)
+        g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), rg, flags)
+        (a0, a1, a2), (b0, b1, b2) = g.wrange()
+        n0 = (b0 - a0 + 1) * (b1 - a1 + 1) * (b2 - a2 + 1) * int(np.prod(g.N(w.levels - 1)))
+        assert res.status == oracle.OK
+        assert res.children_scored == res.nodes_scored - n0 > 0
+        if flags == oracle.TRANSLATION_ONLY:
+            assert res.bound_violations == 0 and res.bound_excess == 0.0
+        else:
+            assert 0 < res.bound_violations < res.children_scored
+            assert 0.0 < res.bound_excess <= res.bound_violations
