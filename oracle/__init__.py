@@ -12,6 +12,8 @@ CUDA library.  Each wrapper names the passage of the paper it follows:
 * ``children`` -- Sec. III-D, Eq. (13)
 * ``localize`` -- Sec. III-E, Algorithm 2 (canonical best-first iteration)
 * ``brute_force`` -- Sec. III-B, Eq. (1) over the leaf set
+* ``threads`` / ``mt=True`` -- the same code built with OpenMP: Table I's CPU
+  multi-thread configurations (Sec. IV), scoring loops in parallel
 """
 from __future__ import annotations
 
@@ -24,8 +26,10 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liborc.so")
+_LIB_MT_PATH = os.path.join(_HERE, "liborc_mt.so")   # the same source with OpenMP (Table I's CPU multi-thread rows)
 _lock = threading.Lock()
 _lib = None
+_lib_mt = None
 
 OK, NOT_FOUND, EINVAL, ENOMEM, EKEYRANGE = 0, 1, -1, -2, -5
 TRANSLATION_ONLY, LEAF_UNDILATED, PRUNE_GE, ANGLE_LOWER_EDGE, CHILD_LITERAL = 0x1, 0x2, 0x4, 0x8, 0x10
@@ -39,19 +43,29 @@ def exact_flags(e: int) -> int:
 MAX_LEVELS = 16
 
 
-def build(force: bool = False) -> str:
-    """Compile liborc.so with gcc (no FMA contraction, no fast-math)."""
+def _compile(out, extra, force):
     src = os.path.join(_HERE, "oracle.c")
-    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= max(
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= max(
         os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "oracle.h"))
     ):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        return out
+    tmp = out + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-Wall", "-o", tmp, src, "-lm"]
+           "-Wall", *extra, "-o", tmp, src, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile liborc.so with gcc (no FMA contraction, no fast-math), and
+    liborc_mt.so, the same source with OpenMP, where gcc supports it."""
+    path = _compile(_LIB_PATH, ["-Wno-unknown-pragmas"], force)
+    try:
+        _compile(_LIB_MT_PATH, ["-fopenmp"], force)
+    except (subprocess.CalledProcessError, OSError):
+        pass   # no OpenMP here: the multi-thread variant is unavailable
+    return path
 
 
 class Ranges(C.Structure):
@@ -81,13 +95,17 @@ class ResultT(C.Structure):
     ]
 
 
-def _load():
-    global _lib
+def _load(mt: bool = False):
+    """The oracle library; mt=True: its OpenMP build (ImportError when gcc
+    had no OpenMP)."""
+    global _lib, _lib_mt
     with _lock:
-        if _lib is not None:
-            return _lib
+        if (_lib_mt if mt else _lib) is not None:
+            return _lib_mt if mt else _lib
         build()
-        L = C.CDLL(_LIB_PATH)
+        if mt and not os.path.exists(_LIB_MT_PATH):
+            raise ImportError("liborc_mt.so was not built (no OpenMP in this gcc)")
+        L = C.CDLL(_LIB_MT_PATH if mt else _LIB_PATH)
         P = C.POINTER
         f32p, i32p, i64p, dp = P(C.c_float), P(C.c_int32), P(C.c_int64), P(C.c_double)
         L.orc_delta.restype = C.c_double
@@ -122,8 +140,19 @@ def _load():
         L.orc_localize.argtypes = [C.c_void_p, f32p, C.c_int64, P(Ranges), C.c_double, C.c_int64,
                                    C.c_double, C.c_uint32, C.c_int64, P(ResultT)]
         L.orc_brute_force.argtypes = [C.c_void_p, P(GridT), f32p, C.c_int64, i32p, i32p]
-        _lib = L
+        L.orc_threads.argtypes = [C.c_int]
+        if mt:
+            _lib_mt = L
+        else:
+            _lib = L
         return L
+
+
+def threads(n: int = 0) -> int:
+    """Threads of the OpenMP oracle (n > 0 sets them): the CPU multi-thread
+    configurations of Table I.  The searches and scores are the plain
+    oracle's; only the scoring loops run in parallel."""
+    return _load(mt=True).orc_threads(int(n))
 
 
 def _f32(a):
@@ -263,24 +292,26 @@ class Maps:
         _load().orc_maps_bbox(self.h, lo, hi)
         return tuple(lo), tuple(hi)
 
-    def score_nodes(self, grid: Grid, scan, nodes) -> np.ndarray:
+    def score_nodes(self, grid: Grid, scan, nodes, mt: bool = False) -> np.ndarray:
         s, sp = _f32(scan)
         n, np_ = _i32(np.asarray(nodes).reshape(-1, 7))
         out = np.zeros(len(n), np.int32)
-        rc = _load().orc_score_nodes(self.h, C.byref(grid.g), sp, len(s), np_, len(n),
-                                     out.ctypes.data_as(C.POINTER(C.c_int32)))
+        rc = _load(mt).orc_score_nodes(self.h, C.byref(grid.g), sp, len(s), np_, len(n),
+                                       out.ctypes.data_as(C.POINTER(C.c_int32)))
         if rc != OK:
             raise ValueError(f"orc_score_nodes failed: {rc}")
         return out
 
 
 def localize(maps: Maps, scan, ranges: Ranges, score_frac=0.95, batch=10000, d_max=0.0, flags=0,
-             max_frontier=0) -> ResultT:
-    """Canonical best-first batched BnB (Algorithm 2 with the reading in oracle.c)."""
+             max_frontier=0, mt: bool = False) -> ResultT:
+    """Canonical best-first batched BnB (Algorithm 2 with the reading in
+    oracle.c); mt=True runs the OpenMP build (same result, scoring loops in
+    parallel)."""
     s, sp = _f32(scan)
     res = ResultT()
-    _load().orc_localize(maps.h, sp, len(s), C.byref(ranges), float(score_frac), int(batch),
-                         float(d_max), int(flags), int(max_frontier), C.byref(res))
+    _load(mt).orc_localize(maps.h, sp, len(s), C.byref(ranges), float(score_frac), int(batch),
+                           float(d_max), int(flags), int(max_frontier), C.byref(res))
     return res
 
 

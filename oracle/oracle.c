@@ -11,6 +11,9 @@
  */
 #define _POSIX_C_SOURCE 199309L
 #include "oracle.h"
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #include <math.h>
 #include <stdlib.h>
@@ -563,8 +566,22 @@ int orc_score_nodes(const orc_maps* m, const orc_grid* g, const float* scan, int
 {
     for (int64_t i = 0; i < n; ++i)
         if (!node_valid(g, nodes + 7 * i)) return ORC_EINVAL;
+#pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < n; ++i) scores[i] = orc_score(m, g, scan, k, nodes + 7 * i);
     return ORC_OK;
+}
+
+/* Threads of the OpenMP build (liborc_mt.so); the plain build has one and
+ * returns 1. */
+int orc_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /* ======================================================================== */
@@ -600,6 +617,64 @@ static int lex_less(const int32_t* a, const int32_t* b)
         if (a[i] > b[i]) return 0;
     }
     return 0;
+}
+
+/* Scores of a list of nodes (Eq. (11)) into out[].  The scores are
+ * independent of one another: built with OpenMP (liborc_mt.so, the CPU
+ * multi-thread rows of Table I) they are computed in parallel; the callers
+ * consume them in list order either way, so the search is the same. */
+static void score_list(const orc_maps* m, const orc_grid* g, const float* scan, int64_t k, const node7* v,
+                       int64_t n, int32_t* out)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) out[i] = orc_score(m, g, scan, k, v[i].c);
+}
+
+/* Every child (Eq. (13)) of the parents P in parent order, with the index of
+ * its parent, and their scores. */
+typedef struct {
+    nodevec kids;
+    int64_t* parent;
+    int32_t* score;
+    int64_t cap;
+} childset;
+
+static int children_scored(const orc_maps* m, const orc_grid* g, const float* scan, int64_t k, const nodevec* P,
+                           childset* C)
+{
+    C->kids.n = 0;
+    int64_t total = 0;
+    for (int64_t i = 0; i < P->n; ++i) total += orc_num_children(g, P->v[i].c);
+    if (C->kids.cap < total) {
+        node7* nv = (node7*)realloc(C->kids.v, sizeof(node7) * (size_t)total);
+        if (!nv) return ORC_ENOMEM;
+        C->kids.v = nv;
+        C->kids.cap = total;
+    }
+    if (C->cap < total) {
+        int64_t* np = (int64_t*)realloc(C->parent, sizeof(int64_t) * (size_t)total);
+        if (!np) return ORC_ENOMEM;
+        C->parent = np;
+        int32_t* ns = (int32_t*)realloc(C->score, sizeof(int32_t) * (size_t)total);
+        if (!ns) return ORC_ENOMEM;
+        C->score = ns;
+        C->cap = total;
+    }
+    for (int64_t i = 0; i < P->n; ++i) {
+        const int64_t nk = orc_num_children(g, P->v[i].c);
+        orc_children(g, P->v[i].c, &C->kids.v[C->kids.n].c[0], nk);
+        for (int64_t j = 0; j < nk; ++j) C->parent[C->kids.n + j] = i;
+        C->kids.n += nk;
+    }
+    score_list(m, g, scan, k, C->kids.v, C->kids.n, C->score);
+    return ORC_OK;
+}
+
+static void childset_free(childset* C)
+{
+    free(C->kids.v);
+    free(C->parent);
+    free(C->score);
 }
 
 /* The frontier F: nodes bucketed by integer score (the queue "sorted by
@@ -685,7 +760,8 @@ static int dfs_search(const orc_maps* m, const orc_grid* g, const float* scan, i
 {
     const int L = g->levels;
     int32_t best = *best_io;
-    nodevec P = {0}, kids = {0};
+    nodevec P = {0};
+    childset C = {{0}, 0, 0, 0};
     int32_t* Ps = NULL;   /* score of each popped parent */
     int64_t Ps_cap = 0;
     int rc = ORC_OK;
@@ -738,26 +814,17 @@ static int dfs_search(const orc_maps* m, const orc_grid* g, const float* scan, i
         if (rc || P.n == 0) break;
         res->iterations++;
         res->parents_branched += P.n;
-        for (int64_t i = 0; i < P.n && !rc; ++i) {
-            int64_t nk = orc_num_children(g, P.v[i].c);
-            if (kids.cap < nk) {
-                node7* nv = (node7*)realloc(kids.v, sizeof(node7) * (size_t)nk);
-                if (!nv) { rc = ORC_ENOMEM; break; }
-                kids.v = nv;
-                kids.cap = nk;
-            }
-            orc_children(g, P.v[i].c, &kids.v[0].c[0], nk);
-            for (int64_t j = 0; j < nk && !rc; ++j) {
-                int32_t s = orc_score(m, g, scan, k, kids.v[j].c);
-                res->nodes_scored++;
-                bound_check(res, Ps[i], s);
-                if (s > best) rc = fr_push(&FL[kids.v[j].c[6]], s, kids.v[j].c);
-            }
+        rc = children_scored(m, g, scan, k, &P, &C);
+        for (int64_t j = 0; j < C.kids.n && !rc; ++j) {
+            const int32_t s = C.score[j];
+            res->nodes_scored++;
+            bound_check(res, Ps[C.parent[j]], s);
+            if (s > best) rc = fr_push(&FL[C.kids.v[j].c[6]], s, C.kids.v[j].c);
         }
     }
     free(P.v);
     free(Ps);
-    free(kids.v);
+    childset_free(&C);
     *best_io = best;
     return rc;
 }
@@ -804,7 +871,8 @@ int orc_localize(const orc_maps* m, const float* scan, int64_t k, const orc_rang
         }
     }
     frontier F = FL[0];   /* best-first: the one frontier */
-    nodevec P = {0}, kids = {0};
+    nodevec P = {0};
+    childset C = {{0}, 0, 0, 0};
     int32_t* Ps = NULL;   /* score of each popped parent (the bucket it came from) */
     int64_t Ps_cap = 0;
 
@@ -812,6 +880,7 @@ int orc_localize(const orc_maps* m, const float* scan, int64_t k, const orc_rang
      * all rotations at l_max */
     int32_t c[7];
     c[6] = lmax;
+    nodevec init = {0};
     for (int64_t x = g.wmin[0]; x <= g.wmax[0] && !rc; ++x)
         for (int64_t y = g.wmin[1]; y <= g.wmax[1] && !rc; ++y)
             for (int64_t z = g.wmin[2]; z <= g.wmax[2] && !rc; ++z)
@@ -820,10 +889,17 @@ int orc_localize(const orc_maps* m, const float* scan, int64_t k, const orc_rang
                         for (int64_t ig = 0; ig < g.N[lmax][2] && !rc; ++ig) {
                             c[0] = (int32_t)x; c[1] = (int32_t)y; c[2] = (int32_t)z;
                             c[3] = (int32_t)ia; c[4] = (int32_t)ib; c[5] = (int32_t)ig;
-                            int32_t s = orc_score(m, &g, scan, k, c);
-                            res->nodes_scored++;
-                            if (s > best) rc = fr_push(dfs ? &FL[lmax] : &F, s, c);
+                            rc = vec_push(&init, c);
                         }
+    int32_t* init_score = rc ? NULL : (int32_t*)malloc(sizeof(int32_t) * (size_t)(init.n > 0 ? init.n : 1));
+    if (!rc && !init_score) rc = ORC_ENOMEM;
+    if (!rc) score_list(m, &g, scan, k, init.v, init.n, init_score);
+    for (int64_t i = 0; i < init.n && !rc; ++i) {
+        res->nodes_scored++;
+        if (init_score[i] > best) rc = fr_push(dfs ? &FL[lmax] : &F, init_score[i], init.v[i].c);
+    }
+    free(init.v);
+    free(init_score);
     if (F.size > res->peak_frontier) res->peak_frontier = F.size;
 
     if (dfs && !rc) rc = dfs_search(m, &g, scan, k, batch, max_frontier, FL, &best, match, &found, res);
@@ -868,21 +944,12 @@ int orc_localize(const orc_maps* m, const float* scan, int64_t k, const orc_rang
         if (rc || P.n == 0) break;
         res->iterations++;
         res->parents_branched += P.n;
-        for (int64_t i = 0; i < P.n && !rc; ++i) {
-            int64_t nk = orc_num_children(&g, P.v[i].c);
-            if (kids.cap < nk) {
-                node7* nv = (node7*)realloc(kids.v, sizeof(node7) * (size_t)nk);
-                if (!nv) { rc = ORC_ENOMEM; break; }
-                kids.v = nv;
-                kids.cap = nk;
-            }
-            orc_children(&g, P.v[i].c, &kids.v[0].c[0], nk);
-            for (int64_t j = 0; j < nk && !rc; ++j) {
-                int32_t s = orc_score(m, &g, scan, k, kids.v[j].c);
-                res->nodes_scored++;
-                bound_check(res, Ps[i], s);
-                if (s > best) rc = fr_push(&F, s, kids.v[j].c);
-            }
+        rc = children_scored(m, &g, scan, k, &P, &C);
+        for (int64_t j = 0; j < C.kids.n && !rc; ++j) {
+            const int32_t s = C.score[j];
+            res->nodes_scored++;
+            bound_check(res, Ps[C.parent[j]], s);
+            if (s > best) rc = fr_push(&F, s, C.kids.v[j].c);
         }
         if (F.size > res->peak_frontier) res->peak_frontier = F.size;
     }
@@ -895,7 +962,7 @@ int orc_localize(const orc_maps* m, const float* scan, int64_t k, const orc_rang
     free(FL);
     free(P.v);
     free(Ps);
-    free(kids.v);
+    childset_free(&C);
     res->probes = res->nodes_scored * k;
     res->ms_total = now_ms() - t0;
     if (rc) return res->status = rc;

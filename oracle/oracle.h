@@ -131,6 +131,8 @@ int64_t orc_children(const orc_grid* g, const int32_t parent[7], int32_t* out_no
 int  orc_localize(const orc_maps* m, const float* scan, int64_t k, const orc_ranges* rg,
                   double score_frac, int64_t batch, double d_max, uint32_t flags,
                   int64_t max_frontier, orc_result* res);
+/* threads of the OpenMP build (n > 0 sets them); 1 for the plain build */
+int  orc_threads(int n);
 /* exhaustive max over the leaf set (all leaf translations of the grid's window,
  * all level-0 rotations); returns the max score, lexmin argmax in best_node */
 int  orc_brute_force(const orc_maps* m, const orc_grid* g, const float* scan, int64_t k,

@@ -223,3 +223,36 @@ def test_bound_check_statistic(room, scan_index):
         else:
             assert 0 < res.bound_violations < res.children_scored
             assert 0.0 < res.bound_excess <= res.bound_violations
+
+
+def test_multithread_oracle_is_the_same_search(room):
+    """Table I's CPU multi-thread configurations: the OpenMP build of the
+    oracle scores each batch's children in parallel and consumes them in the
+    same order, so every search is the single-threaded one (best-first and
+    depth-first, roto-translational and translation-only branching)."""
+    try:
+        n = oracle.threads()
+    except ImportError:
+        pytest.skip("no OpenMP build of the oracle")
+    assert n >= 1
+    w, m, s, _ = room
+    M = oracle.Maps(m, w.r, w.levels)
+    rg = oracle.make_ranges(w.lo, w.hi, w.ang_lo, w.ang_hi)
+    s2, pose = synth.make_scan(w.scene, 2)
+    wr = _window_ranges(pose)
+
+    def key(r):
+        return (r.status, r.best_score, list(r.node), r.iterations, r.nodes_scored, r.peak_frontier,
+                r.children_scored, r.bound_violations, r.bound_excess)
+
+    cases = [(s, rg, 0, w.batch), (s2[:300], wr, oracle.SEARCH_DFS, 500), (s2[:300], wr, oracle.TRANSLATION_ONLY, 64)]
+    for scan, r, flags, b in cases:
+        a = oracle.localize(M, scan, r, score_frac=0.9, batch=b, flags=flags)
+        t = oracle.localize(M, scan, r, score_frac=0.9, batch=b, flags=flags, mt=True)
+        assert key(a) == key(t), flags
+    g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), rg)
+    rng = np.random.default_rng(4)
+    nodes = np.array([[int(rng.integers(0, 40)), int(rng.integers(0, 40)), int(rng.integers(0, 10)),
+                       int(rng.integers(0, g.N(0)[0])), int(rng.integers(0, g.N(0)[1])),
+                       int(rng.integers(0, g.N(0)[2])), 0] for _ in range(3000)], np.int32)
+    assert np.array_equal(M.score_nodes(g, s, nodes), M.score_nodes(g, s, nodes, mt=True))
