@@ -116,7 +116,8 @@ typedef struct {
     double   d_max;         /* maximum scan range for Eq. (2); default max_k |s_k|           */
     uint32_t flags;         /* BBS_* flags                                                   */
     void*    cuda_stream;   /* cudaStream_t to run on; NULL = legacy default stream          */
-    int64_t  max_frontier;  /* frontier capacity in nodes; default 2^24; BBS_ENOMEM beyond   */
+    int64_t  max_frontier;  /* largest frontier in nodes: the arrays start at up to 2^24 and  */
+                            /* double as the search needs; default 2^30; BBS_ENOMEM beyond  */
 } bbs_opts;
 
 /* Result of a localization.  pose = x_c of the matched leaf (Sec. III-B):
@@ -145,6 +146,12 @@ typedef struct {
     double  score_ms;       /* their summed device time (BBS_TIME_KERNELS), else 0            */
     int64_t h2d_bytes;      /* host-to-device bytes the call copied                           */
     int64_t d2h_bytes;      /* device-to-host bytes the call copied                           */
+    /* Sec. IV-A's check of the approximate rotational bound: children scored
+     * while branching (the initial set excluded), those scoring above their
+     * parent, and the sum over them of (child - parent) / child */
+    int64_t children_scored;
+    int64_t bound_violations;
+    double  bound_excess;
 } bbs_result;
 
 /* bbs_pose_matrix -- the rigid transform of a result pose (x, y, z, roll,
@@ -230,18 +237,31 @@ int  bbs_set_probe_layout(int layout);
  *                 evenly over the scoring CTAs before the rest is handed out
  *                 in shrinking grabs, 1..1000 (default 750);
  *   grab_min      smallest grab in slices, 1..2^20 (default 16);
- *   ctas_per_sm   scoring CTAs per SM, 1..4 (default 4).
+ *   ctas_per_sm   scoring CTAs per SM, 1..4 (default 4);
+ *   frontier_log2 the frontier arrays of later bbs_localize and
+ *                 bbs_localize_many calls start at 2^frontier_log2 nodes,
+ *                 10..30, and double as a search needs (default: up to 2^24
+ *                 nodes plus room for one round).
  * NULL restores every default.  BBS_EINVAL for a field out of range. */
 typedef struct {
     int64_t launch_tasks;
     int32_t static_pm;
     int32_t grab_min;
     int32_t ctas_per_sm;
-    int32_t reserved;
+    int32_t frontier_log2;
 } bbs_tuning;
 int  bbs_set_tuning(const bbs_tuning* t);
 /* The tuning in effect (defaults filled in). */
 int  bbs_get_tuning(bbs_tuning* t);
+
+/* bbs_launch_log -- the scoring launches of the last search call on this
+ * thread that ran with BBS_TIME_KERNELS: per launch its units (rotational
+ * children x scan points, each unit scoring 8 translational children) and
+ * its device milliseconds between CUDA events on the call's stream.  units
+ * and ms: host arrays of cap entries; *n receives the count (a size query
+ * with cap = 0 returns BBS_OK when the log is empty, else BBS_EINVAL with *n
+ * set).  The paper has no counterpart: it serves the roofline measurement. */
+int  bbs_launch_log(int64_t* units, double* ms, int64_t cap, int64_t* n);
 
 /* All voxel keys of level `level` (n_voxels x 3 int32) into the host buffer
  * out (capacity cap keys); *n receives the count.  BBS_EINVAL if cap is short. */

@@ -12,6 +12,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cstring>
 #include <stdint.h>
 
 #include "bbs.h"
@@ -324,7 +325,33 @@ __host__ __device__ __forceinline__ int64_t node_children(const DevGrid& g, int 
     return n;
 }
 
+// Programmatic dependent launch (sm_90+): a kernel launched with it may start
+// while its predecessor in the stream still runs; pdl_wait() blocks until the
+// predecessor has completed and its writes are visible (a no-op without the
+// launch attribute), and pdl_trigger() lets the successor's CTAs be
+// scheduled once every CTA of this grid has triggered or exited.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ---- host side ------------------------------------------------------------
+
+// launch `k` on `st`, with the programmatic-dependent-launch attribute when pdl
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, bool pdl, Args... args)
+{
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? at : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, ((KArgs)args)...);
+}
 
 int set_error(int code, const char* fmt, ...);
 void clear_error();

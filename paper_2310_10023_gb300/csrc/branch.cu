@@ -19,9 +19,6 @@ namespace bbs {
 
 namespace {
 
-// bits {0, 1, 5, 6} of w (children jx + 5 jy of one z-plane) into bytes 0..3
-__device__ __forceinline__ uint32_t spread4(uint32_t w) { return ((w & 0x63u) * 0x40881u) & 0x01010101u; }
-
 // Paired FP32 arithmetic (sm_100+ f32x2): each lane of a pair is an IEEE
 // FP32 operation with its own rounding, exactly the scalar result, two points
 // per instruction.
@@ -110,32 +107,44 @@ __device__ __forceinline__ void child_bits(const LevelView& L, uint32_t bx, uint
     }
 }
 
-// The 8 child counts of one point from a byte grid (LAYOUT_BYTES): relative
-// keys clamped to the empty key past the box, one byte load, and each nibble
-// (children jz = 0, then jz = 1) spread to 4 byte counters by one multiply
-// (bit i of the nibble lands on bit 8 i; the other partial products fall on
-// distinct bits outside the mask, so no carry reaches a counter).
-__device__ __forceinline__ void bytes_count(uint32_t v, uint32_t& acc0, uint32_t& acc1)
+// Child counters: one 4-bit counter per translational child in one 32-bit
+// word, child i = jx + 2 jy + 4 jz at bit 4 (jx + 2 jz) + 16 jy, so that
+// (acc >> 4 k) & 0x000F000F holds the children (jx, jz) = (k & 1, k >> 1)
+// with jy = 0 and jy = 1 in its two 16-bit halves.  A point adds
+// CHILD_LUT[v] for its 8-bit child mask v (one shared-memory load and one
+// add).  A thread counts at most PCHUNK / 256 = 8 points of a run, so no
+// counter passes 15.
+__host__ __device__ constexpr uint32_t child_lut_entry(uint32_t v)
 {
-    acc0 += ((v & 0xFu) * 0x204081u) & 0x01010101u;
-    acc1 += ((v >> 4) * 0x204081u) & 0x01010101u;
+    return ((v & 1u) << 0) | (((v >> 1) & 1u) << 4) | (((v >> 2) & 1u) << 16) | (((v >> 3) & 1u) << 20) |
+           (((v >> 4) & 1u) << 8) | (((v >> 5) & 1u) << 12) | (((v >> 6) & 1u) << 24) | (((v >> 7) & 1u) << 28);
 }
-__device__ __forceinline__ void bytes_acc(const LevelView& L, uint32_t bx, uint32_t by, uint32_t bz, uint32_t ex,
-                                          uint32_t ey, uint32_t ez, uint32_t& acc0, uint32_t& acc1)
+static_assert(PCHUNK / 256 <= 15, "4-bit child counters hold the points of one run per thread");
+
+// The 8-bit child mask of one point from a byte grid (LAYOUT_BYTES): relative
+// keys clamped to the empty key past the box, one byte load.
+__device__ __forceinline__ uint32_t bytes_mask(const LevelView& L, uint32_t bx, uint32_t by, uint32_t bz, uint32_t ex,
+                                               uint32_t ey, uint32_t ez)
 {
     const uint32_t rx = min(bx ^ KB, ex), ry = min(by ^ KB, ey), rz = min(bz ^ KB, ez);
-    bytes_count(__ldg(reinterpret_cast<const uint8_t*>(L.slots) + ((rx * L.nby + ry) * L.nbz + rz)), acc0, acc1);
+    return __ldg(reinterpret_cast<const uint8_t*>(L.slots) + ((rx * L.nby + ry) * L.nbz + rz));
 }
 // The same for a run whose every point is known to land inside the grid (the
 // chunk-box test of the run): no per-axis clamp, and the -KB of the three
 // patterns folded into one constant, cfix = -KB (ny nz + nz + 1) mod 2^32 --
 // the index is exact because its true value is below 2^31.  One min against
 // the last cell (L.mask) keeps every load inside the grid whatever the test.
-__device__ __forceinline__ void bytes_acc_inside(const LevelView& L, uint32_t bx, uint32_t by, uint32_t bz,
-                                                 uint32_t cfix, uint32_t& acc0, uint32_t& acc1)
+__device__ __forceinline__ uint32_t bytes_mask_inside(const LevelView& L, uint32_t bx, uint32_t by, uint32_t bz,
+                                                      uint32_t cfix)
 {
     const uint32_t idx = min((bx * L.nby + by) * L.nbz + bz + cfix, L.mask);
-    bytes_count(__ldg(reinterpret_cast<const uint8_t*>(L.slots) + idx), acc0, acc1);
+    return __ldg(reinterpret_cast<const uint8_t*>(L.slots) + idx);
+}
+// the 8-bit child mask from the two plane words of the brick layouts
+// (bits {0, 1, 5, 6}: children jx + 5 jy of the z = 0 and z = 1 planes)
+__device__ __forceinline__ uint32_t planes_mask(uint32_t w0, uint32_t w1)
+{
+    return (w0 & 3u) | ((w0 >> 3) & 0xCu) | ((w1 & 3u) << 4) | ((w1 << 1) & 0xC0u);
 }
 
 // One run (a rotational child over blocks of the staged chunk), two points
@@ -148,10 +157,17 @@ __device__ __forceinline__ void bytes_acc_inside(const LevelView& L, uint32_t bx
 template <int LAYOUT, bool INSIDE = false>
 __device__ __forceinline__ void score_run(const ulonglong2* sxy, const f2* sz, int n, int jlo, int jhi,
                                           const LevelView& L, const Row2& r0, const Row2& r1, const Row2& r2, f2 S,
-                                          f2 Cx, f2 Cy, f2 Cz, uint32_t& acc0, uint32_t& acc1)
+                                          f2 Cx, f2 Cy, f2 Cz, const uint32_t* lut, uint32_t& acc)
 {
     const uint32_t ex = L.rmax[0] + 1u, ey = L.rmax[1] + 1u, ez = L.rmax[2] + 1u;   // bytes: the empty key past the box
     const uint32_t cfix = 0u - KB * (L.nby * L.nbz + L.nbz + 1u);
+    auto mask = [&](uint32_t bx, uint32_t by, uint32_t bz) -> uint32_t {
+        if (LAYOUT == LAYOUT_BYTES && INSIDE) return bytes_mask_inside(L, bx, by, bz, cfix);
+        if (LAYOUT == LAYOUT_BYTES) return bytes_mask(L, bx, by, bz, ex, ey, ez);
+        uint32_t w0, w1;
+        child_bits<LAYOUT>(L, bx, by, bz, w0, w1);
+        return planes_mask(w0, w1);
+    };
     auto pair = [&](int j) {
         const ulonglong2 xy = sxy[j];
         const f2 Z = sz[j];
@@ -159,25 +175,8 @@ __device__ __forceinline__ void score_run(const ulonglong2* sxy, const f2* sz, i
         up2(fma2rm(rot2(r0, xy.x, xy.y, Z), S, Cx), bx1, bx2);
         up2(fma2rm(rot2(r1, xy.x, xy.y, Z), S, Cy), by1, by2);
         up2(fma2rm(rot2(r2, xy.x, xy.y, Z), S, Cz), bz1, bz2);
-        if (LAYOUT == LAYOUT_BYTES && INSIDE) {
-            bytes_acc_inside(L, (uint32_t)bx1, (uint32_t)by1, (uint32_t)bz1, cfix, acc0, acc1);
-            if (2 * j + 1 < n) bytes_acc_inside(L, (uint32_t)bx2, (uint32_t)by2, (uint32_t)bz2, cfix, acc0, acc1);
-            return;
-        }
-        if (LAYOUT == LAYOUT_BYTES) {
-            bytes_acc(L, (uint32_t)bx1, (uint32_t)by1, (uint32_t)bz1, ex, ey, ez, acc0, acc1);
-            if (2 * j + 1 < n) bytes_acc(L, (uint32_t)bx2, (uint32_t)by2, (uint32_t)bz2, ex, ey, ez, acc0, acc1);
-            return;
-        }
-        uint32_t w0, w1;
-        child_bits<LAYOUT>(L, (uint32_t)bx1, (uint32_t)by1, (uint32_t)bz1, w0, w1);
-        acc0 += spread4(w0);
-        acc1 += spread4(w1);
-        if (2 * j + 1 < n) {
-            child_bits<LAYOUT>(L, (uint32_t)bx2, (uint32_t)by2, (uint32_t)bz2, w0, w1);
-            acc0 += spread4(w0);
-            acc1 += spread4(w1);
-        }
+        acc += lut[mask((uint32_t)bx1, (uint32_t)by1, (uint32_t)bz1)];
+        if (2 * j + 1 < n) acc += lut[mask((uint32_t)bx2, (uint32_t)by2, (uint32_t)bz2)];
     };
     int j = jlo + threadIdx.x;
     if (LAYOUT == LAYOUT_DENSE || LAYOUT == LAYOUT_BYTES)   // two pairs per step: four gathers in flight per thread
@@ -303,11 +302,14 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
     branch3_kernel(Plan* __restrict__ P, const SearchDev* __restrict__ Sall, const TaskRec* __restrict__ tasks,
                    int32_t* dense)
 {
-    if (P->status != PLAN_OK) return;
+    pdl_wait();   // the round's plan and tasks are written by the kernels before
+    pdl_trigger();
+    if (P->status != PLAN_OK || P->grow) return;
     __shared__ ulonglong2 sxy[PCHUNK / 2];
     __shared__ f2 sz[PCHUNK / 2];
     __shared__ RunDesc rd[NRUN];
     __shared__ uint32_t red[NRUN][4];
+    __shared__ uint32_t lut[256];   // child counter increments per 8-bit child mask
     // the CTA's walk, kept in shared memory (uniform; frees registers for the runs)
     __shared__ int64_t s_cur, s_end, s_next;
     // the staged chunk is (s_staged_sid, s_staged_c) between rounds; within a
@@ -328,6 +330,7 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
         s_staged_c = -1;
     }
     for (int i = tid; i < 4 * NRUN; i += blockDim.x) (&red[0][0])[i] = 0u;
+    for (int i = tid; i < 256; i += blockDim.x) lut[i] = child_lut_entry((uint32_t)i);
     float* fxy = reinterpret_cast<float*>(sxy);
     float* fz = reinterpret_cast<float*>(sz);
     for (;;) {
@@ -478,32 +481,33 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
             const Row2 r2{d.a[6], d.a[7], d.a[8]};
             const int n = min(PCHUNK, S.K - d.c * PCHUNK);
             const int jlo = d.b0 * (PBLK / 2), jhi = min(d.b1 * (PBLK / 2), (n + 1) >> 1);
-            uint32_t acc0 = 0, acc1 = 0;   // bytes: children (0,4,2,6) and (1,5,3,7)
+            uint32_t acc = 0;   // 4-bit child counters (child_lut_entry)
             if (BYTES) {   // every level of every search is a byte grid: only its path is compiled
                 if (d.inside)
                     score_run<LAYOUT_BYTES, true>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1],
-                                                  d.kc[2], acc0, acc1);
+                                                  d.kc[2], lut, acc);
                 else
-                    score_run<LAYOUT_BYTES>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], acc0,
-                                            acc1);
+                    score_run<LAYOUT_BYTES>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
+                                            acc);
             } else if (Lv.layout == LAYOUT_BYTES && d.inside)
                 score_run<LAYOUT_BYTES, true>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2],
-                                              acc0, acc1);
+                                              lut, acc);
             else if (Lv.layout == LAYOUT_BYTES)
-                score_run<LAYOUT_BYTES>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], acc0,
-                                        acc1);
+                score_run<LAYOUT_BYTES>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
+                                        acc);
             else if (Lv.layout == LAYOUT_DENSE)
-                score_run<LAYOUT_DENSE>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], acc0,
-                                        acc1);
+                score_run<LAYOUT_DENSE>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
+                                        acc);
             else if (Lv.layout == LAYOUT_COMPACT)
-                score_run<LAYOUT_COMPACT>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], acc0,
-                                          acc1);
+                score_run<LAYOUT_COMPACT>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
+                                          acc);
             else
-                score_run<LAYOUT_WIDE>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], acc0,
-                                       acc1);
+                score_run<LAYOUT_WIDE>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
+                                       acc);
+            // word k: children (jx, jz) = (k & 1, k >> 1), jy = 0 low and jy = 1 high;
             // 16-bit fields: at most 8 points per thread x 32 lanes, x 8 warps, per field
-            uint32_t e0 = acc0 & 0x00FF00FFu, o0 = (acc0 >> 8) & 0x00FF00FFu;
-            uint32_t e1 = acc1 & 0x00FF00FFu, o1 = (acc1 >> 8) & 0x00FF00FFu;
+            uint32_t e0 = acc & 0x000F000Fu, o0 = (acc >> 4) & 0x000F000Fu;
+            uint32_t e1 = (acc >> 8) & 0x000F000Fu, o1 = (acc >> 12) & 0x000F000Fu;
             e0 = __reduce_add_sync(0xffffffffu, e0);
             o0 = __reduce_add_sync(0xffffffffu, o0);
             e1 = __reduce_add_sync(0xffffffffu, e1);
@@ -539,7 +543,7 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
 __device__ __noinline__ void lex_rotation_pass(SearchDev* S, const FrontDev& F, const LoopState* LS)
 {
     const int cur = LS->cur;
-    const int64_t n = min((int64_t)LS->fn[cur], F.cap);   // appends past the capacity were not stored
+    const int64_t n = min((int64_t)LS->fn[cur], LS->cap);   // appends past the capacity were not stored
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t key = F.keys[cur][i];
         Ctl* c = S[key >> 24].ctl;
@@ -563,8 +567,11 @@ __device__ __noinline__ void lex_rotation_pass(SearchDev* S, const FrontDev& F, 
 template <int MODE>
 __global__ void __launch_bounds__(256) finalize_kernel(const Plan* __restrict__ P, SearchDev* S,
                                                        const TaskRec* __restrict__ tasks, int32_t* dense, FrontDev F,
-                                                       LoopState* LS, int lex_only)
+                                                       LoopState* LS, int lex_only, const int32_t* __restrict__ tscore)
 {
+    pdl_wait();   // the scores are written by the scoring kernel before
+    pdl_trigger();
+    if (P->grow) return;   // the round waits for the host to grow the frontier
     if (MODE == MODE_SEARCH && LS->lex_pass) lex_rotation_pass(S, F, LS);
     if (lex_only || P->status != PLAN_OK) return;
     __shared__ uint32_t s_woff[8];
@@ -580,7 +587,8 @@ __global__ void __launch_bounds__(256) finalize_kernel(const Plan* __restrict__ 
     __syncthreads();
     for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < n_dense; b0 += stride) {   // uniform per CTA
         const int64_t d = b0 + threadIdx.x;
-        bool surv = false;
+        bool surv = false, viol = false;
+        double vex = 0.0;
         int32_t score = 0, sid = 0;
         NodeRec nd;
         nd.cx = nd.cy = nd.cz = 0;
@@ -616,6 +624,11 @@ __global__ void __launch_bounds__(256) finalize_kernel(const Plan* __restrict__ 
             // the dense array must be zero for the next launch: consume it
             const int32_t dv = dense[d];
             if (dv) dense[d] = 0;
+            if (MODE == MODE_SEARCH && tscore) {   // Sec. IV-A: does the child beat its parent's bound?
+                const int32_t ps = tscore[u];
+                viol = dv > ps;
+                if (viol) vex = (double)(dv - ps) / (double)dv;
+            }
             if (valid) {
                 score = dv;
                 surv = score > g.best;
@@ -623,6 +636,22 @@ __global__ void __launch_bounds__(256) finalize_kernel(const Plan* __restrict__ 
                 nd.cy = ty;
                 nd.cz = tz;
                 nd.rl = rl_pack(crot, m);
+            }
+        }
+        if (MODE == MODE_SEARCH && tscore) {   // the bound check's counts
+            const uint32_t vb = __ballot_sync(0xffffffffu, viol);
+            if (vb && one) {   // one search: one atomic pair per warp
+                double x = vex;
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                if ((__ffs(vb) - 1) == lane) {
+                    Ctl* c = S[sid].ctl;
+                    atomicAdd(&c->st_viol, (unsigned long long)__popc(vb));
+                    atomicAdd(&c->st_excess, x);
+                }
+            } else if (viol) {
+                Ctl* c = S[sid].ctl;
+                atomicAdd(&c->st_viol, 1ull);
+                atomicAdd(&c->st_excess, vex);
             }
         }
         const uint32_t ball = __ballot_sync(0xffffffffu, surv);
@@ -659,7 +688,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(const Plan* __restrict__ 
                 const uint32_t kids = (uint32_t)node_children(s.grid, m, crot);
                 const uint32_t gk = __reduce_add_sync(peers, kids);
                 const uint32_t gl = __reduce_add_sync(peers, m == 0 ? 1u : 0u);
-                if (pos < (unsigned long long)F.cap) {
+                if (pos < (unsigned long long)LS->cap) {   // the run's limit (at most the arrays' size)
                     F.nodes[nxt][pos] = nd;
                     F.keys[nxt][pos] = key;
                 } else {
@@ -681,26 +710,25 @@ __global__ void __launch_bounds__(256) finalize_kernel(const Plan* __restrict__ 
 }
 
 cudaError_t launch_branch(int mode, Plan* P, const SearchDev* S, const TaskRec* tasks, int32_t* dense, int blocks,
-                          cudaStream_t st, bool bytes_only)
+                          cudaStream_t st, bool bytes_only, bool pdl)
 {
     if (blocks <= 0) return cudaSuccess;
-    if (mode == MODE_INITIAL) {
-        if (bytes_only) branch3_kernel<MODE_INITIAL, true><<<blocks, 256, 0, st>>>(P, S, tasks, dense);
-        else branch3_kernel<MODE_INITIAL, false><<<blocks, 256, 0, st>>>(P, S, tasks, dense);
-    } else {
-        if (bytes_only) branch3_kernel<MODE_SEARCH, true><<<blocks, 256, 0, st>>>(P, S, tasks, dense);
-        else branch3_kernel<MODE_SEARCH, false><<<blocks, 256, 0, st>>>(P, S, tasks, dense);
-    }
-    return cudaGetLastError();
+    void (*k)(Plan*, const SearchDev*, const TaskRec*, int32_t*);
+    if (mode == MODE_INITIAL) k = bytes_only ? branch3_kernel<MODE_INITIAL, true> : branch3_kernel<MODE_INITIAL, false>;
+    else k = bytes_only ? branch3_kernel<MODE_SEARCH, true> : branch3_kernel<MODE_SEARCH, false>;
+    return launch_pdl(k, dim3(blocks), dim3(256), st, pdl, P, S, tasks, dense);
 }
 
 cudaError_t launch_finalize(int mode, const Plan* P, SearchDev* S, const TaskRec* tasks, int32_t* dense,
-                            const FrontDev& F, LoopState* LS, int blocks, cudaStream_t st, bool lex_only)
+                            const FrontDev& F, LoopState* LS, int blocks, cudaStream_t st, bool lex_only,
+                            const int32_t* tscore, bool pdl)
 {
     if (blocks <= 0) return cudaSuccess;
-    if (mode == MODE_INITIAL) finalize_kernel<MODE_INITIAL><<<blocks, 256, 0, st>>>(P, S, tasks, dense, F, LS, 0);
-    else finalize_kernel<MODE_SEARCH><<<blocks, 256, 0, st>>>(P, S, tasks, dense, F, LS, lex_only ? 1 : 0);
-    return cudaGetLastError();
+    if (mode == MODE_INITIAL)
+        return launch_pdl(finalize_kernel<MODE_INITIAL>, dim3(blocks), dim3(256), st, pdl, P, S, tasks, dense, F, LS, 0,
+                          (const int32_t*)nullptr);
+    return launch_pdl(finalize_kernel<MODE_SEARCH>, dim3(blocks), dim3(256), st, pdl, P, S, tasks, dense, F, LS,
+                      lex_only ? 1 : 0, tscore);
 }
 
 }  // namespace bbs

@@ -49,6 +49,8 @@ struct Ctl {
     int32_t pad;
     // statistics kept on the device (the search loop may run without the host)
     int64_t st_iters, st_parents, st_nodes, st_gathers;
+    unsigned long long st_viol;   // children scoring above their parent (Sec. IV-A's bound check)
+    double st_excess;             // sum over them of (child - parent) / child
     unsigned long long t_start_ns, t_match_ns, t_end_ns;   // %globaltimer
 };
 
@@ -88,7 +90,9 @@ struct LoopState {
     int32_t cur;                // the array holding the current nodes
     int32_t lex_pass;           // a search popped a leaf bucket this iteration
     uint32_t select_done;       // select CTAs finished this iteration (the last one plans)
-    int32_t pad;
+    int32_t exit_on_finish;     // the device loop also ends when a search finishes or fails
+    int64_t cap;                // nodes each frontier array holds
+    int64_t grow_need;          // a round that asked to grow: nodes the arrays must hold
 };
 
 enum { MODE_INITIAL = 0, MODE_SEARCH = 1, MODE_DENSE = 2 };
@@ -133,7 +137,8 @@ struct Plan {
     int32_t status;          // PLAN_*: the scoring kernels of a round run only when PLAN_OK
     int32_t iters;           // iterations of the current device-driven loop
     int32_t max_iters;       // the device-driven loop stops after this many
-    int32_t pad;
+    int32_t grow;            // the round's survivors may not fit the frontier arrays: the host grows
+                             // them before the round goes on (compact, score and survivors wait)
     Seg seg[MAXSEG];
 };
 
@@ -165,10 +170,11 @@ struct Tuning {
     int32_t static_pm = 750;
     int32_t grab_min = 16;
     int32_t ctas_per_sm = 4;
+    int32_t frontier_log2 = 0;   // 0: the default starting capacity
     bool operator==(const Tuning& o) const
     {
         return launch_tasks == o.launch_tasks && static_pm == o.static_pm && grab_min == o.grab_min &&
-               ctas_per_sm == o.ctas_per_sm;
+               ctas_per_sm == o.ctas_per_sm && frontier_log2 == o.frontier_log2;
     }
 };
 Tuning current_tuning();
@@ -186,11 +192,12 @@ constexpr int BRANCH_CTAS_PER_SM = 4;
 // the scoring kernel compiled for byte-grid levels alone (every level of
 // every search of the launch must be one: maps_all_bytes)
 cudaError_t launch_branch(int mode, Plan* P, const SearchDev* S, const TaskRec* tasks, int32_t* dense, int blocks,
-                          cudaStream_t st, bool bytes_only);
+                          cudaStream_t st, bool bytes_only, bool pdl = false);
 // survivors (score above their search's best) are appended to the frontier
 // array the next iteration reads, with their bucket counts; in search mode
 // first the second lexmin pass of a popped leaf bucket (lex_only: that alone)
 cudaError_t launch_finalize(int mode, const Plan* P, SearchDev* S, const TaskRec* tasks, int32_t* dense,
-                            const FrontDev& F, LoopState* LS, int blocks, cudaStream_t st, bool lex_only = false);
+                            const FrontDev& F, LoopState* LS, int blocks, cudaStream_t st, bool lex_only = false,
+                            const int32_t* tscore = nullptr, bool pdl = false);
 
 }  // namespace bbs

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "branch.cuh"
+#include "engine.cuh"
 
 namespace bbs {
 
@@ -563,6 +564,20 @@ int bbs_set_tuning(const bbs_tuning* t)
     return set_tuning(t);
 }
 
+int bbs_launch_log(int64_t* units, double* ms, int64_t cap, int64_t* n)
+{
+    clear_error();
+    if (!n) return set_error(BBS_EINVAL, "launch_log: n is NULL");
+    const LaunchLog& L = launch_log();
+    *n = (int64_t)L.ms.size();
+    if (cap < *n || (*n > 0 && (!units || !ms))) return *n == 0 ? BBS_OK : set_error(BBS_EINVAL, "launch_log: capacity %lld < %lld", (long long)cap, (long long)*n);
+    for (size_t i = 0; i < L.ms.size(); ++i) {
+        units[i] = L.units[i];
+        ms[i] = L.ms[i];
+    }
+    return BBS_OK;
+}
+
 int bbs_get_tuning(bbs_tuning* t)
 {
     clear_error();
@@ -573,6 +588,7 @@ int bbs_get_tuning(bbs_tuning* t)
     t->static_pm = v.static_pm;
     t->grab_min = v.grab_min;
     t->ctas_per_sm = v.ctas_per_sm;
+    t->frontier_log2 = v.frontier_log2;
     return BBS_OK;
 }
 

@@ -84,7 +84,10 @@ __device__ __forceinline__ void block_excl_scan_n(const int64_t (&v)[N], int64_t
 namespace {
 std::mutex g_tuning_mu;
 Tuning g_tuning;
+thread_local LaunchLog g_launch_log;
 }  // namespace
+
+LaunchLog& launch_log() { return g_launch_log; }
 
 Tuning current_tuning()
 {
@@ -100,6 +103,9 @@ int set_tuning(const bbs_tuning* t)
         if (t->static_pm) v.static_pm = t->static_pm;
         if (t->grab_min) v.grab_min = t->grab_min;
         if (t->ctas_per_sm) v.ctas_per_sm = t->ctas_per_sm;
+        if (t->frontier_log2) v.frontier_log2 = t->frontier_log2;
+        if (v.frontier_log2 && (v.frontier_log2 < 10 || v.frontier_log2 > 30))
+            return set_error(BBS_EINVAL, "tuning: frontier_log2 %d outside 10..30", v.frontier_log2);
         if (v.launch_tasks < 1 || v.launch_tasks > TASK_CAP)
             return set_error(BBS_EINVAL, "tuning: launch_tasks %lld outside 1..%lld", (long long)v.launch_tasks,
                              (long long)TASK_CAP);
@@ -122,6 +128,20 @@ __device__ __forceinline__ unsigned long long gtimer_ns()
     return t;
 }
 
+// Holds the stream until the host has enqueued a timed scoring launch behind
+// it, so that the launch's opening event fires right before the kernel starts
+// instead of while the host is still submitting it.  The wait is bounded (at
+// most about 20 ms): past it the gate records the overrun in *err and lets the
+// stream go, which only lengthens that launch's measured time.
+__global__ void timing_gate_kernel(const volatile int* open, int* err)
+{
+    for (int i = 0; i < 200000; ++i) {
+        if (*open) return;
+        __nanosleep(100);
+    }
+    *err = 1;
+}
+
 // reset the bucket arrays of one search (blockIdx.x = slot in `slots`)
 __global__ void slot_init_kernel(SearchDev* S, const int32_t* slots)
 {
@@ -139,8 +159,10 @@ __global__ void slot_init_kernel(SearchDev* S, const int32_t* slots)
 __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, Plan* P, LoopState* LS,
                                                       int64_t* poff, int64_t* toff, unsigned long long* pcnt,
                                                       unsigned long long* tcnt, cudaGraphConditionalHandle cond,
-                                                      int use_cond, Tuning tune)
+                                                      int use_cond, Tuning tune, const volatile int* wake)
 {
+    pdl_wait();   // the previous iteration's survivors and bucket counts are in
+    pdl_trigger();
     __shared__ int64_t sh[32 * 4];
     __shared__ int s_first;
     __shared__ int32_t s_star, s_reason;
@@ -267,7 +289,7 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
         __threadfence();
     }
     int64_t cp = 0, ct = 0, cs = 0, cn = 0;
-    int any3 = 0;
+    int any3 = 0, anyfin = 0;
     for (int base = 0; base < nslots; base += blockDim.x) {
         const int s = base + tid;
         int64_t np = 0, nt = 0, sl = 0, has = 0;
@@ -281,6 +303,7 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
             }
             // a leaf bucket popped in this round (the search may have finished with it)
             if (c->active && !c->err && c->match_changed) any3 = 1;
+            if (c->active && (c->done || c->err)) anyfin = 1;
             sl = nt * S[s].nblk;
             has = nt > 0;
             pcnt[s] = 0;
@@ -314,6 +337,7 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
         __syncthreads();   // sh read before the next pass
     }
     any3 = __syncthreads_or(any3);
+    anyfin = __syncthreads_or(anyfin);
     if (tid == 0) {
         P->nseg = (int32_t)(cn < MAXSEG ? cn : MAXSEG);
         P->n_slices = cs;
@@ -326,6 +350,11 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
         if (cp == 0) st = PLAN_EMPTY;
         else if (cn > MAXSEG || ct > tune.launch_tasks) st = PLAN_OVERFLOW;
         P->status = st;
+        // the other array receives the kept nodes (at most the current ones)
+        // and the survivors (at most 8 per task): grow first when that may not fit
+        const int64_t need = (int64_t)min(LS->fn[1 - LS->cur], (unsigned long long)LS->cap) + 8 * ct;
+        P->grow = (st != PLAN_EMPTY && need > LS->cap) ? 1 : 0;
+        LS->grow_need = need;
         P->iters += 1;
         // the nodes the last round appended become current; the other array
         // receives the kept and the new nodes
@@ -334,14 +363,20 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
         LS->fn[1 - cur] = 0;
         LS->lex_pass = any3;
         LS->select_done = 0;
-        if (use_cond && (st != PLAN_OK || P->iters >= P->max_iters)) cudaGraphSetConditional(cond, 0);
+        // the device loop ends with an empty or oversized round, after its
+        // iteration cap, when the host asks (wake), or, for the server, when a
+        // search finished or failed (its result is reported at once)
+        const bool stop = st != PLAN_OK || P->grow || P->iters >= P->max_iters || (LS->exit_on_finish && anyfin) ||
+                          *wake != 0;
+        if (use_cond && stop) cudaGraphSetConditional(cond, 0);
     }
 }
 
 // the tasks (rotational children, Eq. (13)) of parent nd for t in [t0, t1),
 // written at tasks[dst + t]: translation and rl (the scoring kernel forms the rows)
 __device__ __forceinline__ void write_tasks(const DevGrid& g, const NodeRec& nd, const int32_t lo[3],
-                                            const int32_t ext[3], int32_t t0, int32_t t1, TaskRec* tasks, int64_t dst)
+                                            const int32_t ext[3], int32_t t0, int32_t t1, TaskRec* tasks, int64_t dst,
+                                            int32_t* tscore, int32_t pscore)
 {
     const int l = rl_level(nd.rl);
     const int64_t nb = g.N[l - 1][1], ng = g.N[l - 1][2];
@@ -356,6 +391,7 @@ __device__ __forceinline__ void write_tasks(const DevGrid& g, const NodeRec& nd,
                 r.ty = 2 * nd.cy;
                 r.tz = 2 * nd.cz;
                 r.rl = rl_pack(crot, l - 1);
+                tscore[dst + t] = pscore;
             }
 }
 
@@ -366,14 +402,18 @@ __device__ __forceinline__ void write_tasks(const DevGrid& g, const NodeRec& nd,
 // bucket take part in the first lexmin pass (smallest translation key).
 __global__ void __launch_bounds__(256) compact_kernel(SearchDev* S, FrontDev F, LoopState* LS, const Plan* P,
                                                       NodeRec* __restrict__ parents, int64_t* __restrict__ pfirst,
-                                                      TaskRec* __restrict__ tasks, const int64_t* __restrict__ poff,
+                                                      int32_t* __restrict__ pscore, TaskRec* __restrict__ tasks,
+                                                      int32_t* __restrict__ tscore, const int64_t* __restrict__ poff,
                                                       const int64_t* __restrict__ toff, unsigned long long* pcnt,
                                                       unsigned long long* tcnt)
 {
+    pdl_wait();   // select's round plan is in
+    pdl_trigger();
+    if (P->grow) return;   // the round waits for the host to grow the frontier
     const int cur = LS->cur, nxt = 1 - cur;
     // appends past the capacity were not stored (their searches failed): the
     // count is clamped wherever it is read
-    const int64_t n = min((int64_t)LS->fn[cur], F.cap);
+    const int64_t n = min((int64_t)LS->fn[cur], LS->cap);
     const bool emit = P->status == PLAN_OK;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -381,6 +421,7 @@ __global__ void __launch_bounds__(256) compact_kernel(SearchDev* S, FrontDev F, 
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
         bool keep = false, popped = false;
         uint32_t key = 0;
+        int32_t score = 0;
         int sid = 0;
         int32_t T = 0, lo[3], ext[3];
         NodeRec nd;
@@ -391,7 +432,7 @@ __global__ void __launch_bounds__(256) compact_kernel(SearchDev* S, FrontDev F, 
             key = F.keys[cur][i];
             nd = F.nodes[cur][i];
             sid = (int)(key >> 24);
-            const int32_t score = (int32_t)(key & 0xFFFFFFu);
+            score = (int32_t)(key & 0xFFFFFFu);
             SearchDev& f = S[sid];
             c = f.ctl;
             if (c->active && !c->err) {
@@ -439,7 +480,9 @@ __global__ void __launch_bounds__(256) compact_kernel(SearchDev* S, FrontDev F, 
                     const int64_t pi = poff[sid] + (int64_t)p;
                     parents[pi] = nd;
                     pfirst[pi] = toff[sid] + (int64_t)t0;
-                    if (emit && T > 0) write_tasks(S[sid].grid, nd, lo, ext, 0, T, tasks, toff[sid] + (int64_t)t0);
+                    pscore[pi] = score;
+                    if (emit && T > 0)
+                        write_tasks(S[sid].grid, nd, lo, ext, 0, T, tasks, toff[sid] + (int64_t)t0, tscore, score);
                 } else {
                     atomicOr(&c->err, 4);   // bucket counts disagree with the nodes: fail the search
                 }
@@ -461,8 +504,9 @@ __global__ void __launch_bounds__(256) compact_kernel(SearchDev* S, FrontDev F, 
 // the tasks [ga, gb) of one search's round (gathered parents [p0, p1), their
 // first tasks in pfirst) -> tasks[la ..]: a round scored in several launches
 __global__ void expand_kernel(const SearchDev* S, int sid, const NodeRec* __restrict__ parents,
-                              const int64_t* __restrict__ pfirst, int64_t p0, int64_t p1, int64_t ga, int64_t gb,
-                              int64_t la, TaskRec* __restrict__ tasks)
+                              const int64_t* __restrict__ pfirst, const int32_t* __restrict__ pscore, int64_t p0,
+                              int64_t p1, int64_t ga, int64_t gb, int64_t la, TaskRec* __restrict__ tasks,
+                              int32_t* __restrict__ tscore)
 {
     const DevGrid& g = S[sid].grid;
     for (int64_t p = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < p1; p += (int64_t)gridDim.x * blockDim.x) {
@@ -473,7 +517,7 @@ __global__ void expand_kernel(const SearchDev* S, int sid, const NodeRec* __rest
         const int32_t T = rot_children(g, rl_level(nd.rl), rl_rot(nd.rl), lo, ext);
         if (b + T <= ga) continue;
         const int32_t t0 = (int32_t)(ga > b ? ga - b : 0), t1 = (int32_t)(gb < b + T ? gb - b : T);
-        write_tasks(g, nd, lo, ext, t0, t1, tasks, la + b - ga);
+        write_tasks(g, nd, lo, ext, t0, t1, tasks, la + b - ga, tscore, pscore[p]);
     }
 }
 
@@ -485,7 +529,7 @@ __global__ void purge_reset_kernel(LoopState* LS) { LS->fn[LS->cur] = 0; }
 __global__ void purge_kernel(FrontDev F, LoopState* LS, int slot)
 {
     const int in = 1 - LS->cur, out = LS->cur;
-    const int64_t n = min((int64_t)LS->fn[in], F.cap);   // appends past the capacity were not stored
+    const int64_t n = min((int64_t)LS->fn[in], LS->cap);   // appends past the capacity were not stored
     const int lane = threadIdx.x & 31;
     const int64_t n_round = (n + 31) & ~(int64_t)31;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_round; i += (int64_t)gridDim.x * blockDim.x) {
@@ -542,6 +586,7 @@ Engine::~Engine()
     if (h_off_) cudaFreeHost(h_off_);
     if (h_misc_) cudaFreeHost(h_misc_);
     if (h_zero_) cudaFreeHost(h_zero_);
+    if (h_wake_) cudaFreeHost(h_wake_);
 }
 
 int Engine::init()
@@ -571,6 +616,8 @@ int Engine::init()
     BBS_TRY(get(&parents_, (size_t)fcap_));
     BBS_TRY(get(&pfirst_, (size_t)fcap_));
     BBS_TRY(get(&tasks_, (size_t)TASK_CAP));
+    BBS_TRY(get(&tscore_, (size_t)TASK_CAP));
+    BBS_TRY(get(&pscore_, (size_t)fcap_));
     BBS_TRY(get(&d_poff_, (size_t)max_slots_));
     BBS_TRY(get(&d_toff_, (size_t)max_slots_));
     BBS_TRY(get(&d_pcnt_, (size_t)max_slots_));
@@ -589,6 +636,9 @@ int Engine::init()
     BBS_CUDA_TRY(cudaMallocHost((void**)&h_off_, 2 * sizeof(int64_t) * (size_t)max_slots_));
     BBS_CUDA_TRY(cudaMallocHost((void**)&h_misc_, 4 * sizeof(int32_t)));
     BBS_CUDA_TRY(cudaMallocHost((void**)&h_zero_, sizeof(Ctl)));
+    BBS_CUDA_TRY(cudaHostAlloc((void**)&h_wake_, 4 * sizeof(int), cudaHostAllocMapped));
+    h_wake_[0] = h_wake_[1] = h_wake_[2] = h_wake_[3] = 0;
+    BBS_CUDA_TRY(cudaHostGetDevicePointer((void**)&d_wake_, h_wake_, 0));
     std::memset(h_ctl_, 0, sizeof(Ctl) * (size_t)max_slots_);
     std::memset(h_misc_, 0, 4 * sizeof(int32_t));
     std::memset(h_zero_, 0, sizeof(Ctl));
@@ -605,7 +655,129 @@ int Engine::init()
         blank[(size_t)i].ctl = d_ctl_ + i;
     }
     BBS_CUDA_TRY(cudaMemcpyAsync(d_S_, blank.data(), sizeof(SearchDev) * blank.size(), cudaMemcpyHostToDevice, st_));
+    max_nodes_ = fcap_;
+    BBS_TRY(upload_cap());
     BBS_CUDA_TRY(cudaStreamSynchronize(st_));   // the host copy above must outlive its transfer
+    return BBS_OK;
+}
+
+int Engine::upload_cap()
+{
+    cap_eff_ = std::min(fcap_, max_nodes_);
+    // pageable source: staged before the call returns
+    BBS_CUDA_TRY(cudaMemcpyAsync(&d_ls_->cap, &cap_eff_, sizeof(int64_t), cudaMemcpyHostToDevice, st_));
+    return BBS_OK;
+}
+
+int Engine::set_max_nodes(int64_t n)
+{
+    max_nodes_ = n;
+    return upload_cap();
+}
+
+// A round whose survivors might not fit asked to grow the frontier arrays
+// (select planned it; compaction, scoring and survivors waited).  The
+// arrays double until they hold the round's need, within max_nodes_; the
+// current nodes move over; the graph, captured with the old arrays, is
+// rebuilt on the next iterate.  When the need is beyond max_nodes_ the round
+// goes on as it is and the searches whose survivors do not fit fail alone.
+// The round planned by the last select asked to grow the frontier arrays
+// (compaction, scoring and survivors waited): grow to its need, then let
+// the round go on.  The live nodes are in the array select made current.
+int Engine::grow_frontier()
+{
+    LoopState ls;
+    BBS_CUDA_TRY(cudaMemcpyAsync(&ls, d_ls_, sizeof(ls), cudaMemcpyDeviceToHost, st_));
+    BBS_CUDA_TRY(cudaStreamSynchronize(st_));
+    BBS_TRY(grow_to(ls.grow_need, ls.cur, (int64_t)ls.fn[ls.cur]));
+    const int32_t zero = 0;
+    BBS_CUDA_TRY(cudaMemcpyAsync(&d_plan_->grow, &zero, sizeof(zero), cudaMemcpyHostToDevice, st_));
+    return BBS_OK;
+}
+
+// The frontier arrays double until they hold `need` nodes, within
+// max_nodes_; the n live nodes of array `live` move over; the graph,
+// captured with the old arrays, is rebuilt on the next iterate.  When the
+// need is beyond max_nodes_ nothing changes: the searches whose survivors do
+// not fit fail alone, as without growth.
+int Engine::grow_to(int64_t need, int live, int64_t n)
+{
+    if (need <= cap_eff_ || need > max_nodes_) return BBS_OK;
+    int64_t ncap = fcap_;
+    while (ncap < need) ncap *= 2;
+    if (ncap > max_nodes_) ncap = max_nodes_;
+    std::vector<void*> fresh;
+    size_t fresh_bytes = 0;
+    auto get = [&](auto** p, size_t cnt) -> int {
+        void* q = nullptr;
+        const size_t bytes = cnt * sizeof(**p) + 16;
+        const cudaError_t e = cudaMallocAsync(&q, bytes, st_);
+        if (e != cudaSuccess) return set_error(BBS_ENOMEM, "engine: growing the frontier: %s", cudaGetErrorString(e));
+        fresh.push_back(q);
+        fresh_bytes += bytes;
+        *p = (typename std::remove_reference<decltype(*p)>::type)q;
+        return BBS_OK;
+    };
+    FrontDev nf = front_;
+    NodeRec* np = nullptr;
+    int64_t* nfirst = nullptr;
+    int32_t* nscore = nullptr;
+    int rc = BBS_OK;
+    for (int b = 0; b < 2 && rc == BBS_OK; ++b) {
+        rc = get(&nf.nodes[b], (size_t)ncap);
+        if (rc == BBS_OK) rc = get(&nf.keys[b], (size_t)ncap);
+    }
+    if (rc == BBS_OK) rc = get(&np, (size_t)ncap);
+    if (rc == BBS_OK) rc = get(&nfirst, (size_t)ncap);
+    if (rc == BBS_OK) rc = get(&nscore, (size_t)ncap);
+    if (rc != BBS_OK) {
+        for (void* q : fresh) cudaFreeAsync(q, st_);
+        return rc;
+    }
+    nf.cap = ncap;
+    n = std::min<int64_t>(n, cap_eff_);   // appends past the run's cap were not stored
+    BBS_CUDA_TRY(cudaMemcpyAsync(nf.nodes[live], front_.nodes[live], sizeof(NodeRec) * (size_t)n,
+                                 cudaMemcpyDeviceToDevice, st_));
+    BBS_CUDA_TRY(cudaMemcpyAsync(nf.keys[live], front_.keys[live], sizeof(uint32_t) * (size_t)n,
+                                 cudaMemcpyDeviceToDevice, st_));
+    // retire the old arrays (stream-ordered, after the copies)
+    const void* old[7] = {front_.nodes[0], front_.keys[0], front_.nodes[1], front_.keys[1], parents_, pfirst_, pscore_};
+    for (const void* q : old)
+        for (size_t i = 0; i < fixed_.size(); ++i)
+            if (fixed_[i] == q) {
+                cudaFreeAsync(fixed_[i], st_);
+                fixed_.erase(fixed_.begin() + (long)i);
+                break;
+            }
+    for (void* q : fresh) fixed_.push_back(q);
+    // each array was allocated with 16 bytes to spare (see init)
+    const size_t per_node = 2 * (sizeof(NodeRec) + sizeof(uint32_t)) + sizeof(NodeRec) + sizeof(int64_t) + sizeof(int32_t);
+    fixed_bytes_ = fixed_bytes_ + fresh_bytes - ((size_t)fcap_ * per_node + 7 * 16);
+    front_ = nf;
+    parents_ = np;
+    pfirst_ = nfirst;
+    pscore_ = nscore;
+    fcap_ = ncap;
+    BBS_TRY(upload_cap());
+    if (exec_) {   // the captured graph holds the old arrays
+        cudaGraphExecDestroy(exec_);
+        exec_ = nullptr;
+    }
+    grown_ += 1;
+    return BBS_OK;
+}
+
+// the rest of a round that waited for growth: compaction and the lexmin
+// leaf, then the control blocks (the caller scores the round)
+int Engine::resume_grown(std::vector<int>* finished)
+{
+    BBS_TRY(grow_frontier());
+    BBS_CUDA_TRY(launch_compact(st_));
+    BBS_CUDA_TRY(launch_finalize(MODE_SEARCH, d_plan_, d_S_, tasks_, dense_, front_, d_ls_, nsm_ * 8, st_, true));
+    launches_ += 2;
+    BBS_CUDA_TRY(cudaGetLastError());
+    BBS_TRY(read_ctl());
+    mark_finished(finished);
     return BBS_OK;
 }
 
@@ -638,6 +810,10 @@ int Engine::begin_run(cudaStream_t st, bool timed)
     evs_.clear();
     // a finished run leaves no nodes; start from empty arrays all the same
     BBS_CUDA_TRY(cudaMemsetAsync(d_ls_, 0, sizeof(LoopState), st_));
+    exit_on_finish_ = false;
+    max_nodes_ = fcap_;
+    BBS_TRY(upload_cap());
+    *h_wake_ = 0;
     h_misc_[2] = 0;
     return BBS_OK;
 }
@@ -786,9 +962,31 @@ int Engine::add(const bbs_maps* m, const float* xyz, int64_t k, int is_device, c
 int Engine::start()
 {
     std::vector<int32_t> slots;
-    for (int i = 0; i < max_slots_; ++i)
+    bool others = false;   // searches already iterating keep nodes in the frontier
+    for (int i = 0; i < max_slots_; ++i) {
         if (hosts_[(size_t)i].fresh) slots.push_back(i);
+        else if (hosts_[(size_t)i].live) others = true;
+    }
     if (slots.empty()) return BBS_OK;
+    // the initial sets' survivors (at most 8 per task) join the incoming array:
+    // grow first when they may not fit
+    if (max_nodes_ > cap_eff_) {
+        int64_t extra = 0;
+        for (int i : slots) {
+            const SearchHost& h = hosts_[(size_t)i];
+            extra += 8 * (int64_t)h.dev.pext[0] * h.dev.pext[1] * h.dev.pext[2] * h.scan.grid.nrot[h.scan.grid.levels - 1];
+        }
+        int64_t held = 0;
+        int incoming = 1;
+        if (others || extra > cap_eff_) {
+            LoopState ls;
+            BBS_CUDA_TRY(cudaMemcpyAsync(&ls, d_ls_, sizeof(ls), cudaMemcpyDeviceToHost, st_));
+            BBS_CUDA_TRY(cudaStreamSynchronize(st_));
+            incoming = 1 - ls.cur;
+            held = others ? (int64_t)ls.fn[incoming] : 0;
+        }
+        if (held + extra > cap_eff_) BBS_TRY(grow_to(held + extra, incoming, held));
+    }
     BBS_CUDA_TRY(cudaMemcpyAsync(d_slots_, slots.data(), sizeof(int32_t) * slots.size(), cudaMemcpyHostToDevice, st_));
     slot_init_kernel<<<(int)slots.size(), 1024, 0, st_>>>(d_S_, d_slots_);
     launches_ += 1;
@@ -898,16 +1096,18 @@ void Engine::mark_finished(std::vector<int>* finished)
     }
 }
 
-void Engine::launch_select(cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond)
+cudaError_t Engine::launch_select(cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond)
 {
     select_kernel<<<max_slots_, 1024, 0, s>>>(d_S_, max_slots_, d_plan_, d_ls_, d_poff_, d_toff_, d_pcnt_, d_tcnt_, cond,
-                                             use_cond, tune_);
+                                             use_cond, tune_, d_wake_);
+    return cudaGetLastError();
 }
 
-void Engine::launch_compact(cudaStream_t s)
+cudaError_t Engine::launch_compact(cudaStream_t s, bool pdl)
 {
-    compact_kernel<<<nsm_ * 4, 256, 0, s>>>(d_S_, front_, d_ls_, d_plan_, parents_, pfirst_, tasks_, d_poff_, d_toff_,
-                                           d_pcnt_, d_tcnt_);
+    return launch_pdl(compact_kernel, dim3(nsm_ * 4), dim3(256), s, pdl, d_S_, front_, d_ls_, (const Plan*)d_plan_,
+                      parents_, pfirst_, pscore_, tasks_, tscore_, (const int64_t*)d_poff_, (const int64_t*)d_toff_,
+                      d_pcnt_, d_tcnt_);
 }
 
 // one host-driven iteration: select (+ plan), compaction and the second
@@ -920,16 +1120,18 @@ int Engine::step(std::vector<int>* finished)
     h_plan_.iters = 0;
     h_plan_.max_iters = 1 << 30;
     BBS_CUDA_TRY(cudaMemcpyAsync(&d_plan_->iters, &h_plan_.iters, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, st_));
-    launch_select(st_, 0, 0);
-    launch_compact(st_);
+    BBS_CUDA_TRY(launch_select(st_, 0, 0));
+    BBS_CUDA_TRY(launch_compact(st_));
     // the lexmin leaf must be complete when the control blocks are read below
     BBS_CUDA_TRY(launch_finalize(MODE_SEARCH, d_plan_, d_S_, tasks_, dense_, front_, d_ls_, nsm_ * 8, st_, true));
     launches_ += 3;
     BBS_CUDA_TRY(cudaGetLastError());
-    BBS_CUDA_TRY(cudaMemcpyAsync(h_misc_, &d_plan_->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
+    // status, iterations, cap and the grow request of the plan
+    BBS_CUDA_TRY(cudaMemcpyAsync(h_misc_, &d_plan_->status, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
     BBS_TRY(read_ctl());
-    mark_finished(finished);
     const int32_t status = h_misc_[0];
+    if (h_misc_[3]) BBS_TRY(resume_grown(finished));
+    else mark_finished(finished);
     if (status == PLAN_OK) return score_launch(MODE_SEARCH, nullptr, 0, 0);
     if (status == PLAN_OVERFLOW) return score_overflow();
     return BBS_OK;
@@ -963,8 +1165,9 @@ int Engine::score_overflow()
                 continue;
             }
             const int blocks = (int)std::min<int64_t>((np + 255) / 256, 4096);
-            expand_kernel<<<std::max(blocks, 1), 256, 0, st_>>>(d_S_, i, parents_, pfirst_, h_off_[i], h_off_[i] + np,
-                                                                 h_off_[n + i] + t0, h_off_[n + i] + t0 + take, ntk, tasks_);
+            expand_kernel<<<std::max(blocks, 1), 256, 0, st_>>>(d_S_, i, parents_, pfirst_, pscore_, h_off_[i],
+                                                                 h_off_[i] + np, h_off_[n + i] + t0,
+                                                                 h_off_[n + i] + t0 + take, ntk, tasks_, tscore_);
             launches_ += 1;
             BBS_CUDA_TRY(cudaGetLastError());
             Seg sg;
@@ -984,42 +1187,72 @@ int Engine::score_overflow()
     return flush();
 }
 
-int Engine::build_graph()
+// One iteration of the device loop: select (+ plan), compaction, scoring
+// (+ lexmin, survivors).  With pdl, each kernel after the first is a
+// programmatic dependent launch: its CTAs are scheduled while its predecessor
+// drains and wait (pdl_wait) for it to complete, hiding the launch gaps.
+cudaError_t Engine::capture_body(cudaGraph_t body, cudaGraphConditionalHandle cond, bool pdl)
 {
     cudaStream_t cs;
-    BBS_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaGraphCreate(&g, 0);
-    cudaGraphConditionalHandle cond = 0;
-    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
-    alignas(cudaGraphNodeParams) unsigned char np_buf[sizeof(cudaGraphNodeParams)];
-    std::memset(np_buf, 0, sizeof(np_buf));
-    cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(np_buf);
-    np.type = cudaGraphNodeTypeConditional;
-    np.conditional.handle = cond;
-    np.conditional.type = cudaGraphCondTypeWhile;
-    np.conditional.size = 1;
-    cudaGraphNode_t node;
-    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
-    cudaGraph_t body = e == cudaSuccess ? np.conditional.phGraph_out[0] : nullptr;
-    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        // one iteration: select (+ plan), compaction, score (+ lexmin, survivors)
-        launch_select(cs, cond, 1);
-        launch_compact(cs);
-        launch_branch(MODE_SEARCH, d_plan_, d_S_, tasks_, dense_, nsm_ * tune_.ctas_per_sm, cs, graph_bytes_);
-        launch_finalize(MODE_SEARCH, d_plan_, d_S_, tasks_, dense_, front_, d_ls_, nsm_ * 8, cs);
+        cudaError_t le = launch_select(cs, cond, 1);
+        if (le == cudaSuccess) le = launch_compact(cs, pdl);
+        if (le == cudaSuccess)
+            le = launch_branch(MODE_SEARCH, d_plan_, d_S_, tasks_, dense_, nsm_ * tune_.ctas_per_sm, cs, graph_bytes_,
+                               pdl);
+        if (le == cudaSuccess)
+            le = launch_finalize(MODE_SEARCH, d_plan_, d_S_, tasks_, dense_, front_, d_ls_, nsm_ * 8, cs, false, tscore_,
+                                 pdl);
         cudaGraph_t out = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cs, &out);
-        e = e2 != cudaSuccess ? e2 : cudaGetLastError();
+        e = le != cudaSuccess ? le : e2;
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec_, g, 0);
-    if (g) cudaGraphDestroy(g);
     cudaStreamDestroy(cs);
-    if (e != cudaSuccess) {
+    return e;
+}
+
+int Engine::build_graph()
+{
+    // with programmatic dependent launches first; a driver that refuses them
+    // inside the loop body gets the plain launches
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        const bool pdl = graph_pdl_ && attempt == 0;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaGraphCreate(&g, 0);
+        cudaGraphConditionalHandle cond = 0;
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+        alignas(cudaGraphNodeParams) unsigned char np_buf[sizeof(cudaGraphNodeParams)];
+        std::memset(np_buf, 0, sizeof(np_buf));
+        cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(np_buf);
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = cond;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+        if (e == cudaSuccess) e = capture_body(np.conditional.phGraph_out[0], cond, pdl);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec_, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e == cudaSuccess) {
+            graph_pdl_ = pdl;
+            return BBS_OK;
+        }
         exec_ = nullptr;
-        return set_error(BBS_ECUDA, "engine: building the iteration graph: %s", cudaGetErrorString(e));
+        cudaGetLastError();   // a refused capture leaves no sticky error
+        if (!pdl) return set_error(BBS_ECUDA, "engine: building the iteration graph: %s", cudaGetErrorString(e));
     }
+    return set_error(BBS_ECUDA, "engine: building the iteration graph");
+}
+
+int Engine::set_exit_on_finish(bool v)
+{
+    exit_on_finish_ = v;
+    const int32_t x = v ? 1 : 0;
+    // pageable source: staged before the call returns
+    BBS_CUDA_TRY(cudaMemcpyAsync(&d_ls_->exit_on_finish, &x, sizeof(x), cudaMemcpyHostToDevice, st_));
     return BBS_OK;
 }
 
@@ -1044,10 +1277,16 @@ int Engine::iterate(int max_iters, std::vector<int>* finished)
     BBS_CUDA_TRY(cudaMemcpyAsync(&d_plan_->iters, &h_plan_.iters, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, st_));
     BBS_CUDA_TRY(cudaGraphLaunch(exec_, st_));
     // status and the iterations the device loop ran, with the control blocks
-    BBS_CUDA_TRY(cudaMemcpyAsync(h_misc_, &d_plan_->status, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
+    BBS_CUDA_TRY(cudaMemcpyAsync(h_misc_, &d_plan_->status, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
     BBS_TRY(read_ctl());
     const int32_t status = h_misc_[0];
     launches_ += 4 * (int64_t)h_misc_[1];   // every iteration of the loop runs the body's 4 kernels
+    if (h_misc_[3]) {   // the last round waits for the frontier to grow; then it is scored from the host
+        BBS_TRY(resume_grown(finished));
+        if (status == PLAN_OK) return score_launch(MODE_SEARCH, nullptr, 0, 0);
+        if (status == PLAN_OVERFLOW) return score_overflow();
+        return BBS_OK;
+    }
     mark_finished(finished);
     if (status == PLAN_OVERFLOW) return score_overflow();   // the selected round did not fit one launch
     return BBS_OK;
@@ -1061,14 +1300,21 @@ int Engine::finalize(int i, bbs_result* out)
     Ctl c;
     std::memset(&c, 0, sizeof(c));
     if (h.scan.k > 0) c = h_ctl_[i];
-    if (!evs_.empty()) BBS_CUDA_TRY(cudaEventSynchronize(evs_.back()));
+    if (!evs_.empty()) {
+        BBS_CUDA_TRY(cudaEventSynchronize(evs_.back()));
+        g_launch_log.units.clear();
+        g_launch_log.ms.clear();
+    }
     for (size_t e = 0; e + 1 < evs_.size(); e += 2) {
         float ms = 0.0f;
         BBS_CUDA_TRY(cudaEventElapsedTime(&ms, evs_[e], evs_[e + 1]));
         score_ms_ += ms;
+        g_launch_log.units.push_back(e / 2 < ev_units_.size() ? ev_units_[e / 2] : 0);
+        g_launch_log.ms.push_back(ms);
     }
     for (cudaEvent_t e : evs_) cudaEventDestroy(e);
     evs_.clear();
+    ev_units_.clear();
     bbs_result* r = &h.res;
     const double t_fin = now_ms();
     if (h.t_end == 0) h.t_end = t_fin;
@@ -1086,6 +1332,9 @@ int Engine::finalize(int i, bbs_result* out)
         r->iterations = c.st_iters;
         r->parents_branched = c.st_parents;
         r->nodes_scored += c.st_nodes;
+        r->children_scored = c.st_nodes;
+        r->bound_violations = (int64_t)c.st_viol;
+        r->bound_excess = c.st_excess;
         r->gathers += c.st_gathers;
         r->probes = r->nodes_scored * h.scan.k;
         r->best_score = c.best;
@@ -1183,16 +1432,37 @@ int Engine::score_launch(int mode, const std::vector<Seg>* segs, int64_t n_slice
                                      cudaMemcpyHostToDevice, st_));
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    volatile int* gate = h_wake_ + 1;   // h_wake_[1]: the timing gate, h_wake_[2]: its overrun flag
     if (timed_) {
         BBS_CUDA_TRY(cudaEventCreate(&e0));
         evs_.push_back(e0);
         BBS_CUDA_TRY(cudaEventCreate(&e1));
         evs_.push_back(e1);
+        *gate = 0;
+        timing_gate_kernel<<<1, 1, 0, st_>>>(d_wake_ + 1, d_wake_ + 2);
+        // the launch's units: a host plan's segments, else the tasks the
+        // control blocks (read before every device-planned launch) report
+        int64_t u = 0;
+        if (segs) {
+            for (const Seg& g : *segs) u += g.n_tasks * (int64_t)hosts_[(size_t)g.sid].scan.k;
+        } else {
+            for (int i = 0; i < max_slots_; ++i)
+                if (hosts_[(size_t)i].live && h_ctl_[i].active && !h_ctl_[i].done && !h_ctl_[i].err)
+                    u += h_ctl_[i].n_tasks * hosts_[(size_t)i].scan.k;
+        }
+        ev_units_.push_back(u);
         BBS_CUDA_TRY(cudaEventRecord(e0, st_));
     }
-    BBS_CUDA_TRY(launch_branch(mode, d_plan_, d_S_, tasks_, dense_, nsm_ * tune_.ctas_per_sm, st_, bytes_only()));
-    if (timed_) BBS_CUDA_TRY(cudaEventRecord(e1, st_));
-    BBS_CUDA_TRY(launch_finalize(mode, d_plan_, d_S_, tasks_, dense_, front_, d_ls_, nsm_ * 8, st_));
+    const cudaError_t le = launch_branch(mode, d_plan_, d_S_, tasks_, dense_, nsm_ * tune_.ctas_per_sm, st_, bytes_only());
+    if (timed_) {
+        const cudaError_t re = cudaEventRecord(e1, st_);
+        *gate = 1;   // everything is enqueued: the stream may run the launch
+        BBS_CUDA_TRY(le);
+        BBS_CUDA_TRY(re);
+    }
+    BBS_CUDA_TRY(le);
+    BBS_CUDA_TRY(launch_finalize(mode, d_plan_, d_S_, tasks_, dense_, front_, d_ls_, nsm_ * 8, st_, false,
+                                 mode == MODE_SEARCH ? tscore_ : nullptr));
     BBS_CUDA_TRY(cudaGetLastError());
     launches_ += 2;
     score_launches_ += 1;
@@ -1266,14 +1536,19 @@ void release_engine(Engine* e, bool healthy)
 int search_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device, const bbs_ranges* rg,
                const bbs_opts* opts, cudaStream_t st, bbs_result* res)
 {
-    const int64_t max_frontier = (opts && opts->max_frontier > 0) ? opts->max_frontier : ((int64_t)1 << 24);
+    // the frontier starts at up to 2^24 nodes and doubles as a search needs, up to max_frontier
+    const int64_t max_frontier = (opts && opts->max_frontier > 0) ? opts->max_frontier : ((int64_t)1 << 30);
     const bool timed = opts && (opts->flags & BBS_TIME_KERNELS);
-    const int64_t pool_nodes = max_frontier + (int64_t)CH * std::min<int64_t>(k + 1, 8192);
+    const int64_t slack = (int64_t)CH * std::min<int64_t>(k + 1, 8192);
+    const int32_t f2 = current_tuning().frontier_log2;
+    const int64_t pool_nodes = f2 ? std::min<int64_t>(max_frontier, (int64_t)1 << f2)
+                                  : std::min<int64_t>(max_frontier, (int64_t)1 << 24) + slack;
     std::memset(res, 0, sizeof(*res));
     int rc = BBS_OK;
     Engine* E = acquire_engine(1, pool_nodes, st, timed, &rc);
     if (!E) return rc;
     int slot = -1;
+    if (rc == BBS_OK) rc = E->set_max_nodes(std::max(pool_nodes, max_frontier));
     if (rc == BBS_OK) rc = E->add(m, xyz, k, is_device, rg, opts, 0, &slot);
     if (rc == BBS_OK) rc = E->start();
     E->set_host_driven(opts && (opts->flags & BBS_HOST_DRIVEN));
@@ -1290,18 +1565,21 @@ int search_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device, co
 int search_run_many(const bbs_maps* m, int n, const float* const* scans, const int64_t* ks, int is_device,
                     const bbs_ranges* rg, const bbs_opts* opts, cudaStream_t st, bbs_result* res)
 {
-    const int64_t max_frontier = (opts && opts->max_frontier > 0) ? opts->max_frontier : ((int64_t)1 << 24);
+    const int64_t max_frontier = (opts && opts->max_frontier > 0) ? opts->max_frontier : ((int64_t)1 << 30);
     const bool timed = opts && (opts->flags & BBS_TIME_KERNELS);
     int64_t kmax = 1;
     for (int i = 0; i < n; ++i) kmax = std::max(kmax, ks[i]);
     // at most MAX_SLOTS searches advance together; the others take slots as
     // searches finish (each result is the same either way)
     const int slots = std::min(n, MAX_SLOTS);
-    const int64_t pool_nodes =
-        max_frontier + (int64_t)CH * std::min<int64_t>((kmax + 1) * slots, 8192 * (int64_t)slots);
+    const int64_t slack = (int64_t)CH * std::min<int64_t>((kmax + 1) * slots, 8192 * (int64_t)slots);
+    const int32_t f2 = current_tuning().frontier_log2;
+    const int64_t pool_nodes = f2 ? std::min<int64_t>(max_frontier, (int64_t)1 << f2)
+                                  : std::min<int64_t>(max_frontier, (int64_t)1 << 24) + slack;
     int rc = BBS_OK;
     Engine* E = acquire_engine(slots, pool_nodes, st, timed, &rc);
     if (!E) return rc;
+    if (rc == BBS_OK) rc = E->set_max_nodes(std::max(pool_nodes, max_frontier));
     int next = 0;
     auto admit = [&]() {
         for (int slot = -1; rc == BBS_OK && next < n && E->used_count() < slots; ++next) {

@@ -40,6 +40,14 @@ struct SearchHost {
 // search slots of one engine: a frontier key holds its search in the top byte
 constexpr int MAX_SLOTS = 256;
 
+// the scoring launches of the last timed call on this thread: units (tasks x
+// scan points) and device milliseconds of each (bbs_launch_log)
+struct LaunchLog {
+    std::vector<int64_t> units;
+    std::vector<double> ms;
+};
+LaunchLog& launch_log();
+
 class Engine {
   public:
     Engine(cudaStream_t st, int max_slots, int64_t pool_nodes, bool timed);
@@ -64,6 +72,17 @@ class Engine {
     // one host-driven step.  Results are identical either way.
     int iterate(int max_iters, std::vector<int>* finished);
     void set_host_driven(bool v) { host_driven_ = v; }
+    // the device loop of iterate() also ends at the first iteration in which a
+    // search finishes or fails (the server reports each result at once)
+    int set_exit_on_finish(bool v);
+    // host-written flag the device loop polls every iteration: nonzero ends
+    // it after the current iteration (the server sets it when a request
+    // arrives or is cancelled, so the new work joins without waiting)
+    volatile int* wake_flag() { return h_wake_; }
+    // the frontier of this run holds at most n nodes: the arrays grow
+    // (doubling) up to n when a round's survivors might not fit, and a larger
+    // pool left by an earlier run is used only up to n
+    int set_max_nodes(int64_t n);
     // the search's result; the slot and its memory are released
     int finalize(int slot, bbs_result* out);
     // stop a search early and release it (its result reports status `code`)
@@ -83,12 +102,17 @@ class Engine {
     static constexpr int64_t DENSE_CAP = 8 * TASK_CAP;   // child scores per scoring launch
     int score_launch(int mode, const std::vector<Seg>* segs, int64_t n_slices, int64_t n_tasks);
     int score_overflow();
-    void launch_select(cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond);
-    void launch_compact(cudaStream_t s);
+    cudaError_t launch_select(cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond);
+    cudaError_t launch_compact(cudaStream_t s, bool pdl = false);
     int read_ctl();
+    int upload_cap();
+    int grow_frontier();
+    int grow_to(int64_t need, int live, int64_t n);
+    int resume_grown(std::vector<int>* finished);
     void finish_never_live(std::vector<int>* finished);
     void mark_finished(std::vector<int>* finished);
     int build_graph();
+    cudaError_t capture_body(cudaGraph_t body, cudaGraphConditionalHandle cond, bool pdl);
     int upload_slot(int slot);
     int release(int slot);
     template <class T>
@@ -98,6 +122,8 @@ class Engine {
     int max_slots_;
     bool timed_;
     int64_t fcap_;                 // frontier capacity (nodes, all searches)
+    int64_t max_nodes_ = 0;        // the run's frontier limit: the capacity may grow to this
+    int64_t cap_eff_ = 0;          // nodes the run may hold: min(fcap_, max_nodes_)
     Tuning tune_;                  // launch shape of this run
     size_t fixed_bytes_ = 0;
     FrontDev front_{};
@@ -107,6 +133,8 @@ class Engine {
     NodeRec* parents_ = nullptr;   // popped nodes of a round (per search at poff)
     int64_t* pfirst_ = nullptr;    // first task of each popped node
     TaskRec* tasks_ = nullptr;     // the launch's tasks
+    int32_t* tscore_ = nullptr;    // each task's parent score (the bound check of finalize)
+    int32_t* pscore_ = nullptr;    // each popped node's score (tasks expanded in windows)
     int64_t* d_poff_ = nullptr;
     int64_t* d_toff_ = nullptr;
     unsigned long long* d_pcnt_ = nullptr;
@@ -117,18 +145,24 @@ class Engine {
     int64_t* h_off_ = nullptr;     // pinned: parent and task offsets of an overflowing round
     int32_t* h_misc_ = nullptr;    // pinned: plan status, loop iterations
     Ctl* h_zero_ = nullptr;        // pinned, all zero
+    int* h_wake_ = nullptr;        // pinned and mapped: the device loop's wake-up flag
+    int* d_wake_ = nullptr;        // its device address
+    bool exit_on_finish_ = false;
     Plan* d_plan_ = nullptr;
     Plan h_plan_{};
     int nsm_ = 152;
     cudaGraphExec_t exec_ = nullptr;
     bool graph_bytes_ = false;     // the graph's scoring kernel is the byte-grid-only variant
+    bool graph_pdl_ = true;        // capture the loop body with programmatic dependent launches
     bool bytes_only() const;
     bool host_driven_ = false;
     std::vector<void*> fixed_;
     std::vector<SearchHost> hosts_;
     std::vector<cudaEvent_t> evs_;
+    std::vector<int64_t> ev_units_;   // units (tasks x scan points) of each timed scoring launch
     double score_ms_ = 0.0;
     int64_t launches_ = 0, score_launches_ = 0;
+    int64_t grown_ = 0;            // times the frontier arrays grew
 };
 
 }  // namespace bbs

@@ -230,13 +230,17 @@ int hostqueue_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device,
     // the popped parents' rotational children (Eq. (13)), scored in launches of
     // at most the tuning's task count; children above best join the frontier
     std::vector<NodeRec> parents;
+    std::vector<int32_t> pscores;   // the score of each parent (the bucket it was popped from)
+    std::vector<int32_t> tps;       // each task's parent score
     auto branch_parents = [&](int64_t pk) -> int {
         res->iterations += 1;
         res->parents_branched += (int64_t)parents.size();
         res->nodes_scored += pk;
         res->gathers += (pk / 8) * k;
         tk.clear();
-        for (const NodeRec& nd : parents) {
+        tps.clear();
+        for (size_t pi = 0; pi < parents.size(); ++pi) {
+            const NodeRec& nd = parents[pi];
             const int l = rl_level(nd.rl);
             int32_t lo[3], ext[3];
             if (rot_children(dg, l, rl_rot(nd.rl), lo, ext) == 0) continue;
@@ -251,6 +255,7 @@ int hostqueue_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device,
                         t.tz = 2 * nd.cz;
                         t.rl = rl_pack((uint32_t)(((int64_t)(lo[0] + ja) * nb + (lo[1] + jb)) * ng + (lo[2] + jg)), l - 1);
                         tk.push_back(t);
+                        tps.push_back(pscores[pi]);
                     }
         }
         std::vector<TaskRec> all;
@@ -258,10 +263,16 @@ int hostqueue_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device,
         for (size_t u0 = 0; u0 < all.size(); u0 += (size_t)tn.launch_tasks) {
             const size_t u1 = std::min(all.size(), u0 + (size_t)tn.launch_tasks);
             tk.assign(all.begin() + (long)u0, all.begin() + (long)u1);
+            res->children_scored += 8 * (int64_t)tk.size();
             BBS_TRY(score_tasks());
             for (size_t u = 0; u < tk.size(); ++u)
                 for (int j = 0; j < 8; ++j) {
                     const int32_t sc = dense[8 * u + j];
+                    const int32_t ps = tps[u0 + u];
+                    if (sc > ps) {   // Sec. IV-A: the child beats its parent's bound
+                        res->bound_violations += 1;
+                        res->bound_excess += (double)(sc - ps) / (double)sc;
+                    }
                     if (sc <= best) continue;
                     insert(NodeRec{tk[u].tx + (j >> 2), tk[u].ty + ((j >> 1) & 1), tk[u].tz + (j & 1), tk[u].rl}, sc);
                 }
@@ -295,6 +306,7 @@ int hostqueue_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device,
                 }
         }
         parents.clear();
+        pscores.clear();
         int64_t pk = 0;
         for (int l = 1; l < nfr && pk < batch; ++l)
             for (int32_t t = ltop[(size_t)l]; t > best && pk < batch; --t) {
@@ -302,6 +314,7 @@ int hostqueue_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device,
                 if (hb.nodes.empty()) continue;
                 pk += hb.kids;
                 parents.insert(parents.end(), hb.nodes.begin(), hb.nodes.end());
+                pscores.insert(pscores.end(), hb.nodes.size(), t);
                 lsize[(size_t)l] -= (int64_t)hb.nodes.size();
                 size -= (int64_t)hb.nodes.size();
                 hb = HostBucket();
@@ -343,11 +356,13 @@ int hostqueue_run(const bbs_maps* m, const float* xyz, int64_t k, int is_device,
             t_match = ms_now();
         }
         parents.clear();
+        pscores.clear();
         int64_t pk = 0;
         for (int32_t s = top; s > sstar; --s) {
             HostBucket& b = F[(size_t)s];
             pk += b.kids;
             parents.insert(parents.end(), b.nodes.begin(), b.nodes.end());
+            pscores.insert(pscores.end(), b.nodes.size(), s);
             b = HostBucket();
         }
         if (clear)

@@ -2,7 +2,10 @@
 //
 // One worker thread owns an Engine (engine.cuh) and a CUDA stream.  Clients
 // submit requests (a map handle, a scan that is copied, ranges, options) and
-// poll tickets.  Between iterations the worker admits queued requests into free
+// poll tickets.  The worker runs the engine's device loop until a search
+// finishes or fails or a request arrives or is cancelled (a flag in mapped
+// host memory the loop polls every iteration); then it reports finished
+// searches and admits queued requests into free
 // search slots as long as the device-memory budget allows -- the shared
 // frontier pool is charged once, each admitted search its scan, rotation
 // tables and frontier arrays -- so requests that arrive while others run join
@@ -113,6 +116,8 @@ void worker_main(bbs_server* S)
             std::unique_lock<std::mutex> lock(S->mu);
             S->cv_work.wait(lock, [&] { return S->stop || !S->queue.empty() || S->engine->used_count() > 0; });
             if (S->stop) break;
+            // arrivals and cancels after this point wake the device loop again
+            *S->engine->wake_flag() = 0;
             for (uint64_t t : S->cancels) {
                 auto it = S->running.find(t);
                 if (it != S->running.end()) to_cancel.push_back({it->second, t});
@@ -168,7 +173,9 @@ void worker_main(bbs_server* S)
         }
         int rc = S->engine->start();
         fin.clear();
-        if (rc >= 0) rc = S->engine->iterate(4, &fin);   // a few device iterations, then admission again
+        // the device loop runs until a search finishes or fails, or a request
+        // arrives or is cancelled (the wake flag): then admission again
+        if (rc >= 0) rc = S->engine->iterate(1 << 20, &fin);
         if (rc < 0) {
             std::lock_guard<std::mutex> lock(S->mu);
             S->fatal = rc;
@@ -229,6 +236,7 @@ int bbs_server_create(const bbs_server_opts* o, bbs_server** out)
     if (rc == BBS_OK && S->engine->fixed_bytes() > S->budget)
         rc = set_error(BBS_ENOMEM, "server_create: the frontier pool needs %zu bytes, budget %zu",
                        S->engine->fixed_bytes(), S->budget);
+    if (rc == BBS_OK) rc = S->engine->set_exit_on_finish(true);
     if (rc == BBS_OK && cudaStreamSynchronize(S->st) != cudaSuccess) rc = set_error(BBS_ECUDA, "server_create: init");
     if (rc < 0) {
         delete S->engine;
@@ -279,6 +287,7 @@ int bbs_server_submit(bbs_server* S, const bbs_maps* maps, const float* scan_xyz
         return BBS_OK;
     }
     S->queue.push_back(std::move(q));
+    *S->engine->wake_flag() = 1;   // a running device loop ends after its current iteration
     S->cv_work.notify_one();
     return BBS_OK;
 }
@@ -330,6 +339,7 @@ int bbs_server_cancel(bbs_server* S, uint64_t ticket)
         }
     if (S->running.count(ticket)) {
         S->cancels.insert(ticket);
+        *S->engine->wake_flag() = 1;   // the device loop returns so that the cancel takes effect
         S->cv_work.notify_one();
         return BBS_OK;
     }

@@ -59,6 +59,7 @@ class Result(C.Structure):
         ("ms_to_optimum", C.c_double), ("ms_total", C.c_double), ("phase_ms", C.c_double * 5),
         ("gathers", C.c_int64), ("launches", C.c_int64), ("score_launches", C.c_int64), ("score_ms", C.c_double),
         ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64),
+        ("children_scored", C.c_int64), ("bound_violations", C.c_int64), ("bound_excess", C.c_double),
     ]
 
     def as_dict(self) -> dict:
@@ -70,6 +71,8 @@ class Result(C.Structure):
             "ms_to_optimum": self.ms_to_optimum, "ms_total": self.ms_total, "phase_ms": list(self.phase_ms),
             "gathers": self.gathers, "launches": self.launches, "score_launches": self.score_launches,
             "score_ms": self.score_ms, "h2d_bytes": self.h2d_bytes, "d2h_bytes": self.d2h_bytes,
+            "children_scored": self.children_scored, "bound_violations": self.bound_violations,
+            "bound_excess": self.bound_excess,
         }
 
 
@@ -92,11 +95,11 @@ class GicpResult(C.Structure):
 class Tuning(C.Structure):
     """bbs_tuning: launch shape of the search (0 = default)."""
     _fields_ = [("launch_tasks", C.c_int64), ("static_pm", C.c_int32), ("grab_min", C.c_int32),
-                ("ctas_per_sm", C.c_int32), ("reserved", C.c_int32)]
+                ("ctas_per_sm", C.c_int32), ("frontier_log2", C.c_int32)]
 
     def as_dict(self):
         return {"launch_tasks": self.launch_tasks, "static_pm": self.static_pm, "grab_min": self.grab_min,
-                "ctas_per_sm": self.ctas_per_sm}
+                "ctas_per_sm": self.ctas_per_sm, "frontier_log2": self.frontier_log2}
 
 
 class ServerOpts(C.Structure):
@@ -159,6 +162,7 @@ def load():
         L.bbs_localize_hostqueue.argtypes = [vp, vp, i64, C.c_int, vp, vp, vp]
         L.bbs_exact_dilation.argtypes = [vp, vp, i64, C.c_int, vp, vp, i32p]
         L.bbs_get_tuning.argtypes = [C.c_void_p]
+        L.bbs_launch_log.argtypes = [vp, vp, i64, i64p]
         L.bbs_server_create.argtypes = [P(ServerOpts), P(C.c_void_p)]
         L.bbs_server_submit.argtypes = [vp, vp, vp, i64, P(Ranges), P(Opts), P(C.c_uint64)]
         L.bbs_server_poll.argtypes = [vp, C.c_uint64, C.c_int, P(Result)]
@@ -612,13 +616,28 @@ def bbs_exact_dilation(maps: Maps, scan, ranges=None, opts=None) -> int:
 
 
 def bbs_set_tuning(launch_tasks: int = 0, static_pm: int = 0, grab_min: int = 0, ctas_per_sm: int = 0,
-                   reset: bool = False) -> None:
+                   frontier_log2: int = 0, reset: bool = False) -> None:
     """Launch shape of later searches (0 = default); reset=True restores every default."""
     if reset:
         _check(load().bbs_set_tuning(None))
         return
-    t = Tuning(int(launch_tasks), int(static_pm), int(grab_min), int(ctas_per_sm), 0)
+    t = Tuning(int(launch_tasks), int(static_pm), int(grab_min), int(ctas_per_sm), int(frontier_log2))
     _check(load().bbs_set_tuning(C.byref(t)))
+
+
+def bbs_launch_log():
+    """(units, ms) of each scoring launch of the last BBS_TIME_KERNELS search
+    call on this thread: numpy arrays (rotational children x scan points per
+    launch, device milliseconds)."""
+    n = C.c_int64()
+    rc = load().bbs_launch_log(None, None, 0, C.byref(n))
+    units = np.zeros(max(n.value, 1), np.int64)
+    ms = np.zeros(max(n.value, 1), np.float64)
+    if n.value:
+        _check(load().bbs_launch_log(C.c_void_p(units.ctypes.data), C.c_void_p(ms.ctypes.data), n.value, C.byref(n)))
+    else:
+        _check(rc)
+    return units[:n.value], ms[:n.value]
 
 
 def bbs_get_tuning() -> dict:

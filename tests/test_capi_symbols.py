@@ -45,7 +45,8 @@ def test_tuning_validation_without_gpu():
             nv.bbs_set_tuning(**bad)
         assert e.value.code == nv.EINVAL
     nv.bbs_set_tuning(launch_tasks=100, static_pm=500)
-    assert nv.bbs_get_tuning() == {"launch_tasks": 100, "static_pm": 500, "grab_min": 16, "ctas_per_sm": 4}
+    assert nv.bbs_get_tuning() == {"launch_tasks": 100, "static_pm": 500, "grab_min": 16, "ctas_per_sm": 4,
+                                   "frontier_log2": 0}
     nv.bbs_set_tuning(reset=True)
     assert nv.bbs_get_tuning()["launch_tasks"] == 1 << 19
 

@@ -1,5 +1,6 @@
 """The integer and floating-point identities the scoring kernel relies on,
-checked on the CPU: the byte-counter spreads (exhaustive), the bit pattern of
+checked on the CPU: the 4-bit child counters and the brick planes' child
+masks, the bit pattern of
 a floored level key, the folded index constant of clamp-free runs, and the
 FP32 bound of the per-run inside test (emulated with FP32 arithmetic, the
 tightest point placed on the bound)."""
@@ -12,29 +13,52 @@ import numpy as np
 KB = 0x4B400000   # bit pattern of 1.5 * 2^23
 
 
-def test_nibble_spread_is_carry_free():
-    """((v & 0xF) * 0x204081) & 0x01010101 puts bit i of the nibble in byte i,
-    and the product is a sum of distinct powers of two (no carry can reach a
-    counter), for every byte and both nibbles."""
-    for v in range(256):
-        for nib in (v & 0xF, v >> 4):
-            prod = nib * 0x204081
-            assert bin(prod).count("1") == 4 * bin(nib).count("1")
-            spread = prod & 0x01010101
-            assert spread == sum(((nib >> i) & 1) << (8 * i) for i in range(4))
+def _lut_entry(v):
+    # the scoring kernel's child counter increment (child_lut_entry): child
+    # i = jx + 2 jy + 4 jz of the 8-bit mask v at bit 4 (jx + 2 jz) + 16 jy
+    out = 0
+    for i in range(8):
+        jx, jy, jz = i & 1, (i >> 1) & 1, i >> 2
+        out |= ((v >> i) & 1) << (4 * (jx + 2 * jz) + 16 * jy)
+    return out
 
 
-def test_plane_spread_reaches_counters_exactly():
-    """((w & 0x63) * 0x40881) & 0x01010101 puts bits 0, 1, 5, 6 of a brick
-    plane (children jx + 5 jy) in bytes 0..3.  Partial products of bits 1 and
-    5 meet at bit 12, but the carry chain ends by bit 14, below the counter
-    bit of byte 2, so the masked result is exact for every plane."""
-    for w in range(1 << 7):
-        m = w & 0x63
-        prod = m * 0x40881
-        want = sum(((w >> b) & 1) << (8 * i) for i, b in enumerate((0, 1, 5, 6)))
-        assert prod & 0x01010101 == want
-        assert prod < 1 << 25
+def test_child_counter_words():
+    """Summing the counter increments of up to 8 points (one run of one
+    thread) never carries between 4-bit counters, and (acc >> 4 k) &
+    0x000F000F gives the counts of children (jx, jz) = (k & 1, k >> 1) with
+    jy = 0 in the low and jy = 1 in the high 16-bit half, for every mix of
+    masks (random mixes, and the all-ones worst case)."""
+    rng = np.random.default_rng(1)
+    for trial in range(3000):
+        n = int(rng.integers(1, 9))
+        vs = [255] * 8 if trial == 0 else [int(x) for x in rng.integers(0, 256, n)]
+        acc = sum(_lut_entry(v) for v in vs)
+        assert acc < 1 << 32
+        for k in range(4):
+            jx, jz = k & 1, k >> 1
+            word = (acc >> (4 * k)) & 0x000F000F
+            for jy in (0, 1):
+                i = jx + 2 * jy + 4 * jz
+                assert (word >> (16 * jy)) & 0xFFFF == sum((v >> i) & 1 for v in vs)
+
+
+def test_plane_mask_takes_the_children_bits():
+    """The brick layouts' plane words hold children jx + 5 jy of the z = 0 and
+    z = 1 planes at bits {0, 1, 5, 6}; their 8-bit child mask has child
+    jx + 2 jy + 4 jz at bit jx + 2 jy + 4 jz, for every pair of planes
+    (other bits of the words ignored)."""
+    def planes_mask(w0, w1):
+        return (w0 & 3) | ((w0 >> 3) & 0xC) | ((w1 & 3) << 4) | ((w1 << 1) & 0xC0)
+    rng = np.random.default_rng(2)
+    for _ in range(20000):
+        w0, w1 = (int(x) for x in rng.integers(0, 1 << 32, 2, dtype=np.uint64))
+        want = 0
+        for i in range(8):
+            jx, jy, jz = i & 1, (i >> 1) & 1, i >> 2
+            w = w1 if jz else w0
+            want |= ((w >> (jx + 5 * jy)) & 1) << i
+        assert planes_mask(w0, w1) == want
 
 
 def test_floored_key_bit_pattern():
