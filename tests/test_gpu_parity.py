@@ -32,6 +32,11 @@ def _keyset(a):
     return set(map(tuple, np.asarray(a).reshape(-1, 3).tolist()))
 
 
+def _sorted_keys(a):
+    a = np.asarray(a, np.int64).reshape(-1, 3)
+    return a[np.lexsort((a[:, 2], a[:, 1], a[:, 0]))]
+
+
 @pytest.fixture(scope="module")
 def room_pair(nv):
     w = synth.WORKLOADS["room"]
@@ -49,8 +54,8 @@ def _ranges(nv, w, lo=None, hi=None, alo=None, ahi=None):
 
 def test_room_map_levels_equal_oracle(nv, room_pair):
     w, m, dm, om = room_pair
-    for l in range(w.levels):
-        assert _keyset(nv.bbs_maps_keys(dm, l)) == _keyset(om.keys(l)), l
+    for l in range(w.levels):   # every level's full key set
+        assert np.array_equal(_sorted_keys(nv.bbs_maps_keys(dm, l)), _sorted_keys(om.keys(l))), l
         info = nv.bbs_maps_info(dm, l)
         assert info["voxels"] == om.count(l)
         assert info["buckets"] * 2 <= info["table_size"] * 1.0 + 1024
@@ -265,6 +270,11 @@ def _same_search(res, ores):
         assert np.allclose(list(res.pose), list(ores.pose), rtol=0, atol=1e-12)
     assert res.iterations == ores.iterations
     assert res.nodes_scored == ores.nodes_scored
+    # Sec. IV-A's bound check along the same trajectory: the same children,
+    # the same violations; the excess sums differ only in summation order
+    assert res.children_scored == ores.children_scored
+    assert res.bound_violations == ores.bound_violations
+    assert math.isclose(res.bound_excess, ores.bound_excess, rel_tol=1e-9, abs_tol=1e-12)
 
 
 @pytest.mark.parametrize("batch", [1, 500, 10000, 100000])
@@ -437,6 +447,82 @@ def test_localize_many_with_oracle(nv, room_pair):
         _same_search(r, oracle.localize(om, s, orr, score_frac=w.score_frac, batch=w.batch))
 
 
+def test_localize_many_uneven_indoor_scans_with_oracle(nv, indoor_pair):
+    """The batched form on its own workload: 64 indoor scans of 2 k-30 k
+    points (log-uniform, the benchmark's set) in one bbs_localize_many call.
+    Four of them (the smallest, which the oracle finishes in seconds) against
+    the CPU oracle's searches, run side by side on the host's cores; every
+    result equals the scan localized alone on the GPU."""
+    import oracle_pool
+    w, m, dm, om = indoor_pair
+    nr, orr = _ranges(nv, w)
+    ks = synth.loguniform_sizes(4, 64, 2000, 30000)
+    scans = [synth.make_scan(w.scene, 500 + i, k=int(k))[0] for i, k in enumerate(ks)]
+    op = nv.make_opts(score_frac=w.score_frac, batch=w.batch)
+    many = nv.bbs_localize_many(dm, [torch.from_numpy(s).cuda() for s in scans], nr, op)
+    for s, r in zip(scans, many):
+        a = nv.bbs_localize(dm, s, nr, op)
+        assert (r.status, r.best_score, list(r.node), r.iterations, r.nodes_scored) == \
+               (a.status, a.best_score, list(a.node), a.iterations, a.nodes_scored)
+    pick = sorted(range(len(scans)), key=lambda i: len(scans[i]))[:4]
+    jobs = [("indoor", scans[i], (w.lo, w.hi, w.ang_lo, w.ang_hi), w.score_frac, w.batch, 0, 0) for i in pick]
+    for i, o in zip(pick, oracle_pool.localize_many(jobs)):
+        r = many[i]
+        assert (r.status, r.best_score, list(r.node), r.iterations, r.nodes_scored, r.children_scored,
+                r.bound_violations) == (o["status"], o["best_score"], o["node"], o["iterations"], o["nodes_scored"],
+                                        o["children_scored"], o["bound_violations"]), (i, len(scans[i]))
+
+
+def test_frontier_grows_as_the_search_needs(nv, room_pair):
+    """The frontier arrays start at 2^10 nodes and double when a round's
+    survivors might not fit (the round waits while the host grows them):
+    the searches are the ones run with the default capacity, in the graph loop,
+    the host-driven loop and a multi-scan call; a cap below the search's need
+    still fails with BBS_ENOMEM."""
+    w, m, dm, om = room_pair
+    nr, _ = _ranges(nv, w)
+    scans = [synth.make_scan(w.scene, i)[0] for i in (0, 5)]
+
+    def key(r):
+        return (r.status, r.best_score, list(r.node), r.iterations, r.nodes_scored, r.peak_frontier,
+                r.children_scored, r.bound_violations)
+
+    op = nv.make_opts(score_frac=w.score_frac, batch=w.batch)
+    base = [nv.bbs_localize(dm, s, nr, op) for s in scans]
+    assert max(r.peak_frontier for r in base) > 4 << 10
+    try:
+        nv.bbs_set_tuning(frontier_log2=10)
+        for flags in (0, nv.HOST_DRIVEN):
+            o = nv.make_opts(score_frac=w.score_frac, batch=w.batch, flags=flags)
+            for s, b in zip(scans, base):
+                assert key(nv.bbs_localize(dm, s, nr, o)) == key(b), flags
+        many = nv.bbs_localize_many(dm, scans, nr, op)
+        for r, b in zip(many, base):
+            assert (r.status, r.best_score, list(r.node), r.iterations, r.nodes_scored) == \
+                   (b.status, b.best_score, list(b.node), b.iterations, b.nodes_scored)
+        with pytest.raises(nv.BBSError) as e:
+            nv.bbs_localize(dm, scans[0], nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch,
+                                                           max_frontier=2048))
+        assert e.value.code == nv.ENOMEM
+    finally:
+        nv.bbs_set_tuning(reset=True)
+
+
+def test_launch_log_matches_the_timed_result(nv, room_pair):
+    """bbs_launch_log lists the timed call's scoring launches: as many as the
+    result reports, their units summing to its gathers (tasks x scan points)
+    and their milliseconds to its scoring time."""
+    w, m, dm, om = room_pair
+    nr, _ = _ranges(nv, w)
+    s, _ = synth.make_scan(w.scene, 1)
+    r = nv.bbs_localize(dm, s, nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch, flags=nv.TIME_KERNELS))
+    units, ms = nv.bbs_launch_log()
+    assert len(units) == r.score_launches > 1
+    assert int(units.sum()) == r.gathers
+    assert math.isclose(float(ms.sum()), r.score_ms, rel_tol=1e-5)
+    assert (units > 0).all() and (ms > 0).all()
+
+
 def test_localize_many_empty_and_not_found(nv, room_pair):
     w, m, dm, om = room_pair
     nr, _ = _ranges(nv, w)
@@ -492,8 +578,8 @@ def test_indoor_maps_and_scores_bit_exact(nv, indoor_pair):
     w, m, dm, om = indoor_pair
     for l in range(w.levels):
         assert nv.bbs_maps_info(dm, l)["voxels"] == om.count(l)
-    for l in (w.levels - 1, 2):
-        assert _keyset(nv.bbs_maps_keys(dm, l)) == _keyset(om.keys(l))
+    for l in range(w.levels):
+        assert _keyset(nv.bbs_maps_keys(dm, l)) == _keyset(om.keys(l)), l
     s, _ = synth.make_scan(2, 0)
     nr, orr = _ranges(nv, w)
     g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), orr)
@@ -514,18 +600,41 @@ def test_indoor_localize_equals_oracle(nv, indoor_pair):
     ores = oracle.localize(om, s, orr, score_frac=w.score_frac, batch=w.batch)
     _same_search(res, ores)
     assert res.status == nv.OK
-    for i in range(3):
-        assert abs(res.pose[i] - pose[i]) <= w.r + 0.1
+    from planted import check_planted
+    g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), orr)
+    steps = check_planted(w.r, g, om, s, pose, list(res.node), res.best_score, list(res.pose))
+    assert max(steps) <= 1.0   # this scan resolves every angle to one step
 
 
-def test_outdoor_sampled_parity_and_planted_pose(nv):
+@pytest.fixture(scope="module")
+def outdoor_pair(nv):
+    w = synth.WORKLOADS["outdoor"]
+    m = synth.make_map(w.scene)
+    return w, m, nv.bbs_build_maps(torch.from_numpy(np.array(m)).cuda(), w.r, w.levels), oracle.Maps(m, w.r, w.levels)
+
+
+def test_outdoor_search_equals_oracle(nv, outdoor_pair):
+    """The outdoor workload's own search (800 x 800 x 40 m city, 40 M map
+    points, r = 1 m, 8 levels, the 400 x 400 x 10 m window, full yaw) with
+    the scan thinned to every 10th of its 20 k points (the oracle's search of
+    the whole scan takes minutes on one core): the GPU follows the oracle's
+    trajectory exactly -- best score, match, iterations, nodes scored and the
+    bound check."""
+    w, m, dm, om = outdoor_pair
+    s, pose = synth.make_scan(3, 2)
+    s = np.ascontiguousarray(s[::10])
+    nr, orr = _ranges(nv, w)
+    res = nv.bbs_localize(dm, torch.from_numpy(s).cuda(), nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch))
+    ores = oracle.localize(om, s, orr, score_frac=w.score_frac, batch=w.batch)
+    _same_search(res, ores)
+    assert res.status == nv.OK and res.best_score >= math.ceil(w.score_frac * len(s))
+
+
+def test_outdoor_sampled_parity_and_planted_pose(nv, outdoor_pair):
     """800 x 800 x 40 m city, 40 M map points, 20 k-point scan: sampled scores
     bit-exact, the returned leaf's oracle score equals the reported best, and
     the planted pose is recovered."""
-    w = synth.WORKLOADS["outdoor"]
-    m = synth.make_map(w.scene)
-    dm = nv.bbs_build_maps(torch.from_numpy(np.array(m)).cuda(), w.r, w.levels)
-    om = oracle.Maps(m, w.r, w.levels)
+    w, m, dm, om = outdoor_pair
     s, pose = synth.make_scan(3, 2)
     nr, orr = _ranges(nv, w)
     g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), orr)
@@ -534,10 +643,8 @@ def test_outdoor_sampled_parity_and_planted_pose(nv):
     res = nv.bbs_localize(dm, torch.from_numpy(s).cuda(), nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch))
     assert res.status == nv.OK
     assert om.score_nodes(g, s, [list(res.node)])[0] == res.best_score
-    for i in range(3):
-        assert abs(res.pose[i] - pose[i]) <= w.r + 0.1
-    dyaw = (res.pose[5] - pose[5] + math.pi) % (2 * math.pi) - math.pi
-    assert abs(dyaw) <= 2 * g.dprime(0)[2]
+    from planted import check_planted
+    check_planted(w.r, g, om, s, pose, list(res.node), res.best_score, list(res.pose))
 
 
 # ---- the device-driven iteration loop --------------------------------------------
@@ -596,7 +703,8 @@ def test_launch_shape_does_not_change_results(nv, room_pair, indoor_pair):
                 assert [key(r) for r in nv.bbs_localize_many(dm, scans, nr, o)] == base_many, (shape, flags)
     finally:
         nv.bbs_set_tuning(reset=True)
-    assert nv.bbs_get_tuning() == {"launch_tasks": 1 << 19, "static_pm": 750, "grab_min": 16, "ctas_per_sm": 4}
+    assert nv.bbs_get_tuning() == {"launch_tasks": 1 << 19, "static_pm": 750, "grab_min": 16, "ctas_per_sm": 4,
+                                   "frontier_log2": 0}
 
 
 # ---- exact-bound mode --------------------------------------------------------
@@ -645,16 +753,23 @@ def test_exact_bound_maps_and_search_equal_oracle(nv, leaf):
 
 def test_host_queue_equals_device_frontier(nv, room_pair, indoor_pair):
     """The host-queue search (per-batch copies, host buckets) follows the same
-    canonical iteration as the device-resident engine: identical results and
-    counts, also when rounds are split into small launches."""
+    canonical iteration as the CPU oracle (room scans) and the device-resident
+    engine: identical results and counts, also when rounds are split into
+    small launches."""
     def key(r):
-        return (r.status, r.best_score, list(r.node), r.iterations, r.nodes_scored, r.peak_frontier)
+        return (r.status, r.best_score, list(r.node), r.iterations, r.nodes_scored, r.peak_frontier,
+                r.children_scored, r.bound_violations)
 
     cases = []
     w, m, dm, om = room_pair
-    nr, _ = _ranges(nv, w)
+    nr, orr = _ranges(nv, w)
     for i in (0, 3):
-        cases.append((dm, synth.make_scan(w.scene, i)[0], nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch)))
+        s = synth.make_scan(w.scene, i)[0]
+        cases.append((dm, s, nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch)))
+        ores = oracle.localize(om, s, orr, score_frac=w.score_frac, batch=w.batch)
+        res = nv.bbs_localize_hostqueue(dm, s, nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch))
+        _same_search(res, ores)
+        assert res.peak_frontier == ores.peak_frontier
     w, m, dm, om = indoor_pair
     nr, _ = _ranges(nv, w)
     cases.append((dm, synth.make_scan(w.scene, 2)[0], nr, nv.make_opts(score_frac=w.score_frac, batch=w.batch)))

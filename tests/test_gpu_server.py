@@ -1,6 +1,7 @@
 """The continuous-batching server: requests against two resident maps arrive
 while others run, share launches, and each result equals the same request
-localized alone; admission follows the device-memory budget."""
+localized alone and the CPU oracle's search of it; admission follows the
+device-memory budget."""
 import time
 
 import numpy as np
@@ -73,6 +74,21 @@ def test_served_results_equal_alone(nv, two_maps):
         w, dm = two_maps[name]
         alone = nv.bbs_localize(dm, s, rg, nv.make_opts(score_frac=w.score_frac, batch=w.batch))
         assert _same(results[t], alone), name
+    # and the CPU oracle's search of the same request: every room request and
+    # the two smallest indoor ones (the oracle takes tens of seconds per
+    # larger indoor scan), run side by side on the host's cores
+    import oracle_pool
+    indoor = sorted((len(s), i) for i, (name, s, _, _, _) in enumerate(reqs) if name == "indoor")[:2]
+    pick = [i for i, r in enumerate(reqs) if r[0] == "room"] + [i for _, i in indoor]
+    jobs = []
+    for i in pick:
+        name, s, _, _, _ = reqs[i]
+        w = synth.WORKLOADS[name]
+        jobs.append((name, s, (w.lo, w.hi, w.ang_lo, w.ang_hi), w.score_frac, w.batch, 0, 0))
+    for i, o in zip(pick, oracle_pool.localize_many(jobs)):
+        r = results[reqs[i][4]]
+        assert (r.status, r.best_score, list(r.node), r.iterations, r.nodes_scored, r.bound_violations) == \
+               (o["status"], o["best_score"], o["node"], o["iterations"], o["nodes_scored"], o["bound_violations"]), i
 
 
 def test_budget_admission_and_rejection(nv, two_maps):
