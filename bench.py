@@ -172,9 +172,61 @@ def _oracle_sample(w, m, scan, n_nodes, seed, om=None):
     return om, g, np.array(nodes, np.int32)
 
 
-def cpu_probe_rate(w, m, scan, target_s=12.0):
+def _cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or None."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def cpu_legs(w, m, scans, n_poses=5):
+    """The CPU oracle on the same workload: its map build, its Eq. (11)
+    scoring rate on one thread (a bounded random node sample), and its whole
+    BnB per planted pose for n_poses scans on all host cores (the OpenMP
+    build: Table I's CPU multi-thread configuration (h); the same searches as
+    the single-threaded oracle, pinned)."""
+    import oracle
+    t = time.perf_counter()
+    om = oracle.Maps(m, w.r, w.levels)
+    build_s = time.perf_counter() - t
+    rate, n, dt = cpu_probe_rate(w, m, scans[0], om=om)
+    out = {"value": rate, "unit": "probes/s", "cores": 1, "kind": "oracle",
+           "sample": f"{n} random nodes over all levels x {len(scans[0])}-point scan, Eq. (11) scoring "
+                     f"({dt:.1f} s, single-threaded C oracle on the host)",
+           "nproc": os.cpu_count(), "cpu_model": _cpu_model(), "map_build_ms": build_s * 1e3}
+    try:
+        threads = oracle.threads(os.cpu_count() or 1)
+    except ImportError as ex:
+        out["bnb_per_pose"] = {"unavailable": str(ex)}
+        return out
+    rg = oracle.make_ranges(w.lo, w.hi, w.ang_lo, w.ang_hi)
+    ms, probes, found = [], 0, 0
+    for s_ in scans[:n_poses]:
+        t = time.perf_counter()
+        r = oracle.localize(om, s_, rg, score_frac=w.score_frac, batch=w.batch, mt=True)
+        ms.append((time.perf_counter() - t) * 1e3)
+        probes += r.probes
+        found += r.status == oracle.OK
+    out["bnb_per_pose"] = {"kind": "oracle, OpenMP build (Table I configuration (h))", "threads": threads,
+                           "poses": len(ms), "ms_per_scan": statistics.mean(ms), "ms_per_scan_each": ms,
+                           "probes_per_s": probes / (sum(ms) / 1e3), "found": f"{found}/{len(ms)}"}
+    return out
+
+
+def cpu_probe_rate(w, m, scan, target_s=12.0, om=None):
     """Oracle Eq. (11) scoring throughput (probes/s) on one host thread."""
-    om, g, nodes = _oracle_sample(w, m, scan, 200, 1)
+    om, g, nodes = _oracle_sample(w, m, scan, 200, 1, om)
     t = time.perf_counter()
     om.score_nodes(g, scan, nodes)
     dt = time.perf_counter() - t
@@ -187,38 +239,63 @@ def cpu_probe_rate(w, m, scan, target_s=12.0):
 
 
 def run_reference(a):
+    """The reference arm: the CPU oracle on the same workload as the GPU arm.
+    Each step is one whole BnB (Algorithm 2's canonical iteration) of the
+    next of the same --scans planted-pose scans, run by the oracle's OpenMP
+    build on every host core (Table I's CPU multi-thread configuration (h);
+    the same search as the single-threaded oracle, pinned); probes/s over the
+    timed steps.  Without OpenMP it falls back to the single-threaded oracle
+    scoring a bounded random node sample per step."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    import numpy as np
+    import oracle
 
     from paper_2310_10023_gb300 import synth
     w = synth.WORKLOADS[a.workload]
     m = synth.make_map(w.scene)
-    scan, _ = synth.make_scan(w.scene, 0)
-    om, g, nodes = _oracle_sample(w, m, scan, 1000, 7)
-    t = time.perf_counter()
-    om.score_nodes(g, scan, nodes[:100])
-    per_node = (time.perf_counter() - t) / 100
-    n = max(50, int(2.0 / max(per_node, 1e-9)))        # ~2 s of oracle work per step
-    om, g, nodes = _oracle_sample(w, m, scan, n, 7, om)
-    for _ in range(a.warmup):
-        om.score_nodes(g, scan, nodes[: max(1, n // 10)])
-    times = []
-    for _ in range(a.steps):
+    scans = [synth.make_scan(w.scene, i)[0] for i in rank_scans(0, a.scans)]
+    om = oracle.Maps(m, w.r, w.levels)
+    rg = oracle.make_ranges(w.lo, w.hi, w.ang_lo, w.ang_hi)
+    try:
+        threads = oracle.threads(os.cpu_count() or 1)
+        mt = True
+    except ImportError:
+        threads, mt = 1, False
+    times, probes = [], 0
+    if mt:
+        for i in range(a.warmup + a.steps):
+            t = time.perf_counter()
+            r = oracle.localize(om, scans[i % a.scans], rg, score_frac=w.score_frac, batch=w.batch, mt=True)
+            dt = time.perf_counter() - t
+            if i >= a.warmup:
+                times.append(dt)
+                probes += r.probes
+        sample = (f"whole BnB of each step's scan ({a.scans} planted-pose scans cycled, the GPU arm's), "
+                  f"OpenMP build of the C oracle on {threads} threads")
+    else:
+        _, g, nodes = _oracle_sample(w, m, scans[0], 1000, 7, om)
         t = time.perf_counter()
-        om.score_nodes(g, scan, nodes)
-        times.append(time.perf_counter() - t)
+        om.score_nodes(g, scans[0], nodes[:100])
+        per_node = (time.perf_counter() - t) / 100
+        n = max(50, int(2.0 / max(per_node, 1e-9)))        # ~2 s of oracle work per step
+        _, g, nodes = _oracle_sample(w, m, scans[0], n, 7, om)
+        for i in range(a.warmup + a.steps):
+            t = time.perf_counter()
+            om.score_nodes(g, scans[0], nodes)
+            if i >= a.warmup:
+                times.append(time.perf_counter() - t)
+                probes += n * len(scans[0])
+        sample = (f"{n} random nodes over all levels x {len(scans[0])}-point scan per step "
+                  "(Eq. (11) scoring, single-threaded C oracle; no OpenMP build)")
     total = sum(times)
-    probes = n * len(scan) * a.steps
     v = probes / total
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "probes/s", "n_gpus": ws, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": total / a.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": _workload_desc(w, len(m), len(scan), 1),
-            "cpu_baseline": {"value": v, "unit": "probes/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{n} random nodes over all levels x {len(scan)}-point scan per step "
-                                       "(Eq. (11) scoring, single-threaded C oracle)"},
+            "config": _workload_desc(w, len(m), statistics.mean(len(s_) for s_ in scans), a.scans),
+            "cpu_baseline": {"value": v, "unit": "probes/s", "cores": threads, "kind": "oracle", "sample": sample,
+                             "cpu_model": _cpu_model(), "nproc": os.cpu_count()},
             "e2e": {"value": v, "unit": "probes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -288,8 +365,27 @@ def run_exact(nv, torch, stream, n_scans=4):
         out[name] = {"ms_per_scan": e0.elapsed_time(e1) / len(scans_d),
                      "nodes_scored_mean": statistics.mean(r.nodes_scored for r in res),
                      "best_scores": [r.best_score for r in res]}
+        if name == "approximate":
+            out["bound_check"] = _bound_check([r.as_dict() for r in res])
     out["same_best_score"] = f"{sum(x == y for x, y in zip(out['approximate']['best_scores'], out['exact']['best_scores']))}/{len(scans_d)}"
+    # the exact-bound BnB returns the exhaustive optimum (pinned against brute
+    # force), so its best score measures the approximate bound's gap
+    gaps = [(e - a) / e for a, e in zip(out["approximate"]["best_scores"], out["exact"]["best_scores"]) if e > 0]
+    out["gap_to_exhaustive_optimum"] = {"mean": statistics.mean(gaps) if gaps else None,
+                                        "scans_short": sum(g > 0 for g in gaps), "scans": len(gaps)}
     return out
+
+
+def _bound_check(results):
+    """Sec. IV-A's check of the approximate rotational bound over a set of
+    searches: children scored while branching, the fraction scoring above
+    their parent, and their mean excess (child - parent) / child."""
+    c = sum(r["children_scored"] for r in results)
+    v = sum(r["bound_violations"] for r in results)
+    x = sum(r["bound_excess"] for r in results)
+    return {"children_scored": c, "violations": v, "rate": v / c if c else None,
+            "mean_excess": x / v if v else None,
+            "paper": "0.001 % of cases, about 1.5 % average error (Sec. IV-A)"}
 
 
 def run_host_queue(nv, torch, maps, w, scans_d, stream):
@@ -381,9 +477,10 @@ def _form(fn, *args):
         return {"error": f"{type(ex).__name__}: {ex}"}
 
 
-def run_outdoor(nv, torch, stream, n_scans=4, reps=2):
+def run_outdoor(nv, torch, stream, nsm=152, gather_gbs=None, n_scans=4, reps=2):
     """The outdoor workload (800 x 800 x 40 m city, 40 M map points, r = 1 m,
-    8 levels, 20 k-point scans): plain probes/s and ms per scan."""
+    8 levels, 20 k-point scans): plain probes/s and ms per scan, and the
+    scoring kernel's roofline from a kernel-timed pass over the same scans."""
     from paper_2310_10023_gb300 import synth
     w = synth.WORKLOADS["outdoor"]
     m = synth.make_map(w.scene)
@@ -408,28 +505,42 @@ def run_outdoor(nv, torch, stream, n_scans=4, reps=2):
     e1.synchronize()
     ms = e0.elapsed_time(e1)
     probes = sum(r.probes for r in res)
-    return {"workload": f"outdoor city 800x800x40 m, {len(m) / 1e6:.1f} M map points, r={w.r} m, {w.levels} levels; "
+    at = nv.workload_args(w, stream=stream.cuda_stream, flags=nv.TIME_KERNELS)
+    with Clocks(torch.cuda.current_device()) as clk:
+        kres = [nv.bbs_localize(maps, s_, at.ranges, at.opts) for s_ in scans for _ in range(reps)]
+    kms = sum(r.score_ms for r in kres)
+    kc = clk.summary() or {}
+    roof = _roofline(sum(r.gathers for r in kres) / (kms / 1e3) if kms > 0 else 0.0, kms,
+                     sum(r.score_launches for r in kres), kc.get("sm_mhz") or 2070.0, nsm, "outdoor", gather_gbs)
+    return {"roofline": roof,
+            "workload": f"outdoor city 800x800x40 m, {len(m) / 1e6:.1f} M map points, r={w.r} m, {w.levels} levels; "
                         f"{n_scans} scans of ~{statistics.mean(len(s_) for s_ in scans):.0f} points",
             "probes_per_s": probes / (ms / 1e3), "ms_per_scan": ms / len(res),
             "ms_to_optimum_mean": statistics.mean(r.ms_to_optimum for r in res),
             "found": f"{sum(r.status == nv.OK for r in res)}/{len(res)}", "map_build_ms": build_ms}
 
 
-def run_served(nv, torch, lam=200.0, n=64, seed=9):
-    """Poisson arrivals (rate lam) of requests with 2k-30k-point scans against
-    two resident maps (room and indoor), served by the continuous-batching
-    server, vs one-at-a-time plain BnB on the same arrival trace (FIFO)."""
+def _served_maps(nv, torch):
     from paper_2310_10023_gb300 import synth
     maps = {}
     for name in ("room", "indoor"):
         w = synth.WORKLOADS[name]
         maps[name] = (w, nv.bbs_build_maps(torch.from_numpy(np.array(synth.make_map(w.scene))).cuda(), w.r, w.levels))
+    return maps
+
+
+def run_served(nv, torch, maps, lam=200.0, n=64, seed=9, max_active=4):
+    """Poisson arrivals (rate lam) of requests with 2k-30k-point scans against
+    two resident maps (room and indoor), served by the continuous-batching
+    server, vs one-at-a-time plain BnB on the same arrival trace (FIFO: each
+    request's service time measured alone, queued in arrival order)."""
+    from paper_2310_10023_gb300 import synth
     arr, ks = synth.poisson_trace(seed, lam, n, 2000, 30000)
     reqs = []
     for i in range(n):
         name = "room" if i % 2 == 0 else "indoor"
         w, dm = maps[name]
-        s = synth.make_scan(w.scene, 900 + i, k=int(ks[i]))[0]
+        s = synth.make_scan(w.scene, 900 + 100 * seed + i, k=int(ks[i]))[0]
         a = nv.workload_args(w, stream=0)
         reqs.append((dm, s, a.ranges, a.opts))
     # one-at-a-time service times (device synchronized per request)
@@ -446,7 +557,7 @@ def run_served(nv, torch, lam=200.0, n=64, seed=9):
         start = max(t_arr, free_at)
         free_at = start + d
         fifo.append(free_at - t_arr)
-    srv = nv.bbs_server_create(max_active=32)
+    srv = nv.bbs_server_create(max_active=max_active)
     tickets = []
     t0 = time.perf_counter()
     for (dm, s, rg, op), t_arr in zip(reqs, arr):
@@ -458,13 +569,27 @@ def run_served(nv, torch, lam=200.0, n=64, seed=9):
     srv.close()
     q = sorted(fifo)
     pct = lambda v, p: v[min(len(v) - 1, int(round(p * (len(v) - 1))))]
-    return {"workload": f"{n} requests, Poisson {lam:.0f}/s, K log-uniform 2k-30k, maps room + indoor resident",
-            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "throughput_rps": st["throughput_rps"],
-            "probes_per_s": st["probes_per_s"], "peak_active": st["peak_active"],
-            "found": sum(o[0] == nv.OK for o in out),
+    return {"rate_rps": lam, "requests": n, "max_active": max_active, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "throughput_rps": st["throughput_rps"], "probes_per_s": st["probes_per_s"],
+            "peak_active": st["peak_active"], "found": sum(o[0] == nv.OK for o in out),
             "plain_fifo_p50_ms": pct(q, 0.5), "plain_fifo_p99_ms": pct(q, 0.99),
             "plain_throughput_rps": n / (max(free_at, arr[-1] * 1e3) / 1e3),
             "plain_mean_service_ms": statistics.mean(svc)}
+
+
+def run_served_sweep(nv, torch, rates=(20, 50, 100, 200, 500, 1000), n=64, max_active=4):
+    """The served form over arrival rates from light load to overload (one
+    seeded trace per rate), each against one-at-a-time FIFO on its trace.
+    At most max_active requests share the device loop: each shared launch
+    lengthens every member's iterations, and beyond a few members the
+    throughput gained is small while every request's latency keeps growing."""
+    maps = _served_maps(nv, torch)
+    out = {"workload": f"{n} requests per rate, Poisson arrivals, K log-uniform 2k-30k, maps room + indoor "
+                       f"resident, at most {max_active} requests in the device loop at once; plain: one "
+                       "bbs_localize at a time in arrival order (FIFO)",
+           "rates": [run_served(nv, torch, maps, float(lam), n, seed=9 + j, max_active=max_active)
+                     for j, lam in enumerate(rates)]}
+    return out
 
 
 def _kernel_hash():
@@ -474,24 +599,77 @@ def _kernel_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic_from_profile(workload=WORKLOAD):
-    """DRAM bytes per launch of the scoring kernel from the committed ncu
-    summary of the workload (profiles/branch3_kernel_<workload>.md, "key:
-    value" lines), if it was taken on the current kernel source."""
+def _profile_kv(workload=WORKLOAD):
+    """The machine-readable lines ("- key: `value`") of the committed ncu
+    summary of the scoring kernel on a workload
+    (profiles/branch3_kernel_<workload>.md), if it was taken on the current
+    kernel source; else {}."""
     p = os.path.join(ROOT, "profiles", f"branch3_kernel_{workload}.md")
     if not os.path.exists(p):
-        return None
+        return {}
     kv = {}
     for line in open(p):
         if ":" in line and line.startswith("- "):
             k, v = line[2:].split(":", 1)
             kv[k.strip()] = v.strip().strip("`")
     if kv.get("kernel_hash") != _kernel_hash():
+        return {}
+    out = {}
+    for k, v in kv.items():
+        try:
+            out[k] = float(v)
+        except ValueError:
+            out[k] = v
+    return out
+
+
+def _by_launch_size(log, peak_gops):
+    """The scoring launches split at their median size: units, device time and
+    the ALU fraction of the smaller and the larger half."""
+    if not log:
         return None
-    try:
-        return float(kv.get("dram_bytes_per_launch"))
-    except (TypeError, ValueError):
-        return None
+    log = sorted(log)
+    half = len(log) // 2
+    out = {}
+    for name, part in (("smaller_half", log[:half]), ("larger_half", log[half:])):
+        u = sum(x for x, _ in part)
+        t = sum(y for _, y in part)
+        out[name] = {"launches": len(part), "units_mean": u / len(part) if part else None, "ms": t,
+                     "frac": (u / (t / 1e3) * ALG_OPS_PER_UNIT / 1e9) / peak_gops if t > 0 else None}
+    return out
+
+
+def _roofline(units_per_s, score_ms, launches, sm_mhz, nsm, workload, gather_peak_gbs=None):
+    """The scoring kernel's roofline.  Bound: ALU issue (L1 serves most of its
+    probes).  Algorithmic work per unit (one scan point x one rotational
+    child, which answers its 8 translational children): 15 FP32 ops of the
+    rotation, 3 floors, 3 shifts + 3 adds to the level key, 8 membership
+    accumulations = 32 ops; peak: SMs x 128 INT32/FP32 lanes x the SM clock
+    sampled during the timed region.  The L2 and L1 sector rates come from
+    the committed ncu capture of the same kernel source (sectors and duration
+    of the captured launches), the L2 peak from this run's random-gather
+    plateau."""
+    alu_peak = nsm * 128 * sm_mhz * 1e6 / 1e9          # Gop/s
+    achieved = units_per_s * ALG_OPS_PER_UNIT / 1e9
+    kv = _profile_kv(workload)
+    out = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gop/s", "frac": achieved / alu_peak,
+           "traffic": kv.get("dram_bytes_per_launch"),
+           "kernel": "branch3_kernel (fused branch + Eq. (11) scoring)",
+           "algorithmic_ops": f"{ALG_OPS_PER_UNIT} per scan point per rotational child "
+                              "(rotation 15, floor 3, level key 6, 8 child counts)",
+           "units_per_s": units_per_s, "launches": launches, "kernel_ms": score_ms,
+           "peak_source": f"{nsm} SMs x 128 lanes x {sm_mhz:.0f} MHz (median SM clock in the timed region)"}
+    dur = kv.get("duration_us_per_launch")
+    if dur:
+        l2 = kv.get("lts_sectors_per_launch", 0.0) * 32 / (dur * 1e-6) / 1e9
+        l1 = kv.get("l1_sectors_per_launch", 0.0) * 32 / (dur * 1e-6) / 1e9
+        out["l2"] = {"achieved": l2, "peak": gather_peak_gbs, "unit": "GB/s",
+                     "frac": l2 / gather_peak_gbs if gather_peak_gbs else None,
+                     "source": f"lts__t_sectors / gpu__time_duration of profiles/branch3_kernel_{workload}.md; "
+                               "peak: random 32-byte gathers over an L2-resident table (bbs_bench_gather, this run)"}
+        out["l1"] = {"achieved": l1, "unit": "GB/s",
+                     "source": "l1tex__t_sectors_pipe_lsu_mem_global_op_ld / gpu__time_duration, same capture"}
+    return out
 
 
 def run_ours(a):
@@ -553,6 +731,8 @@ def run_ours(a):
         nv.bbs_localize(maps, scans_d[i % a.scans], args.ranges, args.opts)
 
     # ---- timed: device-resident scans (device-driven search loop) -------------
+    launch_log = []   # (units, ms) of every scoring launch of the kernel-timed steps
+
     def timed_steps(opts):
         res, ms = [], []
         barrier()
@@ -570,6 +750,8 @@ def run_ours(a):
                 e1.synchronize()
                 ms.append(e0.elapsed_time(e1))
                 res.append(r.as_dict())
+                if opts.flags & nv.TIME_KERNELS:
+                    launch_log.extend(zip(*nv.bbs_launch_log()))
         barrier()
         return res, ms, clk.summary()
 
@@ -607,26 +789,17 @@ def run_ours(a):
     e2e_probes = probes  # the same scans in the same order
 
     # ---- rooflines (measured live) -------------------------------------------
-    # ALU: the scoring kernel is issue-bound (L1 serves ~97 % of its probes).
-    # Algorithmic work per unit (one scan point x one rotational child, which
-    # answers its 8 translational children): 15 FP32 ops of the rotation, 3
-    # floors, 3 shifts + 3 adds to the level key, 8 membership accumulations
-    # = 32 ops.  Peak: 152 SMs x 128 INT32/FP32 lanes x the SM clock sampled
-    # during the timed region.
     units_per_s = gathers / (score_ms / 1e3) if score_ms > 0 else 0.0
     sm_mhz = (kclocks or clocks or {}).get("sm_mhz") or 2070.0
-    alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e9          # Gop/s
-    alu_achieved = units_per_s * ALG_OPS_PER_UNIT / 1e9
-    # L2 gather: one 32-byte sector per unit (a byte-grid cell or a bucket
-    # half lives in one sector) against random 32-byte gathers over an
-    # L2-resident table of the level-0 table's size (the plateau of
-    # bbs_bench_gather)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    # the L2 random-gather plateau over a table of the level-0 table's size
     lvl0 = nv.bbs_maps_info(maps, 0)
     table_bytes = lvl0["table_size"] * (1 if lvl0["layout"] == nv.LAYOUT_BYTES else 32)
     gb = 1 << 27
     peak_ms = min(nv.bbs_bench_gather(max(table_bytes, 1 << 22), gb, stream.cuda_stream) for _ in range(3))
-    peak_gbs = gb * 32 / peak_ms / 1e6
-    achieved_gbs = units_per_s * 32 / 1e9
+    gather_gbs = gb * 32 / peak_ms / 1e6
+    roofline = _roofline(units_per_s, score_ms, score_launches, sm_mhz, nsm, a.workload, gather_gbs)
+    roofline["by_launch_size"] = _by_launch_size(launch_log, roofline["peak"])
 
     # ---- reduce over ranks ----------------------------------------------------
     total_ms, e2e_total, probes_all, e2e_probes_all = reduce_over_ranks(torch, ws, total_ms, e2e_total, probes,
@@ -635,17 +808,14 @@ def run_ours(a):
     batched = served = exact = outdoor = host_queue = refine = None
     if rank == 0 and ws == 1 and not a.no_forms:
         batched = _form(run_batched, nv, torch, maps, w, stream)
-        served = _form(run_served, nv, torch)
+        served = _form(run_served_sweep, nv, torch)
         exact = _form(run_exact, nv, torch, stream)
-        outdoor = _form(run_outdoor, nv, torch, stream)
+        outdoor = _form(run_outdoor, nv, torch, stream, nsm, gather_gbs)
         host_queue = _form(run_host_queue, nv, torch, maps, w, scans_d, stream)
         refine = _form(run_gicp, nv, torch, maps, w, stream)
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
-        rate, n, dt = cpu_probe_rate(w, m, scans[0])
-        cpu = {"value": rate, "unit": "probes/s", "cores": 1, "kind": "oracle",
-               "sample": f"{n} random nodes over all levels x {len(scans[0])}-point scan, Eq. (11) scoring "
-                         f"({dt:.1f} s, single-threaded C oracle on the host)"}
+        cpu = cpu_legs(w, m, scans)
     if rank == 0:
         line = {
             "metric": METRIC, "value": probes_all / (total_ms / 1e3), "unit": "probes/s", "n_gpus": ws,
@@ -662,19 +832,8 @@ def run_ours(a):
                                                  "device_*: %globaltimer from the initial set's start"),
             "found": f"{found}/{a.steps}",
             "map_build_ms": build_ms,
-            "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Gop/s",
-                         "frac": alu_achieved / alu_peak,
-                         "traffic": _traffic_from_profile(a.workload),
-                         "kernel": "branch3_kernel (fused branch + Eq. (11) scoring)",
-                         "algorithmic_ops": f"{ALG_OPS_PER_UNIT} per scan point per rotational child "
-                                            "(rotation 15, floor 3, level key 6, 8 child counts)",
-                         "units_per_s": units_per_s, "launches": score_launches, "kernel_ms": score_ms,
-                         "peak_source": f"152 SMs x 128 lanes x {sm_mhz:.0f} MHz (median SM clock in the timed region)"},
-            "l2_gather": {"achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
-                          "frac": achieved_gbs / peak_gbs if peak_gbs else None,
-                          "note": "32 B per unit vs random 32-byte gathers over a "
-                                  f"{max(table_bytes, 1 << 22) >> 20} MiB L2-resident table (bbs_bench_gather, "
-                                  "this run); L1 hits let the kernel exceed the random-gather plateau"},
+            "bound_check": _bound_check(results),
+            "roofline": roofline,
             "batched": batched,
             "served": served,
             "exact_bound": exact,
