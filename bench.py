@@ -336,15 +336,15 @@ def run_batched(nv, torch, maps, w, stream, n=64, seed=4):
             "found": sum(r.status == nv.OK for r in many), "results_equal_plain": f"{same}/{n}"}
 
 
-def run_exact(nv, torch, stream, n_scans=4):
-    """The exact-bound mode on the room workload (config 1, whose exhaustive
-    search is the reference of the oracle pins): levels above the leaves
-    widened so that every node's score bounds its leaves' under rotation too.
-    Nodes scored, time per scan and best scores vs the approximate (default)
-    bound on the same scans.  (On the indoor workload the widened coarse levels
-    keep nearly every node: the frontier outgrows its default capacity.)"""
+def run_exact(nv, torch, stream, workload="room", n_scans=4):
+    """The exact-bound mode: levels above the leaves widened so that every
+    node's score bounds its leaves' under rotation too.  Nodes scored, peak
+    frontier, time per scan and best scores vs the approximate (default)
+    bound on the same scans.  On the room workload (whose exhaustive search
+    is the reference of the oracle pins) and on the indoor one, where the
+    widened coarse levels keep most nodes and the frontier grows to ~10^8."""
     from paper_2310_10023_gb300 import synth
-    w = synth.WORKLOADS["room"]
+    w = synth.WORKLOADS[workload]
     m = synth.make_map(w.scene)
     md = torch.from_numpy(np.array(m)).cuda()
     maps = nv.bbs_build_maps(md, w.r, w.levels)
@@ -352,7 +352,7 @@ def run_exact(nv, torch, stream, n_scans=4):
     a = nv.workload_args(w, stream=stream.cuda_stream)
     e = max(nv.bbs_exact_dilation(maps, s_, a.ranges, a.opts) for s_ in scans_d)
     em = nv.bbs_build_maps(md, w.r, w.levels, nv.exact_bound_flags(e))
-    out = {"workload": f"room 20x20x5 m, r={w.r} m, {w.levels} levels, {n_scans} scans of "
+    out = {"workload": f"{workload}, r={w.r} m, {w.levels} levels, {n_scans} scans of "
                        f"{statistics.mean(len(s_) for s_ in scans_d):.0f} points", "extra_dilation": e}
     for name, mp in (("approximate", maps), ("exact", em)):
         nv.bbs_localize(mp, scans_d[0], a.ranges, a.opts)
@@ -364,6 +364,7 @@ def run_exact(nv, torch, stream, n_scans=4):
         e1.synchronize()
         out[name] = {"ms_per_scan": e0.elapsed_time(e1) / len(scans_d),
                      "nodes_scored_mean": statistics.mean(r.nodes_scored for r in res),
+                     "peak_frontier_max": max(r.peak_frontier for r in res),
                      "best_scores": [r.best_score for r in res]}
         if name == "approximate":
             out["bound_check"] = _bound_check([r.as_dict() for r in res])
@@ -809,7 +810,8 @@ def run_ours(a):
     if rank == 0 and ws == 1 and not a.no_forms:
         batched = _form(run_batched, nv, torch, maps, w, stream)
         served = _form(run_served_sweep, nv, torch)
-        exact = _form(run_exact, nv, torch, stream)
+        exact = {"room": _form(run_exact, nv, torch, stream, "room", 4),
+                 "indoor": _form(run_exact, nv, torch, stream, "indoor", 2)}
         outdoor = _form(run_outdoor, nv, torch, stream, nsm, gather_gbs)
         host_queue = _form(run_host_queue, nv, torch, maps, w, scans_d, stream)
         refine = _form(run_gicp, nv, torch, maps, w, stream)

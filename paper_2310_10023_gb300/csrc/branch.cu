@@ -112,14 +112,17 @@ __device__ __forceinline__ void child_bits(const LevelView& L, uint32_t bx, uint
 // (acc >> 4 k) & 0x000F000F holds the children (jx, jz) = (k & 1, k >> 1)
 // with jy = 0 and jy = 1 in its two 16-bit halves.  A point adds
 // CHILD_LUT[v] for its 8-bit child mask v (one shared-memory load and one
-// add).  A thread counts at most PCHUNK / 256 = 8 points of a run, so no
-// counter passes 15.
+// add).  A scoring thread counts at most 10 points of a run (a run is at
+// most PCHUNK points over 224 threads, two points per pair), so no counter
+// passes 15.
 __host__ __device__ constexpr uint32_t child_lut_entry(uint32_t v)
 {
     return ((v & 1u) << 0) | (((v >> 1) & 1u) << 4) | (((v >> 2) & 1u) << 16) | (((v >> 3) & 1u) << 20) |
            (((v >> 4) & 1u) << 8) | (((v >> 5) & 1u) << 12) | (((v >> 6) & 1u) << 24) | (((v >> 7) & 1u) << 28);
 }
-static_assert(PCHUNK / 256 <= 15, "4-bit child counters hold the points of one run per thread");
+// the scoring CTA: warps 0..6 score (NCONS threads), warp 7 describes the rounds
+constexpr int NCONS = 224;
+static_assert(2 * ((PCHUNK / 2 + NCONS - 1) / NCONS) <= 15, "4-bit child counters hold the points of one run per thread");
 
 // The 8-bit child mask of one point from a byte grid (LAYOUT_BYTES): relative
 // keys clamped to the empty key past the box, one byte load.
@@ -150,14 +153,14 @@ __device__ __forceinline__ uint32_t planes_mask(uint32_t w0, uint32_t w1)
 // One run (a rotational child over blocks of the staged chunk), two points
 // per step.  The chunk is staged as pairs: sxy[j] = (x_2j, x_2j+1, y_2j,
 // y_2j+1) and sz[j] = (z_2j, z_2j+1), so each coordinate pair is one 64-bit
-// register for the f32x2 operations; thread t takes pairs jlo + t, jlo + t +
-// blockDim, ... below jhi.  q = (A_i0 x + A_i1 y) + A_i2 z is rounded to FP32
+// register for the f32x2 operations; thread t of the nt scoring threads takes
+// pairs jlo + t, jlo + t + nt, ... below jhi.  q = (A_i0 x + A_i1 y) + A_i2 z is rounded to FP32
 // after every product and sum (no FMA), as the oracle; the floor, the level
 // shift and the key offset are one fma.rm of that q (see KB).
 template <int LAYOUT, bool INSIDE = false>
 __device__ __forceinline__ void score_run(const ulonglong2* sxy, const f2* sz, int n, int jlo, int jhi,
                                           const LevelView& L, const Row2& r0, const Row2& r1, const Row2& r2, f2 S,
-                                          f2 Cx, f2 Cy, f2 Cz, const uint32_t* lut, uint32_t& acc)
+                                          f2 Cx, f2 Cy, f2 Cz, const uint32_t* lut, uint32_t& acc, int t, int nt)
 {
     const uint32_t ex = L.rmax[0] + 1u, ey = L.rmax[1] + 1u, ez = L.rmax[2] + 1u;   // bytes: the empty key past the box
     const uint32_t cfix = 0u - KB * (L.nby * L.nbz + L.nbz + 1u);
@@ -178,13 +181,13 @@ __device__ __forceinline__ void score_run(const ulonglong2* sxy, const f2* sz, i
         acc += lut[mask((uint32_t)bx1, (uint32_t)by1, (uint32_t)bz1)];
         if (2 * j + 1 < n) acc += lut[mask((uint32_t)bx2, (uint32_t)by2, (uint32_t)bz2)];
     };
-    int j = jlo + threadIdx.x;
+    int j = jlo + t;
     if (LAYOUT == LAYOUT_DENSE || LAYOUT == LAYOUT_BYTES)   // two pairs per step: four gathers in flight per thread
-        for (; j + (int)blockDim.x < jhi; j += 2 * blockDim.x) {
+        for (; j + nt < jhi; j += 2 * nt) {
             pair(j);
-            pair(j + blockDim.x);
+            pair(j + nt);
         }
-    for (; j < jhi; j += blockDim.x) pair(j);
+    for (; j < jhi; j += nt) pair(j);
 }
 
 // the segment holding launch-local slice w (segments in slice order)
@@ -274,84 +277,67 @@ constexpr int NRUN = 32;   // runs described per round of a CTA
 
 }  // namespace
 
-// The rotation rows (A = fl32(R / r)) of the runs of a round, from their
-// tasks' rl: entry e of run r is formed by thread e * nrun + r, so a warp
-// forms one entry of 32 runs and the short FP64 chains spread over every warp
-// of the CTA (kept out of line: the scoring loop keeps its registers).
-__device__ __noinline__ void form_rows(RunDesc* rd, const TaskRec* __restrict__ tasks, const SearchDev& S, int64_t v0,
-                                       int64_t nt, int nrun)
+// The rotation rows (A = fl32(R / r)) of one run's task, from its rl, into
+// the run's descriptor (kept out of line: the scoring loop keeps its
+// registers; the describing warp forms one run per lane).
+__device__ __noinline__ void run_rows(RunDesc& d, uint32_t rl, const SearchDev& S)
 {
-    for (int q = threadIdx.x; q < 9 * nrun; q += blockDim.x) {
-        const int e = q / nrun, r = q - e * nrun;
-        const int64_t v = v0 + r;
-        const int64_t u = v - (v / nt) * nt;
-        const uint32_t rl = __ldg(&tasks[u].rl);
-        const float a = rotation_entry(S.cs, S.grid, rl_level(rl), rl_rot(rl), e);
-        rd[r].a[e] = pk2(a, a);
-    }
+    float A[9];
+    rotation_rows(S.cs, S.grid, rl_level(rl), rl_rot(rl), A);
+#pragma unroll
+    for (int e = 0; e < 9; ++e) d.a[e] = pk2(A[e], A[e]);
 }
 
-// Fused branch + score.  The launch's slices (task, PBLK-point block) are
-// split into gridDim.x equal contiguous ranges, one per CTA; a CTA walks its
-// range in rounds of at most NRUN runs (maximal pieces of one task over one
-// chunk), describing every run of a round in parallel (task record, parent,
-// rotation rows), staging a chunk of the scan only when the chunk changes,
-// and adding each run's 8 child counts to the dense scores at the round's end.
-template <int MODE, bool BYTES>
-__global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
-    branch3_kernel(Plan* __restrict__ P, const SearchDev* __restrict__ Sall, const TaskRec* __restrict__ tasks,
-                   int32_t* dense)
+// named barriers of the scoring CTA (0 is __syncthreads): the describing
+// warp fills round buffer b and arrives on FULL + b; the scoring warps wait
+// there, score, and arrive on EMPTY + b when they no longer read the buffer;
+// CONS synchronizes the scoring warps alone
+constexpr int BAR_FULL = 1, BAR_EMPTY = 3, BAR_CONS = 5;
+__device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ void bar_arrive(int id, int n) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
+// The describing warp of a scoring CTA (out of line: its registers and its
+// FP64 row formation stay out of the scoring warps' allocation).
+template <int MODE>
+__device__ __noinline__ void describe_rounds(Plan* __restrict__ P, const SearchDev* __restrict__ Sall,
+                                             const TaskRec* __restrict__ tasks, RunDesc (*rd)[NRUN], int32_t* s_nrun,
+                                             int64_t n_slices)
 {
-    pdl_wait();   // the round's plan and tasks are written by the kernels before
-    pdl_trigger();
-    if (P->status != PLAN_OK || P->grow) return;
-    __shared__ ulonglong2 sxy[PCHUNK / 2];
-    __shared__ f2 sz[PCHUNK / 2];
-    __shared__ RunDesc rd[NRUN];
-    __shared__ uint32_t red[NRUN][4];
-    __shared__ uint32_t lut[256];   // child counter increments per 8-bit child mask
-    // the CTA's walk, kept in shared memory (uniform; frees registers for the runs)
-    __shared__ int64_t s_cur, s_end, s_next;
-    // the staged chunk is (s_staged_sid, s_staged_c) between rounds; within a
-    // round, run 0's chunk is staged before the runs and run r's chunk after
-    // run r - 1 (the tag is written only at the round's end)
-    __shared__ int32_t s_gi, s_nrun, s_staged_sid, s_staged_c;
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int64_t n_slices = P->n_slices;
+    const int lane = threadIdx.x & 31;
     // the first static_pm / 1000 of the slices in equal static shares; the
     // rest handed out in shrinking grabs (at least grab_min) as CTAs finish
     const int64_t n_static = n_slices * P->static_pm / 1000;
     const int64_t grab_min = P->grab_min > 0 ? P->grab_min : 1;
-    if (tid == 0) {
-        s_cur = n_static * blockIdx.x / gridDim.x;
-        s_end = n_static * (blockIdx.x + 1) / gridDim.x;
-        s_gi = -1;
-        s_staged_sid = -1;
-        s_staged_c = -1;
-    }
-    for (int i = tid; i < 4 * NRUN; i += blockDim.x) (&red[0][0])[i] = 0u;
-    for (int i = tid; i < 256; i += blockDim.x) lut[i] = child_lut_entry((uint32_t)i);
-    float* fxy = reinterpret_cast<float*>(sxy);
-    float* fz = reinterpret_cast<float*>(sz);
-    for (;;) {
-        __syncthreads();   // the walk state is current; the previous round's descriptors and partials are consumed
-        if (s_cur >= s_end) {   // uniform: this range is done, take the next grab
-            if (tid == 0) {
+    int64_t cur = n_static * blockIdx.x / gridDim.x, end = n_static * (blockIdx.x + 1) / gridDim.x;
+    int gi = -1;
+    int round = 0;
+    for (;; ++round) {
+        const int b = round & 1;
+        if (round >= 2) bar_sync(BAR_EMPTY + b, 256);   // the scoring warps are done with buffer b
+        if (cur >= end) {   // this range is done: take the next grab
+            unsigned long long got = 0, want = 0;
+            if (lane == 0) {
                 const unsigned long long seen = *(volatile unsigned long long*)&P->next_slice;
                 const int64_t left = n_slices - n_static - (int64_t)seen;
-                int64_t want = left / (2 * (int64_t)gridDim.x);
-                if (want < grab_min) want = grab_min;
-                const int64_t got = n_static + (int64_t)atomicAdd(&P->next_slice, (unsigned long long)want);
-                s_cur = got;
-                s_end = min(got + want, n_slices);
-                s_gi = -1;
+                int64_t w = left / (2 * (int64_t)gridDim.x);
+                if (w < grab_min) w = grab_min;
+                want = (unsigned long long)w;
+                got = (unsigned long long)n_static + atomicAdd(&P->next_slice, want);
             }
-            __syncthreads();
-            if (s_cur >= s_end) break;   // uniform: every slice is handed out
+            got = __shfl_sync(0xffffffffu, got, 0);
+            want = __shfl_sync(0xffffffffu, want, 0);
+            cur = (int64_t)got;
+            end = min((int64_t)(got + want), n_slices);
+            gi = -1;
         }
-        const int64_t s1 = s_end;
-        const int64_t cur = s_cur;
-        int gi = s_gi >= 0 ? s_gi : find_slice_seg(P, cur);
+        if (cur >= end) {   // every slice is handed out: the scoring warps stop
+            if (lane == 0) s_nrun[b] = 0;
+            __syncwarp();
+            bar_arrive(BAR_FULL + b, 256);
+            if (round >= 1) bar_sync(BAR_EMPTY + (b ^ 1), 256);   // the last round's release
+            break;
+        }
+        if (gi < 0) gi = find_slice_seg(P, cur);
         const Seg* g = &P->seg[gi];
         int64_t seg_end = g->first_slice + g->n_tasks * g->nblk;
         while (cur >= seg_end) {   // the range continues in a later segment
@@ -362,7 +348,7 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
         const int nchunk = (g->nblk + 3) >> 2;
         const int nbl = g->nblk - 4 * (nchunk - 1);   // blocks of the last chunk
         // seg-relative slices: chunk c holds tasks 0..nt-1 of nbc(c) blocks each
-        const int64_t x0 = cur - g->first_slice, xh = min(s1, seg_end) - g->first_slice;
+        const int64_t x0 = cur - g->first_slice, xh = min(end, seg_end) - g->first_slice;
         auto tc_of = [&](int64_t x) -> int64_t {   // (chunk * nt + task) of slice x
             int64_t c = x / (4 * nt);
             if (c > nchunk - 1) c = nchunk - 1;
@@ -377,32 +363,15 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
         const int64_t v0 = tc_of(x0), vh = tc_of(xh - 1);
         const int nrun = (int)(vh - v0 + 1 < NRUN ? vh - v0 + 1 : NRUN);
         const int64_t xe = v0 + nrun <= vh ? tc_first(v0 + nrun) : xh;   // this round ends at slice xe
-        // the round's first chunk is staged by every thread while the descriptors
-        // are formed (the top barrier ended the previous chunk's readers)
-        {
-            const int32_t c0 = (int32_t)(v0 / nt);
-            if (g->sid != s_staged_sid || c0 != s_staged_c) {   // uniform
-                const SearchDev& S0 = Sall[g->sid];
-                const int32_t k0 = c0 * PCHUNK;
-                const int32_t n0 = min(PCHUNK, S0.K - k0);
-                for (int i = tid; i < n0; i += blockDim.x) {
-                    const float4 p = __ldg(S0.scan + k0 + i);
-                    const int j = i >> 1, h = i & 1;
-                    fxy[4 * j + h] = p.x;
-                    fxy[4 * j + 2 + h] = p.y;
-                    fz[2 * j + h] = p.z;
-                }
-            }
-        }
-        if (tid < nrun) {
+        if (lane < nrun) {
             const SearchDev& S = Sall[g->sid];
-            const int64_t v = v0 + tid;
+            const int64_t v = v0 + lane;
             const int64_t c = v / nt, u = v - c * nt;
             const int nbc = c < nchunk - 1 ? 4 : nbl;
             const int64_t rs = c * 4 * nt + u * nbc;
             int m;
             int32_t tx, ty, tz;
-            RunDesc& d = rd[tid];
+            RunDesc& d = rd[b][lane];
             if (MODE == MODE_INITIAL) {
                 virtual_parent(S, g->first_parent + u / g->R, tx, ty, tz);
                 tx *= 2;
@@ -420,6 +389,7 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
                 tx = tr.tx;
                 ty = tr.ty;
                 tz = tr.tz;
+                run_rows(d, tr.rl, S);
             }
             const LevelView& L = S.maps[m];
             const bool cmp = L.layout != LAYOUT_WIDE;
@@ -429,8 +399,8 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
                 // (|floor(q / 2^m)| <= 2^18 by the scan bound), as the clamped one does
                 int32_t o = t3[i] - (cmp ? L.base[i] : 0);
                 o = o > (1 << 21) ? (1 << 21) : (o < -(1 << 21) ? -(1 << 21) : o);
-                const float c = 12582912.0f + (float)o;   // exact: an integer below 2^24
-                d.kc[i] = pk2(c, c);
+                const float cf = 12582912.0f + (float)o;   // exact: an integer below 2^24
+                d.kc[i] = pk2(cf, cf);
             }
             const float sc = __int_as_float((127 - m) << 23);   // 2^-m
             d.s = pk2(sc, sc);
@@ -440,40 +410,76 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
             d.b0 = (int32_t)(max(rs, x0) - rs);
             d.b1 = (int32_t)(min(rs + nbc, xe) - rs);
             d.task = g->first_task + u;
-            if (MODE == MODE_INITIAL) d.inside = L.layout == LAYOUT_BYTES ? (int32_t)run_inside(d, S.cbox + 2 * c, L) : 0;
+            d.inside = L.layout == LAYOUT_BYTES ? (int32_t)run_inside(d, S.cbox + 2 * c, L) : 0;
         }
-        if (MODE != MODE_INITIAL) {
-            // the rotation rows of the round's tasks
-            const SearchDev& S = Sall[g->sid];
-            form_rows(rd, tasks + g->first_task, S, v0, nt, nrun);
-            __syncthreads();   // the rows are in
-            if (tid < nrun) {
-                RunDesc& d = rd[tid];
-                const LevelView& L = S.maps[d.m];
-                d.inside = L.layout == LAYOUT_BYTES ? (int32_t)run_inside(d, S.cbox + 2 * d.c, L) : 0;
-            }
-        }
-        if (tid == 0) {
-            s_nrun = nrun;
-            s_next = g->first_slice + xe;
-            s_gi = gi;
-        }
-        __syncthreads();   // descriptors visible
-        for (int r = 0; r < s_nrun; ++r) {
-            const RunDesc& d = rd[r];
+        if (lane == 0) s_nrun[b] = nrun;
+        __syncwarp();
+        bar_arrive(BAR_FULL + b, 256);   // buffer b holds the round
+        cur = g->first_slice + xe;
+    }
+}
+
+// Fused branch + score.  The launch's slices (task, PBLK-point block) are
+// split into equal contiguous ranges, one per CTA, for the first static_pm
+// per mille, the rest handed out in shrinking grabs.  Warp 7 of a CTA walks
+// its ranges in rounds of at most NRUN runs (maximal pieces of one task over
+// one chunk) and describes each round into one of two buffers (task record,
+// rotation rows, key offsets, the chunk-box test), one run per lane, while
+// warps 0..6 score the round before: staging a chunk of the scan only when
+// the chunk changes, and adding each run's 8 child counts to the dense
+// scores at the round's end.  Describing overlaps scoring, so a round's
+// loads and FP64 row formation no longer stall the scoring warps.
+template <int MODE, bool BYTES>
+__global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
+    branch3_kernel(Plan* __restrict__ P, const SearchDev* __restrict__ Sall, const TaskRec* __restrict__ tasks,
+                   int32_t* dense)
+{
+    pdl_wait();   // the round's plan and tasks are written by the kernels before
+    pdl_trigger();
+    if (P->status != PLAN_OK || P->grow) return;
+    __shared__ ulonglong2 sxy[PCHUNK / 2];
+    __shared__ f2 sz[PCHUNK / 2];
+    __shared__ RunDesc rd[2][NRUN];
+    __shared__ uint32_t red[2][NRUN][4];
+    __shared__ uint32_t lut[256];   // child counter increments per 8-bit child mask
+    __shared__ int32_t s_nrun[2];
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int i = tid; i < 2 * 4 * NRUN; i += blockDim.x) (&red[0][0][0])[i] = 0u;
+    for (int i = tid; i < 256; i += blockDim.x) lut[i] = child_lut_entry((uint32_t)i);
+    __syncthreads();
+    const int64_t n_slices = P->n_slices;
+
+    if (tid >= NCONS) {   // the describing warp
+        describe_rounds<MODE>(P, Sall, tasks, rd, s_nrun, n_slices);
+        return;
+    }
+
+    // ---- the scoring warps (threads 0 .. NCONS - 1) -------------------------
+    float* fxy = reinterpret_cast<float*>(sxy);
+    float* fz = reinterpret_cast<float*>(sz);
+    int32_t staged_sid = -1, staged_c = -1;   // the chunk in shared memory (the same in every scoring thread)
+    for (int round = 0;; ++round) {
+        const int b = round & 1;
+        bar_sync(BAR_FULL + b, 256);   // the describing warp filled buffer b
+        const int nrun = s_nrun[b];
+        if (nrun == 0) break;
+        for (int r = 0; r < nrun; ++r) {
+            const RunDesc& d = rd[b][r];
             const SearchDev& S = Sall[d.sid];
-            if (r > 0 && (d.sid != rd[r - 1].sid || d.c != rd[r - 1].c)) {   // uniform
-                __syncthreads();   // the previous chunk's readers are done
+            if (d.sid != staged_sid || d.c != staged_c) {   // uniform over the scoring threads
+                if (staged_sid >= 0) bar_sync(BAR_CONS, NCONS);   // the previous chunk's readers are done
                 const int32_t k0 = d.c * PCHUNK;
                 const int32_t n = min(PCHUNK, S.K - k0);
-                for (int i = tid; i < n; i += blockDim.x) {
+                for (int i = tid; i < n; i += NCONS) {
                     const float4 p = __ldg(S.scan + k0 + i);
                     const int j = i >> 1, h = i & 1;
                     fxy[4 * j + h] = p.x;
                     fxy[4 * j + 2 + h] = p.y;
                     fz[2 * j + h] = p.z;
                 }
-                __syncthreads();   // staged points visible
+                staged_sid = d.sid;
+                staged_c = d.c;
+                bar_sync(BAR_CONS, NCONS);   // staged points visible
             }
             const LevelView Lv = S.maps[d.m];
             const Row2 r0{d.a[0], d.a[1], d.a[2]};
@@ -485,27 +491,27 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
             if (BYTES) {   // every level of every search is a byte grid: only its path is compiled
                 if (d.inside)
                     score_run<LAYOUT_BYTES, true>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1],
-                                                  d.kc[2], lut, acc);
+                                                  d.kc[2], lut, acc, tid, NCONS);
                 else
                     score_run<LAYOUT_BYTES>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
-                                            acc);
+                                            acc, tid, NCONS);
             } else if (Lv.layout == LAYOUT_BYTES && d.inside)
                 score_run<LAYOUT_BYTES, true>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2],
-                                              lut, acc);
+                                              lut, acc, tid, NCONS);
             else if (Lv.layout == LAYOUT_BYTES)
                 score_run<LAYOUT_BYTES>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
-                                        acc);
+                                        acc, tid, NCONS);
             else if (Lv.layout == LAYOUT_DENSE)
                 score_run<LAYOUT_DENSE>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
-                                        acc);
+                                        acc, tid, NCONS);
             else if (Lv.layout == LAYOUT_COMPACT)
                 score_run<LAYOUT_COMPACT>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
-                                          acc);
+                                          acc, tid, NCONS);
             else
                 score_run<LAYOUT_WIDE>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
-                                       acc);
+                                       acc, tid, NCONS);
             // word k: children (jx, jz) = (k & 1, k >> 1), jy = 0 low and jy = 1 high;
-            // 16-bit fields: at most 8 points per thread x 32 lanes, x 8 warps, per field
+            // 16-bit fields: at most 10 points per thread x 32 lanes, x 7 warps, per field
             uint32_t e0 = acc & 0x000F000Fu, o0 = (acc >> 4) & 0x000F000Fu;
             uint32_t e1 = (acc >> 8) & 0x000F000Fu, o1 = (acc >> 12) & 0x000F000Fu;
             e0 = __reduce_add_sync(0xffffffffu, e0);
@@ -513,28 +519,24 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
             e1 = __reduce_add_sync(0xffffffffu, e1);
             o1 = __reduce_add_sync(0xffffffffu, o1);
             if (lane == 0) {
-                if (e0) atomicAdd(&red[r][0], e0);
-                if (o0) atomicAdd(&red[r][1], o0);
-                if (e1) atomicAdd(&red[r][2], e1);
-                if (o1) atomicAdd(&red[r][3], o1);
+                if (e0) atomicAdd(&red[b][r][0], e0);
+                if (o0) atomicAdd(&red[b][r][1], o0);
+                if (e1) atomicAdd(&red[b][r][2], e1);
+                if (o1) atomicAdd(&red[b][r][3], o1);
             }
         }
-        __syncthreads();   // every warp's partial sums are in
-        for (int w = tid; w < 4 * s_nrun; w += blockDim.x) {
+        bar_sync(BAR_CONS, NCONS);   // every scoring warp's partial sums are in
+        for (int w = tid; w < 4 * nrun; w += NCONS) {
             // word k of a run: children with jx = k & 1, jz = k >> 1; low half jy = 0, high half jy = 1
             const int r = w >> 2, k = w & 3;
-            const uint32_t sum = red[r][k];
+            const uint32_t sum = red[b][r][k];
             if (!sum) continue;
-            red[r][k] = 0u;
-            int32_t* dd = dense + rd[r].task * 8 + 4 * (k & 1) + (k >> 1);
+            red[b][r][k] = 0u;   // zero again before the buffer's next round
+            int32_t* dd = dense + rd[b][r].task * 8 + 4 * (k & 1) + (k >> 1);
             if (sum & 0xFFFFu) atomicAdd(dd, (int32_t)(sum & 0xFFFFu));
             if (sum >> 16) atomicAdd(dd + 2, (int32_t)(sum >> 16));
         }
-        if (tid == 0) {
-            s_cur = s_next;
-            s_staged_sid = rd[s_nrun - 1].sid;
-            s_staged_c = rd[s_nrun - 1].c;
-        }
+        bar_arrive(BAR_EMPTY + b, 256);   // buffer b may be refilled
     }
 }
 

@@ -613,6 +613,40 @@ def outdoor_pair(nv):
     return w, m, nv.bbs_build_maps(torch.from_numpy(np.array(m)).cuda(), w.r, w.levels), oracle.Maps(m, w.r, w.levels)
 
 
+def test_exact_bound_indoor_window_equals_oracle(nv):
+    """The exact-bound mode on indoor data: the indoor map cropped to 32 x 32 m
+    around the planted pose of scan 1, the scan's points within 10 m (every
+    4th), a window of level-5 cells (6.4 m) around the pose, roll / pitch
+    +-0.02 rad and yaw +-0.05 rad.  Maps widened by the required e; the GPU
+    search (whose frontier grows past its start) follows the oracle's exactly."""
+    w = synth.WORKLOADS["indoor"]
+    m = synth.make_map(w.scene)
+    s, pose = synth.make_scan(w.scene, 1)
+    R5 = w.r * 32
+    kx, ky = math.floor(pose[0] / R5), math.floor(pose[1] / R5)
+    cx, cy = (kx + 0.5) * R5, (ky + 0.5) * R5
+    crop = np.ascontiguousarray(m[(np.abs(m[:, 0] - cx) < 16) & (np.abs(m[:, 1] - cy) < 16)])
+    near = np.ascontiguousarray(s[np.linalg.norm(s, axis=1) < 10.0][::4])
+    lo, hi = (kx * R5, ky * R5, 0.0), (kx * R5, ky * R5, 0.0)
+    alo, ahi = (-0.02, -0.02, pose[5] - 0.05), (0.02, 0.02, pose[5] + 0.05)
+    nr, orr = nv.make_ranges(lo, hi, alo, ahi), oracle.make_ranges(lo, hi, alo, ahi)
+    g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(near), orr)
+    e = g.exact_dilation(oracle.scan_dmax(near))
+    dme = nv.bbs_build_maps(crop, w.r, w.levels, nv.exact_bound_flags(e))
+    assert nv.bbs_exact_dilation(dme, near, nr, nv.make_opts()) == e
+    ome = oracle.Maps(crop, w.r, w.levels, oracle.exact_flags(e))
+    for l in range(w.levels):
+        assert np.array_equal(_sorted_keys(nv.bbs_maps_keys(dme, l)), _sorted_keys(ome.keys(l))), l
+    try:
+        nv.bbs_set_tuning(frontier_log2=12)
+        res = nv.bbs_localize(dme, near, nr, nv.make_opts(score_frac=0.8, batch=w.batch))
+    finally:
+        nv.bbs_set_tuning(reset=True)
+    ores = oracle.localize(ome, near, orr, score_frac=0.8, batch=w.batch)
+    _same_search(res, ores)
+    assert res.status == nv.OK and res.peak_frontier > 1 << 12
+
+
 def test_outdoor_search_equals_oracle(nv, outdoor_pair):
     """The outdoor workload's own search (800 x 800 x 40 m city, 40 M map
     points, r = 1 m, 8 levels, the 400 x 400 x 10 m window, full yaw) with
