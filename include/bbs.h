@@ -235,7 +235,8 @@ int  bbs_set_probe_layout(int layout);
  *                 launches planned on the host;
  *   static_pm     per-mille of a launch's (task, 512-point block) slices split
  *                 evenly over the scoring CTAs before the rest is handed out
- *                 in shrinking grabs, 1..1000 (default 750);
+ *                 in shrinking grabs, 1..1000 (default 750; a launch of fewer
+ *                 than 256 slices per CTA is split statically);
  *   grab_min      smallest grab in slices, 1..2^20 (default 16);
  *   ctas_per_sm   scoring CTAs per SM, 1..4 (default 4);
  *   frontier_log2 the frontier arrays of later bbs_localize and

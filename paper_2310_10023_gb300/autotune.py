@@ -33,7 +33,7 @@ DEFAULT = {"layout": 0, "load_factor": 0.25, "static_pm": 750, "grab_min": 16, "
 SPACE = {
     "layout": [0, 2],
     "load_factor": [0.5, 0.35, 0.25, 0.15],
-    "static_pm": [500, 750, 875],
+    "static_pm": [625, 750, 1000],
     "grab_min": [8, 16, 32],
     "ctas_per_sm": [3, 4],
 }

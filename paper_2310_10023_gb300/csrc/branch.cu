@@ -293,6 +293,7 @@ __device__ __noinline__ void run_rows(RunDesc& d, uint32_t rl, const SearchDev& 
 // there, score, and arrive on EMPTY + b when they no longer read the buffer;
 // CONS synchronizes the scoring warps alone
 constexpr int BAR_FULL = 1, BAR_EMPTY = 3, BAR_CONS = 5;
+constexpr int64_t SMALL_LAUNCH = 256;   // slices per CTA below which a launch is split statically
 __device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 __device__ __forceinline__ void bar_arrive(int id, int n) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
@@ -305,8 +306,12 @@ __device__ __noinline__ void describe_rounds(Plan* __restrict__ P, const SearchD
 {
     const int lane = threadIdx.x & 31;
     // the first static_pm / 1000 of the slices in equal static shares; the
-    // rest handed out in shrinking grabs (at least grab_min) as CTAs finish
-    const int64_t n_static = n_slices * P->static_pm / 1000;
+    // rest handed out in shrinking grabs (at least grab_min) as CTAs finish.
+    // A launch of fewer than SMALL_LAUNCH slices per CTA (about one round
+    // each) is split statically: there a grab's round costs more than the
+    // balance it buys (measured, indoor)
+    const int64_t n_static =
+        n_slices < SMALL_LAUNCH * (int64_t)gridDim.x ? n_slices : n_slices * P->static_pm / 1000;
     const int64_t grab_min = P->grab_min > 0 ? P->grab_min : 1;
     int64_t cur = n_static * blockIdx.x / gridDim.x, end = n_static * (blockIdx.x + 1) / gridDim.x;
     int gi = -1;
