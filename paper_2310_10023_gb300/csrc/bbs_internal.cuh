@@ -169,6 +169,151 @@ __device__ __forceinline__ void rotation_rows(const double2* __restrict__ cs, co
     for (int i = 0; i < 9; ++i) A[i] = div_r_f32(R[i], g.r, g.inv_r);
 }
 
+// ---- the same rows without FP64 arithmetic ----------------------------------
+// A value held as h + l in two floats (double-float).  FP64 runs at a small
+// fraction of the FP32 rate on this part, so the search's own row formation
+// takes the rows of rotation_rows from FP32 operations and falls back to
+// rotation_rows only where those cannot decide the result.
+struct DF {
+    float h, l;
+};
+
+// x as h + l: h its leading 24 significand bits (truncated, exact), l the
+// remaining 29 bits rounded to a float, so |h + l - x| <= 2^-47 |x|.  Integer
+// work and one conversion.  ok becomes false unless x is zero or a normal
+// number with |x| in [2^-60, 2^30) (the cos / sin of an angle a rounding
+// residue away from a multiple of pi/2 lies near 1e-16: kept; a product of
+// two such stays in the FP32 normal range, and the absolute error of its low
+// part, which may fall below it, is far below the tolerance of any entry it
+// feeds).
+__device__ __forceinline__ DF df_split(double x, bool& ok)
+{
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const uint32_t sgn = hi & 0x80000000u;
+    if (((hi & 0x7FFFFFFFu) | lo) == 0u) return DF{__uint_as_float(sgn), 0.0f};
+    const int e = (int)((hi >> 20) & 0x7FFu) - 1023;
+    ok = ok && e >= -60 && e < 30;
+    const int ec = e < -60 ? -60 : (e >= 30 ? 29 : e);   // keeps the bit patterns below well-formed
+    const uint32_t hb = sgn | ((uint32_t)(ec + 127) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    // the low 29 significand bits weigh 2^(e - 52) each
+    const float l = __fmul_rn(__uint2float_rn(lo & 0x1FFFFFFFu), __uint_as_float((uint32_t)(ec - 52 + 127) << 23));
+    return DF{__uint_as_float(hb), sgn ? -l : l};
+}
+
+// a * b: h = fl(a.h b.h), l = its exact error plus the cross terms (a.l b.l
+// dropped); relative error below 2^-45 for inputs of 2^-47 and unnormalized
+// products of this function
+__device__ __forceinline__ DF df_mul(DF a, DF b)
+{
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return DF{p, e};
+}
+
+// exact sum of two floats: s + t = a + b
+__device__ __forceinline__ DF two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return DF{s, t};
+}
+
+// a + b, normalized (|l| <= ulp(h) / 2)
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    const DF s = two_sum(a.h, b.h);
+    return two_sum(s.h, __fadd_rn(__fadd_rn(s.l, a.l), b.l));
+}
+
+// fl32 of a real y known to lie within D of h + l (h + l normalized with h
+// the float nearest to it): h itself unless y may lie across a rounding
+// boundary of h (or h is zero, tiny or huge), which clears ok
+__device__ __forceinline__ float df_round(DF v, float D, bool& ok)
+{
+    const uint32_t hb = __float_as_uint(v.h);
+    const uint32_t eb = hb & 0x7F800000u;
+    ok = ok && eb >= (40u << 23) && eb < (215u << 23);
+    // half the spacing of the floats around h; the gap below a power of two is half as wide
+    float half = __uint_as_float((eb < (40u << 23) ? (40u << 23) : eb) - (24u << 23));
+    if ((hb & 0x7FFFFFu) == 0u) half = __fmul_rn(half, 0.5f);
+    ok = ok && __fadd_rn(fabsf(v.l), D) < half;
+    return v.h;
+}
+
+// A = fl32(R / r) of rotation `rot` at level l, equal bit for bit to
+// rotation_rows wherever this returns true.  Every entry of R is formed from
+// double-float copies of the FP64 cos / sin values with FP32 operations
+// (error-free products by FMA, error-free sums): the result lies within
+// D = 2^-40 (|V| + (|t1| + |t2|) / r) of fl64(R_i / r) (V the double-float
+// quotient, t1 and t2 the two product terms of a sum entry; the actual error,
+// FP64 roundings of R included, stays below 2^-42 of the same quantity), and
+// where every real within D of V rounds to one float, that float is
+// fl32(fl64(R_i / r)), the value rotation_rows returns (its quotient test only
+// chooses how that value is reached).  A term with an exactly zero factor
+// (sin 0) is an exact signed zero in both arithmetics, formed here with the
+// same IEEE sign rules (products, and the sum of two zero terms).  Otherwise,
+// and for inputs or entries out of range or too close to a rounding
+// boundary, it returns false and the caller forms the rows in FP64.
+__device__ __forceinline__ bool rotation_rows_df(const double2* __restrict__ cs, const DevGrid& g, int l, uint32_t rot,
+                                                 float A[9])
+{
+    const uint32_t ng = (uint32_t)g.N[l][2], nb = (uint32_t)g.N[l][1];
+    const uint32_t q1 = rot / ng, ig = rot - q1 * ng, ia = q1 / nb, ib = q1 - ia * nb;
+    const double2 A_ = cs[g.cs_off[l][0] + (int32_t)ia];
+    const double2 B_ = cs[g.cs_off[l][1] + (int32_t)ib];
+    const double2 G_ = cs[g.cs_off[l][2] + (int32_t)ig];
+    bool ok = true;
+    const DF ca = df_split(A_.x, ok), sa = df_split(A_.y, ok), cb = df_split(B_.x, ok), sb = df_split(B_.y, ok);
+    const DF cg = df_split(G_.x, ok), sg = df_split(G_.y, ok), ir = df_split(g.inv_r, ok);
+    constexpr float TOL = 9.094947e-13f;    // 2^-40
+    // 2^-100: a sum entry's terms must reach it together; a term far below
+    // (two sines a rounding residue from zero) may lose bits to the FP32
+    // range, an absolute error far below the tolerance
+    constexpr float TINY = 7.888609e-31f;
+    const float irh = fabsf(ir.h);
+    // a product entry x y, then the quotient
+    auto prod = [&](DF x, DF y) -> float {
+        if (x.h == 0.0f || y.h == 0.0f) return __fmul_rn(__fmul_rn(x.h, y.h), irh);   // exact signed zero
+        DF v = df_mul(df_mul(x, y), ir);
+        v = two_sum(v.h, v.l);
+        return df_round(v, __fmul_rn(TOL, fabsf(v.h)), ok);
+    };
+    // a sum entry (x1 y1) z1 + s x2 y2 (s = -1 when neg), then the quotient
+    auto sum = [&](DF x1, DF y1, DF z1, DF x2, DF y2, bool neg) -> float {
+        const bool zero1 = x1.h == 0.0f || y1.h == 0.0f || z1.h == 0.0f, zero2 = x2.h == 0.0f || y2.h == 0.0f;
+        const DF t1 = df_mul(df_mul(x1, y1), z1);
+        DF t2 = df_mul(x2, y2);
+        if (neg) t2 = DF{-t2.h, -t2.l};
+        if (zero1 && zero2) return __fmul_rn(__fadd_rn(t1.h, t2.h), irh);   // two zero terms: exact signed zero
+        ok = ok && __fadd_rn(fabsf(t1.h), fabsf(t2.h)) >= TINY;
+        DF v = df_mul(df_add(t1, t2), ir);
+        v = two_sum(v.h, v.l);
+        const float D = __fmul_rn(TOL, __fadd_rn(fabsf(v.h), __fmul_rn(__fadd_rn(fabsf(t1.h), fabsf(t2.h)), irh)));
+        return df_round(v, D, ok);
+    };
+    A[0] = prod(cg, cb);
+    A[1] = sum(cg, sb, sa, sg, ca, true);
+    A[2] = sum(cg, sb, ca, sg, sa, false);
+    A[3] = prod(sg, cb);
+    A[4] = sum(sg, sb, sa, cg, ca, false);
+    A[5] = sum(sg, sb, ca, cg, sa, true);
+    A[6] = prod(DF{-sb.h, -sb.l}, DF{1.0f, 0.0f});   // R6 = -sb exactly
+    A[7] = prod(cb, sa);
+    A[8] = prod(cb, ca);
+    return ok;
+}
+
+// The rows the search and the pose grid use: rotation_rows_df, and the FP64
+// formation for the rare rotations it cannot decide (the same bits either way)
+__device__ __forceinline__ void search_rows(const double2* __restrict__ cs, const DevGrid& g, int l, uint32_t rot,
+                                            float A[9])
+{
+    if (!rotation_rows_df(cs, g, l, rot, A)) rotation_rows(cs, g, l, rot, A);
+}
+
 // Node / task record in HBM: translation indices and (rotation index << 5 | level).
 struct __align__(16) NodeRec {
     int32_t cx, cy, cz;

@@ -279,11 +279,13 @@ constexpr int NRUN = 32;   // runs described per round of a CTA
 
 // The rotation rows (A = fl32(R / r)) of one run's task, from its rl, into
 // the run's descriptor (kept out of line: the scoring loop keeps its
-// registers; the describing warp forms one run per lane).
+// registers; the describing warp forms one run per lane).  FP32 double-float
+// arithmetic gives the rows' exact bits but for rare entries near a rounding
+// boundary (or out of its range), which take the FP64 formation.
 __device__ __noinline__ void run_rows(RunDesc& d, uint32_t rl, const SearchDev& S)
 {
     float A[9];
-    rotation_rows(S.cs, S.grid, rl_level(rl), rl_rot(rl), A);
+    search_rows(S.cs, S.grid, rl_level(rl), rl_rot(rl), A);
 #pragma unroll
     for (int e = 0; e < 9; ++e) d.a[e] = pk2(A[e], A[e]);
 }
@@ -297,6 +299,29 @@ constexpr int64_t SMALL_LAUNCH = 256;   // slices per CTA below which a launch i
 __device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 __device__ __forceinline__ void bar_arrive(int id, int n) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
+// The CTA's static range [cur, end) of the launch's slices: the first
+// static_pm / 1000 of them in equal shares, the rest handed out later in
+// shrinking grabs.  A launch of fewer than SMALL_LAUNCH slices per CTA (about
+// one round each) is split statically: there a grab's round costs more than
+// the balance it buys (measured, indoor).
+__device__ __forceinline__ int64_t static_slices(const Plan* P, int64_t n_slices)
+{
+    return n_slices < SMALL_LAUNCH * (int64_t)gridDim.x ? n_slices : n_slices * P->static_pm / 1000;
+}
+
+// The search and point chunk of slice x (false when its segment is empty):
+// the chunk the CTA's first run reads
+__device__ __forceinline__ bool slice_chunk(const Plan* P, int64_t x, int32_t& sid, int32_t& c)
+{
+    const Seg& g = P->seg[find_slice_seg(P, x)];
+    if (g.n_tasks <= 0 || x < g.first_slice || x >= g.first_slice + g.n_tasks * g.nblk) return false;
+    const int64_t cc = (x - g.first_slice) / (4 * g.n_tasks);
+    const int nchunk = (g.nblk + 3) >> 2;
+    sid = g.sid;
+    c = (int32_t)(cc < nchunk - 1 ? cc : nchunk - 1);
+    return true;
+}
+
 // The describing warp of a scoring CTA (out of line: its registers and its
 // FP64 row formation stay out of the scoring warps' allocation).
 template <int MODE>
@@ -305,13 +330,8 @@ __device__ __noinline__ void describe_rounds(Plan* __restrict__ P, const SearchD
                                              int64_t n_slices)
 {
     const int lane = threadIdx.x & 31;
-    // the first static_pm / 1000 of the slices in equal static shares; the
-    // rest handed out in shrinking grabs (at least grab_min) as CTAs finish.
-    // A launch of fewer than SMALL_LAUNCH slices per CTA (about one round
-    // each) is split statically: there a grab's round costs more than the
-    // balance it buys (measured, indoor)
-    const int64_t n_static =
-        n_slices < SMALL_LAUNCH * (int64_t)gridDim.x ? n_slices : n_slices * P->static_pm / 1000;
+    // the static range first, then grabs of at least grab_min as CTAs finish
+    const int64_t n_static = static_slices(P, n_slices);
     const int64_t grab_min = P->grab_min > 0 ? P->grab_min : 1;
     int64_t cur = n_static * blockIdx.x / gridDim.x, end = n_static * (blockIdx.x + 1) / gridDim.x;
     int gi = -1;
@@ -439,9 +459,6 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
     branch3_kernel(Plan* __restrict__ P, const SearchDev* __restrict__ Sall, const TaskRec* __restrict__ tasks,
                    int32_t* dense)
 {
-    pdl_wait();   // the round's plan and tasks are written by the kernels before
-    pdl_trigger();
-    if (P->status != PLAN_OK || P->grow) return;
     __shared__ ulonglong2 sxy[PCHUNK / 2];
     __shared__ f2 sz[PCHUNK / 2];
     __shared__ RunDesc rd[2][NRUN];
@@ -449,9 +466,13 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
     __shared__ uint32_t lut[256];   // child counter increments per 8-bit child mask
     __shared__ int32_t s_nrun[2];
     const int tid = threadIdx.x, lane = tid & 31;
+    // launch-independent set-up, before waiting on the kernel before
     for (int i = tid; i < 2 * 4 * NRUN; i += blockDim.x) (&red[0][0][0])[i] = 0u;
     for (int i = tid; i < 256; i += blockDim.x) lut[i] = child_lut_entry((uint32_t)i);
+    pdl_wait();   // the round's plan and tasks are written by the kernels before
+    pdl_trigger();
     __syncthreads();
+    if (P->status != PLAN_OK || P->grow) return;
     const int64_t n_slices = P->n_slices;
 
     if (tid >= NCONS) {   // the describing warp
@@ -463,6 +484,32 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
     float* fxy = reinterpret_cast<float*>(sxy);
     float* fz = reinterpret_cast<float*>(sz);
     int32_t staged_sid = -1, staged_c = -1;   // the chunk in shared memory (the same in every scoring thread)
+    auto stage = [&](int32_t sid, int32_t c) {   // chunk c of search sid's scan, as coordinate pairs
+        const SearchDev& S = Sall[sid];
+        const int32_t k0 = c * PCHUNK;
+        const int32_t n = min(PCHUNK, S.K - k0);
+        for (int i = tid; i < n; i += NCONS) {
+            const float4 p = __ldg(S.scan + k0 + i);
+            const int j = i >> 1, h = i & 1;
+            fxy[4 * j + h] = p.x;
+            fxy[4 * j + 2 + h] = p.y;
+            fz[2 * j + h] = p.z;
+        }
+        staged_sid = sid;
+        staged_c = c;
+        bar_sync(BAR_CONS, NCONS);   // staged points visible
+    };
+    {   // the chunk of the CTA's first static slice, staged while warp 7 describes
+        const int64_t ns = static_slices(P, n_slices);
+        const int64_t cur = ns * blockIdx.x / gridDim.x, end = ns * (blockIdx.x + 1) / gridDim.x;
+        int32_t sid, c;
+        if (cur < end && slice_chunk(P, cur, sid, c)) stage(sid, c);
+    }
+    // Thread t takes the pairs whose index in the CTA's stream of pairs (all
+    // its runs in order) is t modulo NCONS, so every thread scores within one
+    // pair of its share whatever the runs' lengths.  g0 = that stream's length
+    // modulo NCONS before the current run.
+    int g0 = 0;
     for (int round = 0;; ++round) {
         const int b = round & 1;
         bar_sync(BAR_FULL + b, 256);   // the describing warp filled buffer b
@@ -473,18 +520,7 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
             const SearchDev& S = Sall[d.sid];
             if (d.sid != staged_sid || d.c != staged_c) {   // uniform over the scoring threads
                 if (staged_sid >= 0) bar_sync(BAR_CONS, NCONS);   // the previous chunk's readers are done
-                const int32_t k0 = d.c * PCHUNK;
-                const int32_t n = min(PCHUNK, S.K - k0);
-                for (int i = tid; i < n; i += NCONS) {
-                    const float4 p = __ldg(S.scan + k0 + i);
-                    const int j = i >> 1, h = i & 1;
-                    fxy[4 * j + h] = p.x;
-                    fxy[4 * j + 2 + h] = p.y;
-                    fz[2 * j + h] = p.z;
-                }
-                staged_sid = d.sid;
-                staged_c = d.c;
-                bar_sync(BAR_CONS, NCONS);   // staged points visible
+                stage(d.sid, d.c);
             }
             const LevelView Lv = S.maps[d.m];
             const Row2 r0{d.a[0], d.a[1], d.a[2]};
@@ -492,29 +528,31 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
             const Row2 r2{d.a[6], d.a[7], d.a[8]};
             const int n = min(PCHUNK, S.K - d.c * PCHUNK);
             const int jlo = d.b0 * (PBLK / 2), jhi = min(d.b1 * (PBLK / 2), (n + 1) >> 1);
+            const int t = tid >= g0 ? tid - g0 : tid - g0 + NCONS;   // this run's first pair is jlo + t
+            g0 = (g0 + max(jhi - jlo, 0)) % NCONS;
             uint32_t acc = 0;   // 4-bit child counters (child_lut_entry)
             if (BYTES) {   // every level of every search is a byte grid: only its path is compiled
                 if (d.inside)
                     score_run<LAYOUT_BYTES, true>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1],
-                                                  d.kc[2], lut, acc, tid, NCONS);
+                                                  d.kc[2], lut, acc, t, NCONS);
                 else
                     score_run<LAYOUT_BYTES>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
-                                            acc, tid, NCONS);
+                                            acc, t, NCONS);
             } else if (Lv.layout == LAYOUT_BYTES && d.inside)
                 score_run<LAYOUT_BYTES, true>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2],
-                                              lut, acc, tid, NCONS);
+                                              lut, acc, t, NCONS);
             else if (Lv.layout == LAYOUT_BYTES)
                 score_run<LAYOUT_BYTES>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
-                                        acc, tid, NCONS);
+                                        acc, t, NCONS);
             else if (Lv.layout == LAYOUT_DENSE)
                 score_run<LAYOUT_DENSE>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
-                                        acc, tid, NCONS);
+                                        acc, t, NCONS);
             else if (Lv.layout == LAYOUT_COMPACT)
                 score_run<LAYOUT_COMPACT>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
-                                          acc, tid, NCONS);
+                                          acc, t, NCONS);
             else
                 score_run<LAYOUT_WIDE>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
-                                       acc, tid, NCONS);
+                                       acc, t, NCONS);
             // word k: children (jx, jz) = (k & 1, k >> 1), jy = 0 low and jy = 1 high;
             // 16-bit fields: at most 10 points per thread x 32 lanes, x 7 warps, per field
             uint32_t e0 = acc & 0x000F000Fu, o0 = (acc >> 4) & 0x000F000Fu;

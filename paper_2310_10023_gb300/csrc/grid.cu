@@ -224,12 +224,13 @@ __global__ void __launch_bounds__(PACK_THREADS) scan_pack_kernel(const float* __
     if (lane == 0 && m > 0.0) atomicMax(smax_bits, (unsigned long long)__double_as_longlong(m));
 }
 
-// the rows of every rotation of one level (rotation_rows)
+// the rows of every rotation of one level (search_rows: the search's own
+// row formation, so the pose grid's rows pin it)
 __global__ void level_rows_kernel(const double2* __restrict__ cs, DevGrid g, int level, int64_t n, float4* __restrict__ out)
 {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         float A[9];
-        rotation_rows(cs, g, level, (uint32_t)t, A);
+        search_rows(cs, g, level, (uint32_t)t, A);
         out[3 * t + 0] = make_float4(A[0], A[1], A[2], 0.0f);
         out[3 * t + 1] = make_float4(A[3], A[4], A[5], 0.0f);
         out[3 * t + 2] = make_float4(A[6], A[7], A[8], 0.0f);

@@ -138,6 +138,30 @@ def test_pose_grid_bits_equal_oracle(nv, room_pair, flags):
             assert np.array_equal(A[t].view(np.uint32), g.rotation(l, ia, ib, ig).view(np.uint32)), (l, t)
 
 
+@pytest.mark.parametrize("name", ["indoor", "outdoor"])
+@pytest.mark.parametrize("flags", [0, oracle.ANGLE_LOWER_EDGE])
+def test_search_rows_equal_oracle_bits(nv, name, flags):
+    """The rows the search forms (FP32 double-float arithmetic, FP64 where it
+    cannot decide the rounding; the pose grid's rows come from the same
+    function) equal the oracle's FP64 rows bit for bit: every rotation of
+    every level up to 60 k rotations, 60 k sampled beyond, on the indoor and
+    outdoor grids, with segment-centre and lower-edge angles (the latter put
+    exact zeros and rounding residues near 1e-17 into the tables)."""
+    w = synth.WORKLOADS[name]
+    s, _ = synth.make_scan(w.scene, 0)
+    dm = nv.bbs_build_maps(np.array([[0.0, 0.0, 0.0], [5.0, 3.0, 1.0]], np.float32), w.r, w.levels)
+    nr, orr = _ranges(nv, w)
+    g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), orr, flags)
+    for l in range(w.levels):
+        dims, A = nv.bbs_pose_grid(dm, s, nr, nv.make_opts(flags=flags), l)
+        assert dims["N"] == g.N(l)
+        idx = np.arange(len(A)) if len(A) <= 60000 else np.random.default_rng(l).choice(len(A), 60000, replace=False)
+        na, nb, ng = g.N(l)
+        want = np.array([g.rotation(l, t // (nb * ng), (t // ng) % nb, t % ng) for t in idx])
+        bad = np.nonzero((A[idx].view(np.uint32) != want.view(np.uint32)).any(axis=1))[0]
+        assert len(bad) == 0, (l, idx[bad[:5]], A[idx[bad[:5]]], want[bad[:5]])
+
+
 # ---- scores ----------------------------------------------------------------
 
 def _random_nodes(g, rng, n, levels, tmin=-3, tmax=45):

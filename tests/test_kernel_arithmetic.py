@@ -24,15 +24,17 @@ def _lut_entry(v):
 
 
 def test_child_counter_words():
-    """Summing the counter increments of up to 8 points (one run of one
-    thread) never carries between 4-bit counters, and (acc >> 4 k) &
-    0x000F000F gives the counts of children (jx, jz) = (k & 1, k >> 1) with
-    jy = 0 in the low and jy = 1 in the high 16-bit half, for every mix of
-    masks (random mixes, and the all-ones worst case)."""
+    """Summing the counter increments of up to 10 points (one run of one
+    scoring thread: at most ceil(1024 / 224) = 5 pairs of a 2048-point chunk)
+    never carries between 4-bit counters, and (acc >> 4 k) & 0x000F000F gives
+    the counts of children (jx, jz) = (k & 1, k >> 1) with jy = 0 in the low
+    and jy = 1 in the high 16-bit half, for every mix of masks (random mixes,
+    and the all-ones worst case)."""
+    assert 2 * -(-(2048 // 2) // 224) == 10
     rng = np.random.default_rng(1)
     for trial in range(3000):
-        n = int(rng.integers(1, 9))
-        vs = [255] * 8 if trial == 0 else [int(x) for x in rng.integers(0, 256, n)]
+        n = int(rng.integers(1, 11))
+        vs = [255] * 10 if trial == 0 else [int(x) for x in rng.integers(0, 256, n)]
         acc = sum(_lut_entry(v) for v in vs)
         assert acc < 1 << 32
         for k in range(4):
