@@ -505,11 +505,6 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
         int32_t sid, c;
         if (cur < end && slice_chunk(P, cur, sid, c)) stage(sid, c);
     }
-    // Thread t takes the pairs whose index in the CTA's stream of pairs (all
-    // its runs in order) is t modulo NCONS, so every thread scores within one
-    // pair of its share whatever the runs' lengths.  g0 = that stream's length
-    // modulo NCONS before the current run.
-    int g0 = 0;
     for (int round = 0;; ++round) {
         const int b = round & 1;
         bar_sync(BAR_FULL + b, 256);   // the describing warp filled buffer b
@@ -528,31 +523,29 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
             const Row2 r2{d.a[6], d.a[7], d.a[8]};
             const int n = min(PCHUNK, S.K - d.c * PCHUNK);
             const int jlo = d.b0 * (PBLK / 2), jhi = min(d.b1 * (PBLK / 2), (n + 1) >> 1);
-            const int t = tid >= g0 ? tid - g0 : tid - g0 + NCONS;   // this run's first pair is jlo + t
-            g0 = (g0 + max(jhi - jlo, 0)) % NCONS;
             uint32_t acc = 0;   // 4-bit child counters (child_lut_entry)
             if (BYTES) {   // every level of every search is a byte grid: only its path is compiled
                 if (d.inside)
                     score_run<LAYOUT_BYTES, true>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1],
-                                                  d.kc[2], lut, acc, t, NCONS);
+                                                  d.kc[2], lut, acc, tid, NCONS);
                 else
                     score_run<LAYOUT_BYTES>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
-                                            acc, t, NCONS);
+                                            acc, tid, NCONS);
             } else if (Lv.layout == LAYOUT_BYTES && d.inside)
                 score_run<LAYOUT_BYTES, true>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2],
-                                              lut, acc, t, NCONS);
+                                              lut, acc, tid, NCONS);
             else if (Lv.layout == LAYOUT_BYTES)
                 score_run<LAYOUT_BYTES>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
-                                        acc, t, NCONS);
+                                        acc, tid, NCONS);
             else if (Lv.layout == LAYOUT_DENSE)
                 score_run<LAYOUT_DENSE>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
-                                        acc, t, NCONS);
+                                        acc, tid, NCONS);
             else if (Lv.layout == LAYOUT_COMPACT)
                 score_run<LAYOUT_COMPACT>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
-                                          acc, t, NCONS);
+                                          acc, tid, NCONS);
             else
                 score_run<LAYOUT_WIDE>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
-                                       acc, t, NCONS);
+                                       acc, tid, NCONS);
             // word k: children (jx, jz) = (k & 1, k >> 1), jy = 0 low and jy = 1 high;
             // 16-bit fields: at most 10 points per thread x 32 lanes, x 7 warps, per field
             uint32_t e0 = acc & 0x000F000Fu, o0 = (acc >> 4) & 0x000F000Fu;
