@@ -32,7 +32,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "candidate-pose point-probes/sec and ms-to-optimum per scan (batched vs plain, same GPU)"
-ALG_OPS_PER_UNIT = 32
+# Algorithmic work of Eq. (11): per probe (one scan point x one rotational
+# child, which answers its 8 translational children) 3 translation adds and
+# 8 child counts; per rotated scan point 9 products, 6 sums and 3 floors
+# (with the level shift) -- once per point for all tasks that share a rotation
+OPS_PER_PROBE = 11
+OPS_PER_ROTATION = 18
 WORKLOAD = "indoor"
 
 
@@ -515,7 +520,8 @@ def run_outdoor(nv, torch, stream, nsm=152, gather_gbs=None, n_scans=4, reps=2):
     kms = sum(r.score_ms for r in kres)
     kc = clk.summary() or {}
     roof = _roofline(sum(r.gathers for r in kres) / (kms / 1e3) if kms > 0 else 0.0, kms,
-                     sum(r.score_launches for r in kres), kc.get("sm_mhz") or 2070.0, nsm, "outdoor", gather_gbs)
+                     sum(r.score_launches for r in kres), kc.get("sm_mhz") or 2070.0, nsm, "outdoor", gather_gbs,
+                     rot_per_unit=sum(r.rotations for r in kres) / max(1, sum(r.gathers for r in kres)))
     return {"roofline": roof,
             "workload": f"outdoor city 800x800x40 m, {len(m) / 1e6:.1f} M map points, r={w.r} m, {w.levels} levels; "
                         f"{n_scans} scans of ~{statistics.mean(len(s_) for s_ in scans):.0f} points",
@@ -627,9 +633,10 @@ def _profile_kv(workload=WORKLOAD):
     return out
 
 
-def _by_launch_size(log, peak_gops):
+def _by_launch_size(log, peak_gops, ops_per_unit):
     """The scoring launches split at their median size: units, device time and
-    the ALU fraction of the smaller and the larger half."""
+    the ALU fraction of the smaller and the larger half (ops per unit: the
+    run's average, the launch log holds units only)."""
     if not log:
         return None
     log = sorted(log)
@@ -639,29 +646,33 @@ def _by_launch_size(log, peak_gops):
         u = sum(x for x, _ in part)
         t = sum(y for _, y in part)
         out[name] = {"launches": len(part), "units_mean": u / len(part) if part else None, "ms": t,
-                     "frac": (u / (t / 1e3) * ALG_OPS_PER_UNIT / 1e9) / peak_gops if t > 0 else None}
+                     "frac": (u / (t / 1e3) * ops_per_unit / 1e9) / peak_gops if t > 0 else None}
     return out
 
 
-def _roofline(units_per_s, score_ms, launches, sm_mhz, nsm, workload, gather_peak_gbs=None):
+def _roofline(units_per_s, score_ms, launches, sm_mhz, nsm, workload, gather_peak_gbs=None, rot_per_unit=1.0):
     """The scoring kernel's roofline.  Bound: ALU issue (L1 serves most of its
-    probes).  Algorithmic work per unit (one scan point x one rotational
-    child, which answers its 8 translational children): 15 FP32 ops of the
-    rotation, 3 floors, 3 shifts + 3 adds to the level key, 8 membership
-    accumulations = 32 ops; peak: SMs x 128 INT32/FP32 lanes x the SM clock
-    sampled during the timed region.  The L2 and L1 sector rates come from
-    the committed ncu capture of the same kernel source (sectors and duration
-    of the captured launches), the L2 peak from this run's random-gather
+    probes).  Algorithmic work: OPS_PER_PROBE per unit (one scan point x one
+    rotational child, which answers its 8 translational children) plus
+    OPS_PER_ROTATION per rotated scan point, counted as the kernel rotates
+    them (once per run of tasks that share a rotation: rot_per_unit rotated
+    points per unit); peak: SMs x 128 INT32/FP32 lanes x the SM clock sampled
+    during the timed region.  The L2 and L1 sector rates come from the
+    committed ncu capture of the same kernel source (sectors and duration of
+    the captured launches), the L2 peak from this run's random-gather
     plateau."""
     alu_peak = nsm * 128 * sm_mhz * 1e6 / 1e9          # Gop/s
-    achieved = units_per_s * ALG_OPS_PER_UNIT / 1e9
+    ops_per_unit = OPS_PER_PROBE + OPS_PER_ROTATION * rot_per_unit
+    achieved = units_per_s * ops_per_unit / 1e9
     kv = _profile_kv(workload)
     out = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gop/s", "frac": achieved / alu_peak,
            "traffic": kv.get("dram_bytes_per_launch"),
            "kernel": "branch3_kernel (fused branch + Eq. (11) scoring)",
-           "algorithmic_ops": f"{ALG_OPS_PER_UNIT} per scan point per rotational child "
-                              "(rotation 15, floor 3, level key 6, 8 child counts)",
-           "units_per_s": units_per_s, "launches": launches, "kernel_ms": score_ms,
+           "algorithmic_ops": f"{OPS_PER_PROBE} per scan point per rotational child (3 translation adds, 8 child "
+                              f"counts) + {OPS_PER_ROTATION} per rotated scan point (9 products, 6 sums, 3 floors); "
+                              f"{rot_per_unit:.4f} rotated points per unit here: {ops_per_unit:.2f} per unit",
+           "units_per_s": units_per_s, "rotated_points_per_unit": rot_per_unit, "launches": launches,
+           "kernel_ms": score_ms,
            "peak_source": f"{nsm} SMs x 128 lanes x {sm_mhz:.0f} MHz (median SM clock in the timed region)"}
     dur = kv.get("duration_us_per_launch")
     if dur:
@@ -777,6 +788,7 @@ def run_ours(a):
     score_ms = sum(r["score_ms"] for r in kres)
     score_launches = sum(r["score_launches"] for r in kres)
     gathers = sum(r["gathers"] for r in kres)
+    rotations = sum(r["rotations"] for r in kres)
 
     # ---- timed: host buffers through the same C-ABI call ------------------
     e2e_ms = []
@@ -805,8 +817,10 @@ def run_ours(a):
     gb = 1 << 27
     peak_ms = min(nv.bbs_bench_gather(max(table_bytes, 1 << 22), gb, stream.cuda_stream) for _ in range(3))
     gather_gbs = gb * 32 / peak_ms / 1e6
-    roofline = _roofline(units_per_s, score_ms, score_launches, sm_mhz, nsm, a.workload, gather_gbs)
-    roofline["by_launch_size"] = _by_launch_size(launch_log, roofline["peak"])
+    roofline = _roofline(units_per_s, score_ms, score_launches, sm_mhz, nsm, a.workload, gather_gbs,
+                         rot_per_unit=rotations / gathers if gathers else 1.0)
+    roofline["by_launch_size"] = _by_launch_size(launch_log, roofline["peak"],
+                                                 OPS_PER_PROBE + OPS_PER_ROTATION * roofline["rotated_points_per_unit"])
 
     # ---- reduce over ranks ----------------------------------------------------
     total_ms, e2e_total, probes_all, e2e_probes_all = reduce_over_ranks(torch, ws, total_ms, e2e_total, probes,

@@ -152,6 +152,10 @@ typedef struct {
     int64_t children_scored;
     int64_t bound_violations;
     double  bound_excess;
+    /* scan points the scoring kernel rotated: the tasks of a run share one
+     * rotation (one evaluation of Eq. (11)'s R s per point for the run);
+     * gathers / rotations is the average number of tasks sharing one */
+    int64_t rotations;
 } bbs_result;
 
 /* bbs_pose_matrix -- the rigid transform of a result pose (x, y, z, roll,

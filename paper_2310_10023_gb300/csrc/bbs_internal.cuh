@@ -599,7 +599,7 @@ void default_ranges(const bbs_maps* m, bbs_ranges* rg);
 // Per-call scan + grid state on the device.
 // Scan points staged per CTA by the scoring kernel; the scan's chunk boxes
 // are kept at this granularity.
-constexpr int SCAN_CHUNK = 2048;
+constexpr int SCAN_CHUNK = 1568;
 
 struct ScanState {
     float4* scan;      // K points, w = 0

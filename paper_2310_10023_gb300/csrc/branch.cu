@@ -3,59 +3,35 @@
 //
 // Work: every rotational child ("task") of every parent of a launch, over
 // every point of its search's scan.  The launch's work is cut into slices
-// (task, block of PBLK points) and each CTA of one resident wave takes an
+// (task, chunk of PCHUNK points) and each CTA of one resident wave takes an
 // equal contiguous range of them, so the SMs finish together whatever the mix
-// of parents.  For each task, every thread rotates its points (FP32, fixed
-// order, no FMA), floors them exactly, and makes ONE brick probe per point
-// that answers all 8 translational children 2c + j (Sec. III-C layout, see
-// bbs_internal.cuh).  The 8 child counts are kept as two byte-packed
-// registers (4 counts each), reduced per warp with redux.sync on 16-bit
-// fields, summed across warps in shared memory, and added to a dense
-// (task, child) score array.  The survivor pass then keeps children scoring
-// above their search's best.
+// of parents.  Consecutive tasks that share their rotation (the engine orders
+// a round's tasks by rotation) form runs: every scoring thread rotates its
+// points of the chunk once per run (FP32, fixed order, no FMA), floors them
+// exactly into level-key patterns, and then makes ONE byte probe per point
+// and task that answers all 8 translational children 2c + j (Sec. III-C
+// layout, see bbs_internal.cuh), the task's translation being an integer
+// offset of the key.  The 8 child counts are kept as 4-bit fields of one
+// register, reduced per warp with redux.sync on 16-bit fields, summed across
+// warps in shared memory, and added to a dense (task, child) score array.
+// The survivor pass then keeps children scoring above their search's best.
 #include "branch.cuh"
 
 namespace bbs {
 
 namespace {
 
-// Paired FP32 arithmetic (sm_100+ f32x2): each lane of a pair is an IEEE
-// FP32 operation with its own rounding, exactly the scalar result, two points
-// per instruction.
-typedef unsigned long long f2;
-__device__ __forceinline__ f2 pk2(float a, float b)
+// The rotated coordinate of Eq. (11), q_i = (A_i0 x + A_i1 y) + A_i2 z, with
+// every product and sum rounded to FP32 on its own as the oracle does.
+// Scalar IEEE operations with explicit rounding: the compiler neither
+// contracts nor reorders them.  (Paired f32x2 multiplies and adds are not
+// used: measured on this part, the compiler fuses them into FMAs whatever
+// their rounding modifier and -fmad=false, which moves about a third of the
+// q values by an ulp and, rarely, a floor across an integer.)
+__device__ __forceinline__ float rot_q(const float* a, float x, float y, float z)
 {
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
+    return __fadd_rn(__fadd_rn(__fmul_rn(a[0], x), __fmul_rn(a[1], y)), __fmul_rn(a[2], z));
 }
-__device__ __forceinline__ void up2(f2 v, int32_t& a, int32_t& b) { asm("mov.b64 {%0, %1}, %2;" : "=r"(a), "=r"(b) : "l"(v)); }
-__device__ __forceinline__ f2 mul2(f2 a, f2 b)
-{
-    f2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 add2(f2 a, f2 b)
-{
-    f2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-// fl_rd(a * b + c) per lane, one rounding of the exact value
-__device__ __forceinline__ f2 fma2rm(f2 a, f2 b, f2 c)
-{
-    f2 d;
-    asm("fma.rm.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-
-struct Row2 {
-    f2 x, y, z;
-};
-
-// ((a0 x + a1 y) + a2 z) for two points, the scalar order and rounding
-__device__ __forceinline__ f2 rot2(const Row2& r, f2 X, f2 Y, f2 Z) { return add2(add2(mul2(r.x, X), mul2(r.y, Y)), mul2(r.z, Z)); }
 
 // Bit pattern of a floored key: for the per-axis constant C = 1.5 * 2^23 + d
 // (d an integer, |d| < 2^21), fl_rd(q * 2^-m + C) rounds the exact value once,
@@ -63,6 +39,9 @@ __device__ __forceinline__ f2 rot2(const Row2& r, f2 X, f2 Y, f2 Z) { return add
 // the level-m key of Eq. (11), offset by d, in the low 22 bits.  Outside that
 // range the pattern leaves [KB, KB + 2^22) and fails every range check below.
 constexpr uint32_t KB = 0x4B400000u;   // bit pattern of 1.5 * 2^23
+// the bit pattern of fl_rd(q * s + c): with s = 2^-m and c = 1.5 * 2^23 + d,
+// KB + floor(q / 2^m) + d
+__device__ __forceinline__ uint32_t key_bits(float q, float s, float c) { return __float_as_uint(__fmaf_rd(q, s, c)); }
 
 // the 8 child bits of one point from the bit patterns of its level-m key,
 // offset so that the key block (kx, ky, kz) + {0,1}^3 is relative to the
@@ -108,21 +87,19 @@ __device__ __forceinline__ void child_bits(const LevelView& L, uint32_t bx, uint
 }
 
 // Child counters: one 4-bit counter per translational child in one 32-bit
-// word, child i = jx + 2 jy + 4 jz at bit 4 (jx + 2 jz) + 16 jy, so that
-// (acc >> 4 k) & 0x000F000F holds the children (jx, jz) = (k & 1, k >> 1)
-// with jy = 0 and jy = 1 in its two 16-bit halves.  A point adds
-// CHILD_LUT[v] for its 8-bit child mask v (one shared-memory load and one
-// add).  A scoring thread counts at most 10 points of a run (a run is at
-// most PCHUNK points over 224 threads, two points per pair), so no counter
-// passes 15.
+// word, child i = jx + 2 jy + 4 jz (bit i of a byte grid's child mask) at
+// bits 4i .. 4i + 3.  A point adds CHILD_LUT[v] for its 8-bit child mask v
+// (one shared-memory load and one add).  A scoring thread counts at most
+// PPT = 7 points of a task (a chunk is PCHUNK = 7 x 224 points), so no
+// counter passes 7, and the even and the odd children's counters, spread to
+// bytes, sum over a warp's 32 lanes to at most 224 per byte.
 __host__ __device__ constexpr uint32_t child_lut_entry(uint32_t v)
 {
-    return ((v & 1u) << 0) | (((v >> 1) & 1u) << 4) | (((v >> 2) & 1u) << 16) | (((v >> 3) & 1u) << 20) |
-           (((v >> 4) & 1u) << 8) | (((v >> 5) & 1u) << 12) | (((v >> 6) & 1u) << 24) | (((v >> 7) & 1u) << 28);
+    return ((v & 1u) << 0) | (((v >> 1) & 1u) << 4) | (((v >> 2) & 1u) << 8) | (((v >> 3) & 1u) << 12) |
+           (((v >> 4) & 1u) << 16) | (((v >> 5) & 1u) << 20) | (((v >> 6) & 1u) << 24) | (((v >> 7) & 1u) << 28);
 }
 // the scoring CTA: warps 0..6 score (NCONS threads), warp 7 describes the rounds
 constexpr int NCONS = 224;
-static_assert(2 * ((PCHUNK / 2 + NCONS - 1) / NCONS) <= 15, "4-bit child counters hold the points of one run per thread");
 
 // The 8-bit child mask of one point from a byte grid (LAYOUT_BYTES): relative
 // keys clamped to the empty key past the box, one byte load.
@@ -132,17 +109,6 @@ __device__ __forceinline__ uint32_t bytes_mask(const LevelView& L, uint32_t bx, 
     const uint32_t rx = min(bx ^ KB, ex), ry = min(by ^ KB, ey), rz = min(bz ^ KB, ez);
     return __ldg(reinterpret_cast<const uint8_t*>(L.slots) + ((rx * L.nby + ry) * L.nbz + rz));
 }
-// The same for a run whose every point is known to land inside the grid (the
-// chunk-box test of the run): no per-axis clamp, and the -KB of the three
-// patterns folded into one constant, cfix = -KB (ny nz + nz + 1) mod 2^32 --
-// the index is exact because its true value is below 2^31.  One min against
-// the last cell (L.mask) keeps every load inside the grid whatever the test.
-__device__ __forceinline__ uint32_t bytes_mask_inside(const LevelView& L, uint32_t bx, uint32_t by, uint32_t bz,
-                                                      uint32_t cfix)
-{
-    const uint32_t idx = min((bx * L.nby + by) * L.nbz + bz + cfix, L.mask);
-    return __ldg(reinterpret_cast<const uint8_t*>(L.slots) + idx);
-}
 // the 8-bit child mask from the two plane words of the brick layouts
 // (bits {0, 1, 5, 6}: children jx + 5 jy of the z = 0 and z = 1 planes)
 __device__ __forceinline__ uint32_t planes_mask(uint32_t w0, uint32_t w1)
@@ -150,44 +116,31 @@ __device__ __forceinline__ uint32_t planes_mask(uint32_t w0, uint32_t w1)
     return (w0 & 3u) | ((w0 >> 3) & 0xCu) | ((w1 & 3u) << 4) | ((w1 << 1) & 0xC0u);
 }
 
-// One run (a rotational child over blocks of the staged chunk), two points
-// per step.  The chunk is staged as pairs: sxy[j] = (x_2j, x_2j+1, y_2j,
-// y_2j+1) and sz[j] = (z_2j, z_2j+1), so each coordinate pair is one 64-bit
-// register for the f32x2 operations; thread t of the nt scoring threads takes
-// pairs jlo + t, jlo + t + nt, ... below jhi.  q = (A_i0 x + A_i1 y) + A_i2 z is rounded to FP32
-// after every product and sum (no FMA), as the oracle; the floor, the level
-// shift and the key offset are one fma.rm of that q (see KB).
-template <int LAYOUT, bool INSIDE = false>
-__device__ __forceinline__ void score_run(const ulonglong2* sxy, const f2* sz, int n, int jlo, int jhi,
-                                          const LevelView& L, const Row2& r0, const Row2& r1, const Row2& r2, f2 S,
-                                          f2 Cx, f2 Cy, f2 Cz, const uint32_t* lut, uint32_t& acc, int t, int nt)
+// One task over points [plo, phi) of the staged chunk (the clamped path:
+// every point rotated and floored with the task's own offsets); thread t of
+// the nt scoring threads takes points plo + t, plo + t + nt, ...  The floor,
+// the level shift and the key offset are one fma.rm of q (see KB).
+template <int LAYOUT>
+__device__ __forceinline__ void score_run(const float4* sp, int plo, int phi, const LevelView& L, const float (&A)[9],
+                                          float s, float cx, float cy, float cz, const uint32_t* lut, uint32_t& acc,
+                                          int t, int nt)
 {
     const uint32_t ex = L.rmax[0] + 1u, ey = L.rmax[1] + 1u, ez = L.rmax[2] + 1u;   // bytes: the empty key past the box
-    const uint32_t cfix = 0u - KB * (L.nby * L.nbz + L.nbz + 1u);
-    auto mask = [&](uint32_t bx, uint32_t by, uint32_t bz) -> uint32_t {
-        if (LAYOUT == LAYOUT_BYTES && INSIDE) return bytes_mask_inside(L, bx, by, bz, cfix);
-        if (LAYOUT == LAYOUT_BYTES) return bytes_mask(L, bx, by, bz, ex, ey, ez);
-        uint32_t w0, w1;
-        child_bits<LAYOUT>(L, bx, by, bz, w0, w1);
-        return planes_mask(w0, w1);
-    };
-    auto pair = [&](int j) {
-        const ulonglong2 xy = sxy[j];
-        const f2 Z = sz[j];
-        int32_t bx1, bx2, by1, by2, bz1, bz2;
-        up2(fma2rm(rot2(r0, xy.x, xy.y, Z), S, Cx), bx1, bx2);
-        up2(fma2rm(rot2(r1, xy.x, xy.y, Z), S, Cy), by1, by2);
-        up2(fma2rm(rot2(r2, xy.x, xy.y, Z), S, Cz), bz1, bz2);
-        acc += lut[mask((uint32_t)bx1, (uint32_t)by1, (uint32_t)bz1)];
-        if (2 * j + 1 < n) acc += lut[mask((uint32_t)bx2, (uint32_t)by2, (uint32_t)bz2)];
-    };
-    int j = jlo + t;
-    if (LAYOUT == LAYOUT_DENSE || LAYOUT == LAYOUT_BYTES)   // two pairs per step: four gathers in flight per thread
-        for (; j + nt < jhi; j += 2 * nt) {
-            pair(j);
-            pair(j + nt);
+    for (int p = plo + t; p < phi; p += nt) {
+        const float4 v4 = sp[p];
+        const uint32_t bx = key_bits(rot_q(A, v4.x, v4.y, v4.z), s, cx);
+        const uint32_t by = key_bits(rot_q(A + 3, v4.x, v4.y, v4.z), s, cy);
+        const uint32_t bz = key_bits(rot_q(A + 6, v4.x, v4.y, v4.z), s, cz);
+        uint32_t v;
+        if (LAYOUT == LAYOUT_BYTES) {
+            v = bytes_mask(L, bx, by, bz, ex, ey, ez);
+        } else {
+            uint32_t w0, w1;
+            child_bits<LAYOUT>(L, bx, by, bz, w0, w1);
+            v = planes_mask(w0, w1);
         }
-    for (; j < jhi; j += nt) pair(j);
+        acc += lut[v];
+    }
 }
 
 // the segment holding launch-local slice w (segments in slice order)
@@ -222,88 +175,83 @@ __device__ __forceinline__ void virtual_parent(const SearchDev& S, int64_t vp, i
     px = S.pmin[0] + (int32_t)(vp / ((int64_t)S.pext[2] * S.pext[1]));
 }
 
-// Whether every point of run d lands inside its level's byte grid L.  The
-// key of axis i is floor(q_i / 2^m) + o_i (o_i = t_i - base_i, the run's key
-// offset) with q_i the FP32 value of sum_k A_ik x_k.  Over the chunk's box
-// the exact sum lies in [lo, hi] (per term the smaller and larger of the
-// corner products).  Here lo and hi are formed in FP32 (three products, two
-// sums: within 3u / (1 - 3u) of mag = sum_k |A_ik| max |x_k|, u = 2^-24), and
-// each point's FP32 q_i lies within as much again of its exact value, so
-// widening by 2e-6 mag (which also covers the rounding of mag and of the
-// widening) bounds every q_i.  Inside: every key in [0, rmax_i + 1].  A
-// clamped offset (|o| = 2^21) never passes.  FP32 throughout: FP64 runs at a
-// small fraction of the FP32 rate on this part.
-template <typename RD>
-__device__ __forceinline__ bool run_inside(const RD& d, const float4* __restrict__ box, const LevelView& L)
+// The key bounds of a chunk under rotation rows A at level m: for every
+// point of the chunk and axis i, klo_i <= floor(q_i / 2^m) <= khi_i, with q_i
+// the FP32 value of sum_k A_ik x_k (the translation is added to the key
+// afterwards, exactly).  Over the chunk's box the exact sum lies in [lo, hi]
+// (per term the smaller and larger of the corner products).  Here lo and hi
+// are formed in FP32 (three products, two sums: within 3u / (1 - 3u) of mag =
+// sum_k |A_ik| max |x_k|, u = 2^-24), and each point's FP32 q_i lies within
+// as much again of its exact value, so widening by 2e-6 mag (which also
+// covers the rounding of mag and of the widening) bounds every q_i.  The
+// floors are exact integers (|q / 2^m| <= 2^18 by the scan bound).  FP32
+// throughout: FP64 runs at a small fraction of the FP32 rate on this part.
+__device__ __forceinline__ void chunk_key_bounds(const float A[9], const float4* __restrict__ box, int m,
+                                                 float klo[3], float khi[3])
 {
     const float4 blo = __ldg(box), bhi = __ldg(box + 1);
     const float lo3[3] = {blo.x, blo.y, blo.z}, hi3[3] = {bhi.x, bhi.y, bhi.z};
-    const float s = __int_as_float((127 - d.m) << 23);   // 2^-m
-    bool in = true;
+    const float s = __int_as_float((127 - m) << 23);   // 2^-m
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         float qlo = 0.0f, qhi = 0.0f, mag = 0.0f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float a = __int_as_float((int)(uint32_t)d.a[3 * i + k]);
+            const float a = A[3 * i + k];
             const float p1 = __fmul_rn(a, lo3[k]), p2 = __fmul_rn(a, hi3[k]);
             qlo = __fadd_rn(qlo, fminf(p1, p2));
             qhi = __fadd_rn(qhi, fmaxf(p1, p2));
             mag = __fadd_rn(mag, __fmul_rn(fabsf(a), fmaxf(fabsf(lo3[k]), fabsf(hi3[k]))));
         }
         const float marg = __fadd_rn(__fmul_rn(2e-6f, mag), 1e-30f);
-        const float o = __int_as_float((int)(uint32_t)d.kc[i]) - 12582912.0f;
-        in = in && floorf(__fmul_rn(__fsub_rn(qlo, marg), s)) + o >= 0.0f &&
-             floorf(__fmul_rn(__fadd_rn(qhi, marg), s)) + o <= (float)L.rmax[i] + 1.0f;
+        klo[i] = floorf(__fmul_rn(__fsub_rn(qlo, marg), s));
+        khi[i] = floorf(__fmul_rn(__fadd_rn(qhi, marg), s));
     }
-    return in;
 }
 
-// A run: one task over blocks [b0, b1) of point chunk c, described in shared
-// memory for the whole CTA.
+// A run: consecutive slices of one round that score one chunk of one
+// search's scan under one rotation (tasks sharing their rotational child,
+// translations apart), described in shared memory for the whole CTA.  The
+// scoring threads rotate their points of the chunk once per run and probe
+// once per point and task.
 struct __align__(16) RunDesc {
-    f2 a[9];          // rotation entries A_ik, each duplicated for the paired lanes
-    f2 kc[3];         // per-axis 1.5 * 2^23 + translation (- box origin), paired
-    f2 s;             // 2^-m, paired
+    float a[9];       // rotation entries A_ik
+    float s;          // 2^-m
     int32_t m;        // child level
     int32_t c;        // point chunk
-    int32_t b0, b1;   // PBLK-point blocks [b0, b1) of the chunk
     int32_t sid;      // search
-    int32_t inside;   // every point of the run lands inside the level's byte grid
-    int64_t task;     // launch-local task index
+    int32_t first;    // the run's slices: slots [first, first + n) of the round
+    int32_t n;
+    int32_t pad[2];
 };
 
-constexpr int NRUN = 32;   // runs described per round of a CTA
+// One slice of a round: a task over its run's chunk.
+struct __align__(16) SlotDesc {
+    float kc[3];      // per-axis 1.5 * 2^23 + translation (- box origin) (the clamped path)
+    uint32_t pad;
+    int64_t task;     // launch-local task index
+    uint32_t delta;   // byte grids: index offset of the translation, with the folded pattern constant
+    int32_t inside;   // every point of the chunk lands inside the level's byte grid
+};
+
+constexpr int NSLOT = 32;   // slices per round, one per lane of the describing warp
 
 }  // namespace
-
-// The rotation rows (A = fl32(R / r)) of one run's task, from its rl, into
-// the run's descriptor (kept out of line: the scoring loop keeps its
-// registers; the describing warp forms one run per lane).  FP32 double-float
-// arithmetic gives the rows' exact bits but for rare entries near a rounding
-// boundary (or out of its range), which take the FP64 formation.
-__device__ __noinline__ void run_rows(RunDesc& d, uint32_t rl, const SearchDev& S)
-{
-    float A[9];
-    search_rows(S.cs, S.grid, rl_level(rl), rl_rot(rl), A);
-#pragma unroll
-    for (int e = 0; e < 9; ++e) d.a[e] = pk2(A[e], A[e]);
-}
 
 // named barriers of the scoring CTA (0 is __syncthreads): the describing
 // warp fills round buffer b and arrives on FULL + b; the scoring warps wait
 // there, score, and arrive on EMPTY + b when they no longer read the buffer;
 // CONS synchronizes the scoring warps alone
 constexpr int BAR_FULL = 1, BAR_EMPTY = 3, BAR_CONS = 5;
-constexpr int64_t SMALL_LAUNCH = 256;   // slices per CTA below which a launch is split statically
+constexpr int64_t SMALL_LAUNCH = 0;    // slices per CTA below which a launch is split statically
 __device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 __device__ __forceinline__ void bar_arrive(int id, int n) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
 // The CTA's static range [cur, end) of the launch's slices: the first
 // static_pm / 1000 of them in equal shares, the rest handed out later in
 // shrinking grabs.  A launch of fewer than SMALL_LAUNCH slices per CTA (about
-// one round each) is split statically: there a grab's round costs more than
-// the balance it buys (measured, indoor).
+// two rounds each) is split statically: there a grab's round costs more than
+// the balance it buys.
 __device__ __forceinline__ int64_t static_slices(const Plan* P, int64_t n_slices)
 {
     return n_slices < SMALL_LAUNCH * (int64_t)gridDim.x ? n_slices : n_slices * P->static_pm / 1000;
@@ -315,19 +263,20 @@ __device__ __forceinline__ bool slice_chunk(const Plan* P, int64_t x, int32_t& s
 {
     const Seg& g = P->seg[find_slice_seg(P, x)];
     if (g.n_tasks <= 0 || x < g.first_slice || x >= g.first_slice + g.n_tasks * g.nblk) return false;
-    const int64_t cc = (x - g.first_slice) / (4 * g.n_tasks);
-    const int nchunk = (g.nblk + 3) >> 2;
     sid = g.sid;
-    c = (int32_t)(cc < nchunk - 1 ? cc : nchunk - 1);
+    c = (int32_t)((x - g.first_slice) / g.n_tasks);
     return true;
 }
 
 // The describing warp of a scoring CTA (out of line: its registers and its
-// FP64 row formation stay out of the scoring warps' allocation).
+// row formation stay out of the scoring warps' allocation).  A round is up to
+// NSLOT consecutive slices of one segment, one per lane; lanes whose slice
+// opens a new chunk or a new rotation lead a run and form its rotation rows
+// and its chunk's key bounds, every lane its task's offsets and inside test.
 template <int MODE>
 __device__ __noinline__ void describe_rounds(Plan* __restrict__ P, const SearchDev* __restrict__ Sall,
-                                             const TaskRec* __restrict__ tasks, RunDesc (*rd)[NRUN], int32_t* s_nrun,
-                                             int64_t n_slices)
+                                             const TaskRec* __restrict__ tasks, RunDesc (*rd)[NSLOT],
+                                             SlotDesc (*sd)[NSLOT], int32_t (*s_cnt)[2], int64_t n_slices)
 {
     const int lane = threadIdx.x & 31;
     // the static range first, then grabs of at least grab_min as CTAs finish
@@ -335,8 +284,18 @@ __device__ __noinline__ void describe_rounds(Plan* __restrict__ P, const SearchD
     const int64_t grab_min = P->grab_min > 0 ? P->grab_min : 1;
     int64_t cur = n_static * blockIdx.x / gridDim.x, end = n_static * (blockIdx.x + 1) / gridDim.x;
     int gi = -1;
-    int round = 0;
-    for (;; ++round) {
+    // scan points rotated for the current search (lane 0), added to its control block on a change of search
+    // (searches scored outside the engine -- bbs_score_children, the host queue -- have none)
+    int rot_sid = -1;
+    unsigned long long rot_pts = 0;
+    auto flush_rot = [&]() {
+        if (lane == 0 && rot_sid >= 0 && rot_pts) {
+            Ctl* c = Sall[rot_sid].ctl;
+            if (c) atomicAdd(&c->st_rotpts, rot_pts);
+        }
+        rot_pts = 0;
+    };
+    for (int round = 0;; ++round) {
         const int b = round & 1;
         if (round >= 2) bar_sync(BAR_EMPTY + b, 256);   // the scoring warps are done with buffer b
         if (cur >= end) {   // this range is done: take the next grab
@@ -356,9 +315,10 @@ __device__ __noinline__ void describe_rounds(Plan* __restrict__ P, const SearchD
             gi = -1;
         }
         if (cur >= end) {   // every slice is handed out: the scoring warps stop
-            if (lane == 0) s_nrun[b] = 0;
+            if (lane == 0) s_cnt[b][0] = 0;
             __syncwarp();
             bar_arrive(BAR_FULL + b, 256);
+            flush_rot();
             if (round >= 1) bar_sync(BAR_EMPTY + (b ^ 1), 256);   // the last round's release
             break;
         }
@@ -370,104 +330,221 @@ __device__ __noinline__ void describe_rounds(Plan* __restrict__ P, const SearchD
             seg_end = g->first_slice + g->n_tasks * g->nblk;
         }
         const int64_t nt = g->n_tasks;
-        const int nchunk = (g->nblk + 3) >> 2;
-        const int nbl = g->nblk - 4 * (nchunk - 1);   // blocks of the last chunk
-        // seg-relative slices: chunk c holds tasks 0..nt-1 of nbc(c) blocks each
+        // seg-relative slices: slice x is task x mod nt over chunk x / nt
         const int64_t x0 = cur - g->first_slice, xh = min(end, seg_end) - g->first_slice;
-        auto tc_of = [&](int64_t x) -> int64_t {   // (chunk * nt + task) of slice x
-            int64_t c = x / (4 * nt);
-            if (c > nchunk - 1) c = nchunk - 1;
-            const int nbc = c < nchunk - 1 ? 4 : nbl;
-            return c * nt + (x - c * 4 * nt) / nbc;
-        };
-        auto tc_first = [&](int64_t v) -> int64_t {   // first slice of (chunk * nt + task) v
-            const int64_t c = v / nt;
-            const int nbc = c < nchunk - 1 ? 4 : nbl;
-            return c * 4 * nt + (v - c * nt) * nbc;
-        };
-        const int64_t v0 = tc_of(x0), vh = tc_of(xh - 1);
-        const int nrun = (int)(vh - v0 + 1 < NRUN ? vh - v0 + 1 : NRUN);
-        const int64_t xe = v0 + nrun <= vh ? tc_first(v0 + nrun) : xh;   // this round ends at slice xe
-        if (lane < nrun) {
-            const SearchDev& S = Sall[g->sid];
-            const int64_t v = v0 + lane;
-            const int64_t c = v / nt, u = v - c * nt;
-            const int nbc = c < nchunk - 1 ? 4 : nbl;
-            const int64_t rs = c * 4 * nt + u * nbc;
-            int m;
-            int32_t tx, ty, tz;
-            RunDesc& d = rd[b][lane];
+        const int cnt = (int)(xh - x0 < NSLOT ? xh - x0 : NSLOT);
+        const bool valid = lane < cnt;
+        const SearchDev& S = Sall[g->sid];
+        int64_t c = -1, u = 0;
+        uint32_t key = 0;   // the slice's rotation: rl, or the top table's index
+        int32_t m = 0, t3[3] = {0, 0, 0};
+        if (valid) {
+            const int64_t x = x0 + lane;
+            c = x / nt;
+            u = x - c * nt;
             if (MODE == MODE_INITIAL) {
-                virtual_parent(S, g->first_parent + u / g->R, tx, ty, tz);
-                tx *= 2;
-                ty *= 2;
-                tz *= 2;
-                const float4* At = S.rot + 3 * (u % g->R);   // the top level's table
-                const float4 a0 = __ldg(At), a1 = __ldg(At + 1), a2 = __ldg(At + 2);
-                d.a[0] = pk2(a0.x, a0.x), d.a[1] = pk2(a0.y, a0.y), d.a[2] = pk2(a0.z, a0.z);
-                d.a[3] = pk2(a1.x, a1.x), d.a[4] = pk2(a1.y, a1.y), d.a[5] = pk2(a1.z, a1.z);
-                d.a[6] = pk2(a2.x, a2.x), d.a[7] = pk2(a2.y, a2.y), d.a[8] = pk2(a2.z, a2.z);
+                // rotation-major: the virtual parents of one rotation are consecutive tasks
+                const int64_t take = nt / g->R;
+                const int64_t ri = u / take;
+                virtual_parent(S, g->first_parent + (u - ri * take), t3[0], t3[1], t3[2]);
+                for (int i = 0; i < 3; ++i) t3[i] *= 2;
+                key = (uint32_t)ri;
                 m = S.lmax;
             } else {
                 const TaskRec tr = tasks[g->first_task + u];
+                key = tr.rl;
                 m = rl_level(tr.rl);
-                tx = tr.tx;
-                ty = tr.ty;
-                tz = tr.tz;
-                run_rows(d, tr.rl, S);
+                t3[0] = tr.tx;
+                t3[1] = tr.ty;
+                t3[2] = tr.tz;
             }
-            const LevelView& L = S.maps[m];
-            const bool cmp = L.layout != LAYOUT_WIDE;
-            const int32_t t3[3] = {tx, ty, tz};
-            for (int i = 0; i < 3; ++i) {
-                // |offset| >= 2^21 puts every point of the run outside the key range
-                // (|floor(q / 2^m)| <= 2^18 by the scan bound), as the clamped one does
-                int32_t o = t3[i] - (cmp ? L.base[i] : 0);
-                o = o > (1 << 21) ? (1 << 21) : (o < -(1 << 21) ? -(1 << 21) : o);
-                const float cf = 12582912.0f + (float)o;   // exact: an integer below 2^24
-                d.kc[i] = pk2(cf, cf);
+        }
+        const int64_t cprev = __shfl_up_sync(0xffffffffu, c, 1);
+        const uint32_t kprev = __shfl_up_sync(0xffffffffu, key, 1);
+        const bool start = valid && (lane == 0 || c != cprev || key != kprev);
+        const uint32_t starts = __ballot_sync(0xffffffffu, start);
+        const uint32_t below = starts & (0xFFFFFFFFu >> (31 - lane));   // run starts at lanes <= lane
+        const int lead = 31 - __clz(below);                             // lane 0 always starts
+        float klo[3] = {0.0f, 0.0f, 0.0f}, khi[3] = {0.0f, 0.0f, 0.0f};
+        if (start) {
+            RunDesc& d = rd[b][__popc(below) - 1];
+            float A[9];
+            if (MODE == MODE_INITIAL) {
+                const float4* At = S.rot + 3 * key;   // the top level's table
+                const float4 a0 = __ldg(At), a1 = __ldg(At + 1), a2 = __ldg(At + 2);
+                A[0] = a0.x, A[1] = a0.y, A[2] = a0.z;
+                A[3] = a1.x, A[4] = a1.y, A[5] = a1.z;
+                A[6] = a2.x, A[7] = a2.y, A[8] = a2.z;
+            } else {
+                search_rows(S.cs, S.grid, m, rl_rot(key), A);
             }
+#pragma unroll
+            for (int e = 0; e < 9; ++e) d.a[e] = A[e];
             const float sc = __int_as_float((127 - m) << 23);   // 2^-m
-            d.s = pk2(sc, sc);
+            d.s = sc;
             d.m = m;
             d.c = (int32_t)c;
             d.sid = g->sid;
-            d.b0 = (int32_t)(max(rs, x0) - rs);
-            d.b1 = (int32_t)(min(rs + nbc, xe) - rs);
-            d.task = g->first_task + u;
-            d.inside = L.layout == LAYOUT_BYTES ? (int32_t)run_inside(d, S.cbox + 2 * c, L) : 0;
+            d.first = lane;
+            const uint32_t above = lane == 31 ? 0u : starts >> (lane + 1);
+            d.n = (above ? __ffs(above) + lane : cnt) - lane;
+            chunk_key_bounds(A, S.cbox + 2 * c, m, klo, khi);
         }
-        if (lane == 0) s_nrun[b] = nrun;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            klo[i] = __shfl_sync(0xffffffffu, klo[i], lead);
+            khi[i] = __shfl_sync(0xffffffffu, khi[i], lead);
+        }
+        bool own = false;   // the slice rotates the chunk on its own (edge or brick layout)
+        if (valid) {
+            const LevelView& L = S.maps[m];
+            const bool cmp = L.layout != LAYOUT_WIDE;
+            SlotDesc& e = sd[b][lane];
+            bool in = L.layout == LAYOUT_BYTES;
+            int32_t o[3];
+            for (int i = 0; i < 3; ++i) {
+                // |offset| >= 2^21 puts every point outside the key range
+                // (|floor(q / 2^m)| <= 2^18 by the scan bound), as the clamped one does
+                int32_t v = t3[i] - (cmp ? L.base[i] : 0);
+                v = v > (1 << 21) ? (1 << 21) : (v < -(1 << 21) ? -(1 << 21) : v);
+                o[i] = v;
+                const float cf = 12582912.0f + (float)v;   // exact: an integer below 2^24
+                e.kc[i] = cf;
+                // inside: every key of the chunk in [0, rmax_i + 1] (sums of integers below 2^24: exact)
+                in = in && klo[i] + (float)v >= 0.0f && khi[i] + (float)v <= (float)L.rmax[i] + 1.0f;
+            }
+            e.task = g->first_task + u;
+            e.inside = in ? 1 : 0;
+            own = !in;
+            // index of key (k + o) = base pattern index (rotate_keys) + delta, mod 2^32:
+            // the offsets' index plus -KB (ny nz + nz + 1), the patterns' constant
+            e.delta = ((uint32_t)o[0] * L.nby + (uint32_t)o[1]) * L.nbz + (uint32_t)o[2] -
+                      KB * (L.nby * L.nbz + L.nbz + 1u);
+        }
+        // scan points rotated by this round: a byte-grid run's shared rotation and every own one
+        const uint32_t owns = __ballot_sync(0xffffffffu, own);
+        uint32_t rp = 0;   // at most NSLOT + 1 rotations of PCHUNK points per round
+        if (start) {
+            const uint32_t above = lane == 31 ? 0u : starts >> (lane + 1);
+            const int nr = (above ? __ffs(above) + lane : cnt) - lane;   // the run's slices
+            const uint32_t rmask = (nr >= 32 ? 0xFFFFFFFFu : ((1u << nr) - 1u)) << lane;
+            const int npts = min(PCHUNK, S.K - (int32_t)c * PCHUNK);
+            const bool shared_rot = S.maps[m].layout == LAYOUT_BYTES;
+            rp = (uint32_t)npts * ((shared_rot ? 1u : 0u) + (uint32_t)__popc(owns & rmask));
+        }
+        rp = __reduce_add_sync(0xffffffffu, rp);
+        if (g->sid != rot_sid) {
+            flush_rot();
+            rot_sid = g->sid;
+        }
+        rot_pts += rp;
+        if (lane == 0) {
+            s_cnt[b][0] = __popc(starts);
+            s_cnt[b][1] = cnt;
+        }
         __syncwarp();
         bar_arrive(BAR_FULL + b, 256);   // buffer b holds the round
-        cur = g->first_slice + xe;
+        cur += cnt;
     }
 }
 
-// Fused branch + score.  The launch's slices (task, PBLK-point block) are
+// points per scoring thread of a chunk: tid + i NCONS, i = 0 .. PPT - 1
+constexpr int PPT = PCHUNK / NCONS;
+static_assert(PPT * NCONS == PCHUNK, "a chunk is PPT points per scoring thread");
+static_assert(PPT * 32 <= 255, "a warp's byte-wide child counts hold one chunk");
+
+// The base indices of this thread's points of the staged chunk under run d's
+// rotation: the floored level-m key patterns (KB + floor(q / 2^m) per axis,
+// see KB) combined as (bx ny + by) nz + bz, mod 2^32.  A task adds its slot's
+// delta: for a task inside the grid the sum is the key's byte index.
+__device__ __forceinline__ void rotate_keys(const float4* sp, const RunDesc& d, const LevelView& L,
+                                            uint32_t (&base)[PPT], int tid)
+{
+    float A[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) A[e] = d.a[e];
+    const float s = d.s, c0 = 12582912.0f;
+    const uint32_t ny = L.nby, nz = L.nbz;
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+        const float4 v = sp[tid + i * NCONS];
+        const uint32_t bx = key_bits(rot_q(A, v.x, v.y, v.z), s, c0);
+        const uint32_t by = key_bits(rot_q(A + 3, v.x, v.y, v.z), s, c0);
+        const uint32_t bz = key_bits(rot_q(A + 6, v.x, v.y, v.z), s, c0);
+        base[i] = (bx * ny + by) * nz + bz;
+    }
+}
+
+// One task inside its byte grid: one byte load per point (the 8 child bits)
+// and one counter increment.  Points i >= nv of this thread lie past the
+// chunk's end (their base indices are stale): their increments are masked
+// off.  The min against the last cell keeps every load inside the grid
+// whatever the inside test.
+template <bool FULL>
+__device__ __forceinline__ uint32_t gather_inside(const uint32_t (&base)[PPT], uint32_t delta, const LevelView& L,
+                                                  const uint32_t* lut, int nv)
+{
+    const uint8_t* __restrict__ cell = reinterpret_cast<const uint8_t*>(L.slots);
+    const uint32_t last = L.mask;
+    uint32_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+        const uint32_t inc = lut[__ldg(cell + min(base[i] + delta, last))];
+        acc += FULL ? inc : (i < nv ? inc : 0u);
+    }
+    return acc;
+}
+
+// One slice near its byte grid's edge: every point rotated and floored with
+// the task's own offsets and clamped per axis.
+__device__ __forceinline__ uint32_t edge_counts(const float4* sp, int n, const LevelView& L, const RunDesc& d,
+                                                const SlotDesc& e, const uint32_t* lut, int tid)
+{
+    float A[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) A[k] = d.a[k];
+    uint32_t acc = 0;
+    score_run<LAYOUT_BYTES>(sp, 0, n, L, A, d.s, e.kc[0], e.kc[1], e.kc[2], lut, acc, tid, NCONS);
+    return acc;
+}
+
+// A thread's 4-bit child counters of one task, summed over the warp: the
+// even children's counters spread to the four bytes of one word, the odd
+// children's to another (at most PPT x 32 = 224 per byte), stored by lane 0
+// in the warp's own two words of the slot (no atomics).
+__device__ __forceinline__ void reduce_counts(uint32_t acc, uint32_t* red2, int lane)
+{
+    const uint32_t ev = __reduce_add_sync(0xffffffffu, acc & 0x0F0F0F0Fu);
+    const uint32_t od = __reduce_add_sync(0xffffffffu, (acc >> 4) & 0x0F0F0F0Fu);
+    if (lane == 0) {
+        red2[0] = ev;
+        red2[1] = od;
+    }
+}
+
+// Fused branch + score.  The launch's slices (task, chunk of the scan) are
 // split into equal contiguous ranges, one per CTA, for the first static_pm
 // per mille, the rest handed out in shrinking grabs.  Warp 7 of a CTA walks
-// its ranges in rounds of at most NRUN runs (maximal pieces of one task over
-// one chunk) and describes each round into one of two buffers (task record,
-// rotation rows, key offsets, the chunk-box test), one run per lane, while
-// warps 0..6 score the round before: staging a chunk of the scan only when
-// the chunk changes, and adding each run's 8 child counts to the dense
-// scores at the round's end.  Describing overlaps scoring, so a round's
-// loads and FP64 row formation no longer stall the scoring warps.
+// its ranges in rounds of at most NSLOT slices and describes each round into
+// one of two buffers -- runs of slices that share a chunk and a rotation
+// (their rows and the chunk's key bounds), and per slice its task's offsets
+// and inside test -- while warps 0..6 score the round before: staging a
+// chunk of the scan only when the chunk changes, rotating their points once
+// per run, probing once per point and slice, and adding each slice's 8 child
+// counts to the dense scores at the round's end.
 template <int MODE, bool BYTES>
 __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
     branch3_kernel(Plan* __restrict__ P, const SearchDev* __restrict__ Sall, const TaskRec* __restrict__ tasks,
                    int32_t* dense)
 {
-    __shared__ ulonglong2 sxy[PCHUNK / 2];
-    __shared__ f2 sz[PCHUNK / 2];
-    __shared__ RunDesc rd[2][NRUN];
-    __shared__ uint32_t red[2][NRUN][4];
+    __shared__ float4 sp[PCHUNK];        // the staged chunk: (x, y, z, 0) per point
+    __shared__ RunDesc rd[2][NSLOT];
+    __shared__ SlotDesc sd[2][NSLOT];
+    __shared__ uint32_t red[2][NSLOT][NCONS / 32][2];   // per slot and scoring warp: even, odd children's byte counts
     __shared__ uint32_t lut[256];   // child counter increments per 8-bit child mask
-    __shared__ int32_t s_nrun[2];
-    const int tid = threadIdx.x, lane = tid & 31;
+    __shared__ int32_t s_cnt[2][2]; // per buffer: runs, slices
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // launch-independent set-up, before waiting on the kernel before
-    for (int i = tid; i < 2 * 4 * NRUN; i += blockDim.x) (&red[0][0][0])[i] = 0u;
     for (int i = tid; i < 256; i += blockDim.x) lut[i] = child_lut_entry((uint32_t)i);
     pdl_wait();   // the round's plan and tasks are written by the kernels before
     pdl_trigger();
@@ -476,25 +553,17 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
     const int64_t n_slices = P->n_slices;
 
     if (tid >= NCONS) {   // the describing warp
-        describe_rounds<MODE>(P, Sall, tasks, rd, s_nrun, n_slices);
+        describe_rounds<MODE>(P, Sall, tasks, rd, sd, s_cnt, n_slices);
         return;
     }
 
     // ---- the scoring warps (threads 0 .. NCONS - 1) -------------------------
-    float* fxy = reinterpret_cast<float*>(sxy);
-    float* fz = reinterpret_cast<float*>(sz);
     int32_t staged_sid = -1, staged_c = -1;   // the chunk in shared memory (the same in every scoring thread)
-    auto stage = [&](int32_t sid, int32_t c) {   // chunk c of search sid's scan, as coordinate pairs
+    auto stage = [&](int32_t sid, int32_t c) {   // chunk c of search sid's scan
         const SearchDev& S = Sall[sid];
         const int32_t k0 = c * PCHUNK;
         const int32_t n = min(PCHUNK, S.K - k0);
-        for (int i = tid; i < n; i += NCONS) {
-            const float4 p = __ldg(S.scan + k0 + i);
-            const int j = i >> 1, h = i & 1;
-            fxy[4 * j + h] = p.x;
-            fxy[4 * j + 2 + h] = p.y;
-            fz[2 * j + h] = p.z;
-        }
+        for (int i = tid; i < n; i += NCONS) sp[i] = __ldg(S.scan + k0 + i);
         staged_sid = sid;
         staged_c = c;
         bar_sync(BAR_CONS, NCONS);   // staged points visible
@@ -508,7 +577,7 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
     for (int round = 0;; ++round) {
         const int b = round & 1;
         bar_sync(BAR_FULL + b, 256);   // the describing warp filled buffer b
-        const int nrun = s_nrun[b];
+        const int nrun = s_cnt[b][0];
         if (nrun == 0) break;
         for (int r = 0; r < nrun; ++r) {
             const RunDesc& d = rd[b][r];
@@ -518,59 +587,67 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
                 stage(d.sid, d.c);
             }
             const LevelView Lv = S.maps[d.m];
-            const Row2 r0{d.a[0], d.a[1], d.a[2]};
-            const Row2 r1{d.a[3], d.a[4], d.a[5]};
-            const Row2 r2{d.a[6], d.a[7], d.a[8]};
             const int n = min(PCHUNK, S.K - d.c * PCHUNK);
-            const int jlo = d.b0 * (PBLK / 2), jhi = min(d.b1 * (PBLK / 2), (n + 1) >> 1);
-            uint32_t acc = 0;   // 4-bit child counters (child_lut_entry)
-            if (BYTES) {   // every level of every search is a byte grid: only its path is compiled
-                if (d.inside)
-                    score_run<LAYOUT_BYTES, true>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1],
-                                                  d.kc[2], lut, acc, tid, NCONS);
-                else
-                    score_run<LAYOUT_BYTES>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
-                                            acc, tid, NCONS);
-            } else if (Lv.layout == LAYOUT_BYTES && d.inside)
-                score_run<LAYOUT_BYTES, true>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2],
-                                              lut, acc, tid, NCONS);
-            else if (Lv.layout == LAYOUT_BYTES)
-                score_run<LAYOUT_BYTES>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
-                                        acc, tid, NCONS);
-            else if (Lv.layout == LAYOUT_DENSE)
-                score_run<LAYOUT_DENSE>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
-                                        acc, tid, NCONS);
-            else if (Lv.layout == LAYOUT_COMPACT)
-                score_run<LAYOUT_COMPACT>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
-                                          acc, tid, NCONS);
-            else
-                score_run<LAYOUT_WIDE>(sxy, sz, n, jlo, jhi, Lv, r0, r1, r2, d.s, d.kc[0], d.kc[1], d.kc[2], lut,
-                                       acc, tid, NCONS);
-            // word k: children (jx, jz) = (k & 1, k >> 1), jy = 0 low and jy = 1 high;
-            // 16-bit fields: at most 10 points per thread x 32 lanes, x 7 warps, per field
-            uint32_t e0 = acc & 0x000F000Fu, o0 = (acc >> 4) & 0x000F000Fu;
-            uint32_t e1 = (acc >> 8) & 0x000F000Fu, o1 = (acc >> 12) & 0x000F000Fu;
-            e0 = __reduce_add_sync(0xffffffffu, e0);
-            o0 = __reduce_add_sync(0xffffffffu, o0);
-            e1 = __reduce_add_sync(0xffffffffu, e1);
-            o1 = __reduce_add_sync(0xffffffffu, o1);
-            if (lane == 0) {
-                if (e0) atomicAdd(&red[b][r][0], e0);
-                if (o0) atomicAdd(&red[b][r][1], o0);
-                if (e1) atomicAdd(&red[b][r][2], e1);
-                if (o1) atomicAdd(&red[b][r][3], o1);
+            const int t0 = d.first, t1 = d.first + d.n;
+            if (BYTES || Lv.layout == LAYOUT_BYTES) {
+                {   // the slices inside the grid: the run's rotated keys once, one probe per point and slice
+                    uint32_t base[PPT];
+                    rotate_keys(sp, d, Lv, base, tid);
+                    if (n == PCHUNK) {
+                        for (int t = t0; t < t1; ++t) {
+                            const SlotDesc& e = sd[b][t];
+                            if (e.inside) reduce_counts(gather_inside<true>(base, e.delta, Lv, lut, PPT), red[b][t][warp], lane);
+                        }
+                    } else {   // the scan's last chunk: this thread's points below n
+                        const int nv = n > tid ? (n - tid + NCONS - 1) / NCONS : 0;
+                        for (int t = t0; t < t1; ++t) {
+                            const SlotDesc& e = sd[b][t];
+                            if (e.inside) reduce_counts(gather_inside<false>(base, e.delta, Lv, lut, nv), red[b][t][warp], lane);
+                        }
+                    }
+                }
+                for (int t = t0; t < t1; ++t) {   // near the grid's edge: per-axis clamps
+                    const SlotDesc& e = sd[b][t];
+                    if (!e.inside) reduce_counts(edge_counts(sp, n, Lv, d, e, lut, tid), red[b][t][warp], lane);
+                }
+            } else {   // brick layouts: every slice rotates and probes on its own
+                float A[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) A[k] = d.a[k];
+                for (int t = t0; t < t1; ++t) {
+                    const SlotDesc& e = sd[b][t];
+                    uint32_t acc = 0;
+                    if (Lv.layout == LAYOUT_DENSE)
+                        score_run<LAYOUT_DENSE>(sp, 0, n, Lv, A, d.s, e.kc[0], e.kc[1], e.kc[2], lut, acc, tid, NCONS);
+                    else if (Lv.layout == LAYOUT_COMPACT)
+                        score_run<LAYOUT_COMPACT>(sp, 0, n, Lv, A, d.s, e.kc[0], e.kc[1], e.kc[2], lut, acc, tid, NCONS);
+                    else
+                        score_run<LAYOUT_WIDE>(sp, 0, n, Lv, A, d.s, e.kc[0], e.kc[1], e.kc[2], lut, acc, tid, NCONS);
+                    reduce_counts(acc, red[b][t][warp], lane);
+                }
             }
         }
-        bar_sync(BAR_CONS, NCONS);   // every scoring warp's partial sums are in
-        for (int w = tid; w < 4 * nrun; w += NCONS) {
-            // word k of a run: children with jx = k & 1, jz = k >> 1; low half jy = 0, high half jy = 1
-            const int r = w >> 2, k = w & 3;
-            const uint32_t sum = red[b][r][k];
-            if (!sum) continue;
-            red[b][r][k] = 0u;   // zero again before the buffer's next round
-            int32_t* dd = dense + rd[b][r].task * 8 + 4 * (k & 1) + (k >> 1);
-            if (sum & 0xFFFFu) atomicAdd(dd, (int32_t)(sum & 0xFFFFu));
-            if (sum >> 16) atomicAdd(dd + 2, (int32_t)(sum >> 16));
+        bar_sync(BAR_CONS, NCONS);   // every scoring warp's counts are in
+        // Each slot's counts summed over the scoring warps: word k holds the
+        // children i = 2 q + k (q = 0..3) in its bytes; bytes 0, 2 and 1, 3
+        // are summed in 16-bit fields (at most 7 x 224 each).
+        const int nsl = s_cnt[b][1];
+        for (int w = tid; w < 2 * nsl; w += NCONS) {
+            const int t = w >> 1, k = w & 1;
+            uint32_t lo = 0, hi = 0;
+#pragma unroll
+            for (int v = 0; v < NCONS / 32; ++v) {
+                const uint32_t x = red[b][t][v][k];
+                lo += x & 0x00FF00FFu;
+                hi += (x >> 8) & 0x00FF00FFu;
+            }
+            // child i = jx + 2 jy + 4 jz -> dense 4 jx + 2 jy + jz (jx = k)
+            int32_t* dd = dense + sd[b][t].task * 8 + 4 * k;
+            const uint32_t c0 = lo & 0xFFFFu, c2 = hi & 0xFFFFu, c4 = lo >> 16, c6 = hi >> 16;   // i = k + 0, 2, 4, 6
+            if (c0) atomicAdd(dd, (int32_t)c0);       // jy = 0, jz = 0
+            if (c2) atomicAdd(dd + 2, (int32_t)c2);   // jy = 1, jz = 0
+            if (c4) atomicAdd(dd + 1, (int32_t)c4);   // jy = 0, jz = 1
+            if (c6) atomicAdd(dd + 3, (int32_t)c6);   // jy = 1, jz = 1
         }
         bar_arrive(BAR_EMPTY + b, 256);   // buffer b may be refilled
     }
@@ -643,14 +720,17 @@ __global__ void __launch_bounds__(256) finalize_kernel(const Plan* __restrict__ 
             if (MODE == MODE_INITIAL) {
                 const SearchDev& s = S[sid];
                 const int64_t lu = u - g.first_task;
-                virtual_parent(s, g.first_parent + lu / g.R, tx, ty, tz);
+                // rotation-major, as the scoring kernel reads the initial set
+                const int64_t take = g.n_tasks / g.R;
+                const int64_t ri = lu / take;
+                virtual_parent(s, g.first_parent + (lu - ri * take), tx, ty, tz);
                 tx = 2 * tx + (j >> 2);
                 ty = 2 * ty + ((j >> 1) & 1);
                 tz = 2 * tz + (j & 1);
                 valid = tx >= s.wmin[0] && tx <= s.wmax[0] && ty >= s.wmin[1] && ty <= s.wmax[1] && tz >= s.wmin[2] &&
                         tz <= s.wmax[2];
                 m = s.lmax;
-                crot = (uint32_t)(lu % g.R);
+                crot = (uint32_t)ri;
             } else {
                 const TaskRec& tr = tasks[u];
                 m = rl_level(tr.rl);

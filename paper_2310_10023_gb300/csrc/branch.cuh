@@ -9,9 +9,9 @@
 namespace bbs {
 
 constexpr int CH = 256;        // nodes per frontier chunk
-constexpr int PCHUNK = 2048;   // scan points staged in shared memory per CTA
+constexpr int PCHUNK = 1568;   // scan points staged in shared memory per CTA (7 per scoring thread)
 static_assert(PCHUNK == SCAN_CHUNK, "chunk boxes are kept per staged chunk");
-constexpr int PBLK = 512;      // scan points per slice (one point pair per thread of a 256-thread CTA)
+constexpr int PBLK = PCHUNK;   // scan points per slice: a slice is one task over one chunk
 constexpr int MAXSEG = 256;    // task runs per scoring launch
 constexpr int64_t TASK_CAP = (int64_t)1 << 19;   // rotational-child tasks per scoring launch
 
@@ -51,6 +51,7 @@ struct Ctl {
     int64_t st_iters, st_parents, st_nodes, st_gathers;
     unsigned long long st_viol;   // children scoring above their parent (Sec. IV-A's bound check)
     double st_excess;             // sum over them of (child - parent) / child
+    unsigned long long st_rotpts; // scan points the scoring kernel rotated (once per run of a shared rotation)
     unsigned long long t_start_ns, t_match_ns, t_end_ns;   // %globaltimer
 };
 
@@ -63,7 +64,7 @@ struct SearchDev {
     int32_t K;
     int32_t lmax;
     int64_t batch;
-    int32_t nblk;               // PBLK-point blocks of the scan
+    int32_t nblk;               // PCHUNK-point chunks of the scan
     int32_t pad0;
     int32_t pmin[3], pext[3];   // virtual parents of the initial set
     int32_t wmin[3], wmax[3];   // initial translation window, Eq. (3)-(5)
@@ -82,6 +83,24 @@ struct FrontDev {
     NodeRec* nodes[2];
     uint32_t* keys[2];
     int64_t cap;
+};
+
+// Rotation groups of a round that scores in one launch (engine.cu): an
+// open-addressing table over (search, rl) keys whose entry index names the
+// group, per-entry arrays (GROUP_TABLE entries each), and per-search lists
+// of the entries in use and per-parent arrays (TASK_CAP entries each).
+constexpr int64_t GROUP_TABLE = 2 * TASK_CAP;
+constexpr unsigned long long GROUP_EMPTY = ~0ull;
+struct GroupDev {
+    unsigned long long* tab;   // GROUP_TABLE entries: the key (search << 32 | rl), or GROUP_EMPTY
+    uint32_t* cnt;             // per entry: parents joined (zero between rounds)
+    uint32_t* ntask;           // per entry: rotational children of each of its parents
+    int64_t* off;              // per entry: the group's first task
+    uint32_t* np;              // per entry: the group's parents
+    uint32_t* ngrp;            // per search slot: groups created this round
+    uint32_t* list;            // the entries of search s's groups, at poff[s] .. poff[s] + ngrp[s]
+    uint32_t* pslot;           // per parent: its group's entry
+    uint32_t* pidx;            // per parent: its index in the group
 };
 
 // Device state of the iteration loop.
@@ -106,17 +125,18 @@ struct __align__(16) TaskRec {
     uint32_t rl;
 };
 
-// A run of tasks of one search inside a scoring launch.  The run's work is
-// split into slices (task, PBLK-point block of the scan), ordered by point
-// chunk, then task, then block, so that consecutive slices reuse the staged
-// chunk; each CTA of the launch takes an equal contiguous range of slices.
+// A segment: the tasks of one search inside a scoring launch.  Its work is
+// split into slices (task, PCHUNK-point chunk of the scan), ordered by chunk,
+// then task, so that consecutive slices reuse the staged chunk and tasks
+// that share a rotation stay next to each other; each CTA of the launch takes
+// an equal contiguous range of slices.
 struct Seg {
     int64_t first_parent;   // initial set: first virtual parent of the run
     int64_t first_task;     // launch-local index of the run's first task
     int64_t n_tasks;
     int64_t first_slice;    // launch-local index of the run's first slice
     int32_t sid;
-    int32_t nblk;           // PBLK-point blocks of the search's scan
+    int32_t nblk;           // PCHUNK-point chunks of the search's scan
     int32_t R;              // initial set: rotations per virtual parent
     int32_t best;           // the search's best when the launch was planned: survivors score above it
 };
@@ -129,6 +149,7 @@ enum { PLAN_OK = 0, PLAN_EMPTY = 1, PLAN_OVERFLOW = 2, PLAN_SPLIT = 3 };
 struct Plan {
     int64_t n_slices;
     int64_t n_tasks;         // dense child scores: 8 per task, at most 8 * TASK_CAP
+    int64_t n_parents;       // device-planned rounds: the popped parents of every search
     unsigned long long next_slice;   // dynamic share: the next slice not yet handed out (0 at launch)
     int32_t static_pm;       // per-mille of the slices split statically over the CTAs
     int32_t grab_min;        // smallest dynamic grab (slices)
@@ -139,6 +160,7 @@ struct Plan {
     int32_t max_iters;       // the device-driven loop stops after this many
     int32_t grow;            // the round's survivors may not fit the frontier arrays: the host grows
                              // them before the round goes on (compact, score and survivors wait)
+
     Seg seg[MAXSEG];
 };
 

@@ -342,6 +342,7 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
         P->nseg = (int32_t)(cn < MAXSEG ? cn : MAXSEG);
         P->n_slices = cs;
         P->n_tasks = ct;
+        P->n_parents = cp;
         P->next_slice = 0;
         P->static_pm = tune.static_pm;
         P->grab_min = tune.grab_min;
@@ -373,10 +374,11 @@ __global__ void __launch_bounds__(1024) select_kernel(SearchDev* S, int nslots, 
 }
 
 // the tasks (rotational children, Eq. (13)) of parent nd for t in [t0, t1),
-// written at tasks[dst + t]: translation and rl (the scoring kernel forms the rows)
+// written at tasks[dst + t * stride]: translation and rl (the scoring kernel
+// forms the rows)
 __device__ __forceinline__ void write_tasks(const DevGrid& g, const NodeRec& nd, const int32_t lo[3],
                                             const int32_t ext[3], int32_t t0, int32_t t1, TaskRec* tasks, int64_t dst,
-                                            int32_t* tscore, int32_t pscore)
+                                            int32_t* tscore, int32_t pscore, int64_t stride = 1)
 {
     const int l = rl_level(nd.rl);
     const int64_t nb = g.N[l - 1][1], ng = g.N[l - 1][2];
@@ -386,26 +388,162 @@ __device__ __forceinline__ void write_tasks(const DevGrid& g, const NodeRec& nd,
             for (int32_t jg = 0; jg < ext[2]; ++jg, ++t) {
                 if (t < t0 || t >= t1) continue;
                 const uint32_t crot = (uint32_t)(((int64_t)(lo[0] + ja) * nb + (lo[1] + jb)) * ng + (lo[2] + jg));
-                TaskRec& r = tasks[dst + t];
+                const int64_t at = dst + t * stride;
+                TaskRec& r = tasks[at];
                 r.tx = 2 * nd.cx;
                 r.ty = 2 * nd.cy;
                 r.tz = 2 * nd.cz;
                 r.rl = rl_pack(crot, l - 1);
-                tscore[dst + t] = pscore;
+                tscore[at] = pscore;
             }
+}
+
+// ---- rotation groups of a round -------------------------------------------
+//
+// The parents a round pops that share their level and rotation have the
+// same rotational children (Eq. (13)): their tasks share rotations and
+// differ in translation only.  A round that scores in one launch lays its
+// tasks out by group so that the scoring kernel rotates a chunk of the scan
+// once for all tasks of one rotation: group G of a search (P_G parents,
+// T_G rotational children each) holds tasks goff[G] + j P_G + i for child
+// rotation j and the group's parent i.  Groups are found by open addressing
+// over (search, rl) keys, the entry naming the group: compact_kernel joins
+// each parent to its group (one insert and one count per group and warp);
+// group_scan_kernel gives each search's groups their task ranges (in the
+// search's range at toff) and empties their entries; emit_tasks_kernel
+// writes the task records.
+
+__device__ __forceinline__ uint32_t group_hash(unsigned long long key)
+{
+    key ^= key >> 29;
+    key *= 0xBF58476D1CE4E5B9ull;
+    key ^= key >> 32;
+    return (uint32_t)key;
+}
+
+// The table entry of key (search sid, rl) with T rotational children per
+// parent, inserted if absent; the thread that inserts it lists it among the
+// search's groups (list at g0 + ngrp[sid]).  The table has twice the
+// launch's task capacity in entries, a round at most that many parents: an
+// empty entry is always found.  GROUP_TABLE on failure (cannot happen).
+__device__ uint32_t group_entry(const GroupDev& G, int sid, uint32_t rl, int32_t T, int64_t g0)
+{
+    const unsigned long long key = ((unsigned long long)sid << 32) | rl;
+    uint32_t h = group_hash(key) & (uint32_t)(GROUP_TABLE - 1);
+    for (int64_t probe = 0; probe < GROUP_TABLE; ++probe) {
+        unsigned long long v = *(volatile unsigned long long*)&G.tab[h];
+        if (v == GROUP_EMPTY) {
+            v = atomicCAS(&G.tab[h], GROUP_EMPTY, key);
+            if (v == GROUP_EMPTY) {   // this thread created the group
+                G.ntask[h] = (uint32_t)T;
+                const uint32_t k = atomicAdd(&G.ngrp[sid], 1u);
+                if (g0 + k >= TASK_CAP) return (uint32_t)GROUP_TABLE;
+                G.list[g0 + k] = h;
+                return h;
+            }
+        }
+        if (v == key) return h;
+        h = (h + 1) & (uint32_t)(GROUP_TABLE - 1);
+    }
+    return (uint32_t)GROUP_TABLE;
+}
+
+// One CTA per search slot: the task ranges of the search's groups in its
+// range at toff (exclusive scan of P_G T_G in group-id order), the groups'
+// parent counts for the emission, and the table emptied for the next round.
+__global__ void __launch_bounds__(1024) group_scan_kernel(SearchDev* S, int nslots, const Plan* P,
+                                                          const int64_t* __restrict__ poff,
+                                                          const int64_t* __restrict__ toff, GroupDev G)
+{
+    pdl_wait();   // the compaction's groups are in
+    pdl_trigger();
+    if (P->status != PLAN_OK || P->grow) return;
+    __shared__ int64_t sh[32];
+    const int tid = threadIdx.x;
+    for (int si = blockIdx.x; si < nslots; si += gridDim.x) {
+        const uint32_t ng = G.ngrp[si];   // uniform
+        if (ng == 0) continue;
+        const int64_t g0 = poff[si];
+        int64_t run = toff[si];
+        for (uint32_t base = 0; base < ng; base += blockDim.x) {
+            const uint32_t g = base + tid;
+            int64_t v[1] = {0}, ex[1], tot[1];
+            uint32_t h = 0, cnt = 0;
+            const bool have = g < ng && g0 + g < TASK_CAP;   // ids past the list's end were never listed
+            if (have) {
+                h = G.list[g0 + g];
+                cnt = G.cnt[h];
+                v[0] = (int64_t)cnt * G.ntask[h];
+            }
+            block_excl_scan_n<1>(v, ex, tot, sh);
+            if (have) {
+                G.off[h] = run + ex[0];
+                G.np[h] = cnt;
+                G.cnt[h] = 0;
+                G.tab[h] = GROUP_EMPTY;
+            }
+            run += tot[0];
+            __syncthreads();   // sh read before the next pass
+        }
+        if (tid == 0) {
+            G.ngrp[si] = 0;
+            Ctl* c = S[si].ctl;
+            if (run != toff[si] + c->n_tasks) atomicOr(&c->err, 4);   // groups disagree with the round
+        }
+    }
+}
+
+// the segment holding parent pi of a device-planned round (segments in parent order)
+__device__ __forceinline__ int find_parent_seg(const Plan* P, int64_t pi)
+{
+    int lo = 0, hi = P->nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P->seg[mid].first_parent <= pi) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The task records of a round that scores in one launch, by group: parent i
+// of group G writes its child rotation j at goff[G] + j P_G + i.
+__global__ void __launch_bounds__(256) emit_tasks_kernel(SearchDev* S, const Plan* P,
+                                                         const NodeRec* __restrict__ parents,
+                                                         const int32_t* __restrict__ pscore, GroupDev G,
+                                                         TaskRec* __restrict__ tasks, int32_t* __restrict__ tscore)
+{
+    pdl_wait();   // the groups' task ranges are in
+    pdl_trigger();
+    if (P->status != PLAN_OK || P->grow) return;
+    const int64_t np = min(P->n_parents, TASK_CAP);
+    for (int64_t pi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pi < np; pi += (int64_t)gridDim.x * blockDim.x) {
+        const Seg& g = P->seg[find_parent_seg(P, pi)];
+        const NodeRec nd = parents[pi];
+        const DevGrid& dg = S[g.sid].grid;
+        int32_t lo[3], ext[3];
+        const int32_t T = rot_children(dg, rl_level(nd.rl), rl_rot(nd.rl), lo, ext);
+        const uint32_t h = G.pslot[pi];
+        if (T <= 0 || h >= (uint32_t)GROUP_TABLE) continue;
+        const int64_t first = G.off[h] + G.pidx[pi], stride = (int64_t)G.np[h];
+        if (first < 0 || first + (int64_t)(T - 1) * stride >= P->n_tasks) {   // groups disagree with the round
+            atomicOr(&S[g.sid].ctl->err, 4);
+            continue;
+        }
+        write_tasks(dg, nd, lo, ext, 0, T, tasks, first, tscore, pscore[pi], stride);
+    }
 }
 
 // The current node array after select: popped nodes become the round's
 // parents (their first task in pfirst) and, when the round scores in one
-// launch, task records; kept nodes move to the other array; cleared nodes,
-// and those of failed or released searches, go.  Leaves of a popped leaf
-// bucket take part in the first lexmin pass (smallest translation key).
+// launch, join their rotation's group (group_entry; emit_tasks_kernel
+// writes the task records); kept nodes move to the other array; cleared
+// nodes, and those of failed or released searches, go.  Leaves of a popped
+// leaf bucket take part in the first lexmin pass (smallest translation key).
 __global__ void __launch_bounds__(256) compact_kernel(SearchDev* S, FrontDev F, LoopState* LS, const Plan* P,
                                                       NodeRec* __restrict__ parents, int64_t* __restrict__ pfirst,
-                                                      int32_t* __restrict__ pscore, TaskRec* __restrict__ tasks,
-                                                      int32_t* __restrict__ tscore, const int64_t* __restrict__ poff,
+                                                      int32_t* __restrict__ pscore, const int64_t* __restrict__ poff,
                                                       const int64_t* __restrict__ toff, unsigned long long* pcnt,
-                                                      unsigned long long* tcnt)
+                                                      unsigned long long* tcnt, GroupDev G)
 {
     pdl_wait();   // select's round plan is in
     pdl_trigger();
@@ -475,16 +613,36 @@ __global__ void __launch_bounds__(256) compact_kernel(SearchDev* S, FrontDev F, 
                 p = atomicAdd(&pcnt[sid], 1ull);
                 t0 = T ? atomicAdd(&tcnt[sid], (unsigned long long)T) : 0ull;
             }
+            bool grouping = false;
+            int64_t pi = 0;
             if (popped) {
                 if ((int64_t)p < c->n_parents && (int64_t)(t0 + T) <= c->n_tasks) {
-                    const int64_t pi = poff[sid] + (int64_t)p;
+                    pi = poff[sid] + (int64_t)p;
                     parents[pi] = nd;
                     pfirst[pi] = toff[sid] + (int64_t)t0;
                     pscore[pi] = score;
-                    if (emit && T > 0)
-                        write_tasks(S[sid].grid, nd, lo, ext, 0, T, tasks, toff[sid] + (int64_t)t0, tscore, score);
+                    grouping = emit && T > 0 && pi < TASK_CAP;
                 } else {
                     atomicOr(&c->err, 4);   // bucket counts disagree with the nodes: fail the search
+                }
+            }
+            // rotation groups: the warp's parents of one key join with one insert and one count
+            const unsigned long long gkey = grouping ? (((unsigned long long)sid << 32) | nd.rl) : GROUP_EMPTY;
+            const uint32_t peers = __match_any_sync(0xffffffffu, gkey);
+            const int gl = __ffs(peers) - 1;
+            uint32_t h = 0, gbase = 0;
+            if (grouping && lane == gl) {
+                h = group_entry(G, sid, nd.rl, T, poff[sid]);
+                if (h < (uint32_t)GROUP_TABLE) gbase = atomicAdd(&G.cnt[h], (uint32_t)__popc(peers));
+            }
+            h = __shfl_sync(0xffffffffu, h, gl);
+            gbase = __shfl_sync(0xffffffffu, gbase, gl);
+            if (grouping) {
+                if (h < (uint32_t)GROUP_TABLE) {
+                    G.pslot[pi] = h;
+                    G.pidx[pi] = gbase + __popc(peers & ((1u << lane) - 1u));
+                } else {
+                    atomicOr(&c->err, 4);   // more groups than parents: cannot happen
                 }
             }
         }
@@ -625,13 +783,26 @@ int Engine::init()
     BBS_TRY(get(&d_plan_, 1));
     BBS_TRY(get(&d_slots_, (size_t)max_slots_));
     BBS_TRY(get(&dense_, (size_t)DENSE_CAP));
+    BBS_TRY(get(&grp_.tab, (size_t)GROUP_TABLE));
+    BBS_TRY(get(&grp_.cnt, (size_t)GROUP_TABLE));
+    BBS_TRY(get(&grp_.ntask, (size_t)GROUP_TABLE));
+    BBS_TRY(get(&grp_.off, (size_t)GROUP_TABLE));
+    BBS_TRY(get(&grp_.np, (size_t)GROUP_TABLE));
+    BBS_TRY(get(&grp_.ngrp, (size_t)max_slots_));
+    BBS_TRY(get(&grp_.list, (size_t)TASK_CAP));
+    BBS_TRY(get(&grp_.pslot, (size_t)TASK_CAP));
+    BBS_TRY(get(&grp_.pidx, (size_t)TASK_CAP));
     BBS_CUDA_TRY(cudaMemsetAsync(d_ctl_, 0, sizeof(Ctl) * (size_t)max_slots_, st_));
     BBS_CUDA_TRY(cudaMemsetAsync(d_S_, 0, sizeof(SearchDev) * (size_t)max_slots_, st_));
     BBS_CUDA_TRY(cudaMemsetAsync(d_ls_, 0, sizeof(LoopState), st_));
     BBS_CUDA_TRY(cudaMemsetAsync(d_pcnt_, 0, sizeof(unsigned long long) * (size_t)max_slots_, st_));
     BBS_CUDA_TRY(cudaMemsetAsync(d_tcnt_, 0, sizeof(unsigned long long) * (size_t)max_slots_, st_));
     BBS_CUDA_TRY(cudaMemsetAsync(d_plan_, 0, sizeof(Plan), st_));
+
     BBS_CUDA_TRY(cudaMemsetAsync(dense_, 0, sizeof(int32_t) * (size_t)DENSE_CAP, st_));
+    BBS_CUDA_TRY(cudaMemsetAsync(grp_.tab, 0xFF, sizeof(unsigned long long) * (size_t)GROUP_TABLE, st_));
+    BBS_CUDA_TRY(cudaMemsetAsync(grp_.ngrp, 0, sizeof(uint32_t) * (size_t)max_slots_, st_));
+    BBS_CUDA_TRY(cudaMemsetAsync(grp_.cnt, 0, sizeof(uint32_t) * (size_t)GROUP_TABLE, st_));
     BBS_CUDA_TRY(cudaMallocHost((void**)&h_ctl_, sizeof(Ctl) * (size_t)max_slots_));
     BBS_CUDA_TRY(cudaMallocHost((void**)&h_off_, 2 * sizeof(int64_t) * (size_t)max_slots_));
     BBS_CUDA_TRY(cudaMallocHost((void**)&h_misc_, 4 * sizeof(int32_t)));
@@ -773,8 +944,9 @@ int Engine::resume_grown(std::vector<int>* finished)
 {
     BBS_TRY(grow_frontier());
     BBS_CUDA_TRY(launch_compact(st_));
+    BBS_CUDA_TRY(launch_group(st_));
     BBS_CUDA_TRY(launch_finalize(MODE_SEARCH, d_plan_, d_S_, tasks_, dense_, front_, d_ls_, nsm_ * 8, st_, true));
-    launches_ += 2;
+    launches_ += 4;
     BBS_CUDA_TRY(cudaGetLastError());
     BBS_TRY(read_ctl());
     mark_finished(finished);
@@ -1106,8 +1278,19 @@ cudaError_t Engine::launch_select(cudaStream_t s, cudaGraphConditionalHandle con
 cudaError_t Engine::launch_compact(cudaStream_t s, bool pdl)
 {
     return launch_pdl(compact_kernel, dim3(nsm_ * 4), dim3(256), s, pdl, d_S_, front_, d_ls_, (const Plan*)d_plan_,
-                      parents_, pfirst_, pscore_, tasks_, tscore_, (const int64_t*)d_poff_, (const int64_t*)d_toff_,
-                      d_pcnt_, d_tcnt_);
+                      parents_, pfirst_, pscore_, (const int64_t*)d_poff_, (const int64_t*)d_toff_, d_pcnt_, d_tcnt_,
+                      grp_);
+}
+
+// the round's rotation groups: task ranges, then the task records (both
+// return at once unless the round scores in one launch)
+cudaError_t Engine::launch_group(cudaStream_t s, bool pdl)
+{
+    cudaError_t e = launch_pdl(group_scan_kernel, dim3(max_slots_), dim3(1024), s, pdl, d_S_, max_slots_,
+                               (const Plan*)d_plan_, (const int64_t*)d_poff_, (const int64_t*)d_toff_, grp_);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(emit_tasks_kernel, dim3(nsm_ * 4), dim3(256), s, pdl, d_S_, (const Plan*)d_plan_,
+                      (const NodeRec*)parents_, (const int32_t*)pscore_, grp_, tasks_, tscore_);
 }
 
 // one host-driven iteration: select (+ plan), compaction and the second
@@ -1122,9 +1305,10 @@ int Engine::step(std::vector<int>* finished)
     BBS_CUDA_TRY(cudaMemcpyAsync(&d_plan_->iters, &h_plan_.iters, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, st_));
     BBS_CUDA_TRY(launch_select(st_, 0, 0));
     BBS_CUDA_TRY(launch_compact(st_));
+    BBS_CUDA_TRY(launch_group(st_));
     // the lexmin leaf must be complete when the control blocks are read below
     BBS_CUDA_TRY(launch_finalize(MODE_SEARCH, d_plan_, d_S_, tasks_, dense_, front_, d_ls_, nsm_ * 8, st_, true));
-    launches_ += 3;
+    launches_ += 5;
     BBS_CUDA_TRY(cudaGetLastError());
     // status, iterations, cap and the grow request of the plan
     BBS_CUDA_TRY(cudaMemcpyAsync(h_misc_, &d_plan_->status, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
@@ -1187,8 +1371,8 @@ int Engine::score_overflow()
     return flush();
 }
 
-// One iteration of the device loop: select (+ plan), compaction, scoring
-// (+ lexmin, survivors).  With pdl, each kernel after the first is a
+// One iteration of the device loop: select (+ plan), compaction, the
+// rotation groups' task ranges and records, scoring (+ lexmin, survivors).  With pdl, each kernel after the first is a
 // programmatic dependent launch: its CTAs are scheduled while its predecessor
 // drains and wait (pdl_wait) for it to complete, hiding the launch gaps.
 cudaError_t Engine::capture_body(cudaGraph_t body, cudaGraphConditionalHandle cond, bool pdl)
@@ -1200,6 +1384,7 @@ cudaError_t Engine::capture_body(cudaGraph_t body, cudaGraphConditionalHandle co
     if (e == cudaSuccess) {
         cudaError_t le = launch_select(cs, cond, 1);
         if (le == cudaSuccess) le = launch_compact(cs, pdl);
+        if (le == cudaSuccess) le = launch_group(cs, pdl);
         if (le == cudaSuccess)
             le = launch_branch(MODE_SEARCH, d_plan_, d_S_, tasks_, dense_, nsm_ * tune_.ctas_per_sm, cs, graph_bytes_,
                                pdl);
@@ -1280,7 +1465,7 @@ int Engine::iterate(int max_iters, std::vector<int>* finished)
     BBS_CUDA_TRY(cudaMemcpyAsync(h_misc_, &d_plan_->status, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
     BBS_TRY(read_ctl());
     const int32_t status = h_misc_[0];
-    launches_ += 4 * (int64_t)h_misc_[1];   // every iteration of the loop runs the body's 4 kernels
+    launches_ += 6 * (int64_t)h_misc_[1];   // every iteration of the loop runs the body's 6 kernels
     if (h_misc_[3]) {   // the last round waits for the frontier to grow; then it is scored from the host
         BBS_TRY(resume_grown(finished));
         if (status == PLAN_OK) return score_launch(MODE_SEARCH, nullptr, 0, 0);
@@ -1335,6 +1520,7 @@ int Engine::finalize(int i, bbs_result* out)
         r->children_scored = c.st_nodes;
         r->bound_violations = (int64_t)c.st_viol;
         r->bound_excess = c.st_excess;
+        r->rotations = (int64_t)c.st_rotpts;
         r->gathers += c.st_gathers;
         r->probes = r->nodes_scored * h.scan.k;
         r->best_score = c.best;

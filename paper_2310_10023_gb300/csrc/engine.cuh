@@ -104,6 +104,7 @@ class Engine {
     int score_overflow();
     cudaError_t launch_select(cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond);
     cudaError_t launch_compact(cudaStream_t s, bool pdl = false);
+    cudaError_t launch_group(cudaStream_t s, bool pdl = false);
     int read_ctl();
     int upload_cap();
     int grow_frontier();
@@ -135,6 +136,7 @@ class Engine {
     TaskRec* tasks_ = nullptr;     // the launch's tasks
     int32_t* tscore_ = nullptr;    // each task's parent score (the bound check of finalize)
     int32_t* pscore_ = nullptr;    // each popped node's score (tasks expanded in windows)
+    GroupDev grp_{};               // rotation groups of a round scored in one launch
     int64_t* d_poff_ = nullptr;
     int64_t* d_toff_ = nullptr;
     unsigned long long* d_pcnt_ = nullptr;

@@ -159,7 +159,7 @@ void default_ranges(const bbs_maps* m, bbs_ranges* rg)
 // whose FP32 estimate lies within 1e-6 of the chunk's largest estimate (the
 // two differ by under 4e-7 relative, so the FP64 maximum is among them).
 constexpr int PACK_THREADS = 256;
-constexpr int PACK_PER = SCAN_CHUNK / PACK_THREADS;
+constexpr int PACK_PER = (SCAN_CHUNK + PACK_THREADS - 1) / PACK_THREADS;
 __global__ void __launch_bounds__(PACK_THREADS) scan_pack_kernel(const float* __restrict__ xyz, int64_t k,
                                                                  float4* __restrict__ out, float4* __restrict__ cbox,
                                                                  float bound, unsigned long long* __restrict__ smax_bits,
@@ -173,9 +173,10 @@ __global__ void __launch_bounds__(PACK_THREADS) scan_pack_kernel(const float* __
     float px[PACK_PER], py[PACK_PER], pz[PACK_PER], ps[PACK_PER];
 #pragma unroll
     for (int j = 0; j < PACK_PER; ++j) {
-        const int64_t i = c0 + threadIdx.x + (int64_t)j * PACK_THREADS;
+        const int r = (int)threadIdx.x + j * PACK_THREADS;   // the point's place in the chunk
+        const int64_t i = c0 + r;
         ps[j] = -1.0f;
-        if (i < k) {
+        if (r < SCAN_CHUNK && i < k) {
             const float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
             out[i] = make_float4(x, y, z, 0.0f);
             if (!(fabsf(x) <= bound && fabsf(y) <= bound && fabsf(z) <= bound)) b = 1;   // also catches NaN

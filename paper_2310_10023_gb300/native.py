@@ -60,6 +60,7 @@ class Result(C.Structure):
         ("gathers", C.c_int64), ("launches", C.c_int64), ("score_launches", C.c_int64), ("score_ms", C.c_double),
         ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64),
         ("children_scored", C.c_int64), ("bound_violations", C.c_int64), ("bound_excess", C.c_double),
+        ("rotations", C.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -72,7 +73,7 @@ class Result(C.Structure):
             "gathers": self.gathers, "launches": self.launches, "score_launches": self.score_launches,
             "score_ms": self.score_ms, "h2d_bytes": self.h2d_bytes, "d2h_bytes": self.d2h_bytes,
             "children_scored": self.children_scored, "bound_violations": self.bound_violations,
-            "bound_excess": self.bound_excess,
+            "bound_excess": self.bound_excess, "rotations": self.rotations,
         }
 
 

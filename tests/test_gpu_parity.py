@@ -257,10 +257,11 @@ def test_branch_kernel_children_bit_exact(nv, room_pair, flags):
 
 @pytest.mark.parametrize("layout", [0, 2])
 def test_branch_kernel_chunk_edges(nv, layout):
-    """The fused kernel stages the scan in 2048-point chunks of 512-point
-    blocks, two points per thread: scans that end on, just before and just
-    after each of those boundaries (and the odd single point), under the
-    byte-grid and the hashed layout, score every child as the oracle does."""
+    """The fused kernel stages the scan in 1568-point chunks, seven points per
+    scoring thread (224 threads): scans that end on, just before and just
+    after the chunk and thread-row boundaries (and the single point), under
+    the byte-grid and the hashed layout, score every child as the oracle
+    does."""
     w = synth.WORKLOADS["room"]
     m = synth.make_map(w.scene)
     om = oracle.Maps(m, w.r, w.levels)
@@ -271,7 +272,7 @@ def test_branch_kernel_chunk_edges(nv, layout):
         nv.bbs_set_probe_layout(0)
     base, _ = synth.make_scan(1, 9, k=4200)
     nr, orr = _ranges(nv, w)
-    for k in (1, 2, 3, 511, 512, 513, 1024, 2047, 2048, 2049, 4097):
+    for k in (1, 2, 3, 223, 224, 225, 448, 449, 1567, 1568, 1569, 1792, 3135, 3136, 3137, 4097):
         sk = np.ascontiguousarray(base[:k])
         g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(sk), orr)
         parents = _random_nodes(g, np.random.default_rng(k), 24, w.levels)
@@ -282,6 +283,33 @@ def test_branch_kernel_chunk_edges(nv, layout):
         nodes, scores = nv.bbs_score_children(dm, sk, parents, nr)
         assert np.array_equal(nodes, np.concatenate([g.children(p) for p in parents])), k
         assert np.array_equal(scores, om.score_nodes(g, sk, nodes)), (layout, k)
+
+
+def test_branch_kernel_bit_exact_many_probes(nv, room_pair):
+    """About a hundred million probes of the fused kernel against the oracle,
+    element by element: 800 random parents over the room (levels 1 and 2,
+    the whole rotation range), a 4200-point scan over three chunks.  A
+    rotated coordinate rounded other than by the oracle's FP32 chain (for
+    instance a product fused into the following sum) moves a floor across
+    an integer about once in a few million probes, so a sample of this size
+    catches it."""
+    w, m, dm, om = room_pair
+    s, _ = synth.make_scan(1, 9, k=4200)
+    nr, orr = _ranges(nv, w)
+    g = oracle.Grid(w.r, w.levels, oracle.scan_dmax(s), orr)
+    parents = _random_nodes(g, np.random.default_rng(77), 800, w.levels)
+    parents[:, 6] = np.maximum(parents[:, 6], 1)
+    for i, p in enumerate(parents):
+        for a in range(3):
+            parents[i, 3 + a] = min(p[3 + a], g.N(p[6])[a] - 1)
+    nodes, scores = nv.bbs_score_children(dm, s, parents, nr)
+    assert len(nodes) * len(s) > 5e7
+    try:
+        want = om.score_nodes(g, s, nodes, mt=True)
+    except ImportError:   # no OpenMP build of the oracle
+        want = om.score_nodes(g, s, nodes)
+    bad = np.nonzero(scores != want)[0]
+    assert len(bad) == 0, [(nodes[b].tolist(), int(scores[b]), int(want[b])) for b in bad[:5]]
 
 
 # ---- search ----------------------------------------------------------------

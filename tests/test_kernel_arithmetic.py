@@ -15,34 +15,51 @@ KB = 0x4B400000   # bit pattern of 1.5 * 2^23
 
 def _lut_entry(v):
     # the scoring kernel's child counter increment (child_lut_entry): child
-    # i = jx + 2 jy + 4 jz of the 8-bit mask v at bit 4 (jx + 2 jz) + 16 jy
+    # i = jx + 2 jy + 4 jz of the 8-bit mask v at bits 4 i .. 4 i + 3
     out = 0
     for i in range(8):
-        jx, jy, jz = i & 1, (i >> 1) & 1, i >> 2
-        out |= ((v >> i) & 1) << (4 * (jx + 2 * jz) + 16 * jy)
+        out |= ((v >> i) & 1) << (4 * i)
     return out
 
 
 def test_child_counter_words():
-    """Summing the counter increments of up to 10 points (one run of one
-    scoring thread: at most ceil(1024 / 224) = 5 pairs of a 2048-point chunk)
-    never carries between 4-bit counters, and (acc >> 4 k) & 0x000F000F gives
-    the counts of children (jx, jz) = (k & 1, k >> 1) with jy = 0 in the low
-    and jy = 1 in the high 16-bit half, for every mix of masks (random mixes,
-    and the all-ones worst case)."""
-    assert 2 * -(-(2048 // 2) // 224) == 10
+    """A scoring thread counts at most 7 points of a task (a 1568-point chunk
+    over 224 scoring threads): summing their counter increments never
+    carries between 4-bit counters, the even and the odd children's
+    counters spread to bytes (acc & 0x0F0F0F0F, (acc >> 4) & 0x0F0F0F0F) sum
+    over a warp's 32 lanes without a carry between bytes (at most 224), and
+    byte q of the even word holds child 2 q, of the odd word child 2 q + 1;
+    then seven warps' bytes 0, 2 and 1, 3 summed in 16-bit fields stay
+    below 2^16.  Random mixes of masks and the all-ones worst case."""
+    assert 1568 // 224 == 7 and 1568 % 224 == 0
     rng = np.random.default_rng(1)
-    for trial in range(3000):
-        n = int(rng.integers(1, 11))
-        vs = [255] * 10 if trial == 0 else [int(x) for x in rng.integers(0, 256, n)]
-        acc = sum(_lut_entry(v) for v in vs)
-        assert acc < 1 << 32
-        for k in range(4):
-            jx, jz = k & 1, k >> 1
-            word = (acc >> (4 * k)) & 0x000F000F
-            for jy in (0, 1):
-                i = jx + 2 * jy + 4 * jz
-                assert (word >> (16 * jy)) & 0xFFFF == sum((v >> i) & 1 for v in vs)
+    for trial in range(300):
+        warps_ev, warps_od = [], []
+        counts = np.zeros(8, np.int64)
+        for w in range(7):
+            ev = od = 0
+            for lane in range(32):
+                n = 7 if trial == 0 else int(rng.integers(0, 8))
+                vs = [255] * n if trial == 0 else [int(x) for x in rng.integers(0, 256, n)]
+                acc = sum(_lut_entry(v) for v in vs)
+                assert acc < 1 << 32
+                for i in range(8):
+                    assert (acc >> (4 * i)) & 15 == sum((v >> i) & 1 for v in vs)
+                    counts[i] += sum((v >> i) & 1 for v in vs)
+                ev += acc & 0x0F0F0F0F
+                od += (acc >> 4) & 0x0F0F0F0F
+            assert ev < 1 << 32 and od < 1 << 32
+            for q in range(4):   # no carry between bytes: each byte is its own sum
+                assert (ev >> (8 * q)) & 255 <= 224 and (od >> (8 * q)) & 255 <= 224
+            warps_ev.append(ev)
+            warps_od.append(od)
+        for k, words in ((0, warps_ev), (1, warps_od)):
+            lo = sum(x & 0x00FF00FF for x in words)
+            hi = sum((x >> 8) & 0x00FF00FF for x in words)
+            assert lo < 1 << 32 and hi < 1 << 32
+            got = {k + 0: lo & 0xFFFF, k + 2: hi & 0xFFFF, k + 4: lo >> 16, k + 6: hi >> 16}
+            for i, c in got.items():
+                assert c == counts[i], (trial, i)
 
 
 def test_plane_mask_takes_the_children_bits():
@@ -80,19 +97,24 @@ def test_floored_key_bit_pattern():
 
 
 def test_folded_index_constant():
-    """((bx ny + by) nz + bz + cfix) mod 2^32 with cfix = -KB (ny nz + nz + 1)
-    equals the relative index (rx ny + ry) nz + rz when b = KB + r and the
-    relative index is below 2^31."""
+    """A run's base index of a point, ((bx ny + by) nz + bz) mod 2^32 with the
+    offset-free patterns b = KB + k (k = floor(q / 2^m), any sign), plus a
+    task's delta = ((ox ny + oy) nz + oz - KB (ny nz + nz + 1)) mod 2^32 (any
+    signs of o), equals the byte index ((kx + ox) ny + (ky + oy)) nz + (kz + oz)
+    of key k + o whenever k + o lies in the grid (index below 2^31)."""
     rng = np.random.default_rng(1)
     M = 1 << 32
     for _ in range(3000):
         ny, nz = int(rng.integers(2, 4000)), int(rng.integers(2, 4000))
         nx = int(rng.integers(2, max(3, (1 << 31) // (ny * nz))))
-        r = [int(rng.integers(0, n)) for n in (nx, ny, nz)]
-        b = [KB + x for x in r]
-        cfix = (-KB * (ny * nz + nz + 1)) % M
-        got = (((b[0] * ny + b[1]) % M * nz + b[2]) % M + cfix) % M
-        assert got == (r[0] * ny + r[1]) * nz + r[2]
+        r = [int(rng.integers(0, n)) for n in (nx, ny, nz)]          # the key in the grid
+        o = [int(rng.integers(-(1 << 21), 1 << 21)) for _ in range(3)]   # the task's offset
+        k = [r[i] - o[i] for i in range(3)]                              # the rotated point's key
+        assert all(abs(x) < 1 << 22 for x in k)
+        b = [(KB + x) % M for x in k]
+        base = ((b[0] * ny + b[1]) % M * nz + b[2]) % M
+        delta = ((o[0] * ny + o[1]) * nz + o[2] - KB * (ny * nz + nz + 1)) % M
+        assert (base + delta) % M == (r[0] * ny + r[1]) * nz + r[2]
 
 
 def _rot(ang, r):
@@ -115,7 +137,7 @@ def test_inside_bound_has_no_false_positive():
         r = float(rng.choice([0.05, 0.2, 0.5, 1.0]))
         m = int(rng.integers(0, 8))
         A = _rot(rng.uniform(-np.pi, np.pi, 3) * rng.choice([1.0, 0.05]), r)
-        n = int(rng.integers(1, 2049))
+        n = int(rng.integers(1, 1569))
         P = (rng.uniform(-1, 1, (n, 3)) * rng.uniform(0.1, 60.0, 3) + rng.uniform(-20, 20, 3)).astype(f32)
         lo3, hi3 = P.min(0), P.max(0)
         q = ((A[:, 0][None] * P[:, 0:1]).astype(f32) + (A[:, 1][None] * P[:, 1:2]).astype(f32)).astype(f32)
