@@ -243,18 +243,20 @@ constexpr int NSLOT = 32;   // slices per round, one per lane of the describing 
 // there, score, and arrive on EMPTY + b when they no longer read the buffer;
 // CONS synchronizes the scoring warps alone
 constexpr int BAR_FULL = 1, BAR_EMPTY = 3, BAR_CONS = 5;
-constexpr int64_t SMALL_LAUNCH = 0;    // slices per CTA below which a launch is split statically
 __device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 __device__ __forceinline__ void bar_arrive(int id, int n) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
 // The CTA's static range [cur, end) of the launch's slices: the first
 // static_pm / 1000 of them in equal shares, the rest handed out later in
-// shrinking grabs.  A launch of fewer than SMALL_LAUNCH slices per CTA (about
-// two rounds each) is split statically: there a grab's round costs more than
-// the balance it buys.
-__device__ __forceinline__ int64_t static_slices(const Plan* P, int64_t n_slices)
+// shrinking grabs.  (Weighing a scan's short last chunk by its points
+// measured slower: a slice's description and reduction cost the same
+// whatever its points.)
+__device__ __forceinline__ void static_range(const Plan* P, int64_t n_slices, int64_t& cur, int64_t& end,
+                                             int64_t& n_static)
 {
-    return n_slices < SMALL_LAUNCH * (int64_t)gridDim.x ? n_slices : n_slices * P->static_pm / 1000;
+    n_static = n_slices * P->static_pm / 1000;
+    cur = n_static * blockIdx.x / gridDim.x;
+    end = n_static * (blockIdx.x + 1) / gridDim.x;
 }
 
 // The search and point chunk of slice x (false when its segment is empty):
@@ -280,9 +282,9 @@ __device__ __noinline__ void describe_rounds(Plan* __restrict__ P, const SearchD
 {
     const int lane = threadIdx.x & 31;
     // the static range first, then grabs of at least grab_min as CTAs finish
-    const int64_t n_static = static_slices(P, n_slices);
+    int64_t cur, end, n_static;
+    static_range(P, n_slices, cur, end, n_static);
     const int64_t grab_min = P->grab_min > 0 ? P->grab_min : 1;
-    int64_t cur = n_static * blockIdx.x / gridDim.x, end = n_static * (blockIdx.x + 1) / gridDim.x;
     int gi = -1;
     // scan points rotated for the current search (lane 0), added to its control block on a change of search
     // (searches scored outside the engine -- bbs_score_children, the host queue -- have none)
@@ -569,8 +571,8 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
         bar_sync(BAR_CONS, NCONS);   // staged points visible
     };
     {   // the chunk of the CTA's first static slice, staged while warp 7 describes
-        const int64_t ns = static_slices(P, n_slices);
-        const int64_t cur = ns * blockIdx.x / gridDim.x, end = ns * (blockIdx.x + 1) / gridDim.x;
+        int64_t cur, end, ns;
+        static_range(P, n_slices, cur, end, ns);
         int32_t sid, c;
         if (cur < end && slice_chunk(P, cur, sid, c)) stage(sid, c);
     }
