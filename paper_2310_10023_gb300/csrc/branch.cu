@@ -101,14 +101,6 @@ __host__ __device__ constexpr uint32_t child_lut_entry(uint32_t v)
 // the scoring CTA: warps 0..6 score (NCONS threads), warp 7 describes the rounds
 constexpr int NCONS = 224;
 
-// The 8-bit child mask of one point from a byte grid (LAYOUT_BYTES): relative
-// keys clamped to the empty key past the box, one byte load.
-__device__ __forceinline__ uint32_t bytes_mask(const LevelView& L, uint32_t bx, uint32_t by, uint32_t bz, uint32_t ex,
-                                               uint32_t ey, uint32_t ez)
-{
-    const uint32_t rx = min(bx ^ KB, ex), ry = min(by ^ KB, ey), rz = min(bz ^ KB, ez);
-    return __ldg(reinterpret_cast<const uint8_t*>(L.slots) + ((rx * L.nby + ry) * L.nbz + rz));
-}
 // the 8-bit child mask from the two plane words of the brick layouts
 // (bits {0, 1, 5, 6}: children jx + 5 jy of the z = 0 and z = 1 planes)
 __device__ __forceinline__ uint32_t planes_mask(uint32_t w0, uint32_t w1)
@@ -116,8 +108,8 @@ __device__ __forceinline__ uint32_t planes_mask(uint32_t w0, uint32_t w1)
     return (w0 & 3u) | ((w0 >> 3) & 0xCu) | ((w1 & 3u) << 4) | ((w1 << 1) & 0xC0u);
 }
 
-// One task over points [plo, phi) of the staged chunk (the clamped path:
-// every point rotated and floored with the task's own offsets); thread t of
+// One task of a brick layout over points [plo, phi) of the staged chunk:
+// every point rotated and floored with the task's own offsets; thread t of
 // the nt scoring threads takes points plo + t, plo + t + nt, ...  The floor,
 // the level shift and the key offset are one fma.rm of q (see KB).
 template <int LAYOUT>
@@ -125,21 +117,14 @@ __device__ __forceinline__ void score_run(const float4* sp, int plo, int phi, co
                                           float s, float cx, float cy, float cz, const uint32_t* lut, uint32_t& acc,
                                           int t, int nt)
 {
-    const uint32_t ex = L.rmax[0] + 1u, ey = L.rmax[1] + 1u, ez = L.rmax[2] + 1u;   // bytes: the empty key past the box
     for (int p = plo + t; p < phi; p += nt) {
         const float4 v4 = sp[p];
         const uint32_t bx = key_bits(rot_q(A, v4.x, v4.y, v4.z), s, cx);
         const uint32_t by = key_bits(rot_q(A + 3, v4.x, v4.y, v4.z), s, cy);
         const uint32_t bz = key_bits(rot_q(A + 6, v4.x, v4.y, v4.z), s, cz);
-        uint32_t v;
-        if (LAYOUT == LAYOUT_BYTES) {
-            v = bytes_mask(L, bx, by, bz, ex, ey, ez);
-        } else {
-            uint32_t w0, w1;
-            child_bits<LAYOUT>(L, bx, by, bz, w0, w1);
-            v = planes_mask(w0, w1);
-        }
-        acc += lut[v];
+        uint32_t w0, w1;
+        child_bits<LAYOUT>(L, bx, by, bz, w0, w1);
+        acc += lut[planes_mask(w0, w1)];
     }
 }
 
@@ -227,8 +212,10 @@ struct __align__(16) RunDesc {
 
 // One slice of a round: a task over its run's chunk.
 struct __align__(16) SlotDesc {
-    float kc[3];      // per-axis 1.5 * 2^23 + translation (- box origin) (the clamped path)
+    float kc[3];      // per-axis 1.5 * 2^23 + translation (- box origin) (brick layouts)
     uint32_t pad;
+    uint32_t ok[3];   // byte grids near the edge: per-axis translation (- box origin) - KB, mod 2^32
+    uint32_t pad2;
     int64_t task;     // launch-local task index
     uint32_t delta;   // byte grids: index offset of the translation, with the folded pattern constant
     int32_t inside;   // every point of the chunk lands inside the level's byte grid
@@ -412,6 +399,7 @@ __device__ __noinline__ void describe_rounds(Plan* __restrict__ P, const SearchD
                 o[i] = v;
                 const float cf = 12582912.0f + (float)v;   // exact: an integer below 2^24
                 e.kc[i] = cf;
+                e.ok[i] = (uint32_t)v - KB;   // pattern KB + k plus this: the relative key k + v
                 // inside: every key of the chunk in [0, rmax_i + 1] (sums of integers below 2^24: exact)
                 in = in && klo[i] + (float)v >= 0.0f && khi[i] + (float)v <= (float)L.rmax[i] + 1.0f;
             }
@@ -423,7 +411,8 @@ __device__ __noinline__ void describe_rounds(Plan* __restrict__ P, const SearchD
             e.delta = ((uint32_t)o[0] * L.nby + (uint32_t)o[1]) * L.nbz + (uint32_t)o[2] -
                       KB * (L.nby * L.nbz + L.nbz + 1u);
         }
-        // scan points rotated by this round: a byte-grid run's shared rotation and every own one
+        // scan points rotated by this round: a byte-grid run rotates once, and once more for its slices
+        // near the grid's edge; a brick-layout run once per slice
         const uint32_t owns = __ballot_sync(0xffffffffu, own);
         uint32_t rp = 0;   // at most NSLOT + 1 rotations of PCHUNK points per round
         if (start) {
@@ -431,8 +420,8 @@ __device__ __noinline__ void describe_rounds(Plan* __restrict__ P, const SearchD
             const int nr = (above ? __ffs(above) + lane : cnt) - lane;   // the run's slices
             const uint32_t rmask = (nr >= 32 ? 0xFFFFFFFFu : ((1u << nr) - 1u)) << lane;
             const int npts = min(PCHUNK, S.K - (int32_t)c * PCHUNK);
-            const bool shared_rot = S.maps[m].layout == LAYOUT_BYTES;
-            rp = (uint32_t)npts * ((shared_rot ? 1u : 0u) + (uint32_t)__popc(owns & rmask));
+            const uint32_t nown = (uint32_t)__popc(owns & rmask);
+            rp = (uint32_t)npts * (S.maps[m].layout == LAYOUT_BYTES ? 1u + (nown ? 1u : 0u) : nown);
         }
         rp = __reduce_add_sync(0xffffffffu, rp);
         if (g->sid != rot_sid) {
@@ -497,16 +486,43 @@ __device__ __forceinline__ uint32_t gather_inside(const uint32_t (&base)[PPT], u
     return acc;
 }
 
-// One slice near its byte grid's edge: every point rotated and floored with
-// the task's own offsets and clamped per axis.
-__device__ __forceinline__ uint32_t edge_counts(const float4* sp, int n, const LevelView& L, const RunDesc& d,
-                                                const SlotDesc& e, const uint32_t* lut, int tid)
+// The floored level-m key patterns of this thread's points under run d's
+// rotation, per axis (KB + floor(q / 2^m), see KB): the slices of the run
+// near the grid's edge clamp each axis on its own.
+__device__ __forceinline__ void rotate_keys3(const float4* sp, const RunDesc& d, uint32_t (&kx)[PPT],
+                                             uint32_t (&ky)[PPT], uint32_t (&kz)[PPT], int tid)
 {
     float A[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) A[k] = d.a[k];
+    for (int e = 0; e < 9; ++e) A[e] = d.a[e];
+    const float s = d.s, c0 = 12582912.0f;
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+        const float4 v = sp[tid + i * NCONS];
+        kx[i] = key_bits(rot_q(A, v.x, v.y, v.z), s, c0);
+        ky[i] = key_bits(rot_q(A + 3, v.x, v.y, v.z), s, c0);
+        kz[i] = key_bits(rot_q(A + 6, v.x, v.y, v.z), s, c0);
+    }
+}
+
+// One slice near its byte grid's edge: each point's relative key k + v per
+// axis (pattern + ok, mod 2^32: a negative key wraps past every bound) is
+// clamped to the empty key past the box (rmax + 1), then one byte load.
+// Points i >= nv of this thread lie past the chunk's end: masked off.
+__device__ __forceinline__ uint32_t edge_counts(const uint32_t (&kx)[PPT], const uint32_t (&ky)[PPT],
+                                                const uint32_t (&kz)[PPT], const SlotDesc& e, const LevelView& L,
+                                                const uint32_t* lut, int nv)
+{
+    const uint8_t* __restrict__ cell = reinterpret_cast<const uint8_t*>(L.slots);
+    const uint32_t ex = L.rmax[0] + 1u, ey = L.rmax[1] + 1u, ez = L.rmax[2] + 1u;
+    const uint32_t ox = e.ok[0], oy = e.ok[1], oz = e.ok[2], ny = L.nby, nz = L.nbz;
     uint32_t acc = 0;
-    score_run<LAYOUT_BYTES>(sp, 0, n, L, A, d.s, e.kc[0], e.kc[1], e.kc[2], lut, acc, tid, NCONS);
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+        const uint32_t rx = min(kx[i] + ox, ex), ry = min(ky[i] + oy, ey), rz = min(kz[i] + oz, ez);
+        const uint32_t inc = lut[__ldg(cell + ((rx * ny + ry) * nz + rz))];
+        acc += i < nv ? inc : 0u;
+    }
     return acc;
 }
 
@@ -608,9 +624,16 @@ __global__ void __launch_bounds__(256, BRANCH_CTAS_PER_SM)
                         }
                     }
                 }
-                for (int t = t0; t < t1; ++t) {   // near the grid's edge: per-axis clamps
-                    const SlotDesc& e = sd[b][t];
-                    if (!e.inside) reduce_counts(edge_counts(sp, n, Lv, d, e, lut, tid), red[b][t][warp], lane);
+                bool edge = false;   // uniform: the slot descriptors are shared
+                for (int t = t0; t < t1 && !edge; ++t) edge = !sd[b][t].inside;
+                if (edge) {   // near the grid's edge: the run's keys per axis, each clamped
+                    uint32_t kx[PPT], ky[PPT], kz[PPT];
+                    rotate_keys3(sp, d, kx, ky, kz, tid);
+                    const int nv = n > tid ? (n - tid + NCONS - 1) / NCONS : 0;
+                    for (int t = t0; t < t1; ++t) {
+                        const SlotDesc& e = sd[b][t];
+                        if (!e.inside) reduce_counts(edge_counts(kx, ky, kz, e, Lv, lut, nv), red[b][t][warp], lane);
+                    }
                 }
             } else {   // brick layouts: every slice rotates and probes on its own
                 float A[9];
