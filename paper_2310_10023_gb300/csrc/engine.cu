@@ -409,9 +409,10 @@ __device__ __forceinline__ void write_tasks(const DevGrid& g, const NodeRec& nd,
 // rotation j and the group's parent i.  Groups are found by open addressing
 // over (search, rl) keys, the entry naming the group: compact_kernel joins
 // each parent to its group (one insert and one count per group and warp);
-// group_scan_kernel gives each search's groups their task ranges (in the
-// search's range at toff) and empties their entries; emit_tasks_kernel
-// writes the task records.
+// group_scan_search gives each search's groups their task ranges (in the
+// search's range at toff) and empties their entries -- in the compaction's
+// last CTA for a one-slot engine, else in group_scan_kernel;
+// emit_tasks_kernel writes the task records.
 
 __device__ __forceinline__ uint32_t group_hash(unsigned long long key)
 {
@@ -448,9 +449,47 @@ __device__ uint32_t group_entry(const GroupDev& G, int sid, uint32_t rl, int32_t
     return (uint32_t)GROUP_TABLE;
 }
 
-// One CTA per search slot: the task ranges of the search's groups in its
-// range at toff (exclusive scan of P_G T_G in group-id order), the groups'
-// parent counts for the emission, and the table emptied for the next round.
+// One search's groups (by the calling CTA): their task ranges in the
+// search's range at toff (exclusive scan of P_G T_G in group-id order), their
+// parent counts for the emission, and their entries emptied for the next
+// round; the sum is checked against the search's task count.
+__device__ void group_scan_search(SearchDev* S, int si, const int64_t* __restrict__ poff,
+                                  const int64_t* __restrict__ toff, const GroupDev& G, int64_t* sh)
+{
+    const int tid = threadIdx.x;
+    const uint32_t ng = G.ngrp[si];   // uniform
+    if (ng == 0) return;
+    const int64_t g0 = poff[si];
+    int64_t run = toff[si];
+    for (uint32_t base = 0; base < ng; base += blockDim.x) {
+        const uint32_t g = base + tid;
+        int64_t v[1] = {0}, ex[1], tot[1];
+        uint32_t h = 0, cnt = 0;
+        const bool have = g < ng && g0 + g < TASK_CAP;   // ids past the list's end were never listed
+        if (have) {
+            h = G.list[g0 + g];
+            cnt = G.cnt[h];
+            v[0] = (int64_t)cnt * G.ntask[h];
+        }
+        block_excl_scan_n<1>(v, ex, tot, sh);
+        if (have) {
+            G.off[h] = run + ex[0];
+            G.np[h] = cnt;
+            G.cnt[h] = 0;
+            G.tab[h] = GROUP_EMPTY;
+        }
+        run += tot[0];
+        __syncthreads();   // sh read before the next pass
+    }
+    if (tid == 0) {
+        G.ngrp[si] = 0;
+        Ctl* c = S[si].ctl;
+        if (run != toff[si] + c->n_tasks) atomicOr(&c->err, 4);   // groups disagree with the round
+    }
+}
+
+// One CTA per search slot: group_scan_search of each (engines with several
+// slots; a one-slot engine's compaction does it in its last CTA).
 __global__ void __launch_bounds__(1024) group_scan_kernel(SearchDev* S, int nslots, const Plan* P,
                                                           const int64_t* __restrict__ poff,
                                                           const int64_t* __restrict__ toff, GroupDev G)
@@ -459,38 +498,7 @@ __global__ void __launch_bounds__(1024) group_scan_kernel(SearchDev* S, int nslo
     pdl_trigger();
     if (P->status != PLAN_OK || P->grow) return;
     __shared__ int64_t sh[32];
-    const int tid = threadIdx.x;
-    for (int si = blockIdx.x; si < nslots; si += gridDim.x) {
-        const uint32_t ng = G.ngrp[si];   // uniform
-        if (ng == 0) continue;
-        const int64_t g0 = poff[si];
-        int64_t run = toff[si];
-        for (uint32_t base = 0; base < ng; base += blockDim.x) {
-            const uint32_t g = base + tid;
-            int64_t v[1] = {0}, ex[1], tot[1];
-            uint32_t h = 0, cnt = 0;
-            const bool have = g < ng && g0 + g < TASK_CAP;   // ids past the list's end were never listed
-            if (have) {
-                h = G.list[g0 + g];
-                cnt = G.cnt[h];
-                v[0] = (int64_t)cnt * G.ntask[h];
-            }
-            block_excl_scan_n<1>(v, ex, tot, sh);
-            if (have) {
-                G.off[h] = run + ex[0];
-                G.np[h] = cnt;
-                G.cnt[h] = 0;
-                G.tab[h] = GROUP_EMPTY;
-            }
-            run += tot[0];
-            __syncthreads();   // sh read before the next pass
-        }
-        if (tid == 0) {
-            G.ngrp[si] = 0;
-            Ctl* c = S[si].ctl;
-            if (run != toff[si] + c->n_tasks) atomicOr(&c->err, 4);   // groups disagree with the round
-        }
-    }
+    for (int si = blockIdx.x; si < nslots; si += gridDim.x) group_scan_search(S, si, poff, toff, G, sh);
 }
 
 // the segment holding parent pi of a device-planned round (segments in parent order)
@@ -543,7 +551,8 @@ __global__ void __launch_bounds__(256) compact_kernel(SearchDev* S, FrontDev F, 
                                                       NodeRec* __restrict__ parents, int64_t* __restrict__ pfirst,
                                                       int32_t* __restrict__ pscore, const int64_t* __restrict__ poff,
                                                       const int64_t* __restrict__ toff, unsigned long long* pcnt,
-                                                      unsigned long long* tcnt, GroupDev G)
+                                                      unsigned long long* tcnt, GroupDev G, int nslots,
+                                                      int scan_here, uint32_t* done)
 {
     pdl_wait();   // select's round plan is in
     pdl_trigger();
@@ -655,6 +664,23 @@ __global__ void __launch_bounds__(256) compact_kernel(SearchDev* S, FrontDev F, 
             const unsigned long long pos = base + __popc(ball & ((1u << lane) - 1u));
             F.nodes[nxt][pos] = nd;
             F.keys[nxt][pos] = key;
+        }
+    }
+    // a one-slot engine: the last CTA to finish gives the groups their task
+    // ranges (the launch the group scan kernel would take is saved)
+    if (scan_here && emit) {   // uniform
+        __shared__ int s_last;
+        __shared__ int64_t sh[32];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            for (int si = 0; si < nslots; ++si) group_scan_search(S, si, poff, toff, G, sh);
+            if (threadIdx.x == 0) *done = 0u;
         }
     }
 }
@@ -792,6 +818,7 @@ int Engine::init()
     BBS_TRY(get(&grp_.list, (size_t)TASK_CAP));
     BBS_TRY(get(&grp_.pslot, (size_t)TASK_CAP));
     BBS_TRY(get(&grp_.pidx, (size_t)TASK_CAP));
+    BBS_TRY(get(&cdone_, 1));
     BBS_CUDA_TRY(cudaMemsetAsync(d_ctl_, 0, sizeof(Ctl) * (size_t)max_slots_, st_));
     BBS_CUDA_TRY(cudaMemsetAsync(d_S_, 0, sizeof(SearchDev) * (size_t)max_slots_, st_));
     BBS_CUDA_TRY(cudaMemsetAsync(d_ls_, 0, sizeof(LoopState), st_));
@@ -803,6 +830,7 @@ int Engine::init()
     BBS_CUDA_TRY(cudaMemsetAsync(grp_.tab, 0xFF, sizeof(unsigned long long) * (size_t)GROUP_TABLE, st_));
     BBS_CUDA_TRY(cudaMemsetAsync(grp_.ngrp, 0, sizeof(uint32_t) * (size_t)max_slots_, st_));
     BBS_CUDA_TRY(cudaMemsetAsync(grp_.cnt, 0, sizeof(uint32_t) * (size_t)GROUP_TABLE, st_));
+    BBS_CUDA_TRY(cudaMemsetAsync(cdone_, 0, sizeof(uint32_t), st_));
     BBS_CUDA_TRY(cudaMallocHost((void**)&h_ctl_, sizeof(Ctl) * (size_t)max_slots_));
     BBS_CUDA_TRY(cudaMallocHost((void**)&h_off_, 2 * sizeof(int64_t) * (size_t)max_slots_));
     BBS_CUDA_TRY(cudaMallocHost((void**)&h_misc_, 4 * sizeof(int32_t)));
@@ -946,7 +974,7 @@ int Engine::resume_grown(std::vector<int>* finished)
     BBS_CUDA_TRY(launch_compact(st_));
     BBS_CUDA_TRY(launch_group(st_));
     BBS_CUDA_TRY(launch_finalize(MODE_SEARCH, d_plan_, d_S_, tasks_, dense_, front_, d_ls_, nsm_ * 8, st_, true));
-    launches_ += 4;
+    launches_ += max_slots_ > 1 ? 4 : 3;
     BBS_CUDA_TRY(cudaGetLastError());
     BBS_TRY(read_ctl());
     mark_finished(finished);
@@ -1279,16 +1307,18 @@ cudaError_t Engine::launch_compact(cudaStream_t s, bool pdl)
 {
     return launch_pdl(compact_kernel, dim3(nsm_ * 4), dim3(256), s, pdl, d_S_, front_, d_ls_, (const Plan*)d_plan_,
                       parents_, pfirst_, pscore_, (const int64_t*)d_poff_, (const int64_t*)d_toff_, d_pcnt_, d_tcnt_,
-                      grp_);
+                      grp_, max_slots_, max_slots_ == 1 ? 1 : 0, cdone_);
 }
 
 // the round's rotation groups: task ranges, then the task records (both
 // return at once unless the round scores in one launch)
 cudaError_t Engine::launch_group(cudaStream_t s, bool pdl)
 {
-    cudaError_t e = launch_pdl(group_scan_kernel, dim3(max_slots_), dim3(1024), s, pdl, d_S_, max_slots_,
-                               (const Plan*)d_plan_, (const int64_t*)d_poff_, (const int64_t*)d_toff_, grp_);
-    if (e != cudaSuccess) return e;
+    if (max_slots_ > 1) {   // a one-slot engine's compaction scans its groups itself
+        cudaError_t e = launch_pdl(group_scan_kernel, dim3(max_slots_), dim3(1024), s, pdl, d_S_, max_slots_,
+                                   (const Plan*)d_plan_, (const int64_t*)d_poff_, (const int64_t*)d_toff_, grp_);
+        if (e != cudaSuccess) return e;
+    }
     return launch_pdl(emit_tasks_kernel, dim3(nsm_ * 4), dim3(256), s, pdl, d_S_, (const Plan*)d_plan_,
                       (const NodeRec*)parents_, (const int32_t*)pscore_, grp_, tasks_, tscore_);
 }
@@ -1308,7 +1338,7 @@ int Engine::step(std::vector<int>* finished)
     BBS_CUDA_TRY(launch_group(st_));
     // the lexmin leaf must be complete when the control blocks are read below
     BBS_CUDA_TRY(launch_finalize(MODE_SEARCH, d_plan_, d_S_, tasks_, dense_, front_, d_ls_, nsm_ * 8, st_, true));
-    launches_ += 5;
+    launches_ += max_slots_ > 1 ? 5 : 4;
     BBS_CUDA_TRY(cudaGetLastError());
     // status, iterations, cap and the grow request of the plan
     BBS_CUDA_TRY(cudaMemcpyAsync(h_misc_, &d_plan_->status, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
@@ -1465,7 +1495,7 @@ int Engine::iterate(int max_iters, std::vector<int>* finished)
     BBS_CUDA_TRY(cudaMemcpyAsync(h_misc_, &d_plan_->status, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
     BBS_TRY(read_ctl());
     const int32_t status = h_misc_[0];
-    launches_ += 6 * (int64_t)h_misc_[1];   // every iteration of the loop runs the body's 6 kernels
+    launches_ += (max_slots_ > 1 ? 6 : 5) * (int64_t)h_misc_[1];   // the loop body's kernels per iteration
     if (h_misc_[3]) {   // the last round waits for the frontier to grow; then it is scored from the host
         BBS_TRY(resume_grown(finished));
         if (status == PLAN_OK) return score_launch(MODE_SEARCH, nullptr, 0, 0);

@@ -137,6 +137,7 @@ class Engine {
     int32_t* tscore_ = nullptr;    // each task's parent score (the bound check of finalize)
     int32_t* pscore_ = nullptr;    // each popped node's score (tasks expanded in windows)
     GroupDev grp_{};               // rotation groups of a round scored in one launch
+    uint32_t* cdone_ = nullptr;    // the compaction's finished CTAs (its last one scans a one-slot round's groups)
     int64_t* d_poff_ = nullptr;
     int64_t* d_toff_ = nullptr;
     unsigned long long* d_pcnt_ = nullptr;
