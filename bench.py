@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import math
 import os
@@ -603,9 +604,14 @@ def run_served_sweep(nv, torch, rates=(20, 50, 100, 200, 500, 1000), n=128, max_
 
 
 def _kernel_hash():
+    """Hash of the scoring kernel's source files with their comments and
+    blank lines removed (a comment edit keeps a capture valid)."""
     h = hashlib.sha256()
     for f in ("branch.cu", "bbs_internal.cuh", "branch.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2310_10023_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_2310_10023_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in src.splitlines()]
+        h.update("\n".join(ln for ln in lines if ln.strip()).encode())
     return h.hexdigest()[:16]
 
 

@@ -12,7 +12,7 @@
 // and task that answers all 8 translational children 2c + j (Sec. III-C
 // layout, see bbs_internal.cuh), the task's translation being an integer
 // offset of the key.  The 8 child counts are kept as 4-bit fields of one
-// register, reduced per warp with redux.sync on 16-bit fields, summed across
+// register, summed per warp with redux.sync on byte fields, then across
 // warps in shared memory, and added to a dense (task, child) score array.
 // The survivor pass then keeps children scoring above their search's best.
 #include "branch.cuh"
