@@ -15,13 +15,17 @@
 //            parent and task ranges of every search and the scoring launch's
 //            slice map; it ends the device loop when the round is empty or too
 //            large for one launch, or after the iteration cap.
-//   compact  the current node array: popped nodes become parents and tasks
-//            (their rotational children), kept ones move to the other array,
+//   compact  the current node array: popped nodes become parents and join
+//            their rotation group (parents of one level and rotation share
+//            their rotational children), kept ones move to the other array,
 //            cleared ones go; a popped leaf bucket's leaves give the lexmin key
-//   score    (branch.cu) every child of every task (the kernel forms each
-//            task's rotation rows); then the lexmin rotation of a popped leaf
-//            bucket, and survivors above best appended to the other array
-//            with their bucket counts
+//   groups   each group its task range, then the task records (the
+//            rotational children) written so that one child rotation's tasks
+//            are consecutive
+//   score    (branch.cu) every child of every task (the kernel forms a run's
+//            rotation rows once for the tasks that share them); then the
+//            lexmin rotation of a popped leaf bucket, and survivors above best
+//            appended to the other array with their bucket counts
 // Only popping a leaf changes a search's best, so how its batch is split into
 // launches, and which other searches share them, cannot change its result;
 // node order inside F is free.
