@@ -186,3 +186,24 @@ def test_exponent_range_test():
     for v in vals:
         for q in (float(v), -float(v)):
             assert by_value(q) == by_bits(q), q
+
+
+def test_edge_key_clamp_from_shared_patterns():
+    """Slices near the grid's edge share their run's offset-free patterns
+    b = KB + k (|k| < 2^19) and add o - KB (|o| <= 2^21) mod 2^32 per axis:
+    the sum is the relative key k + o when that is in [0, rmax + 1], and any
+    key outside (negative keys wrap past 2^31) is clamped by min to rmax + 1,
+    the empty key past the box -- the same key as clamping k + o directly."""
+    rng = np.random.default_rng(3)
+    M = 1 << 32
+    for _ in range(20000):
+        k = int(rng.integers(-(1 << 19) + 1, 1 << 19))
+        o = int(rng.integers(-(1 << 21), (1 << 21) + 1))
+        rmax = int(rng.integers(0, 1 << 20))
+        if rng.random() < 0.5:   # keys near the box
+            o = int(rng.integers(-k - 3, -k + rmax + 4))
+        r = ((KB + k) % M + (o - KB) % M) % M
+        got = min(r, rmax + 1)
+        key = k + o
+        want = key if 0 <= key <= rmax + 1 else rmax + 1
+        assert got == want, (k, o, rmax)
